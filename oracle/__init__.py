@@ -1,0 +1,282 @@
+"""FP64 CPU oracle for the periodic single-hop energy change and the KMC step.
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the CPU-baseline
+leg of the benchmark are the only callers.  The product path (the CUDA
+library and its Python binding) never imports this package, and this package
+never imports the product.  Both sides share only the seeded input generators
+in ``workloads``, which hold none of the method's arithmetic.
+
+Definition followed (Sec. 2.2.1 periodic images, Sec. 2.2.2 / App. B boundary
+at infinity, Sec. 3.1 periodic near/far split of the hop energy): the tinfoil
+Ewald energy of a neutral cubic cell,
+
+    U  = 1/2 sum_i sum_j sum'_n q_i q_j / |r_i - r_j + n a|,
+    dU = q_k [phi_{-k}(r') - phi_{-k}(r)],  phi_{-k}(x) = sum_{j != k} q_j psi(x - r_j).
+
+The Ewald pair potential psi and everything that is O(N) per proposal live in
+plain C (``kmc_oracle.c``).  The lattice site potential for large grids is a
+circular convolution of the charge grid with the tabulated psi, done with a
+library FFT (numpy) as one step.
+
+Parity status: psi, psi_reg(0), the energy, dU and the KMC selection are
+pinned by tests against the NaCl Madelung constant, brute-force cubic-shell
+image sums with Richardson extrapolation, beta independence, hop reversal,
+lattice symmetries, U(after) - U(before) and a chi-square test of selection
+frequencies.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kmc_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+DEFAULT_BETA_A = 4.5  # beta * a; with one real-space image shell erfc(1.5*4.5) ~ 1e-21
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (-O2, OpenMP).  Returns the .so path."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        D, I64, I, P = ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+        sig = {
+            "oracle_default_kmax": (I, [D]),
+            "oracle_num_threads": (I, []),
+            "oracle_psi": (D, [D, D, I, I, D, D, D]),
+            "oracle_psi_reg0": (D, [D, D, I, I]),
+            "oracle_energy": (D, [I64, P, P, D, D, I, I]),
+            "oracle_delta_u": (D, [I64, P, P, D, D, I, I, I64, P]),
+            "oracle_delta_u_many": (None, [I64, P, P, D, D, I, I, I64, P, P, P]),
+            "oracle_psi_table": (None, [I64, D, I, I, P]),
+            "oracle_site_potential": (None, [I64, P, I64, P, P, P]),
+            "oracle_site_update": (None, [I64, P, P, I64, I64, D]),
+            "oracle_hop_target": (I64, [I64, I64, I]),
+            "oracle_lattice_delta_u": (None, [I64, P, P, I64, P, P, P, P, P]),
+            "oracle_lattice_delta_u_list": (None, [I64, P, P, P, P, I64, P, P, P]),
+            "oracle_rates": (None, [I64, P, P, D, P]),
+            "oracle_select": (I64, [I64, P, D, D, P, P]),
+            "oracle_cumsum": (None, [I64, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _p(x: np.ndarray):
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def ewald_params(a: float, beta_a: float = DEFAULT_BETA_A):
+    """(beta, kmax) for box edge a."""
+    lib = _load()
+    return beta_a / a, int(lib.oracle_default_kmax(beta_a))
+
+
+# ---------------------------------------------------------------- pair potential
+def psi(a: float, d, beta_a: float = DEFAULT_BETA_A, nreal: int = 1, kmax: int | None = None) -> float:
+    """Tinfoil Ewald pair potential psi(d) for a cubic box of edge a."""
+    lib = _load()
+    beta, k = ewald_params(a, beta_a)
+    if kmax is not None:
+        k = kmax
+    return float(lib.oracle_psi(a, beta, nreal, k, float(d[0]), float(d[1]), float(d[2])))
+
+
+def psi_reg0(a: float, beta_a: float = DEFAULT_BETA_A, nreal: int = 1, kmax: int | None = None) -> float:
+    """lim_{d->0} psi(d) - 1/|d| (self-image potential)."""
+    lib = _load()
+    beta, k = ewald_params(a, beta_a)
+    if kmax is not None:
+        k = kmax
+    return float(lib.oracle_psi_reg0(a, beta, nreal, k))
+
+
+def energy(pos: np.ndarray, q: np.ndarray, a: float, beta_a: float = DEFAULT_BETA_A) -> float:
+    """Total tinfoil energy U (O(N^2) pair potentials; small systems only)."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    beta, k = ewald_params(a, beta_a)
+    return float(lib.oracle_energy(len(q), _p(pos), _p(q), a, beta, 1, k))
+
+
+def delta_u(pos: np.ndarray, q: np.ndarray, a: float, particle, target,
+            beta_a: float = DEFAULT_BETA_A) -> np.ndarray:
+    """dU for each (particle[t], target[t]) proposal, direct O(N) Ewald sum each."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    particle = np.ascontiguousarray(np.atleast_1d(particle), dtype=np.int64)
+    target = np.ascontiguousarray(np.asarray(target, dtype=np.float64).reshape(-1, 3))
+    out = np.empty(len(particle), dtype=np.float64)
+    beta, k = ewald_params(a, beta_a)
+    lib.oracle_delta_u_many(len(q), _p(pos), _p(q), a, beta, 1, k, len(particle), _p(particle),
+                            _p(target), _p(out))
+    return out
+
+
+# ---------------------------------------------------------------- lattice mode
+_table_cache: dict = {}
+
+
+def psi_table(E: int, beta_a: float = DEFAULT_BETA_A) -> np.ndarray:
+    """G[d] = psi(d) on the E^3 integer displacement grid (spacing 1), G[0] = psi_reg(0).
+
+    Flat array indexed d = dx + E*(dy + E*dz)."""
+    key = (int(E), float(beta_a))
+    if key in _table_cache:
+        return _table_cache[key]
+    lib = _load()
+    beta, k = ewald_params(float(E), beta_a)
+    G = np.empty(E ** 3, dtype=np.float64)
+    lib.oracle_psi_table(E, beta, 1, k, _p(G))
+    _table_cache[key] = G
+    return G
+
+
+def site_potential(E: int, G: np.ndarray, sites: np.ndarray, q: np.ndarray, method: str = "auto") -> np.ndarray:
+    """phi_s = sum_j q_j G[s - s_j] for all E^3 sites (includes the j = s self term G[0])."""
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    if method == "auto":
+        method = "direct" if E ** 3 * len(q) <= 2e9 else "fft"
+    if method == "direct":
+        lib = _load()
+        phi = np.empty(E ** 3, dtype=np.float64)
+        lib.oracle_site_potential(E, _p(G), len(q), _p(sites), _p(q), _p(phi))
+        return phi
+    # circular convolution of the charge grid with G, via a library FFT
+    rho = np.zeros(E ** 3, dtype=np.float64)
+    np.add.at(rho, sites, q)
+    rho = rho.reshape(E, E, E)
+    g = G.reshape(E, E, E)
+    phi = np.fft.irfftn(np.fft.rfftn(rho) * np.fft.rfftn(g), s=(E, E, E), axes=(0, 1, 2))
+    return np.ascontiguousarray(phi.reshape(-1))
+
+
+def hop_target(E: int, s: int, k: int) -> int:
+    return int(_load().oracle_hop_target(E, s, k))
+
+
+class LatticeState:
+    """Lattice KMC state in the oracle: sites, charges, occupancy and the site potential.
+
+    Hop directions k = 0..5 are (+x, -x, +y, -y, +z, -z); event index j = 6 i + k."""
+
+    def __init__(self, E: int, sites: np.ndarray, q: np.ndarray, beta_a: float = DEFAULT_BETA_A,
+                 method: str = "auto"):
+        self.E = int(E)
+        self.sites = np.array(sites, dtype=np.int64)
+        self.q = np.array(q, dtype=np.float64)
+        self.n = len(self.q)
+        self.G = psi_table(self.E, beta_a)
+        self.occ = np.zeros(self.E ** 3, dtype=np.uint8)
+        self.occ[self.sites] = 1
+        self.phi = site_potential(self.E, self.G, self.sites, self.q, method)
+
+    def propose(self):
+        lib = _load()
+        dU = np.empty(6 * self.n, dtype=np.float64)
+        mask = np.empty(6 * self.n, dtype=np.uint8)
+        lib.oracle_lattice_delta_u(self.E, _p(self.G), _p(self.phi), self.n, _p(self.sites), _p(self.q),
+                                   _p(self.occ), _p(dU), _p(mask))
+        return dU.reshape(self.n, 6), mask.reshape(self.n, 6)
+
+    def delta_u_list(self, particle, target_site) -> np.ndarray:
+        lib = _load()
+        particle = np.ascontiguousarray(particle, dtype=np.int64)
+        target_site = np.ascontiguousarray(target_site, dtype=np.int64)
+        out = np.empty(len(particle), dtype=np.float64)
+        lib.oracle_lattice_delta_u_list(self.E, _p(self.G), _p(self.phi), _p(self.sites), _p(self.q),
+                                        len(particle), _p(particle), _p(target_site), _p(out))
+        return out
+
+    def energy(self) -> float:
+        """U = 1/2 sum_i q_i phi_{s_i} (phi includes the self-image term q_i G[0])."""
+        return float(0.5 * np.dot(self.q, self.phi[self.sites]))
+
+    def target(self, i: int, k: int) -> int:
+        return hop_target(self.E, int(self.sites[i]), int(k))
+
+    def accept(self, i: int, k: int) -> None:
+        s_old = int(self.sites[i])
+        s_new = self.target(i, k)
+        if self.occ[s_new]:
+            raise ValueError("target site occupied")
+        lib = _load()
+        lib.oracle_site_update(self.E, _p(self.G), _p(self.phi), s_old, s_new, float(self.q[i]))
+        self.occ[s_old] = 0
+        self.occ[s_new] = 1
+        self.sites[i] = s_new
+
+
+# ---------------------------------------------------------------- KMC step
+def rates(dU: np.ndarray, mask: np.ndarray | None, kT: float) -> np.ndarray:
+    lib = _load()
+    dU = np.ascontiguousarray(dU, dtype=np.float64).reshape(-1)
+    out = np.empty_like(dU)
+    if mask is None:
+        lib.oracle_rates(len(dU), _p(dU), None, kT, _p(out))
+    else:
+        mask = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+        lib.oracle_rates(len(dU), _p(dU), _p(mask), kT, _p(out))
+    return out
+
+
+def select(rate: np.ndarray, zeta: float, xi: float):
+    """(j, Q, dt): j with R_{j-1} < Q zeta <= R_j, sequential FP64 cumulative sum."""
+    lib = _load()
+    rate = np.ascontiguousarray(rate, dtype=np.float64).reshape(-1)
+    Q = ctypes.c_double()
+    dt = ctypes.c_double()
+    j = lib.oracle_select(len(rate), _p(rate), zeta, xi, ctypes.byref(Q), ctypes.byref(dt))
+    return int(j), float(Q.value), float(dt.value)
+
+
+def cumsum(rate: np.ndarray) -> np.ndarray:
+    lib = _load()
+    rate = np.ascontiguousarray(rate, dtype=np.float64).reshape(-1)
+    out = np.empty_like(rate)
+    lib.oracle_cumsum(len(rate), _p(rate), _p(out))
+    return out
+
+
+def kmc_step(state: LatticeState, kT: float, zeta: float, xi: float):
+    """One rejection-free KMC step on the lattice state; returns (j, dt, Q, dU, mask)."""
+    dU, mask = state.propose()
+    r = rates(dU, mask, kT)
+    j, Q, dt = select(r, zeta, xi)
+    if j >= 0:
+        state.accept(j // 6, j % 6)
+    return j, dt, Q, dU, mask
