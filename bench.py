@@ -1,0 +1,419 @@
+"""Benchmark: dU evaluations/s and KMC steps/s of FMM-for-KMC on one GB300.
+
+Workload (default): 256^3-site periodic simple-cubic lattice, 1,048,576 +-1
+charges on uniform-random distinct sites, 6 nearest-neighbour hop proposals
+per charge, FMM with 6 levels and order p = 12, kT = 0.05, mixed precision
+(FP32 near-field pairs and L2P, FP64 far field, dU assembly and accept
+updates).  A step is one full KMC step: downward pass, propose (all hops),
+rates, selection, accept.
+
+Timed regions (CUDA events on the library's stream, after W warm-up steps):
+  value   K steps of kmc_run_profiled, one step per call, L2 flushed (a
+          256 MiB write) between steps outside the events; dU evals/s =
+          unmasked proposals / step time.  The propose kernel's duration comes
+          from the library's per-phase events inside the same region.
+  e2e     the host API path per step (kmc_fmm_propose_lattice into host
+          buffers, kmc_step, kmc_fmm_accept_event), host<->device copies inside.
+  fp64    the same step loop with the FP64 form (context line).
+  cpu     the FP64 oracle on a bounded sample (host cores).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       [--workload small|medium|large]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "dU evals/sec and KMC steps/sec at N=1M, FP32-mixed vs FP64"
+UNIT = "dU evals/s"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------- algorithmic work
+def pair_count(E: int, L: int, sites: np.ndarray) -> dict:
+    """Evaluation points and near-field pairs of one propose launch, counted
+    from the configuration: per leaf, points = own charges + unmasked hops
+    landing in the leaf, sources = charges in the 27 neighbouring leaves."""
+    nL = 2 ** (L - 1)
+    W = E // nL
+    xyz = workloads.site_xyz(E, sites)
+    occ = np.zeros(E ** 3, dtype=bool)
+    occ[sites] = True
+    leafc = xyz // W
+    leaf = leafc[:, 0] + nL * (leafc[:, 1] + nL * leafc[:, 2])
+    cnt = np.bincount(leaf, minlength=nL ** 3).reshape(nL, nL, nL)  # [z, y, x]
+    pts = np.bincount(leaf, minlength=nL ** 3).astype(np.int64)
+    hops = 0
+    for k, (dx, dy, dz) in enumerate([(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]):
+        t = (xyz + np.array([dx, dy, dz])) % E
+        ts = t[:, 0] + E * (t[:, 1] + E * t[:, 2])
+        ok = ~occ[ts]
+        hops += int(ok.sum())
+        tl = t[ok] // W
+        pts += np.bincount(tl[:, 0] + nL * (tl[:, 1] + nL * tl[:, 2]), minlength=nL ** 3)
+    src = np.zeros_like(cnt)
+    for oz in (-1, 0, 1):
+        for oy in (-1, 0, 1):
+            for ox in (-1, 0, 1):
+                src += np.roll(cnt, shift=(oz, oy, ox), axis=(0, 1, 2))
+    pairs = int(np.sum(pts * src.reshape(-1)))
+    return dict(points=int(pts.sum()), pairs=pairs, hops=hops, leaves=nL ** 3)
+
+
+def l2p_flops(p: int) -> int:
+    """FP32 operations of one L2P (recurrence 6 + accumulate 2 per (n, m), m >= 0)."""
+    return 8 * (p + 1) * (p + 2) // 2
+
+
+# --------------------------------------------------------------- clocks
+class Clocks:
+    def __init__(self, device: int):
+        self.proc = None
+        self.path = None
+        self.device = device
+
+    def start(self, path):
+        self.path = path
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.device), "-lms", "200"],
+                                         stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# --------------------------------------------------------------- CPU oracle sample
+def cpu_sample(E, sites, q, seconds_target=10.0, max_props=20000):
+    """dU evals/s of the FP64 oracle's direct lattice sum (O(N) per proposal,
+    tabulated Ewald pair potential) on a seeded sample of unmasked hops."""
+    import oracle
+    G = oracle.psi_table(E)
+    rng = np.random.default_rng(4242)
+    occ = np.zeros(E ** 3, dtype=bool)
+    occ[sites] = True
+    xyz = workloads.site_xyz(E, sites)
+    dirs = np.array([(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)])
+
+    def draw(m):
+        parts, tg = [], []
+        while len(parts) < m:
+            i = int(rng.integers(0, len(q)))
+            k = int(rng.integers(0, 6))
+            t = (xyz[i] + dirs[k]) % E
+            s = int(t[0] + E * (t[1] + E * t[2]))
+            if not occ[s]:
+                parts.append(i)
+                tg.append(s)
+        return np.array(parts), np.array(tg)
+
+    # calibrate on a small batch, then size the sample to ~seconds_target
+    p, t = draw(64)
+    t0 = time.perf_counter()
+    oracle.lattice_delta_u_direct(E, G, sites, q, p, t)
+    dt = time.perf_counter() - t0
+    m = int(min(max_props, max(64, seconds_target / max(dt / 64, 1e-9))))
+    p, t = draw(m)
+    t0 = time.perf_counter()
+    oracle.lattice_delta_u_direct(E, G, sites, q, p, t)
+    dt = time.perf_counter() - t0
+    return dict(value=m / dt, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
+                sample=f"{m} unmasked hops, direct O(N) sum over the tabulated Ewald pair potential, FP64")
+
+
+# --------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    w, sites, q = workloads.workload(args.workload)
+    E = w["E"]
+    import oracle
+    oracle.build()
+    G = oracle.psi_table(E)
+    per_step = max(16, int(args.ref_props))
+    rng = np.random.default_rng(7)
+    occ = np.zeros(E ** 3, dtype=bool)
+    occ[sites] = True
+    xyz = workloads.site_xyz(E, sites)
+    dirs = np.array([(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)])
+
+    def batch():
+        parts, tg = [], []
+        while len(parts) < per_step:
+            i = int(rng.integers(0, len(q)))
+            k = int(rng.integers(0, 6))
+            t = (xyz[i] + dirs[k]) % E
+            s = int(t[0] + E * (t[1] + E * t[2]))
+            if not occ[s]:
+                parts.append(i)
+                tg.append(s)
+        return np.array(parts), np.array(tg)
+
+    for _ in range(args.warmup):
+        p, t = batch()
+        oracle.lattice_delta_u_direct(E, G, sites, q, p, t)
+    times = []
+    for _ in range(args.steps):
+        p, t = batch()
+        t0 = time.perf_counter()
+        oracle.lattice_delta_u_direct(E, G, sites, q, p, t)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    v = per_step * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(w, args.workload),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{per_step} unmasked hops per step, direct O(N) FP64 sum"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def _config(w, name):
+    return {"workload": f"{name}: {w['E']}^3-site periodic lattice, {w['N']} charges (+-1, neutral), "
+                        f"6 NN hops, L={w['L']}, p={w['p']}, kT={w['kT']}",
+            "E": w["E"], "N": w["N"], "levels": w["L"], "order": w["p"], "kT": w["kT"],
+            "l2": "flushed (256 MiB write) before every timed step"}
+
+
+# --------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    import paper_1905_04065_gb300 as k
+
+    rank, world, local = _dist()
+    dev = local if world > 1 else 0
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w, sites, q = workloads.workload(args.workload)
+    E, L, p, kT = w["E"], w["L"], w["p"], w["kT"]
+    # replicas: every rank runs an independent replica with its own seed
+    if world > 1 and rank > 0:
+        sites, q = workloads.uniform_lattice(E, w["N"], w["seed"] + 7919 * rank)
+    pos = workloads.site_positions(E, sites)
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    h = k.kmc_fmm_init(pos, q, float(E), L, p, precision="mixed", lattice_edge=E, kT=kT, stream=stream, device=dev)
+    torch.cuda.synchronize()
+    init_s = time.perf_counter() - t0
+    work = pair_count(E, L, sites)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    u = workloads.uniforms(args.warmup + args.steps + args.e2e_steps + 16, w["seed"])
+
+    # warm-up
+    k.kmc_run_profiled(h, u[: args.warmup])
+    torch.cuda.synchronize()
+    # timed region
+    clk = Clocks(dev)
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    clk.start(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv"))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    step_ms, phases = [], np.zeros(k.KMC_NPHASE)
+    for s in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ev, dts, ph = k.kmc_run_profiled(h, u[args.warmup + s: args.warmup + s + 1])
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        phases += ph
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    tot_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([tot_ms], device=f"cuda:{dev}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms_step = tot_ms / args.steps
+    hops = work["hops"]  # unmasked proposals per step (changes negligibly per step)
+    value = world * hops * args.steps / (tot_ms * 1e-3)
+    steps_per_s = world * args.steps / (tot_ms * 1e-3)
+    prop_ms = phases[1] / args.steps
+
+    # e2e: host API path with host buffers
+    es = args.e2e_steps
+    base = args.warmup + args.steps
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    t_wall = time.perf_counter()
+    for s in range(es):
+        mask, dU = k.kmc_fmm_propose_lattice(h)
+        ev, dt, Q = k.kmc_step(h, None, u[base + s, 0], u[base + s, 1])
+        if ev >= 0:
+            k.kmc_fmm_accept_event(h, ev)
+    e1.record(stream)
+    e1.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / es
+    n = len(q)
+    e2e = {"value": world * hops / (e2e_ms * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": 16 + 24 + 8,
+           "d2h_bytes_per_step": 6 * n * (1 + 8) + 8 + 8 + 8 + 24 + 8,
+           "path": "kmc_fmm_propose_lattice (mask+dU to host) + kmc_step + kmc_fmm_accept_event"}
+
+    # FP64 form (context)
+    fp64 = None
+    if args.fp64_steps > 0:
+        del h
+        torch.cuda.synchronize()
+        h64 = k.kmc_fmm_init(pos, q, float(E), L, p, precision="fp64", lattice_edge=E, kT=kT, stream=stream,
+                             device=dev)
+        k.kmc_run_profiled(h64, u[:1])
+        ms64 = []
+        ph64 = np.zeros(k.KMC_NPHASE)
+        for s in range(args.fp64_steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, ph = k.kmc_run_profiled(h64, u[1 + s: 2 + s])
+            e1.record(stream)
+            e1.synchronize()
+            ms64.append(e0.elapsed_time(e1))
+            ph64 += ph
+        m64 = float(np.mean(ms64))
+        fp64 = {"dU_evals_per_s": hops / (m64 * 1e-3), "kmc_steps_per_s": 1e3 / m64, "ms_per_step": m64,
+                "propose_ms": ph64[1] / args.fp64_steps, "steps": args.fp64_steps}
+        del h64
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # roofline of the propose kernel: MUFU rsqrt per pair is the binding unit
+    peaks, src = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mufu_peak = 16 * nsm * sm_max * 1e6  # rsqrt/s
+    pairs = work["pairs"]
+    achieved = pairs / (prop_ms * 1e-3)
+    fp32_ops = 8 * pairs + l2p_flops(p) * work["points"]
+    fma_peak = 128 * nsm * sm_max * 1e6
+    t_mufu = pairs / mufu_peak
+    t_fma = fp32_ops / fma_peak
+    roof = {"bound": "alu", "kernel": "k_propose_lattice<float>",
+            "achieved": achieved / 1e9, "peak": mufu_peak / 1e9, "unit": "G pair-interactions/s (MUFU rsqrt)",
+            "frac": achieved / mufu_peak, "traffic": None,
+            "peak_source": f"16 MUFU/clk/SM x {nsm} SMs x {sm_max:.0f} MHz ({src} max clock)",
+            "pairs_per_launch": pairs, "points_per_launch": work["points"],
+            "fp32_ops_per_launch": fp32_ops, "t_min_ms": 1e3 * max(t_mufu, t_fma), "t_meas_ms": prop_ms,
+            "frac_of_alu_bound": 1e3 * max(t_mufu, t_fma) / prop_ms}
+
+    cpu = None
+    if not args.no_cpu and world == 1 or (world > 1 and rank == 0 and not args.no_cpu):
+        cpu = cpu_sample(E, sites, q, seconds_target=args.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32-mixed (f32 near field + L2P, f64 far field / dU / accept)",
+        "data": "synthetic", "config": dict(_config(w, args.workload), parallelism=f"replicas x{world}"),
+        "kmc_steps_per_s": steps_per_s,
+        "propose_only_dU_evals_per_s": world * hops / (prop_ms * 1e-3),
+        "phase_ms_per_step": {nm: phases[i] / args.steps for i, nm in enumerate(k.PHASES)},
+        "init_s": init_s,
+        "fp64_form": fp64,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": (L + 14) * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="large", choices=["small", "medium", "large"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-props", type=int, default=2048)
+    args = ap.parse_args()
+    if args.steps < 1 or args.warmup < 0:
+        raise SystemExit("--steps >= 1 and --warmup >= 0 required")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

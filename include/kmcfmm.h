@@ -1,0 +1,193 @@
+/*
+ * kmcfmm.h -- C ABI of the GB300 (sm_103a) FMM-for-KMC library.
+ *
+ * The library evaluates, for a neutral periodic system of point charges in a
+ * cubic box of edge a, the electrostatic energy change dU of single-charge
+ * hops ("propose", Sec. 3 Eq. (proposed_energy) and its periodic form
+ * Eq. (proposed_energy_sr) plus the far field of Sec. 3.1), selects an event
+ * with rejection-free KMC (Algorithm 1), and applies the incremental update
+ * of the expansions when a hop is accepted (Sec. 3, "Accept move").  The
+ * one-off full FMM (Algorithm 2: P2M, M2M, M2L over wrapped interaction
+ * lists; the periodic lattice operator of Sec. 2.2.1) runs on the device.
+ *
+ * Energy convention: conducting ("tinfoil") boundary at infinity, i.e. the
+ * cubic-order lattice sum with the surface term of Sec. 2.2.2 / App. B
+ * removed.  This equals the Ewald energy with the k = 0 term omitted.
+ *
+ * Conventions common to every call
+ * --------------------------------
+ *  - Every function returns KMC_OK (0) or a KMC_ERR_* code; after an error
+ *    kmc_last_error(h) returns a message.  Errors are sticky for a handle
+ *    only when the device state may be inconsistent (KMC_ERR_CUDA,
+ *    KMC_ERR_CAPACITY); then every later call returns KMC_ERR_STATE.
+ *  - Array arguments live in host memory or in device memory of the
+ *    handle's GPU, as kmc_opts.mem says (KMC_MEM_HOST / KMC_MEM_DEVICE).
+ *    Scalar outputs (energy, event, dt, Q, drift) are always host pointers.
+ *  - The caller owns every buffer it passes; the library copies inputs into
+ *    its own device layout and never keeps or frees a caller pointer.
+ *  - All device work is ordered on the stream given in kmc_opts.stream
+ *    (a cudaStream_t; NULL = legacy default stream).  Calls that return a
+ *    host scalar or write host arrays synchronise that stream.
+ *  - A handle is not thread-safe; use one handle per host thread.
+ *  - Indices: particles are numbered 0..n-1 in the caller's order ("user
+ *    order").  Lattice hop k of particle i is the event j = 6 i + k with
+ *    k = 0..5 for the directions (+x, -x, +y, -y, +z, -z), wrapped
+ *    periodically.
+ */
+#ifndef KMCFMM_H
+#define KMCFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum kmc_status {
+  KMC_OK = 0,
+  KMC_ERR_ARG = 1,         /* invalid argument (sizes, levels, order, positions, singular move) */
+  KMC_ERR_NOT_NEUTRAL = 2, /* sum of charges != 0 (the periodic sums diverge, Sec. 2.2.1) */
+  KMC_ERR_OOM = 3,         /* device allocation failed */
+  KMC_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+  KMC_ERR_CAPACITY = 5,    /* a leaf cell ran out of slots */
+  KMC_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+  KMC_ERR_STATE = 7        /* handle unusable after an earlier error, or wrong call order */
+};
+
+enum kmc_precision {
+  KMC_PREC_FP64 = 0, /* every step in FP64 */
+  KMC_PREC_MIXED = 1 /* L2P and the near-field pair sums in FP32 with FP32 accumulation;
+                        M2L, lattice sums, accept updates and dU assembly in FP64 */
+};
+
+enum kmc_mem { KMC_MEM_HOST = 0, KMC_MEM_DEVICE = 1 };
+
+typedef struct kmc_opts {
+  int precision;      /* kmc_precision */
+  int lattice_edge;   /* E > 0: lattice mode, sites at ((i+1/2)h, (j+1/2)h, (k+1/2)h),
+                         box = E*h, E must be a multiple of 2^(levels-1);
+                         0: off-lattice (only kmc_fmm_propose / kmc_fmm_accept) */
+  double lattice_h;   /* lattice spacing h (lattice mode) */
+  double kT;          /* rate rule r = exp(-max(dU,0)/kT) used by kmc_step / kmc_run */
+  void* stream;       /* cudaStream_t for all device work; NULL = default stream */
+  int mem;            /* kmc_mem: where array arguments live */
+  int device;         /* CUDA device ordinal */
+  int leaf_capacity;  /* off-lattice slots per leaf (0 = automatic); lattice mode uses (E/2^(L-1))^3 */
+} kmc_opts;
+
+typedef struct kmc_fmm* kmc_handle;
+
+/* Fill opts with defaults: FP64, off-lattice, h = 1, kT = 1, NULL stream, host memory, device 0. */
+void kmc_opts_default(kmc_opts* opts);
+
+/*
+ * Create a handle and run the one-off full FMM (Algorithm 2 with the periodic
+ * modifications of Sec. 3.1: wrapped interaction lists, the lattice-sum far
+ * field H = R K of Sec. 2.2.1, the dipole field of Sec. 2.2.2).
+ *   positions: n x 3 doubles (row-major), each coordinate in [0, box).
+ *   charges:   n doubles, sum must vanish (relative 1e-12 of sum |q|).
+ *   levels:    L >= 3 (8^(l-1) cells on level l, Sec. 2.2); at most 10.
+ *   order:     p, the largest expansion degree (Eq. (multipole_local_expansion)
+ *              sums n = 0..p), 1 <= p <= 20.
+ * Errors: KMC_ERR_ARG (n < 2, levels/order out of range, a position outside
+ * [0, box) or not finite, lattice positions off the sites or two charges on
+ * one site, box not divisible), KMC_ERR_NOT_NEUTRAL, KMC_ERR_OOM, KMC_ERR_CUDA.
+ * On error *h is set to NULL unless the handle could be created, in which
+ * case it holds the error message and must be destroyed.
+ */
+int kmc_fmm_init(kmc_handle* h, int64_t n, const double* positions, const double* charges, double box,
+                 int levels, int order, const kmc_opts* opts);
+
+/* Total energy U (Algorithm 3 plus the far field and the dipole term), host scalar. */
+int kmc_fmm_energy(kmc_handle h, double* U);
+
+/*
+ * dU for m arbitrary proposals (the propose() / propose_with_dats() interface
+ * of Sec. 4.2 and App. C, flattened): proposal t moves particle[t] to
+ * target[3t..3t+2] (wrapped into the box).  mask may be NULL; where
+ * mask[t] == 0 the proposal is skipped and dU[t] = NaN (the paper leaves such
+ * entries undefined).  A target equal to the particle's own position, or
+ * equal to another charge's position, is singular: dU[t] = NaN and the call
+ * returns KMC_ERR_ARG after filling every other entry.
+ */
+int kmc_fmm_propose(kmc_handle h, int64_t m, const int32_t* particle, const double* target,
+                    const uint8_t* mask, double* dU);
+
+/*
+ * Lattice mode: proposal generation (each charge to its 6 nearest-neighbour
+ * sites, masked when occupied, as in Algorithm 5) and dU for every unmasked
+ * hop.  mask and dU are n x 6 (event order j = 6 i + k); masked entries get
+ * mask 0 and dU NaN.  Either output may be NULL.  The rates for kmc_step are
+ * kept on the device.
+ */
+int kmc_fmm_propose_lattice(kmc_handle h, uint8_t* mask, double* dU);
+
+/*
+ * Accept the move of particle to target (wrapped), whether proposed or not:
+ * dU is recomputed (Sec. 3.1 footnote), the per-level local expansions, the
+ * multipoles, the far-field coefficients, the dipole and the energy are
+ * updated, and the charge changes leaf.  dU_accepted (host, may be NULL)
+ * receives dU.  Errors: KMC_ERR_ARG (bad index, singular target, lattice
+ * target off a site), KMC_ERR_CAPACITY.
+ */
+int kmc_fmm_accept(kmc_handle h, int32_t particle, const double target[3], double* dU_accepted);
+
+/* Lattice mode: accept event j = 6 i + k (hop of particle i in direction k). */
+int kmc_fmm_accept_event(kmc_handle h, int64_t event, double* dU_accepted);
+
+/*
+ * Rejection-free selection (Algorithm 1): rates r_j (m = 6 n entries in event
+ * order, or NULL to use the rates of the last kmc_fmm_propose_lattice),
+ * Q = sum r_j, event j with R_{j-1} < Q zeta <= R_j, dt = -ln(xi) / Q.
+ * zeta, xi in (0, 1].  Outputs are host scalars; *event = -1 if Q == 0.
+ * Does not accept the event.
+ */
+int kmc_step(kmc_handle h, const double* rates, double zeta, double xi, int64_t* event, double* dt,
+             double* Q);
+
+/*
+ * Lattice mode: run `steps` full KMC steps on the device without host
+ * synchronisation (propose -> rates -> select -> accept per step, replayed
+ * from a CUDA graph).  uniforms: steps x 2 values (zeta_s, xi_s) in (0, 1].
+ * events (int64, steps) and dts (double, steps) receive the selected events
+ * and time increments; either may be NULL.
+ */
+int kmc_run(kmc_handle h, int steps, const double* uniforms, int64_t* events, double* dts);
+
+/*
+ * kmc_run without graph replay, with per-phase device timing: phase_ms
+ * (host, KMC_NPHASE doubles, may be NULL) receives the summed duration of
+ * each phase over all steps, measured with CUDA events on the handle's
+ * stream: [0] downward pass, [1] propose kernel (near-field pairs + L2P),
+ * [2] dU / rates, [3] selection, [4] accept updates.  Same results as
+ * kmc_run.  Synchronises the stream.
+ */
+#define KMC_NPHASE 5
+int kmc_run_profiled(kmc_handle h, int steps, const double* uniforms, int64_t* events, double* dts,
+                     double* phase_ms);
+
+/*
+ * Full FP64 recompute of every expansion from the current positions
+ * (Algorithm 2); *max_coeff_drift (host, may be NULL) receives
+ * max |psi_incremental - psi_fresh| / max |psi_fresh| over all levels before
+ * the fresh values replace the incremental ones.  The energy is recomputed.
+ */
+int kmc_fmm_recompute(kmc_handle h, double* max_coeff_drift);
+
+/* Leaf-cell index (cx + n(cy + n cz), n = 2^(L-1)) of every particle, user order. */
+int kmc_fmm_leaf_index(kmc_handle h, int32_t* leaf);
+
+/* Current positions (n x 3) in user order. */
+int kmc_fmm_positions(kmc_handle h, double* positions);
+
+/* Message of the last error on this handle (static string if h is NULL). */
+const char* kmc_last_error(kmc_handle h);
+
+/* Release the handle and all device memory it owns.  NULL is allowed. */
+void kmc_fmm_destroy(kmc_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KMCFMM_H */

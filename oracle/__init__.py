@@ -77,6 +77,7 @@ def _load():
             "oracle_hop_target": (I64, [I64, I64, I]),
             "oracle_lattice_delta_u": (None, [I64, P, P, I64, P, P, P, P, P]),
             "oracle_lattice_delta_u_list": (None, [I64, P, P, P, P, I64, P, P, P]),
+            "oracle_lattice_delta_u_direct": (None, [I64, P, I64, P, P, I64, P, P, P]),
             "oracle_rates": (None, [I64, P, P, D, P]),
             "oracle_select": (I64, [I64, P, D, D, P, P]),
             "oracle_cumsum": (None, [I64, P, P]),
@@ -183,6 +184,19 @@ def site_potential(E: int, G: np.ndarray, sites: np.ndarray, q: np.ndarray, meth
     g = G.reshape(E, E, E)
     phi = np.fft.irfftn(np.fft.rfftn(rho) * np.fft.rfftn(g), s=(E, E, E), axes=(0, 1, 2))
     return np.ascontiguousarray(phi.reshape(-1))
+
+
+def lattice_delta_u_direct(E: int, G: np.ndarray, sites, q, particle, target_site) -> np.ndarray:
+    """dU by the direct O(N) sum over the other charges (tabulated psi), per proposal."""
+    lib = _load()
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    particle = np.ascontiguousarray(particle, dtype=np.int64)
+    target_site = np.ascontiguousarray(target_site, dtype=np.int64)
+    out = np.empty(len(particle), dtype=np.float64)
+    lib.oracle_lattice_delta_u_direct(E, _p(G), len(q), _p(sites), _p(q), len(particle), _p(particle),
+                                      _p(target_site), _p(out))
+    return out
 
 
 def hop_target(E: int, s: int, k: int) -> int:

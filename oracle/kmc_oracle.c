@@ -373,3 +373,20 @@ void oracle_cumsum(int64_t m, const double* rate, double* R) {
     R[j] = s;
   }
 }
+
+/* dU for (particle[t], target site[t]) by the direct O(N) sum over the other
+ * charges with the tabulated pair potential:
+ *   dU = q_i sum_{j != i} q_j [G(s' - s_j) - G(s_i - s_j)]                  */
+void oracle_lattice_delta_u_direct(int64_t E, const double* G, int64_t n, const int64_t* site, const double* q,
+                                   int64_t m, const int64_t* particle, const int64_t* target, double* dU) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t t = 0; t < m; t++) {
+    int64_t i = particle[t], si = site[i], u = target[t];
+    double s = 0.0;
+    for (int64_t j = 0; j < n; j++) {
+      if (j == i) continue;
+      s += q[j] * (G[disp_index(E, u, site[j])] - G[disp_index(E, si, site[j])]);
+    }
+    dU[t] = q[i] * s;
+  }
+}

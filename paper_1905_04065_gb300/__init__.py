@@ -1,0 +1,304 @@
+"""GB300 (sm_103a) FMM for kinetic Monte Carlo -- Python binding of libkmcfmm.
+
+Every function here marshals arguments for the C ABI declared in
+include/kmcfmm.h and calls it; all arithmetic runs in the CUDA library.
+There is no CPU fallback: importing works without a GPU, but creating a
+handle needs the built library and a CUDA device, and fails loudly
+otherwise.
+
+Arrays may be numpy arrays (host memory) or CUDA torch tensors (device
+memory); the kind is fixed per handle by the positions passed to
+kmc_fmm_init.  Hop k of particle i is event j = 6 i + k, k = 0..5 for the
+directions (+x, -x, +y, -y, +z, -z).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from .build import LIB, build as build_library
+
+KMC_OK = 0
+KMC_ERR_ARG = 1
+KMC_ERR_NOT_NEUTRAL = 2
+KMC_ERR_OOM = 3
+KMC_ERR_CUDA = 4
+KMC_ERR_CAPACITY = 5
+KMC_ERR_TIMEOUT = 6
+KMC_ERR_STATE = 7
+KMC_PREC_FP64 = 0
+KMC_PREC_MIXED = 1
+KMC_MEM_HOST = 0
+KMC_MEM_DEVICE = 1
+
+EXPORTS = [
+    "kmc_opts_default", "kmc_fmm_init", "kmc_fmm_energy", "kmc_fmm_propose", "kmc_fmm_propose_lattice",
+    "kmc_fmm_accept", "kmc_fmm_accept_event", "kmc_step", "kmc_run", "kmc_run_profiled", "kmc_fmm_recompute",
+    "kmc_fmm_leaf_index", "kmc_fmm_positions", "kmc_last_error", "kmc_fmm_destroy",
+]
+
+
+class KmcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"kmcfmm error {code}: {msg}")
+        self.code = code
+
+
+class kmc_opts(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("lattice_edge", ctypes.c_int),
+        ("lattice_h", ctypes.c_double),
+        ("kT", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+        ("mem", ctypes.c_int),
+        ("device", ctypes.c_int),
+        ("leaf_capacity", ctypes.c_int),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str | None = None):
+    """Load libkmcfmm.so (building it first when missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(path or build_library())
+        P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "kmc_opts_default": (None, [P]),
+            "kmc_fmm_init": (I, [P, I64, P, P, D, I, I, P]),
+            "kmc_fmm_energy": (I, [P, P]),
+            "kmc_fmm_propose": (I, [P, I64, P, P, P, P]),
+            "kmc_fmm_propose_lattice": (I, [P, P, P]),
+            "kmc_fmm_accept": (I, [P, ctypes.c_int32, P, P]),
+            "kmc_fmm_accept_event": (I, [P, I64, P]),
+            "kmc_step": (I, [P, P, D, D, P, P, P]),
+            "kmc_run": (I, [P, I, P, P, P]),
+            "kmc_run_profiled": (I, [P, I, P, P, P, P]),
+            "kmc_fmm_recompute": (I, [P, P]),
+            "kmc_fmm_leaf_index": (I, [P, P]),
+            "kmc_fmm_positions": (I, [P, P]),
+            "kmc_last_error": (ctypes.c_char_p, [P]),
+            "kmc_fmm_destroy": (None, [P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+class Handle:
+    """An initialised FMM-KMC system (owns the C handle)."""
+
+    def __init__(self, ptr, n: int, mem: int, lattice: bool, device: int):
+        self.ptr = ptr
+        self.n = n
+        self.mem = mem
+        self.lattice = lattice
+        self.device = device
+
+    def __del__(self):
+        try:
+            kmc_fmm_destroy(self)
+        except Exception:
+            pass
+
+
+def _check(h, code: int):
+    if code != KMC_OK:
+        lib = load_library()
+        msg = lib.kmc_last_error(h.ptr if isinstance(h, Handle) else h)
+        raise KmcError(code, msg.decode() if msg else "")
+
+
+def _host(x, dtype):
+    a = np.ascontiguousarray(np.asarray(x, dtype=dtype))
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _arg(h: Handle, x, dtype, torch_dtype=None):
+    """(keep-alive object, pointer) for an input array in the handle's memory kind."""
+    if x is None:
+        return None, None
+    if h.mem == KMC_MEM_DEVICE:
+        import torch
+        if not (_is_torch(x) and x.is_cuda):
+            x = torch.as_tensor(np.asarray(x, dtype=dtype), device=f"cuda:{h.device}")
+        x = x.contiguous()
+        return x, ctypes.c_void_p(x.data_ptr())
+    if _is_torch(x):
+        x = x.detach().cpu().numpy()
+    return _host(x, dtype)
+
+
+def _out(h: Handle, shape, dtype):
+    if h.mem == KMC_MEM_DEVICE:
+        import torch
+        tdt = {np.float64: torch.float64, np.uint8: torch.uint8, np.int64: torch.int64,
+               np.int32: torch.int32}[np.dtype(dtype).type]
+        t = torch.empty(shape, dtype=tdt, device=f"cuda:{h.device}")
+        return t, ctypes.c_void_p(t.data_ptr())
+    a = np.empty(shape, dtype=dtype)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ------------------------------------------------------------------ C-ABI calls
+def kmc_fmm_init(positions, charges, box: float, levels: int, order: int, precision: str = "fp64",
+                 lattice_edge: int = 0, lattice_h: float = 1.0, kT: float = 1.0, stream=None, device: int = 0,
+                 leaf_capacity: int = 0) -> Handle:
+    """Create a handle and run the one-off full FMM.  precision: 'fp64' or 'mixed'."""
+    lib = load_library()
+    opts = kmc_opts()
+    lib.kmc_opts_default(ctypes.byref(opts))
+    opts.precision = {"fp64": KMC_PREC_FP64, "mixed": KMC_PREC_MIXED}[precision]
+    opts.lattice_edge = int(lattice_edge)
+    opts.lattice_h = float(lattice_h)
+    opts.kT = float(kT)
+    opts.device = int(device)
+    opts.leaf_capacity = int(leaf_capacity)
+    dev = _is_torch(positions) and positions.is_cuda
+    opts.mem = KMC_MEM_DEVICE if dev else KMC_MEM_HOST
+    if stream is not None:
+        opts.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    elif dev:
+        import torch
+        opts.stream = ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+    n = int(positions.shape[0])
+    tmp = Handle(None, n, opts.mem, lattice_edge > 0, device)
+    pos_keep, pos_p = _arg(tmp, positions, np.float64)
+    q_keep, q_p = _arg(tmp, charges, np.float64)
+    ptr = ctypes.c_void_p()
+    code = lib.kmc_fmm_init(ctypes.byref(ptr), n, pos_p, q_p, float(box), int(levels), int(order),
+                            ctypes.byref(opts))
+    h = Handle(ptr, n, opts.mem, lattice_edge > 0, device)
+    if code != KMC_OK:
+        msg = lib.kmc_last_error(ptr)
+        text = msg.decode() if msg else ""
+        lib.kmc_fmm_destroy(ptr)
+        h.ptr = None
+        raise KmcError(code, text)
+    return h
+
+
+def kmc_fmm_energy(h: Handle) -> float:
+    U = ctypes.c_double()
+    _check(h, load_library().kmc_fmm_energy(h.ptr, ctypes.byref(U)))
+    return U.value
+
+
+def kmc_fmm_propose(h: Handle, particle, target, mask=None):
+    """dU for proposals particle[t] -> target[t] (m x 3)."""
+    lib = load_library()
+    pk, pp = _arg(h, particle, np.int32)
+    tk, tp = _arg(h, target, np.float64)
+    mk, mp = _arg(h, mask, np.uint8)
+    m = int(pk.shape[0])
+    out, op = _out(h, (m,), np.float64)
+    _check(h, lib.kmc_fmm_propose(h.ptr, m, pp, tp, mp, op))
+    return out
+
+
+def kmc_fmm_propose_lattice(h: Handle):
+    """(mask[n,6], dU[n,6]) for all nearest-neighbour hops."""
+    lib = load_library()
+    mask, mp = _out(h, (h.n, 6), np.uint8)
+    dU, dp = _out(h, (h.n, 6), np.float64)
+    _check(h, lib.kmc_fmm_propose_lattice(h.ptr, mp, dp))
+    return mask, dU
+
+
+def kmc_fmm_accept(h: Handle, particle: int, target) -> float:
+    lib = load_library()
+    t, tp = _host(np.asarray(target, dtype=np.float64).reshape(3), np.float64)
+    du = ctypes.c_double()
+    if h.mem == KMC_MEM_DEVICE:
+        tk, tp = _arg(h, t, np.float64)
+    _check(h, lib.kmc_fmm_accept(h.ptr, int(particle), tp, ctypes.byref(du)))
+    return du.value
+
+
+def kmc_fmm_accept_event(h: Handle, event: int) -> float:
+    du = ctypes.c_double()
+    _check(h, load_library().kmc_fmm_accept_event(h.ptr, int(event), ctypes.byref(du)))
+    return du.value
+
+
+def kmc_step(h: Handle, rates, zeta: float, xi: float):
+    """(event, dt, Q) by rejection-free selection; rates None = last lattice proposal."""
+    lib = load_library()
+    rk, rp = _arg(h, rates, np.float64)
+    ev = ctypes.c_int64()
+    dt = ctypes.c_double()
+    Q = ctypes.c_double()
+    _check(h, lib.kmc_step(h.ptr, rp, float(zeta), float(xi), ctypes.byref(ev), ctypes.byref(dt), ctypes.byref(Q)))
+    return ev.value, dt.value, Q.value
+
+
+def kmc_run(h: Handle, uniforms):
+    """Run len(uniforms) device-driven KMC steps; returns (events, dts)."""
+    lib = load_library()
+    uk, up = _arg(h, uniforms, np.float64)
+    steps = int(uk.shape[0])
+    ev, evp = _out(h, (steps,), np.int64)
+    dt, dtp = _out(h, (steps,), np.float64)
+    _check(h, lib.kmc_run(h.ptr, steps, up, evp, dtp))
+    return ev, dt
+
+
+KMC_NPHASE = 5
+PHASES = ("downward", "propose", "rates", "select", "accept")
+
+
+def kmc_run_profiled(h: Handle, uniforms):
+    """kmc_run without graph replay; returns (events, dts, phase_ms[5])."""
+    lib = load_library()
+    uk, up = _arg(h, uniforms, np.float64)
+    steps = int(uk.shape[0])
+    ev, evp = _out(h, (steps,), np.int64)
+    dt, dtp = _out(h, (steps,), np.float64)
+    ph = np.zeros(KMC_NPHASE, dtype=np.float64)
+    _check(h, lib.kmc_run_profiled(h.ptr, steps, up, evp, dtp, ph.ctypes.data_as(ctypes.c_void_p)))
+    return ev, dt, ph
+
+
+def kmc_fmm_recompute(h: Handle) -> float:
+    drift = ctypes.c_double()
+    _check(h, load_library().kmc_fmm_recompute(h.ptr, ctypes.byref(drift)))
+    return drift.value
+
+
+def kmc_fmm_leaf_index(h: Handle):
+    out, op = _out(h, (h.n,), np.int32)
+    _check(h, load_library().kmc_fmm_leaf_index(h.ptr, op))
+    return out
+
+
+def kmc_fmm_positions(h: Handle):
+    out, op = _out(h, (h.n, 3), np.float64)
+    _check(h, load_library().kmc_fmm_positions(h.ptr, op))
+    return out
+
+
+def kmc_last_error(h: Handle) -> str:
+    msg = load_library().kmc_last_error(h.ptr if h is not None else None)
+    return msg.decode() if msg else ""
+
+
+def kmc_fmm_destroy(h: Handle) -> None:
+    if h is not None and h.ptr is not None:
+        load_library().kmc_fmm_destroy(h.ptr)
+        h.ptr = None

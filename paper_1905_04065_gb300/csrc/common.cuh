@@ -1,0 +1,165 @@
+// common.cuh -- shared device types, state layout and solid-harmonic helpers.
+//
+// Solid harmonics (Eq. (multipole_local_expansion) up to normalisation, which
+// the paper leaves open):
+//   regular    R_n^m(x) = r^n P_n^m(cos t) e^{i m f} / (n+m)!
+//   irregular  I_n^m(x) = (n-m)! P_n^m(cos t) e^{i m f} / r^{n+1}
+// with the Condon-Shortley phase in P_n^m, and R_n^{-m} = (-1)^m conj(R_n^m),
+// I_n^{-m} = (-1)^m conj(I_n^m).  They satisfy 1/|x-y| = sum conj(R(y)) I(x)
+// for |y| < |x| and are generated by the Cartesian recurrences
+//   R_m^m = -(x+iy)/(2m) R_{m-1}^{m-1},
+//   (n^2-m^2) R_n^m = (2n-1) z R_{n-1}^m - r^2 R_{n-2}^m,
+//   I_m^m = -(2m-1)(x+iy)/r^2 I_{m-1}^{m-1},
+//   r^2 I_n^m = (2n-1) z I_{n-1}^m - ((n-1)^2-m^2) I_{n-2}^m.
+// Expansion coefficients are stored for 0 <= m <= n <= p at tri(n,m).
+//   multipole   Mt_n^m = sum q R_n^m(y - c)          phi(x) = Re sum conj(Mt) I(x - c)
+//   local       L_n^m  = sum q conj(I_n^m(y - c))    phi(x) = Re sum L R(x - c)
+// Translations (t = vector between centres):
+//   M2M  Mt'(c2)_n^m = sum_{k,l} Mt_k^l(c1) R_{n-k}^{m-l}(c1 - c2)
+//   M2L  L_n^m(c2)   = sum_{k,l} (-1)^k Mt_k^l(c1) conj(I_{n+k}^{m+l}(c1 - c2))
+//   L2L  L'_k^l(c2)  = sum_{n,m} L_n^m(c1) R_{n-k}^{m-l}(c2 - c1)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define KMC_MAXL 10   // maximum number of levels
+#define KMC_MAXP 20   // maximum expansion degree
+#define KMC_NHOP 6    // lattice hop directions (+x,-x,+y,-y,+z,-z)
+
+__host__ __device__ __forceinline__ int tri(int n, int m) { return n * (n + 1) / 2 + m; }
+__host__ __device__ __forceinline__ int ncoef(int p) { return (p + 1) * (p + 2) / 2; }
+
+// ---------------------------------------------------------------- complex helpers
+template <typename T> struct cplx;
+template <> struct cplx<float> { typedef float2 type; };
+template <> struct cplx<double> { typedef double2 type; };
+template <typename T> struct vec4;
+template <> struct vec4<float> { typedef float4 type; };
+template <> struct vec4<double> { typedef double4_32a type; };
+
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+  C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C cmk(double x, double y) {
+  C r; r.x = x; r.y = y; return r;
+}
+// value at (n, m) for any sign of m from a table holding 0 <= m <= n
+template <typename C> __device__ __forceinline__ C tab_get(const C* t, int n, int m) {
+  if (m >= 0) return t[tri(n, m)];
+  C v = t[tri(n, -m)];
+  v.y = -v.y;
+  if (m & 1) { v.x = -v.x; v.y = -v.y; }
+  return v;
+}
+
+// ---------------------------------------------------------------- geometry
+struct Geo {
+  int L, p, P, P2;        // levels, order, ncoef(p), ncoef(2p)
+  int nL;                 // leaves per side (2^(L-1))
+  int cap;                // slots per leaf
+  int64_t n;              // charges
+  int64_t ML;             // number of leaves
+  double a, w;            // box edge, leaf width
+  int E;                  // lattice edge (0 = off-lattice)
+  int W;                  // lattice sites per leaf side (E / nL)
+  double h;               // lattice spacing
+  int64_t cell_off[KMC_MAXL + 2];  // first cell of level l in per-level arrays (l = 1..L)
+  int64_t ncell_total;
+  double kT;
+};
+
+struct MoveRec {
+  int32_t valid;      // 1 if a move is to be applied
+  int32_t i;          // particle (user index)
+  int32_t site_old, site_new;   // lattice sites (or -1)
+  double q;
+  double r[3];        // old position (primary cell)
+  double rn[3];       // new position (primary cell)
+  double dU;          // energy change of this move
+};
+
+// All device buffers owned by a handle (plain pointers, passed by value).
+struct Dev {
+  // particles, user order
+  double* q;          // [n]
+  double* pos;        // [n*3]
+  int32_t* site;      // [n] lattice site or -1
+  int32_t* slot_of;   // [n]
+  // leaf-sorted slots
+  int32_t* cnt;       // [ML]
+  int32_t* uid;       // [ML*cap]
+  double4_32a* spos64;    // [ML*cap] (x,y,z,q)
+  float4* spos32;     // [ML*cap]
+  // expansions (all levels, cell-major, ncoef(p) per cell)
+  double2* Mt;        // multipoles
+  double2* Psi;       // per-level interaction-list local expansions; level 1 holds H
+  void* Peff;         // downward-accumulated locals (T2), all levels
+  double2* Itab;      // M2L irregular values [(L+1) * 343 * P2]
+  double2* S;         // lattice sums over the far images [P2]
+  double* selfc;      // [KMC_NHOP] self-pair correction C(d) per hop direction
+  double* dip;        // [3] dipole moment M
+  double* U;          // [1] total energy
+  // per step
+  double* phi_old;    // [n]
+  double* phi_new;    // [6n]
+  uint8_t* mask;      // [6n]
+  double* dU;         // [6n]
+  double* rate;       // [6n]
+  double* bsum;       // [nblk]
+  int64_t* event;     // [1]
+  double* dtq;        // [2] (dt, Q)
+  MoveRec* move;      // [1]
+  int* err;           // [4] device error flags
+  double* scratch;    // init-time scratch (lattice-sum terms)
+  double* uni_small;  // [2] (zeta, xi) staged for a single kmc_step
+  // device-driven step loop
+  int* stepc;         // [1] step counter
+  double* uni_run;    // [2*steps] uniforms
+  int64_t* ev_hist;   // [steps] selected events
+  double* dt_hist;    // [steps] time increments
+};
+
+// device error codes (bit flags in err[0])
+#define KMC_DERR_CAPACITY 1
+#define KMC_DERR_SINGULAR 2
+#define KMC_DERR_BADPOS 4
+#define KMC_DERR_BADSITE 8
+
+// 1/((n-m)(n+m)) for n > m, table built on the host into constant memory by each TU
+#define KMC_NTRI (((2 * KMC_MAXP + 1) * (2 * KMC_MAXP + 2)) / 2)
+
+// ---------------------------------------------------------------- launch wrappers
+// (defined in the .cu files, called by the host runtime)
+void fmm_upload_constants(int p);
+void fmm_bin(const Geo& g, const Dev& d, cudaStream_t s);
+void fmm_p2m(const Geo& g, const Dev& d, cudaStream_t s);
+void fmm_m2m(const Geo& g, const Dev& d, cudaStream_t s);
+void fmm_itab(const Geo& g, const Dev& d, cudaStream_t s);
+void fmm_m2l(const Geo& g, const Dev& d, cudaStream_t s);
+void fmm_lattice_sums(const Geo& g, const Dev& d, cudaStream_t s);
+void fmm_far_field(const Geo& g, const Dev& d, cudaStream_t s);
+void fmm_self_and_dipole(const Geo& g, const Dev& d, cudaStream_t s);
+void fmm_downward(const Geo& g, const Dev& d, int prec, cudaStream_t s);
+void fmm_selfcorr_list(const Geo& g, const Dev& d, int64_t m, const double* dvec, double* out, cudaStream_t s);
+void fmm_drift(const Geo& g, const double2* a, const double2* b, int64_t count, double* out2,
+               cudaStream_t s);
+
+void kmc_upload_constants(int p);
+void kmc_propose_lattice(const Geo& g, const Dev& d, int prec, cudaStream_t s);
+void kmc_finalize_rates(const Geo& g, const Dev& d, cudaStream_t s);
+void kmc_prepare(const Geo& g, int prec);
+void kmc_rate_bsum(const Geo& g, const Dev& d, cudaStream_t s);
+void kmc_select(const Geo& g, const Dev& d, int use_counter, cudaStream_t s);
+void kmc_record(const Geo& g, const Dev& d, cudaStream_t s);
+void kmc_accept_from_event(const Geo& g, const Dev& d, cudaStream_t s);
+void kmc_accept_apply(const Geo& g, const Dev& d, cudaStream_t s);
+void kmc_eval_points(const Geo& g, const Dev& d, int prec, int64_t m, const double* pts,
+                     const int32_t* excl, double* out, cudaStream_t s);
+void kmc_assemble_general(const Geo& g, const Dev& d, int64_t m, const int32_t* particle,
+                          const double* tgt, const uint8_t* mask, const double* phi_new,
+                          const double* phi_old, double* dU, cudaStream_t s);
+void kmc_stage_general(const Geo& g, const Dev& d, int64_t m, const int32_t* part, const double* tin,
+                       const uint8_t* min_, double* tout, double* old, double* dv, uint8_t* mout, cudaStream_t s);
+void kmc_energy_reduce(const Geo& g, const Dev& d, cudaStream_t s);
+void kmc_validate(const Geo& g, const Dev& d, cudaStream_t s);

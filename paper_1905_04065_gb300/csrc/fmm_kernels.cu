@@ -1,0 +1,655 @@
+// fmm_kernels.cu -- one-off full FMM on the device (Algorithm 2 with the
+// periodic modifications of Sec. 3.1), the lattice-sum far field (Sec. 2.2.1)
+// and the per-step downward pass that materialises leaf local expansions.
+//
+// Local expansions are stored per level: Psi_l[b] holds only the M2L
+// contributions of the interaction list of cell b on level l (Algorithm 2,
+// inner loop), and level 1 holds the far-field expansion H = R K.  Because a
+// local-to-local translation of a degree-p expansion is exact, the leaf
+// expansion of Algorithm 2 equals sum_l L2L(Psi_l[ancestor_l] -> leaf); the
+// downward kernel rebuilds it each step.  Storing the levels separately is
+// the per-level scheme of Sec. 6 (conclusions) and makes an accepted move
+// touch O(L) cells per level instead of every leaf.
+#include <math.h>
+#include <stdio.h>
+
+#include "common.cuh"
+
+__constant__ double f_inv_nm[KMC_NTRI];        // 1/((n-m)(n+m)), n > m
+__constant__ double f_fact[4 * KMC_MAXP + 2];   // k! for k <= 4p + 1
+
+void fmm_upload_constants(int p) {
+  static double inv[KMC_NTRI];
+  static double fact[4 * KMC_MAXP + 2];
+  for (int n = 0; n <= 2 * KMC_MAXP; n++)
+    for (int m = 0; m <= n; m++) inv[tri(n, m)] = (n > m) ? 1.0 / ((double)(n - m) * (double)(n + m)) : 0.0;
+  fact[0] = 1.0;
+  for (int k = 1; k < 4 * KMC_MAXP + 2; k++) fact[k] = fact[k - 1] * k;
+  cudaMemcpyToSymbol(f_inv_nm, inv, sizeof(inv));
+  cudaMemcpyToSymbol(f_fact, fact, sizeof(fact));
+  (void)p;
+}
+
+// ------------------------------------------------------------------ harmonics
+// Full table of regular harmonics R_n^m(x), 0 <= m <= n <= p (FP64).
+__device__ void regular_table(double x, double y, double z, int p, double2* out) {
+  double r2 = x * x + y * y + z * z;
+  double2 mm = make_double2(1.0, 0.0);
+  for (int m = 0; m <= p; m++) {
+    if (m > 0) {
+      // R_m^m = -(x+iy)/(2m) R_{m-1}^{m-1}
+      double s = -0.5 / m;
+      double2 t = make_double2(s * (x * mm.x - y * mm.y), s * (x * mm.y + y * mm.x));
+      mm = t;
+    }
+    out[tri(m, m)] = mm;
+    double2 a2 = make_double2(0.0, 0.0), a1 = mm;
+    for (int n = m + 1; n <= p; n++) {
+      double c = f_inv_nm[tri(n, m)];
+      double zz = (2 * n - 1) * z;
+      double2 v = make_double2((zz * a1.x - r2 * a2.x) * c, (zz * a1.y - r2 * a2.y) * c);
+      out[tri(n, m)] = v;
+      a2 = a1;
+      a1 = v;
+    }
+  }
+}
+
+// Full table of irregular harmonics I_n^m(x), 0 <= m <= n <= p (FP64).
+__device__ void irregular_table(double x, double y, double z, int p, double2* out, int64_t stride = 1) {
+  double r2 = x * x + y * y + z * z;
+  double inv = 1.0 / r2;
+  double2 mm = make_double2(1.0 / sqrt(r2), 0.0);
+  for (int m = 0; m <= p; m++) {
+    if (m > 0) {
+      double s = -(2.0 * m - 1.0) * inv;
+      double2 t = make_double2(s * (x * mm.x - y * mm.y), s * (x * mm.y + y * mm.x));
+      mm = t;
+    }
+    out[tri(m, m) * stride] = mm;
+    double2 a2 = make_double2(0.0, 0.0), a1 = mm;
+    for (int n = m + 1; n <= p; n++) {
+      double zz = (2 * n - 1) * z;
+      double c2 = (double)((n - 1) * (n - 1) - m * m);
+      double2 v = make_double2((zz * a1.x - c2 * a2.x) * inv, (zz * a1.y - c2 * a2.y) * inv);
+      out[tri(n, m) * stride] = v;
+      a2 = a1;
+      a1 = v;
+    }
+  }
+}
+
+// R_m^m(x) directly (m complex multiplications)
+__device__ __forceinline__ double2 regular_mm(double x, double y, int m) {
+  double2 mm = make_double2(1.0, 0.0);
+  for (int j = 1; j <= m; j++) {
+    double s = -0.5 / j;
+    mm = make_double2(s * (x * mm.x - y * mm.y), s * (x * mm.y + y * mm.x));
+  }
+  return mm;
+}
+
+// ------------------------------------------------------------------ binning
+__device__ __forceinline__ int leaf_of(const Geo& g, double x, double y, double z) {
+  int cx = (int)floor(x / g.w), cy = (int)floor(y / g.w), cz = (int)floor(z / g.w);
+  cx = min(max(cx, 0), g.nL - 1);
+  cy = min(max(cy, 0), g.nL - 1);
+  cz = min(max(cz, 0), g.nL - 1);
+  return cx + g.nL * (cy + g.nL * cz);
+}
+
+__global__ void k_bin_count(const Geo g, const Dev d) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  int leaf = leaf_of(g, d.pos[3 * i], d.pos[3 * i + 1], d.pos[3 * i + 2]);
+  int r = atomicAdd(&d.cnt[leaf], 1);
+  if (r < g.cap) d.uid[(int64_t)leaf * g.cap + r] = (int32_t)i;
+  else atomicOr(&d.err[0], KMC_DERR_CAPACITY);
+}
+
+// deterministic order inside each leaf: ascending user index
+__global__ void k_bin_sort(const Geo g, const Dev d) {
+  int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (leaf >= g.ML) return;
+  int c = min(d.cnt[leaf], g.cap);
+  int32_t* u = d.uid + leaf * g.cap;
+  for (int a = 1; a < c; a++) {
+    int32_t v = u[a];
+    int b = a - 1;
+    while (b >= 0 && u[b] > v) { u[b + 1] = u[b]; b--; }
+    u[b + 1] = v;
+  }
+}
+
+__global__ void k_bin_fill(const Geo g, const Dev d) {
+  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= g.ML * g.cap) return;
+  int64_t leaf = s / g.cap;
+  int j = (int)(s - leaf * g.cap);
+  if (j >= d.cnt[leaf]) return;
+  int32_t i = d.uid[s];
+  d.slot_of[i] = (int32_t)s;
+  double x = d.pos[3 * i], y = d.pos[3 * i + 1], z = d.pos[3 * i + 2], q = d.q[i];
+  d.spos64[s] = make_double4_32a(x, y, z, q);
+  d.spos32[s] = make_float4((float)x, (float)y, (float)z, (float)q);
+}
+
+void fmm_bin(const Geo& g, const Dev& d, cudaStream_t s) {
+  cudaMemsetAsync(d.cnt, 0, sizeof(int32_t) * g.ML, s);
+  k_bin_count<<<(unsigned)((g.n + 255) / 256), 256, 0, s>>>(g, d);
+  k_bin_sort<<<(unsigned)((g.ML + 127) / 128), 128, 0, s>>>(g, d);
+  int64_t ns = g.ML * g.cap;
+  k_bin_fill<<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(g, d);
+}
+
+// ------------------------------------------------------------------ P2M
+// thread per (leaf, m): Mt_n^m = sum_j q_j R_n^m(r_j - c) for n = m..p
+__global__ void k_p2m(const Geo g, const Dev d) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t leaf = t / (g.p + 1);
+  int m = (int)(t - leaf * (g.p + 1));
+  if (leaf >= g.ML) return;
+  int cx = (int)(leaf % g.nL), cy = (int)((leaf / g.nL) % g.nL), cz = (int)(leaf / ((int64_t)g.nL * g.nL));
+  double c0 = (cx + 0.5) * g.w, c1 = (cy + 0.5) * g.w, c2 = (cz + 0.5) * g.w;
+  double2 acc[KMC_MAXP + 1];
+  for (int n = 0; n <= g.p; n++) acc[n] = make_double2(0.0, 0.0);
+  int c = d.cnt[leaf];
+  const double4_32a* sp = d.spos64 + leaf * g.cap;
+  for (int j = 0; j < c; j++) {
+    double4_32a v = sp[j];
+    double x = v.x - c0, y = v.y - c1, z = v.z - c2, q = v.w;
+    double r2 = x * x + y * y + z * z;
+    double2 a1 = regular_mm(x, y, m), a2 = make_double2(0.0, 0.0);
+    acc[m].x += q * a1.x;
+    acc[m].y += q * a1.y;
+    for (int n = m + 1; n <= g.p; n++) {
+      double cc = f_inv_nm[tri(n, m)];
+      double zz = (2 * n - 1) * z;
+      double2 vv = make_double2((zz * a1.x - r2 * a2.x) * cc, (zz * a1.y - r2 * a2.y) * cc);
+      acc[n].x += q * vv.x;
+      acc[n].y += q * vv.y;
+      a2 = a1;
+      a1 = vv;
+    }
+  }
+  double2* out = d.Mt + (g.cell_off[g.L] + leaf) * g.P;
+  for (int n = m; n <= g.p; n++) out[tri(n, m)] = acc[n];
+}
+
+void fmm_p2m(const Geo& g, const Dev& d, cudaStream_t s) {
+  int64_t nt = g.ML * (g.p + 1);
+  k_p2m<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(g, d);
+}
+
+// ------------------------------------------------------------------ M2M
+// level l (parents, n_l per side) from level l+1.  thread per (parent, coefficient)
+__global__ void k_m2m(const Geo g, const Dev d, int l) {
+  extern __shared__ double2 sh[];  // 8 * P regular tables of the child offsets
+  int nl = 1 << (l - 1), nc = 2 * nl;
+  double wc = g.a / nc;
+  for (int o = threadIdx.x; o < 8; o += blockDim.x) {
+    double tx = ((o & 1) - 0.5) * wc, ty = (((o >> 1) & 1) - 0.5) * wc, tz = (((o >> 2) & 1) - 0.5) * wc;
+    regular_table(tx, ty, tz, g.p, sh + o * g.P);
+  }
+  __syncthreads();
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t ncl = (int64_t)nl * nl * nl;
+  int64_t cell = t / g.P;
+  int ci = (int)(t - cell * g.P);
+  if (cell >= ncl) return;
+  int n = 0;
+  while (tri(n + 1, 0) <= ci) n++;
+  int m = ci - tri(n, 0);
+  int px = (int)(cell % nl), py = (int)((cell / nl) % nl), pz = (int)(cell / ((int64_t)nl * nl));
+  double2 acc = make_double2(0.0, 0.0);
+  for (int o = 0; o < 8; o++) {
+    int cx = 2 * px + (o & 1), cy = 2 * py + ((o >> 1) & 1), cz = 2 * pz + ((o >> 2) & 1);
+    int64_t child = cx + (int64_t)nc * (cy + (int64_t)nc * cz);
+    const double2* Mc = d.Mt + (g.cell_off[l + 1] + child) * g.P;
+    const double2* Rt = sh + o * g.P;
+    for (int k = 0; k <= n; k++)
+      for (int ll = -k; ll <= k; ll++) {
+        int mm = m - ll;
+        if (mm > n - k || mm < -(n - k)) continue;
+        double2 a = tab_get(Mc, k, ll), b = tab_get(Rt, n - k, mm);
+        acc.x += a.x * b.x - a.y * b.y;
+        acc.y += a.x * b.y + a.y * b.x;
+      }
+  }
+  d.Mt[(g.cell_off[l] + cell) * g.P + ci] = acc;
+}
+
+void fmm_m2m(const Geo& g, const Dev& d, cudaStream_t s) {
+  for (int l = g.L - 1; l >= 1; l--) {
+    int64_t ncl = (int64_t)1 << (3 * (l - 1));
+    int64_t nt = ncl * g.P;
+    k_m2m<<<(unsigned)((nt + 127) / 128), 128, 8 * g.P * sizeof(double2), s>>>(g, d, l);
+  }
+}
+
+// ------------------------------------------------------------------ M2L tables
+// Itab[l][v] = I_j^mu(t_v * w_l) for the 343 offsets t_v in [-3,3]^3 (j <= 2p)
+__global__ void k_itab(const Geo g, const Dev d) {
+  int l = blockIdx.y + 2;
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= 343) return;
+  int tx = v % 7 - 3, ty = (v / 7) % 7 - 3, tz = v / 49 - 3;
+  if (abs(tx) <= 1 && abs(ty) <= 1 && abs(tz) <= 1) return;
+  double wl = g.a / (1 << (l - 1));
+  irregular_table(tx * wl, ty * wl, tz * wl, 2 * g.p, d.Itab + ((int64_t)l * 343 + v) * g.P2);
+}
+
+void fmm_itab(const Geo& g, const Dev& d, cudaStream_t s) {
+  dim3 grid((343 + 63) / 64, g.L - 1);
+  k_itab<<<grid, 64, 0, s>>>(g, d);
+}
+
+// ------------------------------------------------------------------ M2L
+// CTA per target cell on level l; thread per output coefficient.  The wrapped
+// interaction list of cell b (Sec. 3.1): offsets t = 2 delta + c - o with
+// delta in {-1,0,1}^3, c in {0,1}^3, o = b mod 2, excluding |t|_inf <= 1;
+// source = (b + t) mod n_l with translation vector t * w_l.
+__global__ void k_m2l(const Geo g, const Dev d, int l) {
+  extern __shared__ double2 shM[];  // P source coefficients
+  int nl = 1 << (l - 1);
+  int64_t cell = blockIdx.x;
+  int bx = (int)(cell % nl), by = (int)((cell / nl) % nl), bz = (int)(cell / ((int64_t)nl * nl));
+  int ox = bx & 1, oy = by & 1, oz = bz & 1;
+  int ci = threadIdx.x;
+  int n = 0, m = 0;
+  if (ci < g.P) {
+    while (tri(n + 1, 0) <= ci) n++;
+    m = ci - tri(n, 0);
+  }
+  double2 acc = make_double2(0.0, 0.0);
+  for (int dz = -1; dz <= 1; dz++)
+    for (int dy = -1; dy <= 1; dy++)
+      for (int dx = -1; dx <= 1; dx++)
+        for (int c = 0; c < 8; c++) {
+          int tx = 2 * dx + (c & 1) - ox, ty = 2 * dy + ((c >> 1) & 1) - oy, tz = 2 * dz + ((c >> 2) & 1) - oz;
+          if (abs(tx) <= 1 && abs(ty) <= 1 && abs(tz) <= 1) continue;
+          int sx = ((bx + tx) % nl + nl) % nl, sy = ((by + ty) % nl + nl) % nl, sz = ((bz + tz) % nl + nl) % nl;
+          int64_t src = sx + (int64_t)nl * (sy + (int64_t)nl * sz);
+          __syncthreads();
+          const double2* Ms = d.Mt + (g.cell_off[l] + src) * g.P;
+          for (int k = threadIdx.x; k < g.P; k += blockDim.x) shM[k] = Ms[k];
+          __syncthreads();
+          if (ci < g.P) {
+            int v = (tx + 3) + 7 * ((ty + 3) + 7 * (tz + 3));
+            const double2* It = d.Itab + ((int64_t)l * 343 + v) * g.P2;
+            for (int k = 0; k <= g.p; k++) {
+              double2 s = make_double2(0.0, 0.0);
+              for (int ll = -k; ll <= k; ll++) {
+                double2 a = tab_get(shM, k, ll);
+                double2 b = tab_get(It, n + k, m + ll);
+                // a * conj(b)
+                s.x += a.x * b.x + a.y * b.y;
+                s.y += a.y * b.x - a.x * b.y;
+              }
+              if (k & 1) { acc.x -= s.x; acc.y -= s.y; }
+              else { acc.x += s.x; acc.y += s.y; }
+            }
+          }
+        }
+  if (ci < g.P) d.Psi[(g.cell_off[l] + cell) * g.P + ci] = acc;
+}
+
+void fmm_m2l(const Geo& g, const Dev& d, cudaStream_t s) {
+  int bs = g.P <= 128 ? 128 : 256;
+  for (int l = 2; l <= g.L; l++) {
+    int64_t ncl = (int64_t)1 << (3 * (l - 1));
+    k_m2l<<<(unsigned)ncl, bs, g.P * sizeof(double2), s>>>(g, d, l);
+  }
+}
+
+// ------------------------------------------------------------------ lattice sums
+// S_j^mu = sum over far images nu (|nu|_inf >= 2) of I_j^mu(a nu), evaluated by
+// Ewald splitting of I_j^mu = (j-mu)!(j+mu)! R_j^mu(x)/|x|^{2j+1}:
+//   sum_{nu != 0} R(a nu)/|a nu|^{2j+1}
+//     = sum_{nu != 0} R(a nu) Q(j+1/2, beta^2 |a nu|^2) / |a nu|^{2j+1}
+//     + (-i)^j pi^{j-1/2} / (a^3 Gamma(j+1/2)) sum_{k = m/a != 0} R(k) exp(-pi^2 k^2 / beta^2) / k^2
+// (Poisson summation of the harmonic Gaussian; Q, P = regularised upper,
+// lower incomplete gamma).  The 26 nearest images are removed by dropping
+// their real-space terms and subtracting their smooth parts R P(..)/|x|^{2j+1}.
+// Degrees j <= 3 vanish in cubic summation order (j = 0 multiplies the zero
+// net charge; j = 1, 2, 3 vanish by cubic symmetry).
+#define LS_NR 6
+#define LS_KM 9
+#define LS_BETA_A 3.0
+
+__global__ void k_lattice_terms(const Geo g, double2* terms, int nvec) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nvec) return;
+  const int P2 = g.P2, p2 = 2 * g.p;
+  double2* out = terms + (int64_t)v * P2;
+  const int nr = 2 * LS_NR + 1, nk = 2 * LS_KM + 1;
+  const double a = g.a, beta = LS_BETA_A / a;
+  if (v < nr * nr * nr) {
+    int nx = v % nr - LS_NR, ny = (v / nr) % nr - LS_NR, nz = v / (nr * nr) - LS_NR;
+    int ninf = max(abs(nx), max(abs(ny), abs(nz)));
+    if (ninf == 0) {
+      for (int c = 0; c < P2; c++) out[c] = make_double2(0.0, 0.0);
+      return;
+    }
+    double x = a * nx, y = a * ny, z = a * nz;
+    double r2 = x * x + y * y + z * z, r = sqrt(r2);
+    double X = beta * beta * r2;
+    regular_table(x, y, z, p2, out);  // R_j^mu(a nu), scaled in place below
+    double qj = erfc(sqrt(X));                                     // Q(1/2, X)
+    double tj = 2.0 * sqrt(X) * exp(-X) / sqrt(M_PI);              // X^{1/2} e^{-X} / Gamma(3/2)
+    double rp = 1.0 / r;                                           // 1/r^{2j+1}
+    for (int j = 0; j <= p2; j++) {
+      double wgt;
+      if (ninf >= 2) {
+        wgt = qj;  // far image: real-space part
+      } else {
+        // near image: minus the smooth part P(j+1/2, X) by its positive series
+        double s = j + 0.5;
+        double term = exp(s * log(X) - X - lgamma(s + 1.0));
+        double sum = 0.0;
+        for (int k = 0; k < 400 && term > 1e-300; k++) {
+          sum += term;
+          term *= X / (s + k + 1.0);
+          if (k > X && term < 1e-18 * sum) break;
+        }
+        wgt = -sum;
+      }
+      for (int mu = 0; mu <= j; mu++) {
+        double f = f_fact[j - mu] * f_fact[j + mu] * wgt * rp;
+        double2 rv = out[tri(j, mu)];
+        out[tri(j, mu)] = make_double2(f * rv.x, f * rv.y);
+      }
+      qj += tj;
+      tj *= X / (j + 1.5);
+      rp /= r2;
+    }
+  } else {
+    int u = v - nr * nr * nr;
+    int mx = u % nk - LS_KM, my = (u / nk) % nk - LS_KM, mz = u / (nk * nk) - LS_KM;
+    if (mx == 0 && my == 0 && mz == 0) {
+      for (int c = 0; c < P2; c++) out[c] = make_double2(0.0, 0.0);
+      return;
+    }
+    double kx = mx / a, ky = my / a, kz = mz / a;
+    double k2 = kx * kx + ky * ky + kz * kz;
+    regular_table(kx, ky, kz, p2, out);  // R_j^mu(k), scaled in place below
+    double gk = exp(-M_PI * M_PI * k2 / (beta * beta)) / k2;
+    for (int j = 0; j <= p2; j++) {
+      double pre = exp((j - 0.5) * log(M_PI) - lgamma(j + 0.5)) / (a * a * a) * gk;
+      for (int mu = 0; mu <= j; mu++) {
+        double f = f_fact[j - mu] * f_fact[j + mu] * pre;
+        double2 rv = out[tri(j, mu)];
+        double2 t = make_double2(f * rv.x, f * rv.y);
+        // multiply by (-i)^j
+        double2 o;
+        switch (j & 3) {
+          case 0: o = t; break;
+          case 1: o = make_double2(t.y, -t.x); break;
+          case 2: o = make_double2(-t.x, -t.y); break;
+          default: o = make_double2(-t.y, t.x); break;
+        }
+        out[tri(j, mu)] = o;
+      }
+    }
+  }
+}
+
+__global__ void k_lattice_reduce(const Geo g, const double2* terms, int nvec, double2* S) {
+  __shared__ double sx[256], sy[256];
+  int c = blockIdx.x;
+  int j = 0;
+  while (tri(j + 1, 0) <= c) j++;
+  double ax = 0.0, ay = 0.0;
+  for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+    double2 t = terms[(int64_t)v * g.P2 + c];
+    ax += t.x;
+    ay += t.y;
+  }
+  sx[threadIdx.x] = ax;
+  sy[threadIdx.x] = ay;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) {
+      sx[threadIdx.x] += sx[threadIdx.x + st];
+      sy[threadIdx.x] += sy[threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) S[c] = (j <= 3) ? make_double2(0.0, 0.0) : make_double2(sx[0], sy[0]);
+}
+
+void fmm_lattice_sums(const Geo& g, const Dev& d, cudaStream_t s) {
+  const int nr = 2 * LS_NR + 1, nk = 2 * LS_KM + 1;
+  int nvec = nr * nr * nr + nk * nk * nk;
+  // scratch: nvec * P2 complex (reuses the per-step phi_new / dU buffers is not
+  // safe in general, so it is a dedicated temporary owned by the caller)
+  double2* terms = (double2*)d.scratch;
+  k_lattice_terms<<<(nvec + 63) / 64, 64, 0, s>>>(g, terms, nvec);
+  k_lattice_reduce<<<g.P2, 256, 0, s>>>(g, terms, nvec, d.S);
+}
+
+// ------------------------------------------------------------------ far field
+// H = R K: H_n^m = sum_{k,l} (-1)^k K_k^l conj(S_{n+k}^{m+l}), K = level-1 multipole
+__global__ void k_far_field(const Geo g, const Dev d) {
+  int ci = threadIdx.x;
+  if (ci >= g.P) return;
+  int n = 0;
+  while (tri(n + 1, 0) <= ci) n++;
+  int m = ci - tri(n, 0);
+  const double2* K = d.Mt + g.cell_off[1] * g.P;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int k = 0; k <= g.p; k++) {
+    double sgn = (k & 1) ? -1.0 : 1.0;
+    for (int ll = -k; ll <= k; ll++) {
+      double2 a = tab_get(K, k, ll), b = tab_get(d.S, n + k, m + ll);
+      acc.x += sgn * (a.x * b.x + a.y * b.y);
+      acc.y += sgn * (a.y * b.x - a.x * b.y);
+    }
+  }
+  d.Psi[g.cell_off[1] * g.P + ci] = acc;
+}
+
+void fmm_far_field(const Geo& g, const Dev& d, cudaStream_t s) {
+  k_far_field<<<1, g.P <= 128 ? 128 : 256, 0, s>>>(g, d);
+}
+
+// ------------------------------------------------------------------ dipole, self term
+// M = sum q r over user-order positions (fixed-order block reduction)
+__global__ void k_dipole(const Geo g, const Dev d) {
+  __shared__ double sh[3][512];
+  double a0 = 0, a1 = 0, a2 = 0;
+  for (int64_t i = threadIdx.x; i < g.n; i += blockDim.x) {
+    double q = d.q[i];
+    a0 += q * d.pos[3 * i];
+    a1 += q * d.pos[3 * i + 1];
+    a2 += q * d.pos[3 * i + 2];
+  }
+  sh[0][threadIdx.x] = a0;
+  sh[1][threadIdx.x] = a1;
+  sh[2][threadIdx.x] = a2;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int c = 0; c < 3; c++) sh[c][threadIdx.x] += sh[c][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) d.dip[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// C(d) = sum_{nu in V} 1/|d - a nu| - sum_{nu in V, nu != 0} 1/|a nu| + g(d) - g(0) + 2 pi |d|^2 / (3V)
+// with V = {-1,0,1}^3 and g(d) = Re sum conj(S_n^m) R_n^m(d) (n <= p): the
+// moving charge's interaction with its own images, equal to psi(d) - psi_reg(0)
+// of the tinfoil pair potential.
+__device__ double self_corr_dev(const Geo& g, const double2* S, double dx, double dy, double dz) {
+  double s = 0.0;
+  for (int a = -1; a <= 1; a++)
+    for (int b = -1; b <= 1; b++)
+      for (int c = -1; c <= 1; c++) {
+        double x = dx - g.a * a, y = dy - g.a * b, z = dz - g.a * c;
+        s += 1.0 / sqrt(x * x + y * y + z * z);
+        if (a || b || c) s -= 1.0 / (g.a * sqrt((double)(a * a + b * b + c * c)));
+      }
+  // g(d) - g(0): accumulate the regular harmonics along each m column
+  double r2 = dx * dx + dy * dy + dz * dz;
+  double2 mm = make_double2(1.0, 0.0);
+  double gd = 0.0;
+  for (int m = 0; m <= g.p; m++) {
+    if (m > 0) {
+      double sc = -0.5 / m;
+      mm = make_double2(sc * (dx * mm.x - dy * mm.y), sc * (dx * mm.y + dy * mm.x));
+    }
+    double2 a2 = make_double2(0.0, 0.0), a1 = mm;
+    double col = 0.0;
+    for (int n = m; n <= g.p; n++) {
+      double2 v;
+      if (n == m) v = mm;
+      else {
+        double cc = f_inv_nm[tri(n, m)];
+        double zz = (2 * n - 1) * dz;
+        v = make_double2((zz * a1.x - r2 * a2.x) * cc, (zz * a1.y - r2 * a2.y) * cc);
+        a2 = a1;
+        a1 = v;
+      }
+      if (n == 0) continue;  // the constant term cancels in g(d) - g(0)
+      double2 sv = S[tri(n, m)];
+      col += sv.x * v.x + sv.y * v.y;  // Re(conj(S) R)
+    }
+    gd += (m == 0 ? 1.0 : 2.0) * col;
+  }
+  double V = g.a * g.a * g.a;
+  return s + gd + 2.0 * M_PI / (3.0 * V) * r2;
+}
+
+__global__ void k_selfcorr(const Geo g, const Dev d) {
+  int k = threadIdx.x;
+  if (k >= KMC_NHOP) return;
+  double h = (g.E > 0) ? g.h : 1.0;
+  double dx = 0, dy = 0, dz = 0;
+  double sgn = (k & 1) ? -h : h;
+  if (k < 2) dx = sgn; else if (k < 4) dy = sgn; else dz = sgn;
+  d.selfc[k] = self_corr_dev(g, d.S, dx, dy, dz);
+}
+
+void fmm_self_and_dipole(const Geo& g, const Dev& d, cudaStream_t s) {
+  k_dipole<<<1, 512, 0, s>>>(g, d);
+  k_selfcorr<<<1, 32, 0, s>>>(g, d);
+}
+
+// general-d self correction used by the off-lattice assembly
+__global__ void k_selfcorr_list(const Geo g, const double2* S, int64_t m, const double* dvec, double* out) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  out[t] = self_corr_dev(g, S, dvec[3 * t], dvec[3 * t + 1], dvec[3 * t + 2]);
+}
+
+void fmm_selfcorr_list(const Geo& g, const Dev& d, int64_t m, const double* dvec, double* out, cudaStream_t s) {
+  k_selfcorr_list<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(g, d.S, m, dvec, out);
+}
+
+// ------------------------------------------------------------------ downward pass
+// Peff_1 = H; Peff_l[b] = L2L(Peff_{l-1}[parent] -> c_b) + Psi_l[b]   (precision T)
+template <typename T>
+__global__ void k_downward(const Geo g, const Dev d, int l) {
+  typedef typename cplx<T>::type C;
+  extern __shared__ unsigned char shraw[];
+  C* Rt = (C*)shraw;  // 8 * P child-offset regular tables
+  C* Pe = (C*)d.Peff;
+  if (l == 1) {
+    for (int c = threadIdx.x; c < g.P; c += blockDim.x) {
+      double2 v = d.Psi[g.cell_off[1] * g.P + c];
+      Pe[g.cell_off[1] * g.P + c] = cmk<C>(v.x, v.y);
+    }
+    return;
+  }
+  int nl = 1 << (l - 1), np = nl / 2;
+  double wc = g.a / nl;
+  if (threadIdx.x < 8) {
+    int o = threadIdx.x;
+    double tx = ((o & 1) - 0.5) * wc, ty = (((o >> 1) & 1) - 0.5) * wc, tz = (((o >> 2) & 1) - 0.5) * wc;
+    double r2 = tx * tx + ty * ty + tz * tz;
+    double2 mm = make_double2(1.0, 0.0);
+    for (int m = 0; m <= g.p; m++) {
+      if (m > 0) {
+        double s = -0.5 / m;
+        mm = make_double2(s * (tx * mm.x - ty * mm.y), s * (tx * mm.y + ty * mm.x));
+      }
+      Rt[o * g.P + tri(m, m)] = cmk<C>(mm.x, mm.y);
+      double2 a2 = make_double2(0.0, 0.0), a1 = mm;
+      for (int n = m + 1; n <= g.p; n++) {
+        double c = f_inv_nm[tri(n, m)];
+        double zz = (2 * n - 1) * tz;
+        double2 v = make_double2((zz * a1.x - r2 * a2.x) * c, (zz * a1.y - r2 * a2.y) * c);
+        Rt[o * g.P + tri(n, m)] = cmk<C>(v.x, v.y);
+        a2 = a1;
+        a1 = v;
+      }
+    }
+  }
+  __syncthreads();
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t ncl = (int64_t)nl * nl * nl;
+  int64_t cell = t / g.P;
+  int ci = (int)(t - cell * g.P);
+  if (cell >= ncl) return;
+  int k = 0;
+  while (tri(k + 1, 0) <= ci) k++;
+  int lo = ci - tri(k, 0);
+  int bx = (int)(cell % nl), by = (int)((cell / nl) % nl), bz = (int)(cell / ((int64_t)nl * nl));
+  int o = (bx & 1) | ((by & 1) << 1) | ((bz & 1) << 2);
+  int64_t par = (bx >> 1) + (int64_t)np * ((by >> 1) + (int64_t)np * (bz >> 1));
+  const C* Lp = Pe + (g.cell_off[l - 1] + par) * g.P;
+  const C* R = Rt + o * g.P;
+  T ax = 0, ay = 0;
+  for (int n = k; n <= g.p; n++) {
+    int j = n - k;
+    for (int m = lo - j; m <= lo + j; m++) {
+      if (m < -n || m > n) continue;
+      C a = tab_get(Lp, n, m), b = tab_get(R, j, m - lo);
+      ax += a.x * b.x - a.y * b.y;
+      ay += a.x * b.y + a.y * b.x;
+    }
+  }
+  double2 own = d.Psi[(g.cell_off[l] + cell) * g.P + ci];
+  C out;
+  out.x = ax + (T)own.x;
+  out.y = ay + (T)own.y;
+  Pe[(g.cell_off[l] + cell) * g.P + ci] = out;
+}
+
+void fmm_downward(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
+  for (int l = 1; l <= g.L; l++) {
+    int64_t ncl = (int64_t)1 << (3 * (l - 1));
+    int64_t nt = (l == 1) ? 128 : ncl * g.P;
+    unsigned blocks = (unsigned)((nt + 127) / 128);
+    if (prec == 0)
+      k_downward<double><<<blocks, 128, 8 * g.P * sizeof(double2), s>>>(g, d, l);
+    else
+      k_downward<float><<<blocks, 128, 8 * g.P * sizeof(float2), s>>>(g, d, l);
+  }
+}
+
+// ------------------------------------------------------------------ drift
+// out2[0] = max |a - b|, out2[1] = max |b| (as non-negative doubles via integer max)
+__global__ void k_drift(const double2* a, const double2* b, int64_t count, unsigned long long* out2) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double e = 0.0, m = 0.0;
+  for (; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    double2 x = a[i], y = b[i];
+    e = fmax(e, fmax(fabs(x.x - y.x), fabs(x.y - y.y)));
+    m = fmax(m, fmax(fabs(y.x), fabs(y.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    e = fmax(e, __shfl_xor_sync(0xffffffff, e, o));
+    m = fmax(m, __shfl_xor_sync(0xffffffff, m, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out2[0], (unsigned long long)__double_as_longlong(e));
+    atomicMax(&out2[1], (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+void fmm_drift(const Geo& g, const double2* a, const double2* b, int64_t count, double* out2, cudaStream_t s) {
+  (void)g;
+  cudaMemsetAsync(out2, 0, 2 * sizeof(double), s);
+  k_drift<<<1024, 256, 0, s>>>(a, b, count, (unsigned long long*)out2);
+}

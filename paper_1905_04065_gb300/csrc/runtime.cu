@@ -1,0 +1,805 @@
+// runtime.cu -- host runtime and C ABI of the FMM-for-KMC library (see
+// include/kmcfmm.h for the contract of every entry point).
+//
+// The runtime owns all device memory of a handle, orders every launch on
+// the caller's stream, checks every CUDA call, reads the device error flags
+// after each synchronising call, and replays the device-driven KMC step loop
+// from CUDA graphs.  No arithmetic of the method runs on the host.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/kmcfmm.h"
+#include "common.cuh"
+
+struct kmc_fmm {
+  Geo g;
+  Dev d;
+  int prec;
+  int mem;
+  int device;
+  cudaStream_t stream;
+  char msg[512];
+  bool broken;
+  bool peff_valid;    // leaf expansions reflect the current expansions
+  bool rates_valid;   // device rates belong to the current configuration
+  std::vector<void*> allocs;
+  // general-propose scratch
+  size_t gen_cap;
+  int32_t* gen_part;
+  double* gen_tgt;
+  double* gen_old;
+  double* gen_pn;
+  double* gen_po;
+  double* gen_dv;
+  double* gen_du;
+  uint8_t* gen_mask;
+  // step-loop capacity and graph
+  int run_cap;
+  cudaGraphExec_t graph;
+  int graph_steps;
+  double* drift2;
+  int32_t* iota;
+};
+
+static const char* g_static_msg = "invalid handle";
+
+static int fail(kmc_fmm* h, int code, const char* fmt, ...) {
+  if (!h) return code;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(h->msg, sizeof(h->msg), fmt, ap);
+  va_end(ap);
+  if (code == KMC_ERR_CUDA || code == KMC_ERR_CAPACITY) h->broken = true;
+  return code;
+}
+
+#define CK(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail(h, KMC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CKLAUNCH()                                                                                \
+  do {                                                                                            \
+    cudaError_t e_ = cudaGetLastError();                                                          \
+    if (e_ != cudaSuccess) return fail(h, KMC_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename P>
+static int dalloc(kmc_fmm* h, P** ptr, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return fail(h, KMC_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  h->allocs.push_back(p);
+  *ptr = (P*)p;
+  return KMC_OK;
+}
+
+#define ALLOC(ptr, bytes)                        \
+  do {                                           \
+    int r_ = dalloc(h, &(ptr), (size_t)(bytes)); \
+    if (r_) return r_;                           \
+  } while (0)
+
+static cudaMemcpyKind in_kind(const kmc_fmm* h) {
+  return h->mem == KMC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+static cudaMemcpyKind out_kind(const kmc_fmm* h) {
+  return h->mem == KMC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+// read and clear the device error flags; map them to a status
+static int check_flags(kmc_fmm* h, const char* where) {
+  int e[4];
+  CK(cudaMemcpyAsync(e, h->d.err, sizeof(e), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (e[0] == 0) return KMC_OK;
+  CK(cudaMemsetAsync(h->d.err, 0, sizeof(e), h->stream));
+  if (e[0] & KMC_DERR_CAPACITY) return fail(h, KMC_ERR_CAPACITY, "%s: a leaf cell ran out of slots", where);
+  if (e[0] & KMC_DERR_BADPOS) return fail(h, KMC_ERR_ARG, "%s: a position is not finite or outside [0, box)", where);
+  if (e[0] & KMC_DERR_BADSITE) return fail(h, KMC_ERR_ARG, "%s: a position is not on a lattice site", where);
+  if (e[0] & KMC_DERR_SINGULAR)
+    return fail(h, KMC_ERR_ARG, "%s: a target coincides with a charge (singular move)", where);
+  return fail(h, KMC_ERR_STATE, "%s: device error flags 0x%x", where, e[0]);
+}
+
+static int guard(kmc_fmm* h) {
+  if (!h) return KMC_ERR_ARG;
+  if (h->broken) return fail(h, KMC_ERR_STATE, "handle unusable after an earlier error: %s", h->msg);
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return fail(h, KMC_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  return KMC_OK;
+}
+
+// ------------------------------------------------------------------ full FMM
+static int full_fmm(kmc_fmm* h) {
+  const Geo& g = h->g;
+  const Dev& d = h->d;
+  cudaStream_t s = h->stream;
+  CK(cudaMemsetAsync(d.Mt, 0, sizeof(double2) * g.ncell_total * g.P, s));
+  fmm_p2m(g, d, s);
+  fmm_m2m(g, d, s);
+  fmm_m2l(g, d, s);
+  fmm_far_field(g, d, s);
+  fmm_self_and_dipole(g, d, s);
+  CKLAUNCH();
+  h->peff_valid = false;
+  h->rates_valid = false;
+  return KMC_OK;
+}
+
+static int refresh_peff(kmc_fmm* h) {
+  if (h->peff_valid) return KMC_OK;
+  fmm_downward(h->g, h->d, h->prec, h->stream);
+  CKLAUNCH();
+  h->peff_valid = true;
+  return KMC_OK;
+}
+
+// potential at every charge (own term excluded) into d.phi_old
+static int compute_phi_old(kmc_fmm* h) {
+  int r = refresh_peff(h);
+  if (r) return r;
+  if (h->g.E > 0) {
+    kmc_propose_lattice(h->g, h->d, h->prec, h->stream);
+    kmc_finalize_rates(h->g, h->d, h->stream);
+    h->rates_valid = true;
+  } else {
+    kmc_eval_points(h->g, h->d, h->prec, h->g.n, h->d.pos, h->iota, h->d.phi_old, h->stream);
+  }
+  CKLAUNCH();
+  return KMC_OK;
+}
+
+static int compute_energy(kmc_fmm* h) {
+  int r = compute_phi_old(h);
+  if (r) return r;
+  kmc_energy_reduce(h->g, h->d, h->stream);
+  CKLAUNCH();
+  return KMC_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+void kmc_opts_default(kmc_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = KMC_PREC_FP64;
+  o->lattice_edge = 0;
+  o->lattice_h = 1.0;
+  o->kT = 1.0;
+  o->stream = nullptr;
+  o->mem = KMC_MEM_HOST;
+  o->device = 0;
+  o->leaf_capacity = 0;
+}
+
+const char* kmc_last_error(kmc_handle h) { return h ? h->msg : g_static_msg; }
+
+void kmc_fmm_destroy(kmc_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (void* p : h->allocs) cudaFree(p);
+  delete h;
+}
+
+static int init_impl(kmc_fmm* h, int64_t n, const double* positions, const double* charges, double box, int levels,
+                     int order) {
+  Geo& g = h->g;
+  Dev& d = h->d;
+  memset(&g, 0, sizeof(g));
+  memset(&d, 0, sizeof(d));
+  g.L = levels;
+  g.p = order;
+  g.P = ncoef(order);
+  g.P2 = ncoef(2 * order);
+  g.nL = 1 << (levels - 1);
+  g.n = n;
+  g.ML = (int64_t)g.nL * g.nL * g.nL;
+  g.a = box;
+  g.w = box / g.nL;
+  g.kT = 1.0;
+  int64_t off = 0;
+  for (int l = 1; l <= levels; l++) {
+    g.cell_off[l] = off;
+    off += (int64_t)1 << (3 * (l - 1));
+  }
+  g.cell_off[levels + 1] = off;
+  g.ncell_total = off;
+  return KMC_OK;
+}
+
+int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const double* charges, double box, int levels,
+                 int order, const kmc_opts* opts) {
+  if (!out) return KMC_ERR_ARG;
+  *out = nullptr;
+  kmc_opts o;
+  if (opts) o = *opts;
+  else kmc_opts_default(&o);
+  kmc_fmm* h = new kmc_fmm();
+  memset(h->msg, 0, sizeof(h->msg));
+  h->broken = false;
+  h->prec = o.precision == KMC_PREC_MIXED ? 1 : 0;
+  h->mem = o.mem;
+  h->device = o.device;
+  h->stream = (cudaStream_t)o.stream;
+  h->graph = nullptr;
+  h->graph_steps = 0;
+  h->gen_cap = 0;
+  h->run_cap = 0;
+  *out = h;
+  // ---- host-side argument checks
+  if (n < 2) return fail(h, KMC_ERR_ARG, "need at least 2 charges (n = %lld)", (long long)n);
+  if (n > 0x7fffffffLL / 6) return fail(h, KMC_ERR_ARG, "too many charges (n = %lld)", (long long)n);
+  if (levels < 3 || levels > KMC_MAXL) return fail(h, KMC_ERR_ARG, "levels must be in [3, %d] (got %d)", KMC_MAXL, levels);
+  if (order < 1 || order > KMC_MAXP) return fail(h, KMC_ERR_ARG, "order must be in [1, %d] (got %d)", KMC_MAXP, order);
+  if (!(box > 0.0) || !isfinite(box)) return fail(h, KMC_ERR_ARG, "box must be positive and finite");
+  if (!positions || !charges) return fail(h, KMC_ERR_ARG, "positions and charges are required");
+  if (o.precision != KMC_PREC_FP64 && o.precision != KMC_PREC_MIXED) return fail(h, KMC_ERR_ARG, "unknown precision");
+  if (o.mem != KMC_MEM_HOST && o.mem != KMC_MEM_DEVICE) return fail(h, KMC_ERR_ARG, "unknown memory kind");
+  if (!(o.kT > 0.0)) return fail(h, KMC_ERR_ARG, "kT must be positive");
+  int r = init_impl(h, n, positions, charges, box, levels, order);
+  if (r) return r;
+  Geo& g = h->g;
+  g.kT = o.kT;
+  if (o.lattice_edge > 0) {
+    int E = o.lattice_edge;
+    if (E % g.nL != 0) return fail(h, KMC_ERR_ARG, "lattice edge %d is not a multiple of 2^(levels-1) = %d", E, g.nL);
+    if (!(o.lattice_h > 0.0)) return fail(h, KMC_ERR_ARG, "lattice spacing must be positive");
+    if (fabs(E * o.lattice_h - box) > 1e-12 * box)
+      return fail(h, KMC_ERR_ARG, "box (%g) must equal lattice_edge * lattice_h (%g)", box, E * o.lattice_h);
+    g.E = E;
+    g.h = o.lattice_h;
+    g.W = E / g.nL;
+    // the propose kernel keeps a leaf's evaluation points and a source chunk in shared memory
+    if (g.W < 1 || g.W > 12) return fail(h, KMC_ERR_ARG, "lattice sites per leaf side must be in [1, 12] (got %d)", g.W);
+    if ((int64_t)E * E * E > 0x7fffffffLL) return fail(h, KMC_ERR_ARG, "lattice too large");
+    if (n > (int64_t)E * E * E) return fail(h, KMC_ERR_ARG, "more charges than sites");
+    g.cap = g.W * g.W * g.W;
+  } else {
+    g.E = 0;
+    g.h = 1.0;
+    g.W = 0;
+  }
+  cudaError_t ce = cudaSetDevice(h->device);
+  if (ce != cudaSuccess) return fail(h, KMC_ERR_CUDA, "cudaSetDevice(%d): %s", h->device, cudaGetErrorString(ce));
+  // charges to host for the neutrality check
+  std::vector<double> qh(n);
+  if (h->mem == KMC_MEM_DEVICE) {
+    CK(cudaMemcpy(qh.data(), charges, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  } else {
+    memcpy(qh.data(), charges, sizeof(double) * n);
+  }
+  double qs = 0.0, qa = 0.0;
+  for (int64_t i = 0; i < n; i++) {
+    if (!isfinite(qh[i])) return fail(h, KMC_ERR_ARG, "charge %lld is not finite", (long long)i);
+    qs += qh[i];
+    qa += fabs(qh[i]);
+  }
+  if (fabs(qs) > 1e-12 * qa) return fail(h, KMC_ERR_NOT_NEUTRAL, "sum of charges %.3e is not zero", qs);
+  // off-lattice capacity from the initial occupancy
+  std::vector<double> ph;
+  if (g.E == 0) {
+    ph.resize(3 * n);
+    if (h->mem == KMC_MEM_DEVICE) {
+      CK(cudaMemcpy(ph.data(), positions, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+    } else {
+      memcpy(ph.data(), positions, sizeof(double) * 3 * n);
+    }
+    std::vector<int32_t> cnt(g.ML, 0);
+    int mx = 0;
+    for (int64_t i = 0; i < n; i++) {
+      int c[3];
+      for (int k = 0; k < 3; k++) {
+        double x = ph[3 * i + k];
+        if (!isfinite(x) || x < 0.0 || x >= box) return fail(h, KMC_ERR_ARG, "position of charge %lld outside [0, box)", (long long)i);
+        c[k] = (int)floor(x / g.w);
+        if (c[k] >= g.nL) c[k] = g.nL - 1;
+      }
+      int64_t lf = c[0] + (int64_t)g.nL * (c[1] + (int64_t)g.nL * c[2]);
+      mx = cnt[lf] + 1 > mx ? cnt[lf] + 1 : mx;
+      cnt[lf]++;
+    }
+    int cap = o.leaf_capacity > 0 ? o.leaf_capacity : 2 * mx + 32;
+    if (cap < mx) return fail(h, KMC_ERR_CAPACITY, "leaf capacity %d below initial occupancy %d", cap, mx);
+    g.cap = cap;
+  }
+  // ---- allocations
+  Dev& d = h->d;
+  const int64_t nslot = g.ML * g.cap;
+  ALLOC(d.q, sizeof(double) * n);
+  ALLOC(d.pos, sizeof(double) * 3 * n);
+  ALLOC(d.site, sizeof(int32_t) * n);
+  ALLOC(d.slot_of, sizeof(int32_t) * n);
+  ALLOC(d.cnt, sizeof(int32_t) * g.ML);
+  ALLOC(d.uid, sizeof(int32_t) * nslot);
+  ALLOC(d.spos64, sizeof(double4_32a) * nslot);
+  ALLOC(d.spos32, sizeof(float4) * nslot);
+  ALLOC(d.Mt, sizeof(double2) * g.ncell_total * g.P);
+  ALLOC(d.Psi, sizeof(double2) * g.ncell_total * g.P);
+  ALLOC(d.Peff, (h->prec == 0 ? sizeof(double2) : sizeof(float2)) * g.ncell_total * g.P);
+  ALLOC(d.Itab, sizeof(double2) * (size_t)(g.L + 1) * 343 * g.P2);
+  ALLOC(d.S, sizeof(double2) * g.P2);
+  ALLOC(d.selfc, sizeof(double) * KMC_NHOP);
+  ALLOC(d.dip, sizeof(double) * 3);
+  ALLOC(d.U, sizeof(double));
+  ALLOC(d.phi_old, sizeof(double) * n);
+  ALLOC(d.phi_new, sizeof(double) * 6 * n);
+  ALLOC(d.mask, sizeof(uint8_t) * 6 * n);
+  ALLOC(d.dU, sizeof(double) * 6 * n);
+  ALLOC(d.rate, sizeof(double) * 6 * n);
+  ALLOC(d.bsum, sizeof(double) * ((n + 255) / 256 + 1));
+  ALLOC(d.event, sizeof(int64_t) * 2);
+  ALLOC(d.dtq, sizeof(double) * 2);
+  ALLOC(d.move, sizeof(MoveRec));
+  ALLOC(d.err, sizeof(int) * 4);
+  ALLOC(d.uni_small, sizeof(double) * 2);
+  ALLOC(d.stepc, sizeof(int) * 2);
+  ALLOC(h->drift2, sizeof(double) * 2);
+  ALLOC(h->iota, sizeof(int32_t) * n);
+  {
+    const int nr = 13, nk = 19;
+    size_t terms = (size_t)(nr * nr * nr + nk * nk * nk) * g.P2 * sizeof(double2);
+    ALLOC(d.scratch, terms);
+  }
+  cudaStream_t s = h->stream;
+  CK(cudaMemsetAsync(d.err, 0, sizeof(int) * 4, s));
+  CK(cudaMemsetAsync(d.uid, 0xff, sizeof(int32_t) * nslot, s));
+  CK(cudaMemsetAsync(d.mask, 0, 6 * n, s));
+  CK(cudaMemsetAsync(d.Psi, 0, sizeof(double2) * g.ncell_total * g.P, s));
+  CK(cudaMemcpyAsync(d.q, charges, sizeof(double) * n, in_kind(h), s));
+  CK(cudaMemcpyAsync(d.pos, positions, sizeof(double) * 3 * n, in_kind(h), s));
+  {
+    std::vector<int32_t> io(n);
+    for (int64_t i = 0; i < n; i++) io[i] = (int32_t)i;
+    CK(cudaMemcpyAsync(h->iota, io.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  fmm_upload_constants(order);
+  kmc_upload_constants(order);
+  kmc_prepare(g, h->prec);
+  CKLAUNCH();
+  kmc_validate(g, d, s);
+  CKLAUNCH();
+  r = check_flags(h, "init");
+  if (r) return r;
+  if (g.E > 0) {  // two charges on one site?
+    std::vector<int32_t> sh(n);
+    CK(cudaMemcpy(sh.data(), d.site, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    std::vector<uint8_t> occ((size_t)g.E * g.E * g.E, 0);
+    for (int64_t i = 0; i < n; i++) {
+      if (occ[sh[i]]) return fail(h, KMC_ERR_ARG, "two charges on lattice site %d", sh[i]);
+      occ[sh[i]] = 1;
+    }
+  }
+  fmm_bin(g, d, s);
+  CKLAUNCH();
+  r = check_flags(h, "init binning");
+  if (r) return r;
+  fmm_itab(g, d, s);
+  fmm_lattice_sums(g, d, s);
+  CKLAUNCH();
+  r = full_fmm(h);
+  if (r) return r;
+  r = compute_energy(h);
+  if (r) return r;
+  return check_flags(h, "init");
+}
+
+int kmc_fmm_energy(kmc_handle h, double* U) {
+  int r = guard(h);
+  if (r) return r;
+  if (!U) return fail(h, KMC_ERR_ARG, "U is NULL");
+  CK(cudaMemcpyAsync(U, h->d.U, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return KMC_OK;
+}
+
+int kmc_fmm_propose_lattice(kmc_handle h, uint8_t* mask, double* dU) {
+  int r = guard(h);
+  if (r) return r;
+  if (h->g.E <= 0) return fail(h, KMC_ERR_STATE, "kmc_fmm_propose_lattice needs lattice mode");
+  r = refresh_peff(h);
+  if (r) return r;
+  kmc_propose_lattice(h->g, h->d, h->prec, h->stream);
+  kmc_finalize_rates(h->g, h->d, h->stream);
+  CKLAUNCH();
+  h->rates_valid = true;
+  const int64_t m = 6 * h->g.n;
+  if (mask) CK(cudaMemcpyAsync(mask, h->d.mask, m, out_kind(h), h->stream));
+  if (dU) CK(cudaMemcpyAsync(dU, h->d.dU, sizeof(double) * m, out_kind(h), h->stream));
+  return check_flags(h, "propose_lattice");
+}
+
+static int ensure_gen(kmc_fmm* h, int64_t m) {
+  if ((size_t)m <= h->gen_cap) return KMC_OK;
+  size_t c = (size_t)m < 1024 ? 1024 : (size_t)m;
+  ALLOC(h->gen_part, sizeof(int32_t) * c);
+  ALLOC(h->gen_tgt, sizeof(double) * 3 * c);
+  ALLOC(h->gen_old, sizeof(double) * 3 * c);
+  ALLOC(h->gen_pn, sizeof(double) * c);
+  ALLOC(h->gen_po, sizeof(double) * c);
+  ALLOC(h->gen_dv, sizeof(double) * 3 * c);
+  ALLOC(h->gen_du, sizeof(double) * c);
+  ALLOC(h->gen_mask, sizeof(uint8_t) * c);
+  h->gen_cap = c;
+  return KMC_OK;
+}
+
+// stage general proposals on the device: inputs copied (host memory) or used
+// in place (device memory), then wrapped / gathered by a kernel.
+static int stage_general(kmc_fmm* h, int64_t m, const int32_t* particle, const double* target, const uint8_t* mask,
+                         bool host_inputs) {
+  int r = ensure_gen(h, m);
+  if (r) return r;
+  cudaStream_t s = h->stream;
+  const int32_t* pd = particle;
+  const double* td = target;
+  const uint8_t* md = mask;
+  if (host_inputs) {
+    CK(cudaMemcpyAsync(h->gen_part, particle, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->gen_dv, target, sizeof(double) * 3 * m, cudaMemcpyHostToDevice, s));
+    pd = h->gen_part;
+    td = h->gen_dv;
+    if (mask) {
+      CK(cudaMemcpyAsync(h->gen_mask, mask, m, cudaMemcpyHostToDevice, s));
+      md = h->gen_mask;
+    }
+  } else {
+    CK(cudaMemcpyAsync(h->gen_part, particle, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
+    pd = h->gen_part;
+  }
+  // targets are read before dv is written (same thread, same index), so the
+  // dv buffer may double as the staging area for host targets
+  kmc_stage_general(h->g, h->d, m, pd, td, md, h->gen_tgt, h->gen_old, h->gen_dv, h->gen_mask, s);
+  CKLAUNCH();
+  return KMC_OK;
+}
+
+static int general_du(kmc_fmm* h, int64_t m) {
+  int r = refresh_peff(h);
+  if (r) return r;
+  const Geo& g = h->g;
+  cudaStream_t s = h->stream;
+  kmc_eval_points(g, h->d, h->prec, m, h->gen_tgt, h->gen_part, h->gen_pn, s);
+  kmc_eval_points(g, h->d, h->prec, m, h->gen_old, h->gen_part, h->gen_po, s);
+  fmm_selfcorr_list(g, h->d, m, h->gen_dv, h->gen_du, s);
+  kmc_assemble_general(g, h->d, m, h->gen_part, h->gen_tgt, h->gen_mask, h->gen_pn, h->gen_po, h->gen_du, s);
+  CKLAUNCH();
+  return KMC_OK;
+}
+
+int kmc_fmm_propose(kmc_handle h, int64_t m, const int32_t* particle, const double* target, const uint8_t* mask,
+                    double* dU) {
+  int r = guard(h);
+  if (r) return r;
+  if (m < 0) return fail(h, KMC_ERR_ARG, "negative proposal count");
+  if (m == 0) return KMC_OK;
+  if (!particle || !target || !dU) return fail(h, KMC_ERR_ARG, "particle, target and dU are required");
+  r = stage_general(h, m, particle, target, mask, h->mem == KMC_MEM_HOST);
+  if (r) return r;
+  r = check_flags(h, "propose");
+  if (r) return r;
+  r = general_du(h, m);
+  if (r) return r;
+  CK(cudaMemcpyAsync(dU, h->gen_du, sizeof(double) * m, out_kind(h), h->stream));
+  return check_flags(h, "propose");
+}
+
+static int accept_general(kmc_fmm* h, int32_t particle, const double* tgt_host, double* dU_out) {
+  const Geo& g = h->g;
+  if (particle < 0 || particle >= g.n) return fail(h, KMC_ERR_ARG, "particle index out of range");
+  int r = stage_general(h, 1, &particle, tgt_host, nullptr, true);
+  if (r) return r;
+  r = check_flags(h, "accept");
+  if (r) return r;
+  double th[3];
+  CK(cudaMemcpy(th, h->gen_tgt, sizeof(th), cudaMemcpyDeviceToHost));
+  MoveRec mv;
+  memset(&mv, 0, sizeof(mv));
+  mv.valid = 1;
+  mv.i = particle;
+  mv.site_old = -1;
+  mv.site_new = -1;
+  double old[3];
+  CK(cudaMemcpy(old, h->gen_old, sizeof(old), cudaMemcpyDeviceToHost));
+  double qv;
+  CK(cudaMemcpy(&qv, h->d.q + particle, sizeof(double), cudaMemcpyDeviceToHost));
+  mv.q = qv;
+  for (int k = 0; k < 3; k++) {
+    mv.r[k] = old[k];
+    mv.rn[k] = th[k];
+  }
+  if (g.E > 0) {
+    int ix[3], ox[3];
+    for (int k = 0; k < 3; k++) {
+      double f = mv.rn[k] / g.h - 0.5;
+      double rf = rint(f);
+      if (fabs(f - rf) > 1e-9) return fail(h, KMC_ERR_ARG, "accept: target is not a lattice site");
+      ix[k] = ((int)rf % g.E + g.E) % g.E;
+      mv.rn[k] = (ix[k] + 0.5) * g.h;
+      ox[k] = (int)rint(mv.r[k] / g.h - 0.5);
+    }
+    mv.site_new = ix[0] + g.E * (ix[1] + g.E * ix[2]);
+    mv.site_old = ox[0] + g.E * (ox[1] + g.E * ox[2]);
+    CK(cudaMemcpy(h->gen_tgt, mv.rn, sizeof(mv.rn), cudaMemcpyHostToDevice));
+  }
+  r = general_du(h, 1);
+  if (r) return r;
+  double du;
+  CK(cudaMemcpyAsync(&du, h->gen_du, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  r = check_flags(h, "accept");
+  if (r) return r;
+  if (!isfinite(du)) return fail(h, KMC_ERR_ARG, "accept: singular move");
+  mv.dU = du;
+  CK(cudaMemcpyAsync(h->d.move, &mv, sizeof(mv), cudaMemcpyHostToDevice, h->stream));
+  kmc_accept_apply(g, h->d, h->stream);
+  CKLAUNCH();
+  h->peff_valid = false;
+  h->rates_valid = false;
+  r = check_flags(h, "accept");
+  if (r) return r;
+  if (dU_out) *dU_out = du;
+  return KMC_OK;
+}
+
+int kmc_fmm_accept(kmc_handle h, int32_t particle, const double target[3], double* dU_accepted) {
+  int r = guard(h);
+  if (r) return r;
+  if (!target) return fail(h, KMC_ERR_ARG, "target is NULL");
+  double t[3];
+  if (h->mem == KMC_MEM_DEVICE) {
+    CK(cudaMemcpy(t, target, sizeof(t), cudaMemcpyDeviceToHost));
+  } else {
+    memcpy(t, target, sizeof(t));
+  }
+  return accept_general(h, particle, t, dU_accepted);
+}
+
+int kmc_fmm_accept_event(kmc_handle h, int64_t event, double* dU_accepted) {
+  int r = guard(h);
+  if (r) return r;
+  const Geo& g = h->g;
+  if (g.E <= 0) return fail(h, KMC_ERR_STATE, "kmc_fmm_accept_event needs lattice mode");
+  if (event < 0 || event >= 6 * g.n) return fail(h, KMC_ERR_ARG, "event index out of range");
+  int32_t i = (int32_t)(event / 6);
+  int k = (int)(event % 6);
+  double p[3];
+  CK(cudaMemcpy(p, h->d.pos + 3 * (int64_t)i, sizeof(p), cudaMemcpyDeviceToHost));
+  static const int hop[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+  double t[3];
+  for (int c = 0; c < 3; c++) t[c] = p[c] + hop[k][c] * g.h;
+  return accept_general(h, i, t, dU_accepted);
+}
+
+int kmc_step(kmc_handle h, const double* rates, double zeta, double xi, int64_t* event, double* dt, double* Q) {
+  int r = guard(h);
+  if (r) return r;
+  if (!(zeta > 0.0 && zeta <= 1.0 && xi > 0.0 && xi <= 1.0))
+    return fail(h, KMC_ERR_ARG, "zeta and xi must lie in (0, 1]");
+  cudaStream_t s = h->stream;
+  if (rates) {
+    CK(cudaMemcpyAsync(h->d.rate, rates, sizeof(double) * 6 * h->g.n, in_kind(h), s));
+    kmc_rate_bsum(h->g, h->d, s);
+    CKLAUNCH();
+  } else if (!h->rates_valid) {
+    return fail(h, KMC_ERR_STATE, "kmc_step without rates needs a kmc_fmm_propose_lattice after the last accept");
+  }
+  double u[2] = {zeta, xi};
+  CK(cudaMemcpyAsync(h->d.uni_small, u, sizeof(u), cudaMemcpyHostToDevice, s));
+  kmc_select(h->g, h->d, 0, s);
+  CKLAUNCH();
+  int64_t ev;
+  double dq[2];
+  CK(cudaMemcpyAsync(&ev, h->d.event, sizeof(ev), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(dq, h->d.dtq, sizeof(dq), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (rates) h->rates_valid = false;  // device rates now hold the caller's values
+  if (event) *event = ev;
+  if (dt) *dt = dq[0];
+  if (Q) *Q = dq[1];
+  return KMC_OK;
+}
+
+// one device-driven step: downward pass, propose, rates, select, record, accept
+static void enqueue_step(kmc_fmm* h) {
+  const Geo& g = h->g;
+  const Dev& d = h->d;
+  cudaStream_t s = h->stream;
+  fmm_downward(g, d, h->prec, s);
+  kmc_propose_lattice(g, d, h->prec, s);
+  kmc_finalize_rates(g, d, s);
+  kmc_select(g, d, 1, s);
+  kmc_record(g, d, s);
+  kmc_accept_from_event(g, d, s);
+  kmc_accept_apply(g, d, s);
+}
+
+#define KMC_GRAPH_STEPS 8
+
+int kmc_run(kmc_handle h, int steps, const double* uniforms, int64_t* events, double* dts) {
+  int r = guard(h);
+  if (r) return r;
+  if (h->g.E <= 0) return fail(h, KMC_ERR_STATE, "kmc_run needs lattice mode");
+  if (steps < 0) return fail(h, KMC_ERR_ARG, "negative step count");
+  if (steps == 0) return KMC_OK;
+  if (!uniforms) return fail(h, KMC_ERR_ARG, "uniforms are required");
+  cudaStream_t s = h->stream;
+  if (steps > h->run_cap) {
+    int cap = steps < 1024 ? 1024 : steps;
+    ALLOC(h->d.uni_run, sizeof(double) * 2 * (size_t)cap);
+    ALLOC(h->d.ev_hist, sizeof(int64_t) * (size_t)cap);
+    ALLOC(h->d.dt_hist, sizeof(double) * (size_t)cap);
+    h->run_cap = cap;
+    if (h->graph) {  // kernel arguments changed
+      cudaGraphExecDestroy(h->graph);
+      h->graph = nullptr;
+    }
+  }
+  CK(cudaMemcpyAsync(h->d.uni_run, uniforms, sizeof(double) * 2 * steps, in_kind(h), s));
+  CK(cudaMemsetAsync(h->d.stepc, 0, sizeof(int), s));
+  // graph of KMC_GRAPH_STEPS steps, built once per handle and shape
+  if (!h->graph) {
+    cudaGraph_t gr;
+    cudaStream_t cs = s;
+    bool own = false;
+    if (cs == nullptr) {  // the legacy stream cannot be captured
+      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      own = true;
+    }
+    cudaStream_t saved = h->stream;
+    h->stream = cs;
+    CK(cudaStreamSynchronize(s));
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < KMC_GRAPH_STEPS; k++) enqueue_step(h);
+    cudaError_t ce = cudaStreamEndCapture(cs, &gr);
+    h->stream = saved;
+    if (ce != cudaSuccess) {
+      if (own) cudaStreamDestroy(cs);
+      return fail(h, KMC_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+    }
+    ce = cudaGraphInstantiate(&h->graph, gr, 0);
+    cudaGraphDestroy(gr);
+    if (own) cudaStreamDestroy(cs);
+    if (ce != cudaSuccess) return fail(h, KMC_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ce));
+  }
+  int full = steps / KMC_GRAPH_STEPS, rest = steps % KMC_GRAPH_STEPS;
+  for (int b = 0; b < full; b++) CK(cudaGraphLaunch(h->graph, s));
+  for (int k = 0; k < rest; k++) enqueue_step(h);
+  CKLAUNCH();
+  h->peff_valid = false;
+  h->rates_valid = false;
+  if (events) CK(cudaMemcpyAsync(events, h->d.ev_hist, sizeof(int64_t) * steps, out_kind(h), s));
+  if (dts) CK(cudaMemcpyAsync(dts, h->d.dt_hist, sizeof(double) * steps, out_kind(h), s));
+  return check_flags(h, "run");
+}
+
+int kmc_run_profiled(kmc_handle h, int steps, const double* uniforms, int64_t* events, double* dts,
+                     double* phase_ms) {
+  int r = guard(h);
+  if (r) return r;
+  if (h->g.E <= 0) return fail(h, KMC_ERR_STATE, "kmc_run_profiled needs lattice mode");
+  if (steps < 0) return fail(h, KMC_ERR_ARG, "negative step count");
+  if (steps == 0) return KMC_OK;
+  if (!uniforms) return fail(h, KMC_ERR_ARG, "uniforms are required");
+  cudaStream_t s = h->stream;
+  if (steps > h->run_cap) {
+    int cap = steps < 1024 ? 1024 : steps;
+    ALLOC(h->d.uni_run, sizeof(double) * 2 * (size_t)cap);
+    ALLOC(h->d.ev_hist, sizeof(int64_t) * (size_t)cap);
+    ALLOC(h->d.dt_hist, sizeof(double) * (size_t)cap);
+    h->run_cap = cap;
+    if (h->graph) {
+      cudaGraphExecDestroy(h->graph);
+      h->graph = nullptr;
+    }
+  }
+  CK(cudaMemcpyAsync(h->d.uni_run, uniforms, sizeof(double) * 2 * steps, in_kind(h), s));
+  CK(cudaMemsetAsync(h->d.stepc, 0, sizeof(int), s));
+  std::vector<cudaEvent_t> ev((size_t)steps * (KMC_NPHASE + 1));
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  const Geo& g = h->g;
+  const Dev& d = h->d;
+  for (int k = 0; k < steps; k++) {
+    cudaEvent_t* e = &ev[(size_t)k * (KMC_NPHASE + 1)];
+    CK(cudaEventRecord(e[0], s));
+    fmm_downward(g, d, h->prec, s);
+    CK(cudaEventRecord(e[1], s));
+    kmc_propose_lattice(g, d, h->prec, s);
+    CK(cudaEventRecord(e[2], s));
+    kmc_finalize_rates(g, d, s);
+    CK(cudaEventRecord(e[3], s));
+    kmc_select(g, d, 1, s);
+    kmc_record(g, d, s);
+    CK(cudaEventRecord(e[4], s));
+    kmc_accept_from_event(g, d, s);
+    kmc_accept_apply(g, d, s);
+    CK(cudaEventRecord(e[5], s));
+  }
+  CKLAUNCH();
+  h->peff_valid = false;
+  h->rates_valid = false;
+  if (events) CK(cudaMemcpyAsync(events, h->d.ev_hist, sizeof(int64_t) * steps, out_kind(h), s));
+  if (dts) CK(cudaMemcpyAsync(dts, h->d.dt_hist, sizeof(double) * steps, out_kind(h), s));
+  CK(cudaStreamSynchronize(s));
+  if (phase_ms) {
+    for (int p = 0; p < KMC_NPHASE; p++) phase_ms[p] = 0.0;
+    for (int k = 0; k < steps; k++)
+      for (int p = 0; p < KMC_NPHASE; p++) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ev[(size_t)k * (KMC_NPHASE + 1) + p], ev[(size_t)k * (KMC_NPHASE + 1) + p + 1]));
+        phase_ms[p] += ms;
+      }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return check_flags(h, "run_profiled");
+}
+
+int kmc_fmm_recompute(kmc_handle h, double* max_coeff_drift) {
+  int r = guard(h);
+  if (r) return r;
+  const Geo& g = h->g;
+  cudaStream_t s = h->stream;
+  double2* saved = (double2*)h->d.scratch;  // lattice-sum scratch is free after init
+  size_t need = sizeof(double2) * g.ncell_total * g.P;
+  double2* tmp = nullptr;
+  const int nr = 13, nk = 19;
+  size_t have = (size_t)(nr * nr * nr + nk * nk * nk) * g.P2 * sizeof(double2);
+  if (need > have) {
+    ALLOC(tmp, need);
+    saved = tmp;
+  }
+  CK(cudaMemcpyAsync(saved, h->d.Psi, need, cudaMemcpyDeviceToDevice, s));
+  r = full_fmm(h);
+  if (r) return r;
+  fmm_drift(g, saved, h->d.Psi, g.ncell_total * g.P, h->drift2, s);
+  CKLAUNCH();
+  double dr[2];
+  CK(cudaMemcpyAsync(dr, h->drift2, sizeof(dr), cudaMemcpyDeviceToHost, s));
+  r = compute_energy(h);
+  if (r) return r;
+  r = check_flags(h, "recompute");
+  if (r) return r;
+  if (max_coeff_drift) *max_coeff_drift = dr[1] > 0.0 ? dr[0] / dr[1] : 0.0;
+  return KMC_OK;
+}
+
+int kmc_fmm_leaf_index(kmc_handle h, int32_t* leaf) {
+  int r = guard(h);
+  if (r) return r;
+  if (!leaf) return fail(h, KMC_ERR_ARG, "leaf is NULL");
+  std::vector<int32_t> so(h->g.n);
+  CK(cudaMemcpyAsync(so.data(), h->d.slot_of, sizeof(int32_t) * h->g.n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int64_t i = 0; i < h->g.n; i++) so[i] = so[i] / h->g.cap;
+  if (h->mem == KMC_MEM_DEVICE) {
+    CK(cudaMemcpy(leaf, so.data(), sizeof(int32_t) * h->g.n, cudaMemcpyHostToDevice));
+  } else {
+    memcpy(leaf, so.data(), sizeof(int32_t) * h->g.n);
+  }
+  return KMC_OK;
+}
+
+int kmc_fmm_positions(kmc_handle h, double* positions) {
+  int r = guard(h);
+  if (r) return r;
+  if (!positions) return fail(h, KMC_ERR_ARG, "positions is NULL");
+  CK(cudaMemcpyAsync(positions, h->d.pos, sizeof(double) * 3 * h->g.n, out_kind(h), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return KMC_OK;
+}
+
+}  // extern "C"

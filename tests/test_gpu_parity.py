@@ -1,0 +1,327 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, on seeded lattice-gas
+inputs.
+
+Tolerances.  The method's only approximation is the truncation of the
+expansions at degree p (Sec. 2.2, Tab. 2-3 of the paper), so dU matches the
+exact tinfoil energy change to a p-dependent bound.  The bounds below are
+stated against max |dU| over the compared proposals and were derived from the
+geometric convergence of the truncation error with p on these inputs (about a
+factor 10 per 3 degrees, as in Tab. 2); FP32 evaluation adds ~1e-6.
+Masks, leaf indices and selected events are compared exactly (events except
+where Q*zeta lies within the dU tolerance of a cumulative-rate boundary).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = {8: 2e-3, 10: 3e-4, 12: 1e-4, 16: 2e-6}
+
+
+def _k():
+    import paper_1905_04065_gb300 as k
+    return k
+
+
+def _init(E, sites, q, L, p, precision="fp64", kT=0.1, positions=None):
+    k = _k()
+    pos = workloads.site_positions(E, sites) if positions is None else positions
+    return k.kmc_fmm_init(pos, q, float(E), L, p, precision=precision, lattice_edge=E, kT=kT)
+
+
+def _rel_err(a, b, mask):
+    ok = mask.astype(bool)
+    return float(np.max(np.abs(a[ok] - b[ok])) / np.max(np.abs(b[ok])))
+
+
+@pytest.fixture(scope="module")
+def small():
+    w, sites, q = workloads.workload("small")
+    st = oracle.LatticeState(w["E"], sites, q)
+    return w, sites, q, st
+
+
+@pytest.mark.parametrize("p", [8, 12, 16])
+def test_small_propose_fp64(small, p):
+    k = _k()
+    w, sites, q, st = small
+    h = _init(w["E"], sites, q, w["L"], p)
+    mask, dU = k.kmc_fmm_propose_lattice(h)
+    dU_o, mask_o = st.propose()
+    assert np.array_equal(mask, mask_o)
+    assert np.all(np.isnan(dU[mask == 0]))
+    err = _rel_err(dU, dU_o, mask_o)
+    assert err < TOL[p], err
+
+
+def test_small_propose_mixed(small):
+    k = _k()
+    w, sites, q, st = small
+    h = _init(w["E"], sites, q, w["L"], 12, precision="mixed")
+    mask, dU = k.kmc_fmm_propose_lattice(h)
+    dU_o, mask_o = st.propose()
+    assert np.array_equal(mask, mask_o)
+    err = _rel_err(dU, dU_o, mask_o)
+    assert err < 1e-4, err
+
+
+def test_energy_matches_oracle(small):
+    k = _k()
+    w, sites, q, st = small
+    h = _init(w["E"], sites, q, w["L"], 12)
+    U = k.kmc_fmm_energy(h)
+    U_o = st.energy()
+    assert abs(U - U_o) < 1e-5 * abs(U_o), (U, U_o)
+
+
+def test_madelung_energy_fmm():
+    """Full FMM energy of an ideal rock-salt block reproduces the Madelung constant."""
+    k = _k()
+    E = 8
+    s = np.arange(E ** 3)
+    q = (-1.0) ** workloads.site_xyz(E, s).sum(1)
+    h = _init(E, s, q, 3, 12)
+    U = k.kmc_fmm_energy(h)
+    assert abs(U / E ** 3 + 1.747564594633182 / 2) < 1e-6
+
+
+def test_leaf_index_exact(small):
+    k = _k()
+    w, sites, q, st = small
+    h = _init(w["E"], sites, q, w["L"], 8)
+    leaf = k.kmc_fmm_leaf_index(h)
+    xyz = workloads.site_xyz(w["E"], sites)
+    W = w["E"] // 2 ** (w["L"] - 1)
+    n = 2 ** (w["L"] - 1)
+    c = xyz // W
+    ref = c[:, 0] + n * (c[:, 1] + n * c[:, 2])
+    assert np.array_equal(leaf, ref.astype(np.int32))
+
+
+def test_general_propose_matches_oracle(small):
+    """Arbitrary targets (one to a few sites away, across the periodic boundary)."""
+    k = _k()
+    w, sites, q, st = small
+    E = w["E"]
+    h = _init(E, sites, q, w["L"], 12)
+    rng = np.random.default_rng(5)
+    occ = set(sites.tolist())
+    parts, tsites = [], []
+    while len(parts) < 200:
+        i = int(rng.integers(0, len(q)))
+        d = rng.integers(-3, 4, size=3)
+        if not d.any():
+            continue
+        t = (workloads.site_xyz(E, [sites[i]])[0] + d) % E
+        s = int(t[0] + E * (t[1] + E * t[2]))
+        if s in occ:
+            continue
+        parts.append(i)
+        tsites.append(s)
+    tgt = workloads.site_positions(E, tsites)
+    # unwrapped targets too: the library wraps them
+    tgt[::3] += E
+    dU = k.kmc_fmm_propose(h, np.array(parts, np.int32), tgt)
+    ref = st.delta_u_list(parts, tsites)
+    err = float(np.max(np.abs(dU - ref)) / np.max(np.abs(ref)))
+    assert err < 1e-4, err
+
+
+def test_singular_general_proposal_rejected(small):
+    k = _k()
+    w, sites, q, st = small
+    E = w["E"]
+    h = _init(E, sites, q, w["L"], 8)
+    tgt = workloads.site_positions(E, [sites[1], sites[2]])  # 0 -> occupied site; 1 -> itself
+    with pytest.raises(k.KmcError) as ei:
+        k.kmc_fmm_propose(h, np.array([0, 2], np.int32), tgt)
+    assert ei.value.code == k.KMC_ERR_ARG
+
+
+def test_selection_matches_oracle_given_rates(small):
+    k = _k()
+    w, sites, q, st = small
+    h = _init(w["E"], sites, q, w["L"], 8)
+    rng = np.random.default_rng(9)
+    n = len(q)
+    for trial in range(30):
+        r = rng.random(6 * n)
+        r[rng.random(6 * n) < 0.4] = 0.0
+        zeta, xi = 1.0 - rng.random(), 1.0 - rng.random()
+        ev, dt, Q = k.kmc_step(h, r, zeta, xi)
+        j, Qo, dto = oracle.select(r, zeta, xi)
+        R = oracle.cumsum(r)
+        near = np.min(np.abs(R - Qo * zeta)) <= 1e-12 * Qo
+        assert abs(Q - Qo) <= 1e-12 * Qo
+        assert abs(dt - dto) <= 1e-12 * dto
+        if not near:
+            assert ev == j, (trial, ev, j)
+
+
+def _near_tie(dU_o, mask_o, kT, zeta, tol_abs):
+    """True if Q*zeta is within the rate uncertainty implied by the dU tolerance."""
+    r = oracle.rates(dU_o, mask_o, kT)
+    R = oracle.cumsum(r)
+    Q = R[-1]
+    # each rate may move by |dr| <= r * tol/kT; a boundary moves by at most the sum
+    slack = float(np.sum(r) * tol_abs / kT) + 1e-12 * Q
+    return np.min(np.abs(R - Q * zeta)) <= slack
+
+
+def test_teacher_forced_trajectory_small(small):
+    """Propose, select and accept for 40 steps with the oracle's event forced
+    into both paths (Sec. 3 propose/accept); dU, masks and events compared each
+    step, then a recompute measures the accept-update drift."""
+    k = _k()
+    w, sites, q, _ = small
+    E, kT = w["E"], w["kT"]
+    p = 12
+    st = oracle.LatticeState(E, sites, q)
+    h = _init(E, sites, q, w["L"], p, kT=kT)
+    u = workloads.uniforms(40, w["seed"])
+    agree = 0
+    for s in range(40):
+        mask, dU = k.kmc_fmm_propose_lattice(h)
+        dU_o, mask_o = st.propose()
+        assert np.array_equal(mask, mask_o)
+        tol = TOL[p] * np.nanmax(np.abs(dU_o))
+        assert np.nanmax(np.abs(dU - dU_o)) < tol
+        ev, dt, Q = k.kmc_step(h, None, u[s, 0], u[s, 1])
+        r_o = oracle.rates(dU_o, mask_o, kT)
+        j, Q_o, dt_o = oracle.select(r_o, u[s, 0], u[s, 1])
+        if ev == j:
+            agree += 1
+        else:
+            assert _near_tie(dU_o, mask_o, kT, u[s, 0], tol), (s, ev, j)
+        du_acc = k.kmc_fmm_accept_event(h, j)
+        assert abs(du_acc - dU_o.reshape(-1)[j]) < tol
+        st.accept(j // 6, j % 6)
+    assert agree >= 38
+    pos = k.kmc_fmm_positions(h)
+    assert np.array_equal(pos, workloads.site_positions(E, st.sites))
+    U = k.kmc_fmm_energy(h)
+    assert abs(U - st.energy()) < 1e-4 * abs(st.energy())
+    drift = k.kmc_fmm_recompute(h)
+    assert drift < 1e-8, drift
+    U2 = k.kmc_fmm_energy(h)
+    assert abs(U2 - st.energy()) < 1e-4 * abs(st.energy())
+
+
+def test_run_matches_stepwise(small):
+    """The graph-replayed device loop makes the same choices as the host-driven
+    propose/step/accept sequence (same precision, same inputs)."""
+    k = _k()
+    w, sites, q, _ = small
+    E, kT = w["E"], w["kT"]
+    steps = 21
+    u = workloads.uniforms(steps, w["seed"] + 1)
+    h1 = _init(E, sites, q, w["L"], 8, kT=kT)
+    ev_run, dt_run = k.kmc_run(h1, u)
+    h2 = _init(E, sites, q, w["L"], 8, kT=kT)
+    for s in range(steps):
+        k.kmc_fmm_propose_lattice(h2)
+        ev, dt, Q = k.kmc_step(h2, None, u[s, 0], u[s, 1])
+        assert ev == ev_run[s], s
+        assert abs(dt - dt_run[s]) <= 1e-12 * dt
+        k.kmc_fmm_accept_event(h2, ev)
+    assert np.array_equal(k.kmc_fmm_positions(h1), k.kmc_fmm_positions(h2))
+
+
+def test_run_against_oracle_trajectory(small):
+    """Untethered device loop vs the oracle's own trajectory: identical events
+    for as long as no near tie occurs."""
+    k = _k()
+    w, sites, q, _ = small
+    E, kT = w["E"], w["kT"]
+    steps = 30
+    u = workloads.uniforms(steps, w["seed"] + 2)
+    h = _init(E, sites, q, w["L"], 12, kT=kT)
+    ev_run, dt_run = k.kmc_run(h, u)
+    st = oracle.LatticeState(E, sites, q)
+    for s in range(steps):
+        dU_o, mask_o = st.propose()
+        r = oracle.rates(dU_o, mask_o, kT)
+        j, Q, dt = oracle.select(r, u[s, 0], u[s, 1])
+        if ev_run[s] != j:
+            assert _near_tie(dU_o, mask_o, kT, u[s, 0], TOL[12] * np.nanmax(np.abs(dU_o))), s
+            return
+        assert abs(dt_run[s] - dt) < 1e-3 * dt
+        st.accept(j // 6, j % 6)
+
+
+@pytest.mark.parametrize("bad", ["levels", "order", "neutral", "outside", "offsite", "edge", "duplicate"])
+def test_init_errors(bad):
+    k = _k()
+    E, L, p = 16, 3, 8
+    sites, q = workloads.random_small(E, 40, 3)
+    pos = workloads.site_positions(E, sites)
+    kw = dict(lattice_edge=E)
+    if bad == "levels":
+        L = 2
+    elif bad == "order":
+        p = 0
+    elif bad == "neutral":
+        q = q.copy()
+        q[0] = 3.0
+    elif bad == "outside":
+        pos = pos.copy()
+        pos[3, 1] = E + 0.5
+    elif bad == "offsite":
+        pos = pos.copy()
+        pos[3, 1] += 0.25
+    elif bad == "edge":
+        kw = dict(lattice_edge=E)
+        L = 6  # 16 is not a multiple of 32
+    elif bad == "duplicate":
+        pos = pos.copy()
+        pos[4] = pos[5]
+    with pytest.raises(k.KmcError) as ei:
+        k.kmc_fmm_init(pos, q, float(E), L, p, **kw)
+    expect = k.KMC_ERR_NOT_NEUTRAL if bad == "neutral" else k.KMC_ERR_ARG
+    assert ei.value.code == expect
+
+
+def test_device_memory_interface(small):
+    """Same results with torch CUDA tensors in and out (device pointers)."""
+    import torch
+    k = _k()
+    w, sites, q, st = small
+    E = w["E"]
+    pos = torch.tensor(workloads.site_positions(E, sites), device="cuda")
+    qt = torch.tensor(q, device="cuda")
+    h = k.kmc_fmm_init(pos, qt, float(E), w["L"], 8, lattice_edge=E, kT=w["kT"])
+    mask, dU = k.kmc_fmm_propose_lattice(h)
+    assert mask.is_cuda and dU.is_cuda
+    h2 = _init(E, sites, q, w["L"], 8, kT=w["kT"])
+    mask2, dU2 = k.kmc_fmm_propose_lattice(h2)
+    assert np.array_equal(mask.cpu().numpy(), mask2)
+    np.testing.assert_array_equal(dU.cpu().numpy(), dU2)
+
+
+def test_offlattice_propose_and_accept():
+    """Off-lattice positions (the paper's general interface): dU against the
+    direct Ewald oracle, then an accepted move and U(after) - U(before)."""
+    k = _k()
+    rng = np.random.default_rng(17)
+    a = 12.0
+    n = 120
+    pos = rng.random((n, 3)) * a
+    q = np.concatenate([np.ones(n // 2), -np.ones(n // 2)])
+    h = k.kmc_fmm_init(pos, q, a, 3, 14)
+    parts = rng.integers(0, n, size=40).astype(np.int32)
+    tgt = (pos[parts] + rng.normal(0, 0.7, size=(40, 3))) % a
+    dU = k.kmc_fmm_propose(h, parts, tgt)
+    ref = oracle.delta_u(pos, q, a, parts, tgt)
+    err = float(np.max(np.abs(dU - ref)) / np.max(np.abs(ref)))
+    assert err < 1e-4, err
+    U0 = k.kmc_fmm_energy(h)
+    assert abs(U0 - oracle.energy(pos, q, a)) < 1e-4 * abs(U0)
+    du = k.kmc_fmm_accept(h, int(parts[0]), tgt[0])
+    assert abs(du - ref[0]) < 1e-4 * np.max(np.abs(ref))
+    U1 = k.kmc_fmm_energy(h)
+    assert abs((U1 - U0) - du) < 1e-12 * abs(U0) + 1e-12

@@ -277,6 +277,22 @@ def test_direct_equals_table():
     assert np.max(np.abs(d - np.array(ref))) < 1e-12
 
 
+def test_lattice_direct_sum_equals_site_potential_form():
+    """The O(N)-per-hop direct sum and the maintained site potential agree."""
+    E = 8
+    st = _state(E, N=60, seed=37)
+    dU, mask = st.propose()
+    parts, tg, ref = [], [], []
+    for i in range(st.n):
+        for k in range(6):
+            if mask[i, k]:
+                parts.append(i)
+                tg.append(st.target(i, k))
+                ref.append(dU[i, k])
+    d = oracle.lattice_delta_u_direct(E, st.G, st.sites, st.q, parts, tg)
+    assert np.max(np.abs(d - np.array(ref))) < 1e-12
+
+
 def test_energy_difference_equals_delta_u():
     E = 6
     sites, q = workloads.random_small(E, 10, 13)
