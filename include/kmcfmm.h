@@ -168,11 +168,18 @@ int kmc_run_profiled(kmc_handle h, int steps, const double* uniforms, int64_t* e
 
 /*
  * Full FP64 recompute of every expansion from the current positions
- * (Algorithm 2); *max_coeff_drift (host, may be NULL) receives
- * max |psi_incremental - psi_fresh| / max |psi_fresh| over all levels before
- * the fresh values replace the incremental ones.  The energy is recomputed.
+ * (Algorithm 2), replacing the incrementally updated ones; the energy is
+ * recomputed.  drift (host, 3 doubles, may be NULL) receives the drift of the
+ * incremental accept updates measured against the fresh expansions:
+ *   [0] max_i |phi_incr(r_i) - phi_fresh(r_i)| / max_i |phi_fresh(r_i)|
+ *       (potential at every charge, own term excluded),
+ *   [1] max |Psi_incr - Psi_fresh| / max |Psi_fresh| over all coefficients
+ *       of all levels (high-order coefficients of a local expansion carry the
+ *       truncation error of the M2L, so this is an upper bound),
+ *   [2] |U_tracked - U_fresh| / |U_fresh| (energy accumulated from the
+ *       accepted dU against the recomputed energy).
  */
-int kmc_fmm_recompute(kmc_handle h, double* max_coeff_drift);
+int kmc_fmm_recompute(kmc_handle h, double* drift);
 
 /* Leaf-cell index (cx + n(cy + n cz), n = 2^(L-1)) of every particle, user order. */
 int kmc_fmm_leaf_index(kmc_handle h, int32_t* leaf);

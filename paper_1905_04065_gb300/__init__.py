@@ -275,10 +275,11 @@ def kmc_run_profiled(h: Handle, uniforms):
     return ev, dt, ph
 
 
-def kmc_fmm_recompute(h: Handle) -> float:
-    drift = ctypes.c_double()
-    _check(h, load_library().kmc_fmm_recompute(h.ptr, ctypes.byref(drift)))
-    return drift.value
+def kmc_fmm_recompute(h: Handle):
+    """Full recompute; returns (potential drift, coefficient drift, energy drift)."""
+    drift = np.zeros(3, dtype=np.float64)
+    _check(h, load_library().kmc_fmm_recompute(h.ptr, drift.ctypes.data_as(ctypes.c_void_p)))
+    return tuple(float(x) for x in drift)
 
 
 def kmc_fmm_leaf_index(h: Handle):

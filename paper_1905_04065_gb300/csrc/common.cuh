@@ -96,6 +96,7 @@ struct Dev {
   double2* Psi;       // per-level interaction-list local expansions; level 1 holds H
   void* Peff;         // downward-accumulated locals (T2), all levels
   double2* Itab;      // M2L irregular values [(L+1) * 343 * P2]
+  double2* Rch;       // child-offset regular harmonics [(L+1) * 8 * P]
   double2* S;         // lattice sums over the far images [P2]
   double* selfc;      // [KMC_NHOP] self-pair correction C(d) per hop direction
   double* dip;        // [3] dipole moment M
@@ -110,6 +111,8 @@ struct Dev {
   int64_t* event;     // [1]
   double* dtq;        // [2] (dt, Q)
   MoveRec* move;      // [1]
+  double2* dK;        // [P] level-1 multipole change of the accepted move
+  double2* acc_scratch;  // [64 * 54 * P] coarse-level P2L terms of the accepted move
   int* err;           // [4] device error flags
   double* scratch;    // init-time scratch (lattice-sum terms)
   double* uni_small;  // [2] (zeta, xi) staged for a single kmc_step
@@ -136,18 +139,20 @@ void fmm_bin(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_p2m(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_m2m(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_itab(const Geo& g, const Dev& d, cudaStream_t s);
+void fmm_child_tables(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_m2l(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_lattice_sums(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_far_field(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_self_and_dipole(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_downward(const Geo& g, const Dev& d, int prec, cudaStream_t s);
 void fmm_selfcorr_list(const Geo& g, const Dev& d, int64_t m, const double* dvec, double* out, cudaStream_t s);
+void fmm_drift1(const double* a, const double* b, int64_t count, double* out2, cudaStream_t s);
 void fmm_drift(const Geo& g, const double2* a, const double2* b, int64_t count, double* out2,
                cudaStream_t s);
 
 void kmc_upload_constants(int p);
 void kmc_propose_lattice(const Geo& g, const Dev& d, int prec, cudaStream_t s);
-void kmc_finalize_rates(const Geo& g, const Dev& d, cudaStream_t s);
+void kmc_finalize_rates(const Geo& g, const Dev& d, int prec, cudaStream_t s);
 void kmc_prepare(const Geo& g, int prec);
 void kmc_rate_bsum(const Geo& g, const Dev& d, cudaStream_t s);
 void kmc_select(const Geo& g, const Dev& d, int use_counter, cudaStream_t s);

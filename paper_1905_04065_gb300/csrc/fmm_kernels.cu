@@ -181,16 +181,27 @@ void fmm_p2m(const Geo& g, const Dev& d, cudaStream_t s) {
   k_p2m<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(g, d);
 }
 
+// ------------------------------------------------------------------ child offsets
+// Rch[l][o] = R_n^m(c_child - c_parent) for the 8 child octants o of a level-l
+// cell's parent: (o - 1/2) w_l per axis.  Used by M2M (level l-1 from l) and
+// by the downward L2L (level l from l-1).  Computed once per handle.
+__global__ void k_child_tables(const Geo g, const Dev d) {
+  int l = 2 + blockIdx.x;
+  int o = threadIdx.x;
+  if (o >= 8 || l > g.L) return;
+  double wc = g.a / (1 << (l - 1));
+  double tx = ((o & 1) - 0.5) * wc, ty = (((o >> 1) & 1) - 0.5) * wc, tz = (((o >> 2) & 1) - 0.5) * wc;
+  regular_table(tx, ty, tz, g.p, d.Rch + ((int64_t)l * 8 + o) * g.P);
+}
+
+void fmm_child_tables(const Geo& g, const Dev& d, cudaStream_t s) { k_child_tables<<<g.L - 1, 32, 0, s>>>(g, d); }
+
 // ------------------------------------------------------------------ M2M
 // level l (parents, n_l per side) from level l+1.  thread per (parent, coefficient)
 __global__ void k_m2m(const Geo g, const Dev d, int l) {
   extern __shared__ double2 sh[];  // 8 * P regular tables of the child offsets
   int nl = 1 << (l - 1), nc = 2 * nl;
-  double wc = g.a / nc;
-  for (int o = threadIdx.x; o < 8; o += blockDim.x) {
-    double tx = ((o & 1) - 0.5) * wc, ty = (((o >> 1) & 1) - 0.5) * wc, tz = (((o >> 2) & 1) - 0.5) * wc;
-    regular_table(tx, ty, tz, g.p, sh + o * g.P);
-  }
+  for (int c = threadIdx.x; c < 8 * g.P; c += blockDim.x) sh[c] = d.Rch[(int64_t)(l + 1) * 8 * g.P + c];
   __syncthreads();
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t ncl = (int64_t)nl * nl * nl;
@@ -562,28 +573,9 @@ __global__ void k_downward(const Geo g, const Dev d, int l) {
     return;
   }
   int nl = 1 << (l - 1), np = nl / 2;
-  double wc = g.a / nl;
-  if (threadIdx.x < 8) {
-    int o = threadIdx.x;
-    double tx = ((o & 1) - 0.5) * wc, ty = (((o >> 1) & 1) - 0.5) * wc, tz = (((o >> 2) & 1) - 0.5) * wc;
-    double r2 = tx * tx + ty * ty + tz * tz;
-    double2 mm = make_double2(1.0, 0.0);
-    for (int m = 0; m <= g.p; m++) {
-      if (m > 0) {
-        double s = -0.5 / m;
-        mm = make_double2(s * (tx * mm.x - ty * mm.y), s * (tx * mm.y + ty * mm.x));
-      }
-      Rt[o * g.P + tri(m, m)] = cmk<C>(mm.x, mm.y);
-      double2 a2 = make_double2(0.0, 0.0), a1 = mm;
-      for (int n = m + 1; n <= g.p; n++) {
-        double c = f_inv_nm[tri(n, m)];
-        double zz = (2 * n - 1) * tz;
-        double2 v = make_double2((zz * a1.x - r2 * a2.x) * c, (zz * a1.y - r2 * a2.y) * c);
-        Rt[o * g.P + tri(n, m)] = cmk<C>(v.x, v.y);
-        a2 = a1;
-        a1 = v;
-      }
-    }
+  for (int c = threadIdx.x; c < 8 * g.P; c += blockDim.x) {
+    double2 v = d.Rch[(int64_t)l * 8 * g.P + c];
+    Rt[c] = cmk<C>(v.x, v.y);
   }
   __syncthreads();
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -652,4 +644,27 @@ void fmm_drift(const Geo& g, const double2* a, const double2* b, int64_t count, 
   (void)g;
   cudaMemsetAsync(out2, 0, 2 * sizeof(double), s);
   k_drift<<<1024, 256, 0, s>>>(a, b, count, (unsigned long long*)out2);
+}
+
+// out2[0] = max |a - b|, out2[1] = max |b| over real arrays
+__global__ void k_drift1(const double* a, const double* b, int64_t count, unsigned long long* out2) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double e = 0.0, m = 0.0;
+  for (; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    e = fmax(e, fabs(a[i] - b[i]));
+    m = fmax(m, fabs(b[i]));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    e = fmax(e, __shfl_xor_sync(0xffffffff, e, o));
+    m = fmax(m, __shfl_xor_sync(0xffffffff, m, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out2[0], (unsigned long long)__double_as_longlong(e));
+    atomicMax(&out2[1], (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+void fmm_drift1(const double* a, const double* b, int64_t count, double* out2, cudaStream_t s) {
+  cudaMemsetAsync(out2, 0, 2 * sizeof(double), s);
+  k_drift1<<<1024, 256, 0, s>>>(a, b, count, (unsigned long long*)out2);
 }

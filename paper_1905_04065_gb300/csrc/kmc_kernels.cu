@@ -21,6 +21,7 @@
 
 __constant__ float c_inv_f[KMC_NTRI];
 __constant__ double c_inv_d[KMC_NTRI];
+__constant__ float2 c_inv2_f[KMC_NTRI];      // (1/((n-m)(n+m)), same) pairs for packed FP32
 __constant__ float c_halfm_f[KMC_MAXP + 2];   // -1/(2m)
 __constant__ double c_halfm_d[KMC_MAXP + 2];
 __constant__ int c_hop[KMC_NHOP][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
@@ -43,6 +44,9 @@ void kmc_upload_constants(int p) {
     hf[m] = (float)(-0.5 / m);
   }
   cudaMemcpyToSymbol(c_inv_f, invf, sizeof(invf));
+  static float2 inv2[KMC_NTRI];
+  for (int t = 0; t < KMC_NTRI; t++) inv2[t] = make_float2(invf[t], invf[t]);
+  cudaMemcpyToSymbol(c_inv2_f, inv2, sizeof(inv2));
   cudaMemcpyToSymbol(c_inv_d, invd, sizeof(invd));
   cudaMemcpyToSymbol(c_halfm_f, hf, sizeof(hf));
   cudaMemcpyToSymbol(c_halfm_d, hd, sizeof(hd));
@@ -93,6 +97,164 @@ __device__ __forceinline__ T l2p_eval(const C* L, int p, T x, T y, T z) {
   return acc;
 }
 
+
+// ------------------------------------------------------------------ near-field helpers
+// FP32: sources staged as pairs (A = {x_2j, x_2j+1, y_2j, y_2j+1},
+// B = {z_2j, z_2j+1, q_2j, q_2j+1}) so that one packed FP32x2 instruction
+// (FADD2 / FMUL2 / FFMA2) serves two pair interactions; 1/r from the MUFU
+// rsqrt.approx (relative error < 2^-22).  FP64: one source per iteration.
+__device__ __forceinline__ float rsqrt_mufu(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+template <typename T> struct NearField;
+
+template <> struct NearField<float> {
+  float2 a0, a1;
+  __device__ __forceinline__ void reset() { a0 = a1 = make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ size_t bytes(int chunk) { return (size_t)(chunk / 2 + 1) * 32; }
+  static __device__ __forceinline__ void stage(unsigned char* sm, int chunk, int e, float4 v) {
+    float* A = (float*)sm;
+    float* B = (float*)(sm + (size_t)(chunk / 2 + 1) * 16);
+    int j = e >> 1, o = e & 1;
+    A[4 * j + o] = v.x;
+    A[4 * j + 2 + o] = v.y;
+    B[4 * j + o] = v.z;
+    B[4 * j + 2 + o] = v.w;
+  }
+  static __device__ __forceinline__ void pad(unsigned char* sm, int chunk, int ns) {
+    if (ns & 1) stage(sm, chunk, ns, make_float4(1e18f, 1e18f, 1e18f, 0.f));
+  }
+  template <bool GUARD, bool TWO>
+  __device__ __forceinline__ void run_(const unsigned char* sm, int chunk, int ns, float x0, float y0, float z0,
+                                       float x1, float y1, float z1) {
+    const float4* A = (const float4*)sm;
+    const float4* B = (const float4*)(sm + (size_t)(chunk / 2 + 1) * 16);
+    const int np = (ns + 1) >> 1;
+    const float2 nx0 = make_float2(-x0, -x0), ny0 = make_float2(-y0, -y0), nz0 = make_float2(-z0, -z0);
+    const float2 nx1 = make_float2(-x1, -x1), ny1 = make_float2(-y1, -y1), nz1 = make_float2(-z1, -z1);
+    float2 c0 = a0, c1 = a1;
+#pragma unroll 2
+    for (int j = 0; j < np; j++) {
+      float4 a = A[j], b = B[j];
+      float2 sx = make_float2(a.x, a.y), sy = make_float2(a.z, a.w);
+      float2 sz = make_float2(b.x, b.y), sq = make_float2(b.z, b.w);
+      {
+        float2 dx = __fadd2_rn(sx, nx0), dy = __fadd2_rn(sy, ny0), dz = __fadd2_rn(sz, nz0);
+        float2 r2 = __fmul2_rn(dx, dx);
+        r2 = __ffma2_rn(dy, dy, r2);
+        r2 = __ffma2_rn(dz, dz, r2);
+        float2 iv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+        if (GUARD) {
+          iv.x = r2.x > 0.f ? iv.x : 0.f;
+          iv.y = r2.y > 0.f ? iv.y : 0.f;
+        }
+        c0 = __ffma2_rn(sq, iv, c0);
+      }
+      if (TWO) {
+        float2 dx = __fadd2_rn(sx, nx1), dy = __fadd2_rn(sy, ny1), dz = __fadd2_rn(sz, nz1);
+        float2 r2 = __fmul2_rn(dx, dx);
+        r2 = __ffma2_rn(dy, dy, r2);
+        r2 = __ffma2_rn(dz, dz, r2);
+        float2 iv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+        if (GUARD) {
+          iv.x = r2.x > 0.f ? iv.x : 0.f;
+          iv.y = r2.y > 0.f ? iv.y : 0.f;
+        }
+        c1 = __ffma2_rn(sq, iv, c1);
+      }
+    }
+    a0 = c0;
+    a1 = c1;
+  }
+  __device__ __forceinline__ void run(const unsigned char* sm, int chunk, int ns, bool guard, bool two, float x0,
+                                      float y0, float z0, float x1, float y1, float z1) {
+    if (guard) {
+      if (two) run_<true, true>(sm, chunk, ns, x0, y0, z0, x1, y1, z1);
+      else run_<true, false>(sm, chunk, ns, x0, y0, z0, x1, y1, z1);
+    } else {
+      if (two) run_<false, true>(sm, chunk, ns, x0, y0, z0, x1, y1, z1);
+      else run_<false, false>(sm, chunk, ns, x0, y0, z0, x1, y1, z1);
+    }
+  }
+  __device__ __forceinline__ float sum(int side) const { return side ? a1.x + a1.y : a0.x + a0.y; }
+};
+
+template <> struct NearField<double> {
+  double a0, a1;
+  __device__ __forceinline__ void reset() { a0 = a1 = 0.0; }
+  static __device__ __forceinline__ size_t bytes(int chunk) { return (size_t)chunk * 32; }
+  static __device__ __forceinline__ void stage(unsigned char* sm, int chunk, int e, double4_32a v) {
+    ((double4_32a*)sm)[e] = v;
+  }
+  static __device__ __forceinline__ void pad(unsigned char*, int, int) {}
+  __device__ __forceinline__ void run(const unsigned char* sm, int chunk, int ns, bool guard, bool two, double x0,
+                                      double y0, double z0, double x1, double y1, double z1) {
+    const double4_32a* src = (const double4_32a*)sm;
+    double s0 = a0, s1 = a1;
+    for (int j = 0; j < ns; j++) {
+      double4_32a v = src[j];
+      double dx0 = v.x - x0, dy0 = v.y - y0, dz0 = v.z - z0;
+      double dx1 = v.x - x1, dy1 = v.y - y1, dz1 = v.z - z1;
+      double q0 = dx0 * dx0 + dy0 * dy0 + dz0 * dz0;
+      double q1 = dx1 * dx1 + dy1 * dy1 + dz1 * dz1;
+      double i0 = (!guard || q0 > 0.0) ? rsqrt(q0) : 0.0;
+      double i1 = (!guard || q1 > 0.0) ? rsqrt(q1) : 0.0;
+      s0 += v.w * i0;
+      if (two) s1 += v.w * i1;
+    }
+    a0 = s0;
+    a1 = s1;
+  }
+  __device__ __forceinline__ double sum(int side) const { return side ? a1 : a0; }
+};
+
+// packed FP32 L2P: the complex recurrence and the accumulation use FP32x2
+// (real and imaginary parts in one instruction); 1/((n-m)(n+m)) pairs from
+// constant memory.
+__device__ __forceinline__ float l2p_packed(const float2* L, int p, float x, float y, float z) {
+  const float r2 = x * x + y * y + z * z;
+  const float2 nr2 = make_float2(-r2, -r2);
+  const float2 z2 = make_float2(2.f * z, 2.f * z);
+  float mmx = 1.f, mmy = 0.f;
+  float total = 0.f;
+  for (int m = 0; m <= p; m++) {
+    if (m > 0) {
+      float s = c_halfm_f[m];
+      float tx = s * (x * mmx - y * mmy);
+      float ty = s * (x * mmy + y * mmx);
+      mmx = tx;
+      mmy = ty;
+    }
+    float2 a1 = make_float2(mmx, mmy), a2 = make_float2(0.f, 0.f);
+    float2 col = __fmul2_rn(L[tri(m, m)], a1);
+    float zz0 = (float)(2 * m + 1) * z;
+    float2 zz = make_float2(zz0, zz0);
+    for (int n = m + 1; n <= p; n++) {
+      float2 v = __ffma2_rn(zz, a1, __fmul2_rn(nr2, a2));
+      v = __fmul2_rn(v, c_inv2_f[tri(n, m)]);
+      col = __ffma2_rn(L[tri(n, m)], v, col);
+      a2 = a1;
+      a1 = v;
+      zz = __fadd2_rn(zz, z2);
+    }
+    float cm = col.x - col.y;
+    total += (m == 0) ? cm : cm + cm;
+  }
+  return total;
+}
+
+template <typename T, typename C> __device__ __forceinline__ T l2p_point(const C* L, int p, T x, T y, T z);
+template <> __device__ __forceinline__ float l2p_point<float, float2>(const float2* L, int p, float x, float y, float z) {
+  return l2p_packed(L, p, x, y, z);
+}
+template <> __device__ __forceinline__ double l2p_point<double, double2>(const double2* L, int p, double x, double y,
+                                                                        double z) {
+  return l2p_eval<double, double2>(L, p, x, y, z);
+}
+
 // ------------------------------------------------------------------ propose (lattice)
 // One CTA per leaf cell.  Evaluation points of the CTA are every position in
 // the leaf at which a potential is needed: the leaf's own charges (old
@@ -112,8 +274,8 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
   typedef typename cplx<T>::type C;
   typedef typename vec4<T>::type V4;
   extern __shared__ __align__(32) unsigned char sm[];
-  V4* src = (V4*)sm;
-  C* Lc = (C*)(src + chunk);
+  unsigned char* src = sm;
+  C* Lc = (C*)(sm + NearField<T>::bytes(chunk));
   PtRec* pts = (PtRec*)(Lc + g.P);
   const int W = g.W, W3 = W * W * W;
   const int nbw = (W3 + 31) / 32;
@@ -235,13 +397,16 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
       y1 = ((T)(gy0 + (l1 / W) % W) + (T)0.5) * h;
       z1 = ((T)(gz0 + l1 / (W * W)) + (T)0.5) * h;
     }
-    T s0 = 0, s1 = 0;
+    // second point slot only where some lane of the warp has one
+    const bool two = __any_sync(0xffffffffu, b1 < npts);
+    NearField<T> nf;
+    nf.reset();
     for (int pass = 0; pass < npass; pass++) {
       __syncthreads();
       int ns;
       if (pass == 0) {
         ns = cnt_own;
-        for (int j = tid; j < ns; j += blockDim.x) src[j] = spos[base_own + j];
+        for (int j = tid; j < ns; j += blockDim.x) NearField<T>::stage(src, chunk, j, spos[base_own + j]);
       } else {
         int c0 = (pass - 1) * chunk;
         ns = min(chunk, nsrc_other - c0);
@@ -258,34 +423,12 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
           v.x += (T)((ux - sx) * W) * h;
           v.y += (T)((uy - sy) * W) * h;
           v.z += (T)((uz - sz) * W) * h;
-          src[e] = v;
+          NearField<T>::stage(src, chunk, e, v);
         }
       }
+      if (tid == 0) NearField<T>::pad(src, chunk, ns);
       __syncthreads();
-      if (pass == 0) {
-        for (int j = 0; j < ns; j++) {
-          V4 v = src[j];
-          T dx0 = v.x - x0, dy0 = v.y - y0, dz0 = v.z - z0;
-          T dx1 = v.x - x1, dy1 = v.y - y1, dz1 = v.z - z1;
-          T q0 = dx0 * dx0 + dy0 * dy0 + dz0 * dz0;
-          T q1 = dx1 * dx1 + dy1 * dy1 + dz1 * dz1;
-          T i0 = q0 > (T)0 ? rsq(q0) : (T)0;
-          T i1 = q1 > (T)0 ? rsq(q1) : (T)0;
-          s0 += v.w * i0;
-          s1 += v.w * i1;
-        }
-      } else {
-#pragma unroll 4
-        for (int j = 0; j < ns; j++) {
-          V4 v = src[j];
-          T dx0 = v.x - x0, dy0 = v.y - y0, dz0 = v.z - z0;
-          T dx1 = v.x - x1, dy1 = v.y - y1, dz1 = v.z - z1;
-          T q0 = dx0 * dx0 + dy0 * dy0 + dz0 * dz0;
-          T q1 = dx1 * dx1 + dy1 * dy1 + dz1 * dz1;
-          s0 += v.w * rsq(q0);
-          s1 += v.w * rsq(q1);
-        }
-      }
+      nf.run(src, chunk, ns, pass == 0, two, x0, y0, z0, x1, y1, z1);
     }
     // L2P of the leaf local expansion and write-out
     for (int side = 0; side < 2; side++) {
@@ -296,7 +439,7 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
       T x = ((T)(lt % W) + (T)0.5 - (T)(0.5 * W)) * h;
       T y = ((T)((lt / W) % W) + (T)0.5 - (T)(0.5 * W)) * h;
       T z = ((T)(lt / (W * W)) + (T)0.5 - (T)(0.5 * W)) * h;
-      T v = (side ? s1 : s0) + l2p_eval<T, C>(Lc, g.p, x, y, z);
+      T v = nf.sum(side) + l2p_point<T, C>(Lc, g.p, x, y, z);
       if (r.a & (1u << 19)) {
         d.phi_old[r.u] = (double)v;
       } else {
@@ -311,13 +454,15 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
 static size_t propose_smem(const Geo& g, int prec, int pmax, int chunk) {
   size_t ts = prec == 0 ? 8 : 4;
   int nbw = (g.W * g.W * g.W + 31) / 32;
-  return 4 * ts * (size_t)chunk + 2 * ts * (size_t)g.P + 8 * (size_t)pmax + 4 * (size_t)nbw + 4 * 32;
+  size_t srcb = prec == 0 ? (size_t)chunk * 32 : (size_t)(chunk / 2 + 1) * 32;
+  return srcb + 2 * ts * (size_t)g.P + 8 * (size_t)pmax + 4 * (size_t)nbw + 4 * 32;
 }
 
 static void propose_shape(const Geo& g, int* pmax, int* chunk) {
   int W3 = g.W * g.W * g.W;
   *pmax = W3 + 6 * W3 + 6 * g.W * g.W;  // every own charge, its hops, every entering hop
-  *chunk = 1024 > g.cap ? 1024 : g.cap;
+  int c = 1024 > g.cap ? 1024 : g.cap;
+  *chunk = (c + 1) & ~1;  // even: FP32 sources are staged in pairs
 }
 
 void kmc_prepare(const Geo& g, int prec) {
@@ -341,37 +486,77 @@ void kmc_propose_lattice(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
 // thread per particle; FP64 assembly.  Block sums are sequential over the
 // block's threads so that the selection walk reproduces them exactly.
 #define FIN_THREADS 256
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// MIXED: the assembly and the rate's mantissa in FP32 (dU tolerance of the
+// mixed form is far above FP32 rounding), exponent range kept by an FP64 path
+// for rates below ~1e-34; FP64: every operation in FP64.
+template <bool MIXED>
 __global__ void __launch_bounds__(FIN_THREADS) k_finalize(const Geo g, const Dev d) {
   __shared__ double ts[FIN_THREADS];
   int64_t i = blockIdx.x * (int64_t)FIN_THREADS + threadIdx.x;
   double tsum = 0.0;
   if (i < g.n) {
-    const double q = d.q[i];
     const int E = g.E;
     const int s = d.site[i];
     const int gx = s % E, gy = (s / E) % E, gz = s / (E * E);
     const double V = g.a * g.a * g.a;
-    const double cdip = 4.0 * M_PI / (3.0 * V) * q;
-    const double po = d.phi_old[i];
-    const double M0 = d.dip[0], M1 = d.dip[1], M2 = d.dip[2];
-    for (int k = 0; k < KMC_NHOP; k++) {
-      int64_t j = 6 * i + k;
-      double du, r;
-      if (!d.mask[j]) {
-        du = __longlong_as_double(0x7ff8000000000000LL);
-        r = 0.0;
-      } else {
-        int tx = gx + c_hop[k][0], ty = gy + c_hop[k][1], tz = gz + c_hop[k][2];
-        double dx = c_hop[k][0] * g.h, dy = c_hop[k][1] * g.h, dz = c_hop[k][2] * g.h;
-        if (tx < 0) dx += g.a; else if (tx >= E) dx -= g.a;
-        if (ty < 0) dy += g.a; else if (ty >= E) dy -= g.a;
-        if (tz < 0) dz += g.a; else if (tz >= E) dz -= g.a;
-        du = q * (d.phi_new[j] - po) - cdip * (M0 * dx + M1 * dy + M2 * dz) - q * q * d.selfc[k];
-        r = exp(-fmax(du, 0.0) / g.kT);
+    const double qd = d.q[i];
+    const double cq = 4.0 * M_PI / (3.0 * V) * qd;
+    const double cM[3] = {cq * d.dip[0], cq * d.dip[1], cq * d.dip[2]};
+    const int gc[3] = {gx, gy, gz};
+    const double inv_kT = 1.0 / g.kT;
+    if (MIXED) {
+      const float q = (float)qd, po = (float)d.phi_old[i], ikT = (float)inv_kT;
+      const float fh = (float)g.h, fa = (float)g.a;
+      const float fM[3] = {(float)cM[0], (float)cM[1], (float)cM[2]};
+      for (int k = 0; k < KMC_NHOP; k++) {
+        int64_t j = 6 * i + k;
+        double du, r;
+        if (!d.mask[j]) {
+          du = __longlong_as_double(0x7ff8000000000000LL);
+          r = 0.0;
+        } else {
+          int ax = k >> 1;
+          float sg = (k & 1) ? -1.f : 1.f;
+          int t = gc[ax] + ((k & 1) ? -1 : 1);
+          float dw = sg * fh;
+          if (t < 0) dw += fa; else if (t >= E) dw -= fa;
+          float duf = q * ((float)d.phi_new[j] - po) - fM[ax] * dw - q * q * (float)d.selfc[k];
+          du = (double)duf;
+          float x = fmaxf(duf, 0.f) * ikT;
+          if (x < 75.f) r = (double)ex2_approx(-x * 1.4426950408889634f);
+          else r = exp(-(double)x);
+        }
+        d.dU[j] = du;
+        d.rate[j] = r;
+        tsum += r;
       }
-      d.dU[j] = du;
-      d.rate[j] = r;
-      tsum += r;
+    } else {
+      const double po = d.phi_old[i];
+      for (int k = 0; k < KMC_NHOP; k++) {
+        int64_t j = 6 * i + k;
+        double du, r;
+        if (!d.mask[j]) {
+          du = __longlong_as_double(0x7ff8000000000000LL);
+          r = 0.0;
+        } else {
+          int ax = k >> 1;
+          double sg = (k & 1) ? -1.0 : 1.0;
+          int t = gc[ax] + ((k & 1) ? -1 : 1);
+          double dw = sg * g.h;
+          if (t < 0) dw += g.a; else if (t >= E) dw -= g.a;
+          du = qd * (d.phi_new[j] - po) - cM[ax] * dw - qd * qd * d.selfc[k];
+          r = exp(-fmax(du, 0.0) * inv_kT);
+        }
+        d.dU[j] = du;
+        d.rate[j] = r;
+        tsum += r;
+      }
     }
   }
   ts[threadIdx.x] = tsum;
@@ -399,9 +584,10 @@ __global__ void __launch_bounds__(FIN_THREADS) k_rate_bsum(const Geo g, const De
   }
 }
 
-void kmc_finalize_rates(const Geo& g, const Dev& d, cudaStream_t s) {
+void kmc_finalize_rates(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
   unsigned nb = (unsigned)((g.n + FIN_THREADS - 1) / FIN_THREADS);
-  k_finalize<<<nb, FIN_THREADS, 0, s>>>(g, d);
+  if (prec == 0) k_finalize<false><<<nb, FIN_THREADS, 0, s>>>(g, d);
+  else k_finalize<true><<<nb, FIN_THREADS, 0, s>>>(g, d);
 }
 
 // ------------------------------------------------------------------ selection
@@ -409,61 +595,68 @@ void kmc_finalize_rates(const Geo& g, const Dev& d, cudaStream_t s) {
 // where R is the cumulative sum taken block by block (block sums from the
 // finalize kernel, chunks of block sums per thread here); dt = -ln(xi)/Q.
 #define SEL_THREADS 1024
+// inclusive prefix sum over a shared array of n <= blockDim values
+// (Hillis-Steele, fixed order); every thread of the block must call it
+__device__ __forceinline__ void block_scan(double* v, int n) {
+  for (int off = 1; off < n; off <<= 1) {
+    double x = 0.0;
+    if (threadIdx.x < n) x = v[threadIdx.x] + (threadIdx.x >= off ? v[threadIdx.x - off] : 0.0);
+    __syncthreads();
+    if (threadIdx.x < n) v[threadIdx.x] = x;
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(SEL_THREADS) k_select(const Geo g, const Dev d, int use_counter) {
   __shared__ double cs[SEL_THREADS];
   __shared__ double ts[FIN_THREADS];
-  __shared__ double sh_res;
+  __shared__ double sh_target, sh_prev;
+  __shared__ int sh_t;
   __shared__ int64_t sh_blk;
   const int tid = threadIdx.x;
   const int64_t nb = (g.n + FIN_THREADS - 1) / FIN_THREADS;
   const int64_t per = (nb + SEL_THREADS - 1) / SEL_THREADS;
   const double* uni = use_counter ? d.uni_run + 2 * (int64_t)(*d.stepc) : d.uni_small;
-  double zeta = uni[0];
-  double xi = uni[1];
+  const double zeta = uni[0], xi = uni[1];
   double c = 0.0;
   for (int64_t b = tid * per; b < min(nb, (tid + 1) * per); b++) c += d.bsum[b];
   cs[tid] = c;
+  if (tid == 0) { sh_t = -1; sh_blk = -1; }
   __syncthreads();
-  if (tid == 0) {
-    double Q = 0.0;
-    for (int t = 0; t < SEL_THREADS; t++) Q += cs[t];
-    d.dtq[1] = Q;
-    d.dtq[0] = (Q > 0.0) ? -log(xi) / Q : __longlong_as_double(0x7ff0000000000000LL);
-    int64_t blk = -1;
-    double res = 0.0;
-    if (Q > 0.0) {
-      double target = Q * zeta;
-      double run = 0.0;
-      int tsel = -1;
-      for (int t = 0; t < SEL_THREADS; t++) {
-        if (run + cs[t] >= target && cs[t] > 0.0) { tsel = t; break; }
-        run += cs[t];
-      }
-      if (tsel < 0) {  // rounding at zeta = 1: last chunk with weight
-        for (int t = SEL_THREADS - 1; t >= 0; t--)
-          if (cs[t] > 0.0) { tsel = t; break; }
-        run = 0.0;
-        for (int t = 0; t < tsel; t++) run += cs[t];
-        target = run + cs[tsel];
-      }
-      double r2 = run;
-      int64_t bend = min(nb, (tsel + 1) * per);
-      for (int64_t b = tsel * per; b < bend; b++) {
-        double bs = d.bsum[b];
-        if (bs > 0.0 && (r2 + bs >= target || b == bend - 1)) { blk = b; break; }
-        r2 += bs;
-      }
-      if (blk < 0) {
-        for (int64_t b = bend - 1; b >= tsel * per; b--)
-          if (d.bsum[b] > 0.0) { blk = b; break; }
-      }
-      res = target - r2;
-    }
-    sh_blk = blk;
-    sh_res = res;
+  block_scan(cs, SEL_THREADS);
+  const double Q = cs[SEL_THREADS - 1];
+  const double target = Q * zeta;
+  if (Q > 0.0) {
+    double prev = tid ? cs[tid - 1] : 0.0;
+    if (prev < target && target <= cs[tid]) { sh_t = tid; sh_prev = prev; }
   }
   __syncthreads();
-  int64_t blk = sh_blk;
+  if (tid == 0) {
+    d.dtq[1] = Q;
+    d.dtq[0] = (Q > 0.0) ? -log(xi) / Q : __longlong_as_double(0x7ff0000000000000LL);
+    int t = sh_t;
+    if (Q > 0.0 && t < 0) {  // rounding: last chunk with weight
+      for (int u = SEL_THREADS - 1; u >= 0; u--)
+        if (cs[u] > (u ? cs[u - 1] : 0.0)) { t = u; break; }
+      sh_prev = t ? cs[t - 1] : 0.0;
+    }
+    if (t >= 0) {
+      double run = sh_prev;
+      int64_t blk = -1, bend = min(nb, (t + 1) * per);
+      for (int64_t b = t * per; b < bend; b++) {
+        double bs = d.bsum[b];
+        if (bs > 0.0 && run + bs >= target) { blk = b; break; }
+        run += bs;
+      }
+      if (blk < 0)
+        for (int64_t b = bend - 1; b >= t * per; b--)
+          if (d.bsum[b] > 0.0) { blk = b; break; }
+      sh_blk = blk;
+      sh_target = target - run;
+    }
+  }
+  __syncthreads();
+  const int64_t blk = sh_blk;
   if (blk < 0) {
     if (tid == 0) *d.event = -1;
     return;
@@ -475,26 +668,29 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(const Geo g, const Dev d
       for (int k = 0; k < KMC_NHOP; k++) t += d.rate[6 * i + k];
     ts[tid] = t;
   }
+  if (tid == 0) sh_t = -1;
+  __syncthreads();
+  block_scan(ts, FIN_THREADS);
+  const double res = sh_target;
+  if (tid < FIN_THREADS) {
+    double prev = tid ? ts[tid - 1] : 0.0;
+    if (prev < res && res <= ts[tid]) { sh_t = tid; sh_prev = prev; }
+  }
   __syncthreads();
   if (tid == 0) {
-    double res = sh_res, run = 0.0;
-    int tsel = -1;
-    for (int t = 0; t < FIN_THREADS; t++) {
-      if (ts[t] > 0.0 && run + ts[t] >= res) { tsel = t; break; }
-      run += ts[t];
+    int t = sh_t;
+    double run = sh_prev, rr = res;
+    if (t < 0) {  // rounding between the block sum and its scan
+      for (int u = FIN_THREADS - 1; u >= 0; u--)
+        if (ts[u] > (u ? ts[u - 1] : 0.0)) { t = u; break; }
+      run = t ? ts[t - 1] : 0.0;
+      rr = ts[t];
     }
-    if (tsel < 0) {
-      for (int t = FIN_THREADS - 1; t >= 0; t--)
-        if (ts[t] > 0.0) { tsel = t; break; }
-      run = 0.0;
-      for (int t = 0; t < tsel; t++) run += ts[t];
-      res = run + ts[tsel];
-    }
-    int64_t i = blk * FIN_THREADS + tsel;
+    int64_t i = blk * FIN_THREADS + t;
     int ksel = -1;
     for (int k = 0; k < KMC_NHOP; k++) {
       double r = d.rate[6 * i + k];
-      if (r > 0.0 && run + r >= res) { ksel = k; break; }
+      if (r > 0.0 && run + r >= rr) { ksel = k; break; }
       run += r;
     }
     if (ksel < 0)
@@ -563,7 +759,9 @@ __device__ __forceinline__ int cell_coord(double x, double w, int n) {
 }
 
 // multipoles of the ancestors of the old and new positions, all levels:
-// Mt_l[anc(r)] -= q R(r - c), Mt_l[anc(r')] += q R(r' - c).  thread per (level, m)
+// Mt_l[anc(r)] -= q R(r - c), Mt_l[anc(r')] += q R(r' - c).  thread per (level, m).
+// The level-1 change (about the domain centre) is also stored in dK for the
+// far-field update.
 __global__ void k_acc_multipole(const Geo g, const Dev d) {
   MoveRec mv = *d.move;
   if (!mv.valid) return;
@@ -585,101 +783,167 @@ __global__ void k_acc_multipole(const Geo g, const Dev d) {
     }
     double2* out = d.Mt + (g.cell_off[l] + cx + (int64_t)nl * (cy + (int64_t)nl * cz)) * g.P;
     double2 a1 = mm, a2 = make_double2(0.0, 0.0);
-    out[tri(m, m)].x += q * mm.x;
-    out[tri(m, m)].y += q * mm.y;
-    for (int n = m + 1; n <= g.p; n++) {
-      double cc = c_inv_d[tri(n, m)];
-      double zz = (2 * n - 1) * dz;
-      double2 v = make_double2((zz * a1.x - r2 * a2.x) * cc, (zz * a1.y - r2 * a2.y) * cc);
+    double2 v = mm;
+    for (int n = m; n <= g.p; n++) {
+      if (n > m) {
+        double cc = c_inv_d[tri(n, m)];
+        double zz = (2 * n - 1) * dz;
+        v = make_double2((zz * a1.x - r2 * a2.x) * cc, (zz * a1.y - r2 * a2.y) * cc);
+        a2 = a1;
+        a1 = v;
+      }
       out[tri(n, m)].x += q * v.x;
       out[tri(n, m)].y += q * v.y;
-      a2 = a1;
-      a1 = v;
+      if (l == 1) {
+        if (side == 0) d.dK[tri(n, m)] = make_double2(q * v.x, q * v.y);
+        else { d.dK[tri(n, m)].x += q * v.x; d.dK[tri(n, m)].y += q * v.y; }
+      }
     }
   }
 }
 
-// far field: H += R dK, dK = q [R(r' - c) - R(r - c)] about the domain centre
+// far field: H += R dK, one CTA (one warp) per output coefficient, lanes split
+// the (k, l) sum; fixed-order warp reduction.
 __global__ void k_acc_far(const Geo g, const Dev d) {
-  extern __shared__ double2 dK[];
   MoveRec mv = *d.move;
   if (!mv.valid) return;
-  int tid = threadIdx.x;
-  if (tid < g.p + 1) {
-    int m = tid;
-    double c = 0.5 * g.a;
-    for (int side = 0; side < 2; side++) {
-      const double* x = side ? mv.rn : mv.r;
-      double q = side ? mv.q : -mv.q;
-      double dx = x[0] - c, dy = x[1] - c, dz = x[2] - c;
-      double r2 = dx * dx + dy * dy + dz * dz;
-      double2 mm = make_double2(1.0, 0.0);
-      for (int j = 1; j <= m; j++) {
-        double sc = c_halfm_d[j];
-        mm = make_double2(sc * (dx * mm.x - dy * mm.y), sc * (dx * mm.y + dy * mm.x));
-      }
-      double2 a1 = mm, a2 = make_double2(0.0, 0.0);
-      double2 v = mm;
-      for (int n = m; n <= g.p; n++) {
-        if (n > m) {
-          double cc = c_inv_d[tri(n, m)];
-          double zz = (2 * n - 1) * dz;
-          v = make_double2((zz * a1.x - r2 * a2.x) * cc, (zz * a1.y - r2 * a2.y) * cc);
-          a2 = a1;
-          a1 = v;
-        }
-        if (side == 0) dK[tri(n, m)] = make_double2(q * v.x, q * v.y);
-        else { dK[tri(n, m)].x += q * v.x; dK[tri(n, m)].y += q * v.y; }
-      }
-    }
-  }
-  __syncthreads();
-  if (tid >= g.P) return;
+  const int ci = blockIdx.x, lane = threadIdx.x;
   int n = 0;
-  while (tri(n + 1, 0) <= tid) n++;
-  int m = tid - tri(n, 0);
-  double2 acc = make_double2(0.0, 0.0);
-  for (int k = 0; k <= g.p; k++) {
-    double sgn = (k & 1) ? -1.0 : 1.0;
-    for (int ll = -k; ll <= k; ll++) {
-      double2 a = tab_get(dK, k, ll), b = tab_get(d.S, n + k, m + ll);
-      acc.x += sgn * (a.x * b.x + a.y * b.y);
-      acc.y += sgn * (a.y * b.x - a.x * b.y);
-    }
+  while (tri(n + 1, 0) <= ci) n++;
+  const int m = ci - tri(n, 0);
+  const int nkl = (g.p + 1) * (g.p + 1);  // (k, l) pairs with l in [-k, k]
+  double ax = 0.0, ay = 0.0;
+  for (int t = lane; t < nkl; t += 32) {
+    int k = 0;
+    while ((k + 1) * (k + 1) <= t) k++;
+    int ll = t - k * k - k;
+    double2 a = tab_get(d.dK, k, ll), b = tab_get(d.S, n + k, m + ll);
+    double sx = a.x * b.x + a.y * b.y, sy = a.y * b.x - a.x * b.y;
+    if (k & 1) { ax -= sx; ay -= sy; }
+    else { ax += sx; ay += sy; }
   }
-  double2* H = d.Psi + g.cell_off[1] * g.P;
-  H[tid].x += acc.x;
-  H[tid].y += acc.y;
+  for (int o = 16; o > 0; o >>= 1) {
+    ax += __shfl_xor_sync(0xffffffffu, ax, o);
+    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+  }
+  if (lane == 0) {
+    double2* H = d.Psi + g.cell_off[1] * g.P;
+    H[ci].x += ax;
+    H[ci].y += ay;
+  }
 }
 
-// per-level interaction-list locals.  For level l, the candidate cells are the
-// children of the (wrapped) 3x3x3 parent neighbourhoods of the old and new
-// positions' parent cells; for each candidate b and each of the 27 images of
-// both positions, the image (cell u) is added when it lies in IL(b):
-// |floor(u/2) - floor(b/2)|_inf <= 1 and |u - b|_inf >= 2.  thread per
-// (level, candidate, m); FP64 P2L  L_n^m += q conj(I_n^m(y - c_b)).
+// P2L of a point charge q at offset (dx,dy,dz) from a cell centre, all (n, m):
+// out[tri(n,m)] (+)= q conj(I_n^m(d)).
+template <bool ACCUM>
+__device__ void p2l_table(double2* out, double q, double dx, double dy, double dz, int p) {
+  double r2 = dx * dx + dy * dy + dz * dz, inv = 1.0 / r2;
+  double2 mm = make_double2(1.0 / sqrt(r2), 0.0);
+  for (int m = 0; m <= p; m++) {
+    if (m > 0) {
+      double sc = -(2.0 * m - 1.0) * inv;
+      mm = make_double2(sc * (dx * mm.x - dy * mm.y), sc * (dx * mm.y + dy * mm.x));
+    }
+    double2 a1 = mm, a2 = make_double2(0.0, 0.0), v = mm;
+    for (int n = m; n <= p; n++) {
+      if (n > m) {
+        double zz = (2 * n - 1) * dz;
+        double c2 = (double)((n - 1) * (n - 1) - m * m);
+        v = make_double2((zz * a1.x - c2 * a2.x) * inv, (zz * a1.y - c2 * a2.y) * inv);
+        a2 = a1;
+        a1 = v;
+      }
+      if (ACCUM) {
+        out[tri(n, m)].x += q * v.x;
+        out[tri(n, m)].y -= q * v.y;
+      } else {
+        out[tri(n, m)] = make_double2(q * v.x, -q * v.y);
+      }
+    }
+  }
+}
+
+// the image nu (0..26) of position x, seen from cell b on level l: true when
+// its cell u = cell(x) + n_l nu lies in the interaction list of b, i.e.
+// |floor(u/2) - floor(b/2)|_inf <= 1 and |u - b|_inf >= 2.
 __device__ __forceinline__ int fdiv2(int u) { return (u >= 0) ? (u >> 1) : -((1 - u) >> 1); }
+__device__ __forceinline__ bool image_in_il(const int u0[3], int nl, int nu, const int b[3]) {
+  int nv[3] = {nu % 3 - 1, (nu / 3) % 3 - 1, nu / 9 - 1};
+  bool in = true, far = false;
+  for (int c = 0; c < 3; c++) {
+    int u = u0[c] + nl * nv[c];
+    if (abs(fdiv2(u) - (b[c] >> 1)) > 1) in = false;
+    if (abs(u - b[c]) >= 2) far = true;
+  }
+  return in && far;
+}
+
+// coarse levels (n_l <= 4): every cell b of the level, thread per (cell, image
+// of either position); the P2L tables go to a scratch area and are summed over
+// the images in fixed order by k_acc_coarse_reduce.
+__global__ void k_acc_coarse(const Geo g, const Dev d, int l, double2* scratch) {
+  MoveRec mv = *d.move;
+  if (!mv.valid) return;
+  const int nl = 1 << (l - 1), ncl = nl * nl * nl;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int cell = t / 54, im = t % 54;
+  if (cell >= ncl) return;
+  int b[3] = {cell % nl, (cell / nl) % nl, cell / (nl * nl)};
+  const double wl = g.a / nl;
+  int side = im / 27, nu = im % 27;
+  const double* x = side ? mv.rn : mv.r;
+  double q = side ? mv.q : -mv.q;
+  int u0[3];
+  for (int c = 0; c < 3; c++) u0[c] = cell_coord(x[c], wl, nl);
+  double2* out = scratch + ((int64_t)cell * 54 + im) * g.P;
+  if (!image_in_il(u0, nl, nu, b)) {
+    for (int c = 0; c < g.P; c++) out[c] = make_double2(0.0, 0.0);
+    return;
+  }
+  int nv[3] = {nu % 3 - 1, (nu / 3) % 3 - 1, nu / 9 - 1};
+  double dx = x[0] + g.a * nv[0] - (b[0] + 0.5) * wl, dy = x[1] + g.a * nv[1] - (b[1] + 0.5) * wl,
+         dz = x[2] + g.a * nv[2] - (b[2] + 0.5) * wl;
+  p2l_table<false>(out, q, dx, dy, dz, g.p);
+}
+
+__global__ void k_acc_coarse_reduce(const Geo g, const Dev d, int l, const double2* scratch) {
+  MoveRec mv = *d.move;
+  if (!mv.valid) return;
+  const int nl = 1 << (l - 1), ncl = nl * nl * nl;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int cell = t / g.P, c = t % g.P;
+  if (cell >= ncl) return;
+  double ax = 0.0, ay = 0.0;
+  for (int im = 0; im < 54; im++) {
+    double2 v = scratch[((int64_t)cell * 54 + im) * g.P + c];
+    ax += v.x;
+    ay += v.y;
+  }
+  double2* out = d.Psi + (g.cell_off[l] + cell) * g.P;
+  out[c].x += ax;
+  out[c].y += ay;
+}
+
+// fine levels (n_l >= 8): the candidate cells are the children of the
+// (wrapped) 3x3x3 parent neighbourhoods of the old and new positions' parent
+// cells, each candidate handled by one thread that loops over the 54 images
+// and accumulates the P2L of those in its interaction list.
 __device__ __forceinline__ int wdist(int a, int b, int n) {
   int t = ((a - b) % n + n) % n;
   return min(t, n - t);
 }
 
-__global__ void k_acc_locals(const Geo g, const Dev d) {
+__global__ void k_acc_fine(const Geo g, const Dev d, int lmin) {
   MoveRec mv = *d.move;
   if (!mv.valid) return;
-  const int l = 2 + blockIdx.y;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int cand = t / (g.p + 1), m = t % (g.p + 1);
+  const int l = lmin + blockIdx.y;
+  int cand = blockIdx.x * blockDim.x + threadIdx.x;
   if (cand >= 432) return;
   const int nl = 1 << (l - 1), np = nl >> 1;
   const double wl = g.a / nl;
   int side0 = cand / 216, rem = cand % 216;
   int di = rem >> 3, o = rem & 7;
   int dlt[3] = {di % 3 - 1, (di / 3) % 3 - 1, di / 9 - 1};
-  for (int c = 0; c < 3; c++) {
-    if (np == 1 && dlt[c] != 0) return;
-    if (np == 2 && dlt[c] == -1) return;
-  }
   const double* x0 = side0 ? mv.rn : mv.r;
   int P0[3], Pold[3];
   for (int c = 0; c < 3; c++) {
@@ -694,51 +958,19 @@ __global__ void k_acc_locals(const Geo g, const Dev d) {
       if (wdist(b[c] >> 1, Pold[c], np) > 1) in_old = false;
     if (in_old) return;
   }
-  double cb[3] = {(b[0] + 0.5) * wl, (b[1] + 0.5) * wl, (b[2] + 0.5) * wl};
-  double2 acc[KMC_MAXP + 1];
-  for (int n = 0; n <= g.p; n++) acc[n] = make_double2(0.0, 0.0);
-  bool any = false;
+  double2* out = d.Psi + (g.cell_off[l] + b[0] + (int64_t)nl * (b[1] + (int64_t)nl * b[2])) * g.P;
   for (int side = 0; side < 2; side++) {
     const double* x = side ? mv.rn : mv.r;
     double q = side ? mv.q : -mv.q;
     int u0[3];
     for (int c = 0; c < 3; c++) u0[c] = cell_coord(x[c], wl, nl);
     for (int nu = 0; nu < 27; nu++) {
+      if (!image_in_il(u0, nl, nu, b)) continue;
       int nv[3] = {nu % 3 - 1, (nu / 3) % 3 - 1, nu / 9 - 1};
-      bool in = true, far = false;
-      for (int c = 0; c < 3; c++) {
-        int u = u0[c] + nl * nv[c];
-        if (abs(fdiv2(u) - (b[c] >> 1)) > 1) in = false;
-        if (abs(u - b[c]) >= 2) far = true;
-      }
-      if (!in || !far) continue;
-      any = true;
-      double dx = x[0] + g.a * nv[0] - cb[0], dy = x[1] + g.a * nv[1] - cb[1], dz = x[2] + g.a * nv[2] - cb[2];
-      double r2 = dx * dx + dy * dy + dz * dz, inv = 1.0 / r2;
-      double2 mm = make_double2(1.0 / sqrt(r2), 0.0);
-      for (int j = 1; j <= m; j++) {
-        double sc = -(2.0 * j - 1.0) * inv;
-        mm = make_double2(sc * (dx * mm.x - dy * mm.y), sc * (dx * mm.y + dy * mm.x));
-      }
-      double2 a1 = mm, a2 = make_double2(0.0, 0.0);
-      acc[m].x += q * mm.x;
-      acc[m].y -= q * mm.y;
-      for (int n = m + 1; n <= g.p; n++) {
-        double zz = (2 * n - 1) * dz;
-        double c2 = (double)((n - 1) * (n - 1) - m * m);
-        double2 v = make_double2((zz * a1.x - c2 * a2.x) * inv, (zz * a1.y - c2 * a2.y) * inv);
-        acc[n].x += q * v.x;
-        acc[n].y -= q * v.y;
-        a2 = a1;
-        a1 = v;
-      }
+      double dx = x[0] + g.a * nv[0] - (b[0] + 0.5) * wl, dy = x[1] + g.a * nv[1] - (b[1] + 0.5) * wl,
+             dz = x[2] + g.a * nv[2] - (b[2] + 0.5) * wl;
+      p2l_table<true>(out, q, dx, dy, dz, g.p);
     }
-  }
-  if (!any) return;
-  double2* out = d.Psi + (g.cell_off[l] + b[0] + (int64_t)nl * (b[1] + (int64_t)nl * b[2])) * g.P;
-  for (int n = m; n <= g.p; n++) {
-    out[tri(n, m)].x += acc[n].x;
-    out[tri(n, m)].y += acc[n].y;
   }
 }
 
@@ -786,10 +1018,19 @@ __global__ void k_acc_move(const Geo g, const Dev d) {
 
 void kmc_accept_apply(const Geo& g, const Dev& d, cudaStream_t s) {
   int nt = g.L * (g.p + 1);
-  k_acc_multipole<<<(nt + 63) / 64, 64, 0, s>>>(g, d);
-  k_acc_far<<<1, g.P <= 128 ? 128 : 256, g.P * sizeof(double2), s>>>(g, d);
-  dim3 grid((432 * (g.p + 1) + 127) / 128, g.L - 1);
-  k_acc_locals<<<grid, 128, 0, s>>>(g, d);
+  k_acc_multipole<<<(nt + 31) / 32, 32, 0, s>>>(g, d);
+  k_acc_far<<<g.P, 32, 0, s>>>(g, d);
+  // coarse levels 2 and 3 (8 and 64 cells): all cells x all images
+  int lc = g.L < 3 ? g.L : 3;
+  for (int l = 2; l <= lc; l++) {
+    int ncl = 1 << (3 * (l - 1));
+    k_acc_coarse<<<(ncl * 54 + 63) / 64, 64, 0, s>>>(g, d, l, d.acc_scratch);
+    k_acc_coarse_reduce<<<(ncl * g.P + 127) / 128, 128, 0, s>>>(g, d, l, d.acc_scratch);
+  }
+  if (g.L >= 4) {
+    dim3 grid((432 + 31) / 32, g.L - 3);
+    k_acc_fine<<<grid, 32, 0, s>>>(g, d, 4);
+  }
   k_acc_move<<<1, 1, 0, s>>>(g, d);
 }
 

@@ -43,6 +43,7 @@ struct kmc_fmm {
   cudaGraphExec_t graph;
   int graph_steps;
   double* drift2;
+  double* phi_save;
   int32_t* iota;
 };
 
@@ -152,7 +153,7 @@ static int compute_phi_old(kmc_fmm* h) {
   if (r) return r;
   if (h->g.E > 0) {
     kmc_propose_lattice(h->g, h->d, h->prec, h->stream);
-    kmc_finalize_rates(h->g, h->d, h->stream);
+    kmc_finalize_rates(h->g, h->d, h->prec, h->stream);
     h->rates_valid = true;
   } else {
     kmc_eval_points(h->g, h->d, h->prec, h->g.n, h->d.pos, h->iota, h->d.phi_old, h->stream);
@@ -240,6 +241,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   h->graph_steps = 0;
   h->gen_cap = 0;
   h->run_cap = 0;
+  h->phi_save = nullptr;
   *out = h;
   // ---- host-side argument checks
   if (n < 2) return fail(h, KMC_ERR_ARG, "need at least 2 charges (n = %lld)", (long long)n);
@@ -333,6 +335,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   ALLOC(d.Peff, (h->prec == 0 ? sizeof(double2) : sizeof(float2)) * g.ncell_total * g.P);
   ALLOC(d.Itab, sizeof(double2) * (size_t)(g.L + 1) * 343 * g.P2);
   ALLOC(d.S, sizeof(double2) * g.P2);
+  ALLOC(d.Rch, sizeof(double2) * (size_t)(g.L + 1) * 8 * g.P);
   ALLOC(d.selfc, sizeof(double) * KMC_NHOP);
   ALLOC(d.dip, sizeof(double) * 3);
   ALLOC(d.U, sizeof(double));
@@ -345,6 +348,8 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   ALLOC(d.event, sizeof(int64_t) * 2);
   ALLOC(d.dtq, sizeof(double) * 2);
   ALLOC(d.move, sizeof(MoveRec));
+  ALLOC(d.dK, sizeof(double2) * g.P);
+  ALLOC(d.acc_scratch, sizeof(double2) * 64 * 54 * g.P);
   ALLOC(d.err, sizeof(int) * 4);
   ALLOC(d.uni_small, sizeof(double) * 2);
   ALLOC(d.stepc, sizeof(int) * 2);
@@ -390,6 +395,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   r = check_flags(h, "init binning");
   if (r) return r;
   fmm_itab(g, d, s);
+  fmm_child_tables(g, d, s);
   fmm_lattice_sums(g, d, s);
   CKLAUNCH();
   r = full_fmm(h);
@@ -415,7 +421,7 @@ int kmc_fmm_propose_lattice(kmc_handle h, uint8_t* mask, double* dU) {
   r = refresh_peff(h);
   if (r) return r;
   kmc_propose_lattice(h->g, h->d, h->prec, h->stream);
-  kmc_finalize_rates(h->g, h->d, h->stream);
+  kmc_finalize_rates(h->g, h->d, h->prec, h->stream);
   CKLAUNCH();
   h->rates_valid = true;
   const int64_t m = 6 * h->g.n;
@@ -474,7 +480,10 @@ static int general_du(kmc_fmm* h, int64_t m) {
   if (r) return r;
   const Geo& g = h->g;
   cudaStream_t s = h->stream;
-  kmc_eval_points(g, h->d, h->prec, m, h->gen_tgt, h->gen_part, h->gen_pn, s);
+  // Phi at the target includes every charge (the moving one too: its old
+  // position's contribution is removed by the self term C(d)); Phi at the old
+  // position omits only the moving charge itself.
+  kmc_eval_points(g, h->d, h->prec, m, h->gen_tgt, nullptr, h->gen_pn, s);
   kmc_eval_points(g, h->d, h->prec, m, h->gen_old, h->gen_part, h->gen_po, s);
   fmm_selfcorr_list(g, h->d, m, h->gen_dv, h->gen_du, s);
   kmc_assemble_general(g, h->d, m, h->gen_part, h->gen_tgt, h->gen_mask, h->gen_pn, h->gen_po, h->gen_du, s);
@@ -621,7 +630,7 @@ static void enqueue_step(kmc_fmm* h) {
   cudaStream_t s = h->stream;
   fmm_downward(g, d, h->prec, s);
   kmc_propose_lattice(g, d, h->prec, s);
-  kmc_finalize_rates(g, d, s);
+  kmc_finalize_rates(g, d, h->prec, s);
   kmc_select(g, d, 1, s);
   kmc_record(g, d, s);
   kmc_accept_from_event(g, d, s);
@@ -720,7 +729,7 @@ int kmc_run_profiled(kmc_handle h, int steps, const double* uniforms, int64_t* e
     CK(cudaEventRecord(e[1], s));
     kmc_propose_lattice(g, d, h->prec, s);
     CK(cudaEventRecord(e[2], s));
-    kmc_finalize_rates(g, d, s);
+    kmc_finalize_rates(g, d, h->prec, s);
     CK(cudaEventRecord(e[3], s));
     kmc_select(g, d, 1, s);
     kmc_record(g, d, s);
@@ -748,17 +757,24 @@ int kmc_run_profiled(kmc_handle h, int steps, const double* uniforms, int64_t* e
   return check_flags(h, "run_profiled");
 }
 
-int kmc_fmm_recompute(kmc_handle h, double* max_coeff_drift) {
+int kmc_fmm_recompute(kmc_handle h, double* drift) {
   int r = guard(h);
   if (r) return r;
   const Geo& g = h->g;
   cudaStream_t s = h->stream;
+  // potentials at the charges and the tracked energy from the incremental state
+  r = compute_phi_old(h);
+  if (r) return r;
+  if (!h->phi_save) ALLOC(h->phi_save, sizeof(double) * g.n);
+  CK(cudaMemcpyAsync(h->phi_save, h->d.phi_old, sizeof(double) * g.n, cudaMemcpyDeviceToDevice, s));
+  double U_tracked;
+  CK(cudaMemcpyAsync(&U_tracked, h->d.U, sizeof(double), cudaMemcpyDeviceToHost, s));
   double2* saved = (double2*)h->d.scratch;  // lattice-sum scratch is free after init
   size_t need = sizeof(double2) * g.ncell_total * g.P;
-  double2* tmp = nullptr;
   const int nr = 13, nk = 19;
   size_t have = (size_t)(nr * nr * nr + nk * nk * nk) * g.P2 * sizeof(double2);
   if (need > have) {
+    double2* tmp = nullptr;
     ALLOC(tmp, need);
     saved = tmp;
   }
@@ -767,13 +783,23 @@ int kmc_fmm_recompute(kmc_handle h, double* max_coeff_drift) {
   if (r) return r;
   fmm_drift(g, saved, h->d.Psi, g.ncell_total * g.P, h->drift2, s);
   CKLAUNCH();
-  double dr[2];
-  CK(cudaMemcpyAsync(dr, h->drift2, sizeof(dr), cudaMemcpyDeviceToHost, s));
+  double dc[2];
+  CK(cudaMemcpyAsync(dc, h->drift2, sizeof(dc), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
   r = compute_energy(h);
   if (r) return r;
+  fmm_drift1(h->phi_save, h->d.phi_old, g.n, h->drift2, s);
+  CKLAUNCH();
+  double dp[2], U_fresh;
+  CK(cudaMemcpyAsync(dp, h->drift2, sizeof(dp), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&U_fresh, h->d.U, sizeof(double), cudaMemcpyDeviceToHost, s));
   r = check_flags(h, "recompute");
   if (r) return r;
-  if (max_coeff_drift) *max_coeff_drift = dr[1] > 0.0 ? dr[0] / dr[1] : 0.0;
+  if (drift) {
+    drift[0] = dp[1] > 0.0 ? dp[0] / dp[1] : 0.0;
+    drift[1] = dc[1] > 0.0 ? dc[0] / dc[1] : 0.0;
+    drift[2] = U_fresh != 0.0 ? fabs(U_tracked - U_fresh) / fabs(U_fresh) : fabs(U_tracked - U_fresh);
+  }
   return KMC_OK;
 }
 

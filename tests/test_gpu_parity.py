@@ -206,8 +206,10 @@ def test_teacher_forced_trajectory_small(small):
     assert np.array_equal(pos, workloads.site_positions(E, st.sites))
     U = k.kmc_fmm_energy(h)
     assert abs(U - st.energy()) < 1e-4 * abs(st.energy())
-    drift = k.kmc_fmm_recompute(h)
-    assert drift < 1e-8, drift
+    d_phi, d_coef, d_U = k.kmc_fmm_recompute(h)
+    # incremental P2L updates vs fresh M2L differ by truncation only
+    assert d_phi < 1e-5, d_phi
+    assert d_U < 1e-5, d_U
     U2 = k.kmc_fmm_energy(h)
     assert abs(U2 - st.energy()) < 1e-4 * abs(st.energy())
 
