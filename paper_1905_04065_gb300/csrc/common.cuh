@@ -26,8 +26,8 @@
 #define KMC_MAXP 20   // maximum expansion degree
 #define KMC_NHOP 6    // lattice hop directions (+x,-x,+y,-y,+z,-z)
 
-__host__ __device__ __forceinline__ int tri(int n, int m) { return n * (n + 1) / 2 + m; }
-__host__ __device__ __forceinline__ int ncoef(int p) { return (p + 1) * (p + 2) / 2; }
+__host__ __device__ __forceinline__ constexpr int tri(int n, int m) { return n * (n + 1) / 2 + m; }
+__host__ __device__ __forceinline__ constexpr int ncoef(int p) { return (p + 1) * (p + 2) / 2; }
 
 // ---------------------------------------------------------------- complex helpers
 template <typename T> struct cplx;

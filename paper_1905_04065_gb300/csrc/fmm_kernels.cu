@@ -27,6 +27,8 @@ void fmm_upload_constants(int p) {
   for (int k = 1; k < 4 * KMC_MAXP + 2; k++) fact[k] = fact[k - 1] * k;
   cudaMemcpyToSymbol(f_inv_nm, inv, sizeof(inv));
   cudaMemcpyToSymbol(f_fact, fact, sizeof(fact));
+  void fmm_upload_nm();
+  fmm_upload_nm();
   (void)p;
 }
 
@@ -559,64 +561,77 @@ void fmm_selfcorr_list(const Geo& g, const Dev& d, int64_t m, const double* dvec
 
 // ------------------------------------------------------------------ downward pass
 // Peff_1 = H; Peff_l[b] = L2L(Peff_{l-1}[parent] -> c_b) + Psi_l[b]   (precision T)
+// One CTA per parent cell computes all 8 children: the parent expansion and
+// the 8 child-offset harmonic tables sit in shared memory.
+__constant__ short2 f_nm[ncoef(KMC_MAXP)];  // (n, m) of coefficient index tri(n, m)
+
+void fmm_upload_nm() {
+  static short2 nm[ncoef(KMC_MAXP)];
+  for (int n = 0; n <= KMC_MAXP; n++)
+    for (int m = 0; m <= n; m++) nm[tri(n, m)] = make_short2((short)n, (short)m);
+  cudaMemcpyToSymbol(f_nm, nm, sizeof(nm));
+}
+
 template <typename T>
-__global__ void k_downward(const Geo g, const Dev d, int l) {
+__global__ void k_downward_root(const Geo g, const Dev d) {
   typedef typename cplx<T>::type C;
-  extern __shared__ unsigned char shraw[];
-  C* Rt = (C*)shraw;  // 8 * P child-offset regular tables
   C* Pe = (C*)d.Peff;
-  if (l == 1) {
-    for (int c = threadIdx.x; c < g.P; c += blockDim.x) {
-      double2 v = d.Psi[g.cell_off[1] * g.P + c];
-      Pe[g.cell_off[1] * g.P + c] = cmk<C>(v.x, v.y);
-    }
-    return;
+  for (int c = threadIdx.x; c < g.P; c += blockDim.x) {
+    double2 v = d.Psi[g.cell_off[1] * g.P + c];
+    Pe[g.cell_off[1] * g.P + c] = cmk<C>(v.x, v.y);
   }
-  int nl = 1 << (l - 1), np = nl / 2;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_downward(const Geo g, const Dev d, int l) {
+  typedef typename cplx<T>::type C;
+  extern __shared__ __align__(16) unsigned char shraw[];
+  C* R = (C*)shraw;     // 8 * P child-offset regular tables
+  C* Lp = R + 8 * g.P;  // parent expansion
+  C* Pe = (C*)d.Peff;
+  const int nl = 1 << (l - 1), np = nl / 2;
+  const int64_t par = blockIdx.x;
+  const int px = (int)(par % np), py = (int)((par / np) % np), pz = (int)(par / ((int64_t)np * np));
   for (int c = threadIdx.x; c < 8 * g.P; c += blockDim.x) {
     double2 v = d.Rch[(int64_t)l * 8 * g.P + c];
-    Rt[c] = cmk<C>(v.x, v.y);
+    R[c] = cmk<C>(v.x, v.y);
   }
+  for (int c = threadIdx.x; c < g.P; c += blockDim.x) Lp[c] = Pe[(g.cell_off[l - 1] + par) * g.P + c];
   __syncthreads();
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t ncl = (int64_t)nl * nl * nl;
-  int64_t cell = t / g.P;
-  int ci = (int)(t - cell * g.P);
-  if (cell >= ncl) return;
-  int k = 0;
-  while (tri(k + 1, 0) <= ci) k++;
-  int lo = ci - tri(k, 0);
-  int bx = (int)(cell % nl), by = (int)((cell / nl) % nl), bz = (int)(cell / ((int64_t)nl * nl));
-  int o = (bx & 1) | ((by & 1) << 1) | ((bz & 1) << 2);
-  int64_t par = (bx >> 1) + (int64_t)np * ((by >> 1) + (int64_t)np * (bz >> 1));
-  const C* Lp = Pe + (g.cell_off[l - 1] + par) * g.P;
-  const C* R = Rt + o * g.P;
-  T ax = 0, ay = 0;
-  for (int n = k; n <= g.p; n++) {
-    int j = n - k;
-    for (int m = lo - j; m <= lo + j; m++) {
-      if (m < -n || m > n) continue;
-      C a = tab_get(Lp, n, m), b = tab_get(R, j, m - lo);
-      ax += a.x * b.x - a.y * b.y;
-      ay += a.x * b.y + a.y * b.x;
+  for (int t = threadIdx.x; t < 8 * g.P; t += blockDim.x) {
+    const int o = t / g.P, ci = t - o * g.P;
+    const short2 km = f_nm[ci];
+    const int k = km.x, lo = km.y;
+    const C* Ro = R + o * g.P;
+    T ax = 0, ay = 0;
+    for (int n = k; n <= g.p; n++) {
+      const int j = n - k;
+      const int mlo = max(lo - j, -n), mhi = min(lo + j, n);
+      for (int m = mlo; m <= mhi; m++) {
+        C a = tab_get(Lp, n, m), b = tab_get(Ro, j, m - lo);
+        ax += a.x * b.x - a.y * b.y;
+        ay += a.x * b.y + a.y * b.x;
+      }
     }
+    const int bx = 2 * px + (o & 1), by = 2 * py + ((o >> 1) & 1), bz = 2 * pz + ((o >> 2) & 1);
+    const int64_t cell = bx + (int64_t)nl * (by + (int64_t)nl * bz);
+    double2 own = d.Psi[(g.cell_off[l] + cell) * g.P + ci];
+    C out;
+    out.x = ax + (T)own.x;
+    out.y = ay + (T)own.y;
+    Pe[(g.cell_off[l] + cell) * g.P + ci] = out;
   }
-  double2 own = d.Psi[(g.cell_off[l] + cell) * g.P + ci];
-  C out;
-  out.x = ax + (T)own.x;
-  out.y = ay + (T)own.y;
-  Pe[(g.cell_off[l] + cell) * g.P + ci] = out;
 }
 
 void fmm_downward(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
-  for (int l = 1; l <= g.L; l++) {
-    int64_t ncl = (int64_t)1 << (3 * (l - 1));
-    int64_t nt = (l == 1) ? 128 : ncl * g.P;
-    unsigned blocks = (unsigned)((nt + 127) / 128);
+  if (prec == 0) k_downward_root<double><<<1, 128, 0, s>>>(g, d);
+  else k_downward_root<float><<<1, 128, 0, s>>>(g, d);
+  for (int l = 2; l <= g.L; l++) {
+    unsigned npar = 1u << (3 * (l - 2));
     if (prec == 0)
-      k_downward<double><<<blocks, 128, 8 * g.P * sizeof(double2), s>>>(g, d, l);
+      k_downward<double><<<npar, 256, 9 * g.P * sizeof(double2), s>>>(g, d, l);
     else
-      k_downward<float><<<blocks, 128, 8 * g.P * sizeof(float2), s>>>(g, d, l);
+      k_downward<float><<<npar, 256, 9 * g.P * sizeof(float2), s>>>(g, d, l);
   }
 }
 

@@ -136,7 +136,7 @@ template <> struct NearField<float> {
     const float2 nx0 = make_float2(-x0, -x0), ny0 = make_float2(-y0, -y0), nz0 = make_float2(-z0, -z0);
     const float2 nx1 = make_float2(-x1, -x1), ny1 = make_float2(-y1, -y1), nz1 = make_float2(-z1, -z1);
     float2 c0 = a0, c1 = a1;
-#pragma unroll 2
+#pragma unroll 4
     for (int j = 0; j < np; j++) {
       float4 a = A[j], b = B[j];
       float2 sx = make_float2(a.x, a.y), sy = make_float2(a.z, a.w);
@@ -262,12 +262,19 @@ template <> __device__ __forceinline__ double l2p_point<double, double2>(const d
 // the leaf, whether the hopping charge sits in this leaf or in one of its six
 // face neighbours.  Sources are the charges of the 27 neighbouring leaves
 // (periodically wrapped images), staged in shared memory.
-struct PtRec {
-  uint32_t a;  // local site index (bits 0..15), hop k (16..18), old flag (bit 19)
-  int32_t u;   // user index of the hopping charge
-};
+// point record (32 bits): local site (bits 0-11), hop k (12-14), old-position
+// flag (15), owner leaf f (16-18: 0 = this leaf, 1..6 = face neighbour f-1),
+// slot j of the hopping charge in its owner leaf (19-31)
+#define PT_SITE(r) ((r) & 0xfffu)
+#define PT_K(r) (((r) >> 12) & 7u)
+#define PT_OLD(r) (((r) >> 15) & 1u)
+#define PT_F(r) (((r) >> 16) & 7u)
+#define PT_J(r) ((r) >> 19)
+__device__ __forceinline__ uint32_t pt_make(int site, int k, int old, int f, int j) {
+  return (uint32_t)site | ((uint32_t)k << 12) | ((uint32_t)old << 15) | ((uint32_t)f << 16) | ((uint32_t)j << 19);
+}
 
-#define PROP_THREADS 128
+#define PROP_THREADS 256
 
 template <typename T>
 __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, const Dev d, int pmax, int chunk) {
@@ -275,12 +282,13 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
   typedef typename vec4<T>::type V4;
   extern __shared__ __align__(32) unsigned char sm[];
   unsigned char* src = sm;
-  C* Lc = (C*)(sm + NearField<T>::bytes(chunk));
-  PtRec* pts = (PtRec*)(Lc + g.P);
+  C* Lc = (C*)(sm + NearField<T>::bytes(chunk));  // 8-byte aligned
+  int64_t* owner = (int64_t*)(Lc + g.P);            // [7] slot base of this leaf and its face neighbours
+  uint32_t* pts = (uint32_t*)(owner + 8);
   const int W = g.W, W3 = W * W * W;
   const int nbw = (W3 + 31) / 32;
-  uint32_t* bits = (uint32_t*)(pts + pmax);
-  int* ctr = (int*)(bits + nbw);  // [0] npts, [1..28] source prefix offsets
+  uint32_t* bits = pts + pmax;
+  int* ctr = (int*)(bits + nbw);  // [0] npts, [1..27] source prefix offsets
 
   const int tid = threadIdx.x;
   const int nL = g.nL, E = g.E;
@@ -294,7 +302,15 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
   const C* Pe = (const C*)d.Peff + (g.cell_off[g.L] + leaf) * g.P;
   for (int c = tid; c < g.P; c += blockDim.x) Lc[c] = Pe[c];
   for (int c = tid; c < nbw; c += blockDim.x) bits[c] = 0u;
-  if (tid == 0) ctr[0] = 0;
+  if (tid == 0) {
+    ctr[0] = 0;
+    owner[0] = leaf * g.cap;
+  }
+  if (tid >= 1 && tid <= KMC_NHOP) {
+    int f = tid - 1;
+    int mx = (lx + c_hop[f][0] + nL) % nL, my = (ly + c_hop[f][1] + nL) % nL, mz = (lz + c_hop[f][2] + nL) % nL;
+    owner[tid] = (mx + (int64_t)nL * (my + (int64_t)nL * mz)) * g.cap;
+  }
   __syncthreads();
 
   // occupancy bitmap of this leaf's sites
@@ -316,7 +332,7 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
     int gx = s % E, gy = (s / E) % E, gz = s / (E * E);
     int ls = (gx - gx0) + W * ((gy - gy0) + W * (gz - gz0));
     int slot = atomicAdd(&ctr[0], 1);
-    if (slot < pmax) pts[slot] = PtRec{(uint32_t)ls | (1u << 19), u};
+    if (slot < pmax) pts[slot] = pt_make(ls, 0, 1, 0, j);
     for (int k = 0; k < KMC_NHOP; k++) {
       int tx = gx + c_hop[k][0], ty = gy + c_hop[k][1], tz = gz + c_hop[k][2];
       tx = (tx + E) % E; ty = (ty + E) % E; tz = (tz + E) % E;
@@ -328,18 +344,17 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
         d.phi_new[6 * (int64_t)u + k] = __longlong_as_double(0x7ff8000000000000LL);
       } else {
         int sl = atomicAdd(&ctr[0], 1);
-        if (sl < pmax) pts[sl] = PtRec{(uint32_t)lt | ((uint32_t)k << 16), u};
+        if (sl < pmax) pts[sl] = pt_make(lt, k, 0, 0, j);
       }
     }
   }
   // hops entering from the six face neighbours
   for (int f = 0; f < KMC_NHOP; f++) {
-    int mx = (lx + c_hop[f][0] + nL) % nL, my = (ly + c_hop[f][1] + nL) % nL, mz = (lz + c_hop[f][2] + nL) % nL;
-    int64_t mu = mx + (int64_t)nL * (my + (int64_t)nL * mz);
+    int64_t mb = owner[1 + f];
     int kin = f ^ 1;  // direction from the neighbour back into this leaf
-    int cm = d.cnt[mu];
+    int cm = d.cnt[mb / g.cap];
     for (int j = tid; j < cm; j += blockDim.x) {
-      int32_t u = d.uid[mu * g.cap + j];
+      int32_t u = d.uid[mb + j];
       int s = d.site[u];
       int tx = s % E + c_hop[kin][0], ty = (s / E) % E + c_hop[kin][1], tz = s / (E * E) + c_hop[kin][2];
       tx = (tx + E) % E; ty = (ty + E) % E; tz = (tz + E) % E;
@@ -351,7 +366,7 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
         d.phi_new[6 * (int64_t)u + kin] = __longlong_as_double(0x7ff8000000000000LL);
       } else {
         int sl = atomicAdd(&ctr[0], 1);
-        if (sl < pmax) pts[sl] = PtRec{(uint32_t)lt | ((uint32_t)kin << 16), u};
+        if (sl < pmax) pts[sl] = pt_make(lt, kin, 0, 1 + f, j);
       }
     }
   }
@@ -377,27 +392,27 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
   }
 
   // ---- near-field pair sums, then L2P.  Points are processed in rounds of
-  // 2 * blockDim (two per thread, accumulators in registers); each round
-  // streams the sources: pass 0 = own leaf (self pair skipped by r2 > 0),
-  // passes 1.. = the 26 other leaves in chunks.
+  // 2 * blockDim (slot 0 for every thread, slot 1 only in warps that have
+  // one); each round streams the sources: pass 0 = own leaf (self pair
+  // skipped by r2 > 0), passes 1.. = the 26 other leaves in chunks.
   const int nsrc_other = ctr[27];
   const int npass = 1 + (nsrc_other + chunk - 1) / chunk;
   for (int rb = 0; rb < npts; rb += 2 * blockDim.x) {
     const int b0 = rb + tid, b1 = rb + tid + blockDim.x;
     T x0 = (T)1e18, y0 = (T)1e18, z0 = (T)1e18, x1 = (T)1e18, y1 = (T)1e18, z1 = (T)1e18;
     if (b0 < npts) {
-      int l0 = pts[b0].a & 0xffff;
+      int l0 = PT_SITE(pts[b0]);
       x0 = ((T)(gx0 + l0 % W) + (T)0.5) * h;
       y0 = ((T)(gy0 + (l0 / W) % W) + (T)0.5) * h;
       z0 = ((T)(gz0 + l0 / (W * W)) + (T)0.5) * h;
     }
     if (b1 < npts) {
-      int l1 = pts[b1].a & 0xffff;
+      int l1 = PT_SITE(pts[b1]);
       x1 = ((T)(gx0 + l1 % W) + (T)0.5) * h;
       y1 = ((T)(gy0 + (l1 / W) % W) + (T)0.5) * h;
       z1 = ((T)(gz0 + l1 / (W * W)) + (T)0.5) * h;
     }
-    // second point slot only where some lane of the warp has one
+    const bool one = __any_sync(0xffffffffu, b0 < npts);  // warp has work at all
     const bool two = __any_sync(0xffffffffu, b1 < npts);
     NearField<T> nf;
     nf.reset();
@@ -428,24 +443,25 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
       }
       if (tid == 0) NearField<T>::pad(src, chunk, ns);
       __syncthreads();
-      nf.run(src, chunk, ns, pass == 0, two, x0, y0, z0, x1, y1, z1);
+      if (one) nf.run(src, chunk, ns, pass == 0, two, x0, y0, z0, x1, y1, z1);
     }
     // L2P of the leaf local expansion and write-out
     for (int side = 0; side < 2; side++) {
       int b = side ? b1 : b0;
       if (b >= npts) continue;
-      PtRec r = pts[b];
-      int lt = r.a & 0xffff;
+      uint32_t r = pts[b];
+      int lt = PT_SITE(r);
       T x = ((T)(lt % W) + (T)0.5 - (T)(0.5 * W)) * h;
       T y = ((T)((lt / W) % W) + (T)0.5 - (T)(0.5 * W)) * h;
       T z = ((T)(lt / (W * W)) + (T)0.5 - (T)(0.5 * W)) * h;
       T v = nf.sum(side) + l2p_point<T, C>(Lc, g.p, x, y, z);
-      if (r.a & (1u << 19)) {
-        d.phi_old[r.u] = (double)v;
+      int32_t u = d.uid[owner[PT_F(r)] + PT_J(r)];
+      if (PT_OLD(r)) {
+        d.phi_old[u] = (double)v;
       } else {
-        int k = (r.a >> 16) & 7;
-        d.phi_new[6 * (int64_t)r.u + k] = (double)v;
-        d.mask[6 * (int64_t)r.u + k] = 1;
+        int k = PT_K(r);
+        d.phi_new[6 * (int64_t)u + k] = (double)v;
+        d.mask[6 * (int64_t)u + k] = 1;
       }
     }
   }
@@ -455,13 +471,13 @@ static size_t propose_smem(const Geo& g, int prec, int pmax, int chunk) {
   size_t ts = prec == 0 ? 8 : 4;
   int nbw = (g.W * g.W * g.W + 31) / 32;
   size_t srcb = prec == 0 ? (size_t)chunk * 32 : (size_t)(chunk / 2 + 1) * 32;
-  return srcb + 2 * ts * (size_t)g.P + 8 * (size_t)pmax + 4 * (size_t)nbw + 4 * 32;
+  return srcb + 2 * ts * (size_t)g.P + 4 * (size_t)pmax + 4 * (size_t)nbw + 4 * 32 + 8 * 8;
 }
 
 static void propose_shape(const Geo& g, int* pmax, int* chunk) {
   int W3 = g.W * g.W * g.W;
   *pmax = W3 + 6 * W3 + 6 * g.W * g.W;  // every own charge, its hops, every entering hop
-  int c = 1024 > g.cap ? 1024 : g.cap;
+  int c = 512 > g.cap ? 512 : g.cap;
   *chunk = (c + 1) & ~1;  // even: FP32 sources are staged in pairs
 }
 
@@ -770,10 +786,13 @@ __global__ void k_acc_multipole(const Geo g, const Dev d) {
   if (l > g.L) return;
   int nl = 1 << (l - 1);
   double wl = g.a / nl;
+  double2 row[2][KMC_MAXP + 1];
+  int64_t cell[2];
   for (int side = 0; side < 2; side++) {
     const double* x = side ? mv.rn : mv.r;
     double q = side ? mv.q : -mv.q;
     int cx = cell_coord(x[0], wl, nl), cy = cell_coord(x[1], wl, nl), cz = cell_coord(x[2], wl, nl);
+    cell[side] = cx + (int64_t)nl * (cy + (int64_t)nl * cz);
     double dx = x[0] - (cx + 0.5) * wl, dy = x[1] - (cy + 0.5) * wl, dz = x[2] - (cz + 0.5) * wl;
     double r2 = dx * dx + dy * dy + dz * dz;
     double2 mm = make_double2(1.0, 0.0);
@@ -781,24 +800,35 @@ __global__ void k_acc_multipole(const Geo g, const Dev d) {
       double sc = c_halfm_d[j];
       mm = make_double2(sc * (dx * mm.x - dy * mm.y), sc * (dx * mm.y + dy * mm.x));
     }
-    double2* out = d.Mt + (g.cell_off[l] + cx + (int64_t)nl * (cy + (int64_t)nl * cz)) * g.P;
     double2 a1 = mm, a2 = make_double2(0.0, 0.0);
-    double2 v = mm;
-    for (int n = m; n <= g.p; n++) {
-      if (n > m) {
-        double cc = c_inv_d[tri(n, m)];
-        double zz = (2 * n - 1) * dz;
-        v = make_double2((zz * a1.x - r2 * a2.x) * cc, (zz * a1.y - r2 * a2.y) * cc);
-        a2 = a1;
-        a1 = v;
-      }
-      out[tri(n, m)].x += q * v.x;
-      out[tri(n, m)].y += q * v.y;
-      if (l == 1) {
-        if (side == 0) d.dK[tri(n, m)] = make_double2(q * v.x, q * v.y);
-        else { d.dK[tri(n, m)].x += q * v.x; d.dK[tri(n, m)].y += q * v.y; }
-      }
+    row[side][m] = make_double2(q * mm.x, q * mm.y);
+    for (int n = m + 1; n <= g.p; n++) {
+      double cc = c_inv_d[tri(n, m)];
+      double zz = (2 * n - 1) * dz;
+      double2 v = make_double2((zz * a1.x - r2 * a2.x) * cc, (zz * a1.y - r2 * a2.y) * cc);
+      row[side][n] = make_double2(q * v.x, q * v.y);
+      a2 = a1;
+      a1 = v;
     }
+  }
+  if (l == 1)
+    for (int n = m; n <= g.p; n++)
+      d.dK[tri(n, m)] = make_double2(row[0][n].x + row[1][n].x, row[0][n].y + row[1][n].y);
+  if (cell[0] == cell[1]) {
+    for (int n = m; n <= g.p; n++) {
+      row[0][n].x += row[1][n].x;
+      row[0][n].y += row[1][n].y;
+    }
+  }
+  int nside = cell[0] == cell[1] ? 1 : 2;
+  for (int side = 0; side < nside; side++) {
+    double2* out = d.Mt + (g.cell_off[l] + cell[side]) * g.P;
+    for (int n = m; n <= g.p; n++) {
+      double2 v = out[tri(n, m)];
+      row[side][n].x += v.x;
+      row[side][n].y += v.y;
+    }
+    for (int n = m; n <= g.p; n++) out[tri(n, m)] = row[side][n];
   }
 }
 
@@ -937,7 +967,8 @@ __global__ void k_acc_fine(const Geo g, const Dev d, int lmin) {
   MoveRec mv = *d.move;
   if (!mv.valid) return;
   const int l = lmin + blockIdx.y;
-  int cand = blockIdx.x * blockDim.x + threadIdx.x;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int cand = t / (g.p + 1), m = t % (g.p + 1);
   if (cand >= 432) return;
   const int nl = 1 << (l - 1), np = nl >> 1;
   const double wl = g.a / nl;
@@ -958,7 +989,9 @@ __global__ void k_acc_fine(const Geo g, const Dev d, int lmin) {
       if (wdist(b[c] >> 1, Pold[c], np) > 1) in_old = false;
     if (in_old) return;
   }
-  double2* out = d.Psi + (g.cell_off[l] + b[0] + (int64_t)nl * (b[1] + (int64_t)nl * b[2])) * g.P;
+  double2 acc[KMC_MAXP + 1];
+  for (int n = 0; n <= g.p; n++) acc[n] = make_double2(0.0, 0.0);
+  bool any = false;
   for (int side = 0; side < 2; side++) {
     const double* x = side ? mv.rn : mv.r;
     double q = side ? mv.q : -mv.q;
@@ -966,12 +999,39 @@ __global__ void k_acc_fine(const Geo g, const Dev d, int lmin) {
     for (int c = 0; c < 3; c++) u0[c] = cell_coord(x[c], wl, nl);
     for (int nu = 0; nu < 27; nu++) {
       if (!image_in_il(u0, nl, nu, b)) continue;
+      any = true;
       int nv[3] = {nu % 3 - 1, (nu / 3) % 3 - 1, nu / 9 - 1};
       double dx = x[0] + g.a * nv[0] - (b[0] + 0.5) * wl, dy = x[1] + g.a * nv[1] - (b[1] + 0.5) * wl,
              dz = x[2] + g.a * nv[2] - (b[2] + 0.5) * wl;
-      p2l_table<true>(out, q, dx, dy, dz, g.p);
+      double r2 = dx * dx + dy * dy + dz * dz, inv = 1.0 / r2;
+      double2 mm = make_double2(1.0 / sqrt(r2), 0.0);
+      for (int j = 1; j <= m; j++) {
+        double sc = -(2.0 * j - 1.0) * inv;
+        mm = make_double2(sc * (dx * mm.x - dy * mm.y), sc * (dx * mm.y + dy * mm.x));
+      }
+      double2 a1 = mm, a2 = make_double2(0.0, 0.0);
+      acc[m].x += q * mm.x;
+      acc[m].y -= q * mm.y;
+      for (int n = m + 1; n <= g.p; n++) {
+        double zz = (2 * n - 1) * dz;
+        double c2 = (double)((n - 1) * (n - 1) - m * m);
+        double2 v = make_double2((zz * a1.x - c2 * a2.x) * inv, (zz * a1.y - c2 * a2.y) * inv);
+        acc[n].x += q * v.x;
+        acc[n].y -= q * v.y;
+        a2 = a1;
+        a1 = v;
+      }
     }
   }
+  if (!any) return;
+  double2* out = d.Psi + (g.cell_off[l] + b[0] + (int64_t)nl * (b[1] + (int64_t)nl * b[2])) * g.P;
+  // all loads first, then all stores (the row's coefficients are independent)
+  for (int n = m; n <= g.p; n++) {
+    double2 v = out[tri(n, m)];
+    acc[n].x += v.x;
+    acc[n].y += v.y;
+  }
+  for (int n = m; n <= g.p; n++) out[tri(n, m)] = acc[n];
 }
 
 // move the charge between leaf slots; dipole, energy and bookkeeping
@@ -1028,8 +1088,8 @@ void kmc_accept_apply(const Geo& g, const Dev& d, cudaStream_t s) {
     k_acc_coarse_reduce<<<(ncl * g.P + 127) / 128, 128, 0, s>>>(g, d, l, d.acc_scratch);
   }
   if (g.L >= 4) {
-    dim3 grid((432 + 31) / 32, g.L - 3);
-    k_acc_fine<<<grid, 32, 0, s>>>(g, d, 4);
+    dim3 grid((432 * (g.p + 1) + 63) / 64, g.L - 3);
+    k_acc_fine<<<grid, 64, 0, s>>>(g, d, 4);
   }
   k_acc_move<<<1, 1, 0, s>>>(g, d);
 }
