@@ -187,6 +187,32 @@ int kmc_fmm_leaf_index(kmc_handle h, int32_t* leaf);
 /* Current positions (n x 3) in user order. */
 int kmc_fmm_positions(kmc_handle h, double* positions);
 
+/*
+ * Allocation-free selection.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- code running while
+ * a CUDA graph is captured in global capture mode (where cudaMalloc is
+ * prohibited), code inside a framework whose memory pool owns the device, or
+ * host loops that must not stall on the synchronisation an allocation can
+ * cause.  It performs the selection of kmc_step (Q = sum r_j, event j with
+ * R_{j-1} < Q zeta <= R_j, dt = -ln(xi)/Q) without a handle and without
+ * allocating: its scratch is a file-scope device array of KMC_STATIC_MAX_N/256
+ * block sums plus 8 doubles (about 512 KB), held by every GPU that loads the
+ * library until the process exits.
+ *   rates:  6 n doubles in DEVICE memory of the current device (event order
+ *           j = 6 i + k), owned by the caller; 1 <= n <= KMC_STATIC_MAX_N,
+ *           larger n returns KMC_ERR_ARG.
+ *   zeta, xi in (0, 1]; event, dt, Q: host scalars (event = -1 if Q == 0).
+ *   stream: cudaStream_t (NULL = default stream); the call synchronises it.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the array,
+ * so calls whose GPU work overlaps (other streams, other host threads) race;
+ * serialise them.  Nothing in the array has to start at zero: each call
+ * writes every element it reads.
+ */
+#define KMC_STATIC_MAX_N 16777216
+int kmc_select_static(const double* rates, int64_t n, double zeta, double xi, int64_t* event, double* dt,
+                      double* Q, void* stream);
+
 /* Message of the last error on this handle (static string if h is NULL). */
 const char* kmc_last_error(kmc_handle h);
 

@@ -37,7 +37,7 @@ KMC_MEM_DEVICE = 1
 EXPORTS = [
     "kmc_opts_default", "kmc_fmm_init", "kmc_fmm_energy", "kmc_fmm_propose", "kmc_fmm_propose_lattice",
     "kmc_fmm_accept", "kmc_fmm_accept_event", "kmc_step", "kmc_run", "kmc_run_profiled", "kmc_fmm_recompute",
-    "kmc_fmm_leaf_index", "kmc_fmm_positions", "kmc_last_error", "kmc_fmm_destroy",
+    "kmc_fmm_leaf_index", "kmc_fmm_positions", "kmc_last_error", "kmc_fmm_destroy", "kmc_select_static",
 ]
 
 
@@ -88,6 +88,7 @@ def load_library(path: str | None = None):
             "kmc_fmm_positions": (I, [P, P]),
             "kmc_last_error": (ctypes.c_char_p, [P]),
             "kmc_fmm_destroy": (None, [P]),
+            "kmc_select_static": (I, [P, I64, D, D, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -303,3 +304,31 @@ def kmc_fmm_destroy(h: Handle) -> None:
     if h is not None and h.ptr is not None:
         load_library().kmc_fmm_destroy(h.ptr)
         h.ptr = None
+
+
+KMC_STATIC_MAX_N = 16777216
+
+
+def kmc_select_static(rates, n: int, zeta: float, xi: float, stream=None):
+    """Selection without a handle and without device allocation.
+
+    For callers that cannot allocate device memory (graph capture in global
+    mode, a framework-owned memory pool, loops that must not stall on an
+    allocation).  rates: CUDA tensor of 6 n doubles owned by the caller.
+    Returns (event, dt, Q).  Calls share one static scratch array, so calls
+    that overlap on the GPU must be serialised by the caller."""
+    import torch
+    lib = load_library()
+    if not (_is_torch(rates) and rates.is_cuda and rates.dtype == torch.float64 and rates.is_contiguous()):
+        raise KmcError(KMC_ERR_ARG, "rates must be a contiguous float64 CUDA tensor")
+    s = stream if stream is not None else torch.cuda.current_stream(rates.device)
+    sp = ctypes.c_void_p(int(getattr(s, "cuda_stream", s)))
+    ev = ctypes.c_int64()
+    dt = ctypes.c_double()
+    Q = ctypes.c_double()
+    with torch.cuda.device(rates.device):
+        code = lib.kmc_select_static(ctypes.c_void_p(rates.data_ptr()), int(n), float(zeta), float(xi),
+                                     ctypes.byref(ev), ctypes.byref(dt), ctypes.byref(Q), sp)
+    if code != KMC_OK:
+        raise KmcError(code, "kmc_select_static: invalid argument or CUDA error")
+    return ev.value, dt.value, Q.value

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkmcfmm.so")
-SOURCES = ["runtime.cu", "fmm_kernels.cu", "kmc_kernels.cu"]
+SOURCES = ["runtime.cu", "fmm_kernels.cu", "kmc_kernels.cu", "static_select.cu"]
 HEADERS = ["common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -25,6 +25,7 @@
 #define KMC_MAXL 10   // maximum number of levels
 #define KMC_MAXP 20   // maximum expansion degree
 #define KMC_NHOP 6    // lattice hop directions (+x,-x,+y,-y,+z,-z)
+#define KMC_FIN_PARTICLES 256  // particles per block sum of the rates
 
 __host__ __device__ __forceinline__ constexpr int tri(int n, int m) { return n * (n + 1) / 2 + m; }
 __host__ __device__ __forceinline__ constexpr int ncoef(int p) { return (p + 1) * (p + 2) / 2; }

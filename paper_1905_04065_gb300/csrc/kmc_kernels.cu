@@ -501,7 +501,7 @@ void kmc_propose_lattice(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
 // ------------------------------------------------------------------ dU, rates, block sums
 // thread per particle; FP64 assembly.  Block sums are sequential over the
 // block's threads so that the selection walk reproduces them exactly.
-#define FIN_THREADS 256
+#define FIN_THREADS KMC_FIN_PARTICLES
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
