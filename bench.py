@@ -50,27 +50,40 @@ def _dist():
 
 
 # --------------------------------------------------------------- algorithmic work
+def step_bytes(E: int, L: int, N: int, p: int) -> int:
+    """Lower bound of the device bytes one lattice step touches: FP64 rates and
+    FP32 dU for the 6N hops, the leaf-major FP32 coordinates (capacity W^3 per
+    leaf) and the FP32 leaf expansions."""
+    nL = 2 ** (L - 1)
+    ML, W = nL ** 3, E // nL
+    P = (p + 1) * (p + 2) // 2
+    return 6 * N * (8 + 4) + ML * W ** 3 * 16 + ML * P * 8
+
+
 def pair_count(E: int, L: int, sites: np.ndarray) -> dict:
-    """Evaluation points and near-field pairs of one propose launch, counted
-    from the configuration: per leaf, points = own charges + unmasked hops
-    landing in the leaf, sources = charges in the 27 neighbouring leaves."""
+    """Evaluation sites and near-field pairs of one propose launch, counted
+    from the configuration.  The potential is needed once per distinct site:
+    every occupied site (old positions) and every empty site that some charge
+    can hop to; per leaf, pairs = needed sites x charges in the 27
+    neighbouring leaves (the pair at distance 0 included in the count)."""
     nL = 2 ** (L - 1)
     W = E // nL
     xyz = workloads.site_xyz(E, sites)
     occ = np.zeros(E ** 3, dtype=bool)
     occ[sites] = True
-    leafc = xyz // W
-    leaf = leafc[:, 0] + nL * (leafc[:, 1] + nL * leafc[:, 2])
-    cnt = np.bincount(leaf, minlength=nL ** 3).reshape(nL, nL, nL)  # [z, y, x]
-    pts = np.bincount(leaf, minlength=nL ** 3).astype(np.int64)
+    needed = occ.copy()
     hops = 0
-    for k, (dx, dy, dz) in enumerate([(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]):
+    for (dx, dy, dz) in [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]:
         t = (xyz + np.array([dx, dy, dz])) % E
         ts = t[:, 0] + E * (t[:, 1] + E * t[:, 2])
         ok = ~occ[ts]
         hops += int(ok.sum())
-        tl = t[ok] // W
-        pts += np.bincount(tl[:, 0] + nL * (tl[:, 1] + nL * tl[:, 2]), minlength=nL ** 3)
+        needed[ts[ok]] = True
+    ns = np.nonzero(needed)[0]
+    nxyz = workloads.site_xyz(E, ns) // W
+    pts = np.bincount(nxyz[:, 0] + nL * (nxyz[:, 1] + nL * nxyz[:, 2]), minlength=nL ** 3).astype(np.int64)
+    leafc = xyz // W
+    cnt = np.bincount(leafc[:, 0] + nL * (leafc[:, 1] + nL * leafc[:, 2]), minlength=nL ** 3).reshape(nL, nL, nL)
     src = np.zeros_like(cnt)
     for oz in (-1, 0, 1):
         for oy in (-1, 0, 1):
@@ -363,6 +376,7 @@ def run_gpu(args):
     t_fma = fp32_ops / fma_peak
     roof = {"bound": "alu", "kernel": "k_propose_lattice<float>",
             "achieved": achieved / 1e9, "peak": mufu_peak / 1e9, "unit": "G pair-interactions/s (MUFU rsqrt)",
+            "work": "pairs = distinct evaluation sites x charges in the 27 neighbouring leaves",
             "frac": achieved / mufu_peak, "traffic": None,
             "peak_source": f"16 MUFU/clk/SM x {nsm} SMs x {sm_max:.0f} MHz ({src} max clock)",
             "pairs_per_launch": pairs, "points_per_launch": work["points"],
@@ -395,13 +409,75 @@ def run_gpu(args):
     return 0
 
 
+def run_batch(args):
+    """Batched replicas: independent lattice systems of uneven sizes (edges from
+    {32, 48, 64, 96, 128}, occupancy U[0.02, 0.15]) advanced together, one KMC
+    step of every replica per graph replay; L per replica from the autotuner."""
+    import torch
+    import paper_1905_04065_gb300 as k
+    from paper_1905_04065_gb300 import autotune
+
+    rank, world, local = _dist()
+    dev = local if world > 1 else 0
+    torch.cuda.set_device(dev)
+    B = workloads.BATCH
+    reps = workloads.batch_replicas(args.replicas)
+    p, kT = B["p"], B["kT"]
+    t0 = time.perf_counter()
+    handles, hops, levels = [], 0, []
+    for r in reps:
+        pos = workloads.site_positions(r["E"], r["sites"])
+        L = autotune.tune_levels(r["E"], pos, r["q"], p, "mixed", kT) if not args.no_tune else \
+            autotune.valid_levels(r["E"])[0]
+        levels.append(L)
+        handles.append(k.kmc_fmm_init(pos, r["q"], float(r["E"]), L, p, precision="mixed", lattice_edge=r["E"],
+                                      kT=kT, device=dev))
+        hops += pair_count(r["E"], L, r["sites"])["hops"]
+    torch.cuda.synchronize()
+    ws = sum(step_bytes(r["E"], L, r["N"], p) for r, L in zip(reps, levels))
+    setup_s = time.perf_counter() - t0
+    bat = k.kmc_batch_create(handles)
+    R = len(handles)
+    rng = np.random.default_rng(B["seed"] + 17)
+    u = 1.0 - rng.random((args.warmup + args.steps, R, 2))
+    k.kmc_batch_run(bat, u[: args.warmup])
+    # the replicas' working set (rates, expansions, charges) exceeds the 129 MB
+    # L2, so the K timed steps run as one call: the graph is replayed K times
+    clk = Clocks(dev)
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    clk.start(os.path.join(ROOT, "gpurun_out", f"clocks_batch_rank{rank}.csv"))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    k.kmc_batch_run(bat, u[args.warmup: args.warmup + args.steps])
+    torch.cuda.synchronize()
+    ms = [1e3 * (time.perf_counter() - t1) / args.steps] * args.steps
+    clocks = clk.stop()
+    tot = sum(ms)
+    line = {
+        "metric": "dU evals/sec and KMC steps/sec, 64 batched replicas", "value": hops * args.steps / (tot * 1e-3),
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32-mixed (f32 near field + L2P, f64 far field / dU / accept)", "data": "synthetic",
+        "config": {"workload": f"batch: {R} replicas, edges {sorted(set(r['E'] for r in reps))}, occupancy "
+                               f"U[0.02,0.15], {sum(r['N'] for r in reps)} charges in total, p={p}, kT={kT}",
+                   "levels": levels, "working_set_bytes": ws,
+                   "timing": "host wall clock around one kmc_batch_run of K steps (uniform staging and event "
+                             "read-back included); working set larger than L2, no flush"},
+        "replica_steps_per_s": R * args.steps / (tot * 1e-3), "setup_s": setup_s, "clocks": clocks,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="large", choices=["small", "medium", "large"])
+    ap.add_argument("--workload", default="large", choices=["small", "medium", "large", "blobs", "batch"])
+    ap.add_argument("--replicas", type=int, default=None)
+    ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -411,7 +487,11 @@ def main():
     if args.steps < 1 or args.warmup < 0:
         raise SystemExit("--steps >= 1 and --warmup >= 0 required")
     if args.impl == "reference":
+        if args.workload == "batch":
+            args.workload = "medium"
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_gpu(args)
 
 

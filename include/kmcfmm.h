@@ -195,8 +195,8 @@ int kmc_fmm_positions(kmc_handle h, double* positions);
  * host loops that must not stall on the synchronisation an allocation can
  * cause.  It performs the selection of kmc_step (Q = sum r_j, event j with
  * R_{j-1} < Q zeta <= R_j, dt = -ln(xi)/Q) without a handle and without
- * allocating: its scratch is a file-scope device array of KMC_STATIC_MAX_N/256
- * block sums plus 8 doubles (about 512 KB), held by every GPU that loads the
+ * allocating: its scratch is a file-scope device array of KMC_STATIC_MAX_N/128
+ * block sums plus 8 doubles (about 1 MB), held by every GPU that loads the
  * library until the process exits.
  *   rates:  6 n doubles in DEVICE memory of the current device (event order
  *           j = 6 i + k), owned by the caller; 1 <= n <= KMC_STATIC_MAX_N,
@@ -212,6 +212,22 @@ int kmc_fmm_positions(kmc_handle h, double* positions);
 #define KMC_STATIC_MAX_N 16777216
 int kmc_select_static(const double* rates, int64_t n, double zeta, double xi, int64_t* event, double* dt,
                       double* Q, void* stream);
+
+/*
+ * Replica batches (many independent systems advanced together, the ensemble
+ * parallelism of Sec. 5.4 on one GPU).  A batch holds `count` lattice-mode
+ * handles on one device (not owned; they must outlive the batch) and replays
+ * one KMC step of every member from a single CUDA graph whose branches are
+ * the members' steps.
+ *   kmc_batch_run: uniforms (HOST) steps x count x 2 values (zeta, xi) laid
+ *   out [step][member][2]; events (int64) and dts (HOST, steps x count,
+ *   [step][member], may be NULL).  Same results as kmc_run on each member.
+ */
+typedef struct kmc_batch* kmc_batch_handle;
+int kmc_batch_create(kmc_batch_handle* b, int count, const kmc_handle* handles);
+int kmc_batch_run(kmc_batch_handle b, int steps, const double* uniforms, int64_t* events, double* dts);
+const char* kmc_batch_last_error(kmc_batch_handle b);
+void kmc_batch_destroy(kmc_batch_handle b);
 
 /* Message of the last error on this handle (static string if h is NULL). */
 const char* kmc_last_error(kmc_handle h);

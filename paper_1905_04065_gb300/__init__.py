@@ -38,6 +38,7 @@ EXPORTS = [
     "kmc_opts_default", "kmc_fmm_init", "kmc_fmm_energy", "kmc_fmm_propose", "kmc_fmm_propose_lattice",
     "kmc_fmm_accept", "kmc_fmm_accept_event", "kmc_step", "kmc_run", "kmc_run_profiled", "kmc_fmm_recompute",
     "kmc_fmm_leaf_index", "kmc_fmm_positions", "kmc_last_error", "kmc_fmm_destroy", "kmc_select_static",
+    "kmc_batch_create", "kmc_batch_run", "kmc_batch_last_error", "kmc_batch_destroy",
 ]
 
 
@@ -89,6 +90,10 @@ def load_library(path: str | None = None):
             "kmc_last_error": (ctypes.c_char_p, [P]),
             "kmc_fmm_destroy": (None, [P]),
             "kmc_select_static": (I, [P, I64, D, D, P, P, P, P]),
+            "kmc_batch_create": (I, [P, I, P]),
+            "kmc_batch_run": (I, [P, I, P, P, P]),
+            "kmc_batch_last_error": (ctypes.c_char_p, [P]),
+            "kmc_batch_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -332,3 +337,57 @@ def kmc_select_static(rates, n: int, zeta: float, xi: float, stream=None):
     if code != KMC_OK:
         raise KmcError(code, "kmc_select_static: invalid argument or CUDA error")
     return ev.value, dt.value, Q.value
+
+
+class Batch:
+    """Several lattice-mode handles advanced together from one CUDA graph."""
+
+    def __init__(self, ptr, handles):
+        self.ptr = ptr
+        self.handles = list(handles)  # keep the members alive
+
+    def __del__(self):
+        try:
+            kmc_batch_destroy(self)
+        except Exception:
+            pass
+
+
+def kmc_batch_create(handles) -> Batch:
+    lib = load_library()
+    arr = (ctypes.c_void_p * len(handles))(*[h.ptr for h in handles])
+    ptr = ctypes.c_void_p()
+    code = lib.kmc_batch_create(ctypes.byref(ptr), len(handles), arr)
+    b = Batch(ptr, handles)
+    if code != KMC_OK:
+        msg = lib.kmc_batch_last_error(ptr)
+        kmc_batch_destroy(b)
+        raise KmcError(code, msg.decode() if msg else "")
+    return b
+
+
+def kmc_batch_run(b: Batch, uniforms):
+    """uniforms: [steps, members, 2]; returns (events, dts), each [steps, members]."""
+    lib = load_library()
+    u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64))
+    steps, R = int(u.shape[0]), len(b.handles)
+    assert u.shape == (steps, R, 2)
+    ev = np.empty((steps, R), dtype=np.int64)
+    dt = np.empty((steps, R), dtype=np.float64)
+    code = lib.kmc_batch_run(b.ptr, steps, u.ctypes.data_as(ctypes.c_void_p), ev.ctypes.data_as(ctypes.c_void_p),
+                             dt.ctypes.data_as(ctypes.c_void_p))
+    if code != KMC_OK:
+        msg = lib.kmc_batch_last_error(b.ptr)
+        raise KmcError(code, msg.decode() if msg else "")
+    return ev, dt
+
+
+def kmc_batch_last_error(b: Batch) -> str:
+    msg = load_library().kmc_batch_last_error(b.ptr if b is not None else None)
+    return msg.decode() if msg else ""
+
+
+def kmc_batch_destroy(b: Batch) -> None:
+    if b is not None and b.ptr is not None:
+        load_library().kmc_batch_destroy(b.ptr)
+        b.ptr = None

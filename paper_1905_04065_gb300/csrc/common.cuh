@@ -25,7 +25,14 @@
 #define KMC_MAXL 10   // maximum number of levels
 #define KMC_MAXP 20   // maximum expansion degree
 #define KMC_NHOP 6    // lattice hop directions (+x,-x,+y,-y,+z,-z)
-#define KMC_FIN_PARTICLES 256  // particles per block sum of the rates
+#define KMC_FIN_PARTICLES 128  // particles per block sum of the rates
+// Periodic images nu with |nu|_inf <= KMC_TOP are handled by the tree (the
+// level-2 interaction list covers the (2 KMC_TOP + 1)^3 block of domain copies);
+// the rest are the far field V_inf of the lattice operator.
+#define KMC_TOP 2
+#define KMC_TOP_SPAN (4 * KMC_TOP + 3)  // level-2 M2L offsets per axis: [-(2 KMC_TOP + 1), 2 KMC_TOP + 1]
+#define KMC_TOP_NOFF (KMC_TOP_SPAN * KMC_TOP_SPAN * KMC_TOP_SPAN)
+#define KMC_TOP_NIMG ((2 * KMC_TOP + 1) * (2 * KMC_TOP + 1) * (2 * KMC_TOP + 1))
 
 __host__ __device__ __forceinline__ constexpr int tri(int n, int m) { return n * (n + 1) / 2 + m; }
 __host__ __device__ __forceinline__ constexpr int ncoef(int p) { return (p + 1) * (p + 2) / 2; }
@@ -68,7 +75,16 @@ struct Geo {
   int64_t cell_off[KMC_MAXL + 2];  // first cell of level l in per-level arrays (l = 1..L)
   int64_t ncell_total;
   double kT;
+  double inv_a;           // 1 / a
+  int prec;               // 0 = FP64 form, 1 = mixed form
 };
+
+// cell coordinate of x on a level with n cells per side, floor(x n / a)
+// clamped to [0, n); the one rule used by binning, accept and evaluation
+__device__ __forceinline__ int cell_at(double x, int n, double inv_a) {
+  int c = (int)floor(x * ((double)n * inv_a));
+  return min(max(c, 0), n - 1);
+}
 
 struct MoveRec {
   int32_t valid;      // 1 if a move is to be applied
@@ -97,11 +113,21 @@ struct Dev {
   double2* Psi;       // per-level interaction-list local expansions; level 1 holds H
   void* Peff;         // downward-accumulated locals (T2), all levels
   double2* Itab;      // M2L irregular values [(L+1) * 343 * P2]
+  double2* Itab2;     // level-2 M2L irregular values [KMC_TOP_NOFF * P2]
   double2* Rch;       // child-offset regular harmonics [(L+1) * 8 * P]
   double2* S;         // lattice sums over the far images [P2]
   double* selfc;      // [KMC_NHOP] self-pair correction C(d) per hop direction
   double* dip;        // [3] dipole moment M
+  float* fdip;        // [3] (4 pi / 3V) M in FP32 for the mixed rate assembly
   double* U;          // [1] total energy
+  // FP32 copies used by the mixed form (NULL in the FP64 form)
+  float* q32;         // [n] charges
+  float* selfc32;     // [KMC_NHOP]
+  float2* Psi32;      // per-level locals, all levels
+  float2* Rch32;      // child-offset regular harmonics
+  float* phi_old32;   // [n]
+  float* phi_new32;   // [6n]
+  float* dU32;        // [6n]
   // per step
   double* phi_old;    // [n]
   double* phi_new;    // [6n]
@@ -113,7 +139,7 @@ struct Dev {
   double* dtq;        // [2] (dt, Q)
   MoveRec* move;      // [1]
   double2* dK;        // [P] level-1 multipole change of the accepted move
-  double2* acc_scratch;  // [64 * 54 * P] coarse-level P2L terms of the accepted move
+  double2* acc_scratch;  // coarse-level (2, 3) P2L terms of the accepted move
   int* err;           // [4] device error flags
   double* scratch;    // init-time scratch (lattice-sum terms)
   double* uni_small;  // [2] (zeta, xi) staged for a single kmc_step
@@ -145,6 +171,7 @@ void fmm_m2l(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_lattice_sums(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_far_field(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_self_and_dipole(const Geo& g, const Dev& d, cudaStream_t s);
+void fmm_prepare(const Geo& g, int prec);
 void fmm_downward(const Geo& g, const Dev& d, int prec, cudaStream_t s);
 void fmm_selfcorr_list(const Geo& g, const Dev& d, int64_t m, const double* dvec, double* out, cudaStream_t s);
 void fmm_drift1(const double* a, const double* b, int64_t count, double* out2, cudaStream_t s);
@@ -167,5 +194,9 @@ void kmc_assemble_general(const Geo& g, const Dev& d, int64_t m, const int32_t* 
                           const double* phi_old, double* dU, cudaStream_t s);
 void kmc_stage_general(const Geo& g, const Dev& d, int64_t m, const int32_t* part, const double* tin,
                        const uint8_t* min_, double* tout, double* old, double* dv, uint8_t* mout, cudaStream_t s);
+void kmc_widen(const float* src, double* dst, int64_t n, cudaStream_t s);
+void fmm_shadow_all(const Geo& g, const Dev& d, cudaStream_t s);
+int kmc_coarse_slots();
+void raise_dynamic_smem(const void* fn, size_t bytes);
 void kmc_energy_reduce(const Geo& g, const Dev& d, cudaStream_t s);
 void kmc_validate(const Geo& g, const Dev& d, cudaStream_t s);

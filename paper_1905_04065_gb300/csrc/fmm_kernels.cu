@@ -93,10 +93,7 @@ __device__ __forceinline__ double2 regular_mm(double x, double y, int m) {
 
 // ------------------------------------------------------------------ binning
 __device__ __forceinline__ int leaf_of(const Geo& g, double x, double y, double z) {
-  int cx = (int)floor(x / g.w), cy = (int)floor(y / g.w), cz = (int)floor(z / g.w);
-  cx = min(max(cx, 0), g.nL - 1);
-  cy = min(max(cy, 0), g.nL - 1);
-  cz = min(max(cz, 0), g.nL - 1);
+  int cx = cell_at(x, g.nL, g.inv_a), cy = cell_at(y, g.nL, g.inv_a), cz = cell_at(z, g.nL, g.inv_a);
   return cx + g.nL * (cy + g.nL * cz);
 }
 
@@ -193,7 +190,10 @@ __global__ void k_child_tables(const Geo g, const Dev d) {
   if (o >= 8 || l > g.L) return;
   double wc = g.a / (1 << (l - 1));
   double tx = ((o & 1) - 0.5) * wc, ty = (((o >> 1) & 1) - 0.5) * wc, tz = (((o >> 2) & 1) - 0.5) * wc;
-  regular_table(tx, ty, tz, g.p, d.Rch + ((int64_t)l * 8 + o) * g.P);
+  double2* out = d.Rch + ((int64_t)l * 8 + o) * g.P;
+  regular_table(tx, ty, tz, g.p, out);
+  if (d.Rch32)
+    for (int c = 0; c < g.P; c++) d.Rch32[((int64_t)l * 8 + o) * g.P + c] = make_float2((float)out[c].x, (float)out[c].y);
 }
 
 void fmm_child_tables(const Geo& g, const Dev& d, cudaStream_t s) { k_child_tables<<<g.L - 1, 32, 0, s>>>(g, d); }
@@ -252,9 +252,22 @@ __global__ void k_itab(const Geo g, const Dev d) {
   irregular_table(tx * wl, ty * wl, tz * wl, 2 * g.p, d.Itab + ((int64_t)l * 343 + v) * g.P2);
 }
 
+// level 2: offsets t in [-(2 KMC_TOP + 1), 2 KMC_TOP + 1]^3 (the level-2 cells of
+// the (2 KMC_TOP + 1)^3 block of domain copies seen from a level-2 cell)
+__global__ void k_itab2(const Geo g, const Dev d) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= KMC_TOP_NOFF) return;
+  const int h = (KMC_TOP_SPAN - 1) / 2;
+  int tx = v % KMC_TOP_SPAN - h, ty = (v / KMC_TOP_SPAN) % KMC_TOP_SPAN - h, tz = v / (KMC_TOP_SPAN * KMC_TOP_SPAN) - h;
+  if (abs(tx) <= 1 && abs(ty) <= 1 && abs(tz) <= 1) return;
+  double w2 = g.a / 2;
+  irregular_table(tx * w2, ty * w2, tz * w2, 2 * g.p, d.Itab2 + (int64_t)v * g.P2);
+}
+
 void fmm_itab(const Geo& g, const Dev& d, cudaStream_t s) {
   dim3 grid((343 + 63) / 64, g.L - 1);
   k_itab<<<grid, 64, 0, s>>>(g, d);
+  k_itab2<<<(KMC_TOP_NOFF + 63) / 64, 64, 0, s>>>(g, d);
 }
 
 // ------------------------------------------------------------------ M2L
@@ -307,23 +320,69 @@ __global__ void k_m2l(const Geo g, const Dev d, int l) {
   if (ci < g.P) d.Psi[(g.cell_off[l] + cell) * g.P + ci] = acc;
 }
 
+// level 2: every level-2 cell u of the (2 KMC_TOP + 1)^3 block of domain copies
+// (coordinates -2 KMC_TOP .. 2 KMC_TOP + 1 per axis) except the 27 nearest
+// of cell b; source (u mod 2), translation (u - b) w_2
+__global__ void k_m2l_top(const Geo g, const Dev d) {
+  extern __shared__ double2 shM[];
+  const int cell = blockIdx.x;
+  const int bx = cell & 1, by = (cell >> 1) & 1, bz = (cell >> 2) & 1;
+  const int ci = threadIdx.x;
+  int n = 0, m = 0;
+  if (ci < g.P) {
+    while (tri(n + 1, 0) <= ci) n++;
+    m = ci - tri(n, 0);
+  }
+  const int lo = -2 * KMC_TOP, hi = 2 * KMC_TOP + 1, h = (KMC_TOP_SPAN - 1) / 2;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int uz = lo; uz <= hi; uz++)
+    for (int uy = lo; uy <= hi; uy++)
+      for (int ux = lo; ux <= hi; ux++) {
+        const int tx = ux - bx, ty = uy - by, tz = uz - bz;
+        if (abs(tx) <= 1 && abs(ty) <= 1 && abs(tz) <= 1) continue;
+        const int src = (ux & 1) + 2 * ((uy & 1) + 2 * (uz & 1));
+        __syncthreads();
+        const double2* Ms = d.Mt + (g.cell_off[2] + src) * g.P;
+        for (int k = threadIdx.x; k < g.P; k += blockDim.x) shM[k] = Ms[k];
+        __syncthreads();
+        if (ci < g.P) {
+          const int v = (tx + h) + KMC_TOP_SPAN * ((ty + h) + KMC_TOP_SPAN * (tz + h));
+          const double2* It = d.Itab2 + (int64_t)v * g.P2;
+          for (int k = 0; k <= g.p; k++) {
+            double2 s = make_double2(0.0, 0.0);
+            for (int ll = -k; ll <= k; ll++) {
+              double2 a = tab_get(shM, k, ll);
+              double2 b = tab_get(It, n + k, m + ll);
+              s.x += a.x * b.x + a.y * b.y;
+              s.y += a.y * b.x - a.x * b.y;
+            }
+            if (k & 1) { acc.x -= s.x; acc.y -= s.y; }
+            else { acc.x += s.x; acc.y += s.y; }
+          }
+        }
+      }
+  if (ci < g.P) d.Psi[(g.cell_off[2] + cell) * g.P + ci] = acc;
+}
+
 void fmm_m2l(const Geo& g, const Dev& d, cudaStream_t s) {
   int bs = g.P <= 128 ? 128 : 256;
-  for (int l = 2; l <= g.L; l++) {
+  k_m2l_top<<<8, bs, g.P * sizeof(double2), s>>>(g, d);
+  for (int l = 3; l <= g.L; l++) {
     int64_t ncl = (int64_t)1 << (3 * (l - 1));
     k_m2l<<<(unsigned)ncl, bs, g.P * sizeof(double2), s>>>(g, d, l);
   }
 }
 
 // ------------------------------------------------------------------ lattice sums
-// S_j^mu = sum over far images nu (|nu|_inf >= 2) of I_j^mu(a nu), evaluated by
+// S_j^mu = sum over far images nu (|nu|_inf > KMC_TOP) of I_j^mu(a nu), evaluated by
 // Ewald splitting of I_j^mu = (j-mu)!(j+mu)! R_j^mu(x)/|x|^{2j+1}:
 //   sum_{nu != 0} R(a nu)/|a nu|^{2j+1}
 //     = sum_{nu != 0} R(a nu) Q(j+1/2, beta^2 |a nu|^2) / |a nu|^{2j+1}
 //     + (-i)^j pi^{j-1/2} / (a^3 Gamma(j+1/2)) sum_{k = m/a != 0} R(k) exp(-pi^2 k^2 / beta^2) / k^2
 // (Poisson summation of the harmonic Gaussian; Q, P = regularised upper,
-// lower incomplete gamma).  The 26 nearest images are removed by dropping
-// their real-space terms and subtracting their smooth parts R P(..)/|x|^{2j+1}.
+// lower incomplete gamma).  The images of the near block (|nu|_inf <= KMC_TOP)
+// are removed by dropping their real-space terms and subtracting their smooth
+// parts R P(..)/|x|^{2j+1}.
 // Degrees j <= 3 vanish in cubic summation order (j = 0 multiplies the zero
 // net charge; j = 1, 2, 3 vanish by cubic symmetry).
 #define LS_NR 6
@@ -353,7 +412,7 @@ __global__ void k_lattice_terms(const Geo g, double2* terms, int nvec) {
     double rp = 1.0 / r;                                           // 1/r^{2j+1}
     for (int j = 0; j <= p2; j++) {
       double wgt;
-      if (ninf >= 2) {
+      if (ninf > KMC_TOP) {
         wgt = qj;  // far image: real-space part
       } else {
         // near image: minus the smooth part P(j+1/2, X) by its positive series
@@ -486,18 +545,21 @@ __global__ void k_dipole(const Geo g, const Dev d) {
       for (int c = 0; c < 3; c++) sh[c][threadIdx.x] += sh[c][threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x < 3) d.dip[threadIdx.x] = sh[threadIdx.x][0];
+  if (threadIdx.x < 3) {
+    d.dip[threadIdx.x] = sh[threadIdx.x][0];
+    d.fdip[threadIdx.x] = (float)(4.0 * M_PI / (3.0 * g.a * g.a * g.a) * sh[threadIdx.x][0]);
+  }
 }
 
 // C(d) = sum_{nu in V} 1/|d - a nu| - sum_{nu in V, nu != 0} 1/|a nu| + g(d) - g(0) + 2 pi |d|^2 / (3V)
-// with V = {-1,0,1}^3 and g(d) = Re sum conj(S_n^m) R_n^m(d) (n <= p): the
+// with V the near block |nu|_inf <= KMC_TOP and g(d) = Re sum conj(S_n^m) R_n^m(d) (n <= p): the
 // moving charge's interaction with its own images, equal to psi(d) - psi_reg(0)
 // of the tinfoil pair potential.
 __device__ double self_corr_dev(const Geo& g, const double2* S, double dx, double dy, double dz) {
   double s = 0.0;
-  for (int a = -1; a <= 1; a++)
-    for (int b = -1; b <= 1; b++)
-      for (int c = -1; c <= 1; c++) {
+  for (int a = -KMC_TOP; a <= KMC_TOP; a++)
+    for (int b = -KMC_TOP; b <= KMC_TOP; b++)
+      for (int c = -KMC_TOP; c <= KMC_TOP; c++) {
         double x = dx - g.a * a, y = dy - g.a * b, z = dz - g.a * c;
         s += 1.0 / sqrt(x * x + y * y + z * z);
         if (a || b || c) s -= 1.0 / (g.a * sqrt((double)(a * a + b * b + c * c)));
@@ -540,7 +602,9 @@ __global__ void k_selfcorr(const Geo g, const Dev d) {
   double dx = 0, dy = 0, dz = 0;
   double sgn = (k & 1) ? -h : h;
   if (k < 2) dx = sgn; else if (k < 4) dy = sgn; else dz = sgn;
-  d.selfc[k] = self_corr_dev(g, d.S, dx, dy, dz);
+  double c = self_corr_dev(g, d.S, dx, dy, dz);
+  d.selfc[k] = c;
+  if (d.selfc32) d.selfc32[k] = (float)c;
 }
 
 void fmm_self_and_dipole(const Geo& g, const Dev& d, cudaStream_t s) {
@@ -559,6 +623,17 @@ void fmm_selfcorr_list(const Geo& g, const Dev& d, int64_t m, const double* dvec
   k_selfcorr_list<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(g, d.S, m, dvec, out);
 }
 
+// FP32 shadow of every per-level local expansion (after a full FMM)
+__global__ void k_shadow_all(const double2* a, float2* b, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
+void fmm_shadow_all(const Geo& g, const Dev& d, cudaStream_t s) {
+  if (!d.Psi32) return;
+  k_shadow_all<<<1024, 256, 0, s>>>(d.Psi, d.Psi32, g.ncell_total * g.P);
+}
+
 // ------------------------------------------------------------------ downward pass
 // Peff_1 = H; Peff_l[b] = L2L(Peff_{l-1}[parent] -> c_b) + Psi_l[b]   (precision T)
 // One CTA per parent cell computes all 8 children: the parent expansion and
@@ -572,66 +647,111 @@ void fmm_upload_nm() {
   cudaMemcpyToSymbol(f_nm, nm, sizeof(nm));
 }
 
+// the level's own per-level expansion in precision T (FP32 shadow in the mixed form)
+template <typename T> __device__ __forceinline__ typename cplx<T>::type own_coef(const Dev& d, int64_t idx);
+template <> __device__ __forceinline__ float2 own_coef<float>(const Dev& d, int64_t idx) { return d.Psi32[idx]; }
+template <> __device__ __forceinline__ double2 own_coef<double>(const Dev& d, int64_t idx) { return d.Psi[idx]; }
+template <typename T> __device__ __forceinline__ typename cplx<T>::type child_coef(const Dev& d, int64_t idx);
+template <> __device__ __forceinline__ float2 child_coef<float>(const Dev& d, int64_t idx) { return d.Rch32[idx]; }
+template <> __device__ __forceinline__ double2 child_coef<double>(const Dev& d, int64_t idx) { return d.Rch[idx]; }
+
 template <typename T>
 __global__ void k_downward_root(const Geo g, const Dev d) {
   typedef typename cplx<T>::type C;
   C* Pe = (C*)d.Peff;
-  for (int c = threadIdx.x; c < g.P; c += blockDim.x) {
-    double2 v = d.Psi[g.cell_off[1] * g.P + c];
-    Pe[g.cell_off[1] * g.P + c] = cmk<C>(v.x, v.y);
-  }
+  for (int c = threadIdx.x; c < g.P; c += blockDim.x) Pe[g.cell_off[1] * g.P + c] = own_coef<T>(d, g.cell_off[1] * g.P + c);
 }
 
+// CTA of DW_PAR parent cells (32 children).  Warp w computes output
+// coefficients ci = w, w + 8, ... (ascending degree, so the cost per task
+// falls and round-robin balances the warps); lane c is child c, so the loop
+// bounds of a task are the same in every lane.  Outputs are staged in shared
+// memory and written cell-major (coalesced) with the level's own Psi added.
+#define DW_PAR 4
 template <typename T>
 __global__ void __launch_bounds__(256) k_downward(const Geo g, const Dev d, int l) {
   typedef typename cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char shraw[];
-  C* R = (C*)shraw;     // 8 * P child-offset regular tables
-  C* Lp = R + 8 * g.P;  // parent expansion
+  C* R = (C*)shraw;             // 8 * P child-offset regular tables
+  C* Lp = R + 8 * g.P;          // DW_PAR parent expansions
+  C* Out = Lp + DW_PAR * g.P;   // 8 * DW_PAR child outputs
   C* Pe = (C*)d.Peff;
   const int nl = 1 << (l - 1), np = nl / 2;
-  const int64_t par = blockIdx.x;
-  const int px = (int)(par % np), py = (int)((par / np) % np), pz = (int)(par / ((int64_t)np * np));
-  for (int c = threadIdx.x; c < 8 * g.P; c += blockDim.x) {
-    double2 v = d.Rch[(int64_t)l * 8 * g.P + c];
-    R[c] = cmk<C>(v.x, v.y);
+  const int64_t npar = (int64_t)np * np * np;
+  const int64_t par0 = (int64_t)blockIdx.x * DW_PAR;
+  for (int c = threadIdx.x; c < 8 * g.P; c += blockDim.x) R[c] = child_coef<T>(d, (int64_t)l * 8 * g.P + c);
+  for (int c = threadIdx.x; c < DW_PAR * g.P; c += blockDim.x) {
+    int gp = c / g.P;
+    Lp[c] = (par0 + gp < npar) ? Pe[(g.cell_off[l - 1] + par0 + gp) * g.P + (c - gp * g.P)] : cmk<C>(0.0, 0.0);
   }
-  for (int c = threadIdx.x; c < g.P; c += blockDim.x) Lp[c] = Pe[(g.cell_off[l - 1] + par) * g.P + c];
   __syncthreads();
-  for (int t = threadIdx.x; t < 8 * g.P; t += blockDim.x) {
-    const int o = t / g.P, ci = t - o * g.P;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int gp = lane >> 3, o = lane & 7;
+  const C* L = Lp + gp * g.P;
+  const C* Ro = R + o * g.P;
+  for (int ci = warp; ci < g.P; ci += nwarp) {
     const short2 km = f_nm[ci];
     const int k = km.x, lo = km.y;
-    const C* Ro = R + o * g.P;
     T ax = 0, ay = 0;
     for (int n = k; n <= g.p; n++) {
       const int j = n - k;
       const int mlo = max(lo - j, -n), mhi = min(lo + j, n);
       for (int m = mlo; m <= mhi; m++) {
-        C a = tab_get(Lp, n, m), b = tab_get(Ro, j, m - lo);
+        C a = tab_get(L, n, m), b = tab_get(Ro, j, m - lo);
         ax += a.x * b.x - a.y * b.y;
         ay += a.x * b.y + a.y * b.x;
       }
     }
-    const int bx = 2 * px + (o & 1), by = 2 * py + ((o >> 1) & 1), bz = 2 * pz + ((o >> 2) & 1);
-    const int64_t cell = bx + (int64_t)nl * (by + (int64_t)nl * bz);
-    double2 own = d.Psi[(g.cell_off[l] + cell) * g.P + ci];
-    C out;
-    out.x = ax + (T)own.x;
-    out.y = ay + (T)own.y;
-    Pe[(g.cell_off[l] + cell) * g.P + ci] = out;
+    C v;
+    v.x = ax;
+    v.y = ay;
+    Out[lane * g.P + ci] = v;
   }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 8 * DW_PAR * g.P; idx += blockDim.x) {
+    const int c = idx / g.P, ci = idx - c * g.P;
+    const int64_t par = par0 + (c >> 3);
+    if (par >= npar) continue;
+    const int oc = c & 7;
+    const int px = (int)(par % np), py = (int)((par / np) % np), pz = (int)(par / ((int64_t)np * np));
+    const int bx = 2 * px + (oc & 1), by = 2 * py + ((oc >> 1) & 1), bz = 2 * pz + ((oc >> 2) & 1);
+    const int64_t cell = bx + (int64_t)nl * (by + (int64_t)nl * bz);
+    const C own = own_coef<T>(d, (g.cell_off[l] + cell) * g.P + ci);
+    C v = Out[idx];
+    v.x += own.x;
+    v.y += own.y;
+    Pe[(g.cell_off[l] + cell) * g.P + ci] = v;
+  }
+}
+
+static size_t downward_smem(const Geo& g, int prec) {
+  return (size_t)(8 + DW_PAR + 8 * DW_PAR) * g.P * (prec == 0 ? sizeof(double2) : sizeof(float2));
+}
+
+void fmm_prepare(const Geo& g, int prec) {
+  // load every per-step kernel now: with lazy module loading a first launch
+  // inside a stream capture would invalidate the capture
+  cudaFuncAttributes fa;
+  cudaFuncGetAttributes(&fa, k_downward_root<double>);
+  cudaFuncGetAttributes(&fa, k_downward_root<float>);
+  cudaFuncGetAttributes(&fa, k_downward<double>);
+  cudaFuncGetAttributes(&fa, k_downward<float>);
+  size_t sm = downward_smem(g, prec);
+  if (prec == 0) raise_dynamic_smem((const void*)k_downward<double>, sm);
+  else raise_dynamic_smem((const void*)k_downward<float>, sm);
 }
 
 void fmm_downward(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
   if (prec == 0) k_downward_root<double><<<1, 128, 0, s>>>(g, d);
   else k_downward_root<float><<<1, 128, 0, s>>>(g, d);
+  size_t sm = downward_smem(g, prec);
   for (int l = 2; l <= g.L; l++) {
     unsigned npar = 1u << (3 * (l - 2));
+    unsigned blocks = (npar + DW_PAR - 1) / DW_PAR;
     if (prec == 0)
-      k_downward<double><<<npar, 256, 9 * g.P * sizeof(double2), s>>>(g, d, l);
+      k_downward<double><<<blocks, 256, sm, s>>>(g, d, l);
     else
-      k_downward<float><<<npar, 256, 9 * g.P * sizeof(float2), s>>>(g, d, l);
+      k_downward<float><<<blocks, 256, sm, s>>>(g, d, l);
   }
 }
 

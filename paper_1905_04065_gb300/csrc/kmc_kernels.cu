@@ -11,8 +11,8 @@
 // direct sum over the 27 neighbouring leaves, Fig. "fmm_point_eval"),
 // Phi_self omits the singular own term, M is the cell dipole, and
 // C(d) = psi(d) - psi_reg(0) is the moving charge's interaction with its own
-// images (the 19.104/a self-image term of Eq. (proposed_energy_sr) and its
-// far-field part).  The M.d term and the |d|^2 part of C together are the
+// images (the self-image term of Eq. (proposed_energy_sr), here summed over
+// the 5x5x5 block of domain copies the tree covers, and its far-field part).  The M.d term and the |d|^2 part of C together are the
 // change of the surface term that the dipole correction of Sec. 2.2.2 removes.
 #include <math.h>
 #include <stdio.h>
@@ -179,6 +179,90 @@ template <> struct NearField<float> {
       else run_<false, false>(sm, chunk, ns, x0, y0, z0, x1, y1, z1);
     }
   }
+  // sources [0, nguard) may sit on a target (skip r2 = 0); the rest never do
+  __device__ __forceinline__ void run2(const unsigned char* sm, int chunk, int ns, int nguard, bool two, float x0,
+                                       float y0, float z0, float x1, float y1, float z1) {
+    const int gp = (nguard + 1) >> 1, np = (ns + 1) >> 1;
+    const float4* A = (const float4*)sm;
+    const float4* B = (const float4*)(sm + (size_t)(chunk / 2 + 1) * 16);
+    if (gp > 0) {
+      if (two) run_range<true, true>(A, B, 0, gp, x0, y0, z0, x1, y1, z1);
+      else run_range<true, false>(A, B, 0, gp, x0, y0, z0, x1, y1, z1);
+    }
+    if (np > gp) {
+      if (two) run_range<false, true>(A, B, gp, np, x0, y0, z0, x1, y1, z1);
+      else run_range<false, false>(A, B, gp, np, x0, y0, z0, x1, y1, z1);
+    }
+  }
+  template <bool GUARD, bool TWO>
+  __device__ __forceinline__ void run_range(const float4* A, const float4* B, int j0, int j1, float x0, float y0,
+                                            float z0, float x1, float y1, float z1) {
+    const float2 nx0 = make_float2(-x0, -x0), ny0 = make_float2(-y0, -y0), nz0 = make_float2(-z0, -z0);
+    const float2 nx1 = make_float2(-x1, -x1), ny1 = make_float2(-y1, -y1), nz1 = make_float2(-z1, -z1);
+    float2 c0 = a0, c1 = a1, e0 = make_float2(0.f, 0.f), e1 = make_float2(0.f, 0.f);
+    int j = j0;
+    for (; j + 1 < j1; j += 2) {  // two source pairs per iteration, separate accumulators
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        float4 a = A[j + u], b = B[j + u];
+        float2 sx = make_float2(a.x, a.y), sy = make_float2(a.z, a.w);
+        float2 sz = make_float2(b.x, b.y), sq = make_float2(b.z, b.w);
+        float2 dx = __fadd2_rn(sx, nx0), dy = __fadd2_rn(sy, ny0), dz = __fadd2_rn(sz, nz0);
+        float2 r2 = __fmul2_rn(dx, dx);
+        r2 = __ffma2_rn(dy, dy, r2);
+        r2 = __ffma2_rn(dz, dz, r2);
+        float2 iv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+        if (GUARD) {
+          iv.x = r2.x > 0.f ? iv.x : 0.f;
+          iv.y = r2.y > 0.f ? iv.y : 0.f;
+        }
+        if (u == 0) c0 = __ffma2_rn(sq, iv, c0);
+        else e0 = __ffma2_rn(sq, iv, e0);
+        if (TWO) {
+          float2 dx1 = __fadd2_rn(sx, nx1), dy1 = __fadd2_rn(sy, ny1), dz1 = __fadd2_rn(sz, nz1);
+          float2 q2 = __fmul2_rn(dx1, dx1);
+          q2 = __ffma2_rn(dy1, dy1, q2);
+          q2 = __ffma2_rn(dz1, dz1, q2);
+          float2 iw = make_float2(rsqrt_mufu(q2.x), rsqrt_mufu(q2.y));
+          if (GUARD) {
+            iw.x = q2.x > 0.f ? iw.x : 0.f;
+            iw.y = q2.y > 0.f ? iw.y : 0.f;
+          }
+          if (u == 0) c1 = __ffma2_rn(sq, iw, c1);
+          else e1 = __ffma2_rn(sq, iw, e1);
+        }
+      }
+    }
+    for (; j < j1; j++) {
+      float4 a = A[j], b = B[j];
+      float2 sx = make_float2(a.x, a.y), sy = make_float2(a.z, a.w);
+      float2 sz = make_float2(b.x, b.y), sq = make_float2(b.z, b.w);
+      float2 dx = __fadd2_rn(sx, nx0), dy = __fadd2_rn(sy, ny0), dz = __fadd2_rn(sz, nz0);
+      float2 r2 = __fmul2_rn(dx, dx);
+      r2 = __ffma2_rn(dy, dy, r2);
+      r2 = __ffma2_rn(dz, dz, r2);
+      float2 iv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+      if (GUARD) {
+        iv.x = r2.x > 0.f ? iv.x : 0.f;
+        iv.y = r2.y > 0.f ? iv.y : 0.f;
+      }
+      c0 = __ffma2_rn(sq, iv, c0);
+      if (TWO) {
+        float2 dx1 = __fadd2_rn(sx, nx1), dy1 = __fadd2_rn(sy, ny1), dz1 = __fadd2_rn(sz, nz1);
+        float2 q2 = __fmul2_rn(dx1, dx1);
+        q2 = __ffma2_rn(dy1, dy1, q2);
+        q2 = __ffma2_rn(dz1, dz1, q2);
+        float2 iw = make_float2(rsqrt_mufu(q2.x), rsqrt_mufu(q2.y));
+        if (GUARD) {
+          iw.x = q2.x > 0.f ? iw.x : 0.f;
+          iw.y = q2.y > 0.f ? iw.y : 0.f;
+        }
+        c1 = __ffma2_rn(sq, iw, c1);
+      }
+    }
+    a0 = __fadd2_rn(c0, e0);
+    a1 = __fadd2_rn(c1, e1);
+  }
   __device__ __forceinline__ float sum(int side) const { return side ? a1.x + a1.y : a0.x + a0.y; }
 };
 
@@ -196,6 +280,25 @@ template <> struct NearField<double> {
     double s0 = a0, s1 = a1;
     for (int j = 0; j < ns; j++) {
       double4_32a v = src[j];
+      double dx0 = v.x - x0, dy0 = v.y - y0, dz0 = v.z - z0;
+      double dx1 = v.x - x1, dy1 = v.y - y1, dz1 = v.z - z1;
+      double q0 = dx0 * dx0 + dy0 * dy0 + dz0 * dz0;
+      double q1 = dx1 * dx1 + dy1 * dy1 + dz1 * dz1;
+      double i0 = (!guard || q0 > 0.0) ? rsqrt(q0) : 0.0;
+      double i1 = (!guard || q1 > 0.0) ? rsqrt(q1) : 0.0;
+      s0 += v.w * i0;
+      if (two) s1 += v.w * i1;
+    }
+    a0 = s0;
+    a1 = s1;
+  }
+  __device__ __forceinline__ void run2(const unsigned char* sm, int chunk, int ns, int nguard, bool two, double x0,
+                                       double y0, double z0, double x1, double y1, double z1) {
+    const double4_32a* src = (const double4_32a*)sm;
+    double s0 = a0, s1 = a1;
+    for (int j = 0; j < ns; j++) {
+      double4_32a v = src[j];
+      const bool guard = j < nguard;
       double dx0 = v.x - x0, dy0 = v.y - y0, dz0 = v.z - z0;
       double dx1 = v.x - x1, dy1 = v.y - y1, dz1 = v.z - z1;
       double q0 = dx0 * dx0 + dy0 * dy0 + dz0 * dz0;
@@ -262,33 +365,39 @@ template <> __device__ __forceinline__ double l2p_point<double, double2>(const d
 // the leaf, whether the hopping charge sits in this leaf or in one of its six
 // face neighbours.  Sources are the charges of the 27 neighbouring leaves
 // (periodically wrapped images), staged in shared memory.
-// point record (32 bits): local site (bits 0-11), hop k (12-14), old-position
-// flag (15), owner leaf f (16-18: 0 = this leaf, 1..6 = face neighbour f-1),
-// slot j of the hopping charge in its owner leaf (19-31)
-#define PT_SITE(r) ((r) & 0xfffu)
-#define PT_K(r) (((r) >> 12) & 7u)
-#define PT_OLD(r) (((r) >> 15) & 1u)
-#define PT_F(r) (((r) >> 16) & 7u)
-#define PT_J(r) ((r) >> 19)
-__device__ __forceinline__ uint32_t pt_make(int site, int k, int old, int f, int j) {
-  return (uint32_t)site | ((uint32_t)k << 12) | ((uint32_t)old << 15) | ((uint32_t)f << 16) | ((uint32_t)j << 19);
-}
-
 #define PROP_THREADS 256
 
+template <typename T> __device__ __forceinline__ T qnan();
+template <> __device__ __forceinline__ float qnan<float>() { return __int_as_float(0x7fc00000); }
+template <> __device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
+
+// Evaluation is per distinct site of the leaf: the potential at a site is
+// needed once even when several charges propose to hop there, and at an own
+// charge's site it is that charge's old-position potential (the pair at
+// distance 0 is skipped).  Phases: (1) occupancy bits; (2) needed-site bits,
+// masked hops written; (3) compact site list; (4) near-field sums + L2P per
+// site, one site per thread per round; (5) write-out by re-enumerating the
+// same hops.  Potentials are written in precision T (FP32 arrays in the mixed
+// form, FP64 arrays in the FP64 form).
 template <typename T>
 __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, const Dev d, int pmax, int chunk) {
   typedef typename cplx<T>::type C;
   typedef typename vec4<T>::type V4;
   extern __shared__ __align__(32) unsigned char sm[];
+  (void)pmax;
+  const int W = g.W, W3 = W * W * W;
+  const int nbw = (W3 + 31) / 32;
   unsigned char* src = sm;
   C* Lc = (C*)(sm + NearField<T>::bytes(chunk));  // 8-byte aligned
   int64_t* owner = (int64_t*)(Lc + g.P);            // [7] slot base of this leaf and its face neighbours
-  uint32_t* pts = (uint32_t*)(owner + 8);
-  const int W = g.W, W3 = W * W * W;
-  const int nbw = (W3 + 31) / 32;
-  uint32_t* bits = pts + pmax;
-  int* ctr = (int*)(bits + nbw);  // [0] npts, [1..27] source prefix offsets
+  T* phis = (T*)(owner + 8);                        // [W3] potential per local site
+  uint32_t* bits = (uint32_t*)(phis + W3);          // [nbw] occupied sites
+  uint32_t* need = bits + nbw;                      // [nbw] sites where a potential is needed
+  int* woff = (int*)(need + nbw);                   // [nbw + 1] prefix of needed sites per word
+  uint16_t* sites = (uint16_t*)(woff + nbw + 1);    // [W3] needed local sites, compacted
+  int* ctr = (int*)(sites + ((W3 + 1) & ~1));       // [1..27] source prefix offsets
+  T* out_old = (T*)((sizeof(T) == 4) ? (void*)d.phi_old32 : (void*)d.phi_old);
+  T* out_new = (T*)((sizeof(T) == 4) ? (void*)d.phi_new32 : (void*)d.phi_new);
 
   const int tid = threadIdx.x;
   const int nL = g.nL, E = g.E;
@@ -298,14 +407,13 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
   const T h = (T)g.h;
   const V4* spos = (const V4*)((sizeof(T) == 4) ? (const void*)d.spos32 : (const void*)d.spos64);
 
-  // leaf local expansion (downward-accumulated)
   const C* Pe = (const C*)d.Peff + (g.cell_off[g.L] + leaf) * g.P;
   for (int c = tid; c < g.P; c += blockDim.x) Lc[c] = Pe[c];
-  for (int c = tid; c < nbw; c += blockDim.x) bits[c] = 0u;
-  if (tid == 0) {
-    ctr[0] = 0;
-    owner[0] = leaf * g.cap;
+  for (int c = tid; c < nbw; c += blockDim.x) {
+    bits[c] = 0u;
+    need[c] = 0u;
   }
+  if (tid == 0) owner[0] = leaf * g.cap;
   if (tid >= 1 && tid <= KMC_NHOP) {
     int f = tid - 1;
     int mx = (lx + c_hop[f][0] + nL) % nL, my = (ly + c_hop[f][1] + nL) % nL, mz = (lz + c_hop[f][2] + nL) % nL;
@@ -313,60 +421,38 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
   }
   __syncthreads();
 
-  // occupancy bitmap of this leaf's sites
+  // (1) occupancy bitmap of this leaf's sites
   const int cnt_own = d.cnt[leaf];
   const int64_t base_own = leaf * g.cap;
   for (int j = tid; j < cnt_own; j += blockDim.x) {
-    int32_t u = d.uid[base_own + j];
-    int s = d.site[u];
-    int sx = s % E - gx0, sy = (s / E) % E - gy0, sz = s / (E * E) - gz0;
-    int ls = sx + W * (sy + W * sz);
+    int s = d.site[d.uid[base_own + j]];
+    int ls = (s % E - gx0) + W * ((s / E) % E - gy0 + W * (s / (E * E) - gz0));
     atomicOr(&bits[ls >> 5], 1u << (ls & 31));
+    atomicOr(&need[ls >> 5], 1u << (ls & 31));
   }
   __syncthreads();
 
-  // evaluation points: own charges, own hops staying in the leaf
-  for (int j = tid; j < cnt_own; j += blockDim.x) {
-    int32_t u = d.uid[base_own + j];
-    int s = d.site[u];
-    int gx = s % E, gy = (s / E) % E, gz = s / (E * E);
-    int ls = (gx - gx0) + W * ((gy - gy0) + W * (gz - gz0));
-    int slot = atomicAdd(&ctr[0], 1);
-    if (slot < pmax) pts[slot] = pt_make(ls, 0, 1, 0, j);
-    for (int k = 0; k < KMC_NHOP; k++) {
-      int tx = gx + c_hop[k][0], ty = gy + c_hop[k][1], tz = gz + c_hop[k][2];
-      tx = (tx + E) % E; ty = (ty + E) % E; tz = (tz + E) % E;
-      int ux = tx - gx0, uy = ty - gy0, uz = tz - gz0;
-      if (ux < 0 || ux >= W || uy < 0 || uy >= W || uz < 0 || uz >= W) continue;  // other leaf's CTA
-      int lt = ux + W * (uy + W * uz);
-      if (bits[lt >> 5] & (1u << (lt & 31))) {
-        d.mask[6 * (int64_t)u + k] = 0;
-        d.phi_new[6 * (int64_t)u + k] = __longlong_as_double(0x7ff8000000000000LL);
-      } else {
-        int sl = atomicAdd(&ctr[0], 1);
-        if (sl < pmax) pts[sl] = pt_make(lt, k, 0, 0, j);
-      }
-    }
-  }
-  // hops entering from the six face neighbours
-  for (int f = 0; f < KMC_NHOP; f++) {
-    int64_t mb = owner[1 + f];
-    int kin = f ^ 1;  // direction from the neighbour back into this leaf
-    int cm = d.cnt[mb / g.cap];
+  // (2) hop targets inside this leaf: own hops and hops entering from the six
+  // face neighbours (f = 0 own leaf, 1..6 neighbour f-1 hopping in direction f^1)
+  for (int f = 0; f <= KMC_NHOP; f++) {
+    const int64_t mb = owner[f];
+    const int cm = f ? d.cnt[mb / g.cap] : cnt_own;
     for (int j = tid; j < cm; j += blockDim.x) {
       int32_t u = d.uid[mb + j];
       int s = d.site[u];
-      int tx = s % E + c_hop[kin][0], ty = (s / E) % E + c_hop[kin][1], tz = s / (E * E) + c_hop[kin][2];
-      tx = (tx + E) % E; ty = (ty + E) % E; tz = (tz + E) % E;
-      int ux = tx - gx0, uy = ty - gy0, uz = tz - gz0;
-      if (ux < 0 || ux >= W || uy < 0 || uy >= W || uz < 0 || uz >= W) continue;
-      int lt = ux + W * (uy + W * uz);
-      if (bits[lt >> 5] & (1u << (lt & 31))) {
-        d.mask[6 * (int64_t)u + kin] = 0;
-        d.phi_new[6 * (int64_t)u + kin] = __longlong_as_double(0x7ff8000000000000LL);
-      } else {
-        int sl = atomicAdd(&ctr[0], 1);
-        if (sl < pmax) pts[sl] = pt_make(lt, kin, 0, 1 + f, j);
+      int gx = s % E, gy = (s / E) % E, gz = s / (E * E);
+      int k0 = f ? ((f - 1) ^ 1) : 0, k1 = f ? k0 + 1 : KMC_NHOP;
+      for (int k = k0; k < k1; k++) {
+        int tx = (gx + c_hop[k][0] + E) % E, ty = (gy + c_hop[k][1] + E) % E, tz = (gz + c_hop[k][2] + E) % E;
+        int ux = tx - gx0, uy = ty - gy0, uz = tz - gz0;
+        if (ux < 0 || ux >= W || uy < 0 || uy >= W || uz < 0 || uz >= W) continue;  // another leaf's CTA
+        int lt = ux + W * (uy + W * uz);
+        if (bits[lt >> 5] & (1u << (lt & 31))) {
+          d.mask[6 * (int64_t)u + k] = 0;
+          out_new[6 * (int64_t)u + k] = qnan<T>();
+        } else {
+          atomicOr(&need[lt >> 5], 1u << (lt & 31));
+        }
       }
     }
   }
@@ -385,82 +471,104 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
     ctr[27] = off;
   }
   __syncthreads();
-  int npts = ctr[0];
-  if (npts > pmax) {
-    if (tid == 0) atomicOr(&d.err[0], KMC_DERR_CAPACITY);
-    npts = pmax;
+  // (3) compact the needed sites (ascending local index)
+  if (tid == 0) {
+    int acc = 0;
+    for (int w2 = 0; w2 < nbw; w2++) {
+      woff[w2] = acc;
+      acc += __popc(need[w2]);
+    }
+    woff[nbw] = acc;
   }
+  __syncthreads();
+  for (int w2 = tid; w2 < nbw; w2 += blockDim.x) {
+    uint32_t m = need[w2];
+    int o = woff[w2];
+    while (m) {
+      int b = __ffs(m) - 1;
+      sites[o++] = (uint16_t)(32 * w2 + b);
+      m &= m - 1;
+    }
+  }
+  __syncthreads();
+  const int nsites = woff[nbw];
 
-  // ---- near-field pair sums, then L2P.  Points are processed in rounds of
-  // 2 * blockDim (slot 0 for every thread, slot 1 only in warps that have
-  // one); each round streams the sources: pass 0 = own leaf (self pair
-  // skipped by r2 > 0), passes 1.. = the 26 other leaves in chunks.
+  // (4) near-field pair sums and L2P, one site per thread per round.  Sources:
+  // own leaf first (pairs at distance 0 skipped), then the 26 other leaves,
+  // streamed in chunks.
   const int nsrc_other = ctr[27];
-  const int npass = 1 + (nsrc_other + chunk - 1) / chunk;
-  for (int rb = 0; rb < npts; rb += 2 * blockDim.x) {
-    const int b0 = rb + tid, b1 = rb + tid + blockDim.x;
-    T x0 = (T)1e18, y0 = (T)1e18, z0 = (T)1e18, x1 = (T)1e18, y1 = (T)1e18, z1 = (T)1e18;
-    if (b0 < npts) {
-      int l0 = PT_SITE(pts[b0]);
+  const int ntot = cnt_own + nsrc_other;
+  const int npass = (ntot + chunk - 1) / chunk;
+  for (int rb = 0; rb < nsites; rb += blockDim.x) {
+    const int b0 = rb + tid;
+    T x0 = (T)1e18, y0 = (T)1e18, z0 = (T)1e18;
+    int l0 = 0;
+    if (b0 < nsites) {
+      l0 = sites[b0];
       x0 = ((T)(gx0 + l0 % W) + (T)0.5) * h;
       y0 = ((T)(gy0 + (l0 / W) % W) + (T)0.5) * h;
       z0 = ((T)(gz0 + l0 / (W * W)) + (T)0.5) * h;
     }
-    if (b1 < npts) {
-      int l1 = PT_SITE(pts[b1]);
-      x1 = ((T)(gx0 + l1 % W) + (T)0.5) * h;
-      y1 = ((T)(gy0 + (l1 / W) % W) + (T)0.5) * h;
-      z1 = ((T)(gz0 + l1 / (W * W)) + (T)0.5) * h;
-    }
-    const bool one = __any_sync(0xffffffffu, b0 < npts);  // warp has work at all
-    const bool two = __any_sync(0xffffffffu, b1 < npts);
+    const bool one = __any_sync(0xffffffffu, b0 < nsites);
     NearField<T> nf;
     nf.reset();
     for (int pass = 0; pass < npass; pass++) {
-      __syncthreads();
-      int ns;
-      if (pass == 0) {
-        ns = cnt_own;
-        for (int j = tid; j < ns; j += blockDim.x) NearField<T>::stage(src, chunk, j, spos[base_own + j]);
-      } else {
-        int c0 = (pass - 1) * chunk;
-        ns = min(chunk, nsrc_other - c0);
-        for (int e = tid; e < ns; e += blockDim.x) {
-          int ge = c0 + e;
+      const int c0 = pass * chunk;
+      const int ns = min(chunk, ntot - c0);
+      if (npass > 1 || rb > 0) __syncthreads();  // previous pass / round done with the staging area
+      for (int e = tid; e < ns; e += blockDim.x) {
+        const int ge = c0 + e;
+        V4 v;
+        if (ge < cnt_own) {
+          v = spos[base_own + ge];
+        } else {
+          const int go = ge - cnt_own;
           int q = 0;
-          while (q < 25 && ctr[2 + q] <= ge) q++;
+          while (q < 25 && ctr[2 + q] <= go) q++;
           int qq = q >= 13 ? q + 1 : q;  // skip the centre in the 27-neighbourhood order
           int ox = qq % 3 - 1, oy = (qq / 3) % 3 - 1, oz = qq / 9 - 1;
           int ux = lx + ox, uy = ly + oy, uz = lz + oz;
           int sx = (ux + nL) % nL, sy = (uy + nL) % nL, sz = (uz + nL) % nL;
-          int64_t sl = (sx + (int64_t)nL * (sy + (int64_t)nL * sz)) * g.cap + (ge - ctr[1 + q]);
-          V4 v = spos[sl];
+          int64_t sl = (sx + (int64_t)nL * (sy + (int64_t)nL * sz)) * g.cap + (go - ctr[1 + q]);
+          v = spos[sl];
           v.x += (T)((ux - sx) * W) * h;
           v.y += (T)((uy - sy) * W) * h;
           v.z += (T)((uz - sz) * W) * h;
-          NearField<T>::stage(src, chunk, e, v);
         }
+        NearField<T>::stage(src, chunk, e, v);
       }
       if (tid == 0) NearField<T>::pad(src, chunk, ns);
       __syncthreads();
-      if (one) nf.run(src, chunk, ns, pass == 0, two, x0, y0, z0, x1, y1, z1);
+      if (one) {
+        const int nguard = max(0, min(cnt_own - c0, ns));  // own-leaf sources in this pass
+        nf.run2(src, chunk, ns, nguard, false, x0, y0, z0, x0, y0, z0);
+      }
     }
-    // L2P of the leaf local expansion and write-out
-    for (int side = 0; side < 2; side++) {
-      int b = side ? b1 : b0;
-      if (b >= npts) continue;
-      uint32_t r = pts[b];
-      int lt = PT_SITE(r);
-      T x = ((T)(lt % W) + (T)0.5 - (T)(0.5 * W)) * h;
-      T y = ((T)((lt / W) % W) + (T)0.5 - (T)(0.5 * W)) * h;
-      T z = ((T)(lt / (W * W)) + (T)0.5 - (T)(0.5 * W)) * h;
-      T v = nf.sum(side) + l2p_point<T, C>(Lc, g.p, x, y, z);
-      int32_t u = d.uid[owner[PT_F(r)] + PT_J(r)];
-      if (PT_OLD(r)) {
-        d.phi_old[u] = (double)v;
-      } else {
-        int k = PT_K(r);
-        d.phi_new[6 * (int64_t)u + k] = (double)v;
+    if (b0 < nsites) {
+      T x = ((T)(l0 % W) + (T)0.5 - (T)(0.5 * W)) * h;
+      T y = ((T)((l0 / W) % W) + (T)0.5 - (T)(0.5 * W)) * h;
+      T z = ((T)(l0 / (W * W)) + (T)0.5 - (T)(0.5 * W)) * h;
+      phis[l0] = nf.sum(0) + l2p_point<T, C>(Lc, g.p, x, y, z);
+    }
+  }
+  __syncthreads();
+  // (5) write-out: old-position potentials and unmasked hop potentials
+  for (int f = 0; f <= KMC_NHOP; f++) {
+    const int64_t mb = owner[f];
+    const int cm = f ? d.cnt[mb / g.cap] : cnt_own;
+    for (int j = tid; j < cm; j += blockDim.x) {
+      int32_t u = d.uid[mb + j];
+      int s = d.site[u];
+      int gx = s % E, gy = (s / E) % E, gz = s / (E * E);
+      if (f == 0) out_old[u] = phis[(gx - gx0) + W * ((gy - gy0) + W * (gz - gz0))];
+      int k0 = f ? ((f - 1) ^ 1) : 0, k1 = f ? k0 + 1 : KMC_NHOP;
+      for (int k = k0; k < k1; k++) {
+        int tx = (gx + c_hop[k][0] + E) % E, ty = (gy + c_hop[k][1] + E) % E, tz = (gz + c_hop[k][2] + E) % E;
+        int ux = tx - gx0, uy = ty - gy0, uz = tz - gz0;
+        if (ux < 0 || ux >= W || uy < 0 || uy >= W || uz < 0 || uz >= W) continue;
+        int lt = ux + W * (uy + W * uz);
+        if (bits[lt >> 5] & (1u << (lt & 31))) continue;  // masked: written in phase 2
+        out_new[6 * (int64_t)u + k] = phis[lt];
         d.mask[6 * (int64_t)u + k] = 1;
       }
     }
@@ -469,25 +577,31 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
 
 static size_t propose_smem(const Geo& g, int prec, int pmax, int chunk) {
   size_t ts = prec == 0 ? 8 : 4;
-  int nbw = (g.W * g.W * g.W + 31) / 32;
+  int W3 = g.W * g.W * g.W;
+  int nbw = (W3 + 31) / 32;
   size_t srcb = prec == 0 ? (size_t)chunk * 32 : (size_t)(chunk / 2 + 1) * 32;
-  return srcb + 2 * ts * (size_t)g.P + 4 * (size_t)pmax + 4 * (size_t)nbw + 4 * 32 + 8 * 8;
+  (void)pmax;
+  return srcb + 2 * ts * (size_t)g.P + 8 * 8 + ts * (size_t)W3 + 4 * (size_t)(3 * nbw + 1) +
+         2 * (size_t)((W3 + 1) & ~1) + 4 * 32;
 }
 
 static void propose_shape(const Geo& g, int* pmax, int* chunk) {
   int W3 = g.W * g.W * g.W;
   *pmax = W3 + 6 * W3 + 6 * g.W * g.W;  // every own charge, its hops, every entering hop
-  int c = 512 > g.cap ? 512 : g.cap;
+  int c = 1024 > g.cap ? 1024 : g.cap;
   *chunk = (c + 1) & ~1;  // even: FP32 sources are staged in pairs
 }
 
+static void kmc_preload();
+
 void kmc_prepare(const Geo& g, int prec) {
+  kmc_preload();
   if (g.E <= 0) return;
   int pmax, chunk;
   propose_shape(g, &pmax, &chunk);
   size_t sm = propose_smem(g, prec, pmax, chunk);
-  if (prec == 0) cudaFuncSetAttribute(k_propose_lattice<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  else cudaFuncSetAttribute(k_propose_lattice<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (prec == 0) raise_dynamic_smem((const void*)k_propose_lattice<double>, sm);
+  else raise_dynamic_smem((const void*)k_propose_lattice<float>, sm);
 }
 
 void kmc_propose_lattice(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
@@ -508,78 +622,81 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// MIXED: the assembly and the rate's mantissa in FP32 (dU tolerance of the
+// exact FP32 -> FP64 widening of a non-negative normal or zero value by
+// moving the IEEE-754 fields (integer pipe; on this GPU a converting
+// instruction costs as much as FP64 arithmetic)
+__device__ __forceinline__ double widen_nonneg(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const uint32_t e = b >> 23;
+  if (e == 0) return 0.0;
+  const uint64_t bits = ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+// One thread per event j = 6 i + k (coalesced reads of phi_new / mask and
+// writes of dU / rate); per-particle sums of the 6 rates (sequential in k) and
+// the block sum (sequential over the block's particles) are kept in the exact
+// order the selection walk uses.
+// MIXED: the assembly and the rate's mantissa in FP32 (the dU tolerance of the
 // mixed form is far above FP32 rounding), exponent range kept by an FP64 path
-// for rates below ~1e-34; FP64: every operation in FP64.
+// for rates below ~1e-33; FP64: every operation in FP64.
+#define FIN_EVENTS (KMC_NHOP * FIN_THREADS)
 template <bool MIXED>
-__global__ void __launch_bounds__(FIN_THREADS) k_finalize(const Geo g, const Dev d) {
+__global__ void __launch_bounds__(FIN_EVENTS) k_finalize(const Geo g, const Dev d) {
+  __shared__ double rs[FIN_EVENTS];
   __shared__ double ts[FIN_THREADS];
-  int64_t i = blockIdx.x * (int64_t)FIN_THREADS + threadIdx.x;
-  double tsum = 0.0;
-  if (i < g.n) {
+  const int64_t j = blockIdx.x * (int64_t)FIN_EVENTS + threadIdx.x;
+  double r = 0.0;
+  if (j < 6 * g.n) {
+    const int64_t i = j / 6;
+    const int k = (int)(j - 6 * i);
     const int E = g.E;
     const int s = d.site[i];
-    const int gx = s % E, gy = (s / E) % E, gz = s / (E * E);
-    const double V = g.a * g.a * g.a;
-    const double qd = d.q[i];
-    const double cq = 4.0 * M_PI / (3.0 * V) * qd;
-    const double cM[3] = {cq * d.dip[0], cq * d.dip[1], cq * d.dip[2]};
-    const int gc[3] = {gx, gy, gz};
-    const double inv_kT = 1.0 / g.kT;
+    const int ax = k >> 1;
+    const int gc = ax == 0 ? s % E : (ax == 1 ? (s / E) % E : s / (E * E));
+    const int t = gc + ((k & 1) ? -1 : 1);
     if (MIXED) {
-      const float q = (float)qd, po = (float)d.phi_old[i], ikT = (float)inv_kT;
-      const float fh = (float)g.h, fa = (float)g.a;
-      const float fM[3] = {(float)cM[0], (float)cM[1], (float)cM[2]};
-      for (int k = 0; k < KMC_NHOP; k++) {
-        int64_t j = 6 * i + k;
-        double du, r;
-        if (!d.mask[j]) {
-          du = __longlong_as_double(0x7ff8000000000000LL);
-          r = 0.0;
-        } else {
-          int ax = k >> 1;
-          float sg = (k & 1) ? -1.f : 1.f;
-          int t = gc[ax] + ((k & 1) ? -1 : 1);
-          float dw = sg * fh;
-          if (t < 0) dw += fa; else if (t >= E) dw -= fa;
-          float duf = q * ((float)d.phi_new[j] - po) - fM[ax] * dw - q * q * (float)d.selfc[k];
-          du = (double)duf;
-          float x = fmaxf(duf, 0.f) * ikT;
-          if (x < 75.f) r = (double)ex2_approx(-x * 1.4426950408889634f);
-          else r = exp(-(double)x);
-        }
-        d.dU[j] = du;
-        d.rate[j] = r;
-        tsum += r;
+      float duf;
+      if (!d.mask[j]) {
+        duf = __int_as_float(0x7fc00000);
+      } else {
+        const float q = d.q32[i];
+        float dw = (k & 1) ? -(float)g.h : (float)g.h;
+        if (t < 0) dw += (float)g.a; else if (t >= E) dw -= (float)g.a;
+        duf = q * (d.phi_new32[j] - d.phi_old32[i]) - q * d.fdip[ax] * dw - q * q * d.selfc32[k];
+        const float x = fmaxf(duf, 0.f) * (float)(1.0 / g.kT);
+        r = (x < 75.f) ? widen_nonneg(ex2_approx(-x * 1.4426950408889634f)) : exp(-(double)x);
       }
+      d.dU32[j] = duf;
+      d.rate[j] = r;
     } else {
-      const double po = d.phi_old[i];
-      for (int k = 0; k < KMC_NHOP; k++) {
-        int64_t j = 6 * i + k;
-        double du, r;
-        if (!d.mask[j]) {
-          du = __longlong_as_double(0x7ff8000000000000LL);
-          r = 0.0;
-        } else {
-          int ax = k >> 1;
-          double sg = (k & 1) ? -1.0 : 1.0;
-          int t = gc[ax] + ((k & 1) ? -1 : 1);
-          double dw = sg * g.h;
-          if (t < 0) dw += g.a; else if (t >= E) dw -= g.a;
-          du = qd * (d.phi_new[j] - po) - cM[ax] * dw - qd * qd * d.selfc[k];
-          r = exp(-fmax(du, 0.0) * inv_kT);
-        }
-        d.dU[j] = du;
-        d.rate[j] = r;
-        tsum += r;
+      double du;
+      if (!d.mask[j]) {
+        du = __longlong_as_double(0x7ff8000000000000LL);
+      } else {
+        const double q = d.q[i];
+        double dw = (k & 1) ? -g.h : g.h;
+        if (t < 0) dw += g.a; else if (t >= E) dw -= g.a;
+        const double cM = 4.0 * M_PI / (3.0 * g.a * g.a * g.a) * d.dip[ax];
+        du = q * (d.phi_new[j] - d.phi_old[i]) - q * cM * dw - q * q * d.selfc[k];
+        r = exp(-fmax(du, 0.0) / g.kT);
       }
+      d.dU[j] = du;
+      d.rate[j] = r;
     }
   }
-  ts[threadIdx.x] = tsum;
+  rs[threadIdx.x] = r;
+  __syncthreads();
+  if (threadIdx.x < FIN_THREADS) {
+    const double* p = rs + KMC_NHOP * threadIdx.x;
+    double tsum = 0.0;
+    for (int kk = 0; kk < KMC_NHOP; kk++) tsum += p[kk];
+    ts[threadIdx.x] = tsum;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     double b = 0.0;
-    for (int t = 0; t < FIN_THREADS; t++) b += ts[t];
+    for (int t2 = 0; t2 < FIN_THREADS; t2++) b += ts[t2];
     d.bsum[blockIdx.x] = b;
   }
 }
@@ -602,8 +719,8 @@ __global__ void __launch_bounds__(FIN_THREADS) k_rate_bsum(const Geo g, const De
 
 void kmc_finalize_rates(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
   unsigned nb = (unsigned)((g.n + FIN_THREADS - 1) / FIN_THREADS);
-  if (prec == 0) k_finalize<false><<<nb, FIN_THREADS, 0, s>>>(g, d);
-  else k_finalize<true><<<nb, FIN_THREADS, 0, s>>>(g, d);
+  if (prec == 0) k_finalize<false><<<nb, FIN_EVENTS, 0, s>>>(g, d);
+  else k_finalize<true><<<nb, FIN_EVENTS, 0, s>>>(g, d);
 }
 
 // ------------------------------------------------------------------ selection
@@ -762,17 +879,14 @@ __global__ void k_move_from_event(const Geo g, const Dev d) {
     mv.rn[0] = (tx + 0.5) * g.h;
     mv.rn[1] = (ty + 0.5) * g.h;
     mv.rn[2] = (tz + 0.5) * g.h;
-    mv.dU = d.dU[j];
+    mv.dU = g.prec ? (double)d.dU32[j] : d.dU[j];
   }
   *d.move = mv;
 }
 
 void kmc_accept_from_event(const Geo& g, const Dev& d, cudaStream_t s) { k_move_from_event<<<1, 1, 0, s>>>(g, d); }
 
-__device__ __forceinline__ int cell_coord(double x, double w, int n) {
-  int c = (int)floor(x / w);
-  return min(max(c, 0), n - 1);
-}
+
 
 // multipoles of the ancestors of the old and new positions, all levels:
 // Mt_l[anc(r)] -= q R(r - c), Mt_l[anc(r')] += q R(r' - c).  thread per (level, m).
@@ -791,7 +905,7 @@ __global__ void k_acc_multipole(const Geo g, const Dev d) {
   for (int side = 0; side < 2; side++) {
     const double* x = side ? mv.rn : mv.r;
     double q = side ? mv.q : -mv.q;
-    int cx = cell_coord(x[0], wl, nl), cy = cell_coord(x[1], wl, nl), cz = cell_coord(x[2], wl, nl);
+    int cx = cell_at(x[0], nl, g.inv_a), cy = cell_at(x[1], nl, g.inv_a), cz = cell_at(x[2], nl, g.inv_a);
     cell[side] = cx + (int64_t)nl * (cy + (int64_t)nl * cz);
     double dx = x[0] - (cx + 0.5) * wl, dy = x[1] - (cy + 0.5) * wl, dz = x[2] - (cz + 0.5) * wl;
     double r2 = dx * dx + dy * dy + dz * dz;
@@ -858,8 +972,11 @@ __global__ void k_acc_far(const Geo g, const Dev d) {
   }
   if (lane == 0) {
     double2* H = d.Psi + g.cell_off[1] * g.P;
-    H[ci].x += ax;
-    H[ci].y += ay;
+    double2 v = H[ci];
+    v.x += ax;
+    v.y += ay;
+    H[ci] = v;
+    if (d.Psi32) d.Psi32[g.cell_off[1] * g.P + ci] = make_float2((float)v.x, (float)v.y);
   }
 }
 
@@ -908,51 +1025,81 @@ __device__ __forceinline__ bool image_in_il(const int u0[3], int nl, int nu, con
   return in && far;
 }
 
-// coarse levels (n_l <= 4): every cell b of the level, thread per (cell, image
-// of either position); the P2L tables go to a scratch area and are summed over
-// the images in fixed order by k_acc_coarse_reduce.
-__global__ void k_acc_coarse(const Geo g, const Dev d, int l, double2* scratch) {
+// coarse levels 2 and 3: thread per (cell, image of either position); the P2L
+// tables go to a scratch area and are summed over the images in fixed order by
+// k_acc_coarse_reduce.  Level 2 (8 cells) sees every image nu with
+// |nu|_inf <= KMC_TOP (the block its interaction list covers) that is not one
+// of the cell's 27 neighbours; level 3 (64 cells) the 27 nearest images under
+// the usual interaction-list rule.  Slots: level-2 cell c, image i at
+// c * 2 KMC_TOP_NIMG + i; level-3 cell c at the level-2 slots' end + c * 54 + i.
+#define KMC_L2_SLOTS (8 * 2 * KMC_TOP_NIMG)
+#define KMC_COARSE_SLOTS (KMC_L2_SLOTS + 64 * 54)
+#define KMC_COARSE_CELLS 72
+
+__global__ void k_acc_coarse(const Geo g, const Dev d, double2* scratch) {
   MoveRec mv = *d.move;
   if (!mv.valid) return;
-  const int nl = 1 << (l - 1), ncl = nl * nl * nl;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int cell = t / 54, im = t % 54;
-  if (cell >= ncl) return;
-  int b[3] = {cell % nl, (cell / nl) % nl, cell / (nl * nl)};
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= KMC_COARSE_SLOTS) return;
+  int l, cell, im, nimg1, span;
+  if (slot < KMC_L2_SLOTS) {
+    l = 2; cell = slot / (2 * KMC_TOP_NIMG); im = slot % (2 * KMC_TOP_NIMG); nimg1 = KMC_TOP_NIMG; span = KMC_TOP;
+  } else {
+    l = 3; cell = (slot - KMC_L2_SLOTS) / 54; im = (slot - KMC_L2_SLOTS) % 54; nimg1 = 27; span = 1;
+  }
+  const int nl = 1 << (l - 1);
+  const int b[3] = {cell % nl, (cell / nl) % nl, cell / (nl * nl)};
   const double wl = g.a / nl;
-  int side = im / 27, nu = im % 27;
+  const int side = im / nimg1, nu = im % nimg1, w = 2 * span + 1;
+  const int nv[3] = {nu % w - span, (nu / w) % w - span, nu / (w * w) - span};
   const double* x = side ? mv.rn : mv.r;
-  double q = side ? mv.q : -mv.q;
+  const double q = side ? mv.q : -mv.q;
   int u0[3];
-  for (int c = 0; c < 3; c++) u0[c] = cell_coord(x[c], wl, nl);
-  double2* out = scratch + ((int64_t)cell * 54 + im) * g.P;
-  if (!image_in_il(u0, nl, nu, b)) {
+  for (int c = 0; c < 3; c++) u0[c] = cell_at(x[c], nl, g.inv_a);
+  bool in_il;
+  if (l == 2) {  // any image of the block that is not a neighbour of b
+    bool far = false;
+    for (int c = 0; c < 3; c++)
+      if (abs(u0[c] + nl * nv[c] - b[c]) >= 2) far = true;
+    in_il = far;
+  } else {
+    int nu27 = (nv[0] + 1) + 3 * ((nv[1] + 1) + 3 * (nv[2] + 1));
+    in_il = image_in_il(u0, nl, nu27, b);
+  }
+  double2* out = scratch + (int64_t)slot * g.P;
+  if (!in_il) {
     for (int c = 0; c < g.P; c++) out[c] = make_double2(0.0, 0.0);
     return;
   }
-  int nv[3] = {nu % 3 - 1, (nu / 3) % 3 - 1, nu / 9 - 1};
   double dx = x[0] + g.a * nv[0] - (b[0] + 0.5) * wl, dy = x[1] + g.a * nv[1] - (b[1] + 0.5) * wl,
          dz = x[2] + g.a * nv[2] - (b[2] + 0.5) * wl;
   p2l_table<false>(out, q, dx, dy, dz, g.p);
 }
 
-__global__ void k_acc_coarse_reduce(const Geo g, const Dev d, int l, const double2* scratch) {
+__global__ void k_acc_coarse_reduce(const Geo g, const Dev d, const double2* scratch) {
   MoveRec mv = *d.move;
   if (!mv.valid) return;
-  const int nl = 1 << (l - 1), ncl = nl * nl * nl;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int cell = t / g.P, c = t % g.P;
-  if (cell >= ncl) return;
+  int cc = t / g.P, c = t % g.P;
+  if (cc >= KMC_COARSE_CELLS) return;
+  int l, cell, first, nslot;
+  if (cc < 8) { l = 2; cell = cc; first = cc * 2 * KMC_TOP_NIMG; nslot = 2 * KMC_TOP_NIMG; }
+  else { l = 3; cell = cc - 8; first = KMC_L2_SLOTS + cell * 54; nslot = 54; }
   double ax = 0.0, ay = 0.0;
-  for (int im = 0; im < 54; im++) {
-    double2 v = scratch[((int64_t)cell * 54 + im) * g.P + c];
+  for (int s2 = 0; s2 < nslot; s2++) {
+    double2 v = scratch[((int64_t)first + s2) * g.P + c];
     ax += v.x;
     ay += v.y;
   }
-  double2* out = d.Psi + (g.cell_off[l] + cell) * g.P;
-  out[c].x += ax;
-  out[c].y += ay;
+  const int64_t at = (g.cell_off[l] + cell) * g.P + c;
+  double2 v = d.Psi[at];
+  v.x += ax;
+  v.y += ay;
+  d.Psi[at] = v;
+  if (d.Psi32) d.Psi32[at] = make_float2((float)v.x, (float)v.y);
 }
+
+int kmc_coarse_slots() { return KMC_COARSE_SLOTS; }
 
 // fine levels (n_l >= 8): the candidate cells are the children of the
 // (wrapped) 3x3x3 parent neighbourhoods of the old and new positions' parent
@@ -978,8 +1125,8 @@ __global__ void k_acc_fine(const Geo g, const Dev d, int lmin) {
   const double* x0 = side0 ? mv.rn : mv.r;
   int P0[3], Pold[3];
   for (int c = 0; c < 3; c++) {
-    P0[c] = cell_coord(x0[c], 2.0 * wl, np);
-    Pold[c] = cell_coord(mv.r[c], 2.0 * wl, np);
+    P0[c] = cell_at(x0[c], np, g.inv_a);
+    Pold[c] = cell_at(mv.r[c], np, g.inv_a);
   }
   int b[3];
   for (int c = 0; c < 3; c++) b[c] = 2 * (((P0[c] + dlt[c]) % np + np) % np) + ((o >> c) & 1);
@@ -996,7 +1143,7 @@ __global__ void k_acc_fine(const Geo g, const Dev d, int lmin) {
     const double* x = side ? mv.rn : mv.r;
     double q = side ? mv.q : -mv.q;
     int u0[3];
-    for (int c = 0; c < 3; c++) u0[c] = cell_coord(x[c], wl, nl);
+    for (int c = 0; c < 3; c++) u0[c] = cell_at(x[c], nl, g.inv_a);
     for (int nu = 0; nu < 27; nu++) {
       if (!image_in_il(u0, nl, nu, b)) continue;
       any = true;
@@ -1024,7 +1171,8 @@ __global__ void k_acc_fine(const Geo g, const Dev d, int lmin) {
     }
   }
   if (!any) return;
-  double2* out = d.Psi + (g.cell_off[l] + b[0] + (int64_t)nl * (b[1] + (int64_t)nl * b[2])) * g.P;
+  const int64_t base = (g.cell_off[l] + b[0] + (int64_t)nl * (b[1] + (int64_t)nl * b[2])) * g.P;
+  double2* out = d.Psi + base;
   // all loads first, then all stores (the row's coefficients are independent)
   for (int n = m; n <= g.p; n++) {
     double2 v = out[tri(n, m)];
@@ -1032,6 +1180,8 @@ __global__ void k_acc_fine(const Geo g, const Dev d, int lmin) {
     acc[n].y += v.y;
   }
   for (int n = m; n <= g.p; n++) out[tri(n, m)] = acc[n];
+  if (d.Psi32)
+    for (int n = m; n <= g.p; n++) d.Psi32[base + tri(n, m)] = make_float2((float)acc[n].x, (float)acc[n].y);
 }
 
 // move the charge between leaf slots; dipole, energy and bookkeeping
@@ -1043,7 +1193,7 @@ __global__ void k_acc_move(const Geo g, const Dev d) {
   int64_t lo = so / g.cap;
   int ln = 0;
   {
-    int cx = cell_coord(mv.rn[0], g.w, g.nL), cy = cell_coord(mv.rn[1], g.w, g.nL), cz = cell_coord(mv.rn[2], g.w, g.nL);
+    int cx = cell_at(mv.rn[0], g.nL, g.inv_a), cy = cell_at(mv.rn[1], g.nL, g.inv_a), cz = cell_at(mv.rn[2], g.nL, g.inv_a);
     ln = cx + g.nL * (cy + g.nL * cz);
   }
   // remove: move the leaf's last entry into the hole
@@ -1072,7 +1222,12 @@ __global__ void k_acc_move(const Geo g, const Dev d) {
   d.pos[3 * i + 1] = mv.rn[1];
   d.pos[3 * i + 2] = mv.rn[2];
   d.site[i] = mv.site_new;
-  for (int c3 = 0; c3 < 3; c3++) d.dip[c3] += mv.q * (mv.rn[c3] - mv.r[c3]);
+  const double cdip = 4.0 * M_PI / (3.0 * g.a * g.a * g.a);
+  for (int c3 = 0; c3 < 3; c3++) {
+    double m3 = d.dip[c3] + mv.q * (mv.rn[c3] - mv.r[c3]);
+    d.dip[c3] = m3;
+    d.fdip[c3] = (float)(cdip * m3);
+  }
   d.U[0] += mv.dU;
 }
 
@@ -1080,13 +1235,9 @@ void kmc_accept_apply(const Geo& g, const Dev& d, cudaStream_t s) {
   int nt = g.L * (g.p + 1);
   k_acc_multipole<<<(nt + 31) / 32, 32, 0, s>>>(g, d);
   k_acc_far<<<g.P, 32, 0, s>>>(g, d);
-  // coarse levels 2 and 3 (8 and 64 cells): all cells x all images
-  int lc = g.L < 3 ? g.L : 3;
-  for (int l = 2; l <= lc; l++) {
-    int ncl = 1 << (3 * (l - 1));
-    k_acc_coarse<<<(ncl * 54 + 63) / 64, 64, 0, s>>>(g, d, l, d.acc_scratch);
-    k_acc_coarse_reduce<<<(ncl * g.P + 127) / 128, 128, 0, s>>>(g, d, l, d.acc_scratch);
-  }
+  // coarse levels 2 and 3 (8 + 64 cells, L >= 3 always): all cells x all images
+  k_acc_coarse<<<(KMC_COARSE_SLOTS + 63) / 64, 64, 0, s>>>(g, d, d.acc_scratch);
+  k_acc_coarse_reduce<<<(KMC_COARSE_CELLS * g.P + 127) / 128, 128, 0, s>>>(g, d, d.acc_scratch);
   if (g.L >= 4) {
     dim3 grid((432 * (g.p + 1) + 63) / 64, g.L - 3);
     k_acc_fine<<<grid, 64, 0, s>>>(g, d, 4);
@@ -1108,7 +1259,7 @@ __global__ void k_eval_points(const Geo g, const Dev d, int64_t m, const double*
   if (wid >= m) return;
   double X = pts[3 * wid], Y = pts[3 * wid + 1], Z = pts[3 * wid + 2];
   int ex = excl ? excl[wid] : -1;
-  int cx = cell_coord(X, g.w, g.nL), cy = cell_coord(Y, g.w, g.nL), cz = cell_coord(Z, g.w, g.nL);
+  int cx = cell_at(X, g.nL, g.inv_a), cy = cell_at(Y, g.nL, g.inv_a), cz = cell_at(Z, g.nL, g.inv_a);
   int64_t leaf = cx + (int64_t)g.nL * (cy + (int64_t)g.nL * cz);
   const V4* spos = (const V4*)((sizeof(T) == 4) ? (const void*)d.spos32 : (const void*)d.spos64);
   T x = (T)X, y = (T)Y, z = (T)Z;
@@ -1212,6 +1363,16 @@ void kmc_assemble_general(const Geo& g, const Dev& d, int64_t m, const int32_t* 
   k_assemble_general<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(g, d, m, particle, tgt, mask, phi_new, phi_old, dU);
 }
 
+// FP32 -> FP64 copy (API outputs and energy of the mixed form; not per step)
+__global__ void k_widen(const float* src, double* dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
+}
+
+void kmc_widen(const float* src, double* dst, int64_t n, cudaStream_t s) {
+  if (n > 0) k_widen<<<1024, 256, 0, s>>>(src, dst, n);
+}
+
 // ------------------------------------------------------------------ energy
 // U = 1/2 sum q_i Phi_self(r_i) - 2 pi |M|^2 / (3V)  (Algorithm 3 with the far
 // field in Phi and the dipole term of Sec. 2.2.2); fixed-order reduction.
@@ -1300,4 +1461,24 @@ void kmc_stage_general(const Geo& g, const Dev& d, int64_t m, const int32_t* par
                        const uint8_t* min_, double* tout, double* old, double* dv, uint8_t* mout, cudaStream_t s) {
   if (m <= 0) return;
   k_stage_general<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(g, d, m, part, tin, min_, tout, old, dv, mout);
+}
+
+// load every per-step kernel up front: with lazy module loading a first
+// launch inside a stream capture would invalidate the capture
+static void kmc_preload() {
+  cudaFuncAttributes fa;
+  cudaFuncGetAttributes(&fa, k_propose_lattice<float>);
+  cudaFuncGetAttributes(&fa, k_propose_lattice<double>);
+  cudaFuncGetAttributes(&fa, k_finalize<true>);
+  cudaFuncGetAttributes(&fa, k_finalize<false>);
+  cudaFuncGetAttributes(&fa, k_rate_bsum);
+  cudaFuncGetAttributes(&fa, k_select);
+  cudaFuncGetAttributes(&fa, k_record);
+  cudaFuncGetAttributes(&fa, k_move_from_event);
+  cudaFuncGetAttributes(&fa, k_acc_multipole);
+  cudaFuncGetAttributes(&fa, k_acc_far);
+  cudaFuncGetAttributes(&fa, k_acc_coarse);
+  cudaFuncGetAttributes(&fa, k_acc_coarse_reduce);
+  cudaFuncGetAttributes(&fa, k_acc_fine);
+  cudaFuncGetAttributes(&fa, k_acc_move);
 }

@@ -11,6 +11,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "../../include/kmcfmm.h"
@@ -40,6 +43,7 @@ struct kmc_fmm {
   uint8_t* gen_mask;
   // step-loop capacity and graph
   int run_cap;
+  int run_gen;  // bumped whenever the step-loop buffers are reallocated
   cudaGraphExec_t graph;
   int graph_steps;
   double* drift2;
@@ -132,6 +136,7 @@ static int full_fmm(kmc_fmm* h) {
   fmm_m2m(g, d, s);
   fmm_m2l(g, d, s);
   fmm_far_field(g, d, s);
+  fmm_shadow_all(g, d, s);
   fmm_self_and_dipole(g, d, s);
   CKLAUNCH();
   h->peff_valid = false;
@@ -154,6 +159,7 @@ static int compute_phi_old(kmc_fmm* h) {
   if (h->g.E > 0) {
     kmc_propose_lattice(h->g, h->d, h->prec, h->stream);
     kmc_finalize_rates(h->g, h->d, h->prec, h->stream);
+    if (h->prec == 1) kmc_widen(h->d.phi_old32, h->d.phi_old, h->g.n, h->stream);
     h->rates_valid = true;
   } else {
     kmc_eval_points(h->g, h->d, h->prec, h->g.n, h->d.pos, h->iota, h->d.phi_old, h->stream);
@@ -171,6 +177,22 @@ static int compute_energy(kmc_fmm* h) {
 }
 
 // ------------------------------------------------------------------ C ABI
+// The dynamic shared-memory limit of a kernel is a per-device attribute shared
+// by every handle in the process.  Handles of different shapes need different
+// sizes, so the limit only ever grows: a smaller later handle must not lower it
+// below what an earlier one launches with (a launch above the limit fails, and
+// inside a stream capture that failure invalidates the whole capture).
+void raise_dynamic_smem(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> set;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = set[std::make_pair(fn, dev)];
+  if (bytes <= cur) return;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess) cur = bytes;
+}
+
 extern "C" {
 
 void kmc_opts_default(kmc_opts* o) {
@@ -212,7 +234,9 @@ static int init_impl(kmc_fmm* h, int64_t n, const double* positions, const doubl
   g.ML = (int64_t)g.nL * g.nL * g.nL;
   g.a = box;
   g.w = box / g.nL;
+  g.inv_a = 1.0 / box;
   g.kT = 1.0;
+  g.prec = h->prec;
   int64_t off = 0;
   for (int l = 1; l <= levels; l++) {
     g.cell_off[l] = off;
@@ -241,6 +265,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   h->graph_steps = 0;
   h->gen_cap = 0;
   h->run_cap = 0;
+  h->run_gen = 0;
   h->phi_save = nullptr;
   *out = h;
   // ---- host-side argument checks
@@ -308,8 +333,9 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
       for (int k = 0; k < 3; k++) {
         double x = ph[3 * i + k];
         if (!isfinite(x) || x < 0.0 || x >= box) return fail(h, KMC_ERR_ARG, "position of charge %lld outside [0, box)", (long long)i);
-        c[k] = (int)floor(x / g.w);
+        c[k] = (int)floor(x * ((double)g.nL * g.inv_a));
         if (c[k] >= g.nL) c[k] = g.nL - 1;
+        if (c[k] < 0) c[k] = 0;
       }
       int64_t lf = c[0] + (int64_t)g.nL * (c[1] + (int64_t)g.nL * c[2]);
       mx = cnt[lf] + 1 > mx ? cnt[lf] + 1 : mx;
@@ -334,22 +360,33 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   ALLOC(d.Psi, sizeof(double2) * g.ncell_total * g.P);
   ALLOC(d.Peff, (h->prec == 0 ? sizeof(double2) : sizeof(float2)) * g.ncell_total * g.P);
   ALLOC(d.Itab, sizeof(double2) * (size_t)(g.L + 1) * 343 * g.P2);
+  ALLOC(d.Itab2, sizeof(double2) * (size_t)KMC_TOP_NOFF * g.P2);
   ALLOC(d.S, sizeof(double2) * g.P2);
   ALLOC(d.Rch, sizeof(double2) * (size_t)(g.L + 1) * 8 * g.P);
   ALLOC(d.selfc, sizeof(double) * KMC_NHOP);
   ALLOC(d.dip, sizeof(double) * 3);
+  ALLOC(d.fdip, sizeof(float) * 4);
   ALLOC(d.U, sizeof(double));
+  if (h->prec == 1) {
+    ALLOC(d.q32, sizeof(float) * n);
+    ALLOC(d.selfc32, sizeof(float) * KMC_NHOP);
+    ALLOC(d.Psi32, sizeof(float2) * g.ncell_total * g.P);
+    ALLOC(d.Rch32, sizeof(float2) * (size_t)(g.L + 1) * 8 * g.P);
+    ALLOC(d.phi_old32, sizeof(float) * n);
+    ALLOC(d.phi_new32, sizeof(float) * 6 * n);
+    ALLOC(d.dU32, sizeof(float) * 6 * n);
+  }
   ALLOC(d.phi_old, sizeof(double) * n);
   ALLOC(d.phi_new, sizeof(double) * 6 * n);
   ALLOC(d.mask, sizeof(uint8_t) * 6 * n);
   ALLOC(d.dU, sizeof(double) * 6 * n);
   ALLOC(d.rate, sizeof(double) * 6 * n);
-  ALLOC(d.bsum, sizeof(double) * ((n + 255) / 256 + 1));
+  ALLOC(d.bsum, sizeof(double) * ((n + KMC_FIN_PARTICLES - 1) / KMC_FIN_PARTICLES + 1));
   ALLOC(d.event, sizeof(int64_t) * 2);
   ALLOC(d.dtq, sizeof(double) * 2);
   ALLOC(d.move, sizeof(MoveRec));
   ALLOC(d.dK, sizeof(double2) * g.P);
-  ALLOC(d.acc_scratch, sizeof(double2) * 64 * 54 * g.P);
+  ALLOC(d.acc_scratch, sizeof(double2) * (size_t)kmc_coarse_slots() * g.P);
   ALLOC(d.err, sizeof(int) * 4);
   ALLOC(d.uni_small, sizeof(double) * 2);
   ALLOC(d.stepc, sizeof(int) * 2);
@@ -367,6 +404,12 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   CK(cudaMemsetAsync(d.Psi, 0, sizeof(double2) * g.ncell_total * g.P, s));
   CK(cudaMemcpyAsync(d.q, charges, sizeof(double) * n, in_kind(h), s));
   CK(cudaMemcpyAsync(d.pos, positions, sizeof(double) * 3 * n, in_kind(h), s));
+  if (h->prec == 1) {
+    std::vector<float> q32(n);
+    for (int64_t i = 0; i < n; i++) q32[i] = (float)qh[i];
+    CK(cudaMemcpyAsync(d.q32, q32.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
   {
     std::vector<int32_t> io(n);
     for (int64_t i = 0; i < n; i++) io[i] = (int32_t)i;
@@ -376,6 +419,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   fmm_upload_constants(order);
   kmc_upload_constants(order);
   kmc_prepare(g, h->prec);
+  fmm_prepare(g, h->prec);
   CKLAUNCH();
   kmc_validate(g, d, s);
   CKLAUNCH();
@@ -426,7 +470,10 @@ int kmc_fmm_propose_lattice(kmc_handle h, uint8_t* mask, double* dU) {
   h->rates_valid = true;
   const int64_t m = 6 * h->g.n;
   if (mask) CK(cudaMemcpyAsync(mask, h->d.mask, m, out_kind(h), h->stream));
-  if (dU) CK(cudaMemcpyAsync(dU, h->d.dU, sizeof(double) * m, out_kind(h), h->stream));
+  if (dU) {
+    if (h->prec == 1) kmc_widen(h->d.dU32, h->d.dU, m, h->stream);
+    CK(cudaMemcpyAsync(dU, h->d.dU, sizeof(double) * m, out_kind(h), h->stream));
+  }
   return check_flags(h, "propose_lattice");
 }
 
@@ -653,6 +700,7 @@ int kmc_run(kmc_handle h, int steps, const double* uniforms, int64_t* events, do
     ALLOC(h->d.ev_hist, sizeof(int64_t) * (size_t)cap);
     ALLOC(h->d.dt_hist, sizeof(double) * (size_t)cap);
     h->run_cap = cap;
+    h->run_gen++;
     if (h->graph) {  // kernel arguments changed
       cudaGraphExecDestroy(h->graph);
       h->graph = nullptr;
@@ -711,6 +759,7 @@ int kmc_run_profiled(kmc_handle h, int steps, const double* uniforms, int64_t* e
     ALLOC(h->d.ev_hist, sizeof(int64_t) * (size_t)cap);
     ALLOC(h->d.dt_hist, sizeof(double) * (size_t)cap);
     h->run_cap = cap;
+    h->run_gen++;
     if (h->graph) {
       cudaGraphExecDestroy(h->graph);
       h->graph = nullptr;
@@ -825,6 +874,187 @@ int kmc_fmm_positions(kmc_handle h, double* positions) {
   if (!positions) return fail(h, KMC_ERR_ARG, "positions is NULL");
   CK(cudaMemcpyAsync(positions, h->d.pos, sizeof(double) * 3 * h->g.n, out_kind(h), h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  return KMC_OK;
+}
+
+// ------------------------------------------------------------------ replica batches
+// A batch replays one KMC step of every member handle from a single CUDA
+// graph: the steps of different replicas are independent branches of the
+// graph (fork/join over one stream per replica), so small replicas overlap
+// on the GPU instead of waiting for each other's launches.
+struct kmc_batch {
+  std::vector<kmc_fmm*> h;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> join;
+  cudaStream_t s0;
+  cudaEvent_t fork;
+  cudaGraphExec_t graph;
+  int graph_cap;
+  std::vector<int> gen;  // members' buffer generations the graph was captured with
+  bool parallel;         // members captured as parallel branches
+  char msg[512];
+};
+
+static int bfail(kmc_batch* b, int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(b->msg, sizeof(b->msg), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int kmc_batch_create(kmc_batch_handle* out, int count, const kmc_handle* handles) {
+  if (!out) return KMC_ERR_ARG;
+  *out = nullptr;
+  if (count < 1 || !handles) return KMC_ERR_ARG;
+  kmc_batch* b = new kmc_batch();
+  b->graph = nullptr;
+  b->graph_cap = 0;
+  b->parallel = false;
+  b->msg[0] = 0;
+  *out = b;
+  int dev = -1;
+  for (int r = 0; r < count; r++) {
+    kmc_fmm* h = handles[r];
+    if (!h || h->broken) return bfail(b, KMC_ERR_ARG, "member %d is NULL or broken", r);
+    if (h->g.E <= 0) return bfail(b, KMC_ERR_STATE, "member %d is not in lattice mode", r);
+    if (dev >= 0 && h->device != dev) return bfail(b, KMC_ERR_ARG, "members must share one device");
+    dev = h->device;
+    for (int q = 0; q < r; q++)
+      if (handles[q] == h) return bfail(b, KMC_ERR_ARG, "member %d appears twice", r);
+    b->h.push_back(h);
+  }
+  if (cudaSetDevice(dev) != cudaSuccess) return bfail(b, KMC_ERR_CUDA, "cudaSetDevice failed");
+  if (cudaStreamCreateWithFlags(&b->s0, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+    return bfail(b, KMC_ERR_CUDA, "stream / event creation failed");
+  b->streams.resize(count);
+  b->join.resize(count);
+  for (int r = 0; r < count; r++)
+    if (cudaStreamCreateWithFlags(&b->streams[r], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join[r], cudaEventDisableTiming) != cudaSuccess)
+      return bfail(b, KMC_ERR_CUDA, "stream / event creation failed");
+  return KMC_OK;
+}
+
+const char* kmc_batch_last_error(kmc_batch_handle b) { return b ? b->msg : g_static_msg; }
+
+void kmc_batch_destroy(kmc_batch_handle b) {
+  if (!b) return;
+  if (!b->h.empty()) cudaSetDevice(b->h[0]->device);
+  if (b->s0) cudaStreamSynchronize(b->s0);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (size_t r = 0; r < b->streams.size(); r++) {
+    if (b->streams[r]) cudaStreamDestroy(b->streams[r]);
+    if (b->join[r]) cudaEventDestroy(b->join[r]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->s0) cudaStreamDestroy(b->s0);
+  delete b;
+}
+
+int kmc_batch_run(kmc_batch_handle b, int steps, const double* uniforms, int64_t* events, double* dts) {
+  if (!b) return KMC_ERR_ARG;
+  const int R = (int)b->h.size();
+  if (steps < 0 || !uniforms) return bfail(b, KMC_ERR_ARG, "steps >= 0 and uniforms are required");
+  if (steps == 0) return KMC_OK;
+  if (cudaSetDevice(b->h[0]->device) != cudaSuccess) return bfail(b, KMC_ERR_CUDA, "cudaSetDevice failed");
+  for (int r = 0; r < R; r++)
+    if (b->h[r]->broken) return bfail(b, KMC_ERR_STATE, "member %d broken: %s", r, b->h[r]->msg);
+  // per-member buffers for the uniforms and the event history
+  int need = steps;
+  bool realloc = false;
+  for (int r = 0; r < R; r++) {
+    kmc_fmm* h = b->h[r];
+    if (need > h->run_cap) {
+      int cap = need < 1024 ? 1024 : need;
+      if (dalloc(h, &h->d.uni_run, sizeof(double) * 2 * (size_t)cap) || dalloc(h, &h->d.ev_hist, sizeof(int64_t) * (size_t)cap) ||
+          dalloc(h, &h->d.dt_hist, sizeof(double) * (size_t)cap))
+        return bfail(b, KMC_ERR_OOM, "member %d: %s", r, h->msg);
+      h->run_cap = cap;
+      h->run_gen++;
+      if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+      }
+    }
+    if (b->gen.size() == (size_t)R && b->gen[r] != h->run_gen) realloc = true;
+  }
+  if (realloc && b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  std::vector<double> col(2 * (size_t)steps);
+  for (int r = 0; r < R; r++) {
+    kmc_fmm* h = b->h[r];
+    for (int s = 0; s < steps; s++) {
+      col[2 * s] = uniforms[((size_t)s * R + r) * 2];
+      col[2 * s + 1] = uniforms[((size_t)s * R + r) * 2 + 1];
+    }
+    if (cudaMemcpy(h->d.uni_run, col.data(), sizeof(double) * 2 * steps, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(h->d.stepc, 0, sizeof(int)) != cudaSuccess)
+      return bfail(b, KMC_ERR_CUDA, "staging uniforms failed");
+    if (h->stream && cudaStreamSynchronize(h->stream) != cudaSuccess)
+      return bfail(b, KMC_ERR_CUDA, "member stream synchronisation failed");
+  }
+  if (!b->graph) {
+    // fork/join capture (members' steps as parallel branches); if the driver
+    // refuses it, the members are captured one after another on one stream
+    for (int attempt = 0; attempt < 2 && !b->graph; attempt++) {
+      const bool parallel = attempt == 0;
+      cudaGraph_t gr = nullptr;
+      cudaGetLastError();
+      if (cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        return bfail(b, KMC_ERR_CUDA, "capture begin failed");
+      cudaError_t first = cudaSuccess;
+      if (parallel) first = cudaEventRecord(b->fork, b->s0);
+      for (int r = 0; r < R && first == cudaSuccess; r++) {
+        kmc_fmm* h = b->h[r];
+        cudaStream_t st = parallel ? b->streams[r] : b->s0;
+        if (parallel) first = cudaStreamWaitEvent(st, b->fork, 0);
+        if (first != cudaSuccess) break;
+        cudaStream_t saved = h->stream;
+        h->stream = st;
+        enqueue_step(h);
+        h->stream = saved;
+        first = cudaGetLastError();
+        if (first == cudaSuccess && parallel) first = cudaEventRecord(b->join[r], st);
+        if (first == cudaSuccess && parallel) first = cudaStreamWaitEvent(b->s0, b->join[r], 0);
+      }
+      cudaError_t ce = cudaStreamEndCapture(b->s0, &gr);
+      if (first == cudaSuccess && ce == cudaSuccess) {
+        ce = cudaGraphInstantiate(&b->graph, gr, 0);
+        if (ce != cudaSuccess) b->graph = nullptr;
+      }
+      if (gr) cudaGraphDestroy(gr);
+      cudaGetLastError();
+      if (!b->graph && attempt == 1)
+        return bfail(b, KMC_ERR_CUDA, "graph capture failed: %s / %s", cudaGetErrorString(first),
+                     cudaGetErrorString(ce));
+      b->parallel = parallel && b->graph != nullptr;
+    }
+    b->gen.resize(R);
+    for (int r = 0; r < R; r++) b->gen[r] = b->h[r]->run_gen;
+  }
+  for (int s = 0; s < steps; s++)
+    if (cudaGraphLaunch(b->graph, b->s0) != cudaSuccess) return bfail(b, KMC_ERR_CUDA, "graph launch failed");
+  if (cudaStreamSynchronize(b->s0) != cudaSuccess) return bfail(b, KMC_ERR_CUDA, "batch run failed");
+  std::vector<int64_t> ev(steps);
+  std::vector<double> dt(steps);
+  for (int r = 0; r < R; r++) {
+    kmc_fmm* h = b->h[r];
+    h->peff_valid = false;
+    h->rates_valid = false;
+    if (cudaMemcpy(ev.data(), h->d.ev_hist, sizeof(int64_t) * steps, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(dt.data(), h->d.dt_hist, sizeof(double) * steps, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return bfail(b, KMC_ERR_CUDA, "reading events failed");
+    int rc = check_flags(h, "batch run");
+    if (rc) return bfail(b, rc, "member %d: %s", r, h->msg);
+    for (int s = 0; s < steps; s++) {
+      if (events) events[(size_t)s * R + r] = ev[s];
+      if (dts) dts[(size_t)s * R + r] = dt[s];
+    }
+  }
   return KMC_OK;
 }
 

@@ -11,7 +11,7 @@
 // by a handle.  It needs no handle and allocates nothing.
 //
 // The array is a static object of the module: every GPU that loads this
-// library holds it (KMC_STATIC_BLOCKS + 8 doubles, about 512 KB) until the
+// library holds it (KMC_STATIC_BLOCKS + 8 doubles, about 1 MB) until the
 // process exits.  All calls share it, so calls whose GPU work overlaps (two
 // streams, two host threads) race on it; order them on one stream or
 // serialise them.  Every element a call reads is written earlier in the same

@@ -128,3 +128,34 @@ def batch_replicas(n: int | None = None):
 def random_small(E: int, N: int, seed: int):
     """Small uniform lattice system for unit tests."""
     return uniform_lattice(E, N, seed)
+
+
+# Error study of Sec. 5.1: an almost regular cubic arrangement at a density of
+# 0.01 charges per unit volume, small random perturbations, proposals that add
+# a further small displacement, and a fresh system every 100 proposals.
+ERROR_STUDY = dict(density=0.01, jitter=0.1, step=0.3, moves_per_system=100, seed=1006)
+
+
+def perturbed_cubic(n_side: int, seed: int, density: float = ERROR_STUDY["density"],
+                    jitter: float = ERROR_STUDY["jitter"]):
+    """n_side^3 charges on a simple-cubic grid of spacing c = density^(-1/3),
+    each moved by a uniform offset in [-jitter c, jitter c]^3, inside the
+    periodic box a = n_side c; neutral +-1 charges in random order.
+    Returns (positions (N, 3) in [0, a)^3, charges, a, c)."""
+    rng = np.random.default_rng(seed)
+    c = density ** (-1.0 / 3.0)
+    a = n_side * c
+    g = np.stack(np.meshgrid(*[np.arange(n_side)] * 3, indexing="ij"), axis=-1).reshape(-1, 3)
+    pos = (g + 0.5) * c + rng.uniform(-jitter * c, jitter * c, size=g.shape)
+    pos = np.mod(pos, a)
+    q = neutral_charges(rng, len(pos))
+    return pos, q, a, c
+
+
+def small_moves(n: int, c: float, m: int, seed: int, step: float = ERROR_STUDY["step"]):
+    """m proposals (particle index, displacement): particles uniform over the n
+    charges, displacement components uniform in [-step c, step c]."""
+    rng = np.random.default_rng(seed)
+    part = rng.integers(0, n, size=m)
+    disp = rng.uniform(-step * c, step * c, size=(m, 3))
+    return part.astype(np.int32), disp
