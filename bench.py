@@ -49,6 +49,28 @@ def _dist():
     return rank, world, local
 
 
+def aggregate(units: float, ms: float, device=None):
+    """Whole-job figures of independent replicas, one per rank: the units all
+    ranks processed (sum) and the slowest rank's time (max).  No collective
+    touches the data path; this is the only cross-rank exchange."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(units), float(ms)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    m = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(m.item())
+
+
+# per KMC step: downward root + (L - 1) levels, propose, finalize, select,
+# record, move-from-event and six accept kernels
+def launches_per_step(L: int) -> int:
+    return L + 11
+
+
 # --------------------------------------------------------------- algorithmic work
 def step_bytes(E: int, L: int, N: int, p: int) -> int:
     """Lower bound of the device bytes one lattice step touches: FP64 rates and
@@ -300,14 +322,10 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.barrier()
     clocks = clk.stop()
-    tot_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([tot_ms], device=f"cuda:{dev}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    ms_step = tot_ms / args.steps
     hops = work["hops"]  # unmasked proposals per step (changes negligibly per step)
-    value = world * hops * args.steps / (tot_ms * 1e-3)
+    units, tot_ms = aggregate(hops * args.steps, float(sum(step_ms)), device=f"cuda:{dev}")
+    ms_step = tot_ms / args.steps
+    value = units / (tot_ms * 1e-3)
     steps_per_s = world * args.steps / (tot_ms * 1e-3)
     prop_ms = phases[1] / args.steps
 
@@ -326,9 +344,10 @@ def run_gpu(args):
             k.kmc_fmm_accept_event(h, ev)
     e1.record(stream)
     e1.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / es
+    e2e_units, e2e_tot = aggregate(hops * es, e0.elapsed_time(e1), device=f"cuda:{dev}")
+    e2e_ms = e2e_tot / es
     n = len(q)
-    e2e = {"value": world * hops / (e2e_ms * 1e-3), "unit": UNIT,
+    e2e = {"value": e2e_units / (e2e_tot * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": 16 + 24 + 8,
            "d2h_bytes_per_step": 6 * n * (1 + 8) + 8 + 8 + 8 + 24 + 8,
            "path": "kmc_fmm_propose_lattice (mask+dU to host) + kmc_step + kmc_fmm_accept_event"}
@@ -393,14 +412,14 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f32-mixed (f32 near field + L2P, f64 far field / dU / accept)",
         "data": "synthetic", "config": dict(_config(w, args.workload), parallelism=f"replicas x{world}"),
         "kmc_steps_per_s": steps_per_s,
-        "propose_only_dU_evals_per_s": world * hops / (prop_ms * 1e-3),
+        "propose_only_dU_evals_per_s": hops / (prop_ms * 1e-3),
         "phase_ms_per_step": {nm: phases[i] / args.steps for i, nm in enumerate(k.PHASES)},
         "init_s": init_s,
         "fp64_form": fp64,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": (L + 14) * args.steps,
+        "gpu_launches": launches_per_step(L) * args.steps,
         "clocks": clocks,
     }
     print(json.dumps(line))
@@ -420,8 +439,11 @@ def run_batch(args):
     rank, world, local = _dist()
     dev = local if world > 1 else 0
     torch.cuda.set_device(dev)
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
     B = workloads.BATCH
-    reps = workloads.batch_replicas(args.replicas)
+    nrep = args.replicas or B["replicas"]
+    reps = workloads.batch_replicas(nrep, first=rank * nrep)  # each rank its own replicas
     p, kT = B["p"], B["kT"]
     t0 = time.perf_counter()
     handles, hops, levels = [], 0, []
@@ -452,10 +474,14 @@ def run_batch(args):
     torch.cuda.synchronize()
     ms = [1e3 * (time.perf_counter() - t1) / args.steps] * args.steps
     clocks = clk.stop()
-    tot = sum(ms)
+    units, tot = aggregate(hops * args.steps, sum(ms), device=f"cuda:{dev}")
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return 0
     line = {
-        "metric": "dU evals/sec and KMC steps/sec, 64 batched replicas", "value": hops * args.steps / (tot * 1e-3),
-        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps,
+        "metric": "dU evals/sec and KMC steps/sec, 64 batched replicas", "value": units / (tot * 1e-3),
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32-mixed (f32 near field + L2P, f64 far field / dU / accept)", "data": "synthetic",
         "config": {"workload": f"batch: {R} replicas, edges {sorted(set(r['E'] for r in reps))}, occupancy "
@@ -463,7 +489,8 @@ def run_batch(args):
                    "levels": levels, "working_set_bytes": ws,
                    "timing": "host wall clock around one kmc_batch_run of K steps (uniform staging and event "
                              "read-back included); working set larger than L2, no flush"},
-        "replica_steps_per_s": R * args.steps / (tot * 1e-3), "setup_s": setup_s, "clocks": clocks,
+        "replica_steps_per_s": world * R * args.steps / (tot * 1e-3), "setup_s": setup_s, "clocks": clocks,
+        "gpu_launches": launches_per_step(max(levels)) * R * args.steps,
     }
     print(json.dumps(line))
     return 0
@@ -475,7 +502,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="large", choices=["small", "medium", "large", "blobs", "batch"])
+    ap.add_argument("--workload", default="large", choices=["small", "medium", "large", "blobs", "tile", "batch"])
     ap.add_argument("--replicas", type=int, default=None)
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)

@@ -724,6 +724,62 @@ __global__ void __launch_bounds__(256) k_downward(const Geo g, const Dev d, int 
   }
 }
 
+// Upper levels (few cells): CTA per child cell, thread per output
+// coefficient.  The parent's expansion and the child-offset table are first
+// expanded to every order -n..n (the conjugate symmetry applied once), so the
+// inner loop is branch-free: out(k, lo) = sum_{n >= k} sum_m L(n, m) R(n - k, m - lo).
+template <typename T> __device__ __forceinline__ const typename cplx<T>::type* child_table(const Dev& d);
+template <> __device__ __forceinline__ const float2* child_table<float>(const Dev& d) { return d.Rch32; }
+template <> __device__ __forceinline__ const double2* child_table<double>(const Dev& d) { return d.Rch; }
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_downward_cell(const Geo g, const Dev d, int l) {
+  typedef typename cplx<T>::type C;
+  extern __shared__ __align__(16) unsigned char shraw[];
+  const int F = (g.p + 1) * (g.p + 1);
+  C* Lf = (C*)shraw;  // [F] parent expansion, entry n^2 + n + m
+  C* Rf = Lf + F;     // [F] child-offset regular table, same order
+  const int nl = 1 << (l - 1), np = nl / 2;
+  const int64_t cell = blockIdx.x;
+  const int bx = (int)(cell % nl), by = (int)((cell / nl) % nl), bz = (int)(cell / ((int64_t)nl * nl));
+  const int64_t par = (bx >> 1) + (int64_t)np * ((by >> 1) + (int64_t)np * (bz >> 1));
+  const int o = (bx & 1) + 2 * (by & 1) + 4 * (bz & 1);
+  const C* Pp = (const C*)d.Peff + (g.cell_off[l - 1] + par) * g.P;
+  const C* Ro = child_table<T>(d) + ((int64_t)l * 8 + o) * g.P;
+  for (int t = threadIdx.x; t < F; t += blockDim.x) {
+    int n = (int)sqrtf((float)t);
+    while ((n + 1) * (n + 1) <= t) n++;
+    while (n * n > t) n--;
+    const int m = t - n * n - n;
+    Lf[t] = tab_get(Pp, n, m);
+    Rf[t] = tab_get(Ro, n, m);
+  }
+  __syncthreads();
+  C* Pe = (C*)d.Peff;
+  for (int ci = threadIdx.x; ci < g.P; ci += blockDim.x) {
+    const short2 km = f_nm[ci];
+    const int k = km.x, lo = km.y;
+    T ax = 0, ay = 0;
+    for (int n = k; n <= g.p; n++) {
+      const int j = n - k;
+      const int mlo = max(lo - j, -n), mhi = min(lo + j, n);
+      const C* a = Lf + n * n + n;
+      const C* b = Rf + j * j + j - lo;
+      for (int m = mlo; m <= mhi; m++) {
+        const C u = a[m], v = b[m];
+        ax += u.x * v.x - u.y * v.y;
+        ay += u.x * v.y + u.y * v.x;
+      }
+    }
+    const int64_t at = (g.cell_off[l] + cell) * g.P + ci;
+    const C own = own_coef<T>(d, at);
+    C v;
+    v.x = ax + own.x;
+    v.y = ay + own.y;
+    Pe[at] = v;
+  }
+}
+
 static size_t downward_smem(const Geo& g, int prec) {
   return (size_t)(8 + DW_PAR + 8 * DW_PAR) * g.P * (prec == 0 ? sizeof(double2) : sizeof(float2));
 }
@@ -736,6 +792,8 @@ void fmm_prepare(const Geo& g, int prec) {
   cudaFuncGetAttributes(&fa, k_downward_root<float>);
   cudaFuncGetAttributes(&fa, k_downward<double>);
   cudaFuncGetAttributes(&fa, k_downward<float>);
+  cudaFuncGetAttributes(&fa, k_downward_cell<double>);
+  cudaFuncGetAttributes(&fa, k_downward_cell<float>);
   size_t sm = downward_smem(g, prec);
   if (prec == 0) raise_dynamic_smem((const void*)k_downward<double>, sm);
   else raise_dynamic_smem((const void*)k_downward<float>, sm);
@@ -744,8 +802,15 @@ void fmm_prepare(const Geo& g, int prec) {
 void fmm_downward(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
   if (prec == 0) k_downward_root<double><<<1, 128, 0, s>>>(g, d);
   else k_downward_root<float><<<1, 128, 0, s>>>(g, d);
-  size_t sm = downward_smem(g, prec);
+  const size_t sm = downward_smem(g, prec);
+  const size_t smc = (size_t)2 * (g.p + 1) * (g.p + 1) * (prec == 0 ? sizeof(double2) : sizeof(float2));
   for (int l = 2; l <= g.L; l++) {
+    if (l < g.L) {  // few cells: one CTA per cell
+      const unsigned cells = 1u << (3 * (l - 1));
+      if (prec == 0) k_downward_cell<double><<<cells, 128, smc, s>>>(g, d, l);
+      else k_downward_cell<float><<<cells, 128, smc, s>>>(g, d, l);
+      continue;
+    }
     unsigned npar = 1u << (3 * (l - 2));
     unsigned blocks = (npar + DW_PAR - 1) / DW_PAR;
     if (prec == 0)

@@ -99,10 +99,15 @@ __device__ __forceinline__ T l2p_eval(const C* L, int p, T x, T y, T z) {
 
 
 // ------------------------------------------------------------------ near-field helpers
-// FP32: sources staged as pairs (A = {x_2j, x_2j+1, y_2j, y_2j+1},
-// B = {z_2j, z_2j+1, q_2j, q_2j+1}) so that one packed FP32x2 instruction
-// (FADD2 / FMUL2 / FFMA2) serves two pair interactions; 1/r from the MUFU
-// rsqrt.approx (relative error < 2^-22).  FP64: one source per iteration.
+// FP32 (lattice proposals): coordinates in lattice units relative to the leaf
+// corner, so that for source s and target t every term of
+// |s - t|^2 = w_s + w_t - 2 s.t (w = |.|^2) is an integer far below 2^24 and
+// the squared distance is exact.  That form takes four FP32 operations per
+// pair instead of six.  Sources are staged as pairs (A = {x_2j, x_2j+1, y_2j,
+// y_2j+1}, B = {z_2j, z_2j+1, w_2j, w_2j+1}, Q = {q_2j, q_2j+1}) so that one
+// packed FP32x2 instruction (FADD2 / FFMA2) serves two pair interactions; 1/r
+// from the MUFU rsqrt.approx (relative error < 2^-22), scaled by 1/h once per
+// target.  FP64: physical coordinates, one source per iteration.
 __device__ __forceinline__ float rsqrt_mufu(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -112,201 +117,111 @@ __device__ __forceinline__ float rsqrt_mufu(float x) {
 template <typename T> struct NearField;
 
 template <> struct NearField<float> {
-  float2 a0, a1;
-  __device__ __forceinline__ void reset() { a0 = a1 = make_float2(0.f, 0.f); }
-  static __device__ __forceinline__ size_t bytes(int chunk) { return (size_t)(chunk / 2 + 1) * 32; }
-  static __device__ __forceinline__ void stage(unsigned char* sm, int chunk, int e, float4 v) {
-    float* A = (float*)sm;
-    float* B = (float*)(sm + (size_t)(chunk / 2 + 1) * 16);
-    int j = e >> 1, o = e & 1;
-    A[4 * j + o] = v.x;
-    A[4 * j + 2 + o] = v.y;
-    B[4 * j + o] = v.z;
-    B[4 * j + 2 + o] = v.w;
+  float2 c0, e0, c1, e1;  // target 0 and target 1, two accumulation chains each
+  __device__ __forceinline__ void reset() { c0 = e0 = c1 = e1 = make_float2(0.f, 0.f); }
+  // groups of four sources: {x0 x1 y0 y1} {z0 z1 w0 w1} {x2 x3 y2 y3} {z2 z3 w2 w3} {q0 q1 q2 q3}
+  static __host__ __device__ __forceinline__ size_t bytes(int chunk) { return (size_t)((chunk + 3) / 4 + 1) * 80; }
+  static __device__ __forceinline__ void stage(unsigned char* sm, int e, float x, float y, float z, float q) {
+    float* G = (float*)sm + 20 * (e >> 2);
+    const int r = e & 3, o = r & 1;
+    float* A = G + 8 * (r >> 1);
+    A[o] = x;
+    A[2 + o] = y;
+    A[4 + o] = z;
+    A[6 + o] = x * x + y * y + z * z;
+    G[16 + r] = q;
   }
-  static __device__ __forceinline__ void pad(unsigned char* sm, int chunk, int ns) {
-    if (ns & 1) stage(sm, chunk, ns, make_float4(1e18f, 1e18f, 1e18f, 0.f));
+  // fill the last group with chargeless sources far from every target
+  static __device__ __forceinline__ void pad(unsigned char* sm, int ns) {
+    for (int e = ns; e < ((ns + 3) & ~3); e++) stage(sm, e, 1024.f, 1024.f, 1024.f, 0.f);
+  }
+  struct Tgt {
+    float2 tx2, ty2, tz2, wt;  // -2 t and |t|^2, duplicated for the packed lanes
+  };
+  static __device__ __forceinline__ Tgt target(float tx, float ty, float tz) {
+    Tgt t;
+    t.tx2 = make_float2(-2.f * tx, -2.f * tx);
+    t.ty2 = make_float2(-2.f * ty, -2.f * ty);
+    t.tz2 = make_float2(-2.f * tz, -2.f * tz);
+    const float w = tx * tx + ty * ty + tz * tz;
+    t.wt = make_float2(w, w);
+    return t;
+  }
+  template <bool GUARD>
+  static __device__ __forceinline__ void pair2(const float4& A, const float4& B, float2 q, const Tgt& t, float2& acc) {
+    float2 r2 = __fadd2_rn(make_float2(B.z, B.w), t.wt);
+    r2 = __ffma2_rn(make_float2(A.x, A.y), t.tx2, r2);
+    r2 = __ffma2_rn(make_float2(A.z, A.w), t.ty2, r2);
+    r2 = __ffma2_rn(make_float2(B.x, B.y), t.tz2, r2);
+    float2 iv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+    if (GUARD) {
+      iv.x = r2.x > 0.f ? iv.x : 0.f;
+      iv.y = r2.y > 0.f ? iv.y : 0.f;
+    }
+    acc = __ffma2_rn(q, iv, acc);
   }
   template <bool GUARD, bool TWO>
-  __device__ __forceinline__ void run_(const unsigned char* sm, int chunk, int ns, float x0, float y0, float z0,
-                                       float x1, float y1, float z1) {
-    const float4* A = (const float4*)sm;
-    const float4* B = (const float4*)(sm + (size_t)(chunk / 2 + 1) * 16);
-    const int np = (ns + 1) >> 1;
-    const float2 nx0 = make_float2(-x0, -x0), ny0 = make_float2(-y0, -y0), nz0 = make_float2(-z0, -z0);
-    const float2 nx1 = make_float2(-x1, -x1), ny1 = make_float2(-y1, -y1), nz1 = make_float2(-z1, -z1);
-    float2 c0 = a0, c1 = a1;
-#pragma unroll 4
-    for (int j = 0; j < np; j++) {
-      float4 a = A[j], b = B[j];
-      float2 sx = make_float2(a.x, a.y), sy = make_float2(a.z, a.w);
-      float2 sz = make_float2(b.x, b.y), sq = make_float2(b.z, b.w);
-      {
-        float2 dx = __fadd2_rn(sx, nx0), dy = __fadd2_rn(sy, ny0), dz = __fadd2_rn(sz, nz0);
-        float2 r2 = __fmul2_rn(dx, dx);
-        r2 = __ffma2_rn(dy, dy, r2);
-        r2 = __ffma2_rn(dz, dz, r2);
-        float2 iv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-        if (GUARD) {
-          iv.x = r2.x > 0.f ? iv.x : 0.f;
-          iv.y = r2.y > 0.f ? iv.y : 0.f;
-        }
-        c0 = __ffma2_rn(sq, iv, c0);
-      }
+  __device__ __forceinline__ void run_range(const float4* G, int ng, const Tgt& t0, const Tgt& t1) {
+    float2 a = c0, b = e0, c = c1, d = e1;
+#pragma unroll 2
+    for (int g = 0; g < ng; g++, G += 5) {
+      const float4 A0 = G[0], B0 = G[1], A1 = G[2], B1 = G[3], Q = G[4];
+      const float2 q01 = make_float2(Q.x, Q.y), q23 = make_float2(Q.z, Q.w);
+      pair2<GUARD>(A0, B0, q01, t0, a);
+      pair2<GUARD>(A1, B1, q23, t0, b);
       if (TWO) {
-        float2 dx = __fadd2_rn(sx, nx1), dy = __fadd2_rn(sy, ny1), dz = __fadd2_rn(sz, nz1);
-        float2 r2 = __fmul2_rn(dx, dx);
-        r2 = __ffma2_rn(dy, dy, r2);
-        r2 = __ffma2_rn(dz, dz, r2);
-        float2 iv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-        if (GUARD) {
-          iv.x = r2.x > 0.f ? iv.x : 0.f;
-          iv.y = r2.y > 0.f ? iv.y : 0.f;
-        }
-        c1 = __ffma2_rn(sq, iv, c1);
+        pair2<GUARD>(A0, B0, q01, t1, c);
+        pair2<GUARD>(A1, B1, q23, t1, d);
       }
     }
-    a0 = c0;
-    a1 = c1;
+    c0 = a;
+    e0 = b;
+    c1 = c;
+    e1 = d;
   }
-  __device__ __forceinline__ void run(const unsigned char* sm, int chunk, int ns, bool guard, bool two, float x0,
-                                      float y0, float z0, float x1, float y1, float z1) {
-    if (guard) {
-      if (two) run_<true, true>(sm, chunk, ns, x0, y0, z0, x1, y1, z1);
-      else run_<true, false>(sm, chunk, ns, x0, y0, z0, x1, y1, z1);
+  // sources [0, nguard) may sit on a target (skip r2 = 0); the rest never do.
+  // Target 1 is evaluated only when two is set (warp-uniform).
+  __device__ __forceinline__ void run2(const unsigned char* sm, int ns, int nguard, bool two, float tx0, float ty0,
+                                       float tz0, float tx1, float ty1, float tz1) {
+    const int gg = (nguard + 3) >> 2, ng = (ns + 3) >> 2;
+    const float4* G = (const float4*)sm;
+    const Tgt t0 = target(tx0, ty0, tz0), t1 = target(tx1, ty1, tz1);
+    if (two) {
+      if (gg > 0) run_range<true, true>(G, gg, t0, t1);
+      if (ng > gg) run_range<false, true>(G + 5 * gg, ng - gg, t0, t1);
     } else {
-      if (two) run_<false, true>(sm, chunk, ns, x0, y0, z0, x1, y1, z1);
-      else run_<false, false>(sm, chunk, ns, x0, y0, z0, x1, y1, z1);
+      if (gg > 0) run_range<true, false>(G, gg, t0, t1);
+      if (ng > gg) run_range<false, false>(G + 5 * gg, ng - gg, t0, t1);
     }
   }
-  // sources [0, nguard) may sit on a target (skip r2 = 0); the rest never do
-  __device__ __forceinline__ void run2(const unsigned char* sm, int chunk, int ns, int nguard, bool two, float x0,
-                                       float y0, float z0, float x1, float y1, float z1) {
-    const int gp = (nguard + 1) >> 1, np = (ns + 1) >> 1;
-    const float4* A = (const float4*)sm;
-    const float4* B = (const float4*)(sm + (size_t)(chunk / 2 + 1) * 16);
-    if (gp > 0) {
-      if (two) run_range<true, true>(A, B, 0, gp, x0, y0, z0, x1, y1, z1);
-      else run_range<true, false>(A, B, 0, gp, x0, y0, z0, x1, y1, z1);
-    }
-    if (np > gp) {
-      if (two) run_range<false, true>(A, B, gp, np, x0, y0, z0, x1, y1, z1);
-      else run_range<false, false>(A, B, gp, np, x0, y0, z0, x1, y1, z1);
-    }
+  __device__ __forceinline__ float sum(int side) const {
+    const float2 s = side ? __fadd2_rn(c1, e1) : __fadd2_rn(c0, e0);
+    return s.x + s.y;
   }
-  template <bool GUARD, bool TWO>
-  __device__ __forceinline__ void run_range(const float4* A, const float4* B, int j0, int j1, float x0, float y0,
-                                            float z0, float x1, float y1, float z1) {
-    const float2 nx0 = make_float2(-x0, -x0), ny0 = make_float2(-y0, -y0), nz0 = make_float2(-z0, -z0);
-    const float2 nx1 = make_float2(-x1, -x1), ny1 = make_float2(-y1, -y1), nz1 = make_float2(-z1, -z1);
-    float2 c0 = a0, c1 = a1, e0 = make_float2(0.f, 0.f), e1 = make_float2(0.f, 0.f);
-    int j = j0;
-    for (; j + 1 < j1; j += 2) {  // two source pairs per iteration, separate accumulators
-#pragma unroll
-      for (int u = 0; u < 2; u++) {
-        float4 a = A[j + u], b = B[j + u];
-        float2 sx = make_float2(a.x, a.y), sy = make_float2(a.z, a.w);
-        float2 sz = make_float2(b.x, b.y), sq = make_float2(b.z, b.w);
-        float2 dx = __fadd2_rn(sx, nx0), dy = __fadd2_rn(sy, ny0), dz = __fadd2_rn(sz, nz0);
-        float2 r2 = __fmul2_rn(dx, dx);
-        r2 = __ffma2_rn(dy, dy, r2);
-        r2 = __ffma2_rn(dz, dz, r2);
-        float2 iv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-        if (GUARD) {
-          iv.x = r2.x > 0.f ? iv.x : 0.f;
-          iv.y = r2.y > 0.f ? iv.y : 0.f;
-        }
-        if (u == 0) c0 = __ffma2_rn(sq, iv, c0);
-        else e0 = __ffma2_rn(sq, iv, e0);
-        if (TWO) {
-          float2 dx1 = __fadd2_rn(sx, nx1), dy1 = __fadd2_rn(sy, ny1), dz1 = __fadd2_rn(sz, nz1);
-          float2 q2 = __fmul2_rn(dx1, dx1);
-          q2 = __ffma2_rn(dy1, dy1, q2);
-          q2 = __ffma2_rn(dz1, dz1, q2);
-          float2 iw = make_float2(rsqrt_mufu(q2.x), rsqrt_mufu(q2.y));
-          if (GUARD) {
-            iw.x = q2.x > 0.f ? iw.x : 0.f;
-            iw.y = q2.y > 0.f ? iw.y : 0.f;
-          }
-          if (u == 0) c1 = __ffma2_rn(sq, iw, c1);
-          else e1 = __ffma2_rn(sq, iw, e1);
-        }
-      }
-    }
-    for (; j < j1; j++) {
-      float4 a = A[j], b = B[j];
-      float2 sx = make_float2(a.x, a.y), sy = make_float2(a.z, a.w);
-      float2 sz = make_float2(b.x, b.y), sq = make_float2(b.z, b.w);
-      float2 dx = __fadd2_rn(sx, nx0), dy = __fadd2_rn(sy, ny0), dz = __fadd2_rn(sz, nz0);
-      float2 r2 = __fmul2_rn(dx, dx);
-      r2 = __ffma2_rn(dy, dy, r2);
-      r2 = __ffma2_rn(dz, dz, r2);
-      float2 iv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-      if (GUARD) {
-        iv.x = r2.x > 0.f ? iv.x : 0.f;
-        iv.y = r2.y > 0.f ? iv.y : 0.f;
-      }
-      c0 = __ffma2_rn(sq, iv, c0);
-      if (TWO) {
-        float2 dx1 = __fadd2_rn(sx, nx1), dy1 = __fadd2_rn(sy, ny1), dz1 = __fadd2_rn(sz, nz1);
-        float2 q2 = __fmul2_rn(dx1, dx1);
-        q2 = __ffma2_rn(dy1, dy1, q2);
-        q2 = __ffma2_rn(dz1, dz1, q2);
-        float2 iw = make_float2(rsqrt_mufu(q2.x), rsqrt_mufu(q2.y));
-        if (GUARD) {
-          iw.x = q2.x > 0.f ? iw.x : 0.f;
-          iw.y = q2.y > 0.f ? iw.y : 0.f;
-        }
-        c1 = __ffma2_rn(sq, iw, c1);
-      }
-    }
-    a0 = __fadd2_rn(c0, e0);
-    a1 = __fadd2_rn(c1, e1);
-  }
-  __device__ __forceinline__ float sum(int side) const { return side ? a1.x + a1.y : a0.x + a0.y; }
 };
 
 template <> struct NearField<double> {
   double a0, a1;
   __device__ __forceinline__ void reset() { a0 = a1 = 0.0; }
-  static __device__ __forceinline__ size_t bytes(int chunk) { return (size_t)chunk * 32; }
-  static __device__ __forceinline__ void stage(unsigned char* sm, int chunk, int e, double4_32a v) {
-    ((double4_32a*)sm)[e] = v;
-  }
-  static __device__ __forceinline__ void pad(unsigned char*, int, int) {}
-  __device__ __forceinline__ void run(const unsigned char* sm, int chunk, int ns, bool guard, bool two, double x0,
-                                      double y0, double z0, double x1, double y1, double z1) {
+  static __host__ __device__ __forceinline__ size_t bytes(int chunk) { return (size_t)chunk * 32; }
+  static __device__ __forceinline__ void stage(unsigned char* sm, int e, double4_32a v) { ((double4_32a*)sm)[e] = v; }
+  static __device__ __forceinline__ void pad(unsigned char*, int) {}
+  __device__ __forceinline__ void run2(const unsigned char* sm, int ns, int nguard, bool two, double x0, double y0,
+                                       double z0, double x1, double y1, double z1) {
     const double4_32a* src = (const double4_32a*)sm;
     double s0 = a0, s1 = a1;
     for (int j = 0; j < ns; j++) {
-      double4_32a v = src[j];
-      double dx0 = v.x - x0, dy0 = v.y - y0, dz0 = v.z - z0;
-      double dx1 = v.x - x1, dy1 = v.y - y1, dz1 = v.z - z1;
-      double q0 = dx0 * dx0 + dy0 * dy0 + dz0 * dz0;
-      double q1 = dx1 * dx1 + dy1 * dy1 + dz1 * dz1;
-      double i0 = (!guard || q0 > 0.0) ? rsqrt(q0) : 0.0;
-      double i1 = (!guard || q1 > 0.0) ? rsqrt(q1) : 0.0;
-      s0 += v.w * i0;
-      if (two) s1 += v.w * i1;
-    }
-    a0 = s0;
-    a1 = s1;
-  }
-  __device__ __forceinline__ void run2(const unsigned char* sm, int chunk, int ns, int nguard, bool two, double x0,
-                                       double y0, double z0, double x1, double y1, double z1) {
-    const double4_32a* src = (const double4_32a*)sm;
-    double s0 = a0, s1 = a1;
-    for (int j = 0; j < ns; j++) {
-      double4_32a v = src[j];
-      const bool guard = j < nguard;
-      double dx0 = v.x - x0, dy0 = v.y - y0, dz0 = v.z - z0;
-      double dx1 = v.x - x1, dy1 = v.y - y1, dz1 = v.z - z1;
-      double q0 = dx0 * dx0 + dy0 * dy0 + dz0 * dz0;
-      double q1 = dx1 * dx1 + dy1 * dy1 + dz1 * dz1;
-      double i0 = (!guard || q0 > 0.0) ? rsqrt(q0) : 0.0;
-      double i1 = (!guard || q1 > 0.0) ? rsqrt(q1) : 0.0;
-      s0 += v.w * i0;
-      if (two) s1 += v.w * i1;
+      const double4_32a v = src[j];
+      double dx = v.x - x0, dy = v.y - y0, dz = v.z - z0;
+      double r2 = dx * dx + dy * dy + dz * dz;
+      s0 += (j >= nguard || r2 > 0.0) ? v.w * rsqrt(r2) : 0.0;
+      if (two) {
+        dx = v.x - x1;
+        dy = v.y - y1;
+        dz = v.z - z1;
+        r2 = dx * dx + dy * dy + dz * dz;
+        s1 += (j >= nguard || r2 > 0.0) ? v.w * rsqrt(r2) : 0.0;
+      }
     }
     a0 = s0;
     a1 = s1;
@@ -365,46 +280,74 @@ template <> __device__ __forceinline__ double l2p_point<double, double2>(const d
 // the leaf, whether the hopping charge sits in this leaf or in one of its six
 // face neighbours.  Sources are the charges of the 27 neighbouring leaves
 // (periodically wrapped images), staged in shared memory.
-#define PROP_THREADS 256
+#define PROP_THREADS 128
 
 template <typename T> __device__ __forceinline__ T qnan();
 template <> __device__ __forceinline__ float qnan<float>() { return __int_as_float(0x7fc00000); }
 template <> __device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
 
+// Site coordinate of a lattice position (i + 1/2) h: floor(x / h) = i exactly
+// for the lattice sizes accepted at init (E^3 < 2^31).
+__device__ __forceinline__ int lattice_coord(float x, float ih) { return (int)floorf(x * ih); }
+__device__ __forceinline__ int lattice_coord(double x, double ih) { return (int)floor(x * ih); }
+
+// one staged source: FP32 in lattice units relative to the leaf corner, FP64
+// in physical coordinates; (shx, shy, shz) is the periodic image shift in sites
+__device__ __forceinline__ void stage_source(unsigned char* src, int e, float4 v, int shx, int shy, int shz, int gx0,
+                                             int gy0, int gz0, float ih, float) {
+  NearField<float>::stage(src, e, (float)(lattice_coord(v.x, ih) + shx - gx0),
+                          (float)(lattice_coord(v.y, ih) + shy - gy0), (float)(lattice_coord(v.z, ih) + shz - gz0),
+                          v.w);
+}
+__device__ __forceinline__ void stage_source(unsigned char* src, int e, double4_32a v, int shx, int shy, int shz, int,
+                                             int, int, double, double h) {
+  v.x += (double)shx * h;
+  v.y += (double)shy * h;
+  v.z += (double)shz * h;
+  NearField<double>::stage(src, e, v);
+}
+
+// coordinate c + dc (|dc| <= 1) wrapped into [0, E)
+__device__ __forceinline__ int wrap1(int c, int E) { return c < 0 ? c + E : (c >= E ? c - E : c); }
+
 // Evaluation is per distinct site of the leaf: the potential at a site is
 // needed once even when several charges propose to hop there, and at an own
 // charge's site it is that charge's old-position potential (the pair at
-// distance 0 is skipped).  Phases: (1) occupancy bits; (2) needed-site bits,
-// masked hops written; (3) compact site list; (4) near-field sums + L2P per
-// site, one site per thread per round; (5) write-out by re-enumerating the
-// same hops.  Potentials are written in precision T (FP32 arrays in the mixed
-// form, FP64 arrays in the FP64 form).
+// distance 0 is skipped).  Phases: (0) the 27 neighbour leaves (slot base,
+// count, image shift); (1) occupancy bits; (2) needed-site bits, masked hops
+// written; (3) compact site list; (4) near-field sums + L2P per site, one site
+// per thread per round, sources staged one warp per neighbour leaf; (5)
+// write-out by re-enumerating the same hops.  Site coordinates come from the
+// slot positions (coalesced), user indices only where an output is written.
+// Potentials are written in precision T (FP32 arrays in the mixed form, FP64
+// arrays in the FP64 form).
 template <typename T>
-__global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, const Dev d, int pmax, int chunk) {
+__global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, const Dev d, int chunk) {
   typedef typename cplx<T>::type C;
   typedef typename vec4<T>::type V4;
   extern __shared__ __align__(32) unsigned char sm[];
-  (void)pmax;
   const int W = g.W, W3 = W * W * W;
   const int nbw = (W3 + 31) / 32;
   unsigned char* src = sm;
   C* Lc = (C*)(sm + NearField<T>::bytes(chunk));  // 8-byte aligned
-  int64_t* owner = (int64_t*)(Lc + g.P);            // [7] slot base of this leaf and its face neighbours
-  T* phis = (T*)(owner + 8);                        // [W3] potential per local site
+  int64_t* nb_base = (int64_t*)(Lc + g.P);          // [27] slot base: own leaf, then the 26 others
+  int* nb_off = (int*)(nb_base + 27);               // [28] first staged element of each leaf
+  int* nb_sh = nb_off + 28;                         // [27 * 3] image shift in sites
+  int* nb_cnt = nb_sh + 81;                         // [27] charges per leaf
+  T* phis = (T*)(nb_cnt + 27);                      // [W3] potential per local site
   uint32_t* bits = (uint32_t*)(phis + W3);          // [nbw] occupied sites
   uint32_t* need = bits + nbw;                      // [nbw] sites where a potential is needed
   int* woff = (int*)(need + nbw);                   // [nbw + 1] prefix of needed sites per word
   uint16_t* sites = (uint16_t*)(woff + nbw + 1);    // [W3] needed local sites, compacted
-  int* ctr = (int*)(sites + ((W3 + 1) & ~1));       // [1..27] source prefix offsets
   T* out_old = (T*)((sizeof(T) == 4) ? (void*)d.phi_old32 : (void*)d.phi_old);
   T* out_new = (T*)((sizeof(T) == 4) ? (void*)d.phi_new32 : (void*)d.phi_new);
 
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   const int nL = g.nL, E = g.E;
   const int64_t leaf = blockIdx.x;
   const int lx = (int)(leaf % nL), ly = (int)((leaf / nL) % nL), lz = (int)(leaf / ((int64_t)nL * nL));
   const int gx0 = lx * W, gy0 = ly * W, gz0 = lz * W;
-  const T h = (T)g.h;
+  const T h = (T)g.h, ih = (T)(1.0 / g.h);
   const V4* spos = (const V4*)((sizeof(T) == 4) ? (const void*)d.spos32 : (const void*)d.spos64);
 
   const C* Pe = (const C*)d.Peff + (g.cell_off[g.L] + leaf) * g.P;
@@ -413,41 +356,63 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
     bits[c] = 0u;
     need[c] = 0u;
   }
-  if (tid == 0) owner[0] = leaf * g.cap;
-  if (tid >= 1 && tid <= KMC_NHOP) {
-    int f = tid - 1;
-    int mx = (lx + c_hop[f][0] + nL) % nL, my = (ly + c_hop[f][1] + nL) % nL, mz = (lz + c_hop[f][2] + nL) % nL;
-    owner[tid] = (mx + (int64_t)nL * (my + (int64_t)nL * mz)) * g.cap;
+  // (0) list entry 0 is this leaf, entries 1..26 the other neighbours in
+  // 27-neighbourhood order (x fastest), centre skipped
+  if (tid < 27) {
+    const int qq = tid == 0 ? 13 : (tid <= 13 ? tid - 1 : tid);
+    const int ux = lx + qq % 3 - 1, uy = ly + (qq / 3) % 3 - 1, uz = lz + qq / 9 - 1;
+    const int sx = (ux + nL) % nL, sy = (uy + nL) % nL, sz = (uz + nL) % nL;
+    const int64_t nleaf = sx + (int64_t)nL * (sy + (int64_t)nL * sz);
+    nb_base[tid] = nleaf * g.cap;
+    nb_cnt[tid] = d.cnt[nleaf];
+    nb_sh[3 * tid] = (ux - sx) * W;
+    nb_sh[3 * tid + 1] = (uy - sy) * W;
+    nb_sh[3 * tid + 2] = (uz - sz) * W;
   }
   __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int q = 0; q < 27; q++) {
+      nb_off[q] = acc;
+      acc += nb_cnt[q];
+    }
+    nb_off[27] = acc;
+  }
 
   // (1) occupancy bitmap of this leaf's sites
-  const int cnt_own = d.cnt[leaf];
-  const int64_t base_own = leaf * g.cap;
+  const int cnt_own = nb_cnt[0];
+  const int64_t base_own = nb_base[0];
   for (int j = tid; j < cnt_own; j += blockDim.x) {
-    int s = d.site[d.uid[base_own + j]];
-    int ls = (s % E - gx0) + W * ((s / E) % E - gy0 + W * (s / (E * E) - gz0));
+    const V4 v = spos[base_own + j];
+    const int ls = (lattice_coord(v.x, ih) - gx0) + W * (lattice_coord(v.y, ih) - gy0 + W * (lattice_coord(v.z, ih) - gz0));
     atomicOr(&bits[ls >> 5], 1u << (ls & 31));
     atomicOr(&need[ls >> 5], 1u << (ls & 31));
   }
   __syncthreads();
 
   // (2) hop targets inside this leaf: own hops and hops entering from the six
-  // face neighbours (f = 0 own leaf, 1..6 neighbour f-1 hopping in direction f^1)
+  // face neighbours (f = 0 own leaf, f = 1..6 the neighbour across face f-1,
+  // hopping in direction (f-1)^1)
   for (int f = 0; f <= KMC_NHOP; f++) {
-    const int64_t mb = owner[f];
-    const int cm = f ? d.cnt[mb / g.cap] : cnt_own;
+    int li = 0;
+    if (f) {
+      const int* o = c_hop[f - 1];
+      const int qq = (o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1);
+      li = qq < 13 ? qq + 1 : qq;
+    }
+    const int64_t mb = nb_base[li];
+    const int cm = nb_cnt[li];
     for (int j = tid; j < cm; j += blockDim.x) {
-      int32_t u = d.uid[mb + j];
-      int s = d.site[u];
-      int gx = s % E, gy = (s / E) % E, gz = s / (E * E);
-      int k0 = f ? ((f - 1) ^ 1) : 0, k1 = f ? k0 + 1 : KMC_NHOP;
+      const V4 v = spos[mb + j];
+      const int gx = lattice_coord(v.x, ih), gy = lattice_coord(v.y, ih), gz = lattice_coord(v.z, ih);
+      const int k0 = f ? ((f - 1) ^ 1) : 0, k1 = f ? k0 + 1 : KMC_NHOP;
       for (int k = k0; k < k1; k++) {
-        int tx = (gx + c_hop[k][0] + E) % E, ty = (gy + c_hop[k][1] + E) % E, tz = (gz + c_hop[k][2] + E) % E;
+        const int tx = wrap1(gx + c_hop[k][0], E), ty = wrap1(gy + c_hop[k][1], E), tz = wrap1(gz + c_hop[k][2], E);
         int ux = tx - gx0, uy = ty - gy0, uz = tz - gz0;
         if (ux < 0 || ux >= W || uy < 0 || uy >= W || uz < 0 || uz >= W) continue;  // another leaf's CTA
         int lt = ux + W * (uy + W * uz);
         if (bits[lt >> 5] & (1u << (lt & 31))) {
+          const int32_t u = d.uid[mb + j];
           d.mask[6 * (int64_t)u + k] = 0;
           out_new[6 * (int64_t)u + k] = qnan<T>();
         } else {
@@ -455,20 +420,6 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
         }
       }
     }
-  }
-  // source offsets of the 26 other neighbour leaves (fixed order)
-  if (tid == 0) {
-    int off = 0, q = 0;
-    for (int oz = -1; oz <= 1; oz++)
-      for (int oy = -1; oy <= 1; oy++)
-        for (int ox = -1; ox <= 1; ox++) {
-          if (!ox && !oy && !oz) continue;
-          int sx = (lx + ox + nL) % nL, sy = (ly + oy + nL) % nL, sz = (lz + oz + nL) % nL;
-          ctr[1 + q] = off;
-          off += d.cnt[sx + (int64_t)nL * (sy + (int64_t)nL * sz)];
-          q++;
-        }
-    ctr[27] = off;
   }
   __syncthreads();
   // (3) compact the needed sites (ascending local index)
@@ -493,77 +444,75 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
   __syncthreads();
   const int nsites = woff[nbw];
 
-  // (4) near-field pair sums and L2P, one site per thread per round.  Sources:
-  // own leaf first (pairs at distance 0 skipped), then the 26 other leaves,
-  // streamed in chunks.
-  const int nsrc_other = ctr[27];
-  const int ntot = cnt_own + nsrc_other;
+  // (4) near-field pair sums and L2P, two sites per thread per round (sites
+  // b and b + blockDim).  Sources: own leaf first (pairs at distance 0
+  // skipped), then the 26 other leaves, streamed in chunks.
+  const int ntot = nb_off[27];
   const int npass = (ntot + chunk - 1) / chunk;
-  for (int rb = 0; rb < nsites; rb += blockDim.x) {
-    const int b0 = rb + tid;
-    T x0 = (T)1e18, y0 = (T)1e18, z0 = (T)1e18;
-    int l0 = 0;
-    if (b0 < nsites) {
-      l0 = sites[b0];
-      x0 = ((T)(gx0 + l0 % W) + (T)0.5) * h;
-      y0 = ((T)(gy0 + (l0 / W) % W) + (T)0.5) * h;
-      z0 = ((T)(gz0 + l0 / (W * W)) + (T)0.5) * h;
-    }
+  for (int rb = 0; rb < nsites; rb += 2 * blockDim.x) {
+    const int b0 = rb + tid, b1 = b0 + blockDim.x;
+    const int l0 = b0 < nsites ? sites[b0] : 0, l1 = b1 < nsites ? sites[b1] : 0;
+    const int ix0 = l0 % W, iy0 = (l0 / W) % W, iz0 = l0 / (W * W);
+    const int ix1 = l1 % W, iy1 = (l1 / W) % W, iz1 = l1 / (W * W);
     const bool one = __any_sync(0xffffffffu, b0 < nsites);
+    const bool two = __any_sync(0xffffffffu, b1 < nsites);
     NearField<T> nf;
     nf.reset();
     for (int pass = 0; pass < npass; pass++) {
       const int c0 = pass * chunk;
       const int ns = min(chunk, ntot - c0);
       if (npass > 1 || rb > 0) __syncthreads();  // previous pass / round done with the staging area
-      for (int e = tid; e < ns; e += blockDim.x) {
-        const int ge = c0 + e;
-        V4 v;
-        if (ge < cnt_own) {
-          v = spos[base_own + ge];
-        } else {
-          const int go = ge - cnt_own;
-          int q = 0;
-          while (q < 25 && ctr[2 + q] <= go) q++;
-          int qq = q >= 13 ? q + 1 : q;  // skip the centre in the 27-neighbourhood order
-          int ox = qq % 3 - 1, oy = (qq / 3) % 3 - 1, oz = qq / 9 - 1;
-          int ux = lx + ox, uy = ly + oy, uz = lz + oz;
-          int sx = (ux + nL) % nL, sy = (uy + nL) % nL, sz = (uz + nL) % nL;
-          int64_t sl = (sx + (int64_t)nL * (sy + (int64_t)nL * sz)) * g.cap + (go - ctr[1 + q]);
-          v = spos[sl];
-          v.x += (T)((ux - sx) * W) * h;
-          v.y += (T)((uy - sy) * W) * h;
-          v.z += (T)((uz - sz) * W) * h;
-        }
-        NearField<T>::stage(src, chunk, e, v);
+      for (int q = warp; q < 27; q += nwarp) {
+        const int lo = nb_off[q], hi = nb_off[q + 1];
+        const int a = max(lo, c0), b = min(hi, c0 + ns);
+        const int64_t sb = nb_base[q] - lo;
+        const int shx = nb_sh[3 * q], shy = nb_sh[3 * q + 1], shz = nb_sh[3 * q + 2];
+        for (int e = a + lane; e < b; e += 32)
+          stage_source(src, e - c0, spos[sb + e], shx, shy, shz, gx0, gy0, gz0, ih, h);
       }
-      if (tid == 0) NearField<T>::pad(src, chunk, ns);
+      if (tid == 0) NearField<T>::pad(src, ns);
       __syncthreads();
       if (one) {
         const int nguard = max(0, min(cnt_own - c0, ns));  // own-leaf sources in this pass
-        nf.run2(src, chunk, ns, nguard, false, x0, y0, z0, x0, y0, z0);
+        if (sizeof(T) == 4)
+          nf.run2(src, ns, nguard, two, (T)ix0, (T)iy0, (T)iz0, (T)ix1, (T)iy1, (T)iz1);
+        else
+          nf.run2(src, ns, nguard, two, ((T)(gx0 + ix0) + (T)0.5) * h, ((T)(gy0 + iy0) + (T)0.5) * h,
+                  ((T)(gz0 + iz0) + (T)0.5) * h, ((T)(gx0 + ix1) + (T)0.5) * h, ((T)(gy0 + iy1) + (T)0.5) * h,
+                  ((T)(gz0 + iz1) + (T)0.5) * h);
       }
     }
+    const T hw = (T)(0.5 * W);
     if (b0 < nsites) {
-      T x = ((T)(l0 % W) + (T)0.5 - (T)(0.5 * W)) * h;
-      T y = ((T)((l0 / W) % W) + (T)0.5 - (T)(0.5 * W)) * h;
-      T z = ((T)(l0 / (W * W)) + (T)0.5 - (T)(0.5 * W)) * h;
-      phis[l0] = nf.sum(0) + l2p_point<T, C>(Lc, g.p, x, y, z);
+      const T near = sizeof(T) == 4 ? nf.sum(0) * ih : nf.sum(0);
+      phis[l0] = near + l2p_point<T, C>(Lc, g.p, ((T)ix0 + (T)0.5 - hw) * h, ((T)iy0 + (T)0.5 - hw) * h,
+                                        ((T)iz0 + (T)0.5 - hw) * h);
+    }
+    if (b1 < nsites) {
+      const T near = sizeof(T) == 4 ? nf.sum(1) * ih : nf.sum(1);
+      phis[l1] = near + l2p_point<T, C>(Lc, g.p, ((T)ix1 + (T)0.5 - hw) * h, ((T)iy1 + (T)0.5 - hw) * h,
+                                        ((T)iz1 + (T)0.5 - hw) * h);
     }
   }
   __syncthreads();
   // (5) write-out: old-position potentials and unmasked hop potentials
   for (int f = 0; f <= KMC_NHOP; f++) {
-    const int64_t mb = owner[f];
-    const int cm = f ? d.cnt[mb / g.cap] : cnt_own;
+    int li = 0;
+    if (f) {
+      const int* o = c_hop[f - 1];
+      const int qq = (o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1);
+      li = qq < 13 ? qq + 1 : qq;
+    }
+    const int64_t mb = nb_base[li];
+    const int cm = nb_cnt[li];
     for (int j = tid; j < cm; j += blockDim.x) {
-      int32_t u = d.uid[mb + j];
-      int s = d.site[u];
-      int gx = s % E, gy = (s / E) % E, gz = s / (E * E);
+      const int32_t u = d.uid[mb + j];
+      const V4 v = spos[mb + j];
+      const int gx = lattice_coord(v.x, ih), gy = lattice_coord(v.y, ih), gz = lattice_coord(v.z, ih);
       if (f == 0) out_old[u] = phis[(gx - gx0) + W * ((gy - gy0) + W * (gz - gz0))];
-      int k0 = f ? ((f - 1) ^ 1) : 0, k1 = f ? k0 + 1 : KMC_NHOP;
+      const int k0 = f ? ((f - 1) ^ 1) : 0, k1 = f ? k0 + 1 : KMC_NHOP;
       for (int k = k0; k < k1; k++) {
-        int tx = (gx + c_hop[k][0] + E) % E, ty = (gy + c_hop[k][1] + E) % E, tz = (gz + c_hop[k][2] + E) % E;
+        const int tx = wrap1(gx + c_hop[k][0], E), ty = wrap1(gy + c_hop[k][1], E), tz = wrap1(gz + c_hop[k][2], E);
         int ux = tx - gx0, uy = ty - gy0, uz = tz - gz0;
         if (ux < 0 || ux >= W || uy < 0 || uy >= W || uz < 0 || uz >= W) continue;
         int lt = ux + W * (uy + W * uz);
@@ -575,21 +524,21 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
   }
 }
 
-static size_t propose_smem(const Geo& g, int prec, int pmax, int chunk) {
-  size_t ts = prec == 0 ? 8 : 4;
-  int W3 = g.W * g.W * g.W;
-  int nbw = (W3 + 31) / 32;
-  size_t srcb = prec == 0 ? (size_t)chunk * 32 : (size_t)(chunk / 2 + 1) * 32;
-  (void)pmax;
-  return srcb + 2 * ts * (size_t)g.P + 8 * 8 + ts * (size_t)W3 + 4 * (size_t)(3 * nbw + 1) +
-         2 * (size_t)((W3 + 1) & ~1) + 4 * 32;
+static size_t propose_smem(const Geo& g, int prec, int chunk) {
+  const size_t ts = prec == 0 ? 8 : 4;
+  const int W3 = g.W * g.W * g.W;
+  const int nbw = (W3 + 31) / 32;
+  const size_t srcb = prec == 0 ? NearField<double>::bytes(chunk) : NearField<float>::bytes(chunk);
+  return srcb + 2 * ts * (size_t)g.P + 27 * 8 + (28 + 81 + 27) * 4 + ts * (size_t)W3 + 4 * (size_t)(3 * nbw + 1) +
+         2 * (size_t)((W3 + 1) & ~1);
 }
 
-static void propose_shape(const Geo& g, int* pmax, int* chunk) {
-  int W3 = g.W * g.W * g.W;
-  *pmax = W3 + 6 * W3 + 6 * g.W * g.W;  // every own charge, its hops, every entering hop
+// sources are streamed in chunks of at least 1024 (every neighbour leaf's
+// charges in one pass unless the neighbourhood is dense); even: FP32 sources
+// are staged in pairs
+static int propose_chunk(const Geo& g) {
   int c = 1024 > g.cap ? 1024 : g.cap;
-  *chunk = (c + 1) & ~1;  // even: FP32 sources are staged in pairs
+  return (c + 1) & ~1;
 }
 
 static void kmc_preload();
@@ -597,19 +546,17 @@ static void kmc_preload();
 void kmc_prepare(const Geo& g, int prec) {
   kmc_preload();
   if (g.E <= 0) return;
-  int pmax, chunk;
-  propose_shape(g, &pmax, &chunk);
-  size_t sm = propose_smem(g, prec, pmax, chunk);
+  const int chunk = propose_chunk(g);
+  const size_t sm = propose_smem(g, prec, chunk);
   if (prec == 0) raise_dynamic_smem((const void*)k_propose_lattice<double>, sm);
   else raise_dynamic_smem((const void*)k_propose_lattice<float>, sm);
 }
 
 void kmc_propose_lattice(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
-  int pmax, chunk;
-  propose_shape(g, &pmax, &chunk);
-  size_t sm = propose_smem(g, prec, pmax, chunk);
-  if (prec == 0) k_propose_lattice<double><<<(unsigned)g.ML, PROP_THREADS, sm, s>>>(g, d, pmax, chunk);
-  else k_propose_lattice<float><<<(unsigned)g.ML, PROP_THREADS, sm, s>>>(g, d, pmax, chunk);
+  const int chunk = propose_chunk(g);
+  const size_t sm = propose_smem(g, prec, chunk);
+  if (prec == 0) k_propose_lattice<double><<<(unsigned)g.ML, PROP_THREADS, sm, s>>>(g, d, chunk);
+  else k_propose_lattice<float><<<(unsigned)g.ML, PROP_THREADS, sm, s>>>(g, d, chunk);
 }
 
 // ------------------------------------------------------------------ dU, rates, block sums
@@ -633,101 +580,6 @@ __device__ __forceinline__ double widen_nonneg(float v) {
   return __longlong_as_double((long long)bits);
 }
 
-// One thread per event j = 6 i + k (coalesced reads of phi_new / mask and
-// writes of dU / rate); per-particle sums of the 6 rates (sequential in k) and
-// the block sum (sequential over the block's particles) are kept in the exact
-// order the selection walk uses.
-// MIXED: the assembly and the rate's mantissa in FP32 (the dU tolerance of the
-// mixed form is far above FP32 rounding), exponent range kept by an FP64 path
-// for rates below ~1e-33; FP64: every operation in FP64.
-#define FIN_EVENTS (KMC_NHOP * FIN_THREADS)
-template <bool MIXED>
-__global__ void __launch_bounds__(FIN_EVENTS) k_finalize(const Geo g, const Dev d) {
-  __shared__ double rs[FIN_EVENTS];
-  __shared__ double ts[FIN_THREADS];
-  const int64_t j = blockIdx.x * (int64_t)FIN_EVENTS + threadIdx.x;
-  double r = 0.0;
-  if (j < 6 * g.n) {
-    const int64_t i = j / 6;
-    const int k = (int)(j - 6 * i);
-    const int E = g.E;
-    const int s = d.site[i];
-    const int ax = k >> 1;
-    const int gc = ax == 0 ? s % E : (ax == 1 ? (s / E) % E : s / (E * E));
-    const int t = gc + ((k & 1) ? -1 : 1);
-    if (MIXED) {
-      float duf;
-      if (!d.mask[j]) {
-        duf = __int_as_float(0x7fc00000);
-      } else {
-        const float q = d.q32[i];
-        float dw = (k & 1) ? -(float)g.h : (float)g.h;
-        if (t < 0) dw += (float)g.a; else if (t >= E) dw -= (float)g.a;
-        duf = q * (d.phi_new32[j] - d.phi_old32[i]) - q * d.fdip[ax] * dw - q * q * d.selfc32[k];
-        const float x = fmaxf(duf, 0.f) * (float)(1.0 / g.kT);
-        r = (x < 75.f) ? widen_nonneg(ex2_approx(-x * 1.4426950408889634f)) : exp(-(double)x);
-      }
-      d.dU32[j] = duf;
-      d.rate[j] = r;
-    } else {
-      double du;
-      if (!d.mask[j]) {
-        du = __longlong_as_double(0x7ff8000000000000LL);
-      } else {
-        const double q = d.q[i];
-        double dw = (k & 1) ? -g.h : g.h;
-        if (t < 0) dw += g.a; else if (t >= E) dw -= g.a;
-        const double cM = 4.0 * M_PI / (3.0 * g.a * g.a * g.a) * d.dip[ax];
-        du = q * (d.phi_new[j] - d.phi_old[i]) - q * cM * dw - q * q * d.selfc[k];
-        r = exp(-fmax(du, 0.0) / g.kT);
-      }
-      d.dU[j] = du;
-      d.rate[j] = r;
-    }
-  }
-  rs[threadIdx.x] = r;
-  __syncthreads();
-  if (threadIdx.x < FIN_THREADS) {
-    const double* p = rs + KMC_NHOP * threadIdx.x;
-    double tsum = 0.0;
-    for (int kk = 0; kk < KMC_NHOP; kk++) tsum += p[kk];
-    ts[threadIdx.x] = tsum;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double b = 0.0;
-    for (int t2 = 0; t2 < FIN_THREADS; t2++) b += ts[t2];
-    d.bsum[blockIdx.x] = b;
-  }
-}
-
-// block sums of caller-provided rates (same block structure as k_finalize)
-__global__ void __launch_bounds__(FIN_THREADS) k_rate_bsum(const Geo g, const Dev d) {
-  __shared__ double ts[FIN_THREADS];
-  int64_t i = blockIdx.x * (int64_t)FIN_THREADS + threadIdx.x;
-  double tsum = 0.0;
-  if (i < g.n)
-    for (int k = 0; k < KMC_NHOP; k++) tsum += d.rate[6 * i + k];
-  ts[threadIdx.x] = tsum;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double b = 0.0;
-    for (int t = 0; t < FIN_THREADS; t++) b += ts[t];
-    d.bsum[blockIdx.x] = b;
-  }
-}
-
-void kmc_finalize_rates(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
-  unsigned nb = (unsigned)((g.n + FIN_THREADS - 1) / FIN_THREADS);
-  if (prec == 0) k_finalize<false><<<nb, FIN_EVENTS, 0, s>>>(g, d);
-  else k_finalize<true><<<nb, FIN_EVENTS, 0, s>>>(g, d);
-}
-
-// ------------------------------------------------------------------ selection
-// Q = sum of all rates; event j with R_{j-1} < Q zeta <= R_j (Algorithm 1),
-// where R is the cumulative sum taken block by block (block sums from the
-// finalize kernel, chunks of block sums per thread here); dt = -ln(xi)/Q.
-#define SEL_THREADS 1024
 // inclusive prefix sum over a shared array of n <= blockDim values
 // (Hillis-Steele, fixed order); every thread of the block must call it
 __device__ __forceinline__ void block_scan(double* v, int n) {
@@ -739,6 +591,133 @@ __device__ __forceinline__ void block_scan(double* v, int n) {
     __syncthreads();
   }
 }
+
+// rate = m 2^-e for m in (0.5, 1] and 0 <= e <= 1021, formed by moving the
+// IEEE-754 fields (exact; no FP64 arithmetic)
+__device__ __forceinline__ double scale_pow2(float m, int e) {
+  const uint32_t b = __float_as_uint(m);
+  const uint64_t bits = ((uint64_t)((b >> 23) + 896u - (uint32_t)e) << 52) | ((uint64_t)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+// One thread per particle i and its 6 events j = 6 i + k: phi_new and mask
+// read and dU and rate written as 8- and 16-byte vectors.  The per-particle
+// sum of the 6 rates is sequential in k and the block sum is the last element
+// of the same fixed-order scan the selection walk takes, so both see the same
+// cumulative sums.
+// MIXED: the assembly in FP32 (the dU tolerance of the mixed form is far
+// above FP32 rounding); rate = exp(-x) = 2^-y, y = x log2(e) = n + f, with
+// 2^-f from the MUFU ex2 and 2^-n put into the FP64 exponent, so rates keep
+// FP64 range down to 2^-1021 (an FP64 exp below that).  FP64: every
+// operation in FP64.
+template <bool MIXED>
+__global__ void __launch_bounds__(FIN_THREADS) k_finalize(const Geo g, const Dev d) {
+  __shared__ double ts[FIN_THREADS];
+  const int64_t i = blockIdx.x * (int64_t)FIN_THREADS + threadIdx.x;
+  double tsum = 0.0;
+  if (i < g.n) {
+    const int E = g.E;
+    const int s = d.site[i];
+    const int cx = s % E, cy = (s / E) % E, cz = s / (E * E);
+    const uint16_t* mk = (const uint16_t*)(d.mask + 6 * i);
+    const uint32_t mb = (uint32_t)mk[0] | ((uint32_t)mk[1] << 16);
+    const uint32_t mc = mk[2];
+    const uint32_t m6[6] = {mb & 0xff, (mb >> 8) & 0xff, (mb >> 16) & 0xff, mb >> 24, mc & 0xff, mc >> 8};
+    const int cc[3] = {cx, cy, cz};
+    double r6[6];
+    if (MIXED) {
+      const float q = d.q32[i], po = d.phi_old32[i], ikT = (float)(1.0 / g.kT);
+      const float2* pn = (const float2*)(d.phi_new32 + 6 * i);
+      float du[6];
+#pragma unroll
+      for (int k2 = 0; k2 < 3; k2++) {
+        const float2 v = pn[k2];
+#pragma unroll
+        for (int o = 0; o < 2; o++) {
+          const int k = 2 * k2 + o;
+          float dw = o ? -(float)g.h : (float)g.h;
+          if (o == 0 && cc[k2] == E - 1) dw -= (float)g.a;
+          if (o == 1 && cc[k2] == 0) dw += (float)g.a;
+          const float pv = o ? v.y : v.x;
+          float duf = __int_as_float(0x7fc00000);
+          double r = 0.0;
+          if (m6[k]) {
+            duf = q * (pv - po) - q * d.fdip[k2] * dw - q * q * d.selfc32[k];
+            const float y = fmaxf(duf, 0.f) * ikT * 1.4426950408889634f;
+            const float n = floorf(y);
+            const int e = __float_as_int(n + 12582912.0f) - 0x4B400000;  // exact integer value of n
+            r = e <= 1021 ? scale_pow2(ex2_approx(n - y), e) : exp(-(double)fmaxf(duf, 0.f) / g.kT);
+          }
+          du[k] = duf;
+          r6[k] = r;
+        }
+      }
+      float2* dout = (float2*)(d.dU32 + 6 * i);
+#pragma unroll
+      for (int k2 = 0; k2 < 3; k2++) dout[k2] = make_float2(du[2 * k2], du[2 * k2 + 1]);
+    } else {
+      const double q = d.q[i], po = d.phi_old[i];
+      const double2* pn = (const double2*)(d.phi_new + 6 * i);
+      double du[6];
+#pragma unroll
+      for (int k2 = 0; k2 < 3; k2++) {
+        const double2 v = pn[k2];
+        const double cM = 4.0 * M_PI / (3.0 * g.a * g.a * g.a) * d.dip[k2];
+#pragma unroll
+        for (int o = 0; o < 2; o++) {
+          const int k = 2 * k2 + o;
+          double dw = o ? -g.h : g.h;
+          if (o == 0 && cc[k2] == E - 1) dw -= g.a;
+          if (o == 1 && cc[k2] == 0) dw += g.a;
+          double dd = __longlong_as_double(0x7ff8000000000000LL), r = 0.0;
+          if (m6[k]) {
+            dd = q * ((o ? v.y : v.x) - po) - q * cM * dw - q * q * d.selfc[k];
+            r = exp(-fmax(dd, 0.0) / g.kT);
+          }
+          du[k] = dd;
+          r6[k] = r;
+        }
+      }
+      double2* dout = (double2*)(d.dU + 6 * i);
+#pragma unroll
+      for (int k2 = 0; k2 < 3; k2++) dout[k2] = make_double2(du[2 * k2], du[2 * k2 + 1]);
+    }
+    double2* rout = (double2*)(d.rate + 6 * i);
+#pragma unroll
+    for (int k2 = 0; k2 < 3; k2++) rout[k2] = make_double2(r6[2 * k2], r6[2 * k2 + 1]);
+#pragma unroll
+    for (int k = 0; k < KMC_NHOP; k++) tsum += r6[k];
+  }
+  ts[threadIdx.x] = tsum;
+  __syncthreads();
+  block_scan(ts, FIN_THREADS);
+  if (threadIdx.x == 0) d.bsum[blockIdx.x] = ts[FIN_THREADS - 1];
+}
+
+// block sums of caller-provided rates (same block structure as k_finalize)
+__global__ void __launch_bounds__(FIN_THREADS) k_rate_bsum(const Geo g, const Dev d) {
+  __shared__ double ts[FIN_THREADS];
+  int64_t i = blockIdx.x * (int64_t)FIN_THREADS + threadIdx.x;
+  double tsum = 0.0;
+  if (i < g.n)
+    for (int k = 0; k < KMC_NHOP; k++) tsum += d.rate[6 * i + k];
+  ts[threadIdx.x] = tsum;
+  __syncthreads();
+  block_scan(ts, FIN_THREADS);
+  if (threadIdx.x == 0) d.bsum[blockIdx.x] = ts[FIN_THREADS - 1];
+}
+
+void kmc_finalize_rates(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
+  unsigned nb = (unsigned)((g.n + FIN_THREADS - 1) / FIN_THREADS);
+  if (prec == 0) k_finalize<false><<<nb, FIN_THREADS, 0, s>>>(g, d);
+  else k_finalize<true><<<nb, FIN_THREADS, 0, s>>>(g, d);
+}
+
+// ------------------------------------------------------------------ selection
+// Q = sum of all rates; event j with R_{j-1} < Q zeta <= R_j (Algorithm 1),
+// where R is the cumulative sum taken block by block (block sums from the
+// finalize kernel, chunks of block sums per thread here); dt = -ln(xi)/Q.
+#define SEL_THREADS 1024
 
 __global__ void __launch_bounds__(SEL_THREADS) k_select(const Geo g, const Dev d, int use_counter) {
   __shared__ double cs[SEL_THREADS];
@@ -1085,11 +1064,30 @@ __global__ void k_acc_coarse_reduce(const Geo g, const Dev d, const double2* scr
   int l, cell, first, nslot;
   if (cc < 8) { l = 2; cell = cc; first = cc * 2 * KMC_TOP_NIMG; nslot = 2 * KMC_TOP_NIMG; }
   else { l = 3; cell = cc - 8; first = KMC_L2_SLOTS + cell * 54; nslot = 54; }
+  // eight independent partial sums (loads in flight together), combined in a
+  // fixed order
+  double px[8], py[8];
+#pragma unroll
+  for (int u = 0; u < 8; u++) px[u] = py[u] = 0.0;
+  int s2 = 0;
+  for (; s2 + 8 <= nslot; s2 += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const double2 v = scratch[((int64_t)first + s2 + u) * g.P + c];
+      px[u] += v.x;
+      py[u] += v.y;
+    }
+  }
+  for (int u = 0; s2 < nslot; s2++, u++) {
+    const double2 v = scratch[((int64_t)first + s2) * g.P + c];
+    px[u] += v.x;
+    py[u] += v.y;
+  }
   double ax = 0.0, ay = 0.0;
-  for (int s2 = 0; s2 < nslot; s2++) {
-    double2 v = scratch[((int64_t)first + s2) * g.P + c];
-    ax += v.x;
-    ay += v.y;
+#pragma unroll
+  for (int u = 0; u < 8; u++) {
+    ax += px[u];
+    ay += py[u];
   }
   const int64_t at = (g.cell_off[l] + cell) * g.P + c;
   double2 v = d.Psi[at];

@@ -16,6 +16,8 @@ definitions used throughout this repository):
   large   256^3 sites, 1048576 charges, L=6, p=12, kT=0.05, 1000 steps
   batch   64 replicas, edges from {32,48,64,96,128}, occupancy U[0.02,0.15], p=10, 500 steps
   blobs   512^3 sites, 8388608 charges, 70% in 200 Gaussian blobs (sigma 8), L=7, p=10, 200 steps
+  tile    128^3 sites, 131072 charges, L=5, p=12: the leaf shape of "large" (8^3 sites and 32
+          charges per leaf) on 4096 leaves, for kernel profiles that span several waves
 """
 from __future__ import annotations
 
@@ -26,6 +28,7 @@ WORKLOADS = {
     "medium": dict(E=64, N=32768, L=4, p=12, kT=0.05, steps=1000, seed=1002, recompute_every=100),
     "large": dict(E=256, N=1048576, L=6, p=12, kT=0.05, steps=1000, seed=1003, recompute_every=0),
     "blobs": dict(E=512, N=8388608, L=7, p=10, kT=0.05, steps=200, seed=1005, recompute_every=0),
+    "tile": dict(E=128, N=131072, L=5, p=12, kT=0.05, steps=100, seed=1007, recompute_every=0),
 }
 BATCH = dict(replicas=64, edges=(32, 48, 64, 96, 128), occ=(0.02, 0.15), p=10, kT=0.05, steps=500,
              seed=1004, replica_seed0=2000)
@@ -109,17 +112,23 @@ def uniforms(steps: int, seed: int) -> np.ndarray:
     return (1.0 - rng.random(2 * steps)).reshape(steps, 2)
 
 
-def batch_replicas(n: int | None = None):
-    """Replica list for the batched workload: dicts with E, N, sites, q, seed."""
+def batch_replicas(n: int | None = None, first: int = 0):
+    """Replica list for the batched workload: dicts with E, N, sites, q, seed.
+    Replicas first .. first + n - 1; the first 64 draw their edge and occupancy
+    from one stream (seed 1004), later ones from a stream of their own."""
     B = BATCH
     n = B["replicas"] if n is None else n
     rng = np.random.default_rng(B["seed"])
     edges = rng.choice(np.array(B["edges"]), size=B["replicas"])
     occs = rng.uniform(B["occ"][0], B["occ"][1], size=B["replicas"])
     out = []
-    for r in range(n):
-        E = int(edges[r])
-        N = int(round(occs[r] * E ** 3 / 2)) * 2
+    for r in range(first, first + n):
+        if r < B["replicas"]:
+            E, occ = int(edges[r]), float(occs[r])
+        else:
+            rr = np.random.default_rng(B["seed"] + 1 + r)
+            E, occ = int(rr.choice(np.array(B["edges"]))), float(rr.uniform(B["occ"][0], B["occ"][1]))
+        N = int(round(occ * E ** 3 / 2)) * 2
         sites, q = uniform_lattice(E, N, B["replica_seed0"] + r)
         out.append(dict(E=E, N=N, sites=sites, q=q, seed=B["replica_seed0"] + r, occupancy=N / E ** 3))
     return out
