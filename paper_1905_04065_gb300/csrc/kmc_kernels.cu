@@ -99,15 +99,17 @@ __device__ __forceinline__ T l2p_eval(const C* L, int p, T x, T y, T z) {
 
 
 // ------------------------------------------------------------------ near-field helpers
-// FP32 (lattice proposals): coordinates in lattice units relative to the leaf
-// corner, so that for source s and target t every term of
+// FP32 (lattice proposals): coordinates in lattice units relative to the
+// target leaf's corner, so that for source s and target t every term of
 // |s - t|^2 = w_s + w_t - 2 s.t (w = |.|^2) is an integer far below 2^24 and
-// the squared distance is exact.  That form takes four FP32 operations per
-// pair instead of six.  Sources are staged as pairs (A = {x_2j, x_2j+1, y_2j,
-// y_2j+1}, B = {z_2j, z_2j+1, w_2j, w_2j+1}, Q = {q_2j, q_2j+1}) so that one
-// packed FP32x2 instruction (FADD2 / FFMA2) serves two pair interactions; 1/r
-// from the MUFU rsqrt.approx (relative error < 2^-22), scaled by 1/h once per
-// target.  FP64: physical coordinates, one source per iteration.
+// the squared distance is exact; that form takes four FP32 operations per pair
+// instead of six.  Sources come in groups of four ({x0 x1 y0 y1} {z0 z1 w0 w1}
+// {x2 x3 y2 y3} {z2 z3 w2 w3} {q0 q1 q2 q3}: the per-leaf layout kept in
+// device memory, copied as blocks and shifted once into the target leaf's
+// frame) so that one packed FP32x2 instruction (FADD2 / FFMA2) serves two pair
+// interactions; 1/r from the MUFU rsqrt.approx (relative error < 2^-22),
+// scaled by 1/h once per target.  Each thread evaluates two targets against
+// every source it loads.  FP64: physical coordinates, one source per iteration.
 __device__ __forceinline__ float rsqrt_mufu(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -119,22 +121,8 @@ template <typename T> struct NearField;
 template <> struct NearField<float> {
   float2 c0, e0, c1, e1;  // target 0 and target 1, two accumulation chains each
   __device__ __forceinline__ void reset() { c0 = e0 = c1 = e1 = make_float2(0.f, 0.f); }
-  // groups of four sources: {x0 x1 y0 y1} {z0 z1 w0 w1} {x2 x3 y2 y3} {z2 z3 w2 w3} {q0 q1 q2 q3}
+  // shared-memory bytes for `chunk` sources in groups of four (80 bytes each)
   static __host__ __device__ __forceinline__ size_t bytes(int chunk) { return (size_t)((chunk + 3) / 4 + 1) * 80; }
-  static __device__ __forceinline__ void stage(unsigned char* sm, int e, float x, float y, float z, float q) {
-    float* G = (float*)sm + 20 * (e >> 2);
-    const int r = e & 3, o = r & 1;
-    float* A = G + 8 * (r >> 1);
-    A[o] = x;
-    A[2 + o] = y;
-    A[4 + o] = z;
-    A[6 + o] = x * x + y * y + z * z;
-    G[16 + r] = q;
-  }
-  // fill the last group with chargeless sources far from every target
-  static __device__ __forceinline__ void pad(unsigned char* sm, int ns) {
-    for (int e = ns; e < ((ns + 3) & ~3); e++) stage(sm, e, 1024.f, 1024.f, 1024.f, 0.f);
-  }
   struct Tgt {
     float2 tx2, ty2, tz2, wt;  // -2 t and |t|^2, duplicated for the packed lanes
   };
@@ -179,19 +167,18 @@ template <> struct NearField<float> {
     c1 = c;
     e1 = d;
   }
-  // sources [0, nguard) may sit on a target (skip r2 = 0); the rest never do.
-  // Target 1 is evaluated only when two is set (warp-uniform).
-  __device__ __forceinline__ void run2(const unsigned char* sm, int ns, int nguard, bool two, float tx0, float ty0,
-                                       float tz0, float tx1, float ty1, float tz1) {
-    const int gg = (nguard + 3) >> 2, ng = (ns + 3) >> 2;
-    const float4* G = (const float4*)sm;
+  // groups [0, ng) in the targets' frame, the first ngg of them the targets'
+  // own leaf (skip the pair at distance 0).  Target 1 is evaluated only when
+  // two is set (warp-uniform).
+  __device__ __forceinline__ void run_groups(const float4* G, int ngg, int ng, bool two, float tx0, float ty0,
+                                             float tz0, float tx1, float ty1, float tz1) {
     const Tgt t0 = target(tx0, ty0, tz0), t1 = target(tx1, ty1, tz1);
     if (two) {
-      if (gg > 0) run_range<true, true>(G, gg, t0, t1);
-      if (ng > gg) run_range<false, true>(G + 5 * gg, ng - gg, t0, t1);
+      if (ngg > 0) run_range<true, true>(G, ngg, t0, t1);
+      if (ng > ngg) run_range<false, true>(G + 5 * ngg, ng - ngg, t0, t1);
     } else {
-      if (gg > 0) run_range<true, false>(G, gg, t0, t1);
-      if (ng > gg) run_range<false, false>(G + 5 * gg, ng - gg, t0, t1);
+      if (ngg > 0) run_range<true, false>(G, ngg, t0, t1);
+      if (ng > ngg) run_range<false, false>(G + 5 * ngg, ng - ngg, t0, t1);
     }
   }
   __device__ __forceinline__ float sum(int side) const {
@@ -291,56 +278,98 @@ template <> __device__ __forceinline__ double qnan<double>() { return __longlong
 __device__ __forceinline__ int lattice_coord(float x, float ih) { return (int)floorf(x * ih); }
 __device__ __forceinline__ int lattice_coord(double x, double ih) { return (int)floor(x * ih); }
 
-// one staged source: FP32 in lattice units relative to the leaf corner, FP64
-// in physical coordinates; (shx, shy, shz) is the periodic image shift in sites
-__device__ __forceinline__ void stage_source(unsigned char* src, int e, float4 v, int shx, int shy, int shz, int gx0,
-                                             int gy0, int gz0, float ih, float) {
-  NearField<float>::stage(src, e, (float)(lattice_coord(v.x, ih) + shx - gx0),
-                          (float)(lattice_coord(v.y, ih) + shy - gy0), (float)(lattice_coord(v.z, ih) + shz - gz0),
-                          v.w);
+// coordinate c + dc (|dc| <= 1) wrapped into [0, E)
+__device__ __forceinline__ int wrap1(int c, int E) { return c < 0 ? c + E : (c >= E ? c - E : c); }
+
+// ---- bulk asynchronous copies (global -> shared) completed on an mbarrier
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ void stage_source(unsigned char* src, int e, double4_32a v, int shx, int shy, int shz, int,
-                                             int, int, double, double h) {
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// bytes: a multiple of 16; both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  uint64_t gsrc;
+  asm("cvta.to.global.u64 %0, %1;" : "=l"(gsrc) : "l"(src));
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// wait for phase `parity` of the barrier, at most ~limit_ns; false on timeout
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_test(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_test(bar, parity)) {
+    if (global_ns() - t0 > limit_ns) return false;
+    __nanosleep(64);
+  }
+  return true;
+}
+#define KMC_WAIT_NS 1000000000ull  // one second
+
+// FP64 form: one staged source in physical coordinates; (shx, shy, shz) is the
+// periodic image shift in sites
+__device__ __forceinline__ void stage_source(unsigned char* src, int e, double4_32a v, int shx, int shy, int shz,
+                                             double h) {
   v.x += (double)shx * h;
   v.y += (double)shy * h;
   v.z += (double)shz * h;
   NearField<double>::stage(src, e, v);
 }
 
-// coordinate c + dc (|dc| <= 1) wrapped into [0, E)
-__device__ __forceinline__ int wrap1(int c, int E) { return c < 0 ? c + E : (c >= E ? c - E : c); }
-
 // Evaluation is per distinct site of the leaf: the potential at a site is
 // needed once even when several charges propose to hop there, and at an own
 // charge's site it is that charge's old-position potential (the pair at
 // distance 0 is skipped).  Phases: (0) the 27 neighbour leaves (slot base,
-// count, image shift); (1) occupancy bits; (2) needed-site bits, masked hops
-// written; (3) compact site list; (4) near-field sums + L2P per site, one site
-// per thread per round, sources staged one warp per neighbour leaf; (5)
-// write-out by re-enumerating the same hops.  Site coordinates come from the
-// slot positions (coalesced), user indices only where an output is written.
-// Potentials are written in precision T (FP32 arrays in the mixed form, FP64
-// arrays in the FP64 form).
+// count) and the source passes; in the FP32 form the first pass's charge
+// groups are copied into shared memory by bulk asynchronous copies that run
+// while phases 1-3 proceed; (1) occupancy bits; (2) needed-site bits, masked
+// hops written; (3) compact site list; (4) near-field sums + L2P, two sites
+// per thread per round; (5) write-out by re-enumerating the same hops.  Site
+// coordinates come from the slot positions (coalesced), user indices only
+// where an output is written.  Potentials are written in precision T (FP32
+// arrays in the mixed form, FP64 arrays in the FP64 form).
 template <typename T>
 __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, const Dev d, int chunk) {
   typedef typename cplx<T>::type C;
   typedef typename vec4<T>::type V4;
-  extern __shared__ __align__(32) unsigned char sm[];
+  constexpr bool F32 = sizeof(T) == 4;
+  extern __shared__ __align__(128) unsigned char sm[];
   const int W = g.W, W3 = W * W * W;
   const int nbw = (W3 + 31) / 32;
   unsigned char* src = sm;
-  C* Lc = (C*)(sm + NearField<T>::bytes(chunk));  // 8-byte aligned
+  C* Lc = (C*)(sm + NearField<T>::bytes(chunk));  // 16-byte aligned
   int64_t* nb_base = (int64_t*)(Lc + g.P);          // [27] slot base: own leaf, then the 26 others
-  int* nb_off = (int*)(nb_base + 27);               // [28] first staged element of each leaf
-  int* nb_sh = nb_off + 28;                         // [27 * 3] image shift in sites
-  int* nb_cnt = nb_sh + 81;                         // [27] charges per leaf
-  T* phis = (T*)(nb_cnt + 27);                      // [W3] potential per local site
+  uint64_t* bar = (uint64_t*)(nb_base + 27);        // [1] copy barrier (FP32 form)
+  int* nb_off = (int*)(bar + 1);                    // [28] first source of each leaf (FP64) / first group (FP32)
+  int* nb_cnt = nb_off + 28;                        // [27] charges per leaf
+  int* pq = nb_cnt + 27;                            // [28] first leaf of each source pass; pq[npass] = 27
+  int* misc = pq + 28;                              // [3] number of passes (padded to 8 bytes)
+  T* phis = (T*)(misc + 3);                         // [W3] potential per local site
   uint32_t* bits = (uint32_t*)(phis + W3);          // [nbw] occupied sites
   uint32_t* need = bits + nbw;                      // [nbw] sites where a potential is needed
   int* woff = (int*)(need + nbw);                   // [nbw + 1] prefix of needed sites per word
   uint16_t* sites = (uint16_t*)(woff + nbw + 1);    // [W3] needed local sites, compacted
-  T* out_old = (T*)((sizeof(T) == 4) ? (void*)d.phi_old32 : (void*)d.phi_old);
-  T* out_new = (T*)((sizeof(T) == 4) ? (void*)d.phi_new32 : (void*)d.phi_new);
+  T* out_old = (T*)(F32 ? (void*)d.phi_old32 : (void*)d.phi_old);
+  T* out_new = (T*)(F32 ? (void*)d.phi_new32 : (void*)d.phi_new);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   const int nL = g.nL, E = g.E;
@@ -348,7 +377,10 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
   const int lx = (int)(leaf % nL), ly = (int)((leaf / nL) % nL), lz = (int)(leaf / ((int64_t)nL * nL));
   const int gx0 = lx * W, gy0 = ly * W, gz0 = lz * W;
   const T h = (T)g.h, ih = (T)(1.0 / g.h);
-  const V4* spos = (const V4*)((sizeof(T) == 4) ? (const void*)d.spos32 : (const void*)d.spos64);
+  const V4* spos = (const V4*)(F32 ? (const void*)d.spos32 : (const void*)d.spos64);
+  const int64_t gpl = sgrp_groups(g.cap);  // groups per leaf in the FP32 source layout
+  // capacity of one pass: sources (FP64) or groups of four (FP32)
+  const int pass_cap = F32 ? chunk / 4 : chunk;
 
   const C* Pe = (const C*)d.Peff + (g.cell_off[g.L] + leaf) * g.P;
   for (int c = tid; c < g.P; c += blockDim.x) Lc[c] = Pe[c];
@@ -365,18 +397,36 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
     const int64_t nleaf = sx + (int64_t)nL * (sy + (int64_t)nL * sz);
     nb_base[tid] = nleaf * g.cap;
     nb_cnt[tid] = d.cnt[nleaf];
-    nb_sh[3 * tid] = (ux - sx) * W;
-    nb_sh[3 * tid + 1] = (uy - sy) * W;
-    nb_sh[3 * tid + 2] = (uz - sz) * W;
   }
+  if (F32 && tid == 0) mbar_init(bar, 1);
   __syncthreads();
   if (tid == 0) {
-    int acc = 0;
+    // prefix over the leaves (sources or groups) and the greedy split into
+    // passes at leaf boundaries; one leaf always fits (pass_cap >= capacity)
+    int acc = 0, np = 0, start = 0;
+    pq[0] = 0;
     for (int q = 0; q < 27; q++) {
+      const int u = F32 ? (nb_cnt[q] + 3) >> 2 : nb_cnt[q];
+      if (acc + u - start > pass_cap) {
+        pq[++np] = q;
+        start = acc;
+      }
       nb_off[q] = acc;
-      acc += nb_cnt[q];
+      acc += u;
     }
     nb_off[27] = acc;
+    pq[++np] = 27;
+    misc[0] = np;
+    misc[1] = 0;
+    if (F32) {  // first pass: one bulk copy per leaf, overlapped with phases 1-3
+      const int q1 = pq[1];
+      mbar_expect_tx(bar, (uint32_t)(nb_off[q1] * 80));
+      for (int q = 0; q < q1; q++) {
+        const int ng = (nb_cnt[q] + 3) >> 2;
+        if (ng)
+          bulk_copy_g2s(src + 80 * nb_off[q], d.sgrp + 20 * (nb_base[q] / g.cap) * gpl, (uint32_t)(80 * ng), bar);
+      }
+    }
   }
 
   // (1) occupancy bitmap of this leaf's sites
@@ -392,8 +442,8 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
 
   // (2) hop targets inside this leaf: own hops and hops entering from the six
   // face neighbours (f = 0 own leaf, f = 1..6 the neighbour across face f-1,
-  // hopping in direction (f-1)^1)
-  for (int f = 0; f <= KMC_NHOP; f++) {
+  // hopping in direction (f-1)^1); one warp per leaf
+  for (int f = warp; f <= KMC_NHOP; f += nwarp) {
     int li = 0;
     if (f) {
       const int* o = c_hop[f - 1];
@@ -402,7 +452,7 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
     }
     const int64_t mb = nb_base[li];
     const int cm = nb_cnt[li];
-    for (int j = tid; j < cm; j += blockDim.x) {
+    for (int j = lane; j < cm; j += 32) {
       const V4 v = spos[mb + j];
       const int gx = lattice_coord(v.x, ih), gy = lattice_coord(v.y, ih), gz = lattice_coord(v.z, ih);
       const int k0 = f ? ((f - 1) ^ 1) : 0, k1 = f ? k0 + 1 : KMC_NHOP;
@@ -446,9 +496,9 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
 
   // (4) near-field pair sums and L2P, two sites per thread per round (sites
   // b and b + blockDim).  Sources: own leaf first (pairs at distance 0
-  // skipped), then the 26 other leaves, streamed in chunks.
-  const int ntot = nb_off[27];
-  const int npass = (ntot + chunk - 1) / chunk;
+  // skipped), then the 26 other leaves, in passes of whole leaves.
+  const int npass = misc[0];
+  uint32_t waits = 0;  // completed phases of the copy barrier
   for (int rb = 0; rb < nsites; rb += 2 * blockDim.x) {
     const int b0 = rb + tid, b1 = b0 + blockDim.x;
     const int l0 = b0 < nsites ? sites[b0] : 0, l1 = b1 < nsites ? sites[b1] : 0;
@@ -459,44 +509,108 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
     NearField<T> nf;
     nf.reset();
     for (int pass = 0; pass < npass; pass++) {
-      const int c0 = pass * chunk;
-      const int ns = min(chunk, ntot - c0);
-      if (npass > 1 || rb > 0) __syncthreads();  // previous pass / round done with the staging area
-      for (int q = warp; q < 27; q += nwarp) {
-        const int lo = nb_off[q], hi = nb_off[q + 1];
-        const int a = max(lo, c0), b = min(hi, c0 + ns);
-        const int64_t sb = nb_base[q] - lo;
-        const int shx = nb_sh[3 * q], shy = nb_sh[3 * q + 1], shz = nb_sh[3 * q + 2];
-        for (int e = a + lane; e < b; e += 32)
-          stage_source(src, e - c0, spos[sb + e], shx, shy, shz, gx0, gy0, gz0, ih, h);
+      const int q0 = pq[pass], q1 = pq[pass + 1];
+      const bool resident = npass == 1 && rb > 0;  // sources already in shared memory
+      if (!resident && (pass > 0 || rb > 0)) {
+        __syncthreads();  // everyone is done with the previous contents
+        if (F32) {
+          if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(bar, (uint32_t)(80 * (nb_off[q1] - nb_off[q0])));
+            for (int q = q0; q < q1; q++) {
+              const int ng = (nb_cnt[q] + 3) >> 2;
+              if (ng)
+                bulk_copy_g2s(src + 80 * (nb_off[q] - nb_off[q0]), d.sgrp + 20 * (nb_base[q] / g.cap) * gpl,
+                              (uint32_t)(80 * ng), bar);
+            }
+          }
+        }
       }
-      if (tid == 0) NearField<T>::pad(src, ns);
-      __syncthreads();
-      if (one) {
-        const int nguard = max(0, min(cnt_own - c0, ns));  // own-leaf sources in this pass
-        if (sizeof(T) == 4)
-          nf.run2(src, ns, nguard, two, (T)ix0, (T)iy0, (T)iz0, (T)ix1, (T)iy1, (T)iz1);
-        else
-          nf.run2(src, ns, nguard, two, ((T)(gx0 + ix0) + (T)0.5) * h, ((T)(gy0 + iy0) + (T)0.5) * h,
-                  ((T)(gz0 + iz0) + (T)0.5) * h, ((T)(gx0 + ix1) + (T)0.5) * h, ((T)(gy0 + iy1) + (T)0.5) * h,
-                  ((T)(gz0 + iz1) + (T)0.5) * h);
+      if constexpr (F32) {
+        if (!resident) {
+          const bool ok = mbar_wait_bounded(bar, waits & 1, KMC_WAIT_NS);
+          waits++;
+          if (__syncthreads_or(!ok)) {  // copies did not arrive: flag, drain, leave
+            if (tid == 0) {
+              atomicOr(&d.err[0], KMC_DERR_TIMEOUT);
+              mbar_wait_bounded(bar, (waits - 1) & 1, KMC_WAIT_NS);
+            }
+            __syncthreads();
+            return;
+          }
+        }
+        if (!resident) {  // the copied groups into this leaf's corner frame (own leaf: already)
+          for (int q = max(q0, 1) + warp; q < q1; q += nwarp) {
+            const int qq = q <= 13 ? q - 1 : q;
+            const float ox = (float)((qq % 3 - 1) * W), oy = (float)(((qq / 3) % 3 - 1) * W);
+            const float oz = (float)((qq / 9 - 1) * W);
+            float4* G = (float4*)src + 5 * (nb_off[q] - nb_off[q0]);
+            const int ng = (nb_cnt[q] + 3) >> 2;
+            for (int gi = lane; gi < ng; gi += 32) {
+#pragma unroll
+              for (int pr = 0; pr < 2; pr++) {
+                float4 A = G[5 * gi + 2 * pr], B = G[5 * gi + 2 * pr + 1];
+                A.x += ox;
+                A.y += ox;
+                A.z += oy;
+                A.w += oy;
+                B.x += oz;
+                B.y += oz;
+                B.z = A.x * A.x + A.z * A.z + B.x * B.x;
+                B.w = A.y * A.y + A.w * A.w + B.y * B.y;
+                G[5 * gi + 2 * pr] = A;
+                G[5 * gi + 2 * pr + 1] = B;
+              }
+            }
+          }
+          __syncthreads();
+        }
+        if (one) {
+          const int ngt = nb_off[q1] - nb_off[q0];
+          const int ngg = q0 == 0 ? (cnt_own + 3) >> 2 : 0;  // own-leaf groups lead pass 0
+          nf.run_groups((const float4*)src, ngg, ngt, two, (float)ix0, (float)iy0, (float)iz0, (float)ix1,
+                        (float)iy1, (float)iz1);
+        }
+      } else {
+        if (!resident) {
+          for (int q = q0 + warp; q < q1; q += nwarp) {
+            const int qq = q == 0 ? 13 : (q <= 13 ? q - 1 : q);
+            const int ux = lx + qq % 3 - 1, uy = ly + (qq / 3) % 3 - 1, uz = lz + qq / 9 - 1;
+            const int shx = ux - (ux + nL) % nL, shy = uy - (uy + nL) % nL, shz = uz - (uz + nL) % nL;
+            const int e0 = nb_off[q] - nb_off[q0];
+            for (int j = lane; j < nb_cnt[q]; j += 32)
+              stage_source(src, e0 + j, spos[nb_base[q] + j], shx * W, shy * W, shz * W, (double)h);
+          }
+          __syncthreads();
+        }
+        if (one) {
+          const int nguard = q0 == 0 ? cnt_own : 0;  // own-leaf sources lead pass 0
+          nf.run2(src, nb_off[q1] - nb_off[q0], nguard, two, ((T)(gx0 + ix0) + (T)0.5) * h,
+                  ((T)(gy0 + iy0) + (T)0.5) * h, ((T)(gz0 + iz0) + (T)0.5) * h, ((T)(gx0 + ix1) + (T)0.5) * h,
+                  ((T)(gy0 + iy1) + (T)0.5) * h, ((T)(gz0 + iz1) + (T)0.5) * h);
+        }
       }
     }
     const T hw = (T)(0.5 * W);
     if (b0 < nsites) {
-      const T near = sizeof(T) == 4 ? nf.sum(0) * ih : nf.sum(0);
+      const T near = F32 ? nf.sum(0) * ih : nf.sum(0);
       phis[l0] = near + l2p_point<T, C>(Lc, g.p, ((T)ix0 + (T)0.5 - hw) * h, ((T)iy0 + (T)0.5 - hw) * h,
                                         ((T)iz0 + (T)0.5 - hw) * h);
     }
     if (b1 < nsites) {
-      const T near = sizeof(T) == 4 ? nf.sum(1) * ih : nf.sum(1);
+      const T near = F32 ? nf.sum(1) * ih : nf.sum(1);
       phis[l1] = near + l2p_point<T, C>(Lc, g.p, ((T)ix1 + (T)0.5 - hw) * h, ((T)iy1 + (T)0.5 - hw) * h,
                                         ((T)iz1 + (T)0.5 - hw) * h);
     }
   }
+  if (F32 && nsites == 0) {  // the prefetched copies must land before the CTA leaves
+    const bool ok = mbar_wait_bounded(bar, 0, KMC_WAIT_NS);
+    if (!ok && tid == 0) atomicOr(&d.err[0], KMC_DERR_TIMEOUT);
+  }
   __syncthreads();
-  // (5) write-out: old-position potentials and unmasked hop potentials
-  for (int f = 0; f <= KMC_NHOP; f++) {
+  // (5) write-out: old-position potentials and unmasked hop potentials; one
+  // warp per leaf
+  for (int f = warp; f <= KMC_NHOP; f += nwarp) {
     int li = 0;
     if (f) {
       const int* o = c_hop[f - 1];
@@ -505,7 +619,7 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, c
     }
     const int64_t mb = nb_base[li];
     const int cm = nb_cnt[li];
-    for (int j = tid; j < cm; j += blockDim.x) {
+    for (int j = lane; j < cm; j += 32) {
       const int32_t u = d.uid[mb + j];
       const V4 v = spos[mb + j];
       const int gx = lattice_coord(v.x, ih), gy = lattice_coord(v.y, ih), gz = lattice_coord(v.z, ih);
@@ -529,8 +643,8 @@ static size_t propose_smem(const Geo& g, int prec, int chunk) {
   const int W3 = g.W * g.W * g.W;
   const int nbw = (W3 + 31) / 32;
   const size_t srcb = prec == 0 ? NearField<double>::bytes(chunk) : NearField<float>::bytes(chunk);
-  return srcb + 2 * ts * (size_t)g.P + 27 * 8 + (28 + 81 + 27) * 4 + ts * (size_t)W3 + 4 * (size_t)(3 * nbw + 1) +
-         2 * (size_t)((W3 + 1) & ~1);
+  return srcb + 2 * ts * (size_t)g.P + 27 * 8 + 8 + (28 + 27 + 28 + 3) * 4 + ts * (size_t)W3 +
+         4 * (size_t)(3 * nbw + 1) + 2 * (size_t)((W3 + 1) & ~1);
 }
 
 // sources are streamed in chunks of at least 1024 (every neighbour leaf's
@@ -1202,7 +1316,14 @@ __global__ void k_acc_move(const Geo g, const Dev d) {
     d.spos64[so] = d.spos64[last];
     d.spos32[so] = d.spos32[last];
     d.slot_of[ul] = so;
+    if (d.sgrp) {
+      const int sl = d.site[ul], E = g.E, W = g.W;
+      const int lx = (int)(lo % g.nL), ly = (int)((lo / g.nL) % g.nL), lz = (int)(lo / ((int64_t)g.nL * g.nL));
+      sgrp_put(d.sgrp, g.cap, so, (float)(sl % E - lx * W), (float)((sl / E) % E - ly * W),
+               (float)(sl / (E * E) - lz * W), d.spos32[last].w);
+    }
   }
+  if (d.sgrp) sgrp_pad(d.sgrp, g.cap, last);
   d.cnt[lo] -= 1;
   int c = d.cnt[ln];
   if (c >= g.cap) {  // cannot place: undo the removal accounting and flag
@@ -1215,6 +1336,12 @@ __global__ void k_acc_move(const Geo g, const Dev d) {
   d.uid[sn] = i;
   d.spos64[sn] = make_double4_32a(mv.rn[0], mv.rn[1], mv.rn[2], mv.q);
   d.spos32[sn] = make_float4((float)mv.rn[0], (float)mv.rn[1], (float)mv.rn[2], (float)mv.q);
+  if (d.sgrp) {
+    const int sn2 = mv.site_new, E = g.E, W = g.W;
+    const int lx = ln % g.nL, ly = (ln / g.nL) % g.nL, lz = ln / (g.nL * g.nL);
+    sgrp_put(d.sgrp, g.cap, sn, (float)(sn2 % E - lx * W), (float)((sn2 / E) % E - ly * W),
+             (float)(sn2 / (E * E) - lz * W), (float)mv.q);
+  }
   d.slot_of[i] = (int32_t)sn;
   d.pos[3 * i] = mv.rn[0];
   d.pos[3 * i + 1] = mv.rn[1];

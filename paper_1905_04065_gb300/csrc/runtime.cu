@@ -115,6 +115,7 @@ static int check_flags(kmc_fmm* h, const char* where) {
   if (e[0] & KMC_DERR_BADSITE) return fail(h, KMC_ERR_ARG, "%s: a position is not on a lattice site", where);
   if (e[0] & KMC_DERR_SINGULAR)
     return fail(h, KMC_ERR_ARG, "%s: a target coincides with a charge (singular move)", where);
+  if (e[0] & KMC_DERR_TIMEOUT) return fail(h, KMC_ERR_TIMEOUT, "%s: a device-side wait exceeded its limit", where);
   return fail(h, KMC_ERR_STATE, "%s: device error flags 0x%x", where, e[0]);
 }
 
@@ -356,6 +357,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   ALLOC(d.uid, sizeof(int32_t) * nslot);
   ALLOC(d.spos64, sizeof(double4_32a) * nslot);
   ALLOC(d.spos32, sizeof(float4) * nslot);
+  if (g.E > 0) ALLOC(d.sgrp, sizeof(float) * 20 * (size_t)g.ML * (size_t)sgrp_groups(g.cap));
   ALLOC(d.Mt, sizeof(double2) * g.ncell_total * g.P);
   ALLOC(d.Psi, sizeof(double2) * g.ncell_total * g.P);
   ALLOC(d.Peff, (h->prec == 0 ? sizeof(double2) : sizeof(float2)) * g.ncell_total * g.P);
