@@ -218,11 +218,29 @@ def kmc_fmm_propose(h: Handle, particle, target, mask=None):
     return out
 
 
-def kmc_fmm_propose_lattice(h: Handle):
-    """(mask[n,6], dU[n,6]) for all nearest-neighbour hops."""
+def _given(h: Handle, x, shape, dtype):
+    """A caller-provided output buffer (numpy array or torch tensor) in the
+    handle's memory kind: checked for shape, dtype and contiguity."""
+    if _is_torch(x):
+        import torch
+        tdt = {np.float64: torch.float64, np.uint8: torch.uint8}[np.dtype(dtype).type]
+        if tuple(x.shape) != shape or x.dtype != tdt or not x.is_contiguous() or \
+                (x.device.type == "cuda") != (h.mem == KMC_MEM_DEVICE):
+            raise ValueError(f"output buffer must be a contiguous {shape} {tdt} tensor in the handle's memory")
+        return x, ctypes.c_void_p(x.data_ptr())
+    if h.mem == KMC_MEM_DEVICE:
+        raise ValueError("a device-memory handle needs torch CUDA output tensors")
+    if x.shape != shape or x.dtype != np.dtype(dtype) or not x.flags.c_contiguous:
+        raise ValueError(f"output buffer must be a C-contiguous {shape} {np.dtype(dtype)} array")
+    return x, x.ctypes.data_as(ctypes.c_void_p)
+
+
+def kmc_fmm_propose_lattice(h: Handle, mask=None, dU=None):
+    """(mask[n,6], dU[n,6]) for all nearest-neighbour hops.  mask and dU may be
+    caller-owned buffers (e.g. pinned host memory) that are filled in place."""
     lib = load_library()
-    mask, mp = _out(h, (h.n, 6), np.uint8)
-    dU, dp = _out(h, (h.n, 6), np.float64)
+    mask, mp = _out(h, (h.n, 6), np.uint8) if mask is None else _given(h, mask, (h.n, 6), np.uint8)
+    dU, dp = _out(h, (h.n, 6), np.float64) if dU is None else _given(h, dU, (h.n, 6), np.float64)
     _check(h, lib.kmc_fmm_propose_lattice(h.ptr, mp, dp))
     return mask, dU
 

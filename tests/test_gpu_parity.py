@@ -305,6 +305,24 @@ def test_device_memory_interface(small):
     np.testing.assert_array_equal(dU.cpu().numpy(), dU2)
 
 
+def test_caller_owned_pinned_outputs(small):
+    """Outputs written in place into caller-owned pinned host buffers equal the
+    library-allocated ones; mismatched buffers are refused."""
+    import torch
+    k = _k()
+    w, sites, q, st = small
+    h = _init(w["E"], sites, q, w["L"], 8, kT=w["kT"])
+    mask_h = torch.empty((len(q), 6), dtype=torch.uint8, pin_memory=True)
+    dU_h = torch.empty((len(q), 6), dtype=torch.float64, pin_memory=True)
+    m1, d1 = k.kmc_fmm_propose_lattice(h, mask_h, dU_h)
+    assert m1 is mask_h and d1 is dU_h
+    m2, d2 = k.kmc_fmm_propose_lattice(h)
+    assert np.array_equal(mask_h.numpy(), m2)
+    np.testing.assert_array_equal(dU_h.numpy(), d2)
+    with pytest.raises(ValueError):
+        k.kmc_fmm_propose_lattice(h, mask_h, torch.empty((len(q), 5), dtype=torch.float64))
+
+
 def test_offlattice_propose_and_accept():
     """Off-lattice positions (the paper's general interface): dU against the
     direct Ewald oracle, then an accepted move and U(after) - U(before)."""

@@ -128,3 +128,45 @@ def test_large_run_selects_like_stepwise():
         ev, dt, Q = k.kmc_step(h2, None, u[s, 0], u[s, 1])
         assert ev == ev_run[s], s
         k.kmc_fmm_accept_event(h2, ev)
+
+
+def test_blobs_masks_exact_and_sampled_parity():
+    """The clustered 512^3 workload (8.4M charges, 70% in Gaussian blobs, full
+    leaves of 512 charges): every mask bit-exact against the occupancy, every
+    open hop of the most crowded leaf that has open hops and a uniform sample
+    of hops against the oracle's direct O(N) lattice sum, at p = 10."""
+    k = _k()
+    w, sites, q = workloads.workload("blobs")
+    E, L, p, kT = w["E"], w["L"], w["p"], w["kT"]
+    h = k.kmc_fmm_init(workloads.site_positions(E, sites), q, float(E), L, p, precision="mixed",
+                       lattice_edge=E, kT=kT)
+    mask, dU = k.kmc_fmm_propose_lattice(h)
+    occ = np.zeros(E ** 3, dtype=bool)
+    occ[sites] = True
+    xyz = workloads.site_xyz(E, sites)
+    steps = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]])
+    tgt = (xyz[:, None, :] + steps[None, :, :]) % E
+    tsite = tgt[..., 0] + E * (tgt[..., 1] + E * tgt[..., 2])
+    assert np.array_equal(mask.astype(bool), ~occ[tsite])
+    assert np.all(np.isnan(dU[mask == 0]))
+    # the densest leaf's charges and a uniform sample
+    W = E // 2 ** (L - 1)
+    leaf = (xyz[:, 0] // W) + (E // W) * ((xyz[:, 1] // W) + (E // W) * (xyz[:, 2] // W))
+    # the most crowded leaf among those whose charges still have open hops
+    counts = np.bincount(leaf)
+    open_hops = np.bincount(leaf, weights=mask.sum(axis=1))
+    dense = np.nonzero(leaf == np.argmax(np.where(open_hops > 0, counts, -1)))[0]
+    rng = np.random.default_rng(23)
+    ii, kk = np.nonzero(mask)
+    pick = rng.choice(len(ii), size=3000, replace=False)
+    di, dk = np.nonzero(mask[dense])
+    parts = np.concatenate([dense[di], ii[pick]])
+    hops = np.concatenate([dk, kk[pick]])
+    G = oracle.psi_table(E)
+    ref = oracle.lattice_delta_u_direct(E, G, sites, q, parts, tsite[parts, hops])
+    got = dU[parts, hops]
+    err = np.abs(got - ref) / np.max(np.abs(ref))
+    print(f"blobs: {len(parts)} hops ({len(di)} from the densest leaf), max {err.max():.2e} "
+          f"mean {err.mean():.2e} p99 {np.quantile(err, 0.99):.2e}")
+    assert err.max() < 2e-3
+    assert np.quantile(err, 0.99) < 1e-4
