@@ -671,69 +671,7 @@ __global__ void k_downward_root(const Geo g, const Dev d) {
   for (int c = threadIdx.x; c < g.P; c += blockDim.x) Pe[g.cell_off[1] * g.P + c] = own_coef<T>(d, g.cell_off[1] * g.P + c);
 }
 
-// CTA of DW_PAR parent cells (32 children).  Warp w computes output
-// coefficients ci = w, w + 8, ... (ascending degree, so the cost per task
-// falls and round-robin balances the warps); lane c is child c, so the loop
-// bounds of a task are the same in every lane.  Outputs are staged in shared
-// memory and written cell-major (coalesced) with the level's own Psi added.
-#define DW_PAR 4
-template <typename T>
-__global__ void __launch_bounds__(256) k_downward(const Geo g, const Dev d, int l) {
-  typedef typename cplx<T>::type C;
-  extern __shared__ __align__(16) unsigned char shraw[];
-  C* R = (C*)shraw;             // 8 * P child-offset regular tables
-  C* Lp = R + 8 * g.P;          // DW_PAR parent expansions
-  C* Out = Lp + DW_PAR * g.P;   // 8 * DW_PAR child outputs
-  C* Pe = (C*)d.Peff;
-  const int nl = 1 << (l - 1), np = nl / 2;
-  const int64_t npar = (int64_t)np * np * np;
-  const int64_t par0 = (int64_t)blockIdx.x * DW_PAR;
-  for (int c = threadIdx.x; c < 8 * g.P; c += blockDim.x) R[c] = child_coef<T>(d, (int64_t)l * 8 * g.P + c);
-  for (int c = threadIdx.x; c < DW_PAR * g.P; c += blockDim.x) {
-    int gp = c / g.P;
-    Lp[c] = (par0 + gp < npar) ? Pe[(g.cell_off[l - 1] + par0 + gp) * g.P + (c - gp * g.P)] : cmk<C>(0.0, 0.0);
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int gp = lane >> 3, o = lane & 7;
-  const C* L = Lp + gp * g.P;
-  const C* Ro = R + o * g.P;
-  for (int ci = warp; ci < g.P; ci += nwarp) {
-    const short2 km = f_nm[ci];
-    const int k = km.x, lo = km.y;
-    T ax = 0, ay = 0;
-    for (int n = k; n <= g.p; n++) {
-      const int j = n - k;
-      const int mlo = max(lo - j, -n), mhi = min(lo + j, n);
-      for (int m = mlo; m <= mhi; m++) {
-        C a = tab_get(L, n, m), b = tab_get(Ro, j, m - lo);
-        ax += a.x * b.x - a.y * b.y;
-        ay += a.x * b.y + a.y * b.x;
-      }
-    }
-    C v;
-    v.x = ax;
-    v.y = ay;
-    Out[lane * g.P + ci] = v;
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < 8 * DW_PAR * g.P; idx += blockDim.x) {
-    const int c = idx / g.P, ci = idx - c * g.P;
-    const int64_t par = par0 + (c >> 3);
-    if (par >= npar) continue;
-    const int oc = c & 7;
-    const int px = (int)(par % np), py = (int)((par / np) % np), pz = (int)(par / ((int64_t)np * np));
-    const int bx = 2 * px + (oc & 1), by = 2 * py + ((oc >> 1) & 1), bz = 2 * pz + ((oc >> 2) & 1);
-    const int64_t cell = bx + (int64_t)nl * (by + (int64_t)nl * bz);
-    const C own = own_coef<T>(d, (g.cell_off[l] + cell) * g.P + ci);
-    C v = Out[idx];
-    v.x += own.x;
-    v.y += own.y;
-    Pe[(g.cell_off[l] + cell) * g.P + ci] = v;
-  }
-}
-
-// Upper levels (few cells): CTA per child cell, thread per output
+// Downward pass, one level per launch: CTA per child cell, thread per output
 // coefficient.  The parent's expansion and the child-offset table are first
 // expanded to every order -n..n (the conjugate symmetry applied once), so the
 // inner loop is branch-free: out(k, lo) = sum_{n >= k} sum_m L(n, m) R(n - k, m - lo).
@@ -789,43 +727,26 @@ __global__ void __launch_bounds__(128) k_downward_cell(const Geo g, const Dev d,
   }
 }
 
-static size_t downward_smem(const Geo& g, int prec) {
-  return (size_t)(8 + DW_PAR + 8 * DW_PAR) * g.P * (prec == 0 ? sizeof(double2) : sizeof(float2));
-}
-
 void fmm_prepare(const Geo& g, int prec) {
   // load every per-step kernel now: with lazy module loading a first launch
   // inside a stream capture would invalidate the capture
   cudaFuncAttributes fa;
   cudaFuncGetAttributes(&fa, k_downward_root<double>);
   cudaFuncGetAttributes(&fa, k_downward_root<float>);
-  cudaFuncGetAttributes(&fa, k_downward<double>);
-  cudaFuncGetAttributes(&fa, k_downward<float>);
   cudaFuncGetAttributes(&fa, k_downward_cell<double>);
   cudaFuncGetAttributes(&fa, k_downward_cell<float>);
-  size_t sm = downward_smem(g, prec);
-  if (prec == 0) raise_dynamic_smem((const void*)k_downward<double>, sm);
-  else raise_dynamic_smem((const void*)k_downward<float>, sm);
+  (void)g;
+  (void)prec;
 }
 
 void fmm_downward(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
   if (prec == 0) k_downward_root<double><<<1, 128, 0, s>>>(g, d);
   else k_downward_root<float><<<1, 128, 0, s>>>(g, d);
-  const size_t sm = downward_smem(g, prec);
   const size_t smc = (size_t)2 * (g.p + 1) * (g.p + 1) * (prec == 0 ? sizeof(double2) : sizeof(float2));
   for (int l = 2; l <= g.L; l++) {
-    if (l < g.L) {  // few cells: one CTA per cell
-      const unsigned cells = 1u << (3 * (l - 1));
-      if (prec == 0) k_downward_cell<double><<<cells, 128, smc, s>>>(g, d, l);
-      else k_downward_cell<float><<<cells, 128, smc, s>>>(g, d, l);
-      continue;
-    }
-    unsigned npar = 1u << (3 * (l - 2));
-    unsigned blocks = (npar + DW_PAR - 1) / DW_PAR;
-    if (prec == 0)
-      k_downward<double><<<blocks, 256, sm, s>>>(g, d, l);
-    else
-      k_downward<float><<<blocks, 256, sm, s>>>(g, d, l);
+    const unsigned cells = 1u << (3 * (l - 1));
+    if (prec == 0) k_downward_cell<double><<<cells, 128, smc, s>>>(g, d, l);
+    else k_downward_cell<float><<<cells, 128, smc, s>>>(g, d, l);
   }
 }
 

@@ -982,60 +982,57 @@ void kmc_accept_from_event(const Geo& g, const Dev& d, cudaStream_t s) { k_move_
 
 
 // multipoles of the ancestors of the old and new positions, all levels:
-// Mt_l[anc(r)] -= q R(r - c), Mt_l[anc(r')] += q R(r' - c).  thread per (level, m).
+// Mt_l[anc(r)] -= q R(r - c), Mt_l[anc(r')] += q R(r' - c).  thread per
+// (level, coefficient); each value from the regular-harmonic recurrences.
 // The level-1 change (about the domain centre) is also stored in dK for the
 // far-field update.
 __global__ void k_acc_multipole(const Geo g, const Dev d) {
   MoveRec mv = *d.move;
   if (!mv.valid) return;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int l = 1 + t / (g.p + 1), m = t % (g.p + 1);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int l = 1 + t / g.P, ci = t % g.P;
   if (l > g.L) return;
-  int nl = 1 << (l - 1);
-  double wl = g.a / nl;
-  double2 row[2][KMC_MAXP + 1];
+  int n = 0;
+  while (tri(n + 1, 0) <= ci) n++;
+  const int m = ci - tri(n, 0);
+  const int nl = 1 << (l - 1);
+  const double wl = g.a / nl;
+  double2 val[2];
   int64_t cell[2];
   for (int side = 0; side < 2; side++) {
     const double* x = side ? mv.rn : mv.r;
-    double q = side ? mv.q : -mv.q;
-    int cx = cell_at(x[0], nl, g.inv_a), cy = cell_at(x[1], nl, g.inv_a), cz = cell_at(x[2], nl, g.inv_a);
+    const double q = side ? mv.q : -mv.q;
+    const int cx = cell_at(x[0], nl, g.inv_a), cy = cell_at(x[1], nl, g.inv_a), cz = cell_at(x[2], nl, g.inv_a);
     cell[side] = cx + (int64_t)nl * (cy + (int64_t)nl * cz);
-    double dx = x[0] - (cx + 0.5) * wl, dy = x[1] - (cy + 0.5) * wl, dz = x[2] - (cz + 0.5) * wl;
-    double r2 = dx * dx + dy * dy + dz * dz;
+    const double dx = x[0] - (cx + 0.5) * wl, dy = x[1] - (cy + 0.5) * wl, dz = x[2] - (cz + 0.5) * wl;
+    const double r2 = dx * dx + dy * dy + dz * dz;
     double2 mm = make_double2(1.0, 0.0);
     for (int j = 1; j <= m; j++) {
-      double sc = c_halfm_d[j];
+      const double sc = c_halfm_d[j];
       mm = make_double2(sc * (dx * mm.x - dy * mm.y), sc * (dx * mm.y + dy * mm.x));
     }
     double2 a1 = mm, a2 = make_double2(0.0, 0.0);
-    row[side][m] = make_double2(q * mm.x, q * mm.y);
-    for (int n = m + 1; n <= g.p; n++) {
-      double cc = c_inv_d[tri(n, m)];
-      double zz = (2 * n - 1) * dz;
-      double2 v = make_double2((zz * a1.x - r2 * a2.x) * cc, (zz * a1.y - r2 * a2.y) * cc);
-      row[side][n] = make_double2(q * v.x, q * v.y);
+    for (int nn = m + 1; nn <= n; nn++) {
+      const double cc = c_inv_d[tri(nn, m)];
+      const double zz = (2 * nn - 1) * dz;
+      const double2 v = make_double2((zz * a1.x - r2 * a2.x) * cc, (zz * a1.y - r2 * a2.y) * cc);
       a2 = a1;
       a1 = v;
     }
+    val[side] = make_double2(q * a1.x, q * a1.y);
   }
-  if (l == 1)
-    for (int n = m; n <= g.p; n++)
-      d.dK[tri(n, m)] = make_double2(row[0][n].x + row[1][n].x, row[0][n].y + row[1][n].y);
+  if (l == 1) d.dK[ci] = make_double2(val[0].x + val[1].x, val[0].y + val[1].y);
   if (cell[0] == cell[1]) {
-    for (int n = m; n <= g.p; n++) {
-      row[0][n].x += row[1][n].x;
-      row[0][n].y += row[1][n].y;
-    }
+    val[0].x += val[1].x;
+    val[0].y += val[1].y;
   }
-  int nside = cell[0] == cell[1] ? 1 : 2;
+  const int nside = cell[0] == cell[1] ? 1 : 2;
   for (int side = 0; side < nside; side++) {
-    double2* out = d.Mt + (g.cell_off[l] + cell[side]) * g.P;
-    for (int n = m; n <= g.p; n++) {
-      double2 v = out[tri(n, m)];
-      row[side][n].x += v.x;
-      row[side][n].y += v.y;
-    }
-    for (int n = m; n <= g.p; n++) out[tri(n, m)] = row[side][n];
+    double2* out = d.Mt + (g.cell_off[l] + cell[side]) * g.P + ci;
+    double2 v = *out;
+    v.x += val[side].x;
+    v.y += val[side].y;
+    *out = v;
   }
 }
 
@@ -1075,31 +1072,25 @@ __global__ void k_acc_far(const Geo g, const Dev d) {
 
 // P2L of a point charge q at offset (dx,dy,dz) from a cell centre, all (n, m):
 // out[tri(n,m)] (+)= q conj(I_n^m(d)).
-template <bool ACCUM>
-__device__ void p2l_table(double2* out, double q, double dx, double dy, double dz, int p) {
-  double r2 = dx * dx + dy * dy + dz * dz, inv = 1.0 / r2;
+// column m of the P2L table of charge q at offset (dx, dy, dz) from the
+// expansion centre: out[tri(n, m)] = q conj(I_n^m(d)) for n = m .. p
+__device__ void p2l_column(double2* out, double q, double dx, double dy, double dz, int p, int m) {
+  const double r2 = dx * dx + dy * dy + dz * dz, inv = 1.0 / r2;
   double2 mm = make_double2(1.0 / sqrt(r2), 0.0);
-  for (int m = 0; m <= p; m++) {
-    if (m > 0) {
-      double sc = -(2.0 * m - 1.0) * inv;
-      mm = make_double2(sc * (dx * mm.x - dy * mm.y), sc * (dx * mm.y + dy * mm.x));
+  for (int j = 1; j <= m; j++) {
+    const double sc = -(2.0 * j - 1.0) * inv;
+    mm = make_double2(sc * (dx * mm.x - dy * mm.y), sc * (dx * mm.y + dy * mm.x));
+  }
+  double2 a1 = mm, a2 = make_double2(0.0, 0.0), v = mm;
+  for (int n = m; n <= p; n++) {
+    if (n > m) {
+      const double zz = (2 * n - 1) * dz;
+      const double c2 = (double)((n - 1) * (n - 1) - m * m);
+      v = make_double2((zz * a1.x - c2 * a2.x) * inv, (zz * a1.y - c2 * a2.y) * inv);
+      a2 = a1;
+      a1 = v;
     }
-    double2 a1 = mm, a2 = make_double2(0.0, 0.0), v = mm;
-    for (int n = m; n <= p; n++) {
-      if (n > m) {
-        double zz = (2 * n - 1) * dz;
-        double c2 = (double)((n - 1) * (n - 1) - m * m);
-        v = make_double2((zz * a1.x - c2 * a2.x) * inv, (zz * a1.y - c2 * a2.y) * inv);
-        a2 = a1;
-        a1 = v;
-      }
-      if (ACCUM) {
-        out[tri(n, m)].x += q * v.x;
-        out[tri(n, m)].y -= q * v.y;
-      } else {
-        out[tri(n, m)] = make_double2(q * v.x, -q * v.y);
-      }
-    }
+    out[tri(n, m)] = make_double2(q * v.x, -q * v.y);
   }
 }
 
@@ -1118,8 +1109,8 @@ __device__ __forceinline__ bool image_in_il(const int u0[3], int nl, int nu, con
   return in && far;
 }
 
-// coarse levels 2 and 3: thread per (cell, image of either position); the P2L
-// tables go to a scratch area and are summed over the images in fixed order by
+// coarse levels 2 and 3: thread per (cell, image of either position, m); the
+// P2L tables go to a scratch area and are summed over the images in fixed order by
 // k_acc_coarse_reduce.  Level 2 (8 cells) sees every image nu with
 // |nu|_inf <= KMC_TOP (the block its interaction list covers) that is not one
 // of the cell's 27 neighbours; level 3 (64 cells) the 27 nearest images under
@@ -1132,7 +1123,8 @@ __device__ __forceinline__ bool image_in_il(const int u0[3], int nl, int nu, con
 __global__ void k_acc_coarse(const Geo g, const Dev d, double2* scratch) {
   MoveRec mv = *d.move;
   if (!mv.valid) return;
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // (slot, m)
+  const int slot = t / (g.p + 1), m = t - slot * (g.p + 1);
   if (slot >= KMC_COARSE_SLOTS) return;
   int l, cell, im, nimg1, span;
   if (slot < KMC_L2_SLOTS) {
@@ -1161,54 +1153,51 @@ __global__ void k_acc_coarse(const Geo g, const Dev d, double2* scratch) {
   }
   double2* out = scratch + (int64_t)slot * g.P;
   if (!in_il) {
-    for (int c = 0; c < g.P; c++) out[c] = make_double2(0.0, 0.0);
+    for (int n = m; n <= g.p; n++) out[tri(n, m)] = make_double2(0.0, 0.0);
     return;
   }
   double dx = x[0] + g.a * nv[0] - (b[0] + 0.5) * wl, dy = x[1] + g.a * nv[1] - (b[1] + 0.5) * wl,
          dz = x[2] + g.a * nv[2] - (b[2] + 0.5) * wl;
-  p2l_table<false>(out, q, dx, dy, dz, g.p);
+  p2l_column(out, q, dx, dy, dz, g.p, m);
 }
 
-__global__ void k_acc_coarse_reduce(const Geo g, const Dev d, const double2* scratch) {
+// one CTA (8 warps) per coarse cell: warp w sums the slots w, w + 8, ... of
+// the cell (lanes over coefficients, coalesced rows), then the eight warp
+// partials are added in warp order
+#define ACR_WARPS 8
+__global__ void __launch_bounds__(32 * ACR_WARPS) k_acc_coarse_reduce(const Geo g, const Dev d, const double2* scratch) {
+  extern __shared__ double2 acr[];  // [ACR_WARPS][P]
   MoveRec mv = *d.move;
   if (!mv.valid) return;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int cc = t / g.P, c = t % g.P;
-  if (cc >= KMC_COARSE_CELLS) return;
+  const int cc = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int l, cell, first, nslot;
   if (cc < 8) { l = 2; cell = cc; first = cc * 2 * KMC_TOP_NIMG; nslot = 2 * KMC_TOP_NIMG; }
   else { l = 3; cell = cc - 8; first = KMC_L2_SLOTS + cell * 54; nslot = 54; }
-  // eight independent partial sums (loads in flight together), combined in a
-  // fixed order
-  double px[8], py[8];
-#pragma unroll
-  for (int u = 0; u < 8; u++) px[u] = py[u] = 0.0;
-  int s2 = 0;
-  for (; s2 + 8 <= nslot; s2 += 8) {
-#pragma unroll
-    for (int u = 0; u < 8; u++) {
-      const double2 v = scratch[((int64_t)first + s2 + u) * g.P + c];
-      px[u] += v.x;
-      py[u] += v.y;
+  for (int c0 = 0; c0 < g.P; c0 += 32) {
+    const int c = c0 + lane;
+    double ax = 0.0, ay = 0.0;
+    if (c < g.P)
+      for (int s2 = warp; s2 < nslot; s2 += ACR_WARPS) {
+        const double2 v = scratch[((int64_t)first + s2) * g.P + c];
+        ax += v.x;
+        ay += v.y;
+      }
+    if (c < g.P) acr[warp * g.P + c] = make_double2(ax, ay);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < g.P; c += blockDim.x) {
+    double ax = 0.0, ay = 0.0;
+    for (int w = 0; w < ACR_WARPS; w++) {
+      ax += acr[w * g.P + c].x;
+      ay += acr[w * g.P + c].y;
     }
+    const int64_t at = (g.cell_off[l] + cell) * g.P + c;
+    double2 v = d.Psi[at];
+    v.x += ax;
+    v.y += ay;
+    d.Psi[at] = v;
+    if (d.Psi32) d.Psi32[at] = make_float2((float)v.x, (float)v.y);
   }
-  for (int u = 0; s2 < nslot; s2++, u++) {
-    const double2 v = scratch[((int64_t)first + s2) * g.P + c];
-    px[u] += v.x;
-    py[u] += v.y;
-  }
-  double ax = 0.0, ay = 0.0;
-#pragma unroll
-  for (int u = 0; u < 8; u++) {
-    ax += px[u];
-    ay += py[u];
-  }
-  const int64_t at = (g.cell_off[l] + cell) * g.P + c;
-  double2 v = d.Psi[at];
-  v.x += ax;
-  v.y += ay;
-  d.Psi[at] = v;
-  if (d.Psi32) d.Psi32[at] = make_float2((float)v.x, (float)v.y);
 }
 
 int kmc_coarse_slots() { return KMC_COARSE_SLOTS; }
@@ -1254,32 +1243,41 @@ __global__ void k_acc_fine(const Geo g, const Dev d, int lmin) {
   for (int side = 0; side < 2; side++) {
     const double* x = side ? mv.rn : mv.r;
     double q = side ? mv.q : -mv.q;
-    int u0[3];
-    for (int c = 0; c < 3; c++) u0[c] = cell_at(x[c], nl, g.inv_a);
-    for (int nu = 0; nu < 27; nu++) {
-      if (!image_in_il(u0, nl, nu, b)) continue;
-      any = true;
-      int nv[3] = {nu % 3 - 1, (nu / 3) % 3 - 1, nu / 9 - 1};
-      double dx = x[0] + g.a * nv[0] - (b[0] + 0.5) * wl, dy = x[1] + g.a * nv[1] - (b[1] + 0.5) * wl,
-             dz = x[2] + g.a * nv[2] - (b[2] + 0.5) * wl;
-      double r2 = dx * dx + dy * dy + dz * dz, inv = 1.0 / r2;
-      double2 mm = make_double2(1.0 / sqrt(r2), 0.0);
-      for (int j = 1; j <= m; j++) {
-        double sc = -(2.0 * j - 1.0) * inv;
-        mm = make_double2(sc * (dx * mm.x - dy * mm.y), sc * (dx * mm.y + dy * mm.x));
-      }
-      double2 a1 = mm, a2 = make_double2(0.0, 0.0);
-      acc[m].x += q * mm.x;
-      acc[m].y -= q * mm.y;
-      for (int n = m + 1; n <= g.p; n++) {
-        double zz = (2 * n - 1) * dz;
-        double c2 = (double)((n - 1) * (n - 1) - m * m);
-        double2 v = make_double2((zz * a1.x - c2 * a2.x) * inv, (zz * a1.y - c2 * a2.y) * inv);
-        acc[n].x += q * v.x;
-        acc[n].y -= q * v.y;
-        a2 = a1;
-        a1 = v;
-      }
+    // n_l >= 8: the only image of the position's cell within three cells of b
+    // is the minimum image; it contributes when it is in b's interaction list
+    int nv[3];
+    bool in = true, far = false;
+    for (int c = 0; c < 3; c++) {
+      const int u = cell_at(x[c], nl, g.inv_a);
+      int du = b[c] - u;
+      nv[c] = 0;
+      if (2 * du > nl) nv[c] = 1;
+      else if (2 * du < -nl) nv[c] = -1;
+      const int ui = u + nl * nv[c];
+      if (abs(fdiv2(ui) - (b[c] >> 1)) > 1) in = false;
+      if (abs(ui - b[c]) >= 2) far = true;
+    }
+    if (!(in && far)) continue;
+    any = true;
+    const double dx = x[0] + g.a * nv[0] - (b[0] + 0.5) * wl, dy = x[1] + g.a * nv[1] - (b[1] + 0.5) * wl,
+                 dz = x[2] + g.a * nv[2] - (b[2] + 0.5) * wl;
+    const double r2 = dx * dx + dy * dy + dz * dz, inv = 1.0 / r2;
+    double2 mm = make_double2(1.0 / sqrt(r2), 0.0);
+    for (int j = 1; j <= m; j++) {
+      const double sc = -(2.0 * j - 1.0) * inv;
+      mm = make_double2(sc * (dx * mm.x - dy * mm.y), sc * (dx * mm.y + dy * mm.x));
+    }
+    double2 a1 = mm, a2 = make_double2(0.0, 0.0);
+    acc[m].x += q * mm.x;
+    acc[m].y -= q * mm.y;
+    for (int n = m + 1; n <= g.p; n++) {
+      const double zz = (2 * n - 1) * dz;
+      const double c2 = (double)((n - 1) * (n - 1) - m * m);
+      const double2 v = make_double2((zz * a1.x - c2 * a2.x) * inv, (zz * a1.y - c2 * a2.y) * inv);
+      acc[n].x += q * v.x;
+      acc[n].y -= q * v.y;
+      a2 = a1;
+      a1 = v;
     }
   }
   if (!any) return;
@@ -1357,12 +1355,12 @@ __global__ void k_acc_move(const Geo g, const Dev d) {
 }
 
 void kmc_accept_apply(const Geo& g, const Dev& d, cudaStream_t s) {
-  int nt = g.L * (g.p + 1);
-  k_acc_multipole<<<(nt + 31) / 32, 32, 0, s>>>(g, d);
+  const int nt = g.L * g.P;
+  k_acc_multipole<<<(nt + 127) / 128, 128, 0, s>>>(g, d);
   k_acc_far<<<g.P, 32, 0, s>>>(g, d);
   // coarse levels 2 and 3 (8 + 64 cells, L >= 3 always): all cells x all images
-  k_acc_coarse<<<(KMC_COARSE_SLOTS + 63) / 64, 64, 0, s>>>(g, d, d.acc_scratch);
-  k_acc_coarse_reduce<<<(KMC_COARSE_CELLS * g.P + 127) / 128, 128, 0, s>>>(g, d, d.acc_scratch);
+  k_acc_coarse<<<(KMC_COARSE_SLOTS * (g.p + 1) + 127) / 128, 128, 0, s>>>(g, d, d.acc_scratch);
+  k_acc_coarse_reduce<<<KMC_COARSE_CELLS, 32 * ACR_WARPS, sizeof(double2) * ACR_WARPS * g.P, s>>>(g, d, d.acc_scratch);
   if (g.L >= 4) {
     dim3 grid((432 * (g.p + 1) + 63) / 64, g.L - 3);
     k_acc_fine<<<grid, 64, 0, s>>>(g, d, 4);
