@@ -229,6 +229,17 @@ int kmc_batch_run(kmc_batch_handle b, int steps, const double* uniforms, int64_t
 const char* kmc_batch_last_error(kmc_batch_handle b);
 void kmc_batch_destroy(kmc_batch_handle b);
 
+/*
+ * Diagnostic with no counterpart in the paper: runs, on `device`, the bounded
+ * device-side wait that the FP32 lattice propose uses for its bulk copies,
+ * against a barrier phase that can never complete (bytes expected, nothing
+ * copied), with a limit of limit_seconds (clamped to [0.001, 2]).  Returns
+ * KMC_ERR_TIMEOUT when the wait gave up and the kernel returned as designed,
+ * KMC_OK if it did not time out (a defect), KMC_ERR_CUDA on a CUDA error.
+ * Allocates a 4-byte flag for the duration of the call; no handle needed.
+ */
+int kmc_check_bounded_wait(int device, double limit_seconds);
+
 /* Message of the last error on this handle (static string if h is NULL). */
 const char* kmc_last_error(kmc_handle h);
 

@@ -38,6 +38,7 @@ EXPORTS = [
     "kmc_opts_default", "kmc_fmm_init", "kmc_fmm_energy", "kmc_fmm_propose", "kmc_fmm_propose_lattice",
     "kmc_fmm_accept", "kmc_fmm_accept_event", "kmc_step", "kmc_run", "kmc_run_profiled", "kmc_fmm_recompute",
     "kmc_fmm_leaf_index", "kmc_fmm_positions", "kmc_last_error", "kmc_fmm_destroy", "kmc_select_static",
+    "kmc_check_bounded_wait",
     "kmc_batch_create", "kmc_batch_run", "kmc_batch_last_error", "kmc_batch_destroy",
 ]
 
@@ -90,6 +91,7 @@ def load_library(path: str | None = None):
             "kmc_last_error": (ctypes.c_char_p, [P]),
             "kmc_fmm_destroy": (None, [P]),
             "kmc_select_static": (I, [P, I64, D, D, P, P, P, P]),
+            "kmc_check_bounded_wait": (I, [I, D]),
             "kmc_batch_create": (I, [P, I, P]),
             "kmc_batch_run": (I, [P, I, P, P, P]),
             "kmc_batch_last_error": (ctypes.c_char_p, [P]),
@@ -409,3 +411,9 @@ def kmc_batch_destroy(b: Batch) -> None:
     if b is not None and b.ptr is not None:
         load_library().kmc_batch_destroy(b.ptr)
         b.ptr = None
+
+
+def kmc_check_bounded_wait(device: int = 0, limit_seconds: float = 0.05) -> int:
+    """Status of the bounded-wait diagnostic: KMC_ERR_TIMEOUT (6) when the
+    device-side wait gave up and returned as designed."""
+    return int(load_library().kmc_check_bounded_wait(int(device), float(limit_seconds)))

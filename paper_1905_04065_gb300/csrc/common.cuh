@@ -209,6 +209,7 @@ void kmc_upload_constants(int p);
 void kmc_propose_lattice(const Geo& g, const Dev& d, int prec, cudaStream_t s);
 void kmc_finalize_rates(const Geo& g, const Dev& d, int prec, cudaStream_t s);
 void kmc_prepare(const Geo& g, int prec);
+int kmc_wait_probe(double limit_seconds, cudaStream_t s);  // flag bits, -1 on a CUDA error
 void kmc_rate_bsum(const Geo& g, const Dev& d, cudaStream_t s);
 void kmc_select(const Geo& g, const Dev& d, int use_counter, cudaStream_t s);
 void kmc_record(const Geo& g, const Dev& d, cudaStream_t s);

@@ -325,6 +325,35 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 #define KMC_WAIT_NS 1000000000ull  // one second
 
+// diagnostic: the bounded wait against a phase that never completes (16
+// bytes expected on the barrier, nothing copied)
+__global__ void k_wait_probe(uint64_t limit_ns, int* flag) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_expect_tx(&bar, 16);
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) *flag = KMC_DERR_TIMEOUT;
+}
+
+int kmc_wait_probe(double limit_seconds, cudaStream_t s) {
+  if (!(limit_seconds >= 0.001)) limit_seconds = 0.001;
+  if (limit_seconds > 2.0) limit_seconds = 2.0;
+  int* flag = nullptr;
+  if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return -1;
+  int host = 0;
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    k_wait_probe<<<1, 32, 0, s>>>((uint64_t)(limit_seconds * 1e9), flag);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&host, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(flag);
+  return e == cudaSuccess ? host : -1;
+}
+
 // FP64 form: one staged source in physical coordinates; (shx, shy, shz) is the
 // periodic image shift in sites
 __device__ __forceinline__ void stage_source(unsigned char* src, int e, double4_32a v, int shx, int shy, int shz,
@@ -348,7 +377,7 @@ __device__ __forceinline__ void stage_source(unsigned char* src, int e, double4_
 // where an output is written.  Potentials are written in precision T (FP32
 // arrays in the mixed form, FP64 arrays in the FP64 form).
 template <typename T>
-__global__ void __launch_bounds__(PROP_THREADS) k_propose_lattice(const Geo g, const Dev d, int chunk) {
+__global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g, const Dev d, int chunk) {
   typedef typename cplx<T>::type C;
   typedef typename vec4<T>::type V4;
   constexpr bool F32 = sizeof(T) == 4;
@@ -647,11 +676,12 @@ static size_t propose_smem(const Geo& g, int prec, int chunk) {
          4 * (size_t)(3 * nbw + 1) + 2 * (size_t)((W3 + 1) & ~1);
 }
 
-// sources are streamed in chunks of at least 1024 (every neighbour leaf's
-// charges in one pass unless the neighbourhood is dense); even: FP32 sources
-// are staged in pairs
+// sources are streamed in chunks of at least 960 (every neighbour leaf's
+// charges in one pass unless the neighbourhood is dense: 27 x 32 = 864 on
+// average at 1/16 occupancy and 8^3-site leaves), small enough for nine
+// 128-thread CTAs per SM
 static int propose_chunk(const Geo& g) {
-  int c = 1024 > g.cap ? 1024 : g.cap;
+  int c = 960 > g.cap ? 960 : g.cap;
   return (c + 1) & ~1;
 }
 

@@ -939,6 +939,13 @@ int kmc_batch_create(kmc_batch_handle* out, int count, const kmc_handle* handles
   return KMC_OK;
 }
 
+int kmc_check_bounded_wait(int device, double limit_seconds) {
+  if (cudaSetDevice(device) != cudaSuccess) return KMC_ERR_CUDA;
+  const int f = kmc_wait_probe(limit_seconds, 0);
+  if (f < 0) return KMC_ERR_CUDA;
+  return (f & KMC_DERR_TIMEOUT) ? KMC_ERR_TIMEOUT : KMC_OK;
+}
+
 const char* kmc_batch_last_error(kmc_batch_handle b) { return b ? b->msg : g_static_msg; }
 
 void kmc_batch_destroy(kmc_batch_handle b) {

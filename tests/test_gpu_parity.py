@@ -90,6 +90,49 @@ def test_madelung_energy_fmm():
     assert abs(U / E ** 3 + 1.747564594633182 / 2) < 1e-6
 
 
+def test_fully_occupied_lattice_has_no_event():
+    """Degenerate case: every site occupied, so every hop is masked: masks all
+    zero, dU all NaN, total rate Q = 0, no event (-1) and an infinite waiting
+    time; the host-driven and graph-replayed loops agree."""
+    k = _k()
+    E = 8
+    s = np.arange(E ** 3)
+    q = (-1.0) ** workloads.site_xyz(E, s).sum(1)
+    for precision in ("fp64", "mixed"):
+        h = _init(E, s, q, 3, 8, precision=precision)
+        mask, dU = k.kmc_fmm_propose_lattice(h)
+        assert not mask.any() and np.all(np.isnan(dU))
+        ev, dt, Q = k.kmc_step(h, None, 0.5, 0.5)
+        assert ev == -1 and Q == 0.0 and math.isinf(dt)
+        evs, dts = k.kmc_run(h, np.full((3, 2), 0.5))
+        assert np.all(np.asarray(evs) == -1)
+
+
+def test_two_charge_system():
+    """Smallest neutral system: one +1 and one -1 on a 16^3 lattice; every dU
+    against the oracle, a trajectory of accepted hops, and the tracked energy
+    against the oracle's after the moves.  All dU are tiny here (~1e-2), so
+    the bound is absolute: the p = 12 truncation error of one pair
+    interaction across two leaves is ~2e-4 of 1/r ~ 0.08."""
+    k = _k()
+    E = 16
+    sites = np.array([0, 9 + E * (3 + E * 7)])
+    q = np.array([1.0, -1.0])
+    st = oracle.LatticeState(E, sites, q)
+    h = _init(E, sites, q, 3, 12)
+    u = workloads.uniforms(20, 77)
+    for t in range(20):
+        mask, dU = k.kmc_fmm_propose_lattice(h)
+        dU_o, mask_o = st.propose()
+        assert np.array_equal(mask, mask_o)
+        ok = mask_o.astype(bool)
+        assert np.max(np.abs(dU[ok] - dU_o[ok])) < 1e-4
+        j, _, _ = oracle.select(oracle.rates(dU_o, mask_o, 0.1), u[t, 0], u[t, 1])
+        k.kmc_fmm_accept_event(h, j)
+        st.accept(j // 6, j % 6)
+    assert abs(k.kmc_fmm_energy(h) - st.energy()) < 1e-4
+
+
 def test_leaf_index_exact(small):
     k = _k()
     w, sites, q, st = small
@@ -345,3 +388,20 @@ def test_offlattice_propose_and_accept():
     assert abs(du - ref[0]) < 1e-4 * np.max(np.abs(ref))
     U1 = k.kmc_fmm_energy(h)
     assert abs((U1 - U0) - du) < 1e-12 * abs(U0) + 1e-12
+
+
+def test_bounded_device_wait_gives_up_and_context_survives(small):
+    """The bounded mbarrier wait of the propose kernel, run against a phase
+    that never completes, returns KMC_ERR_TIMEOUT after its limit; the CUDA
+    context stays usable (a propose afterwards matches the oracle)."""
+    import time
+    k = _k()
+    t0 = time.perf_counter()
+    assert k.kmc_check_bounded_wait(0, 0.05) == k.KMC_ERR_TIMEOUT
+    assert time.perf_counter() - t0 >= 0.05
+    w, sites, q, st = small
+    h = _init(w["E"], sites, q, w["L"], 8, precision="mixed")
+    mask, dU = k.kmc_fmm_propose_lattice(h)
+    dU_o, mask_o = st.propose()
+    assert np.array_equal(mask, mask_o)
+    assert _rel_err(dU, dU_o, mask_o) < TOL[8]
