@@ -364,6 +364,16 @@ __device__ __forceinline__ void stage_source(unsigned char* src, int e, double4_
   NearField<double>::stage(src, e, v);
 }
 
+// list index of leaf f in {own leaf (f = 0), neighbour across face f - 1}
+// within the 27-neighbourhood list (own leaf first, then x fastest, centre
+// skipped)
+__device__ __forceinline__ int face_leaf(int f) {
+  if (!f) return 0;
+  const int* o = c_hop[f - 1];
+  const int qq = (o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1);
+  return qq < 13 ? qq + 1 : qq;
+}
+
 // Evaluation is per distinct site of the leaf: the potential at a site is
 // needed once even when several charges propose to hop there, and at an own
 // charge's site it is that charge's old-position potential (the pair at
@@ -390,9 +400,10 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
   uint64_t* bar = (uint64_t*)(nb_base + 27);        // [1] copy barrier (FP32 form)
   int* nb_off = (int*)(bar + 1);                    // [28] first source of each leaf (FP64) / first group (FP32)
   int* nb_cnt = nb_off + 28;                        // [27] charges per leaf
-  int* pq = nb_cnt + 27;                            // [28] first leaf of each source pass; pq[npass] = 27
-  int* misc = pq + 28;                              // [3] number of passes (padded to 8 bytes)
-  T* phis = (T*)(misc + 3);                         // [W3] potential per local site
+  int* nb_leaf = nb_cnt + 27;                       // [27] leaf index
+  int* pq = nb_leaf + 27;                           // [28] first leaf of each source pass; pq[npass] = 27
+  int* misc = pq + 28;                              // [4] number of passes (padded to 8 bytes)
+  T* phis = (T*)(misc + 4);                         // [W3] potential per local site
   uint32_t* bits = (uint32_t*)(phis + W3);          // [nbw] occupied sites
   uint32_t* need = bits + nbw;                      // [nbw] sites where a potential is needed
   int* woff = (int*)(need + nbw);                   // [nbw + 1] prefix of needed sites per word
@@ -419,70 +430,99 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
   }
   // (0) list entry 0 is this leaf, entries 1..26 the other neighbours in
   // 27-neighbourhood order (x fastest), centre skipped
-  if (tid < 27) {
-    const int qq = tid == 0 ? 13 : (tid <= 13 ? tid - 1 : tid);
-    const int ux = lx + qq % 3 - 1, uy = ly + (qq / 3) % 3 - 1, uz = lz + qq / 9 - 1;
-    const int sx = (ux + nL) % nL, sy = (uy + nL) % nL, sz = (uz + nL) % nL;
-    const int64_t nleaf = sx + (int64_t)nL * (sy + (int64_t)nL * sz);
-    nb_base[tid] = nleaf * g.cap;
-    nb_cnt[tid] = d.cnt[nleaf];
-  }
   if (F32 && tid == 0) mbar_init(bar, 1);
-  __syncthreads();
-  if (tid == 0) {
-    // prefix over the leaves (sources or groups) and the greedy split into
-    // passes at leaf boundaries; one leaf always fits (pass_cap >= capacity)
-    int acc = 0, np = 0, start = 0;
-    pq[0] = 0;
-    for (int q = 0; q < 27; q++) {
-      const int u = F32 ? (nb_cnt[q] + 3) >> 2 : nb_cnt[q];
-      if (acc + u - start > pass_cap) {
-        pq[++np] = q;
-        start = acc;
-      }
-      nb_off[q] = acc;
-      acc += u;
+  if (warp == 0) {
+    int u = 0;
+    if (lane < 27) {
+      const int qq = lane == 0 ? 13 : (lane <= 13 ? lane - 1 : lane);
+      const int ux = lx + qq % 3 - 1, uy = ly + (qq / 3) % 3 - 1, uz = lz + qq / 9 - 1;
+      const int sx = (ux + nL) % nL, sy = (uy + nL) % nL, sz = (uz + nL) % nL;
+      const int nleaf = sx + nL * (sy + nL * sz);
+      nb_leaf[lane] = nleaf;
+      nb_base[lane] = (int64_t)nleaf * g.cap;
+      const int c = d.cnt[nleaf];
+      nb_cnt[lane] = c;
+      u = F32 ? (c + 3) >> 2 : c;
     }
-    nb_off[27] = acc;
-    pq[++np] = 27;
-    misc[0] = np;
-    misc[1] = 0;
-    if (F32) {  // first pass: one bulk copy per leaf, overlapped with phases 1-3
+    // offsets of the leaves (sources or groups): warp scan
+    int incl = u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t2 = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t2;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 26);
+    if (lane < 27) nb_off[lane] = incl - u;
+    if (lane == 0) nb_off[27] = total;
+    __syncwarp();
+    if (lane == 0) {
+      // the split into passes at leaf boundaries (one pass unless the
+      // neighbourhood is dense); one leaf always fits (pass_cap >= capacity)
+      int np = 0;
+      pq[0] = 0;
+      if (total > pass_cap) {
+        int start = 0;
+        for (int q = 0; q < 27; q++) {
+          const int uq = F32 ? (nb_cnt[q] + 3) >> 2 : nb_cnt[q];
+          if (nb_off[q] + uq - start > pass_cap) {
+            pq[++np] = q;
+            start = nb_off[q];
+          }
+        }
+      }
+      pq[++np] = 27;
+      misc[0] = np;
+      misc[1] = 0;
+    }
+    __syncwarp();
+    if (F32) {  // first pass: one bulk copy per leaf (one lane each), overlapped with phases 1-3
       const int q1 = pq[1];
-      mbar_expect_tx(bar, (uint32_t)(nb_off[q1] * 80));
-      for (int q = 0; q < q1; q++) {
-        const int ng = (nb_cnt[q] + 3) >> 2;
-        if (ng)
-          bulk_copy_g2s(src + 80 * nb_off[q], d.sgrp + 20 * (nb_base[q] / g.cap) * gpl, (uint32_t)(80 * ng), bar);
+      if (lane == 0) mbar_expect_tx(bar, (uint32_t)(nb_off[q1] * 80));
+      __syncwarp();
+      if (lane < q1) {
+        const int ng = (nb_cnt[lane] + 3) >> 2;
+        if (ng) bulk_copy_g2s(src + 80 * nb_off[lane], d.sgrp + 20 * (int64_t)nb_leaf[lane] * gpl, (uint32_t)(80 * ng), bar);
       }
     }
   }
+  __syncthreads();
 
-  // (1) occupancy bitmap of this leaf's sites
+  // (1) + (2): warp w handles the leaves f = w and w + 4 of {own leaf (f = 0),
+  // the neighbour across face f - 1 (f = 1..6)}; the first 32 charges of
+  // each are loaded at once, before the occupancy barrier
+  static_assert(PROP_THREADS == 128, "four warps cover the seven leaves twice");
   const int cnt_own = nb_cnt[0];
   const int64_t base_own = nb_base[0];
-  for (int j = tid; j < cnt_own; j += blockDim.x) {
-    const V4 v = spos[base_own + j];
-    const int ls = (lattice_coord(v.x, ih) - gx0) + W * (lattice_coord(v.y, ih) - gy0 + W * (lattice_coord(v.z, ih) - gz0));
-    atomicOr(&bits[ls >> 5], 1u << (ls & 31));
-    atomicOr(&need[ls >> 5], 1u << (ls & 31));
+  V4 pv[2];
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    const int f = warp + 4 * i;
+    if (f <= KMC_NHOP) {
+      const int li = face_leaf(f);
+      if (lane < nb_cnt[li]) pv[i] = spos[nb_base[li] + lane];
+    }
   }
+  // (1) occupancy bitmap of this leaf's sites (warp 0)
+  if (warp == 0)
+    for (int j = lane; j < cnt_own; j += 32) {
+      const V4 v = j < 32 ? pv[0] : spos[base_own + j];
+      const int ls = (lattice_coord(v.x, ih) - gx0) + W * (lattice_coord(v.y, ih) - gy0 + W * (lattice_coord(v.z, ih) - gz0));
+      atomicOr(&bits[ls >> 5], 1u << (ls & 31));
+      atomicOr(&need[ls >> 5], 1u << (ls & 31));
+    }
   __syncthreads();
 
   // (2) hop targets inside this leaf: own hops and hops entering from the six
-  // face neighbours (f = 0 own leaf, f = 1..6 the neighbour across face f-1,
-  // hopping in direction (f-1)^1); one warp per leaf
-  for (int f = warp; f <= KMC_NHOP; f += nwarp) {
-    int li = 0;
-    if (f) {
-      const int* o = c_hop[f - 1];
-      const int qq = (o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1);
-      li = qq < 13 ? qq + 1 : qq;
-    }
+  // face neighbours (the neighbour across face f - 1 hops in direction (f-1)^1)
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    const int f = warp + 4 * i;
+    if (f > KMC_NHOP) continue;
+    const int li = face_leaf(f);
     const int64_t mb = nb_base[li];
     const int cm = nb_cnt[li];
     for (int j = lane; j < cm; j += 32) {
-      const V4 v = spos[mb + j];
+      const V4 v = j < 32 ? pv[i] : spos[mb + j];
       const int gx = lattice_coord(v.x, ih), gy = lattice_coord(v.y, ih), gz = lattice_coord(v.z, ih);
       const int k0 = f ? ((f - 1) ^ 1) : 0, k1 = f ? k0 + 1 : KMC_NHOP;
       for (int k = k0; k < k1; k++) {
@@ -501,14 +541,23 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
     }
   }
   __syncthreads();
-  // (3) compact the needed sites (ascending local index)
-  if (tid == 0) {
-    int acc = 0;
-    for (int w2 = 0; w2 < nbw; w2++) {
-      woff[w2] = acc;
-      acc += __popc(need[w2]);
+  // (3) compact the needed sites (ascending local index); word offsets by a
+  // warp scan
+  if (warp == 0) {
+    int base = 0;
+    for (int w0 = 0; w0 < nbw; w0 += 32) {
+      const int w2 = w0 + lane;
+      const int c = w2 < nbw ? __popc(need[w2]) : 0;
+      int incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t2 = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t2;
+      }
+      if (w2 < nbw) woff[w2] = base + incl - c;
+      base += __shfl_sync(0xffffffffu, incl, 31);
     }
-    woff[nbw] = acc;
+    if (lane == 0) woff[nbw] = base;
   }
   __syncthreads();
   for (int w2 = tid; w2 < nbw; w2 += blockDim.x) {
@@ -549,7 +598,7 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
             for (int q = q0; q < q1; q++) {
               const int ng = (nb_cnt[q] + 3) >> 2;
               if (ng)
-                bulk_copy_g2s(src + 80 * (nb_off[q] - nb_off[q0]), d.sgrp + 20 * (nb_base[q] / g.cap) * gpl,
+                bulk_copy_g2s(src + 80 * (nb_off[q] - nb_off[q0]), d.sgrp + 20 * (int64_t)nb_leaf[q] * gpl,
                               (uint32_t)(80 * ng), bar);
             }
           }
@@ -620,37 +669,55 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
         }
       }
     }
-    const T hw = (T)(0.5 * W);
-    if (b0 < nsites) {
-      const T near = F32 ? nf.sum(0) * ih : nf.sum(0);
-      phis[l0] = near + l2p_point<T, C>(Lc, g.p, ((T)ix0 + (T)0.5 - hw) * h, ((T)iy0 + (T)0.5 - hw) * h,
-                                        ((T)iz0 + (T)0.5 - hw) * h);
-    }
-    if (b1 < nsites) {
-      const T near = F32 ? nf.sum(1) * ih : nf.sum(1);
-      phis[l1] = near + l2p_point<T, C>(Lc, g.p, ((T)ix1 + (T)0.5 - hw) * h, ((T)iy1 + (T)0.5 - hw) * h,
-                                        ((T)iz1 + (T)0.5 - hw) * h);
-    }
+    if (b0 < nsites) phis[l0] = F32 ? nf.sum(0) * ih : nf.sum(0);
+    if (b1 < nsites) phis[l1] = F32 ? nf.sum(1) * ih : nf.sum(1);
   }
   if (F32 && nsites == 0) {  // the prefetched copies must land before the CTA leaves
     const bool ok = mbar_wait_bounded(bar, 0, KMC_WAIT_NS);
     if (!ok && tid == 0) atomicOr(&d.err[0], KMC_DERR_TIMEOUT);
   }
-  __syncthreads();
-  // (5) write-out: old-position potentials and unmasked hop potentials; one
-  // warp per leaf
-  for (int f = warp; f <= KMC_NHOP; f += nwarp) {
-    int li = 0;
-    if (f) {
-      const int* o = c_hop[f - 1];
-      const int qq = (o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1);
-      li = qq < 13 ? qq + 1 : qq;
+  // the write-out's inputs (first 32 charges of this warp's leaves) are
+  // loaded now, so that their latency passes during the L2P
+  V4 wv[2];
+  int32_t wu[2];
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    const int f = warp + 4 * i;
+    if (f <= KMC_NHOP) {
+      const int li = face_leaf(f);
+      if (lane < nb_cnt[li]) {
+        wu[i] = d.uid[nb_base[li] + lane];
+        wv[i] = spos[nb_base[li] + lane];
+      }
     }
+  }
+  // L2P, each site by the thread that summed its near field
+  {
+    const T hw = (T)(0.5 * W);
+    for (int rb = 0; rb < nsites; rb += 2 * blockDim.x) {
+#pragma unroll
+      for (int s2 = 0; s2 < 2; s2++) {
+        const int b = rb + tid + s2 * blockDim.x;
+        if (b < nsites) {
+          const int l = sites[b];
+          phis[l] += l2p_point<T, C>(Lc, g.p, ((T)(l % W) + (T)0.5 - hw) * h, ((T)((l / W) % W) + (T)0.5 - hw) * h,
+                                     ((T)(l / (W * W)) + (T)0.5 - hw) * h);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // (5) write-out: old-position potentials and unmasked hop potentials
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    const int f = warp + 4 * i;
+    if (f > KMC_NHOP) continue;
+    const int li = face_leaf(f);
     const int64_t mb = nb_base[li];
     const int cm = nb_cnt[li];
     for (int j = lane; j < cm; j += 32) {
-      const int32_t u = d.uid[mb + j];
-      const V4 v = spos[mb + j];
+      const int32_t u = j < 32 ? wu[i] : d.uid[mb + j];
+      const V4 v = j < 32 ? wv[i] : spos[mb + j];
       const int gx = lattice_coord(v.x, ih), gy = lattice_coord(v.y, ih), gz = lattice_coord(v.z, ih);
       if (f == 0) out_old[u] = phis[(gx - gx0) + W * ((gy - gy0) + W * (gz - gz0))];
       const int k0 = f ? ((f - 1) ^ 1) : 0, k1 = f ? k0 + 1 : KMC_NHOP;
@@ -672,7 +739,7 @@ static size_t propose_smem(const Geo& g, int prec, int chunk) {
   const int W3 = g.W * g.W * g.W;
   const int nbw = (W3 + 31) / 32;
   const size_t srcb = prec == 0 ? NearField<double>::bytes(chunk) : NearField<float>::bytes(chunk);
-  return srcb + 2 * ts * (size_t)g.P + 27 * 8 + 8 + (28 + 27 + 28 + 3) * 4 + ts * (size_t)W3 +
+  return srcb + 2 * ts * (size_t)g.P + 27 * 8 + 8 + (28 + 27 + 27 + 28 + 4) * 4 + ts * (size_t)W3 +
          4 * (size_t)(3 * nbw + 1) + 2 * (size_t)((W3 + 1) & ~1);
 }
 
