@@ -9,9 +9,12 @@ rates, selection, accept.
 
 Timed regions (CUDA events on the library's stream, after W warm-up steps):
   value   K steps of kmc_run_profiled, one step per call, L2 flushed (a
-          256 MiB write) between steps outside the events; dU evals/s =
-          unmasked proposals / step time.  The propose kernel's duration comes
-          from the library's per-phase events inside the same region.
+          256 MiB write) before every step; the step time is the device time
+          of the step's kernels, from the library's events recorded on the
+          launching stream before the first and after the last kernel (the
+          per-phase events inside the same call give the propose kernel's
+          duration); dU evals/s = unmasked proposals / step time.  The time
+          including the host-side call overhead is reported beside it.
   e2e     the host API path per step (kmc_fmm_propose_lattice into host
           buffers, kmc_step, kmc_fmm_accept_event), host<->device copies inside.
   fp64    the same step loop with the FP64 form (context line).
@@ -307,7 +310,7 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    step_ms, phases = [], np.zeros(k.KMC_NPHASE)
+    step_ms, outer_ms, phases = [], [], np.zeros(k.KMC_NPHASE)
     for s in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -316,7 +319,11 @@ def run_gpu(args):
         ev, dts, ph = k.kmc_run_profiled(h, u[args.warmup + s: args.warmup + s + 1])
         e1.record(stream)
         e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
+        # device time of the step: the library's events on this stream, from
+        # before the first kernel to after the last (contiguous phases); the
+        # outer pair also holds the host-side call overhead
+        step_ms.append(float(ph.sum()))
+        outer_ms.append(e0.elapsed_time(e1))
         phases += ph
     torch.cuda.synchronize()
     if world > 1:
@@ -373,7 +380,7 @@ def run_gpu(args):
             _, _, ph = k.kmc_run_profiled(h64, u[1 + s: 2 + s])
             e1.record(stream)
             e1.synchronize()
-            ms64.append(e0.elapsed_time(e1))
+            ms64.append(float(ph.sum()))
             ph64 += ph
         m64 = float(np.mean(ms64))
         fp64 = {"dU_evals_per_s": hops / (m64 * 1e-3), "kmc_steps_per_s": 1e3 / m64, "ms_per_step": m64,
@@ -417,6 +424,7 @@ def run_gpu(args):
         "kmc_steps_per_s": steps_per_s,
         "propose_only_dU_evals_per_s": hops / (prop_ms * 1e-3),
         "phase_ms_per_step": {nm: phases[i] / args.steps for i, nm in enumerate(k.PHASES)},
+        "ms_per_step_incl_call_overhead": float(np.mean(outer_ms)),
         "init_s": init_s,
         "fp64_form": fp64,
         "roofline": roof,

@@ -77,6 +77,7 @@ struct Geo {
   double kT;
   double inv_a;           // 1 / a
   int prec;               // 0 = FP64 form, 1 = mixed form
+  double qmax;            // largest |charge|
 };
 
 // cell coordinate of x on a level with n cells per side, floor(x n / a)
@@ -194,7 +195,8 @@ void fmm_p2m(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_m2m(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_itab(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_child_tables(const Geo& g, const Dev& d, cudaStream_t s);
-void fmm_m2l(const Geo& g, const Dev& d, cudaStream_t s);
+size_t fmm_m2l_scratch_bytes(const Geo& g);
+void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s);
 void fmm_lattice_sums(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_far_field(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_self_and_dipole(const Geo& g, const Dev& d, cudaStream_t s);

@@ -280,105 +280,222 @@ void fmm_itab(const Geo& g, const Dev& d, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ M2L
-// CTA per target cell on level l; thread per output coefficient.  The wrapped
-// interaction list of cell b (Sec. 3.1): offsets t = 2 delta + c - o with
-// delta in {-1,0,1}^3, c in {0,1}^3, o = b mod 2, excluding |t|_inf <= 1;
-// source = (b + t) mod n_l with translation vector t * w_l.
-__global__ void k_m2l(const Geo g, const Dev d, int l) {
-  extern __shared__ double2 shM[];  // P source coefficients
-  int nl = 1 << (l - 1);
-  int64_t cell = blockIdx.x;
-  int bx = (int)(cell % nl), by = (int)((cell / nl) % nl), bz = (int)(cell / ((int64_t)nl * nl));
-  int ox = bx & 1, oy = by & 1, oz = bz & 1;
-  int ci = threadIdx.x;
-  int n = 0, m = 0;
-  if (ci < g.P) {
+// The M2L of Algorithm 2 as dense real matrix products grouped by translation
+// vector.  A cell's coefficients (0 <= m <= n <= p, complex) are a real vector
+// of length 2P (re, im interleaved); the translation by t on level l,
+//   Psi_n^m += sum_{k, |l| <= k} (-1)^k Mt_k^l conj(I_{n+k}^{m+l}(t w_l)),
+// with Mt_k^{-l} = (-1)^l conj(Mt_k^l), is a real-linear map R_t (2P x 2P).
+// The wrapped interaction list of cell b (Sec. 3.1) depends only on the
+// parity o = b mod 2: offsets t = 2 delta + c - o with delta in {-1,0,1}^3,
+// c in {0,1}^3 and |t|_inf > 1 (189 of them), source (b + t) mod n_l.  So for
+// each parity class, Psi[:, cells] = sum_t R_t Mt[:, cells + t] is one
+// product of [R_t1 .. R_t189] (2P x 189*2P) with the stacked, gathered
+// source columns.
+
+// R_t for the 343 offsets t in [-3,3]^3 of level l (offsets with |t|_inf <= 1
+// are never used and left unset): R[(v * 2P + kk) * 2P + i] maps input real
+// coefficient kk to output real coefficient i.
+__global__ void k_m2l_rmat(const Geo g, const Dev d, int l, double* R) {
+  const int v = blockIdx.x;
+  const int tx = v % 7 - 3, ty = (v / 7) % 7 - 3, tz = v / 49 - 3;
+  if (abs(tx) <= 1 && abs(ty) <= 1 && abs(tz) <= 1) return;
+  const double2* It = d.Itab + ((int64_t)l * 343 + v) * g.P2;
+  const int n2 = 2 * g.P;
+  double* Rv = R + (int64_t)v * n2 * n2;
+  for (int ci = threadIdx.x; ci < g.P; ci += blockDim.x) {
+    int n = 0;
     while (tri(n + 1, 0) <= ci) n++;
-    m = ci - tri(n, 0);
-  }
-  double2 acc = make_double2(0.0, 0.0);
-  for (int dz = -1; dz <= 1; dz++)
-    for (int dy = -1; dy <= 1; dy++)
-      for (int dx = -1; dx <= 1; dx++)
-        for (int c = 0; c < 8; c++) {
-          int tx = 2 * dx + (c & 1) - ox, ty = 2 * dy + ((c >> 1) & 1) - oy, tz = 2 * dz + ((c >> 2) & 1) - oz;
-          if (abs(tx) <= 1 && abs(ty) <= 1 && abs(tz) <= 1) continue;
-          int sx = ((bx + tx) % nl + nl) % nl, sy = ((by + ty) % nl + nl) % nl, sz = ((bz + tz) % nl + nl) % nl;
-          int64_t src = sx + (int64_t)nl * (sy + (int64_t)nl * sz);
-          __syncthreads();
-          const double2* Ms = d.Mt + (g.cell_off[l] + src) * g.P;
-          for (int k = threadIdx.x; k < g.P; k += blockDim.x) shM[k] = Ms[k];
-          __syncthreads();
-          if (ci < g.P) {
-            int v = (tx + 3) + 7 * ((ty + 3) + 7 * (tz + 3));
-            const double2* It = d.Itab + ((int64_t)l * 343 + v) * g.P2;
-            for (int k = 0; k <= g.p; k++) {
-              double2 s = make_double2(0.0, 0.0);
-              for (int ll = -k; ll <= k; ll++) {
-                double2 a = tab_get(shM, k, ll);
-                double2 b = tab_get(It, n + k, m + ll);
-                // a * conj(b)
-                s.x += a.x * b.x + a.y * b.y;
-                s.y += a.y * b.x - a.x * b.y;
-              }
-              if (k & 1) { acc.x -= s.x; acc.y -= s.y; }
-              else { acc.x += s.x; acc.y += s.y; }
-            }
-          }
+    const int m = ci - tri(n, 0);
+    for (int k = 0; k <= g.p; k++) {
+      const double sk = (k & 1) ? -1.0 : 1.0;
+      for (int lp = 0; lp <= k; lp++) {
+        const double2 I1 = It[tri(n + k, m + lp)];
+        double rr = I1.x, ri = I1.y, ir = -I1.y, ii = I1.x;  // (re, im) out x (a, b) in
+        if (lp > 0) {  // the mirrored input Mt_k^{-lp} = (-1)^lp conj(Mt_k^lp)
+          const double2 I2 = tab_get(It, n + k, m - lp);
+          const double sl = (lp & 1) ? -1.0 : 1.0;
+          rr += sl * I2.x;
+          ri -= sl * I2.y;
+          ir -= sl * I2.y;
+          ii -= sl * I2.x;
         }
-  if (ci < g.P) d.Psi[(g.cell_off[l] + cell) * g.P + ci] = acc;
+        const int kk = 2 * tri(k, lp);
+        Rv[(int64_t)kk * n2 + 2 * ci] = sk * rr;
+        Rv[(int64_t)(kk + 1) * n2 + 2 * ci] = sk * ri;
+        Rv[(int64_t)kk * n2 + 2 * ci + 1] = sk * ir;
+        Rv[(int64_t)(kk + 1) * n2 + 2 * ci + 1] = sk * ii;
+      }
+    }
+  }
 }
 
-// level 2: every level-2 cell u of the (2 KMC_TOP + 1)^3 block of domain copies
-// (coordinates -2 KMC_TOP .. 2 KMC_TOP + 1 per axis) except the 27 nearest
-// of cell b; source (u mod 2), translation (u - b) w_2
-__global__ void k_m2l_top(const Geo g, const Dev d) {
+// One parity class, a tile of G_MT output rows x G_NT target cells, FP64:
+// 256 threads, 4 x 4 outputs each (rows tm + 16 r, cells tn + 16 c).
+#define G_MT 64
+#define G_NT 64
+#define G_KT 16
+__global__ void __launch_bounds__(256) k_m2l_gemm(const Geo g, const Dev d, int l, const double* R) {
+  __shared__ double As[G_KT][G_MT];
+  __shared__ double Bs[G_KT][G_NT];
+  __shared__ int bcell[G_NT];  // target cells of the tile (-1: none)
+  __shared__ int scell[G_NT];  // their sources for the current offset
+  const int nl = 1 << (l - 1), h2 = nl >> 1;
+  const int o = blockIdx.y, ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+  const int64_t ncls = (int64_t)h2 * h2 * h2;
+  const int64_t j0 = (int64_t)blockIdx.x * G_NT;
+  const int i0 = blockIdx.z * G_MT;
+  const int n2 = 2 * g.P;
+  const int tid = threadIdx.x, tm = tid >> 4, tn = tid & 15;
+  if (tid < G_NT) {
+    const int64_t j = j0 + tid;
+    int b = -1;
+    if (j < ncls) {
+      const int jx = (int)(j % h2), jy = (int)((j / h2) % h2), jz = (int)(j / ((int64_t)h2 * h2));
+      b = (2 * jx + ox) + nl * ((2 * jy + oy) + nl * (2 * jz + oz));
+    }
+    bcell[tid] = b;
+  }
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; r++)
+#pragma unroll
+    for (int c = 0; c < 4; c++) acc[r][c] = 0.0;
+  const double* Mt = (const double*)(d.Mt + g.cell_off[l] * g.P);
+  for (int q = 0; q < 216; q++) {
+    const int c8 = q & 7, dl = q >> 3;
+    const int tx = 2 * (dl % 3 - 1) + (c8 & 1) - ox, ty = 2 * ((dl / 3) % 3 - 1) + ((c8 >> 1) & 1) - oy,
+              tz = 2 * (dl / 9 - 1) + (c8 >> 2) - oz;
+    if (abs(tx) <= 1 && abs(ty) <= 1 && abs(tz) <= 1) continue;
+    __syncthreads();  // the previous offset's source list is no longer read
+    if (tid < G_NT) {
+      const int b = bcell[tid];
+      int sc = -1;
+      if (b >= 0) {
+        const int bx = b % nl, by = (b / nl) % nl, bz = b / (nl * nl);
+        sc = ((bx + tx + nl) % nl) + nl * (((by + ty + nl) % nl) + nl * ((bz + tz + nl) % nl));
+      }
+      scell[tid] = sc;
+    }
+    const double* Rv = R + (int64_t)((tx + 3) + 7 * ((ty + 3) + 7 * (tz + 3))) * n2 * n2;
+    for (int k0 = 0; k0 < n2; k0 += G_KT) {
+      __syncthreads();
+      for (int e = tid; e < G_KT * G_MT; e += 256) {
+        const int kk = e / G_MT, i = e % G_MT;
+        As[kk][i] = (k0 + kk < n2 && i0 + i < n2) ? Rv[(int64_t)(k0 + kk) * n2 + i0 + i] : 0.0;
+      }
+      for (int e = tid; e < G_KT * G_NT; e += 256) {
+        const int j = e / G_KT, kk = e % G_KT;
+        const int sc = scell[j];
+        Bs[kk][j] = (sc >= 0 && k0 + kk < n2) ? Mt[(int64_t)sc * n2 + k0 + kk] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < G_KT; kk++) {
+        double a[4], bb[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) a[r] = As[kk][tm + 16 * r];
+#pragma unroll
+        for (int c = 0; c < 4; c++) bb[c] = Bs[kk][tn + 16 * c];
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+          for (int c = 0; c < 4; c++) acc[r][c] = fma(a[r], bb[c], acc[r][c]);
+      }
+    }
+  }
+  double* Ps = (double*)(d.Psi + g.cell_off[l] * g.P);
+#pragma unroll
+  for (int r = 0; r < 4; r++)
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const int i = i0 + tm + 16 * r, b = bcell[tn + 16 * c];
+      if (i < n2 && b >= 0) Ps[(int64_t)b * n2 + i] = acc[r][c];
+    }
+}
+
+// Level 2: cell b receives the M2L of every level-2 cell u of the
+// (2 KMC_TOP + 1)^3 block of domain copies (coordinates -2 KMC_TOP ..
+// 2 KMC_TOP + 1 per axis) except its 27 nearest; u is an image of source
+// cell (u mod 2).  The translation operator is linear in the I table, so the
+// images of one source are summed first: Iagg[b][s] = sum over those u of
+// I((u - b) w_2), then eight M2Ls per cell.
+__global__ void k_m2l_top_agg(const Geo g, const Dev d, double2* Iagg) {
+  const int b = blockIdx.x >> 3, sv = blockIdx.x & 7;
+  const int bx = b & 1, by = (b >> 1) & 1, bz = b >> 2;
+  const int lo = -2 * KMC_TOP, hi = 2 * KMC_TOP + 1, h = (KMC_TOP_SPAN - 1) / 2;
+  for (int c = threadIdx.x; c < g.P2; c += blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int uz = lo; uz <= hi; uz++)
+      for (int uy = lo; uy <= hi; uy++)
+        for (int ux = lo; ux <= hi; ux++) {
+          if ((ux & 1) + 2 * (uy & 1) + 4 * (uz & 1) != sv) continue;
+          const int tx = ux - bx, ty = uy - by, tz = uz - bz;
+          if (abs(tx) <= 1 && abs(ty) <= 1 && abs(tz) <= 1) continue;
+          const int v = (tx + h) + KMC_TOP_SPAN * ((ty + h) + KMC_TOP_SPAN * (tz + h));
+          const double2 t = d.Itab2[(int64_t)v * g.P2 + c];
+          acc.x += t.x;
+          acc.y += t.y;
+        }
+    Iagg[(int64_t)blockIdx.x * g.P2 + c] = acc;
+  }
+}
+
+__global__ void k_m2l_top(const Geo g, const Dev d, const double2* Iagg) {
   extern __shared__ double2 shM[];
   const int cell = blockIdx.x;
-  const int bx = cell & 1, by = (cell >> 1) & 1, bz = (cell >> 2) & 1;
   const int ci = threadIdx.x;
   int n = 0, m = 0;
   if (ci < g.P) {
     while (tri(n + 1, 0) <= ci) n++;
     m = ci - tri(n, 0);
   }
-  const int lo = -2 * KMC_TOP, hi = 2 * KMC_TOP + 1, h = (KMC_TOP_SPAN - 1) / 2;
   double2 acc = make_double2(0.0, 0.0);
-  for (int uz = lo; uz <= hi; uz++)
-    for (int uy = lo; uy <= hi; uy++)
-      for (int ux = lo; ux <= hi; ux++) {
-        const int tx = ux - bx, ty = uy - by, tz = uz - bz;
-        if (abs(tx) <= 1 && abs(ty) <= 1 && abs(tz) <= 1) continue;
-        const int src = (ux & 1) + 2 * ((uy & 1) + 2 * (uz & 1));
-        __syncthreads();
-        const double2* Ms = d.Mt + (g.cell_off[2] + src) * g.P;
-        for (int k = threadIdx.x; k < g.P; k += blockDim.x) shM[k] = Ms[k];
-        __syncthreads();
-        if (ci < g.P) {
-          const int v = (tx + h) + KMC_TOP_SPAN * ((ty + h) + KMC_TOP_SPAN * (tz + h));
-          const double2* It = d.Itab2 + (int64_t)v * g.P2;
-          for (int k = 0; k <= g.p; k++) {
-            double2 s = make_double2(0.0, 0.0);
-            for (int ll = -k; ll <= k; ll++) {
-              double2 a = tab_get(shM, k, ll);
-              double2 b = tab_get(It, n + k, m + ll);
-              s.x += a.x * b.x + a.y * b.y;
-              s.y += a.y * b.x - a.x * b.y;
-            }
-            if (k & 1) { acc.x -= s.x; acc.y -= s.y; }
-            else { acc.x += s.x; acc.y += s.y; }
-          }
+  for (int sv = 0; sv < 8; sv++) {
+    __syncthreads();
+    const double2* Ms = d.Mt + (g.cell_off[2] + sv) * g.P;
+    for (int k = threadIdx.x; k < g.P; k += blockDim.x) shM[k] = Ms[k];
+    __syncthreads();
+    if (ci < g.P) {
+      const double2* It = Iagg + (int64_t)(cell * 8 + sv) * g.P2;
+      for (int k = 0; k <= g.p; k++) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int ll = -k; ll <= k; ll++) {
+          const double2 a = tab_get(shM, k, ll);
+          const double2 b = tab_get(It, n + k, m + ll);
+          s.x += a.x * b.x + a.y * b.y;  // a * conj(b)
+          s.y += a.y * b.x - a.x * b.y;
+        }
+        if (k & 1) {
+          acc.x -= s.x;
+          acc.y -= s.y;
+        } else {
+          acc.x += s.x;
+          acc.y += s.y;
         }
       }
+    }
+  }
   if (ci < g.P) d.Psi[(g.cell_off[2] + cell) * g.P + ci] = acc;
 }
 
-void fmm_m2l(const Geo& g, const Dev& d, cudaStream_t s) {
-  int bs = g.P <= 128 ? 128 : 256;
-  k_m2l_top<<<8, bs, g.P * sizeof(double2), s>>>(g, d);
+// scratch: R tables of one level, (343 (2P)^2 doubles), and 64 aggregated I tables
+size_t fmm_m2l_scratch_bytes(const Geo& g) {
+  const size_t n2 = 2 * (size_t)g.P;
+  return 343 * n2 * n2 * sizeof(double) + 64 * (size_t)g.P2 * sizeof(double2);
+}
+
+void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s) {
+  const size_t n2 = 2 * (size_t)g.P;
+  double* R = (double*)scratch;
+  double2* Iagg = (double2*)(R + 343 * n2 * n2);
+  const int bs = g.P <= 128 ? 128 : 256;
+  k_m2l_top_agg<<<64, 128, 0, s>>>(g, d, Iagg);
+  k_m2l_top<<<8, bs, g.P * sizeof(double2), s>>>(g, d, Iagg);
   for (int l = 3; l <= g.L; l++) {
-    int64_t ncl = (int64_t)1 << (3 * (l - 1));
-    k_m2l<<<(unsigned)ncl, bs, g.P * sizeof(double2), s>>>(g, d, l);
+    k_m2l_rmat<<<343, 128, 0, s>>>(g, d, l, R);
+    const int64_t h2 = (int64_t)1 << (l - 2);
+    dim3 grid((unsigned)((h2 * h2 * h2 + G_NT - 1) / G_NT), 8, (unsigned)((n2 + G_MT - 1) / G_MT));
+    k_m2l_gemm<<<grid, 256, 0, s>>>(g, d, l, R);
   }
 }
 

@@ -17,6 +17,8 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 __constant__ float c_inv_f[KMC_NTRI];
@@ -167,18 +169,19 @@ template <> struct NearField<float> {
     c1 = c;
     e1 = d;
   }
-  // groups [0, ng) in the targets' frame, the first ngg of them the targets'
+  // groups [g0, g1) in the targets' frame; groups below ngg are the targets'
   // own leaf (skip the pair at distance 0).  Target 1 is evaluated only when
   // two is set (warp-uniform).
-  __device__ __forceinline__ void run_groups(const float4* G, int ngg, int ng, bool two, float tx0, float ty0,
-                                             float tz0, float tx1, float ty1, float tz1) {
+  __device__ __forceinline__ void run_span(const float4* G, int g0, int g1, int ngg, bool two, float tx0, float ty0,
+                                           float tz0, float tx1, float ty1, float tz1) {
     const Tgt t0 = target(tx0, ty0, tz0), t1 = target(tx1, ty1, tz1);
+    const int gm = min(max(ngg, g0), g1);
     if (two) {
-      if (ngg > 0) run_range<true, true>(G, ngg, t0, t1);
-      if (ng > ngg) run_range<false, true>(G + 5 * ngg, ng - ngg, t0, t1);
+      if (gm > g0) run_range<true, true>(G + 5 * g0, gm - g0, t0, t1);
+      if (g1 > gm) run_range<false, true>(G + 5 * gm, g1 - gm, t0, t1);
     } else {
-      if (ngg > 0) run_range<true, false>(G, ngg, t0, t1);
-      if (ng > ngg) run_range<false, false>(G + 5 * ngg, ng - ngg, t0, t1);
+      if (gm > g0) run_range<true, false>(G + 5 * g0, gm - g0, t0, t1);
+      if (g1 > gm) run_range<false, false>(G + 5 * gm, g1 - gm, t0, t1);
     }
   }
   __device__ __forceinline__ float sum(int side) const {
@@ -193,11 +196,13 @@ template <> struct NearField<double> {
   static __host__ __device__ __forceinline__ size_t bytes(int chunk) { return (size_t)chunk * 32; }
   static __device__ __forceinline__ void stage(unsigned char* sm, int e, double4_32a v) { ((double4_32a*)sm)[e] = v; }
   static __device__ __forceinline__ void pad(unsigned char*, int) {}
-  __device__ __forceinline__ void run2(const unsigned char* sm, int ns, int nguard, bool two, double x0, double y0,
-                                       double z0, double x1, double y1, double z1) {
+  // sources [j0, j1); those below nguard are the targets' own leaf (skip the
+  // pair at distance 0)
+  __device__ __forceinline__ void run2(const unsigned char* sm, int j0, int j1, int nguard, bool two, double x0,
+                                       double y0, double z0, double x1, double y1, double z1) {
     const double4_32a* src = (const double4_32a*)sm;
     double s0 = a0, s1 = a1;
-    for (int j = 0; j < ns; j++) {
+    for (int j = j0; j < j1; j++) {
       const double4_32a v = src[j];
       double dx = v.x - x0, dy = v.y - y0, dz = v.z - z0;
       double r2 = dx * dx + dy * dy + dz * dz;
@@ -251,9 +256,57 @@ __device__ __forceinline__ float l2p_packed(const float2* L, int p, float x, flo
   return total;
 }
 
+// the same evaluation with the degree known at compile time: fully unrolled,
+// the recurrence factors 1/((n-m)(n+m)) and -1/(2m) as immediates and the
+// coefficient addresses as constant offsets
+template <int P> __device__ __forceinline__ float l2p_fixed(const float2* L, float x, float y, float z) {
+  const float r2 = x * x + y * y + z * z;
+  const float2 nr2 = make_float2(-r2, -r2);
+  const float2 z2 = make_float2(2.f * z, 2.f * z);
+  float mmx = 1.f, mmy = 0.f;
+  float total = 0.f;
+#pragma unroll
+  for (int m = 0; m <= P; m++) {
+    if (m > 0) {
+      const float s = -0.5f / (float)m;
+      const float tx = s * (x * mmx - y * mmy);
+      const float ty = s * (x * mmy + y * mmx);
+      mmx = tx;
+      mmy = ty;
+    }
+    float2 a1 = make_float2(mmx, mmy), a2 = make_float2(0.f, 0.f);
+    float2 col = __fmul2_rn(L[tri(m, m)], a1);
+    const float zz0 = (float)(2 * m + 1) * z;
+    float2 zz = make_float2(zz0, zz0);
+#pragma unroll
+    for (int n = m + 1; n <= P; n++) {
+      const float c = 1.f / (float)((n - m) * (n + m));
+      float2 v = __ffma2_rn(zz, a1, __fmul2_rn(nr2, a2));
+      v = __fmul2_rn(v, make_float2(c, c));
+      col = __ffma2_rn(L[tri(n, m)], v, col);
+      a2 = a1;
+      a1 = v;
+      zz = __fadd2_rn(zz, z2);
+    }
+    const float cm = col.x - col.y;
+    total += (m == 0) ? cm : cm + cm;
+  }
+  return total;
+}
+
+// FP32 L2P with the common degrees unrolled (p is uniform over the launch)
+__device__ __forceinline__ float l2p_f32(const float2* L, int p, float x, float y, float z) {
+  switch (p) {
+    case 8: return l2p_fixed<8>(L, x, y, z);
+    case 10: return l2p_fixed<10>(L, x, y, z);
+    case 12: return l2p_fixed<12>(L, x, y, z);
+    default: return l2p_packed(L, p, x, y, z);
+  }
+}
+
 template <typename T, typename C> __device__ __forceinline__ T l2p_point(const C* L, int p, T x, T y, T z);
 template <> __device__ __forceinline__ float l2p_point<float, float2>(const float2* L, int p, float x, float y, float z) {
-  return l2p_packed(L, p, x, y, z);
+  return l2p_f32(L, p, x, y, z);
 }
 template <> __device__ __forceinline__ double l2p_point<double, double2>(const double2* L, int p, double x, double y,
                                                                         double z) {
@@ -364,6 +417,13 @@ __device__ __forceinline__ void stage_source(unsigned char* src, int e, double4_
   NearField<double>::stage(src, e, v);
 }
 
+// partial near-field sum (already scaled) into a fixed-point accumulator in
+// shared memory, rounded to nearest
+__device__ __forceinline__ void fixed_add(int* a, float v) { atomicAdd(a, __float2int_rn(v)); }
+__device__ __forceinline__ void fixed_add(long long* a, double v) {
+  atomicAdd((unsigned long long*)a, (unsigned long long)__double2ll_rn(v));
+}
+
 // list index of leaf f in {own leaf (f = 0), neighbour across face f - 1}
 // within the 27-neighbourhood list (own leaf first, then x fastest, centre
 // skipped)
@@ -381,8 +441,9 @@ __device__ __forceinline__ int face_leaf(int f) {
 // count) and the source passes; in the FP32 form the first pass's charge
 // groups are copied into shared memory by bulk asynchronous copies that run
 // while phases 1-3 proceed; (1) occupancy bits; (2) needed-site bits, masked
-// hops written; (3) compact site list; (4) near-field sums + L2P, two sites
-// per thread per round; (5) write-out by re-enumerating the same hops.  Site
+// hops written; (3) compact site list; (4) near-field sums (sources split
+// between the warps, fixed-point reduction) + L2P; (5) write-out by
+// re-enumerating the same hops.  Site
 // coordinates come from the slot positions (coalesced), user indices only
 // where an output is written.  Potentials are written in precision T (FP32
 // arrays in the mixed form, FP64 arrays in the FP64 form).
@@ -407,7 +468,7 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
   uint32_t* bits = (uint32_t*)(phis + W3);          // [nbw] occupied sites
   uint32_t* need = bits + nbw;                      // [nbw] sites where a potential is needed
   int* woff = (int*)(need + nbw);                   // [nbw + 1] prefix of needed sites per word
-  uint16_t* sites = (uint16_t*)(woff + nbw + 1);    // [W3] needed local sites, compacted
+  uint16_t* sites = (uint16_t*)(woff + nbw + 1);    // [W3] needed local sites (x | y << 4 | z << 8), compacted
   T* out_old = (T*)(F32 ? (void*)d.phi_old32 : (void*)d.phi_old);
   T* out_new = (T*)(F32 ? (void*)d.phi_new32 : (void*)d.phi_new);
 
@@ -565,116 +626,123 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
     int o = woff[w2];
     while (m) {
       int b = __ffs(m) - 1;
-      sites[o++] = (uint16_t)(32 * w2 + b);
+      const int l = 32 * w2 + b;
+      sites[o++] = (uint16_t)((l % W) | (((l / W) % W) << 4) | ((l / (W * W)) << 8));
       m &= m - 1;
     }
   }
   __syncthreads();
   const int nsites = woff[nbw];
 
-  // (4) near-field pair sums and L2P, two sites per thread per round (sites
-  // b and b + blockDim).  Sources: own leaf first (pairs at distance 0
-  // skipped), then the 26 other leaves, in passes of whole leaves.
-  const int npass = misc[0];
-  uint32_t waits = 0;  // completed phases of the copy barrier
-  for (int rb = 0; rb < nsites; rb += 2 * blockDim.x) {
-    const int b0 = rb + tid, b1 = b0 + blockDim.x;
-    const int l0 = b0 < nsites ? sites[b0] : 0, l1 = b1 < nsites ? sites[b1] : 0;
-    const int ix0 = l0 % W, iy0 = (l0 / W) % W, iz0 = l0 / (W * W);
-    const int ix1 = l1 % W, iy1 = (l1 / W) % W, iz1 = l1 / (W * W);
-    const bool one = __any_sync(0xffffffffu, b0 < nsites);
-    const bool two = __any_sync(0xffffffffu, b1 < nsites);
-    NearField<T> nf;
-    nf.reset();
-    for (int pass = 0; pass < npass; pass++) {
-      const int q0 = pq[pass], q1 = pq[pass + 1];
-      const bool resident = npass == 1 && rb > 0;  // sources already in shared memory
-      if (!resident && (pass > 0 || rb > 0)) {
-        __syncthreads();  // everyone is done with the previous contents
-        if (F32) {
-          if (tid == 0) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(bar, (uint32_t)(80 * (nb_off[q1] - nb_off[q0])));
-            for (int q = q0; q < q1; q++) {
-              const int ng = (nb_cnt[q] + 3) >> 2;
-              if (ng)
-                bulk_copy_g2s(src + 80 * (nb_off[q] - nb_off[q0]), d.sgrp + 20 * (int64_t)nb_leaf[q] * gpl,
-                              (uint32_t)(80 * ng), bar);
-            }
-          }
-        }
-      }
-      if constexpr (F32) {
-        if (!resident) {
-          const bool ok = mbar_wait_bounded(bar, waits & 1, KMC_WAIT_NS);
-          waits++;
-          if (__syncthreads_or(!ok)) {  // copies did not arrive: flag, drain, leave
-            if (tid == 0) {
-              atomicOr(&d.err[0], KMC_DERR_TIMEOUT);
-              mbar_wait_bounded(bar, (waits - 1) & 1, KMC_WAIT_NS);
-            }
-            __syncthreads();
-            return;
-          }
-        }
-        if (!resident) {  // the copied groups into this leaf's corner frame (own leaf: already)
-          for (int q = max(q0, 1) + warp; q < q1; q += nwarp) {
-            const int qq = q <= 13 ? q - 1 : q;
-            const float ox = (float)((qq % 3 - 1) * W), oy = (float)(((qq / 3) % 3 - 1) * W);
-            const float oz = (float)((qq / 9 - 1) * W);
-            float4* G = (float4*)src + 5 * (nb_off[q] - nb_off[q0]);
-            const int ng = (nb_cnt[q] + 3) >> 2;
-            for (int gi = lane; gi < ng; gi += 32) {
-#pragma unroll
-              for (int pr = 0; pr < 2; pr++) {
-                float4 A = G[5 * gi + 2 * pr], B = G[5 * gi + 2 * pr + 1];
-                A.x += ox;
-                A.y += ox;
-                A.z += oy;
-                A.w += oy;
-                B.x += oz;
-                B.y += oz;
-                B.z = A.x * A.x + A.z * A.z + B.x * B.x;
-                B.w = A.y * A.y + A.w * A.w + B.y * B.y;
-                G[5 * gi + 2 * pr] = A;
-                G[5 * gi + 2 * pr + 1] = B;
-              }
-            }
-          }
-          __syncthreads();
-        }
-        if (one) {
-          const int ngt = nb_off[q1] - nb_off[q0];
-          const int ngg = q0 == 0 ? (cnt_own + 3) >> 2 : 0;  // own-leaf groups lead pass 0
-          nf.run_groups((const float4*)src, ngg, ngt, two, (float)ix0, (float)iy0, (float)iz0, (float)ix1,
-                        (float)iy1, (float)iz1);
-        }
-      } else {
-        if (!resident) {
-          for (int q = q0 + warp; q < q1; q += nwarp) {
-            const int qq = q == 0 ? 13 : (q <= 13 ? q - 1 : q);
-            const int ux = lx + qq % 3 - 1, uy = ly + (qq / 3) % 3 - 1, uz = lz + qq / 9 - 1;
-            const int shx = ux - (ux + nL) % nL, shy = uy - (uy + nL) % nL, shz = uz - (uz + nL) % nL;
-            const int e0 = nb_off[q] - nb_off[q0];
-            for (int j = lane; j < nb_cnt[q]; j += 32)
-              stage_source(src, e0 + j, spos[nb_base[q] + j], shx * W, shy * W, shz * W, (double)h);
-          }
-          __syncthreads();
-        }
-        if (one) {
-          const int nguard = q0 == 0 ? cnt_own : 0;  // own-leaf sources lead pass 0
-          nf.run2(src, nb_off[q1] - nb_off[q0], nguard, two, ((T)(gx0 + ix0) + (T)0.5) * h,
-                  ((T)(gy0 + iy0) + (T)0.5) * h, ((T)(gz0 + iz0) + (T)0.5) * h, ((T)(gx0 + ix1) + (T)0.5) * h,
-                  ((T)(gy0 + iy1) + (T)0.5) * h, ((T)(gz0 + iz1) + (T)0.5) * h);
+  // (4) near-field pair sums.  Sources: own leaf first (pairs at distance 0
+  // skipped), then the 26 other leaves, in passes of whole leaves.  The
+  // sources of a pass are split evenly between the four warps, and every warp
+  // evaluates all needed sites against its share, two sites per lane per
+  // round, so that the four warps (one per SM sub-partition) carry the same
+  // number of rsqrt lanes whatever the number of sites.  The per-warp partial
+  // sums meet in fixed point: integer adds are associative, so the potentials
+  // do not depend on the order in which the warps arrive.  Scale 2^ks with
+  // 2^ks * bound < 2^(bits - 2), where bound >= |any partial or total| is
+  // max|q| times the number of sources over the smallest separation (1 site).
+  typedef typename std::conditional<F32, int, long long>::type Acc;
+  Acc* acc = (Acc*)phis;
+  for (int b = tid; b < nsites; b += blockDim.x) {
+    const int sv = sites[b];
+    acc[(sv & 15) + W * (((sv >> 4) & 15) + W * (sv >> 8))] = 0;
+  }
+  const int npass = nsites ? misc[0] : 1;  // no sites: only the prefetch to drain
+  int ks;
+  {
+    const double bound = g.qmax * (double)max(nb_off[27] * (F32 ? 4 : 1), 1) * (F32 ? 1.0 : (double)ih);
+    ks = (F32 ? 30 : 62) - (ilogb(bound) + 1);
+  }
+  const T scale = (T)ldexp(1.0, ks);
+  for (int pass = 0; pass < npass; pass++) {
+    const int q0 = pq[pass], q1 = pq[pass + 1];
+    if (pass > 0) {
+      __syncthreads();  // everyone is done with the previous pass's sources
+      if (F32 && tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, (uint32_t)(80 * (nb_off[q1] - nb_off[q0])));
+        for (int q = q0; q < q1; q++) {
+          const int ng = (nb_cnt[q] + 3) >> 2;
+          if (ng)
+            bulk_copy_g2s(src + 80 * (nb_off[q] - nb_off[q0]), d.sgrp + 20 * (int64_t)nb_leaf[q] * gpl,
+                          (uint32_t)(80 * ng), bar);
         }
       }
     }
-    if (b0 < nsites) phis[l0] = F32 ? nf.sum(0) * ih : nf.sum(0);
-    if (b1 < nsites) phis[l1] = F32 ? nf.sum(1) * ih : nf.sum(1);
-  }
-  if (F32 && nsites == 0) {  // the prefetched copies must land before the CTA leaves
-    const bool ok = mbar_wait_bounded(bar, 0, KMC_WAIT_NS);
-    if (!ok && tid == 0) atomicOr(&d.err[0], KMC_DERR_TIMEOUT);
+    if constexpr (F32) {
+      const bool ok = mbar_wait_bounded(bar, pass & 1, KMC_WAIT_NS);
+      if (__syncthreads_or(!ok)) {  // copies did not arrive: flag, drain, leave
+        if (tid == 0) {
+          atomicOr(&d.err[0], KMC_DERR_TIMEOUT);
+          mbar_wait_bounded(bar, pass & 1, KMC_WAIT_NS);
+        }
+        __syncthreads();
+        return;
+      }
+      // the copied groups into this leaf's corner frame (own leaf: already)
+      for (int q = max(q0, 1) + warp; q < q1; q += nwarp) {
+        const int qq = q <= 13 ? q - 1 : q;
+        const float ox = (float)((qq % 3 - 1) * W), oy = (float)(((qq / 3) % 3 - 1) * W);
+        const float oz = (float)((qq / 9 - 1) * W);
+        float4* G = (float4*)src + 5 * (nb_off[q] - nb_off[q0]);
+        const int ng = (nb_cnt[q] + 3) >> 2;
+        for (int gi = lane; gi < ng; gi += 32) {
+#pragma unroll
+          for (int pr = 0; pr < 2; pr++) {
+            float4 A = G[5 * gi + 2 * pr], B = G[5 * gi + 2 * pr + 1];
+            A.x += ox;
+            A.y += ox;
+            A.z += oy;
+            A.w += oy;
+            B.x += oz;
+            B.y += oz;
+            B.z = A.x * A.x + A.z * A.z + B.x * B.x;
+            B.w = A.y * A.y + A.w * A.w + B.y * B.y;
+            G[5 * gi + 2 * pr] = A;
+            G[5 * gi + 2 * pr + 1] = B;
+          }
+        }
+      }
+    } else {
+      for (int q = q0 + warp; q < q1; q += nwarp) {
+        const int qq = q == 0 ? 13 : (q <= 13 ? q - 1 : q);
+        const int ux = lx + qq % 3 - 1, uy = ly + (qq / 3) % 3 - 1, uz = lz + qq / 9 - 1;
+        const int shx = ux - (ux + nL) % nL, shy = uy - (uy + nL) % nL, shz = uz - (uz + nL) % nL;
+        const int e0 = nb_off[q] - nb_off[q0];
+        for (int j = lane; j < nb_cnt[q]; j += 32)
+          stage_source(src, e0 + j, spos[nb_base[q] + j], shx * W, shy * W, shz * W, (double)h);
+      }
+    }
+    __syncthreads();
+    // this warp's share of the pass's groups (FP32) or sources (FP64)
+    const int nu = nb_off[q1] - nb_off[q0];
+    const int u0 = (nu * warp) / nwarp, u1 = (nu * (warp + 1)) / nwarp;
+    const int nown = q0 == 0 ? (F32 ? (cnt_own + 3) >> 2 : cnt_own) : 0;  // own-leaf units lead pass 0
+    if (u1 > u0) {
+      for (int rb = 0; rb < nsites; rb += 64) {
+        const int b0 = rb + lane, b1 = b0 + 32;
+        const bool two = rb + 32 < nsites;  // warp-uniform
+        const int sv0 = b0 < nsites ? sites[b0] : 0, sv1 = b1 < nsites ? sites[b1] : 0;
+        const int ix0 = sv0 & 15, iy0 = (sv0 >> 4) & 15, iz0 = sv0 >> 8;
+        const int ix1 = sv1 & 15, iy1 = (sv1 >> 4) & 15, iz1 = sv1 >> 8;
+        const int l0 = ix0 + W * (iy0 + W * iz0), l1 = ix1 + W * (iy1 + W * iz1);
+        NearField<T> nf;
+        nf.reset();
+        if constexpr (F32) {
+          nf.run_span((const float4*)src, u0, u1, nown, two, (float)ix0, (float)iy0, (float)iz0, (float)ix1,
+                      (float)iy1, (float)iz1);
+        } else {
+          nf.run2(src, u0, u1, nown, two, ((T)(gx0 + ix0) + (T)0.5) * h, ((T)(gy0 + iy0) + (T)0.5) * h,
+                  ((T)(gz0 + iz0) + (T)0.5) * h, ((T)(gx0 + ix1) + (T)0.5) * h, ((T)(gy0 + iy1) + (T)0.5) * h,
+                  ((T)(gz0 + iz1) + (T)0.5) * h);
+        }
+        if (b0 < nsites) fixed_add(&acc[l0], nf.sum(0) * scale);
+        if (two && b1 < nsites) fixed_add(&acc[l1], nf.sum(1) * scale);
+      }
+    }
   }
   // the write-out's inputs (first 32 charges of this warp's leaves) are
   // loaded now, so that their latency passes during the L2P
@@ -691,19 +759,19 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
       }
     }
   }
-  // L2P, each site by the thread that summed its near field
+  __syncthreads();
+  // near field back to floating point (FP32: lattice units, times 1/h), plus
+  // the L2P of the leaf's local expansion
   {
     const T hw = (T)(0.5 * W);
-    for (int rb = 0; rb < nsites; rb += 2 * blockDim.x) {
-#pragma unroll
-      for (int s2 = 0; s2 < 2; s2++) {
-        const int b = rb + tid + s2 * blockDim.x;
-        if (b < nsites) {
-          const int l = sites[b];
-          phis[l] += l2p_point<T, C>(Lc, g.p, ((T)(l % W) + (T)0.5 - hw) * h, ((T)((l / W) % W) + (T)0.5 - hw) * h,
-                                     ((T)(l / (W * W)) + (T)0.5 - hw) * h);
-        }
-      }
+    const T back = (T)ldexp(1.0, -ks) * (F32 ? ih : (T)1);
+    for (int b = tid; b < nsites; b += blockDim.x) {
+      const int sv = sites[b];
+      const int ix = sv & 15, iy = (sv >> 4) & 15, iz = sv >> 8;
+      const int l = ix + W * (iy + W * iz);
+      const T near = (T)acc[l] * back;
+      phis[l] = near + l2p_point<T, C>(Lc, g.p, ((T)ix + (T)0.5 - hw) * h, ((T)iy + (T)0.5 - hw) * h,
+                                        ((T)iz + (T)0.5 - hw) * h);
     }
   }
   __syncthreads();

@@ -135,7 +135,12 @@ static int full_fmm(kmc_fmm* h) {
   CK(cudaMemsetAsync(d.Mt, 0, sizeof(double2) * g.ncell_total * g.P, s));
   fmm_p2m(g, d, s);
   fmm_m2m(g, d, s);
-  fmm_m2l(g, d, s);
+  {  // M2L scratch (per-level translation matrices), stream-ordered, released after use
+    void* scratch = nullptr;
+    CK(cudaMallocAsync(&scratch, fmm_m2l_scratch_bytes(g), s));
+    fmm_m2l(g, d, scratch, s);
+    CK(cudaFreeAsync(scratch, s));
+  }
   fmm_far_field(g, d, s);
   fmm_shadow_all(g, d, s);
   fmm_self_and_dipole(g, d, s);
@@ -316,6 +321,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
     if (!isfinite(qh[i])) return fail(h, KMC_ERR_ARG, "charge %lld is not finite", (long long)i);
     qs += qh[i];
     qa += fabs(qh[i]);
+    g.qmax = fmax(g.qmax, fabs(qh[i]));
   }
   if (fabs(qs) > 1e-12 * qa) return fail(h, KMC_ERR_NOT_NEUTRAL, "sum of charges %.3e is not zero", qs);
   // off-lattice capacity from the initial occupancy
