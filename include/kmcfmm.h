@@ -62,6 +62,15 @@ enum kmc_precision {
 
 enum kmc_mem { KMC_MEM_HOST = 0, KMC_MEM_DEVICE = 1 };
 
+/* Arithmetic of the one-off M2L (Algorithm 2, translations grouped by vector
+ * as dense real matrix products).  Both give FP64-accurate results. */
+enum kmc_m2l {
+  KMC_M2L_TENSOR = 0, /* bf16 tensor cores with exact integer slicing of the FP64 operands
+                         (six 7-bit slices, 21 slice products, exact per-diagonal sums);
+                         FP64 CUDA cores when p > 16 */
+  KMC_M2L_FP64 = 1    /* FP64 CUDA cores */
+};
+
 typedef struct kmc_opts {
   int precision;      /* kmc_precision */
   int lattice_edge;   /* E > 0: lattice mode, sites at ((i+1/2)h, (j+1/2)h, (k+1/2)h),
@@ -73,11 +82,13 @@ typedef struct kmc_opts {
   int mem;            /* kmc_mem: where array arguments live */
   int device;         /* CUDA device ordinal */
   int leaf_capacity;  /* off-lattice slots per leaf (0 = automatic); lattice mode uses (E/2^(L-1))^3 */
+  int m2l;            /* kmc_m2l: arithmetic of the M2L at init and recompute */
 } kmc_opts;
 
 typedef struct kmc_fmm* kmc_handle;
 
-/* Fill opts with defaults: FP64, off-lattice, h = 1, kT = 1, NULL stream, host memory, device 0. */
+/* Fill opts with defaults: FP64, off-lattice, h = 1, kT = 1, NULL stream, host memory, device 0,
+ * tensor-core M2L. */
 void kmc_opts_default(kmc_opts* opts);
 
 /*

@@ -33,6 +33,8 @@ KMC_PREC_FP64 = 0
 KMC_PREC_MIXED = 1
 KMC_MEM_HOST = 0
 KMC_MEM_DEVICE = 1
+KMC_M2L_TENSOR = 0
+KMC_M2L_FP64 = 1
 
 EXPORTS = [
     "kmc_opts_default", "kmc_fmm_init", "kmc_fmm_energy", "kmc_fmm_propose", "kmc_fmm_propose_lattice",
@@ -59,6 +61,7 @@ class kmc_opts(ctypes.Structure):
         ("mem", ctypes.c_int),
         ("device", ctypes.c_int),
         ("leaf_capacity", ctypes.c_int),
+        ("m2l", ctypes.c_int),
     ]
 
 
@@ -167,8 +170,9 @@ def _out(h: Handle, shape, dtype):
 # ------------------------------------------------------------------ C-ABI calls
 def kmc_fmm_init(positions, charges, box: float, levels: int, order: int, precision: str = "fp64",
                  lattice_edge: int = 0, lattice_h: float = 1.0, kT: float = 1.0, stream=None, device: int = 0,
-                 leaf_capacity: int = 0) -> Handle:
-    """Create a handle and run the one-off full FMM.  precision: 'fp64' or 'mixed'."""
+                 leaf_capacity: int = 0, m2l: str = "tensor") -> Handle:
+    """Create a handle and run the one-off full FMM.  precision: 'fp64' or 'mixed';
+    m2l: 'tensor' (bf16 tensor cores with exact slicing) or 'fp64' (FP64 CUDA cores)."""
     lib = load_library()
     opts = kmc_opts()
     lib.kmc_opts_default(ctypes.byref(opts))
@@ -178,6 +182,7 @@ def kmc_fmm_init(positions, charges, box: float, levels: int, order: int, precis
     opts.kT = float(kT)
     opts.device = int(device)
     opts.leaf_capacity = int(leaf_capacity)
+    opts.m2l = {"tensor": KMC_M2L_TENSOR, "fp64": KMC_M2L_FP64}[m2l]
     dev = _is_torch(positions) and positions.is_cuda
     opts.mem = KMC_MEM_DEVICE if dev else KMC_MEM_HOST
     if stream is not None:

@@ -78,6 +78,7 @@ struct Geo {
   double inv_a;           // 1 / a
   int prec;               // 0 = FP64 form, 1 = mixed form
   double qmax;            // largest |charge|
+  int m2l;                // M2L arithmetic: 0 = bf16 tensor-core slicing (p <= 16, else FP64), 1 = FP64
 };
 
 // cell coordinate of x on a level with n cells per side, floor(x n / a)

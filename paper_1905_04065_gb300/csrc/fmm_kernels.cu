@@ -13,6 +13,8 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 __constant__ double f_inv_nm[KMC_NTRI];        // 1/((n-m)(n+m)), n > m
@@ -478,10 +480,317 @@ __global__ void k_m2l_top(const Geo g, const Dev d, const double2* Iagg) {
   if (ci < g.P) d.Psi[(g.cell_off[2] + cell) * g.P + ci] = acc;
 }
 
-// scratch: R tables of one level, (343 (2P)^2 doubles), and 64 aggregated I tables
+// ------------------------------------------------------------------ M2L on the bf16 tensor cores
+// The same products with FP64 accuracy from bf16 tensor-core MMAs, by exact
+// integer slicing (the Ozaki splitting of a floating-point product into
+// error-free partial products).
+//  * Scaling by powers of two (exact): the input coefficient kk of every cell
+//    of the level is divided by 2^ec(kk) (ec from the level's largest
+//    |Mt[., kk]|), the translation entries R_t[i][kk] are multiplied by it, and
+//    row i of all R_t is divided by 2^er(i) (er from the row's largest entry),
+//    so that every scaled value lies in (-1, 1).
+//  * Slicing: x = sum_{s=1..S} x_s 2^(-7 s) + O(2^(-7S - 1)) with integer
+//    slices, |x_1| <= 128 and |x_s| <= 64 (s > 1), held exactly in bf16.
+//  * The product keeps the slice pairs with a + b = D <= S + 1 and sums each
+//    diagonal D separately: per translation (K = 2P padded, at most 352
+//    terms) the FP32 tensor-core accumulation of integers stays below 2^24
+//    (at most 2*128*64 + (S-2)*64*64 per term), so it is exact; it is then
+//    added into an int32 per diagonal (189 translations below 2^31 for
+//    p <= 16), and the diagonals are combined in FP64 with their weight
+//    2^(er(i) - 7 D).  S = 6: 43 significant bits per operand.
+#define OZ_S 6
+#define OZ_MT 64
+#define OZ_NT 64
+#define OZ_KC 32
+#define OZ_LD (OZ_KC + 8)  // shared row stride (bf16): 80 B rows, conflict-free ldmatrix
+#define OZ_MAXP 16
+
+static __host__ __device__ __forceinline__ int oz_rows(int n2) { return (n2 + OZ_MT - 1) / OZ_MT * OZ_MT; }
+static __host__ __device__ __forceinline__ int oz_cols(int n2) { return (n2 + OZ_KC - 1) / OZ_KC * OZ_KC; }
+
+// 2^e with e the smallest integer such that |x| < 2^e for every |x| <= m (0 if m = 0)
+__device__ __forceinline__ int oz_exp(unsigned long long mbits) {
+  const double m = __longlong_as_double((long long)mbits);
+  return m > 0.0 ? ilogb(m) + 1 : 0;
+}
+
+__device__ __forceinline__ void oz_split(double x, unsigned short* out, size_t stride) {
+  double r = x;
+#pragma unroll
+  for (int sl = 0; sl < OZ_S; sl++) {
+    r *= 128.0;
+    const double q = rint(r);
+    const __nv_bfloat16 b = __float2bfloat16_rn((float)q);  // |q| <= 128, an integer: exact
+    out[sl * stride] = *(const unsigned short*)&b;
+    r -= q;
+  }
+}
+
+// largest |Mt[cell][kk]| over the cells of level l, per real coefficient kk
+__global__ void k_oz_colmax(const Geo g, const Dev d, int l, unsigned long long* colmax) {
+  const int n2 = 2 * g.P;
+  const int64_t ncell = (int64_t)1 << (3 * (l - 1));
+  const double* Mt = (const double*)(d.Mt + g.cell_off[l] * g.P);
+  const int64_t per = (ncell + gridDim.x - 1) / gridDim.x;
+  const int64_t c0 = blockIdx.x * per, c1 = min(ncell, c0 + per);
+  for (int kk = threadIdx.x; kk < n2; kk += blockDim.x) {
+    double m = 0.0;
+    for (int64_t c = c0; c < c1; c++) m = fmax(m, fabs(Mt[c * n2 + kk]));
+    if (c1 > c0) atomicMax(&colmax[kk], (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// largest scaled |R_t[i][kk]| 2^ec(kk) over the used translations, per row i
+__global__ void k_oz_rowmax(const Geo g, const double* R, const unsigned long long* colmax,
+                            unsigned long long* rowmax) {
+  const int v = blockIdx.x;
+  const int tx = v % 7 - 3, ty = (v / 7) % 7 - 3, tz = v / 49 - 3;
+  if (abs(tx) <= 1 && abs(ty) <= 1 && abs(tz) <= 1) return;
+  const int n2 = 2 * g.P;
+  const double* Rv = R + (int64_t)v * n2 * n2;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+    double m = 0.0;
+    for (int kk = 0; kk < n2; kk++) m = fmax(m, ldexp(fabs(Rv[(int64_t)kk * n2 + i]), oz_exp(colmax[kk])));
+    atomicMax(&rowmax[i], (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// A slices: As[((v S + s) rows + i) cols + kk], row-major per translation and slice
+__global__ void k_oz_aslice(const Geo g, const double* R, const unsigned long long* colmax,
+                            const unsigned long long* rowmax, unsigned short* As) {
+  const int v = blockIdx.x;
+  const int tx = v % 7 - 3, ty = (v / 7) % 7 - 3, tz = v / 49 - 3;
+  if (abs(tx) <= 1 && abs(ty) <= 1 && abs(tz) <= 1) return;
+  const int n2 = 2 * g.P, nr = oz_rows(n2), nc = oz_cols(n2);
+  const double* Rv = R + (int64_t)v * n2 * n2;
+  const size_t stride = (size_t)nr * nc;
+  for (int e = threadIdx.x + blockIdx.y * blockDim.x; e < nr * nc; e += blockDim.x * gridDim.y) {
+    const int i = e / nc, kk = e % nc;
+    double x = 0.0;
+    if (i < n2 && kk < n2) x = ldexp(Rv[(int64_t)kk * n2 + i], oz_exp(colmax[kk]) - oz_exp(rowmax[i]));
+    oz_split(x, As + (size_t)v * OZ_S * stride + e, stride);
+  }
+}
+
+// B slices: Bs[(s ncell + cell) cols + kk]
+__global__ void k_oz_bslice(const Geo g, const Dev d, int l, const unsigned long long* colmax, unsigned short* Bs) {
+  const int n2 = 2 * g.P, nc = oz_cols(n2);
+  const int64_t ncell = (int64_t)1 << (3 * (l - 1));
+  const double* Mt = (const double*)(d.Mt + g.cell_off[l] * g.P);
+  const size_t stride = (size_t)ncell * nc;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ncell * nc; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / nc;
+    const int kk = (int)(e % nc);
+    const double x = kk < n2 ? ldexp(Mt[c * n2 + kk], -oz_exp(colmax[kk])) : 0.0;
+    oz_split(x, Bs + e, stride);
+  }
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// One parity class o, a tile of OZ_MT output rows x OZ_NT target cells; four
+// warps of 32 x 32 (2 x 4 MMA tiles of 16 x 8).  One pass per diagonal D.
+// Levels with few cells split the interaction list over gridDim.x / ntile
+// CTAs per tile; those add their exact per-diagonal integer sums into acc64
+// (integer adds: the result does not depend on their order) and
+// k_oz_finish converts.  Otherwise acc64 is null and the CTA writes Psi.
+__global__ void __launch_bounds__(128) k_m2l_oz(const Geo g, const Dev d, int l, const unsigned short* As,
+                                                const unsigned short* Bs, const unsigned long long* rowmax,
+                                                int ntile, long long* acc64) {
+  extern __shared__ __align__(128) unsigned short oz_sm[];
+  unsigned short* sA = oz_sm;                      // [OZ_S][OZ_MT][OZ_LD]
+  unsigned short* sB = sA + OZ_S * OZ_MT * OZ_LD;  // [OZ_S][OZ_NT][OZ_LD]
+  __shared__ int bcell[OZ_NT], scell[OZ_NT];
+  const int nl = 1 << (l - 1), h2 = nl >> 1;
+  const int o = blockIdx.y, ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+  const int64_t ncls = (int64_t)h2 * h2 * h2, ncell = (int64_t)nl * nl * nl;
+  const int tile = blockIdx.x % ntile, split = blockIdx.x / ntile, nsplit = gridDim.x / ntile;
+  const int q_begin = 216 * split / nsplit, q_end = 216 * (split + 1) / nsplit;
+  const int64_t j0 = (int64_t)tile * OZ_NT;
+  const int i0 = blockIdx.z * OZ_MT;
+  const int n2 = 2 * g.P, nr = oz_rows(n2), nc = oz_cols(n2);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, wm = warp & 1, wn = warp >> 1;
+  if (tid < OZ_NT) {
+    const int64_t j = j0 + tid;
+    int b = -1;
+    if (j < ncls) {
+      const int jx = (int)(j % h2), jy = (int)((j / h2) % h2), jz = (int)(j / ((int64_t)h2 * h2));
+      b = (2 * jx + ox) + nl * ((2 * jy + oy) + nl * (2 * jz + oz));
+    }
+    bcell[tid] = b;
+  }
+  const uint32_t sA0 = (uint32_t)__cvta_generic_to_shared(sA), sB0 = (uint32_t)__cvta_generic_to_shared(sB);
+  // ldmatrix lane addresses (bytes, within one slice's tile, k offset 0)
+  const int q = lane >> 3, rr = lane & 7;
+  uint32_t aoff[2], boff[2];
+#pragma unroll
+  for (int mf = 0; mf < 2; mf++) aoff[mf] = 2u * ((32 * wm + 16 * mf + rr + 8 * (q & 1)) * OZ_LD + 8 * (q >> 1));
+#pragma unroll
+  for (int np = 0; np < 2; np++) boff[np] = 2u * ((32 * wn + 16 * np + rr + 8 * (q >> 1)) * OZ_LD + 8 * (q & 1));
+  const size_t astride = (size_t)nr * nc, bstride = (size_t)ncell * nc;
+  const unsigned short* Bl = Bs;
+  double* Ps = (double*)(d.Psi + g.cell_off[l] * g.P);
+
+  for (int D = 2; D <= OZ_S + 1; D++) {
+    const int ns = D - 1;  // slices 0 .. ns - 1 of both operands meet on this diagonal
+    int iacc[2][4][4];
+#pragma unroll
+    for (int mf = 0; mf < 2; mf++)
+#pragma unroll
+      for (int nf = 0; nf < 4; nf++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) iacc[mf][nf][c] = 0;
+    for (int qo = q_begin; qo < q_end; qo++) {
+      const int c8 = qo & 7, dl = qo >> 3;
+      const int tx = 2 * (dl % 3 - 1) + (c8 & 1) - ox, ty = 2 * ((dl / 3) % 3 - 1) + ((c8 >> 1) & 1) - oy,
+                tz = 2 * (dl / 9 - 1) + (c8 >> 2) - oz;
+      if (abs(tx) <= 1 && abs(ty) <= 1 && abs(tz) <= 1) continue;
+      __syncthreads();  // the previous offset's tiles and source list are no longer read
+      if (tid < OZ_NT) {
+        const int b = bcell[tid];
+        int sc = -1;
+        if (b >= 0) {
+          const int bx = b % nl, by = (b / nl) % nl, bz = b / (nl * nl);
+          sc = ((bx + tx + nl) % nl) + nl * (((by + ty + nl) % nl) + nl * ((bz + tz + nl) % nl));
+        }
+        scell[tid] = sc;
+      }
+      const int v = (tx + 3) + 7 * ((ty + 3) + 7 * (tz + 3));
+      const unsigned short* Av = As + (size_t)v * OZ_S * astride;
+      float facc[2][4][4];
+#pragma unroll
+      for (int mf = 0; mf < 2; mf++)
+#pragma unroll
+        for (int nf = 0; nf < 4; nf++)
+#pragma unroll
+          for (int c = 0; c < 4; c++) facc[mf][nf][c] = 0.f;
+      for (int k0 = 0; k0 < nc; k0 += OZ_KC) {
+        __syncthreads();  // scell written; previous chunk consumed
+        // 16-byte pieces: per slice OZ_MT rows x (OZ_KC / 8) pieces of A, the same of B
+        for (int e = tid; e < ns * OZ_MT * (OZ_KC / 8); e += 128) {
+          const int sl = e / (OZ_MT * (OZ_KC / 8)), rem = e % (OZ_MT * (OZ_KC / 8));
+          const int row = rem / (OZ_KC / 8), pc = rem % (OZ_KC / 8);
+          cp_async16(sA0 + 2u * ((sl * OZ_MT + row) * OZ_LD + 8 * pc),
+                     Av + (size_t)sl * astride + (size_t)(i0 + row) * nc + k0 + 8 * pc);
+          const int sc = scell[row];
+          const uint32_t db = sB0 + 2u * ((sl * OZ_NT + row) * OZ_LD + 8 * pc);
+          if (sc >= 0)
+            cp_async16(db, Bl + (size_t)sl * bstride + (size_t)sc * nc + k0 + 8 * pc);
+          else
+            asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(db), "r"(0) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < OZ_KC; ks += 16) {
+          for (int a = 0; a < ns; a++) {
+            const int bsl = ns - 1 - a;
+            uint32_t af[2][4], bfr[2][4];
+#pragma unroll
+            for (int mf = 0; mf < 2; mf++)
+              ldsm_x4(sA0 + 2u * (a * OZ_MT * OZ_LD + ks) + aoff[mf], af[mf][0], af[mf][1], af[mf][2], af[mf][3]);
+#pragma unroll
+            for (int np = 0; np < 2; np++)
+              ldsm_x4(sB0 + 2u * (bsl * OZ_NT * OZ_LD + ks) + boff[np], bfr[np][0], bfr[np][1], bfr[np][2],
+                      bfr[np][3]);
+#pragma unroll
+            for (int mf = 0; mf < 2; mf++)
+#pragma unroll
+              for (int nf = 0; nf < 4; nf++)
+                mma_bf16(facc[mf][nf], af[mf], bfr[nf >> 1][2 * (nf & 1)], bfr[nf >> 1][2 * (nf & 1) + 1]);
+          }
+        }
+      }
+      // this translation's exact integer sums into the diagonal's int32 accumulator
+#pragma unroll
+      for (int mf = 0; mf < 2; mf++)
+#pragma unroll
+        for (int nf = 0; nf < 4; nf++)
+#pragma unroll
+          for (int c = 0; c < 4; c++) iacc[mf][nf][c] += __float2int_rn(facc[mf][nf][c]);
+    }
+    // the diagonal's weight 2^(er(i) - 7 D), accumulated in FP64 into Psi
+    const int g4 = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int mf = 0; mf < 2; mf++)
+#pragma unroll
+      for (int nf = 0; nf < 4; nf++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+          const int i = i0 + 32 * wm + 16 * mf + g4 + 8 * (c >> 1);
+          const int b = bcell[32 * wn + 8 * nf + 2 * t4 + (c & 1)];
+          if (i < n2 && b >= 0) {
+            if (acc64) {
+              atomicAdd((unsigned long long*)(acc64 + ((int64_t)(D - 2) * ncell + b) * n2 + i),
+                        (unsigned long long)(long long)iacc[mf][nf][c]);
+            } else {
+              const double val = ldexp((double)iacc[mf][nf][c], oz_exp(rowmax[i]) - 7 * D);
+              double* out = Ps + (int64_t)b * n2 + i;
+              *out = (D == 2 ? 0.0 : *out) + val;
+            }
+          }
+        }
+  }
+}
+
+// Psi from the split CTAs' per-diagonal integer sums
+__global__ void k_oz_finish(const Geo g, const Dev d, int l, const long long* acc64, const unsigned long long* rowmax) {
+  const int n2 = 2 * g.P;
+  const int64_t ncell = (int64_t)1 << (3 * (l - 1));
+  double* Ps = (double*)(d.Psi + g.cell_off[l] * g.P);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ncell * n2; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n2);
+    const int er = oz_exp(rowmax[i]);
+    double v = 0.0;
+    for (int D = 2; D <= OZ_S + 1; D++) v += ldexp((double)acc64[(int64_t)(D - 2) * ncell * n2 + e], er - 7 * D);
+    Ps[e] = v;
+  }
+}
+
+static size_t oz_dyn_smem() { return (size_t)2 * OZ_S * OZ_MT * OZ_LD * sizeof(unsigned short); }
+
+// interaction-list splits of level l: enough CTAs for three per SM (152 SMs)
+static int oz_splits(const Geo& g, int l) {
+  const int64_t h2 = (int64_t)1 << (l - 2);
+  const int64_t ctas = (h2 * h2 * h2 + OZ_NT - 1) / OZ_NT * 8 * (oz_rows(2 * g.P) / OZ_MT);
+  const int64_t want = (3 * 152 + ctas - 1) / ctas;
+  return (int)(want < 1 ? 1 : (want > 24 ? 24 : want));
+}
+
+// scratch: R tables of one level (343 (2P)^2 doubles), 64 aggregated I
+// tables and, for the tensor-core form, the scaling maxima and the slices
 size_t fmm_m2l_scratch_bytes(const Geo& g) {
   const size_t n2 = 2 * (size_t)g.P;
-  return 343 * n2 * n2 * sizeof(double) + 64 * (size_t)g.P2 * sizeof(double2);
+  size_t b = 343 * n2 * n2 * sizeof(double) + 64 * (size_t)g.P2 * sizeof(double2);
+  if (g.m2l == 0 && g.p <= OZ_MAXP) {
+    const size_t nr = oz_rows((int)n2), nc = oz_cols((int)n2);
+    b += 2 * nr * sizeof(unsigned long long);                      // colmax, rowmax
+    b += 343 * OZ_S * nr * nc * sizeof(unsigned short);             // A slices
+    b += (size_t)OZ_S * (size_t)g.ML * nc * sizeof(unsigned short);  // B slices (leaf level is the largest)
+    size_t acc = 0;  // per-diagonal integer sums of the split levels
+    for (int l = 3; l <= g.L; l++)
+      if (oz_splits(g, l) > 1) {
+        const size_t a = (size_t)(OZ_S) * ((size_t)1 << (3 * (l - 1))) * n2 * sizeof(long long);
+        acc = a > acc ? a : acc;
+      }
+    b += acc;
+  }
+  return b;
 }
 
 void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s) {
@@ -491,11 +800,40 @@ void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s) {
   const int bs = g.P <= 128 ? 128 : 256;
   k_m2l_top_agg<<<64, 128, 0, s>>>(g, d, Iagg);
   k_m2l_top<<<8, bs, g.P * sizeof(double2), s>>>(g, d, Iagg);
+  const bool tensor = g.m2l == 0 && g.p <= OZ_MAXP;
+  unsigned long long *colmax = nullptr, *rowmax = nullptr;
+  unsigned short *As = nullptr, *Bs = nullptr;
+  long long* acc64 = nullptr;
+  if (tensor) {
+    const size_t nr = oz_rows((int)n2), nc = oz_cols((int)n2);
+    colmax = (unsigned long long*)(Iagg + 64 * (size_t)g.P2);
+    rowmax = colmax + nr;
+    As = (unsigned short*)(rowmax + nr);
+    Bs = As + 343 * OZ_S * nr * nc;
+    acc64 = (long long*)(Bs + (size_t)OZ_S * (size_t)g.ML * nc);
+    cudaFuncSetAttribute(k_m2l_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_dyn_smem());
+  }
   for (int l = 3; l <= g.L; l++) {
     k_m2l_rmat<<<343, 128, 0, s>>>(g, d, l, R);
     const int64_t h2 = (int64_t)1 << (l - 2);
-    dim3 grid((unsigned)((h2 * h2 * h2 + G_NT - 1) / G_NT), 8, (unsigned)((n2 + G_MT - 1) / G_MT));
-    k_m2l_gemm<<<grid, 256, 0, s>>>(g, d, l, R);
+    if (tensor) {
+      const int nr = oz_rows((int)n2);
+      cudaMemsetAsync(colmax, 0, 2 * nr * sizeof(unsigned long long), s);
+      k_oz_colmax<<<256, 256, 0, s>>>(g, d, l, colmax);
+      k_oz_rowmax<<<343, 256, 0, s>>>(g, R, colmax, rowmax);
+      k_oz_aslice<<<dim3(343, 8), 256, 0, s>>>(g, R, colmax, rowmax, As);
+      const int64_t nb = ((((int64_t)1 << (3 * (l - 1))) * oz_cols((int)n2)) + 255) / 256;
+      k_oz_bslice<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, s>>>(g, d, l, colmax, Bs);
+      const int ntile = (int)((h2 * h2 * h2 + OZ_NT - 1) / OZ_NT), nsplit = oz_splits(g, l);
+      const int64_t ncell = (int64_t)1 << (3 * (l - 1));
+      if (nsplit > 1) cudaMemsetAsync(acc64, 0, (size_t)OZ_S * ncell * n2 * sizeof(long long), s);
+      dim3 grid((unsigned)(ntile * nsplit), 8, (unsigned)(nr / OZ_MT));
+      k_m2l_oz<<<grid, 128, oz_dyn_smem(), s>>>(g, d, l, As, Bs, rowmax, ntile, nsplit > 1 ? acc64 : nullptr);
+      if (nsplit > 1) k_oz_finish<<<(unsigned)((ncell * n2 + 255) / 256 < 4096 ? (ncell * n2 + 255) / 256 : 4096), 256, 0, s>>>(g, d, l, acc64, rowmax);
+    } else {
+      dim3 grid((unsigned)((h2 * h2 * h2 + G_NT - 1) / G_NT), 8, (unsigned)((n2 + G_MT - 1) / G_MT));
+      k_m2l_gemm<<<grid, 256, 0, s>>>(g, d, l, R);
+    }
   }
 }
 

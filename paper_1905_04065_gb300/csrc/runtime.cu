@@ -212,6 +212,7 @@ void kmc_opts_default(kmc_opts* o) {
   o->mem = KMC_MEM_HOST;
   o->device = 0;
   o->leaf_capacity = 0;
+  o->m2l = KMC_M2L_TENSOR;
 }
 
 const char* kmc_last_error(kmc_handle h) { return h ? h->msg : g_static_msg; }
@@ -284,10 +285,12 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   if (o.precision != KMC_PREC_FP64 && o.precision != KMC_PREC_MIXED) return fail(h, KMC_ERR_ARG, "unknown precision");
   if (o.mem != KMC_MEM_HOST && o.mem != KMC_MEM_DEVICE) return fail(h, KMC_ERR_ARG, "unknown memory kind");
   if (!(o.kT > 0.0)) return fail(h, KMC_ERR_ARG, "kT must be positive");
+  if (o.m2l != KMC_M2L_TENSOR && o.m2l != KMC_M2L_FP64) return fail(h, KMC_ERR_ARG, "unknown M2L arithmetic");
   int r = init_impl(h, n, positions, charges, box, levels, order);
   if (r) return r;
   Geo& g = h->g;
   g.kT = o.kT;
+  g.m2l = o.m2l;
   if (o.lattice_edge > 0) {
     int E = o.lattice_edge;
     if (E % g.nL != 0) return fail(h, KMC_ERR_ARG, "lattice edge %d is not a multiple of 2^(levels-1) = %d", E, g.nL);

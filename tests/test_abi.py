@@ -37,6 +37,7 @@ def test_binding_loads_without_device():
     opts = k.kmc_opts()
     lib.kmc_opts_default(ctypes.byref(opts))  # pure host function
     assert opts.precision == k.KMC_PREC_FP64 and opts.lattice_h == 1.0 and opts.mem == k.KMC_MEM_HOST
+    assert opts.m2l == k.KMC_M2L_TENSOR
     assert lib.kmc_last_error(None) is not None
 
 
