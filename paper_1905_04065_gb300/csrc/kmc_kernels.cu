@@ -328,8 +328,20 @@ template <> __device__ __forceinline__ double qnan<double>() { return __longlong
 
 // Site coordinate of a lattice position (i + 1/2) h: floor(x / h) = i exactly
 // for the lattice sizes accepted at init (E^3 < 2^31).
-__device__ __forceinline__ int lattice_coord(float x, float ih) { return (int)floorf(x * ih); }
+// (FP32 form without the conversion unit, which the pair loop's rsqrt
+// occupies: x ih - 1/2 = i + delta with |delta| far below 1/2, and adding
+// 1.5 2^23 rounds it to the integer 1.5 2^23 + i, whose low bits are i)
+__device__ __forceinline__ int lattice_coord(float x, float ih) {
+  return __float_as_int(fmaf(x, ih, -0.5f) + 12582912.f) - 0x4B400000;
+}
 __device__ __forceinline__ int lattice_coord(double x, double ih) { return (int)floor(x * ih); }
+
+// small integer (|i| < 2^22) to float on the FMA pipe: the float with bits
+// 0x4B400000 + i is 1.5 2^23 + i
+__device__ __forceinline__ float i2f(int i) { return __int_as_float(0x4B400000 + i) - 12582912.f; }
+template <typename T> __device__ __forceinline__ T small_to(int i);
+template <> __device__ __forceinline__ float small_to<float>(int i) { return i2f(i); }
+template <> __device__ __forceinline__ double small_to<double>(int i) { return (double)i; }
 
 // coordinate c + dc (|dc| <= 1) wrapped into [0, E)
 __device__ __forceinline__ int wrap1(int c, int E) { return c < 0 ? c + E : (c >= E ? c - E : c); }
@@ -455,6 +467,7 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
   extern __shared__ __align__(128) unsigned char sm[];
   const int W = g.W, W3 = W * W * W;
   const int nbw = (W3 + 31) / 32;
+  const int rW = (65536 + W - 1) / W;
   unsigned char* src = sm;
   C* Lc = (C*)(sm + NearField<T>::bytes(chunk));  // 16-byte aligned
   int64_t* nb_base = (int64_t*)(Lc + g.P);          // [27] slot base: own leaf, then the 26 others
@@ -475,7 +488,8 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   const int nL = g.nL, E = g.E;
   const int64_t leaf = blockIdx.x;
-  const int lx = (int)(leaf % nL), ly = (int)((leaf / nL) % nL), lz = (int)(leaf / ((int64_t)nL * nL));
+  const int lsh = g.L - 1;  // nL = 2^(L-1)
+  const int lx = (int)(leaf & (nL - 1)), ly = (int)((leaf >> lsh) & (nL - 1)), lz = (int)(leaf >> (2 * lsh));
   const int gx0 = lx * W, gy0 = ly * W, gz0 = lz * W;
   const T h = (T)g.h, ih = (T)(1.0 / g.h);
   const V4* spos = (const V4*)(F32 ? (const void*)d.spos32 : (const void*)d.spos64);
@@ -497,7 +511,7 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
     if (lane < 27) {
       const int qq = lane == 0 ? 13 : (lane <= 13 ? lane - 1 : lane);
       const int ux = lx + qq % 3 - 1, uy = ly + (qq / 3) % 3 - 1, uz = lz + qq / 9 - 1;
-      const int sx = (ux + nL) % nL, sy = (uy + nL) % nL, sz = (uz + nL) % nL;
+      const int sx = wrap1(ux, nL), sy = wrap1(uy, nL), sz = wrap1(uz, nL);
       const int nleaf = sx + nL * (sy + nL * sz);
       nb_leaf[lane] = nleaf;
       nb_base[lane] = (int64_t)nleaf * g.cap;
@@ -627,7 +641,10 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
     while (m) {
       int b = __ffs(m) - 1;
       const int l = 32 * w2 + b;
-      sites[o++] = (uint16_t)((l % W) | (((l / W) % W) << 4) | ((l / (W * W)) << 8));
+      // l = x + W (y + W z) by reciprocal multiplication: floor(l rW / 2^16)
+      // = floor(l / W) for l < 2^16 / W (W <= 12, l < 1728)
+      const int q1 = (l * rW) >> 16, z = (q1 * rW) >> 16;
+      sites[o++] = (uint16_t)((l - q1 * W) | ((q1 - z * W) << 4) | (z << 8));
       m &= m - 1;
     }
   }
@@ -685,8 +702,8 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
       // the copied groups into this leaf's corner frame (own leaf: already)
       for (int q = max(q0, 1) + warp; q < q1; q += nwarp) {
         const int qq = q <= 13 ? q - 1 : q;
-        const float ox = (float)((qq % 3 - 1) * W), oy = (float)(((qq / 3) % 3 - 1) * W);
-        const float oz = (float)((qq / 9 - 1) * W);
+        const float ox = i2f((qq % 3 - 1) * W), oy = i2f(((qq / 3) % 3 - 1) * W);
+        const float oz = i2f((qq / 9 - 1) * W);
         float4* G = (float4*)src + 5 * (nb_off[q] - nb_off[q0]);
         const int ng = (nb_cnt[q] + 3) >> 2;
         for (int gi = lane; gi < ng; gi += 32) {
@@ -710,7 +727,7 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
       for (int q = q0 + warp; q < q1; q += nwarp) {
         const int qq = q == 0 ? 13 : (q <= 13 ? q - 1 : q);
         const int ux = lx + qq % 3 - 1, uy = ly + (qq / 3) % 3 - 1, uz = lz + qq / 9 - 1;
-        const int shx = ux - (ux + nL) % nL, shy = uy - (uy + nL) % nL, shz = uz - (uz + nL) % nL;
+        const int shx = ux - wrap1(ux, nL), shy = uy - wrap1(uy, nL), shz = uz - wrap1(uz, nL);
         const int e0 = nb_off[q] - nb_off[q0];
         for (int j = lane; j < nb_cnt[q]; j += 32)
           stage_source(src, e0 + j, spos[nb_base[q] + j], shx * W, shy * W, shz * W, (double)h);
@@ -732,8 +749,8 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
         NearField<T> nf;
         nf.reset();
         if constexpr (F32) {
-          nf.run_span((const float4*)src, u0, u1, nown, two, (float)ix0, (float)iy0, (float)iz0, (float)ix1,
-                      (float)iy1, (float)iz1);
+          nf.run_span((const float4*)src, u0, u1, nown, two, i2f(ix0), i2f(iy0), i2f(iz0), i2f(ix1), i2f(iy1),
+                      i2f(iz1));
         } else {
           nf.run2(src, u0, u1, nown, two, ((T)(gx0 + ix0) + (T)0.5) * h, ((T)(gy0 + iy0) + (T)0.5) * h,
                   ((T)(gz0 + iz0) + (T)0.5) * h, ((T)(gx0 + ix1) + (T)0.5) * h, ((T)(gy0 + iy1) + (T)0.5) * h,
@@ -770,8 +787,8 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
       const int ix = sv & 15, iy = (sv >> 4) & 15, iz = sv >> 8;
       const int l = ix + W * (iy + W * iz);
       const T near = (T)acc[l] * back;
-      phis[l] = near + l2p_point<T, C>(Lc, g.p, ((T)ix + (T)0.5 - hw) * h, ((T)iy + (T)0.5 - hw) * h,
-                                        ((T)iz + (T)0.5 - hw) * h);
+      phis[l] = near + l2p_point<T, C>(Lc, g.p, (small_to<T>(ix) + (T)0.5 - hw) * h,
+                                        (small_to<T>(iy) + (T)0.5 - hw) * h, (small_to<T>(iz) + (T)0.5 - hw) * h);
     }
   }
   __syncthreads();
