@@ -1126,8 +1126,8 @@ __global__ void k_downward_root(const Geo g, const Dev d) {
   for (int c = threadIdx.x; c < g.P; c += blockDim.x) Pe[g.cell_off[1] * g.P + c] = own_coef<T>(d, g.cell_off[1] * g.P + c);
 }
 
-// Downward pass, one level per launch: CTA per child cell, thread per output
-// coefficient.  The parent's expansion and the child-offset table are first
+// Downward pass for levels with few cells, one level per launch: CTA per
+// child cell, thread per output coefficient.  The parent's expansion and the child-offset table are first
 // expanded to every order -n..n (the conjugate symmetry applied once), so the
 // inner loop is branch-free: out(k, lo) = sum_{n >= k} sum_m L(n, m) R(n - k, m - lo).
 template <typename T> __device__ __forceinline__ const typename cplx<T>::type* child_table(const Dev& d);
@@ -1182,6 +1182,66 @@ __global__ void __launch_bounds__(128) k_downward_cell(const Geo g, const Dev d,
   }
 }
 
+// Downward pass, one level per launch: CTA per parent cell of level l - 1,
+// computing its 8 children.  The parent's expansion and the 8 child-offset
+// tables are expanded to every order -n..n in shared memory (the conjugate
+// symmetry applied once).  A warp task is 4 consecutive output coefficients x
+// the 8 children (lane = 8 c + o): the lanes of a warp run the same (or a
+// neighbouring) degree's loop bounds, so the sums do not diverge, and each
+// parent coefficient read is shared by 8 lanes.  Tasks go to warps in snake
+// order (their cost falls with the degree).
+template <typename T>
+__global__ void __launch_bounds__(256) k_downward_par(const Geo g, const Dev d, int l) {
+  typedef typename cplx<T>::type C;
+  extern __shared__ __align__(16) unsigned char shraw[];
+  const int F = (g.p + 1) * (g.p + 1);
+  C* Lf = (C*)shraw;  // [F] parent expansion, entry n^2 + n + m
+  C* Rf = Lf + F;     // [8][F] child-offset tables, same order
+  const int nl = 1 << (l - 1), np = nl >> 1, sh = l - 2;  // np = 2^(l-2)
+  const int64_t par = blockIdx.x;
+  const int px = (int)(par & (np - 1)), py = (int)((par >> sh) & (np - 1)), pz = (int)(par >> (2 * sh));
+  const C* Pp = (const C*)d.Peff + (g.cell_off[l - 1] + par) * g.P;
+  const C* Rt = child_table<T>(d) + (int64_t)l * 8 * g.P;
+  for (int t = threadIdx.x; t < 9 * F; t += blockDim.x) {
+    const int tb = t / F, u = t - tb * F;
+    const int n = (int)sqrtf((float)u + 0.5f), m = u - n * n - n;  // exact: sqrt(n^2 - 1/2) < n <= sqrt(n^2 + 1/2)
+    if (tb == 0) Lf[u] = tab_get(Pp, n, m);
+    else Rf[(tb - 1) * F + u] = tab_get(Rt + (tb - 1) * g.P, n, m);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int o = lane & 7, cl = lane >> 3;
+  const int64_t child = (2 * px + (o & 1)) + (int64_t)nl * ((2 * py + ((o >> 1) & 1)) + (int64_t)nl * (2 * pz + (o >> 2)));
+  const C* Ro = Rf + o * F;
+  C* Pe = (C*)d.Peff;
+  const int ntask = (g.P + 3) / 4;
+  for (int r = 0; r * nw < ntask; r++) {
+    const int task = r * nw + ((r & 1) ? nw - 1 - warp : warp);
+    const int ci = 4 * task + cl;
+    if (task >= ntask || ci >= g.P) continue;
+    const short2 km = f_nm[ci];
+    const int k = km.x, lo = km.y;
+    T ax = 0, ay = 0;
+    for (int n = k; n <= g.p; n++) {
+      const int j = n - k;
+      const int mlo = max(lo - j, -n), mhi = min(lo + j, n);
+      const C* a = Lf + n * n + n;
+      const C* b = Ro + j * j + j - lo;
+      for (int m = mlo; m <= mhi; m++) {
+        const C u = a[m], v = b[m];
+        ax += u.x * v.x - u.y * v.y;
+        ay += u.x * v.y + u.y * v.x;
+      }
+    }
+    const int64_t at = (g.cell_off[l] + child) * g.P + ci;
+    const C own = own_coef<T>(d, at);
+    C v;
+    v.x = ax + own.x;
+    v.y = ay + own.y;
+    Pe[at] = v;
+  }
+}
+
 void fmm_prepare(const Geo& g, int prec) {
   // load every per-step kernel now: with lazy module loading a first launch
   // inside a stream capture would invalidate the capture
@@ -1190,6 +1250,11 @@ void fmm_prepare(const Geo& g, int prec) {
   cudaFuncGetAttributes(&fa, k_downward_root<float>);
   cudaFuncGetAttributes(&fa, k_downward_cell<double>);
   cudaFuncGetAttributes(&fa, k_downward_cell<float>);
+  cudaFuncGetAttributes(&fa, k_downward_par<double>);
+  cudaFuncGetAttributes(&fa, k_downward_par<float>);
+  const int smax = 9 * (KMC_MAXP + 1) * (KMC_MAXP + 1) * (int)sizeof(double2);
+  cudaFuncSetAttribute(k_downward_par<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  cudaFuncSetAttribute(k_downward_par<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax / 2);
   (void)g;
   (void)prec;
 }
@@ -1198,10 +1263,16 @@ void fmm_downward(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
   if (prec == 0) k_downward_root<double><<<1, 128, 0, s>>>(g, d);
   else k_downward_root<float><<<1, 128, 0, s>>>(g, d);
   const size_t smc = (size_t)2 * (g.p + 1) * (g.p + 1) * (prec == 0 ? sizeof(double2) : sizeof(float2));
+  const size_t smp = (size_t)9 * (g.p + 1) * (g.p + 1) * (prec == 0 ? sizeof(double2) : sizeof(float2));
   for (int l = 2; l <= g.L; l++) {
-    const unsigned cells = 1u << (3 * (l - 1));
-    if (prec == 0) k_downward_cell<double><<<cells, 128, smc, s>>>(g, d, l);
-    else k_downward_cell<float><<<cells, 128, smc, s>>>(g, d, l);
+    const unsigned parents = 1u << (3 * (l - 2));
+    if (parents < 512) {  // few cells: one CTA per child keeps the latency of a level short
+      if (prec == 0) k_downward_cell<double><<<8 * parents, 128, smc, s>>>(g, d, l);
+      else k_downward_cell<float><<<8 * parents, 128, smc, s>>>(g, d, l);
+    } else {
+      if (prec == 0) k_downward_par<double><<<parents, 256, smp, s>>>(g, d, l);
+      else k_downward_par<float><<<parents, 256, smp, s>>>(g, d, l);
+    }
   }
 }
 
