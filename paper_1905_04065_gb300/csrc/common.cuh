@@ -141,7 +141,6 @@ struct Dev {
   int64_t* event;     // [1]
   double* dtq;        // [2] (dt, Q)
   MoveRec* move;      // [1]
-  double2* dK;        // [P] level-1 multipole change of the accepted move
   double2* acc_scratch;  // coarse-level (2, 3) P2L terms of the accepted move
   int* err;           // [4] device error flags
   double* scratch;    // init-time scratch (lattice-sum terms)

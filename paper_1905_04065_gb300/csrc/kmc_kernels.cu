@@ -1161,26 +1161,18 @@ __global__ void k_move_from_event(const Geo g, const Dev d) {
 
 void kmc_accept_from_event(const Geo& g, const Dev& d, cudaStream_t s) { k_move_from_event<<<1, 1, 0, s>>>(g, d); }
 
-
-
 // multipoles of the ancestors of the old and new positions, all levels:
 // Mt_l[anc(r)] -= q R(r - c), Mt_l[anc(r')] += q R(r' - c).  thread per
 // (level, coefficient); each value from the regular-harmonic recurrences.
-// The level-1 change (about the domain centre) is also stored in dK for the
-// far-field update.
-__global__ void k_acc_multipole(const Geo g, const Dev d) {
-  MoveRec mv = *d.move;
-  if (!mv.valid) return;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int l = 1 + t / g.P, ci = t % g.P;
-  if (l > g.L) return;
+// multipole_delta gives the change of coefficient ci on level l for both ends
+// of the move (val[0]: -q at r, val[1]: +q at r'), and the two cells
+__device__ __forceinline__ void multipole_delta(const Geo& g, const MoveRec& mv, int l, int ci, double2* val,
+                                                int64_t* cell) {
   int n = 0;
   while (tri(n + 1, 0) <= ci) n++;
   const int m = ci - tri(n, 0);
   const int nl = 1 << (l - 1);
   const double wl = g.a / nl;
-  double2 val[2];
-  int64_t cell[2];
   for (int side = 0; side < 2; side++) {
     const double* x = side ? mv.rn : mv.r;
     const double q = side ? mv.q : -mv.q;
@@ -1203,7 +1195,14 @@ __global__ void k_acc_multipole(const Geo g, const Dev d) {
     }
     val[side] = make_double2(q * a1.x, q * a1.y);
   }
-  if (l == 1) d.dK[ci] = make_double2(val[0].x + val[1].x, val[0].y + val[1].y);
+}
+
+__device__ __forceinline__ void acc_multipole_role(const Geo& g, const Dev& d, const MoveRec& mv, int t) {
+  const int l = 1 + t / g.P, ci = t % g.P;
+  if (l > g.L) return;
+  double2 val[2];
+  int64_t cell[2];
+  multipole_delta(g, mv, l, ci, val, cell);
   if (cell[0] == cell[1]) {
     val[0].x += val[1].x;
     val[0].y += val[1].y;
@@ -1218,12 +1217,19 @@ __global__ void k_acc_multipole(const Geo g, const Dev d) {
   }
 }
 
-// far field: H += R dK, one CTA (one warp) per output coefficient, lanes split
-// the (k, l) sum; fixed-order warp reduction.
-__global__ void k_acc_far(const Geo g, const Dev d) {
-  MoveRec mv = *d.move;
-  if (!mv.valid) return;
-  const int ci = blockIdx.x, lane = threadIdx.x;
+// far field: H += R dK with dK the level-1 multipole change (about the domain
+// centre), computed by the block into shared memory; one warp per output
+// coefficient, lanes split the (k, l) sum; fixed-order warp reduction.
+__device__ __forceinline__ void acc_far_role(const Geo& g, const Dev& d, const MoveRec& mv, double2* dks, int blk) {
+  for (int c = threadIdx.x; c < g.P; c += blockDim.x) {
+    double2 val[2];
+    int64_t cell[2];
+    multipole_delta(g, mv, 1, c, val, cell);
+    dks[c] = make_double2(val[0].x + val[1].x, val[0].y + val[1].y);
+  }
+  __syncthreads();
+  const int ci = blk * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (ci >= g.P) return;
   int n = 0;
   while (tri(n + 1, 0) <= ci) n++;
   const int m = ci - tri(n, 0);
@@ -1233,7 +1239,7 @@ __global__ void k_acc_far(const Geo g, const Dev d) {
     int k = 0;
     while ((k + 1) * (k + 1) <= t) k++;
     int ll = t - k * k - k;
-    double2 a = tab_get(d.dK, k, ll), b = tab_get(d.S, n + k, m + ll);
+    double2 a = tab_get(dks, k, ll), b = tab_get(d.S, n + k, m + ll);
     double sx = a.x * b.x + a.y * b.y, sy = a.y * b.x - a.x * b.y;
     if (k & 1) { ax -= sx; ay -= sy; }
     else { ax += sx; ay += sy; }
@@ -1302,10 +1308,8 @@ __device__ __forceinline__ bool image_in_il(const int u0[3], int nl, int nu, con
 #define KMC_COARSE_SLOTS (KMC_L2_SLOTS + 64 * 54)
 #define KMC_COARSE_CELLS 72
 
-__global__ void k_acc_coarse(const Geo g, const Dev d, double2* scratch) {
-  MoveRec mv = *d.move;
-  if (!mv.valid) return;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // (slot, m)
+__device__ __forceinline__ void acc_coarse_role(const Geo& g, const MoveRec& mv, double2* scratch, int t) {
+  // t = (slot, m)
   const int slot = t / (g.p + 1), m = t - slot * (g.p + 1);
   if (slot >= KMC_COARSE_SLOTS) return;
   int l, cell, im, nimg1, span;
@@ -1393,11 +1397,7 @@ __device__ __forceinline__ int wdist(int a, int b, int n) {
   return min(t, n - t);
 }
 
-__global__ void k_acc_fine(const Geo g, const Dev d, int lmin) {
-  MoveRec mv = *d.move;
-  if (!mv.valid) return;
-  const int l = lmin + blockIdx.y;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void acc_fine_role(const Geo& g, const Dev& d, const MoveRec& mv, int l, int t) {
   int cand = t / (g.p + 1), m = t % (g.p + 1);
   if (cand >= 432) return;
   const int nl = 1 << (l - 1), np = nl >> 1;
@@ -1477,9 +1477,7 @@ __global__ void k_acc_fine(const Geo g, const Dev d, int lmin) {
 }
 
 // move the charge between leaf slots; dipole, energy and bookkeeping
-__global__ void k_acc_move(const Geo g, const Dev d) {
-  MoveRec mv = *d.move;
-  if (!mv.valid) return;
+__device__ __forceinline__ void acc_move_role(const Geo& g, const Dev& d, const MoveRec& mv) {
   int32_t i = mv.i;
   int32_t so = d.slot_of[i];
   int64_t lo = so / g.cap;
@@ -1536,18 +1534,53 @@ __global__ void k_acc_move(const Geo g, const Dev d) {
   d.U[0] += mv.dU;
 }
 
-void kmc_accept_apply(const Geo& g, const Dev& d, cudaStream_t s) {
-  const int nt = g.L * g.P;
-  k_acc_multipole<<<(nt + 127) / 128, 128, 0, s>>>(g, d);
-  k_acc_far<<<g.P, 32, 0, s>>>(g, d);
-  // coarse levels 2 and 3 (8 + 64 cells, L >= 3 always): all cells x all images
-  k_acc_coarse<<<(KMC_COARSE_SLOTS * (g.p + 1) + 127) / 128, 128, 0, s>>>(g, d, d.acc_scratch);
-  k_acc_coarse_reduce<<<KMC_COARSE_CELLS, 32 * ACR_WARPS, sizeof(double2) * ACR_WARPS * g.P, s>>>(g, d, d.acc_scratch);
-  if (g.L >= 4) {
-    dim3 grid((432 * (g.p + 1) + 63) / 64, g.L - 3);
-    k_acc_fine<<<grid, 64, 0, s>>>(g, d, 4);
+// The independent parts of an accept in one launch, blocks taking roles by
+// range: multipole changes of all levels, the far field, the coarse P2L
+// columns (into scratch), the fine-level P2L updates (levels >= 4, each cell
+// written by one thread) and the slot move.  They read only the move record
+// and write disjoint data; the coarse columns are then summed per cell.
+struct AccPlan {
+  int nmp, nfar, ncoarse, nfine, fine_per_level;
+};
+#define ACC_THREADS 128
+__global__ void __launch_bounds__(ACC_THREADS) k_acc_fused(const Geo g, const Dev d, double2* scratch, AccPlan ap) {
+  __shared__ double2 dks[ncoef(KMC_MAXP)];
+  const MoveRec mv = *d.move;
+  if (!mv.valid) return;
+  int b = blockIdx.x;
+  if (b < ap.nmp) {
+    acc_multipole_role(g, d, mv, b * ACC_THREADS + threadIdx.x);
+    return;
   }
-  k_acc_move<<<1, 1, 0, s>>>(g, d);
+  b -= ap.nmp;
+  if (b < ap.nfar) {
+    acc_far_role(g, d, mv, dks, b);
+    return;
+  }
+  b -= ap.nfar;
+  if (b < ap.ncoarse) {
+    acc_coarse_role(g, mv, scratch, b * ACC_THREADS + threadIdx.x);
+    return;
+  }
+  b -= ap.ncoarse;
+  if (b < ap.nfine) {
+    const int tf = b * ACC_THREADS + threadIdx.x;
+    if (tf < ap.fine_per_level * (g.L - 3)) acc_fine_role(g, d, mv, 4 + tf / ap.fine_per_level, tf % ap.fine_per_level);
+    return;
+  }
+  if (threadIdx.x == 0) acc_move_role(g, d, mv);
+}
+
+void kmc_accept_apply(const Geo& g, const Dev& d, cudaStream_t s) {
+  AccPlan ap;
+  ap.nmp = (g.L * g.P + ACC_THREADS - 1) / ACC_THREADS;
+  ap.nfar = (g.P + ACC_THREADS / 32 - 1) / (ACC_THREADS / 32);
+  // coarse levels 2 and 3 (8 + 64 cells, L >= 3 always): all cells x all images
+  ap.ncoarse = (KMC_COARSE_SLOTS * (g.p + 1) + ACC_THREADS - 1) / ACC_THREADS;
+  ap.fine_per_level = 432 * (g.p + 1);
+  ap.nfine = g.L >= 4 ? (ap.fine_per_level * (g.L - 3) + ACC_THREADS - 1) / ACC_THREADS : 0;
+  k_acc_fused<<<ap.nmp + ap.nfar + ap.ncoarse + ap.nfine + 1, ACC_THREADS, 0, s>>>(g, d, d.acc_scratch, ap);
+  k_acc_coarse_reduce<<<KMC_COARSE_CELLS, 32 * ACR_WARPS, sizeof(double2) * ACR_WARPS * g.P, s>>>(g, d, d.acc_scratch);
 }
 
 // ------------------------------------------------------------------ general points
@@ -1780,10 +1813,6 @@ static void kmc_preload() {
   cudaFuncGetAttributes(&fa, k_select);
   cudaFuncGetAttributes(&fa, k_record);
   cudaFuncGetAttributes(&fa, k_move_from_event);
-  cudaFuncGetAttributes(&fa, k_acc_multipole);
-  cudaFuncGetAttributes(&fa, k_acc_far);
-  cudaFuncGetAttributes(&fa, k_acc_coarse);
+  cudaFuncGetAttributes(&fa, k_acc_fused);
   cudaFuncGetAttributes(&fa, k_acc_coarse_reduce);
-  cudaFuncGetAttributes(&fa, k_acc_fine);
-  cudaFuncGetAttributes(&fa, k_acc_move);
 }

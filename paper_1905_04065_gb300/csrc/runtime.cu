@@ -396,7 +396,6 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   ALLOC(d.event, sizeof(int64_t) * 2);
   ALLOC(d.dtq, sizeof(double) * 2);
   ALLOC(d.move, sizeof(MoveRec));
-  ALLOC(d.dK, sizeof(double2) * g.P);
   ALLOC(d.acc_scratch, sizeof(double2) * (size_t)kmc_coarse_slots() * g.P);
   ALLOC(d.err, sizeof(int) * 4);
   ALLOC(d.uni_small, sizeof(double) * 2);
