@@ -69,9 +69,9 @@ def aggregate(units: float, ms: float, device=None):
 
 
 # per KMC step: downward root + (L - 1) levels, propose, finalize, select,
-# record, move-from-event and six accept kernels
+# record, move-from-event and two accept kernels
 def launches_per_step(L: int) -> int:
-    return L + 11
+    return L + 7
 
 
 # --------------------------------------------------------------- algorithmic work
@@ -85,7 +85,7 @@ def step_bytes(E: int, L: int, N: int, p: int) -> int:
     return 6 * N * (8 + 4) + ML * W ** 3 * 16 + ML * P * 8
 
 
-def pair_count(E: int, L: int, sites: np.ndarray) -> dict:
+def pair_count(E: int, L: int, sites: np.ndarray, nhop: int = 6) -> dict:
     """Evaluation sites and near-field pairs of one propose launch, counted
     from the configuration.  The potential is needed once per distinct site:
     every occupied site (old positions) and every empty site that some charge
@@ -98,7 +98,7 @@ def pair_count(E: int, L: int, sites: np.ndarray) -> dict:
     occ[sites] = True
     needed = occ.copy()
     hops = 0
-    for (dx, dy, dz) in [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]:
+    for (dx, dy, dz) in workloads.hop_vectors(nhop).tolist():
         t = (xyz + np.array([dx, dy, dz])) % E
         ts = t[:, 0] + E * (t[:, 1] + E * t[:, 2])
         ok = ~occ[ts]
@@ -177,7 +177,7 @@ def measured_peaks():
 
 
 # --------------------------------------------------------------- CPU oracle sample
-def cpu_sample(E, sites, q, seconds_target=10.0, max_props=20000):
+def cpu_sample(E, sites, q, seconds_target=10.0, max_props=20000, nhop=6):
     """dU evals/s of the FP64 oracle's direct lattice sum (O(N) per proposal,
     tabulated Ewald pair potential) on a seeded sample of unmasked hops."""
     import oracle
@@ -186,13 +186,13 @@ def cpu_sample(E, sites, q, seconds_target=10.0, max_props=20000):
     occ = np.zeros(E ** 3, dtype=bool)
     occ[sites] = True
     xyz = workloads.site_xyz(E, sites)
-    dirs = np.array([(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)])
+    dirs = workloads.hop_vectors(nhop)
 
     def draw(m):
         parts, tg = [], []
         while len(parts) < m:
             i = int(rng.integers(0, len(q)))
-            k = int(rng.integers(0, 6))
+            k = int(rng.integers(0, nhop))
             t = (xyz[i] + dirs[k]) % E
             s = int(t[0] + E * (t[1] + E * t[2]))
             if not occ[s]:
@@ -267,9 +267,20 @@ def run_reference(args):
     return 0
 
 
+# The paper's own time per KMC step for the Sec. 5.3 benchmark on one node (Tab. 4, strong scaling
+# at P = 1: 10^6 charges on a 300^3 lattice, one charge per 27 sites, 14 hop targets, p = 12,
+# L = 6, FP64 generated C, MPI + OpenMP).  Context for the "sec53" workload line, which runs the
+# same shape on 288^3 sites (884,736 charges); not the same configuration, so vs_baseline stays null.
+PAPER_SEC53 = {"s_per_kmc_step": {"CSD3 Skylake 2x16 cores": 7.43, "Isambard ThunderX2 2x32 cores": 11.93,
+                                  "Balena Ivy Bridge 2x8 cores": 21.33, "Balena Skylake 2x12 cores": 10.26},
+               "source": "Tab. 4, P = 1 (Sec. 5.3)",
+               "configuration": "10^6 charges, 300^3 sites, 14 hops, p = 12, L = 6, FP64"}
+
+
 def _config(w, name):
+    hops = "6 NN hops" if w.get("hops", 6) == 6 else "14 hops (6 faces, 8 body diagonals)"
     return {"workload": f"{name}: {w['E']}^3-site periodic lattice, {w['N']} charges (+-1, neutral), "
-                        f"6 NN hops, L={w['L']}, p={w['p']}, kT={w['kT']}",
+                        f"{hops}, L={w['L']}, p={w['p']}, kT={w['kT']}",
             "E": w["E"], "N": w["N"], "levels": w["L"], "order": w["p"], "kT": w["kT"],
             "l2": "flushed (256 MiB write) before every timed step"}
 
@@ -287,16 +298,18 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     w, sites, q = workloads.workload(args.workload)
     E, L, p, kT = w["E"], w["L"], w["p"], w["kT"]
+    nhop = w.get("hops", 6)
     # replicas: every rank runs an independent replica with its own seed
     if world > 1 and rank > 0:
         sites, q = workloads.uniform_lattice(E, w["N"], w["seed"] + 7919 * rank)
     pos = workloads.site_positions(E, sites)
     stream = torch.cuda.current_stream(dev)
     t0 = time.perf_counter()
-    h = k.kmc_fmm_init(pos, q, float(E), L, p, precision="mixed", lattice_edge=E, kT=kT, stream=stream, device=dev)
+    h = k.kmc_fmm_init(pos, q, float(E), L, p, precision="mixed", lattice_edge=E, kT=kT, stream=stream, device=dev,
+                       hops=nhop)
     torch.cuda.synchronize()
     init_s = time.perf_counter() - t0
-    work = pair_count(E, L, sites)
+    work = pair_count(E, L, sites, nhop)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
     u = workloads.uniforms(args.warmup + args.steps + args.e2e_steps + 16, w["seed"])
 
@@ -343,8 +356,8 @@ def run_gpu(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     # pinned host buffers, allocated once: the caller owns the outputs
-    mask_h = torch.empty((len(q), 6), dtype=torch.uint8, pin_memory=True)
-    dU_h = torch.empty((len(q), 6), dtype=torch.float64, pin_memory=True)
+    mask_h = torch.empty((len(q), nhop), dtype=torch.uint8, pin_memory=True)
+    dU_h = torch.empty((len(q), nhop), dtype=torch.float64, pin_memory=True)
     torch.cuda.synchronize()
     e0.record(stream)
     for s in range(es):
@@ -359,7 +372,7 @@ def run_gpu(args):
     n = len(q)
     e2e = {"value": e2e_units / (e2e_tot * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": 16 + 24 + 8,
-           "d2h_bytes_per_step": 6 * n * (1 + 8) + 8 + 8 + 8 + 24 + 8,
+           "d2h_bytes_per_step": nhop * n * (1 + 8) + 8 + 8 + 8 + 24 + 8,
            "path": "kmc_fmm_propose_lattice (mask+dU into pinned host buffers) + kmc_step + kmc_fmm_accept_event"}
 
     # FP64 form (context)
@@ -367,7 +380,7 @@ def run_gpu(args):
     if args.fp64_steps > 0:
         del h
         torch.cuda.synchronize()
-        h64 = k.kmc_fmm_init(pos, q, float(E), L, p, precision="fp64", lattice_edge=E, kT=kT, stream=stream,
+        h64 = k.kmc_fmm_init(pos, q, float(E), L, p, precision="fp64", lattice_edge=E, kT=kT, stream=stream, hops=nhop,
                              device=dev)
         k.kmc_run_profiled(h64, u[:1])
         ms64 = []
@@ -414,7 +427,7 @@ def run_gpu(args):
 
     cpu = None
     if not args.no_cpu and world == 1 or (world > 1 and rank == 0 and not args.no_cpu):
-        cpu = cpu_sample(E, sites, q, seconds_target=args.cpu_seconds)
+        cpu = cpu_sample(E, sites, q, seconds_target=args.cpu_seconds, nhop=nhop)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -431,6 +444,7 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches_per_step(L) * args.steps,
+        "paper_context": PAPER_SEC53 if args.workload == "sec53" else None,
         "clocks": clocks,
     }
     print(json.dumps(line))
@@ -513,7 +527,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="large", choices=["small", "medium", "large", "blobs", "tile", "batch"])
+    ap.add_argument("--workload", default="large", choices=["small", "medium", "large", "blobs", "tile", "sec53", "batch"])
     ap.add_argument("--replicas", type=int, default=None)
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)

@@ -30,9 +30,11 @@
  *    host scalar or write host arrays synchronise that stream.
  *  - A handle is not thread-safe; use one handle per host thread.
  *  - Indices: particles are numbered 0..n-1 in the caller's order ("user
- *    order").  Lattice hop k of particle i is the event j = 6 i + k with
- *    k = 0..5 for the directions (+x, -x, +y, -y, +z, -z), wrapped
- *    periodically.
+ *    order").  Lattice hop k of particle i is the event j = nh i + k, nh the
+ *    number of hops of the handle's hop set (kmc_opts.hops): k = 0..5 for the
+ *    faces (+x, -x, +y, -y, +z, -z) and, with KMC_HOPS_14, k = 6..13 for the
+ *    body diagonals (+-1, +-1, +-1) with x fastest: (+,+,+), (-,+,+), (+,-,+),
+ *    (-,-,+), (+,+,-), (-,+,-), (+,-,-), (-,-,-).  Targets wrap periodically.
  */
 #ifndef KMCFMM_H
 #define KMCFMM_H
@@ -62,6 +64,13 @@ enum kmc_precision {
 
 enum kmc_mem { KMC_MEM_HOST = 0, KMC_MEM_DEVICE = 1 };
 
+/* Lattice hop set (the moves Algorithm 5 proposes for every charge). */
+enum kmc_hops {
+  KMC_HOPS_6 = 0, /* the 6 nearest-neighbour sites */
+  KMC_HOPS_14 = 1 /* the 6 faces and the 8 body diagonals at distance sqrt(3) h: the hop set of the
+                     paper's Sec. 5.3 scaling benchmark */
+};
+
 /* Arithmetic of the one-off M2L (Algorithm 2, translations grouped by vector
  * as dense real matrix products).  Both give FP64-accurate results. */
 enum kmc_m2l {
@@ -83,12 +92,13 @@ typedef struct kmc_opts {
   int device;         /* CUDA device ordinal */
   int leaf_capacity;  /* off-lattice slots per leaf (0 = automatic); lattice mode uses (E/2^(L-1))^3 */
   int m2l;            /* kmc_m2l: arithmetic of the M2L at init and recompute */
+  int hops;           /* kmc_hops: lattice hop set (nh = 6 or 14 hops per charge) */
 } kmc_opts;
 
 typedef struct kmc_fmm* kmc_handle;
 
 /* Fill opts with defaults: FP64, off-lattice, h = 1, kT = 1, NULL stream, host memory, device 0,
- * tensor-core M2L. */
+ * tensor-core M2L, 6 hops. */
 void kmc_opts_default(kmc_opts* opts);
 
 /*
@@ -125,9 +135,9 @@ int kmc_fmm_propose(kmc_handle h, int64_t m, const int32_t* particle, const doub
                     const uint8_t* mask, double* dU);
 
 /*
- * Lattice mode: proposal generation (each charge to its 6 nearest-neighbour
- * sites, masked when occupied, as in Algorithm 5) and dU for every unmasked
- * hop.  mask and dU are n x 6 (event order j = 6 i + k); masked entries get
+ * Lattice mode: proposal generation (each charge to the nh sites of its hop
+ * set, masked when occupied, as in Algorithm 5) and dU for every unmasked
+ * hop.  mask and dU are n x nh (event order j = nh i + k); masked entries get
  * mask 0 and dU NaN.  Either output may be NULL.  The rates for kmc_step are
  * kept on the device.
  */
@@ -143,11 +153,11 @@ int kmc_fmm_propose_lattice(kmc_handle h, uint8_t* mask, double* dU);
  */
 int kmc_fmm_accept(kmc_handle h, int32_t particle, const double target[3], double* dU_accepted);
 
-/* Lattice mode: accept event j = 6 i + k (hop of particle i in direction k). */
+/* Lattice mode: accept event j = nh i + k (hop k of particle i). */
 int kmc_fmm_accept_event(kmc_handle h, int64_t event, double* dU_accepted);
 
 /*
- * Rejection-free selection (Algorithm 1): rates r_j (m = 6 n entries in event
+ * Rejection-free selection (Algorithm 1): rates r_j (m = nh n entries in event
  * order, or NULL to use the rates of the last kmc_fmm_propose_lattice),
  * Q = sum r_j, event j with R_{j-1} < Q zeta <= R_j, dt = -ln(xi) / Q.
  * zeta, xi in (0, 1].  Outputs are host scalars; *event = -1 if Q == 0.

@@ -244,8 +244,12 @@ class LatticeState:
         return hop_target(self.E, int(self.sites[i]), int(k))
 
     def accept(self, i: int, k: int) -> None:
+        self.accept_site(i, self.target(i, k))
+
+    def accept_site(self, i: int, s_new: int) -> None:
+        """Move charge i to lattice site s_new (any hop set) and update the site potential."""
         s_old = int(self.sites[i])
-        s_new = self.target(i, k)
+        s_new = int(s_new)
         if self.occ[s_new]:
             raise ValueError("target site occupied")
         lib = _load()

@@ -8,8 +8,8 @@ otherwise.
 
 Arrays may be numpy arrays (host memory) or CUDA torch tensors (device
 memory); the kind is fixed per handle by the positions passed to
-kmc_fmm_init.  Hop k of particle i is event j = 6 i + k, k = 0..5 for the
-directions (+x, -x, +y, -y, +z, -z).
+kmc_fmm_init.  Hop k of particle i is event j = nh i + k with nh = 6 (the
+faces +x, -x, +y, -y, +z, -z) or 14 (then the body diagonals, x fastest).
 """
 from __future__ import annotations
 
@@ -35,6 +35,8 @@ KMC_MEM_HOST = 0
 KMC_MEM_DEVICE = 1
 KMC_M2L_TENSOR = 0
 KMC_M2L_FP64 = 1
+KMC_HOPS_6 = 0
+KMC_HOPS_14 = 1
 
 EXPORTS = [
     "kmc_opts_default", "kmc_fmm_init", "kmc_fmm_energy", "kmc_fmm_propose", "kmc_fmm_propose_lattice",
@@ -62,6 +64,7 @@ class kmc_opts(ctypes.Structure):
         ("device", ctypes.c_int),
         ("leaf_capacity", ctypes.c_int),
         ("m2l", ctypes.c_int),
+        ("hops", ctypes.c_int),
     ]
 
 
@@ -115,12 +118,13 @@ def _is_torch(x) -> bool:
 class Handle:
     """An initialised FMM-KMC system (owns the C handle)."""
 
-    def __init__(self, ptr, n: int, mem: int, lattice: bool, device: int):
+    def __init__(self, ptr, n: int, mem: int, lattice: bool, device: int, nhop: int = 6):
         self.ptr = ptr
         self.n = n
         self.mem = mem
         self.lattice = lattice
         self.device = device
+        self.nhop = nhop  # lattice hops per charge (events j = nhop * i + k)
 
     def __del__(self):
         try:
@@ -170,9 +174,10 @@ def _out(h: Handle, shape, dtype):
 # ------------------------------------------------------------------ C-ABI calls
 def kmc_fmm_init(positions, charges, box: float, levels: int, order: int, precision: str = "fp64",
                  lattice_edge: int = 0, lattice_h: float = 1.0, kT: float = 1.0, stream=None, device: int = 0,
-                 leaf_capacity: int = 0, m2l: str = "tensor") -> Handle:
+                 leaf_capacity: int = 0, m2l: str = "tensor", hops: int = 6) -> Handle:
     """Create a handle and run the one-off full FMM.  precision: 'fp64' or 'mixed';
-    m2l: 'tensor' (bf16 tensor cores with exact slicing) or 'fp64' (FP64 CUDA cores)."""
+    m2l: 'tensor' (bf16 tensor cores with exact slicing) or 'fp64' (FP64 CUDA cores);
+    hops: the lattice hop set, 6 (faces) or 14 (faces and body diagonals)."""
     lib = load_library()
     opts = kmc_opts()
     lib.kmc_opts_default(ctypes.byref(opts))
@@ -183,6 +188,7 @@ def kmc_fmm_init(positions, charges, box: float, levels: int, order: int, precis
     opts.device = int(device)
     opts.leaf_capacity = int(leaf_capacity)
     opts.m2l = {"tensor": KMC_M2L_TENSOR, "fp64": KMC_M2L_FP64}[m2l]
+    opts.hops = {6: KMC_HOPS_6, 14: KMC_HOPS_14}[int(hops)]
     dev = _is_torch(positions) and positions.is_cuda
     opts.mem = KMC_MEM_DEVICE if dev else KMC_MEM_HOST
     if stream is not None:
@@ -197,7 +203,7 @@ def kmc_fmm_init(positions, charges, box: float, levels: int, order: int, precis
     ptr = ctypes.c_void_p()
     code = lib.kmc_fmm_init(ctypes.byref(ptr), n, pos_p, q_p, float(box), int(levels), int(order),
                             ctypes.byref(opts))
-    h = Handle(ptr, n, opts.mem, lattice_edge > 0, device)
+    h = Handle(ptr, n, opts.mem, lattice_edge > 0, device, int(hops))
     if code != KMC_OK:
         msg = lib.kmc_last_error(ptr)
         text = msg.decode() if msg else ""
@@ -243,11 +249,12 @@ def _given(h: Handle, x, shape, dtype):
 
 
 def kmc_fmm_propose_lattice(h: Handle, mask=None, dU=None):
-    """(mask[n,6], dU[n,6]) for all nearest-neighbour hops.  mask and dU may be
+    """(mask[n,nh], dU[n,nh]) for all hops of the handle's hop set.  mask and dU may be
     caller-owned buffers (e.g. pinned host memory) that are filled in place."""
     lib = load_library()
-    mask, mp = _out(h, (h.n, 6), np.uint8) if mask is None else _given(h, mask, (h.n, 6), np.uint8)
-    dU, dp = _out(h, (h.n, 6), np.float64) if dU is None else _given(h, dU, (h.n, 6), np.float64)
+    nh = h.nhop
+    mask, mp = _out(h, (h.n, nh), np.uint8) if mask is None else _given(h, mask, (h.n, nh), np.uint8)
+    dU, dp = _out(h, (h.n, nh), np.float64) if dU is None else _given(h, dU, (h.n, nh), np.float64)
     _check(h, lib.kmc_fmm_propose_lattice(h.ptr, mp, dp))
     return mask, dU
 

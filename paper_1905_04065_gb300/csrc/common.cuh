@@ -24,7 +24,15 @@
 
 #define KMC_MAXL 10   // maximum number of levels
 #define KMC_MAXP 20   // maximum expansion degree
-#define KMC_NHOP 6    // lattice hop directions (+x,-x,+y,-y,+z,-z)
+#define KMC_NHOP 6    // lattice hop directions of the nearest-neighbour set (+x,-x,+y,-y,+z,-z)
+#define KMC_MAXHOP 14 // with the 8 body diagonals (the hop set of the paper's Sec. 5.3 benchmark)
+
+// component a (0 = x, 1 = y, 2 = z) of lattice hop k: k < 6 the faces
+// (+x, -x, +y, -y, +z, -z), k = 6 + d the body diagonals with component a
+// negative when bit a of d is set (x fastest: (+,+,+), (-,+,+), (+,-,+), ...)
+__host__ __device__ __forceinline__ constexpr int hop_c(int k, int a) {
+  return k < 6 ? ((k >> 1) == a ? ((k & 1) ? -1 : 1) : 0) : ((((k - 6) >> a) & 1) ? -1 : 1);
+}
 #define KMC_FIN_PARTICLES 128  // particles per block sum of the rates
 // Periodic images nu with |nu|_inf <= KMC_TOP are handled by the tree (the
 // level-2 interaction list covers the (2 KMC_TOP + 1)^3 block of domain copies);
@@ -79,6 +87,7 @@ struct Geo {
   int prec;               // 0 = FP64 form, 1 = mixed form
   double qmax;            // largest |charge|
   int m2l;                // M2L arithmetic: 0 = bf16 tensor-core slicing (p <= 16, else FP64), 1 = FP64
+  int nhop;               // lattice hops per charge: 6 (faces) or 14 (faces and body diagonals)
 };
 
 // cell coordinate of x on a level with n cells per side, floor(x n / a)
@@ -119,24 +128,24 @@ struct Dev {
   double2* Itab2;     // level-2 M2L irregular values [KMC_TOP_NOFF * P2]
   double2* Rch;       // child-offset regular harmonics [(L+1) * 8 * P]
   double2* S;         // lattice sums over the far images [P2]
-  double* selfc;      // [KMC_NHOP] self-pair correction C(d) per hop direction
+  double* selfc;      // [KMC_MAXHOP] self-pair correction C(d) per hop direction
   double* dip;        // [3] dipole moment M
   float* fdip;        // [3] (4 pi / 3V) M in FP32 for the mixed rate assembly
   double* U;          // [1] total energy
   // FP32 copies used by the mixed form (NULL in the FP64 form)
   float* q32;         // [n] charges
-  float* selfc32;     // [KMC_NHOP]
+  float* selfc32;     // [KMC_MAXHOP]
   float2* Psi32;      // per-level locals, all levels
   float2* Rch32;      // child-offset regular harmonics
   float* phi_old32;   // [n]
-  float* phi_new32;   // [6n]
+  float* phi_new32;   // [nhop n]
   float* dU32;        // [6n]
   // per step
   double* phi_old;    // [n]
-  double* phi_new;    // [6n]
-  uint8_t* mask;      // [6n]
-  double* dU;         // [6n]
-  double* rate;       // [6n]
+  double* phi_new;    // [nhop n]
+  uint8_t* mask;      // [nhop n]
+  double* dU;         // [nhop n]
+  double* rate;       // [nhop n]
   double* bsum;       // [nblk]
   int64_t* event;     // [1]
   double* dtq;        // [2] (dt, Q)

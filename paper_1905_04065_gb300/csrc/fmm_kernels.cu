@@ -1061,11 +1061,9 @@ __device__ double self_corr_dev(const Geo& g, const double2* S, double dx, doubl
 
 __global__ void k_selfcorr(const Geo g, const Dev d) {
   int k = threadIdx.x;
-  if (k >= KMC_NHOP) return;
+  if (k >= (g.nhop > 0 ? g.nhop : KMC_NHOP)) return;
   double h = (g.E > 0) ? g.h : 1.0;
-  double dx = 0, dy = 0, dz = 0;
-  double sgn = (k & 1) ? -h : h;
-  if (k < 2) dx = sgn; else if (k < 4) dy = sgn; else dz = sgn;
+  const double dx = hop_c(k, 0) * h, dy = hop_c(k, 1) * h, dz = hop_c(k, 2) * h;
   double c = self_corr_dev(g, d.S, dx, dy, dz);
   d.selfc[k] = c;
   if (d.selfc32) d.selfc32[k] = (float)c;

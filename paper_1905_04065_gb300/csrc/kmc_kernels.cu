@@ -26,7 +26,15 @@ __constant__ double c_inv_d[KMC_NTRI];
 __constant__ float2 c_inv2_f[KMC_NTRI];      // (1/((n-m)(n+m)), same) pairs for packed FP32
 __constant__ float c_halfm_f[KMC_MAXP + 2];   // -1/(2m)
 __constant__ double c_halfm_d[KMC_MAXP + 2];
-__constant__ int c_hop[KMC_NHOP][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+// Hop entries of a leaf's propose CTA, per hop set (0: the 6 faces, 1: the
+// 14 faces and body diagonals): entry 0 is the leaf itself (every hop), the
+// others the neighbour leaves from which a hop can enter it -- the 6 face
+// neighbours for the face set, all 26 for the 14-hop set.  c_ent_leaf is the
+// entry's index in the 27-neighbourhood list, c_ent_hops the bit set of the
+// hops that can enter from there (component -o_a on every axis a where the
+// neighbour's offset o_a is not 0).
+__constant__ int c_ent_leaf[2][27];
+__constant__ uint32_t c_ent_hops[2][27];
 
 void kmc_upload_constants(int p) {
   static float invf[KMC_NTRI];
@@ -52,6 +60,38 @@ void kmc_upload_constants(int p) {
   cudaMemcpyToSymbol(c_inv_d, invd, sizeof(invd));
   cudaMemcpyToSymbol(c_halfm_f, hf, sizeof(hf));
   cudaMemcpyToSymbol(c_halfm_d, hd, sizeof(hd));
+  static int el[2][27];
+  static uint32_t eh[2][27];
+  for (int hs = 0; hs < 2; hs++) {
+    const int nhop = hs ? KMC_MAXHOP : KMC_NHOP, ne = hs ? 27 : 1 + KMC_NHOP;
+    for (int e = 0; e < 27; e++) {
+      el[hs][e] = 0;
+      eh[hs][e] = 0;
+      if (e >= ne) continue;
+      int li = e, off[3] = {0, 0, 0};
+      if (!hs && e > 0)  // the neighbour across face e - 1
+        for (int a = 0; a < 3; a++) off[a] = hop_c(e - 1, a);
+      if (hs && e > 0) {
+        const int qq = e <= 13 ? e - 1 : e;
+        off[0] = qq % 3 - 1;
+        off[1] = (qq / 3) % 3 - 1;
+        off[2] = qq / 9 - 1;
+      }
+      if (!hs && e > 0) {
+        const int qq = (off[0] + 1) + 3 * (off[1] + 1) + 9 * (off[2] + 1);
+        li = qq < 13 ? qq + 1 : qq;
+      }
+      el[hs][e] = li;
+      for (int k = 0; k < nhop; k++) {
+        bool ok = true;
+        for (int a = 0; a < 3; a++)
+          if (off[a] != 0 && hop_c(k, a) != -off[a]) ok = false;
+        if (ok) eh[hs][e] |= 1u << k;
+      }
+    }
+  }
+  cudaMemcpyToSymbol(c_ent_leaf, el, sizeof(el));
+  cudaMemcpyToSymbol(c_ent_hops, eh, sizeof(eh));
   (void)p;
 }
 
@@ -436,15 +476,6 @@ __device__ __forceinline__ void fixed_add(long long* a, double v) {
   atomicAdd((unsigned long long*)a, (unsigned long long)__double2ll_rn(v));
 }
 
-// list index of leaf f in {own leaf (f = 0), neighbour across face f - 1}
-// within the 27-neighbourhood list (own leaf first, then x fastest, centre
-// skipped)
-__device__ __forceinline__ int face_leaf(int f) {
-  if (!f) return 0;
-  const int* o = c_hop[f - 1];
-  const int qq = (o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1);
-  return qq < 13 ? qq + 1 : qq;
-}
 
 // Evaluation is per distinct site of the leaf: the potential at a site is
 // needed once even when several charges propose to hop there, and at an own
@@ -459,7 +490,7 @@ __device__ __forceinline__ int face_leaf(int f) {
 // coordinates come from the slot positions (coalesced), user indices only
 // where an output is written.  Potentials are written in precision T (FP32
 // arrays in the mixed form, FP64 arrays in the FP64 form).
-template <typename T>
+template <typename T, int NH>
 __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g, const Dev d, int chunk) {
   typedef typename cplx<T>::type C;
   typedef typename vec4<T>::type V4;
@@ -565,15 +596,16 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
   // (1) + (2): warp w handles the leaves f = w and w + 4 of {own leaf (f = 0),
   // the neighbour across face f - 1 (f = 1..6)}; the first 32 charges of
   // each are loaded at once, before the occupancy barrier
-  static_assert(PROP_THREADS == 128, "four warps cover the seven leaves twice");
+  static_assert(PROP_THREADS == 128, "four warps: entries warp, warp + 4, ...");
+  constexpr int hs = NH == KMC_NHOP ? 0 : 1, ne = hs ? 27 : 1 + KMC_NHOP, nhop = NH;
   const int cnt_own = nb_cnt[0];
   const int64_t base_own = nb_base[0];
   V4 pv[2];
 #pragma unroll
   for (int i = 0; i < 2; i++) {
-    const int f = warp + 4 * i;
-    if (f <= KMC_NHOP) {
-      const int li = face_leaf(f);
+    const int e = warp + 4 * i;
+    if (e < ne) {
+      const int li = c_ent_leaf[hs][e];
       if (lane < nb_cnt[li]) pv[i] = spos[nb_base[li] + lane];
     }
   }
@@ -587,28 +619,29 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
     }
   __syncthreads();
 
-  // (2) hop targets inside this leaf: own hops and hops entering from the six
-  // face neighbours (the neighbour across face f - 1 hops in direction (f-1)^1)
+  // (2) hop targets inside this leaf: the leaf's own hops and the hops that
+  // enter it from the neighbours of its entry list
 #pragma unroll
-  for (int i = 0; i < 2; i++) {
-    const int f = warp + 4 * i;
-    if (f > KMC_NHOP) continue;
-    const int li = face_leaf(f);
+  for (int i = 0; i < (ne + 3) / 4; i++) {
+    const int e = warp + 4 * i;
+    if (e >= ne) break;
+    const int li = c_ent_leaf[hs][e];
+    const uint32_t hm = c_ent_hops[hs][e];
     const int64_t mb = nb_base[li];
     const int cm = nb_cnt[li];
     for (int j = lane; j < cm; j += 32) {
-      const V4 v = j < 32 ? pv[i] : spos[mb + j];
+      const V4 v = (j < 32 && i < 2) ? (i == 0 ? pv[0] : pv[1]) : spos[mb + j];
       const int gx = lattice_coord(v.x, ih), gy = lattice_coord(v.y, ih), gz = lattice_coord(v.z, ih);
-      const int k0 = f ? ((f - 1) ^ 1) : 0, k1 = f ? k0 + 1 : KMC_NHOP;
-      for (int k = k0; k < k1; k++) {
-        const int tx = wrap1(gx + c_hop[k][0], E), ty = wrap1(gy + c_hop[k][1], E), tz = wrap1(gz + c_hop[k][2], E);
+      for (uint32_t hb = hm; hb; hb &= hb - 1) {
+        const int k = __ffs(hb) - 1;
+        const int tx = wrap1(gx + hop_c(k, 0), E), ty = wrap1(gy + hop_c(k, 1), E), tz = wrap1(gz + hop_c(k, 2), E);
         int ux = tx - gx0, uy = ty - gy0, uz = tz - gz0;
         if (ux < 0 || ux >= W || uy < 0 || uy >= W || uz < 0 || uz >= W) continue;  // another leaf's CTA
         int lt = ux + W * (uy + W * uz);
         if (bits[lt >> 5] & (1u << (lt & 31))) {
           const int32_t u = d.uid[mb + j];
-          d.mask[6 * (int64_t)u + k] = 0;
-          out_new[6 * (int64_t)u + k] = qnan<T>();
+          d.mask[(int64_t)nhop * u + k] = 0;
+          out_new[(int64_t)nhop * u + k] = qnan<T>();
         } else {
           atomicOr(&need[lt >> 5], 1u << (lt & 31));
         }
@@ -761,15 +794,15 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
       }
     }
   }
-  // the write-out's inputs (first 32 charges of this warp's leaves) are
-  // loaded now, so that their latency passes during the L2P
+  // the write-out's inputs (first 32 charges of this warp's first two
+  // entries) are loaded now, so that their latency passes during the L2P
   V4 wv[2];
   int32_t wu[2];
 #pragma unroll
   for (int i = 0; i < 2; i++) {
-    const int f = warp + 4 * i;
-    if (f <= KMC_NHOP) {
-      const int li = face_leaf(f);
+    const int e = warp + 4 * i;
+    if (e < ne) {
+      const int li = c_ent_leaf[hs][e];
       if (lane < nb_cnt[li]) {
         wu[i] = d.uid[nb_base[li] + lane];
         wv[i] = spos[nb_base[li] + lane];
@@ -794,26 +827,28 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
   __syncthreads();
   // (5) write-out: old-position potentials and unmasked hop potentials
 #pragma unroll
-  for (int i = 0; i < 2; i++) {
-    const int f = warp + 4 * i;
-    if (f > KMC_NHOP) continue;
-    const int li = face_leaf(f);
+  for (int i = 0; i < (ne + 3) / 4; i++) {
+    const int e = warp + 4 * i;
+    if (e >= ne) break;
+    const int li = c_ent_leaf[hs][e];
+    const uint32_t hm = c_ent_hops[hs][e];
     const int64_t mb = nb_base[li];
     const int cm = nb_cnt[li];
     for (int j = lane; j < cm; j += 32) {
-      const int32_t u = j < 32 ? wu[i] : d.uid[mb + j];
-      const V4 v = j < 32 ? wv[i] : spos[mb + j];
+      const bool pre = j < 32 && i < 2;
+      const int32_t u = pre ? (i == 0 ? wu[0] : wu[1]) : d.uid[mb + j];
+      const V4 v = pre ? (i == 0 ? wv[0] : wv[1]) : spos[mb + j];
       const int gx = lattice_coord(v.x, ih), gy = lattice_coord(v.y, ih), gz = lattice_coord(v.z, ih);
-      if (f == 0) out_old[u] = phis[(gx - gx0) + W * ((gy - gy0) + W * (gz - gz0))];
-      const int k0 = f ? ((f - 1) ^ 1) : 0, k1 = f ? k0 + 1 : KMC_NHOP;
-      for (int k = k0; k < k1; k++) {
-        const int tx = wrap1(gx + c_hop[k][0], E), ty = wrap1(gy + c_hop[k][1], E), tz = wrap1(gz + c_hop[k][2], E);
+      if (e == 0) out_old[u] = phis[(gx - gx0) + W * ((gy - gy0) + W * (gz - gz0))];
+      for (uint32_t hb = hm; hb; hb &= hb - 1) {
+        const int k = __ffs(hb) - 1;
+        const int tx = wrap1(gx + hop_c(k, 0), E), ty = wrap1(gy + hop_c(k, 1), E), tz = wrap1(gz + hop_c(k, 2), E);
         int ux = tx - gx0, uy = ty - gy0, uz = tz - gz0;
         if (ux < 0 || ux >= W || uy < 0 || uy >= W || uz < 0 || uz >= W) continue;
         int lt = ux + W * (uy + W * uz);
         if (bits[lt >> 5] & (1u << (lt & 31))) continue;  // masked: written in phase 2
-        out_new[6 * (int64_t)u + k] = phis[lt];
-        d.mask[6 * (int64_t)u + k] = 1;
+        out_new[(int64_t)nhop * u + k] = phis[lt];
+        d.mask[(int64_t)nhop * u + k] = 1;
       }
     }
   }
@@ -844,15 +879,26 @@ void kmc_prepare(const Geo& g, int prec) {
   if (g.E <= 0) return;
   const int chunk = propose_chunk(g);
   const size_t sm = propose_smem(g, prec, chunk);
-  if (prec == 0) raise_dynamic_smem((const void*)k_propose_lattice<double>, sm);
-  else raise_dynamic_smem((const void*)k_propose_lattice<float>, sm);
+  if (g.nhop == KMC_MAXHOP) {
+    if (prec == 0) raise_dynamic_smem((const void*)k_propose_lattice<double, KMC_MAXHOP>, sm);
+    else raise_dynamic_smem((const void*)k_propose_lattice<float, KMC_MAXHOP>, sm);
+  } else {
+    if (prec == 0) raise_dynamic_smem((const void*)k_propose_lattice<double, KMC_NHOP>, sm);
+    else raise_dynamic_smem((const void*)k_propose_lattice<float, KMC_NHOP>, sm);
+  }
 }
 
 void kmc_propose_lattice(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
   const int chunk = propose_chunk(g);
   const size_t sm = propose_smem(g, prec, chunk);
-  if (prec == 0) k_propose_lattice<double><<<(unsigned)g.ML, PROP_THREADS, sm, s>>>(g, d, chunk);
-  else k_propose_lattice<float><<<(unsigned)g.ML, PROP_THREADS, sm, s>>>(g, d, chunk);
+  const unsigned nb = (unsigned)g.ML;
+  if (g.nhop == KMC_MAXHOP) {
+    if (prec == 0) k_propose_lattice<double, KMC_MAXHOP><<<nb, PROP_THREADS, sm, s>>>(g, d, chunk);
+    else k_propose_lattice<float, KMC_MAXHOP><<<nb, PROP_THREADS, sm, s>>>(g, d, chunk);
+  } else {
+    if (prec == 0) k_propose_lattice<double, KMC_NHOP><<<nb, PROP_THREADS, sm, s>>>(g, d, chunk);
+    else k_propose_lattice<float, KMC_NHOP><<<nb, PROP_THREADS, sm, s>>>(g, d, chunk);
+  }
 }
 
 // ------------------------------------------------------------------ dU, rates, block sums
@@ -906,7 +952,7 @@ __device__ __forceinline__ double scale_pow2(float m, int e) {
 // 2^-f from the MUFU ex2 and 2^-n put into the FP64 exponent, so rates keep
 // FP64 range down to 2^-1021 (an FP64 exp below that).  FP64: every
 // operation in FP64.
-template <bool MIXED>
+template <bool MIXED, int NH>
 __global__ void __launch_bounds__(FIN_THREADS) k_finalize(const Geo g, const Dev d) {
   __shared__ double ts[FIN_THREADS];
   const int64_t i = blockIdx.x * (int64_t)FIN_THREADS + threadIdx.x;
@@ -914,31 +960,37 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize(const Geo g, const Dev
   if (i < g.n) {
     const int E = g.E;
     const int s = d.site[i];
-    const int cx = s % E, cy = (s / E) % E, cz = s / (E * E);
-    const uint16_t* mk = (const uint16_t*)(d.mask + 6 * i);
-    const uint32_t mb = (uint32_t)mk[0] | ((uint32_t)mk[1] << 16);
-    const uint32_t mc = mk[2];
-    const uint32_t m6[6] = {mb & 0xff, (mb >> 8) & 0xff, (mb >> 16) & 0xff, mb >> 24, mc & 0xff, mc >> 8};
-    const int cc[3] = {cx, cy, cz};
-    double r6[6];
+    const int cc[3] = {s % E, (s / E) % E, s / (E * E)};
+    const uint16_t* mk = (const uint16_t*)(d.mask + NH * i);
+    double r6[NH];
     if (MIXED) {
       const float q = d.q32[i], po = d.phi_old32[i], ikT = (float)(1.0 / g.kT);
-      const float2* pn = (const float2*)(d.phi_new32 + 6 * i);
-      float du[6];
+      const float2* pn = (const float2*)(d.phi_new32 + NH * i);
+      float du[NH];
 #pragma unroll
-      for (int k2 = 0; k2 < 3; k2++) {
+      for (int k2 = 0; k2 < NH / 2; k2++) {
         const float2 v = pn[k2];
+        const uint32_t mb = mk[k2];
 #pragma unroll
         for (int o = 0; o < 2; o++) {
           const int k = 2 * k2 + o;
-          float dw = o ? -(float)g.h : (float)g.h;
-          if (o == 0 && cc[k2] == E - 1) dw -= (float)g.a;
-          if (o == 1 && cc[k2] == 0) dw += (float)g.a;
+          // the dipole change of the wrapped hop vector (components of the
+          // hop, minus the box edge where it crosses the periodic boundary)
+          float qd = 0.f;
+#pragma unroll
+          for (int ax = 0; ax < 3; ax++) {
+            const int hc = hop_c(k, ax);
+            if (hc == 0) continue;
+            float dw = hc > 0 ? (float)g.h : -(float)g.h;
+            if (hc > 0 && cc[ax] == E - 1) dw -= (float)g.a;
+            if (hc < 0 && cc[ax] == 0) dw += (float)g.a;
+            qd += q * d.fdip[ax] * dw;
+          }
           const float pv = o ? v.y : v.x;
           float duf = __int_as_float(0x7fc00000);
           double r = 0.0;
-          if (m6[k]) {
-            duf = q * (pv - po) - q * d.fdip[k2] * dw - q * q * d.selfc32[k];
+          if (o ? (mb >> 8) : (mb & 0xff)) {
+            duf = q * (pv - po) - qd - q * q * d.selfc32[k];
             const float y = fmaxf(duf, 0.f) * ikT * 1.4426950408889634f;
             const float n = floorf(y);
             const int e = __float_as_int(n + 12582912.0f) - 0x4B400000;  // exact integer value of n
@@ -948,41 +1000,49 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize(const Geo g, const Dev
           r6[k] = r;
         }
       }
-      float2* dout = (float2*)(d.dU32 + 6 * i);
+      float2* dout = (float2*)(d.dU32 + NH * i);
 #pragma unroll
-      for (int k2 = 0; k2 < 3; k2++) dout[k2] = make_float2(du[2 * k2], du[2 * k2 + 1]);
+      for (int k2 = 0; k2 < NH / 2; k2++) dout[k2] = make_float2(du[2 * k2], du[2 * k2 + 1]);
     } else {
       const double q = d.q[i], po = d.phi_old[i];
-      const double2* pn = (const double2*)(d.phi_new + 6 * i);
-      double du[6];
+      const double2* pn = (const double2*)(d.phi_new + NH * i);
+      const double cdip = 4.0 * M_PI / (3.0 * g.a * g.a * g.a);
+      double du[NH];
 #pragma unroll
-      for (int k2 = 0; k2 < 3; k2++) {
+      for (int k2 = 0; k2 < NH / 2; k2++) {
         const double2 v = pn[k2];
-        const double cM = 4.0 * M_PI / (3.0 * g.a * g.a * g.a) * d.dip[k2];
+        const uint32_t mb = mk[k2];
 #pragma unroll
         for (int o = 0; o < 2; o++) {
           const int k = 2 * k2 + o;
-          double dw = o ? -g.h : g.h;
-          if (o == 0 && cc[k2] == E - 1) dw -= g.a;
-          if (o == 1 && cc[k2] == 0) dw += g.a;
+          double qd = 0.0;
+#pragma unroll
+          for (int ax = 0; ax < 3; ax++) {
+            const int hc = hop_c(k, ax);
+            if (hc == 0) continue;
+            double dw = hc > 0 ? g.h : -g.h;
+            if (hc > 0 && cc[ax] == E - 1) dw -= g.a;
+            if (hc < 0 && cc[ax] == 0) dw += g.a;
+            qd += q * (cdip * d.dip[ax]) * dw;
+          }
           double dd = __longlong_as_double(0x7ff8000000000000LL), r = 0.0;
-          if (m6[k]) {
-            dd = q * ((o ? v.y : v.x) - po) - q * cM * dw - q * q * d.selfc[k];
+          if (o ? (mb >> 8) : (mb & 0xff)) {
+            dd = q * ((o ? v.y : v.x) - po) - qd - q * q * d.selfc[k];
             r = exp(-fmax(dd, 0.0) / g.kT);
           }
           du[k] = dd;
           r6[k] = r;
         }
       }
-      double2* dout = (double2*)(d.dU + 6 * i);
+      double2* dout = (double2*)(d.dU + NH * i);
 #pragma unroll
-      for (int k2 = 0; k2 < 3; k2++) dout[k2] = make_double2(du[2 * k2], du[2 * k2 + 1]);
+      for (int k2 = 0; k2 < NH / 2; k2++) dout[k2] = make_double2(du[2 * k2], du[2 * k2 + 1]);
     }
-    double2* rout = (double2*)(d.rate + 6 * i);
+    double2* rout = (double2*)(d.rate + NH * i);
 #pragma unroll
-    for (int k2 = 0; k2 < 3; k2++) rout[k2] = make_double2(r6[2 * k2], r6[2 * k2 + 1]);
+    for (int k2 = 0; k2 < NH / 2; k2++) rout[k2] = make_double2(r6[2 * k2], r6[2 * k2 + 1]);
 #pragma unroll
-    for (int k = 0; k < KMC_NHOP; k++) tsum += r6[k];
+    for (int k = 0; k < NH; k++) tsum += r6[k];
   }
   ts[threadIdx.x] = tsum;
   __syncthreads();
@@ -996,7 +1056,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_rate_bsum(const Geo g, const De
   int64_t i = blockIdx.x * (int64_t)FIN_THREADS + threadIdx.x;
   double tsum = 0.0;
   if (i < g.n)
-    for (int k = 0; k < KMC_NHOP; k++) tsum += d.rate[6 * i + k];
+    for (int k = 0; k < g.nhop; k++) tsum += d.rate[(int64_t)g.nhop * i + k];
   ts[threadIdx.x] = tsum;
   __syncthreads();
   block_scan(ts, FIN_THREADS);
@@ -1005,8 +1065,13 @@ __global__ void __launch_bounds__(FIN_THREADS) k_rate_bsum(const Geo g, const De
 
 void kmc_finalize_rates(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
   unsigned nb = (unsigned)((g.n + FIN_THREADS - 1) / FIN_THREADS);
-  if (prec == 0) k_finalize<false><<<nb, FIN_THREADS, 0, s>>>(g, d);
-  else k_finalize<true><<<nb, FIN_THREADS, 0, s>>>(g, d);
+  if (g.nhop == KMC_MAXHOP) {
+    if (prec == 0) k_finalize<false, KMC_MAXHOP><<<nb, FIN_THREADS, 0, s>>>(g, d);
+    else k_finalize<true, KMC_MAXHOP><<<nb, FIN_THREADS, 0, s>>>(g, d);
+  } else {
+    if (prec == 0) k_finalize<false, KMC_NHOP><<<nb, FIN_THREADS, 0, s>>>(g, d);
+    else k_finalize<true, KMC_NHOP><<<nb, FIN_THREADS, 0, s>>>(g, d);
+  }
 }
 
 // ------------------------------------------------------------------ selection
@@ -1073,7 +1138,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(const Geo g, const Dev d
     int64_t i = blk * FIN_THREADS + tid;
     double t = 0.0;
     if (i < g.n)
-      for (int k = 0; k < KMC_NHOP; k++) t += d.rate[6 * i + k];
+      for (int k = 0; k < g.nhop; k++) t += d.rate[(int64_t)g.nhop * i + k];
     ts[tid] = t;
   }
   if (tid == 0) sh_t = -1;
@@ -1096,15 +1161,15 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(const Geo g, const Dev d
     }
     int64_t i = blk * FIN_THREADS + t;
     int ksel = -1;
-    for (int k = 0; k < KMC_NHOP; k++) {
-      double r = d.rate[6 * i + k];
+    for (int k = 0; k < g.nhop; k++) {
+      double r = d.rate[(int64_t)g.nhop * i + k];
       if (r > 0.0 && run + r >= rr) { ksel = k; break; }
       run += r;
     }
     if (ksel < 0)
-      for (int k = KMC_NHOP - 1; k >= 0; k--)
-        if (d.rate[6 * i + k] > 0.0) { ksel = k; break; }
-    *d.event = 6 * i + ksel;
+      for (int k = g.nhop - 1; k >= 0; k--)
+        if (d.rate[(int64_t)g.nhop * i + k] > 0.0) { ksel = k; break; }
+    *d.event = (int64_t)g.nhop * i + ksel;
   }
 }
 
@@ -1137,12 +1202,12 @@ __global__ void k_move_from_event(const Geo g, const Dev d) {
   int64_t j = *d.event;
   mv.valid = 0;
   if (j >= 0) {
-    int64_t i = j / 6;
-    int k = (int)(j - 6 * i);
+    int64_t i = j / g.nhop;
+    int k = (int)(j - (int64_t)g.nhop * i);
     int E = g.E;
     int s = d.site[i];
     int gx = s % E, gy = (s / E) % E, gz = s / (E * E);
-    int tx = (gx + c_hop[k][0] + E) % E, ty = (gy + c_hop[k][1] + E) % E, tz = (gz + c_hop[k][2] + E) % E;
+    int tx = (gx + hop_c(k, 0) + E) % E, ty = (gy + hop_c(k, 1) + E) % E, tz = (gz + hop_c(k, 2) + E) % E;
     mv.valid = 1;
     mv.i = (int32_t)i;
     mv.site_old = s;
@@ -1805,10 +1870,14 @@ void kmc_stage_general(const Geo& g, const Dev& d, int64_t m, const int32_t* par
 // launch inside a stream capture would invalidate the capture
 static void kmc_preload() {
   cudaFuncAttributes fa;
-  cudaFuncGetAttributes(&fa, k_propose_lattice<float>);
-  cudaFuncGetAttributes(&fa, k_propose_lattice<double>);
-  cudaFuncGetAttributes(&fa, k_finalize<true>);
-  cudaFuncGetAttributes(&fa, k_finalize<false>);
+  cudaFuncGetAttributes(&fa, k_propose_lattice<float, KMC_NHOP>);
+  cudaFuncGetAttributes(&fa, k_propose_lattice<double, KMC_NHOP>);
+  cudaFuncGetAttributes(&fa, k_propose_lattice<float, KMC_MAXHOP>);
+  cudaFuncGetAttributes(&fa, k_propose_lattice<double, KMC_MAXHOP>);
+  cudaFuncGetAttributes(&fa, k_finalize<true, KMC_NHOP>);
+  cudaFuncGetAttributes(&fa, k_finalize<false, KMC_NHOP>);
+  cudaFuncGetAttributes(&fa, k_finalize<true, KMC_MAXHOP>);
+  cudaFuncGetAttributes(&fa, k_finalize<false, KMC_MAXHOP>);
   cudaFuncGetAttributes(&fa, k_rate_bsum);
   cudaFuncGetAttributes(&fa, k_select);
   cudaFuncGetAttributes(&fa, k_record);

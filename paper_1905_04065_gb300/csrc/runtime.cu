@@ -213,6 +213,7 @@ void kmc_opts_default(kmc_opts* o) {
   o->device = 0;
   o->leaf_capacity = 0;
   o->m2l = KMC_M2L_TENSOR;
+  o->hops = KMC_HOPS_6;
 }
 
 const char* kmc_last_error(kmc_handle h) { return h ? h->msg : g_static_msg; }
@@ -277,7 +278,8 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   *out = h;
   // ---- host-side argument checks
   if (n < 2) return fail(h, KMC_ERR_ARG, "need at least 2 charges (n = %lld)", (long long)n);
-  if (n > 0x7fffffffLL / 6) return fail(h, KMC_ERR_ARG, "too many charges (n = %lld)", (long long)n);
+  if (n > 0x7fffffffLL / (o.hops == KMC_HOPS_14 ? KMC_MAXHOP : KMC_NHOP))
+    return fail(h, KMC_ERR_ARG, "too many charges (n = %lld)", (long long)n);
   if (levels < 3 || levels > KMC_MAXL) return fail(h, KMC_ERR_ARG, "levels must be in [3, %d] (got %d)", KMC_MAXL, levels);
   if (order < 1 || order > KMC_MAXP) return fail(h, KMC_ERR_ARG, "order must be in [1, %d] (got %d)", KMC_MAXP, order);
   if (!(box > 0.0) || !isfinite(box)) return fail(h, KMC_ERR_ARG, "box must be positive and finite");
@@ -286,11 +288,13 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   if (o.mem != KMC_MEM_HOST && o.mem != KMC_MEM_DEVICE) return fail(h, KMC_ERR_ARG, "unknown memory kind");
   if (!(o.kT > 0.0)) return fail(h, KMC_ERR_ARG, "kT must be positive");
   if (o.m2l != KMC_M2L_TENSOR && o.m2l != KMC_M2L_FP64) return fail(h, KMC_ERR_ARG, "unknown M2L arithmetic");
+  if (o.hops != KMC_HOPS_6 && o.hops != KMC_HOPS_14) return fail(h, KMC_ERR_ARG, "unknown hop set");
   int r = init_impl(h, n, positions, charges, box, levels, order);
   if (r) return r;
   Geo& g = h->g;
   g.kT = o.kT;
   g.m2l = o.m2l;
+  g.nhop = o.hops == KMC_HOPS_14 ? KMC_MAXHOP : KMC_NHOP;
   if (o.lattice_edge > 0) {
     int E = o.lattice_edge;
     if (E % g.nL != 0) return fail(h, KMC_ERR_ARG, "lattice edge %d is not a multiple of 2^(levels-1) = %d", E, g.nL);
@@ -374,24 +378,24 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   ALLOC(d.Itab2, sizeof(double2) * (size_t)KMC_TOP_NOFF * g.P2);
   ALLOC(d.S, sizeof(double2) * g.P2);
   ALLOC(d.Rch, sizeof(double2) * (size_t)(g.L + 1) * 8 * g.P);
-  ALLOC(d.selfc, sizeof(double) * KMC_NHOP);
+  ALLOC(d.selfc, sizeof(double) * KMC_MAXHOP);
   ALLOC(d.dip, sizeof(double) * 3);
   ALLOC(d.fdip, sizeof(float) * 4);
   ALLOC(d.U, sizeof(double));
   if (h->prec == 1) {
     ALLOC(d.q32, sizeof(float) * n);
-    ALLOC(d.selfc32, sizeof(float) * KMC_NHOP);
+    ALLOC(d.selfc32, sizeof(float) * KMC_MAXHOP);
     ALLOC(d.Psi32, sizeof(float2) * g.ncell_total * g.P);
     ALLOC(d.Rch32, sizeof(float2) * (size_t)(g.L + 1) * 8 * g.P);
     ALLOC(d.phi_old32, sizeof(float) * n);
-    ALLOC(d.phi_new32, sizeof(float) * 6 * n);
-    ALLOC(d.dU32, sizeof(float) * 6 * n);
+    ALLOC(d.phi_new32, sizeof(float) * g.nhop * n);
+    ALLOC(d.dU32, sizeof(float) * g.nhop * n);
   }
   ALLOC(d.phi_old, sizeof(double) * n);
-  ALLOC(d.phi_new, sizeof(double) * 6 * n);
-  ALLOC(d.mask, sizeof(uint8_t) * 6 * n);
-  ALLOC(d.dU, sizeof(double) * 6 * n);
-  ALLOC(d.rate, sizeof(double) * 6 * n);
+  ALLOC(d.phi_new, sizeof(double) * g.nhop * n);
+  ALLOC(d.mask, sizeof(uint8_t) * g.nhop * n);
+  ALLOC(d.dU, sizeof(double) * g.nhop * n);
+  ALLOC(d.rate, sizeof(double) * g.nhop * n);
   ALLOC(d.bsum, sizeof(double) * ((n + KMC_FIN_PARTICLES - 1) / KMC_FIN_PARTICLES + 1));
   ALLOC(d.event, sizeof(int64_t) * 2);
   ALLOC(d.dtq, sizeof(double) * 2);
@@ -410,7 +414,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   cudaStream_t s = h->stream;
   CK(cudaMemsetAsync(d.err, 0, sizeof(int) * 4, s));
   CK(cudaMemsetAsync(d.uid, 0xff, sizeof(int32_t) * nslot, s));
-  CK(cudaMemsetAsync(d.mask, 0, 6 * n, s));
+  CK(cudaMemsetAsync(d.mask, 0, (size_t)g.nhop * n, s));
   CK(cudaMemsetAsync(d.Psi, 0, sizeof(double2) * g.ncell_total * g.P, s));
   CK(cudaMemcpyAsync(d.q, charges, sizeof(double) * n, in_kind(h), s));
   CK(cudaMemcpyAsync(d.pos, positions, sizeof(double) * 3 * n, in_kind(h), s));
@@ -478,7 +482,7 @@ int kmc_fmm_propose_lattice(kmc_handle h, uint8_t* mask, double* dU) {
   kmc_finalize_rates(h->g, h->d, h->prec, h->stream);
   CKLAUNCH();
   h->rates_valid = true;
-  const int64_t m = 6 * h->g.n;
+  const int64_t m = (int64_t)h->g.nhop * h->g.n;
   if (mask) CK(cudaMemcpyAsync(mask, h->d.mask, m, out_kind(h), h->stream));
   if (dU) {
     if (h->prec == 1) kmc_widen(h->d.dU32, h->d.dU, m, h->stream);
@@ -640,14 +644,13 @@ int kmc_fmm_accept_event(kmc_handle h, int64_t event, double* dU_accepted) {
   if (r) return r;
   const Geo& g = h->g;
   if (g.E <= 0) return fail(h, KMC_ERR_STATE, "kmc_fmm_accept_event needs lattice mode");
-  if (event < 0 || event >= 6 * g.n) return fail(h, KMC_ERR_ARG, "event index out of range");
-  int32_t i = (int32_t)(event / 6);
-  int k = (int)(event % 6);
+  if (event < 0 || event >= (int64_t)g.nhop * g.n) return fail(h, KMC_ERR_ARG, "event index out of range");
+  int32_t i = (int32_t)(event / g.nhop);
+  int k = (int)(event % g.nhop);
   double p[3];
   CK(cudaMemcpy(p, h->d.pos + 3 * (int64_t)i, sizeof(p), cudaMemcpyDeviceToHost));
-  static const int hop[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
   double t[3];
-  for (int c = 0; c < 3; c++) t[c] = p[c] + hop[k][c] * g.h;
+  for (int c = 0; c < 3; c++) t[c] = p[c] + hop_c(k, c) * g.h;
   return accept_general(h, i, t, dU_accepted);
 }
 
@@ -658,7 +661,7 @@ int kmc_step(kmc_handle h, const double* rates, double zeta, double xi, int64_t*
     return fail(h, KMC_ERR_ARG, "zeta and xi must lie in (0, 1]");
   cudaStream_t s = h->stream;
   if (rates) {
-    CK(cudaMemcpyAsync(h->d.rate, rates, sizeof(double) * 6 * h->g.n, in_kind(h), s));
+    CK(cudaMemcpyAsync(h->d.rate, rates, sizeof(double) * h->g.nhop * h->g.n, in_kind(h), s));
     kmc_rate_bsum(h->g, h->d, s);
     CKLAUNCH();
   } else if (!h->rates_valid) {

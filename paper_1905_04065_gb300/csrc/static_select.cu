@@ -53,6 +53,7 @@ extern "C" int kmc_select_static(const double* rates, int64_t n, double zeta, do
   Geo g;
   memset(&g, 0, sizeof(g));
   g.n = n;
+  g.nhop = KMC_NHOP;
   Dev d;
   memset(&d, 0, sizeof(d));
   d.rate = (double*)rates;

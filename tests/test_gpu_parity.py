@@ -28,10 +28,10 @@ def _k():
     return k
 
 
-def _init(E, sites, q, L, p, precision="fp64", kT=0.1, positions=None):
+def _init(E, sites, q, L, p, precision="fp64", kT=0.1, positions=None, hops=6):
     k = _k()
     pos = workloads.site_positions(E, sites) if positions is None else positions
-    return k.kmc_fmm_init(pos, q, float(E), L, p, precision=precision, lattice_edge=E, kT=kT)
+    return k.kmc_fmm_init(pos, q, float(E), L, p, precision=precision, lattice_edge=E, kT=kT, hops=hops)
 
 
 def _rel_err(a, b, mask):
@@ -255,6 +255,57 @@ def test_teacher_forced_trajectory_small(small):
     assert d_U < 1e-5, d_U
     U2 = k.kmc_fmm_energy(h)
     assert abs(U2 - st.energy()) < 1e-4 * abs(st.energy())
+
+
+def _oracle_hops(st, nh):
+    """Masks and dU of every hop of the hop set (event order j = nh i + k) from
+    the oracle's site potential; the targets come from the workload's hop list."""
+    tg = workloads.hop_targets(st.E, st.sites, nh).reshape(-1)
+    mask = (st.occ[tg] == 0).astype(np.uint8)
+    ok = mask.astype(bool)
+    dU = np.full(len(tg), np.nan)
+    dU[ok] = st.delta_u_list(np.repeat(np.arange(st.n), nh)[ok], tg[ok])
+    return dU, mask, tg
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_teacher_forced_trajectory_14_hops(small, precision):
+    """The hop set of the paper's Sec. 5.3 benchmark (6 faces and 8 body
+    diagonals): masks exactly and dU within the p = 12 tolerance against the
+    oracle at every step of a trajectory on which the oracle's event is
+    accepted on both sides (diagonal hops included), events compared except
+    near ties, and the energy after the trajectory."""
+    k = _k()
+    w, sites, q, _ = small
+    E, kT, p, nh = w["E"], w["kT"], 12, 14
+    st = oracle.LatticeState(E, sites, q)
+    h = _init(E, sites, q, w["L"], p, precision=precision, kT=kT, hops=nh)
+    u = workloads.uniforms(30, w["seed"] + 14)
+    agree, diag = 0, 0
+    for s in range(30):
+        mask, dU = k.kmc_fmm_propose_lattice(h)
+        assert mask.shape == (len(q), nh)
+        dU_o, mask_o, tg = _oracle_hops(st, nh)
+        assert np.array_equal(mask.reshape(-1), mask_o)
+        assert np.all(np.isnan(dU.reshape(-1)[mask_o == 0]))
+        ok = mask_o.astype(bool)
+        tol = TOL[p] * np.max(np.abs(dU_o[ok]))
+        assert np.max(np.abs(dU.reshape(-1)[ok] - dU_o[ok])) < tol
+        ev, dt, Q = k.kmc_step(h, None, u[s, 0], u[s, 1])
+        r_o = oracle.rates(dU_o, mask_o, kT)
+        j, Q_o, dt_o = oracle.select(r_o, u[s, 0], u[s, 1])
+        if ev == j:
+            agree += 1
+        else:
+            assert _near_tie(dU_o, mask_o, kT, u[s, 0], tol), (s, ev, j)
+        du_acc = k.kmc_fmm_accept_event(h, j)
+        assert abs(du_acc - dU_o[j]) < tol
+        diag += int(j % nh >= 6)
+        st.accept_site(j // nh, tg[j])
+    assert agree >= 28
+    assert np.array_equal(k.kmc_fmm_positions(h), workloads.site_positions(E, st.sites))
+    assert abs(k.kmc_fmm_energy(h) - st.energy()) < 1e-4 * abs(st.energy())
+    print(f"14 hops ({precision}): {agree}/30 events agree, {diag} diagonal hops accepted")
 
 
 def test_run_matches_stepwise(small):

@@ -18,6 +18,12 @@ definitions used throughout this repository):
   blobs   512^3 sites, 8388608 charges, 70% in 200 Gaussian blobs (sigma 8), L=7, p=10, 200 steps
   tile    128^3 sites, 131072 charges, L=5, p=12: the leaf shape of "large" (8^3 sites and 32
           charges per leaf) on 4096 leaves, for kernel profiles that span several waves
+  sec53   the paper's Sec. 5.3 single-node benchmark shape: one charge per 27 sites and 14 hop
+          targets (6 faces, 8 body diagonals), L=6, p=12, on 288^3 sites (884,736 charges; the
+          paper's 300^3 lattice is not divisible into 32^3 leaves of whole sites)
+
+Every workload uses the 6 face hops except sec53 (key "hops").  Hop k is HOPS[k]: the faces
+(+x, -x, +y, -y, +z, -z), then the body diagonals with x fastest.
 """
 from __future__ import annotations
 
@@ -29,7 +35,23 @@ WORKLOADS = {
     "large": dict(E=256, N=1048576, L=6, p=12, kT=0.05, steps=1000, seed=1003, recompute_every=0),
     "blobs": dict(E=512, N=8388608, L=7, p=10, kT=0.05, steps=200, seed=1005, recompute_every=0),
     "tile": dict(E=128, N=131072, L=5, p=12, kT=0.05, steps=100, seed=1007, recompute_every=0),
+    "sec53": dict(E=288, N=884736, L=6, p=12, kT=0.05, steps=100, seed=1006, recompute_every=0, hops=14),
 }
+HOPS = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
+        (1, 1, 1), (-1, 1, 1), (1, -1, 1), (-1, -1, 1), (1, 1, -1), (-1, 1, -1), (1, -1, -1), (-1, -1, -1)]
+
+
+def hop_vectors(nhop: int = 6) -> np.ndarray:
+    """The first nhop hop vectors (6: faces; 14: faces and body diagonals), int64 (nhop, 3)."""
+    assert nhop in (6, 14)
+    return np.array(HOPS[:nhop], dtype=np.int64)
+
+
+def hop_targets(E: int, sites: np.ndarray, nhop: int = 6) -> np.ndarray:
+    """Target site of every hop, (n, nhop), event order j = nhop i + k, periodic."""
+    xyz = site_xyz(E, np.asarray(sites, dtype=np.int64))
+    t = (xyz[:, None, :] + hop_vectors(nhop)[None, :, :]) % E
+    return t[..., 0] + E * (t[..., 1] + E * t[..., 2])
 BATCH = dict(replicas=64, edges=(32, 48, 64, 96, 128), occ=(0.02, 0.15), p=10, kT=0.05, steps=500,
              seed=1004, replica_seed0=2000)
 
