@@ -298,3 +298,50 @@ def kmc_step(state: LatticeState, kT: float, zeta: float, xi: float):
     if j >= 0:
         state.accept(j // 6, j % 6)
     return j, dt, Q, dU, mask
+
+
+# ---------------------------------------------------------------- free space
+# Free-space boundary conditions (Sec. 2.2 before the periodic case; Sec. 3,
+# Eq. (proposed_energy)): a finite charge distribution in unbounded space, no
+# images and no neutrality condition.  The definitions, summed directly in
+# FP64 (numpy), are
+#   U  = 1/2 sum_{i != j} q_i q_j / |r_i - r_j|,
+#   dU = q_k sum_{j != k} q_j (1/|r' - r_j| - 1/|r_k - r_j|)   (charge k: r_k -> r').
+# Parity status: pinned by closed forms (two charges, a square of alternating
+# charges), U(after) - U(before), hop reversal and rigid-motion invariance.
+
+def free_energy(pos: np.ndarray, q: np.ndarray) -> float:
+    """Free-space energy, direct pair sum (each pair once)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    U = 0.0
+    for i in range(len(q) - 1):
+        r = np.sqrt(np.sum((pos[i + 1:] - pos[i]) ** 2, axis=1))
+        U += q[i] * np.sum(q[i + 1:] / r)
+    return float(U)
+
+
+def free_delta_u(pos: np.ndarray, q: np.ndarray, particle, target, chunk: int = 512) -> np.ndarray:
+    """Free-space dU of moving charge particle[t] to target[t]; NaN where the
+    target coincides with another charge or with the charge itself."""
+    pos = np.asarray(pos, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    particle = np.atleast_1d(np.asarray(particle, dtype=np.int64))
+    target = np.asarray(target, dtype=np.float64).reshape(-1, 3)
+    out = np.empty(len(particle), dtype=np.float64)
+    for c0 in range(0, len(particle), chunk):
+        pk = particle[c0:c0 + chunk]
+        tk = target[c0:c0 + chunk]
+        d_new = np.sqrt(np.sum((tk[:, None, :] - pos[None, :, :]) ** 2, axis=2))
+        d_old = np.sqrt(np.sum((pos[pk][:, None, :] - pos[None, :, :]) ** 2, axis=2))
+        rows = np.arange(len(pk))
+        with np.errstate(divide="ignore", invalid="ignore"):
+            inv_new = 1.0 / d_new
+            inv_old = 1.0 / d_old
+        inv_new[rows, pk] = 0.0  # the moving charge itself
+        inv_old[rows, pk] = 0.0
+        v = q[pk] * ((inv_new - inv_old) @ q)
+        singular = np.any(d_new == 0.0, axis=1) | np.all(tk == pos[pk], axis=1)
+        v[singular] = np.nan
+        out[c0:c0 + chunk] = v
+    return out

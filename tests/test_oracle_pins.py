@@ -395,3 +395,58 @@ def test_kmc_step_moves_charge():
     assert mask[i, k] == 1
     assert st.sites[i] == oracle.hop_target(8, int(before[i]), k)
     assert np.array_equal(np.delete(st.sites, i), np.delete(before, i))
+
+
+# ---------------------------------------------------------------- free space
+def test_free_two_charges_closed_form():
+    """+1 at the origin moved to (1,0,0) next to -1 at (3,0,0): dU = -(1/2 - 1/3) = -1/6."""
+    pos = np.array([[0.0, 0.0, 0.0], [3.0, 0.0, 0.0]])
+    q = np.array([1.0, -1.0])
+    du = oracle.free_delta_u(pos, q, [0], [[1.0, 0.0, 0.0]])[0]
+    assert abs(du - (-1.0 / 6.0)) < 1e-15
+    assert abs(oracle.free_energy(pos, q) - (-1.0 / 3.0)) < 1e-15
+
+
+def test_free_square_energy_closed_form():
+    """Alternating +-1 on the corners of a unit square: four bonds of -1 and
+    two diagonals of +1/sqrt(2): U = -4 + sqrt(2)."""
+    pos = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0]], dtype=float)
+    q = np.array([1.0, -1.0, 1.0, -1.0])
+    assert abs(oracle.free_energy(pos, q) - (-4.0 + math.sqrt(2.0))) < 1e-14
+
+
+def test_free_delta_u_equals_energy_difference():
+    rng = np.random.default_rng(11)
+    pos = rng.random((40, 3)) * 10.0
+    q = rng.choice([-1.0, 1.0, 2.0], size=40)  # free space: no neutrality needed
+    U0 = oracle.free_energy(pos, q)
+    for k in range(5):
+        t = rng.random(3) * 10.0
+        du = oracle.free_delta_u(pos, q, [k], [t])[0]
+        p2 = pos.copy()
+        p2[k] = t
+        assert abs(du - (oracle.free_energy(p2, q) - U0)) < 1e-12 * max(1.0, abs(U0))
+
+
+def test_free_hop_reverse_and_rigid_motion():
+    rng = np.random.default_rng(12)
+    pos = rng.random((30, 3)) * 8.0
+    q = rng.choice([-1.0, 1.0], size=30)
+    t = pos[3] + np.array([1.0, 0.0, 0.0])
+    du1 = oracle.free_delta_u(pos, q, [3], [t])[0]
+    p2 = pos.copy()
+    p2[3] = t
+    du2 = oracle.free_delta_u(p2, q, [3], [pos[3]])[0]
+    assert abs(du1 + du2) < 1e-13
+    # translation and a rotation by 90 degrees about z leave dU unchanged
+    shift = np.array([3.5, -2.0, 7.25])
+    assert abs(oracle.free_delta_u(pos + shift, q, [3], [t + shift])[0] - du1) < 1e-12
+    rot = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    assert abs(oracle.free_delta_u(pos @ rot.T, q, [3], [rot @ t])[0] - du1) < 1e-12
+
+
+def test_free_singular_targets():
+    pos = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0]])
+    q = np.array([1.0, -1.0])
+    out = oracle.free_delta_u(pos, q, [0, 0], [[1.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    assert np.isnan(out).all()
