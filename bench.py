@@ -177,11 +177,19 @@ def measured_peaks():
 
 
 # --------------------------------------------------------------- CPU oracle sample
-def cpu_sample(E, sites, q, seconds_target=10.0, max_props=20000, nhop=6):
+def cpu_sample(E, sites, q, seconds_target=10.0, max_props=20000, nhop=6, bc="periodic"):
     """dU evals/s of the FP64 oracle's direct lattice sum (O(N) per proposal,
-    tabulated Ewald pair potential) on a seeded sample of unmasked hops."""
+    tabulated Ewald pair potential; free space: the direct Coulomb sum) on a
+    seeded sample of unmasked hops."""
     import oracle
-    G = oracle.psi_table(E)
+    G = oracle.psi_table(E) if bc == "periodic" else None
+    pos = workloads.site_positions(E, sites)
+
+    def evaluate(p, t):
+        if G is not None:
+            oracle.lattice_delta_u_direct(E, G, sites, q, p, t)
+        else:
+            oracle.free_delta_u(pos, q, p, workloads.site_positions(E, t))
     rng = np.random.default_rng(4242)
     occ = np.zeros(E ** 3, dtype=bool)
     occ[sites] = True
@@ -203,15 +211,17 @@ def cpu_sample(E, sites, q, seconds_target=10.0, max_props=20000, nhop=6):
     # calibrate on a small batch, then size the sample to ~seconds_target
     p, t = draw(64)
     t0 = time.perf_counter()
-    oracle.lattice_delta_u_direct(E, G, sites, q, p, t)
+    evaluate(p, t)
     dt = time.perf_counter() - t0
     m = int(min(max_props, max(64, seconds_target / max(dt / 64, 1e-9))))
     p, t = draw(m)
     t0 = time.perf_counter()
-    oracle.lattice_delta_u_direct(E, G, sites, q, p, t)
+    evaluate(p, t)
     dt = time.perf_counter() - t0
-    return dict(value=m / dt, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
-                sample=f"{m} unmasked hops, direct O(N) sum over the tabulated Ewald pair potential, FP64")
+    what = ("direct O(N) sum over the tabulated Ewald pair potential" if G is not None
+            else "direct O(N) free-space Coulomb sum (numpy, one process)")
+    return dict(value=m / dt, unit=UNIT, cores=oracle.num_threads() if G is not None else 1, kind="oracle",
+                sample=f"{m} unmasked hops, {what}, FP64")
 
 
 # --------------------------------------------------------------- reference arm
@@ -306,7 +316,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
     t0 = time.perf_counter()
     h = k.kmc_fmm_init(pos, q, float(E), L, p, precision="mixed", lattice_edge=E, kT=kT, stream=stream, device=dev,
-                       hops=nhop)
+                       hops=nhop, bc=args.bc)
     torch.cuda.synchronize()
     init_s = time.perf_counter() - t0
     work = pair_count(E, L, sites, nhop)
@@ -381,6 +391,7 @@ def run_gpu(args):
         del h
         torch.cuda.synchronize()
         h64 = k.kmc_fmm_init(pos, q, float(E), L, p, precision="fp64", lattice_edge=E, kT=kT, stream=stream, hops=nhop,
+                             bc=args.bc,
                              device=dev)
         k.kmc_run_profiled(h64, u[:1])
         ms64 = []
@@ -427,13 +438,14 @@ def run_gpu(args):
 
     cpu = None
     if not args.no_cpu and world == 1 or (world > 1 and rank == 0 and not args.no_cpu):
-        cpu = cpu_sample(E, sites, q, seconds_target=args.cpu_seconds, nhop=nhop)
+        cpu = cpu_sample(E, sites, q, seconds_target=args.cpu_seconds, nhop=nhop, bc=args.bc)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32-mixed (f32 near field + L2P, f64 far field / dU / accept)",
-        "data": "synthetic", "config": dict(_config(w, args.workload), parallelism=f"replicas x{world}"),
+        "data": "synthetic", "config": dict(_config(w, args.workload), parallelism=f"replicas x{world}",
+                                            bc=args.bc),
         "kmc_steps_per_s": steps_per_s,
         "propose_only_dU_evals_per_s": hops / (prop_ms * 1e-3),
         "phase_ms_per_step": {nm: phases[i] / args.steps for i, nm in enumerate(k.PHASES)},
@@ -527,6 +539,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--bc", default="periodic", choices=["periodic", "free"],
+                    help="boundary conditions of the lattice workloads (the configs are periodic)")
     ap.add_argument("--workload", default="large", choices=["small", "medium", "large", "blobs", "tile", "sec53", "batch"])
     ap.add_argument("--replicas", type=int, default=None)
     ap.add_argument("--no-tune", action="store_true")

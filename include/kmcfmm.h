@@ -64,6 +64,15 @@ enum kmc_precision {
 
 enum kmc_mem { KMC_MEM_HOST = 0, KMC_MEM_DEVICE = 1 };
 
+/* Boundary conditions (Sec. 2.2). */
+enum kmc_bc {
+  KMC_BC_PERIODIC = 0, /* the box replicated periodically, conducting boundary at infinity; the
+                          system must be neutral */
+  KMC_BC_FREE = 1      /* free space: the charges of the box alone, no images (Eq. (proposed_energy)
+                          as written); any net charge; lattice hops leaving the box are masked and
+                          general targets outside [0, box) are rejected */
+};
+
 /* Lattice hop set (the moves Algorithm 5 proposes for every charge). */
 enum kmc_hops {
   KMC_HOPS_6 = 0, /* the 6 nearest-neighbour sites */
@@ -93,12 +102,13 @@ typedef struct kmc_opts {
   int leaf_capacity;  /* off-lattice slots per leaf (0 = automatic); lattice mode uses (E/2^(L-1))^3 */
   int m2l;            /* kmc_m2l: arithmetic of the M2L at init and recompute */
   int hops;           /* kmc_hops: lattice hop set (nh = 6 or 14 hops per charge) */
+  int bc;             /* kmc_bc: boundary conditions */
 } kmc_opts;
 
 typedef struct kmc_fmm* kmc_handle;
 
 /* Fill opts with defaults: FP64, off-lattice, h = 1, kT = 1, NULL stream, host memory, device 0,
- * tensor-core M2L, 6 hops. */
+ * tensor-core M2L, 6 hops, periodic. */
 void kmc_opts_default(kmc_opts* opts);
 
 /*

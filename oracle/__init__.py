@@ -329,6 +329,7 @@ def free_delta_u(pos: np.ndarray, q: np.ndarray, particle, target, chunk: int = 
     particle = np.atleast_1d(np.asarray(particle, dtype=np.int64))
     target = np.asarray(target, dtype=np.float64).reshape(-1, 3)
     out = np.empty(len(particle), dtype=np.float64)
+    chunk = max(1, min(chunk, 4_000_000 // max(len(q), 1)))  # bounded temporaries
     for c0 in range(0, len(particle), chunk):
         pk = particle[c0:c0 + chunk]
         tk = target[c0:c0 + chunk]

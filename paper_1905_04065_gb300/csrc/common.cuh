@@ -88,6 +88,8 @@ struct Geo {
   double qmax;            // largest |charge|
   int m2l;                // M2L arithmetic: 0 = bf16 tensor-core slicing (p <= 16, else FP64), 1 = FP64
   int nhop;               // lattice hops per charge: 6 (faces) or 14 (faces and body diagonals)
+  int bc;                 // boundary conditions: 0 periodic (tinfoil), 1 free space
+  double dipc;            // 4 pi / (3 V): the dipole (surface) term's factor; 0 in free space
 };
 
 // cell coordinate of x on a level with n cells per side, floor(x n / a)

@@ -374,7 +374,9 @@ __global__ void __launch_bounds__(256) k_m2l_gemm(const Geo g, const Dev d, int 
       int sc = -1;
       if (b >= 0) {
         const int bx = b % nl, by = (b / nl) % nl, bz = b / (nl * nl);
-        sc = ((bx + tx + nl) % nl) + nl * (((by + ty + nl) % nl) + nl * ((bz + tz + nl) % nl));
+        const int ux = bx + tx, uy = by + ty, uz = bz + tz;
+        if (!g.bc) sc = ((ux + nl) % nl) + nl * (((uy + nl) % nl) + nl * ((uz + nl) % nl));
+        else if (ux >= 0 && ux < nl && uy >= 0 && uy < nl && uz >= 0 && uz < nl) sc = ux + nl * (uy + nl * uz);
       }
       scell[tid] = sc;
     }
@@ -665,7 +667,9 @@ __global__ void __launch_bounds__(128) k_m2l_oz(const Geo g, const Dev d, int l,
         int sc = -1;
         if (b >= 0) {
           const int bx = b % nl, by = (b / nl) % nl, bz = b / (nl * nl);
-          sc = ((bx + tx + nl) % nl) + nl * (((by + ty + nl) % nl) + nl * ((bz + tz + nl) % nl));
+          const int ux = bx + tx, uy = by + ty, uz = bz + tz;
+          if (!g.bc) sc = ((ux + nl) % nl) + nl * (((uy + nl) % nl) + nl * ((uz + nl) % nl));
+          else if (ux >= 0 && ux < nl && uy >= 0 && uy < nl && uz >= 0 && uz < nl) sc = ux + nl * (uy + nl * uz);
         }
         scell[tid] = sc;
       }
@@ -798,8 +802,12 @@ void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s) {
   double* R = (double*)scratch;
   double2* Iagg = (double2*)(R + 343 * n2 * n2);
   const int bs = g.P <= 128 ? 128 : 256;
-  k_m2l_top_agg<<<64, 128, 0, s>>>(g, d, Iagg);
-  k_m2l_top<<<8, bs, g.P * sizeof(double2), s>>>(g, d, Iagg);
+  if (g.bc) {  // free space: the 8 level-2 cells are all neighbours, the level-2 list is empty
+    cudaMemsetAsync(d.Psi + g.cell_off[2] * g.P, 0, sizeof(double2) * 8 * g.P, s);
+  } else {
+    k_m2l_top_agg<<<64, 128, 0, s>>>(g, d, Iagg);
+    k_m2l_top<<<8, bs, g.P * sizeof(double2), s>>>(g, d, Iagg);
+  }
   const bool tensor = g.m2l == 0 && g.p <= OZ_MAXP;
   unsigned long long *colmax = nullptr, *rowmax = nullptr;
   unsigned short *As = nullptr, *Bs = nullptr;
@@ -955,6 +963,10 @@ __global__ void k_lattice_reduce(const Geo g, const double2* terms, int nvec, do
 }
 
 void fmm_lattice_sums(const Geo& g, const Dev& d, cudaStream_t s) {
+  if (g.bc) {  // free space: no images, no far field
+    cudaMemsetAsync(d.S, 0, sizeof(double2) * g.P2, s);
+    return;
+  }
   const int nr = 2 * LS_NR + 1, nk = 2 * LS_KM + 1;
   int nvec = nr * nr * nr + nk * nk * nk;
   // scratch: nvec * P2 complex (reuses the per-step phi_new / dU buffers is not
@@ -1011,7 +1023,7 @@ __global__ void k_dipole(const Geo g, const Dev d) {
   }
   if (threadIdx.x < 3) {
     d.dip[threadIdx.x] = sh[threadIdx.x][0];
-    d.fdip[threadIdx.x] = (float)(4.0 * M_PI / (3.0 * g.a * g.a * g.a) * sh[threadIdx.x][0]);
+    d.fdip[threadIdx.x] = (float)(g.dipc * sh[threadIdx.x][0]);
   }
 }
 
@@ -1020,6 +1032,7 @@ __global__ void k_dipole(const Geo g, const Dev d) {
 // moving charge's interaction with its own images, equal to psi(d) - psi_reg(0)
 // of the tinfoil pair potential.
 __device__ double self_corr_dev(const Geo& g, const double2* S, double dx, double dy, double dz) {
+  if (g.bc) return 1.0 / sqrt(dx * dx + dy * dy + dz * dz);  // free space: the direct pair alone
   double s = 0.0;
   for (int a = -KMC_TOP; a <= KMC_TOP; a++)
     for (int b = -KMC_TOP; b <= KMC_TOP; b++)

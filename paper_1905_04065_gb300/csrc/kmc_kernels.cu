@@ -546,7 +546,9 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
       const int nleaf = sx + nL * (sy + nL * sz);
       nb_leaf[lane] = nleaf;
       nb_base[lane] = (int64_t)nleaf * g.cap;
-      const int c = d.cnt[nleaf];
+      // free space: a neighbour beyond the box does not exist (no images)
+      const bool exists = !g.bc || (ux >= 0 && ux < nL && uy >= 0 && uy < nL && uz >= 0 && uz < nL);
+      const int c = exists ? d.cnt[nleaf] : 0;
       nb_cnt[lane] = c;
       u = F32 ? (c + 3) >> 2 : c;
     }
@@ -634,7 +636,16 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
       const int gx = lattice_coord(v.x, ih), gy = lattice_coord(v.y, ih), gz = lattice_coord(v.z, ih);
       for (uint32_t hb = hm; hb; hb &= hb - 1) {
         const int k = __ffs(hb) - 1;
-        const int tx = wrap1(gx + hop_c(k, 0), E), ty = wrap1(gy + hop_c(k, 1), E), tz = wrap1(gz + hop_c(k, 2), E);
+        const int rx = gx + hop_c(k, 0), ry = gy + hop_c(k, 1), rz = gz + hop_c(k, 2);
+        if (g.bc && (rx < 0 || rx >= E || ry < 0 || ry >= E || rz < 0 || rz >= E)) {
+          if (e == 0) {  // free space: a hop out of the box is not a move
+            const int32_t u = d.uid[mb + j];
+            d.mask[(int64_t)nhop * u + k] = 0;
+            out_new[(int64_t)nhop * u + k] = qnan<T>();
+          }
+          continue;
+        }
+        const int tx = wrap1(rx, E), ty = wrap1(ry, E), tz = wrap1(rz, E);
         int ux = tx - gx0, uy = ty - gy0, uz = tz - gz0;
         if (ux < 0 || ux >= W || uy < 0 || uy >= W || uz < 0 || uz >= W) continue;  // another leaf's CTA
         int lt = ux + W * (uy + W * uz);
@@ -842,7 +853,9 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
       if (e == 0) out_old[u] = phis[(gx - gx0) + W * ((gy - gy0) + W * (gz - gz0))];
       for (uint32_t hb = hm; hb; hb &= hb - 1) {
         const int k = __ffs(hb) - 1;
-        const int tx = wrap1(gx + hop_c(k, 0), E), ty = wrap1(gy + hop_c(k, 1), E), tz = wrap1(gz + hop_c(k, 2), E);
+        const int rx = gx + hop_c(k, 0), ry = gy + hop_c(k, 1), rz = gz + hop_c(k, 2);
+        if (g.bc && (rx < 0 || rx >= E || ry < 0 || ry >= E || rz < 0 || rz >= E)) continue;  // phase 2
+        const int tx = wrap1(rx, E), ty = wrap1(ry, E), tz = wrap1(rz, E);
         int ux = tx - gx0, uy = ty - gy0, uz = tz - gz0;
         if (ux < 0 || ux >= W || uy < 0 || uy >= W || uz < 0 || uz >= W) continue;
         int lt = ux + W * (uy + W * uz);
@@ -1006,7 +1019,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize(const Geo g, const Dev
     } else {
       const double q = d.q[i], po = d.phi_old[i];
       const double2* pn = (const double2*)(d.phi_new + NH * i);
-      const double cdip = 4.0 * M_PI / (3.0 * g.a * g.a * g.a);
+      const double cdip = g.dipc;
       double du[NH];
 #pragma unroll
       for (int k2 = 0; k2 < NH / 2; k2++) {
@@ -1402,6 +1415,8 @@ __device__ __forceinline__ void acc_coarse_role(const Geo& g, const MoveRec& mv,
     int nu27 = (nv[0] + 1) + 3 * ((nv[1] + 1) + 3 * (nv[2] + 1));
     in_il = image_in_il(u0, nl, nu27, b);
   }
+  // free space: no images, and the level-2 interaction list is empty
+  if (g.bc && (l == 2 || nv[0] || nv[1] || nv[2])) in_il = false;
   double2* out = scratch + (int64_t)slot * g.P;
   if (!in_il) {
     for (int n = m; n <= g.p; n++) out[tri(n, m)] = make_double2(0.0, 0.0);
@@ -1477,11 +1492,14 @@ __device__ __forceinline__ void acc_fine_role(const Geo& g, const Dev& d, const 
     Pold[c] = cell_at(mv.r[c], np, g.inv_a);
   }
   int b[3];
-  for (int c = 0; c < 3; c++) b[c] = 2 * (((P0[c] + dlt[c]) % np + np) % np) + ((o >> c) & 1);
+  for (int c = 0; c < 3; c++) {
+    if (g.bc && (P0[c] + dlt[c] < 0 || P0[c] + dlt[c] >= np)) return;  // free space: beyond the box
+    b[c] = 2 * (((P0[c] + dlt[c]) % np + np) % np) + ((o >> c) & 1);
+  }
   if (side0 == 1) {  // already covered by the old position's list?
     bool in_old = true;
     for (int c = 0; c < 3; c++)
-      if (wdist(b[c] >> 1, Pold[c], np) > 1) in_old = false;
+      if ((g.bc ? abs((b[c] >> 1) - Pold[c]) : wdist(b[c] >> 1, Pold[c], np)) > 1) in_old = false;
     if (in_old) return;
   }
   double2 acc[KMC_MAXP + 1];
@@ -1498,8 +1516,8 @@ __device__ __forceinline__ void acc_fine_role(const Geo& g, const Dev& d, const 
       const int u = cell_at(x[c], nl, g.inv_a);
       int du = b[c] - u;
       nv[c] = 0;
-      if (2 * du > nl) nv[c] = 1;
-      else if (2 * du < -nl) nv[c] = -1;
+      if (!g.bc && 2 * du > nl) nv[c] = 1;  // periodic: the minimum image (free space: none)
+      else if (!g.bc && 2 * du < -nl) nv[c] = -1;
       const int ui = u + nl * nv[c];
       if (abs(fdiv2(ui) - (b[c] >> 1)) > 1) in = false;
       if (abs(ui - b[c]) >= 2) far = true;
@@ -1590,7 +1608,7 @@ __device__ __forceinline__ void acc_move_role(const Geo& g, const Dev& d, const 
   d.pos[3 * i + 1] = mv.rn[1];
   d.pos[3 * i + 2] = mv.rn[2];
   d.site[i] = mv.site_new;
-  const double cdip = 4.0 * M_PI / (3.0 * g.a * g.a * g.a);
+  const double cdip = g.dipc;
   for (int c3 = 0; c3 < 3; c3++) {
     double m3 = d.dip[c3] + mv.q * (mv.rn[c3] - mv.r[c3]);
     d.dip[c3] = m3;
@@ -1671,6 +1689,7 @@ __global__ void k_eval_points(const Geo g, const Dev d, int64_t m, const double*
   for (int o = 0; o < 27; o++) {
     int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
     int ux = cx + ox, uy = cy + oy, uz = cz + oz;
+    if (g.bc && (ux < 0 || ux >= g.nL || uy < 0 || uy >= g.nL || uz < 0 || uz >= g.nL)) continue;  // free space
     int sx = (ux + g.nL) % g.nL, sy = (uy + g.nL) % g.nL, sz = (uz + g.nL) % g.nL;
     int64_t lf = sx + (int64_t)g.nL * (sy + (int64_t)g.nL * sz);
     T shx = (T)((ux - sx) * g.w), shy = (T)((uy - sy) * g.w), shz = (T)((uz - sz) * g.w);
@@ -1747,11 +1766,15 @@ __global__ void k_assemble_general(const Geo g, const Dev d, int64_t m, const in
   int32_t i = particle[t];
   double q = d.q[i];
   double dx = tgt[3 * t] - d.pos[3 * i], dy = tgt[3 * t + 1] - d.pos[3 * i + 1], dz = tgt[3 * t + 2] - d.pos[3 * i + 2];
-  double V = g.a * g.a * g.a;
   double cself = dU[t];
-  double v = q * (phi_new[t] - phi_old[t]) - 4.0 * M_PI / (3.0 * V) * q * (d.dip[0] * dx + d.dip[1] * dy + d.dip[2] * dz) -
+  double v = q * (phi_new[t] - phi_old[t]) - g.dipc * q * (d.dip[0] * dx + d.dip[1] * dy + d.dip[2] * dz) -
              q * q * cself;
-  double dmx = dx - g.a * rint(dx / g.a), dmy = dy - g.a * rint(dy / g.a), dmz = dz - g.a * rint(dz / g.a);
+  double dmx = dx, dmy = dy, dmz = dz;
+  if (!g.bc) {  // periodic: the minimum image
+    dmx -= g.a * rint(dx / g.a);
+    dmy -= g.a * rint(dy / g.a);
+    dmz -= g.a * rint(dz / g.a);
+  }
   if (dmx == 0.0 && dmy == 0.0 && dmz == 0.0) {
     v = __longlong_as_double(0x7ff8000000000000LL);
     atomicOr(&d.err[0], KMC_DERR_SINGULAR);
@@ -1790,9 +1813,8 @@ __global__ void k_energy(const Geo g, const Dev d) {
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    double V = g.a * g.a * g.a;
     double M2 = d.dip[0] * d.dip[0] + d.dip[1] * d.dip[1] + d.dip[2] * d.dip[2];
-    d.U[0] = 0.5 * sh[0] - 2.0 * M_PI / (3.0 * V) * M2;
+    d.U[0] = 0.5 * sh[0] - 0.5 * g.dipc * M2;
   }
 }
 
@@ -1850,13 +1872,21 @@ __global__ void k_stage_general(const Geo g, const Dev d, int64_t m, const int32
       x = 0.0;
       mout[t] = 0;
     }
-    x -= g.a * floor(x / g.a);
-    if (x >= g.a) x -= g.a;
+    if (g.bc) {  // free space: targets must lie in the box
+      if (!(x >= 0.0 && x < g.a)) {
+        atomicOr(&d.err[0], KMC_DERR_BADPOS);
+        x = 0.0;
+        mout[t] = 0;
+      }
+    } else {
+      x -= g.a * floor(x / g.a);
+      if (x >= g.a) x -= g.a;
+    }
     double o = ok ? d.pos[3 * (int64_t)i + k] : 0.0;
     tout[3 * t + k] = x;
     old[3 * t + k] = o;
     double dd = x - o;
-    dv[3 * t + k] = dd - g.a * rint(dd / g.a);
+    dv[3 * t + k] = g.bc ? dd : dd - g.a * rint(dd / g.a);
   }
 }
 

@@ -214,6 +214,7 @@ void kmc_opts_default(kmc_opts* o) {
   o->leaf_capacity = 0;
   o->m2l = KMC_M2L_TENSOR;
   o->hops = KMC_HOPS_6;
+  o->bc = KMC_BC_PERIODIC;
 }
 
 const char* kmc_last_error(kmc_handle h) { return h ? h->msg : g_static_msg; }
@@ -289,12 +290,15 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   if (!(o.kT > 0.0)) return fail(h, KMC_ERR_ARG, "kT must be positive");
   if (o.m2l != KMC_M2L_TENSOR && o.m2l != KMC_M2L_FP64) return fail(h, KMC_ERR_ARG, "unknown M2L arithmetic");
   if (o.hops != KMC_HOPS_6 && o.hops != KMC_HOPS_14) return fail(h, KMC_ERR_ARG, "unknown hop set");
+  if (o.bc != KMC_BC_PERIODIC && o.bc != KMC_BC_FREE) return fail(h, KMC_ERR_ARG, "unknown boundary conditions");
   int r = init_impl(h, n, positions, charges, box, levels, order);
   if (r) return r;
   Geo& g = h->g;
   g.kT = o.kT;
   g.m2l = o.m2l;
   g.nhop = o.hops == KMC_HOPS_14 ? KMC_MAXHOP : KMC_NHOP;
+  g.bc = o.bc == KMC_BC_FREE ? 1 : 0;
+  g.dipc = g.bc ? 0.0 : 4.0 * M_PI / (3.0 * box * box * box);
   if (o.lattice_edge > 0) {
     int E = o.lattice_edge;
     if (E % g.nL != 0) return fail(h, KMC_ERR_ARG, "lattice edge %d is not a multiple of 2^(levels-1) = %d", E, g.nL);
@@ -330,7 +334,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
     qa += fabs(qh[i]);
     g.qmax = fmax(g.qmax, fabs(qh[i]));
   }
-  if (fabs(qs) > 1e-12 * qa) return fail(h, KMC_ERR_NOT_NEUTRAL, "sum of charges %.3e is not zero", qs);
+  if (!g.bc && fabs(qs) > 1e-12 * qa) return fail(h, KMC_ERR_NOT_NEUTRAL, "sum of charges %.3e is not zero", qs);
   // off-lattice capacity from the initial occupancy
   std::vector<double> ph;
   if (g.E == 0) {
