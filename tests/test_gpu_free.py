@@ -41,17 +41,18 @@ def _oracle_lattice(E, sites, q, nh):
     return dU, mask, tg
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_free_space_lattice_trajectory(precision):
+@pytest.mark.parametrize("precision,nh", [("fp64", 6), ("mixed", 6), ("mixed", 14)])
+def test_free_space_lattice_trajectory(precision, nh):
     """Masks, every dU, the selected event and the accepted dU against the
     oracle at each step of a 20-step trajectory (the oracle's event accepted
-    on both sides), then the energy."""
+    on both sides), then the energy; with the 14-hop set, diagonal hops that
+    leave the box through an edge or a corner are masked too."""
     k = _k()
     w, sites, q = workloads.workload("small")
-    E, kT, nh = w["E"], w["kT"], 6
+    E, kT = w["E"], w["kT"]
     sites = sites.copy()
     h = k.kmc_fmm_init(workloads.site_positions(E, sites), q, float(E), w["L"], 12, precision=precision,
-                       lattice_edge=E, kT=kT, bc="free")
+                       lattice_edge=E, kT=kT, bc="free", hops=nh)
     U0 = oracle.free_energy(workloads.site_positions(E, sites), q)
     assert abs(k.kmc_fmm_energy(h) - U0) < 1e-5 * abs(U0)
     u = workloads.uniforms(20, w["seed"] + 21)
@@ -74,7 +75,7 @@ def test_free_space_lattice_trajectory(precision):
     assert agree >= 18
     U1 = oracle.free_energy(workloads.site_positions(E, sites), q)
     assert abs(k.kmc_fmm_energy(h) - U1) < 1e-5 * abs(U1)
-    print(f"free space ({precision}): worst rel dU error {worst:.2e}, {agree}/20 events agree, "
+    print(f"free space ({precision}, {nh} hops): worst rel dU error {worst:.2e}, {agree}/20 events agree, "
           f"energy rel error {abs(k.kmc_fmm_energy(h) - U1) / abs(U1):.1e}")
 
 
