@@ -346,3 +346,81 @@ def free_delta_u(pos: np.ndarray, q: np.ndarray, particle, target, chunk: int = 
         v[singular] = np.nan
         out[c0:c0 + chunk] = v
     return out
+
+
+# ---------------------------------------------------------------- Dirichlet walls
+# Grounded walls (phi = 0) at z = 0 and z = a/2 with an applied field E_z along
+# z, periodic in x and y (Sec. 2.2, Dirichlet, Fig. dirichlet_bc_domain): the
+# physical charges sit on lattice sites with z index < E/2; each has a mirror
+# of opposite charge at z index E - 1 - z (position a - z); the mirrored cell
+# of edge a is replicated periodically (tinfoil).  Then
+#   U_phys = 1/2 U_ext - E_z sum_i q_i z_i,
+# and a hop moves the charge and its mirror together:
+#   dU_phys = 1/2 [U_ext(after) - U_ext(before)] - q E_z dz.
+# With psi the periodic pair potential, dU_1 = q[phi_{-i}(r') - phi_{-i}(r)]
+# the single-charge change in the mirrored system and m the mirror, the mirror
+# symmetry of the other charges gives
+#   dU_phys = dU_1 - q^2/2 [psi(r' - r'_m) - 2 psi(r' - r_m) + psi(r - r_m)] - q E_z dz.
+# Parity status: pinned by the vanishing potential on both walls and by the
+# brute-force Ewald energies of the mirrored system before and after a move.
+
+def mirror_sites(E: int, sites: np.ndarray) -> np.ndarray:
+    """Site of each charge's mirror image: (x, y, z) -> (x, y, E - 1 - z)."""
+    xyz = np.stack([sites % E, (sites // E) % E, sites // (E * E)], axis=1)
+    return xyz[:, 0] + E * (xyz[:, 1] + E * (E - 1 - xyz[:, 2]))
+
+
+class DirichletLattice:
+    """Lattice KMC state between grounded walls (see above); event j = nh i + k over the
+    physical charges, hops from ``hop_vectors`` (integer lattice offsets, (nh, 3))."""
+
+    def __init__(self, E: int, sites: np.ndarray, q: np.ndarray, hop_vectors: np.ndarray, field_z: float = 0.0,
+                 beta_a: float = DEFAULT_BETA_A):
+        self.E, self.n, self.field_z = int(E), len(q), float(field_z)
+        sites = np.asarray(sites, dtype=np.int64)
+        if np.any(sites // (E * E) >= E // 2):
+            raise ValueError("physical charges must sit below the mirror plane z = a/2")
+        self.hops = np.asarray(hop_vectors, dtype=np.int64)
+        q = np.asarray(q, dtype=np.float64)
+        self.ext = LatticeState(E, np.concatenate([sites, mirror_sites(E, sites)]), np.concatenate([q, -q]), beta_a)
+
+    @property
+    def sites(self) -> np.ndarray:
+        return self.ext.sites[: self.n]
+
+    def _G(self, dxyz: np.ndarray) -> np.ndarray:
+        E = self.E
+        d = np.mod(dxyz, E)
+        return self.ext.G[d[..., 0] + E * (d[..., 1] + E * d[..., 2])]
+
+    def energy(self) -> float:
+        q = self.ext.q[: self.n]
+        z = (self.sites // (self.E * self.E)) + 0.5
+        return 0.5 * self.ext.energy() - self.field_z * float(np.dot(q, z))
+
+    def propose(self):
+        """(dU[n, nh], mask[n, nh]); masked: the target is occupied or beyond a wall."""
+        E, n, nh = self.E, self.n, len(self.hops)
+        s = self.sites
+        xyz = np.stack([s % E, (s // E) % E, s // (E * E)], axis=1)
+        raw = xyz[:, None, :] + self.hops[None, :, :]
+        t = np.mod(raw, E)
+        ts = t[..., 0] + E * (t[..., 1] + E * t[..., 2])
+        inside = (raw[..., 2] >= 0) & (raw[..., 2] < E // 2)
+        mask = inside & (self.ext.occ[ts] == 0)
+        dU = np.full((n, nh), np.nan)
+        ii, kk = np.nonzero(mask)
+        d1 = self.ext.delta_u_list(ii, ts[ii, kk])
+        q = self.ext.q[ii]
+        z, zn = xyz[ii, 2], raw[ii, kk, 2]
+        h = self.hops[kk]
+        zero = np.zeros_like(z)
+        g_new_mir = self._G(np.stack([zero, zero, 2 * zn + 1 - E], axis=1))   # r' - r'_m
+        g_cross = self._G(np.stack([h[:, 0], h[:, 1], z + zn + 1 - E], axis=1))  # r' - r_m
+        g_old_mir = self._G(np.stack([zero, zero, 2 * z + 1 - E], axis=1))    # r - r_m
+        dU[ii, kk] = d1 - 0.5 * q * q * (g_new_mir - 2.0 * g_cross + g_old_mir) - q * self.field_z * (zn - z)
+        return dU, mask.astype(np.uint8)
+
+    def accept(self, i: int, target_site: int) -> None:
+        self.ext.accept_site(i, int(target_site))
+        self.ext.accept_site(i + self.n, int(mirror_sites(self.E, np.array([target_site]))[0]))

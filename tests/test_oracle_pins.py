@@ -450,3 +450,60 @@ def test_free_singular_targets():
     q = np.array([1.0, -1.0])
     out = oracle.free_delta_u(pos, q, [0, 0], [[1.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
     assert np.isnan(out).all()
+
+
+# ---------------------------------------------------------------- Dirichlet walls
+def _dirichlet_system(E, n, seed):
+    rng = np.random.default_rng(seed)
+    half = np.arange(E ** 3)[np.arange(E ** 3) // (E * E) < E // 2]
+    sites = rng.choice(half, n, replace=False)
+    q = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    return sites, q
+
+
+def test_dirichlet_potential_vanishes_on_both_walls():
+    """The mirrored cell's potential is zero on z = 0 and on z = a/2 (grounded walls)."""
+    E = 6
+    sites, q = _dirichlet_system(E, 8, 31)
+    st = oracle.DirichletLattice(E, sites, q, workloads.hop_vectors(6))
+    pos = workloads.site_positions(E, st.ext.sites)
+    a = float(E)
+    rng = np.random.default_rng(5)
+    for zw in (0.0, a / 2):
+        for _ in range(3):
+            x = np.array([rng.random() * a, rng.random() * a, zw])
+            phi = sum(st.ext.q[j] * oracle.psi(a, x - pos[j]) for j in range(len(st.ext.q)))
+            assert abs(phi) < 1e-12
+
+
+def test_dirichlet_hop_energy_equals_brute_force():
+    """dU of every allowed hop equals half the brute-force Ewald energy change of
+    the mirrored cell when the charge and its mirror move, plus the field term."""
+    E, fz = 6, 0.3
+    sites, q = _dirichlet_system(E, 10, 32)
+    st = oracle.DirichletLattice(E, sites, q, workloads.hop_vectors(14), field_z=fz)
+    dU, mask = st.propose()
+    a = float(E)
+    pos0 = workloads.site_positions(E, st.ext.sites)
+    U0 = oracle.energy(pos0, st.ext.q, a)
+    assert abs(st.energy() - (0.5 * U0 - fz * np.dot(q, pos0[:10, 2]))) < 1e-12
+    checked = 0
+    for i in (0, 3, 7):
+        for k in range(14):
+            if not mask[i, k]:
+                continue
+            t = workloads.hop_targets(E, st.sites[i:i + 1], 14)[0, k]
+            s2 = st.ext.sites.copy()
+            s2[i] = t
+            s2[i + 10] = oracle.mirror_sites(E, np.array([t]))[0]
+            U1 = oracle.energy(workloads.site_positions(E, s2), st.ext.q, a)
+            dz = (t // (E * E)) - (st.sites[i] // (E * E))
+            assert abs(dU[i, k] - (0.5 * (U1 - U0) - q[i] * fz * dz)) < 1e-11, (i, k)
+            checked += 1
+    assert checked >= 10
+    # hops through a wall are masked
+    zs = st.sites // (E * E)
+    for i in range(10):
+        for k, hv in enumerate(workloads.hop_vectors(14)):
+            if zs[i] + hv[2] < 0 or zs[i] + hv[2] >= E // 2:
+                assert not mask[i, k]
