@@ -68,9 +68,19 @@ enum kmc_mem { KMC_MEM_HOST = 0, KMC_MEM_DEVICE = 1 };
 enum kmc_bc {
   KMC_BC_PERIODIC = 0, /* the box replicated periodically, conducting boundary at infinity; the
                           system must be neutral */
-  KMC_BC_FREE = 1      /* free space: the charges of the box alone, no images (Eq. (proposed_energy)
+  KMC_BC_FREE = 1,     /* free space: the charges of the box alone, no images (Eq. (proposed_energy)
                           as written); any net charge; lattice hops leaving the box are masked and
                           general targets outside [0, box) are rejected */
+  KMC_BC_DIRICHLET_Z = 2 /* grounded walls (phi = 0) at z = 0 and z = box/2 with an applied field
+                          field_z along z, periodic in x and y (the Dirichlet case of Sec. 2.2):
+                          lattice mode only, even lattice edge, every charge below z = box/2.  The
+                          library appends a mirror of opposite charge at (x, y, box - z) for every
+                          charge and runs the periodic method on the mirrored cell; a hop moves a
+                          charge and its mirror together, hops through a wall are masked,
+                          U = U_mirrored / 2 - field_z sum q z and dU = U(after) - U(before).  The
+                          outputs cover the caller's n charges only; general proposals and moves
+                          (kmc_fmm_propose, kmc_fmm_accept) and caller rates in kmc_step return
+                          KMC_ERR_STATE. */
 };
 
 /* Lattice hop set (the moves Algorithm 5 proposes for every charge). */
@@ -103,12 +113,13 @@ typedef struct kmc_opts {
   int m2l;            /* kmc_m2l: arithmetic of the M2L at init and recompute */
   int hops;           /* kmc_hops: lattice hop set (nh = 6 or 14 hops per charge) */
   int bc;             /* kmc_bc: boundary conditions */
+  double field_z;     /* applied electric field along z with Dirichlet walls (energy -q field_z z) */
 } kmc_opts;
 
 typedef struct kmc_fmm* kmc_handle;
 
 /* Fill opts with defaults: FP64, off-lattice, h = 1, kT = 1, NULL stream, host memory, device 0,
- * tensor-core M2L, 6 hops, periodic. */
+ * tensor-core M2L, 6 hops, periodic, no applied field. */
 void kmc_opts_default(kmc_opts* opts);
 
 /*

@@ -39,6 +39,7 @@ KMC_HOPS_6 = 0
 KMC_HOPS_14 = 1
 KMC_BC_PERIODIC = 0
 KMC_BC_FREE = 1
+KMC_BC_DIRICHLET_Z = 2
 
 EXPORTS = [
     "kmc_opts_default", "kmc_fmm_init", "kmc_fmm_energy", "kmc_fmm_propose", "kmc_fmm_propose_lattice",
@@ -68,6 +69,7 @@ class kmc_opts(ctypes.Structure):
         ("m2l", ctypes.c_int),
         ("hops", ctypes.c_int),
         ("bc", ctypes.c_int),
+        ("field_z", ctypes.c_double),
     ]
 
 
@@ -177,11 +179,13 @@ def _out(h: Handle, shape, dtype):
 # ------------------------------------------------------------------ C-ABI calls
 def kmc_fmm_init(positions, charges, box: float, levels: int, order: int, precision: str = "fp64",
                  lattice_edge: int = 0, lattice_h: float = 1.0, kT: float = 1.0, stream=None, device: int = 0,
-                 leaf_capacity: int = 0, m2l: str = "tensor", hops: int = 6, bc: str = "periodic") -> Handle:
+                 leaf_capacity: int = 0, m2l: str = "tensor", hops: int = 6, bc: str = "periodic",
+                 field_z: float = 0.0) -> Handle:
     """Create a handle and run the one-off full FMM.  precision: 'fp64' or 'mixed';
     m2l: 'tensor' (bf16 tensor cores with exact slicing) or 'fp64' (FP64 CUDA cores);
     hops: the lattice hop set, 6 (faces) or 14 (faces and body diagonals);
-    bc: 'periodic' (neutral systems) or 'free' (free space)."""
+    bc: 'periodic' (neutral systems), 'free' (free space) or 'dirichlet' (grounded walls at z = 0 and
+    z = box/2, lattice mode, every charge below box/2, applied field field_z along z)."""
     lib = load_library()
     opts = kmc_opts()
     lib.kmc_opts_default(ctypes.byref(opts))
@@ -193,7 +197,8 @@ def kmc_fmm_init(positions, charges, box: float, levels: int, order: int, precis
     opts.leaf_capacity = int(leaf_capacity)
     opts.m2l = {"tensor": KMC_M2L_TENSOR, "fp64": KMC_M2L_FP64}[m2l]
     opts.hops = {6: KMC_HOPS_6, 14: KMC_HOPS_14}[int(hops)]
-    opts.bc = {"periodic": KMC_BC_PERIODIC, "free": KMC_BC_FREE}[bc]
+    opts.bc = {"periodic": KMC_BC_PERIODIC, "free": KMC_BC_FREE, "dirichlet": KMC_BC_DIRICHLET_Z}[bc]
+    opts.field_z = float(field_z)
     dev = _is_torch(positions) and positions.is_cuda
     opts.mem = KMC_MEM_DEVICE if dev else KMC_MEM_HOST
     if stream is not None:

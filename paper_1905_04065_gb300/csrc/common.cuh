@@ -90,6 +90,9 @@ struct Geo {
   int nhop;               // lattice hops per charge: 6 (faces) or 14 (faces and body diagonals)
   int bc;                 // boundary conditions: 0 periodic (tinfoil), 1 free space
   double dipc;            // 4 pi / (3 V): the dipole (surface) term's factor; 0 in free space
+  int dirichlet;          // 1: grounded walls at z = 0 and z = a/2 by mirror charges (lattice mode)
+  int64_t nphys;          // charges below the mirror plane (the caller's); their mirrors follow
+  double field_z;         // applied field along z (Dirichlet walls)
 };
 
 // cell coordinate of x on a level with n cells per side, floor(x n / a)
@@ -131,6 +134,11 @@ struct Dev {
   double2* Rch;       // child-offset regular harmonics [(L+1) * 8 * P]
   double2* S;         // lattice sums over the far images [P2]
   double* selfc;      // [KMC_MAXHOP] self-pair correction C(d) per hop direction
+  // Dirichlet walls: C(d) of the charge-mirror displacements, FP64 and FP32
+  double* dirA;       // [E/2]  C(0, 0, (2z + 1 - E) h): charge at z-site z and its mirror
+  double* dirB;       // [nhop E/2]  C(hx h, hy h, (2z + hz + 1 - E) h): after hop k, to the old mirror
+  float* dirA32;
+  float* dirB32;
   double* dip;        // [3] dipole moment M
   float* fdip;        // [3] (4 pi / 3V) M in FP32 for the mixed rate assembly
   double* U;          // [1] total energy
@@ -208,6 +216,9 @@ void fmm_itab(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_child_tables(const Geo& g, const Dev& d, cudaStream_t s);
 size_t fmm_m2l_scratch_bytes(const Geo& g);
 void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s);
+void fmm_dirichlet_tables(const Geo& g, const Dev& d, cudaStream_t s);
+void kmc_mirror_move(const Geo& g, const Dev& d, cudaStream_t s);
+void kmc_dirichlet_energy(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_lattice_sums(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_far_field(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_self_and_dipole(const Geo& g, const Dev& d, cudaStream_t s);

@@ -1082,6 +1082,37 @@ __global__ void k_selfcorr(const Geo g, const Dev d) {
   if (d.selfc32) d.selfc32[k] = (float)c;
 }
 
+// Dirichlet walls: the C(d) values the mirror terms of a hop need (d between a
+// charge or its hop target and a mirror; all z-only or hop-shaped, so tabulated
+// per z-site of the physical half)
+__global__ void k_dirichlet_tables(const Geo g, const Dev d) {
+  const int half = g.E / 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= half * (1 + g.nhop)) return;
+  double dx = 0.0, dy = 0.0, dz;
+  if (t < half) {
+    dz = (2.0 * t + 1.0 - g.E) * g.h;
+  } else {
+    const int k = (t - half) / half, z = (t - half) % half;
+    dx = hop_c(k, 0) * g.h;
+    dy = hop_c(k, 1) * g.h;
+    dz = (2.0 * z + hop_c(k, 2) + 1.0 - g.E) * g.h;
+  }
+  const double c = self_corr_dev(g, d.S, dx, dy, dz);
+  if (t < half) {
+    d.dirA[t] = c;
+    if (d.dirA32) d.dirA32[t] = (float)c;
+  } else {
+    d.dirB[t - half] = c;
+    if (d.dirB32) d.dirB32[t - half] = (float)c;
+  }
+}
+
+void fmm_dirichlet_tables(const Geo& g, const Dev& d, cudaStream_t s) {
+  const int nt = (g.E / 2) * (1 + g.nhop);
+  k_dirichlet_tables<<<(nt + 127) / 128, 128, 0, s>>>(g, d);
+}
+
 void fmm_self_and_dipole(const Geo& g, const Dev& d, cudaStream_t s) {
   k_dipole<<<1, 512, 0, s>>>(g, d);
   k_selfcorr<<<1, 32, 0, s>>>(g, d);

@@ -976,6 +976,11 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize(const Geo g, const Dev
     const int cc[3] = {s % E, (s / E) % E, s / (E * E)};
     const uint16_t* mk = (const uint16_t*)(d.mask + NH * i);
     double r6[NH];
+    // Dirichlet walls: the mirrors propose nothing, hops through a wall are
+    // masked, and a hop moves the charge with its mirror:
+    //   dU = dU_1 - q^2/2 [C(r' - r'_m) - 2 C(r' - r_m) + C(r - r_m)] - q E_z dz
+    const bool dirw = g.dirichlet != 0, mirror = dirw && i >= g.nphys;
+    const int half = E >> 1;
     if (MIXED) {
       const float q = d.q32[i], po = d.phi_old32[i], ikT = (float)(1.0 / g.kT);
       const float2* pn = (const float2*)(d.phi_new32 + NH * i);
@@ -1002,8 +1007,17 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize(const Geo g, const Dev
           const float pv = o ? v.y : v.x;
           float duf = __int_as_float(0x7fc00000);
           double r = 0.0;
-          if (o ? (mb >> 8) : (mb & 0xff)) {
+          bool on = o ? (mb >> 8) : (mb & 0xff);
+          const int zn = cc[2] + hop_c(k, 2);
+          if (dirw && (mirror || zn < 0 || zn >= half)) {
+            if (on) d.mask[NH * i + k] = 0;
+            on = false;
+          }
+          if (on) {
             duf = q * (pv - po) - qd - q * q * d.selfc32[k];
+            if (dirw)
+              duf -= 0.5f * q * q * (d.dirA32[zn] - 2.f * d.dirB32[k * half + cc[2]] + d.dirA32[cc[2]]) +
+                     q * (float)(g.field_z * g.h) * (float)hop_c(k, 2);
             const float y = fmaxf(duf, 0.f) * ikT * 1.4426950408889634f;
             const float n = floorf(y);
             const int e = __float_as_int(n + 12582912.0f) - 0x4B400000;  // exact integer value of n
@@ -1039,8 +1053,17 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize(const Geo g, const Dev
             qd += q * (cdip * d.dip[ax]) * dw;
           }
           double dd = __longlong_as_double(0x7ff8000000000000LL), r = 0.0;
-          if (o ? (mb >> 8) : (mb & 0xff)) {
+          bool on = o ? (mb >> 8) : (mb & 0xff);
+          const int zn = cc[2] + hop_c(k, 2);
+          if (dirw && (mirror || zn < 0 || zn >= half)) {
+            if (on) d.mask[NH * i + k] = 0;
+            on = false;
+          }
+          if (on) {
             dd = q * ((o ? v.y : v.x) - po) - qd - q * q * d.selfc[k];
+            if (dirw)
+              dd -= 0.5 * q * q * (d.dirA[zn] - 2.0 * d.dirB[k * half + cc[2]] + d.dirA[cc[2]]) +
+                    q * g.field_z * g.h * hop_c(k, 2);
             r = exp(-fmax(dd, 0.0) / g.kT);
           }
           du[k] = dd;
@@ -1238,6 +1261,44 @@ __global__ void k_move_from_event(const Geo g, const Dev d) {
 }
 
 void kmc_accept_from_event(const Geo& g, const Dev& d, cudaStream_t s) { k_move_from_event<<<1, 1, 0, s>>>(g, d); }
+
+// Dirichlet walls: the accepted hop's mirror move -- charge i + nphys from
+// (x, y, a - z) to (x', y', a - z') with charge -q -- for a second accept
+// update; its energy change is already in the first record (dU = 0 here).
+__device__ __forceinline__ int mirror_site(int s, int E) {
+  const int x = s % E, y = (s / E) % E, z = s / (E * E);
+  return x + E * (y + E * (E - 1 - z));
+}
+__global__ void k_mirror_move(const Geo g, const Dev d) {
+  MoveRec mv = *d.move;
+  if (!mv.valid) return;
+  mv.i += (int32_t)g.nphys;
+  mv.site_old = mirror_site(mv.site_old, g.E);
+  mv.site_new = mirror_site(mv.site_new, g.E);
+  mv.q = -mv.q;
+  mv.r[2] = g.a - mv.r[2];
+  mv.rn[2] = g.a - mv.rn[2];
+  mv.dU = 0.0;
+  *d.move = mv;
+}
+
+void kmc_mirror_move(const Geo& g, const Dev& d, cudaStream_t s) { k_mirror_move<<<1, 1, 0, s>>>(g, d); }
+
+// Dirichlet walls: U = 1/2 U_mirrored - E_z sum_phys q z (fixed-order reduction)
+__global__ void k_dirichlet_energy(const Geo g, const Dev d) {
+  __shared__ double sh[256];
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < g.nphys; i += blockDim.x) a += d.q[i] * d.pos[3 * i + 2];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) d.U[0] = 0.5 * d.U[0] - g.field_z * sh[0];
+}
+
+void kmc_dirichlet_energy(const Geo& g, const Dev& d, cudaStream_t s) { k_dirichlet_energy<<<1, 256, 0, s>>>(g, d); }
 
 // multipoles of the ancestors of the old and new positions, all levels:
 // Mt_l[anc(r)] -= q R(r - c), Mt_l[anc(r')] += q R(r' - c).  thread per
@@ -1913,5 +1974,6 @@ static void kmc_preload() {
   cudaFuncGetAttributes(&fa, k_record);
   cudaFuncGetAttributes(&fa, k_move_from_event);
   cudaFuncGetAttributes(&fa, k_acc_fused);
+  cudaFuncGetAttributes(&fa, k_mirror_move);
   cudaFuncGetAttributes(&fa, k_acc_coarse_reduce);
 }

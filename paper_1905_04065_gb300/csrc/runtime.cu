@@ -178,6 +178,7 @@ static int compute_energy(kmc_fmm* h) {
   int r = compute_phi_old(h);
   if (r) return r;
   kmc_energy_reduce(h->g, h->d, h->stream);
+  if (h->g.dirichlet) kmc_dirichlet_energy(h->g, h->d, h->stream);  // U = U_mirrored / 2 + field term
   CKLAUNCH();
   return KMC_OK;
 }
@@ -215,6 +216,7 @@ void kmc_opts_default(kmc_opts* o) {
   o->m2l = KMC_M2L_TENSOR;
   o->hops = KMC_HOPS_6;
   o->bc = KMC_BC_PERIODIC;
+  o->field_z = 0.0;
 }
 
 const char* kmc_last_error(kmc_handle h) { return h ? h->msg : g_static_msg; }
@@ -290,7 +292,42 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   if (!(o.kT > 0.0)) return fail(h, KMC_ERR_ARG, "kT must be positive");
   if (o.m2l != KMC_M2L_TENSOR && o.m2l != KMC_M2L_FP64) return fail(h, KMC_ERR_ARG, "unknown M2L arithmetic");
   if (o.hops != KMC_HOPS_6 && o.hops != KMC_HOPS_14) return fail(h, KMC_ERR_ARG, "unknown hop set");
-  if (o.bc != KMC_BC_PERIODIC && o.bc != KMC_BC_FREE) return fail(h, KMC_ERR_ARG, "unknown boundary conditions");
+  if (o.bc != KMC_BC_PERIODIC && o.bc != KMC_BC_FREE && o.bc != KMC_BC_DIRICHLET_Z)
+    return fail(h, KMC_ERR_ARG, "unknown boundary conditions");
+  if (!isfinite(o.field_z)) return fail(h, KMC_ERR_ARG, "field_z must be finite");
+  // input arrays: read in the caller's memory kind, except with Dirichlet walls,
+  // where the library appends the mirrors on the host first
+  bool dev_in = h->mem == KMC_MEM_DEVICE;
+  std::vector<double> dir_pos, dir_q;
+  const int64_t nphys = n;
+  if (o.bc == KMC_BC_DIRICHLET_Z) {
+    if (o.lattice_edge <= 0 || o.lattice_edge % 2)
+      return fail(h, KMC_ERR_ARG, "Dirichlet walls need lattice mode with an even lattice edge");
+    if (n > 0x7fffffffLL / (2 * (o.hops == KMC_HOPS_14 ? KMC_MAXHOP : KMC_NHOP)))
+      return fail(h, KMC_ERR_ARG, "too many charges (n = %lld)", (long long)n);
+    dir_pos.resize(6 * n);
+    dir_q.resize(2 * n);
+    if (dev_in) {
+      CK(cudaMemcpy(dir_pos.data(), positions, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(dir_q.data(), charges, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    } else {
+      memcpy(dir_pos.data(), positions, sizeof(double) * 3 * n);
+      memcpy(dir_q.data(), charges, sizeof(double) * n);
+    }
+    for (int64_t i = 0; i < n; i++) {
+      const double z = dir_pos[3 * i + 2];
+      if (!(z >= 0.0 && z < 0.5 * box))
+        return fail(h, KMC_ERR_ARG, "Dirichlet walls: charge %lld lies above the mirror plane z = box/2", (long long)i);
+      dir_pos[3 * (n + i)] = dir_pos[3 * i];
+      dir_pos[3 * (n + i) + 1] = dir_pos[3 * i + 1];
+      dir_pos[3 * (n + i) + 2] = box - z;
+      dir_q[n + i] = -dir_q[i];
+    }
+    n *= 2;
+    positions = dir_pos.data();
+    charges = dir_q.data();
+    dev_in = false;
+  }
   int r = init_impl(h, n, positions, charges, box, levels, order);
   if (r) return r;
   Geo& g = h->g;
@@ -298,6 +335,9 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   g.m2l = o.m2l;
   g.nhop = o.hops == KMC_HOPS_14 ? KMC_MAXHOP : KMC_NHOP;
   g.bc = o.bc == KMC_BC_FREE ? 1 : 0;
+  g.dirichlet = o.bc == KMC_BC_DIRICHLET_Z ? 1 : 0;
+  g.nphys = nphys;
+  g.field_z = g.dirichlet ? o.field_z : 0.0;
   g.dipc = g.bc ? 0.0 : 4.0 * M_PI / (3.0 * box * box * box);
   if (o.lattice_edge > 0) {
     int E = o.lattice_edge;
@@ -322,7 +362,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   if (ce != cudaSuccess) return fail(h, KMC_ERR_CUDA, "cudaSetDevice(%d): %s", h->device, cudaGetErrorString(ce));
   // charges to host for the neutrality check
   std::vector<double> qh(n);
-  if (h->mem == KMC_MEM_DEVICE) {
+  if (dev_in) {
     CK(cudaMemcpy(qh.data(), charges, sizeof(double) * n, cudaMemcpyDeviceToHost));
   } else {
     memcpy(qh.data(), charges, sizeof(double) * n);
@@ -383,6 +423,10 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   ALLOC(d.S, sizeof(double2) * g.P2);
   ALLOC(d.Rch, sizeof(double2) * (size_t)(g.L + 1) * 8 * g.P);
   ALLOC(d.selfc, sizeof(double) * KMC_MAXHOP);
+  if (g.dirichlet) {
+    ALLOC(d.dirA, sizeof(double) * (g.E / 2));
+    ALLOC(d.dirB, sizeof(double) * (g.E / 2) * g.nhop);
+  }
   ALLOC(d.dip, sizeof(double) * 3);
   ALLOC(d.fdip, sizeof(float) * 4);
   ALLOC(d.U, sizeof(double));
@@ -391,6 +435,10 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
     ALLOC(d.selfc32, sizeof(float) * KMC_MAXHOP);
     ALLOC(d.Psi32, sizeof(float2) * g.ncell_total * g.P);
     ALLOC(d.Rch32, sizeof(float2) * (size_t)(g.L + 1) * 8 * g.P);
+    if (g.dirichlet) {
+      ALLOC(d.dirA32, sizeof(float) * (g.E / 2));
+      ALLOC(d.dirB32, sizeof(float) * (g.E / 2) * g.nhop);
+    }
     ALLOC(d.phi_old32, sizeof(float) * n);
     ALLOC(d.phi_new32, sizeof(float) * g.nhop * n);
     ALLOC(d.dU32, sizeof(float) * g.nhop * n);
@@ -420,8 +468,9 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   CK(cudaMemsetAsync(d.uid, 0xff, sizeof(int32_t) * nslot, s));
   CK(cudaMemsetAsync(d.mask, 0, (size_t)g.nhop * n, s));
   CK(cudaMemsetAsync(d.Psi, 0, sizeof(double2) * g.ncell_total * g.P, s));
-  CK(cudaMemcpyAsync(d.q, charges, sizeof(double) * n, in_kind(h), s));
-  CK(cudaMemcpyAsync(d.pos, positions, sizeof(double) * 3 * n, in_kind(h), s));
+  const cudaMemcpyKind ik = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(d.q, charges, sizeof(double) * n, ik, s));
+  CK(cudaMemcpyAsync(d.pos, positions, sizeof(double) * 3 * n, ik, s));
   if (h->prec == 1) {
     std::vector<float> q32(n);
     for (int64_t i = 0; i < n; i++) q32[i] = (float)qh[i];
@@ -459,6 +508,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   fmm_itab(g, d, s);
   fmm_child_tables(g, d, s);
   fmm_lattice_sums(g, d, s);
+  if (g.dirichlet) fmm_dirichlet_tables(g, d, s);
   CKLAUNCH();
   r = full_fmm(h);
   if (r) return r;
@@ -486,7 +536,7 @@ int kmc_fmm_propose_lattice(kmc_handle h, uint8_t* mask, double* dU) {
   kmc_finalize_rates(h->g, h->d, h->prec, h->stream);
   CKLAUNCH();
   h->rates_valid = true;
-  const int64_t m = (int64_t)h->g.nhop * h->g.n;
+  const int64_t m = (int64_t)h->g.nhop * h->g.nphys;  // the caller's charges (not the mirrors)
   if (mask) CK(cudaMemcpyAsync(mask, h->d.mask, m, out_kind(h), h->stream));
   if (dU) {
     if (h->prec == 1) kmc_widen(h->d.dU32, h->d.dU, m, h->stream);
@@ -560,6 +610,8 @@ int kmc_fmm_propose(kmc_handle h, int64_t m, const int32_t* particle, const doub
                     double* dU) {
   int r = guard(h);
   if (r) return r;
+  if (h->g.dirichlet)
+    return fail(h, KMC_ERR_STATE, "general proposals and moves are not available with Dirichlet walls");
   if (m < 0) return fail(h, KMC_ERR_ARG, "negative proposal count");
   if (m == 0) return KMC_OK;
   if (!particle || !target || !dU) return fail(h, KMC_ERR_ARG, "particle, target and dU are required");
@@ -633,6 +685,8 @@ static int accept_general(kmc_fmm* h, int32_t particle, const double* tgt_host, 
 int kmc_fmm_accept(kmc_handle h, int32_t particle, const double target[3], double* dU_accepted) {
   int r = guard(h);
   if (r) return r;
+  if (h->g.dirichlet)
+    return fail(h, KMC_ERR_STATE, "general proposals and moves are not available with Dirichlet walls");
   if (!target) return fail(h, KMC_ERR_ARG, "target is NULL");
   double t[3];
   if (h->mem == KMC_MEM_DEVICE) {
@@ -648,7 +702,42 @@ int kmc_fmm_accept_event(kmc_handle h, int64_t event, double* dU_accepted) {
   if (r) return r;
   const Geo& g = h->g;
   if (g.E <= 0) return fail(h, KMC_ERR_STATE, "kmc_fmm_accept_event needs lattice mode");
-  if (event < 0 || event >= (int64_t)g.nhop * g.n) return fail(h, KMC_ERR_ARG, "event index out of range");
+  if (event < 0 || event >= (int64_t)g.nhop * g.nphys) return fail(h, KMC_ERR_ARG, "event index out of range");
+  if (g.dirichlet) {  // the charge and its mirror move together: the device accept path, twice
+    cudaStream_t s = h->stream;
+    if (!h->rates_valid) {
+      r = refresh_peff(h);
+      if (r) return r;
+      kmc_propose_lattice(g, h->d, h->prec, s);
+      kmc_finalize_rates(g, h->d, h->prec, s);
+      CKLAUNCH();
+      h->rates_valid = true;
+    }
+    uint8_t mk = 0;
+    CK(cudaMemcpyAsync(&mk, h->d.mask + event, 1, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!mk) return fail(h, KMC_ERR_ARG, "event %lld is masked (occupied target or a wall)", (long long)event);
+    double du = 0.0;
+    if (h->prec == 1) {
+      float f = 0.f;
+      CK(cudaMemcpyAsync(&f, h->d.dU32 + event, sizeof(f), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      du = f;
+    } else {
+      CK(cudaMemcpyAsync(&du, h->d.dU + event, sizeof(du), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaMemcpyAsync(h->d.event, &event, sizeof(event), cudaMemcpyHostToDevice, s));
+    kmc_accept_from_event(g, h->d, s);
+    kmc_accept_apply(g, h->d, s);
+    kmc_mirror_move(g, h->d, s);
+    kmc_accept_apply(g, h->d, s);
+    CKLAUNCH();
+    CK(cudaStreamSynchronize(s));
+    h->peff_valid = false;
+    h->rates_valid = false;
+    if (dU_accepted) *dU_accepted = du;
+    return check_flags(h, "accept_event");
+  }
   int32_t i = (int32_t)(event / g.nhop);
   int k = (int)(event % g.nhop);
   double p[3];
@@ -664,6 +753,7 @@ int kmc_step(kmc_handle h, const double* rates, double zeta, double xi, int64_t*
   if (!(zeta > 0.0 && zeta <= 1.0 && xi > 0.0 && xi <= 1.0))
     return fail(h, KMC_ERR_ARG, "zeta and xi must lie in (0, 1]");
   cudaStream_t s = h->stream;
+  if (rates && h->g.dirichlet) return fail(h, KMC_ERR_STATE, "kmc_step with Dirichlet walls takes the device rates");
   if (rates) {
     CK(cudaMemcpyAsync(h->d.rate, rates, sizeof(double) * h->g.nhop * h->g.n, in_kind(h), s));
     kmc_rate_bsum(h->g, h->d, s);
@@ -699,6 +789,10 @@ static void enqueue_step(kmc_fmm* h) {
   kmc_record(g, d, s);
   kmc_accept_from_event(g, d, s);
   kmc_accept_apply(g, d, s);
+  if (g.dirichlet) {  // the mirror moves with the charge
+    kmc_mirror_move(g, d, s);
+    kmc_accept_apply(g, d, s);
+  }
 }
 
 #define KMC_GRAPH_STEPS 8
@@ -802,6 +896,10 @@ int kmc_run_profiled(kmc_handle h, int steps, const double* uniforms, int64_t* e
     CK(cudaEventRecord(e[4], s));
     kmc_accept_from_event(g, d, s);
     kmc_accept_apply(g, d, s);
+    if (g.dirichlet) {
+      kmc_mirror_move(g, d, s);
+      kmc_accept_apply(g, d, s);
+    }
     CK(cudaEventRecord(e[5], s));
   }
   CKLAUNCH();
@@ -873,14 +971,15 @@ int kmc_fmm_leaf_index(kmc_handle h, int32_t* leaf) {
   int r = guard(h);
   if (r) return r;
   if (!leaf) return fail(h, KMC_ERR_ARG, "leaf is NULL");
-  std::vector<int32_t> so(h->g.n);
-  CK(cudaMemcpyAsync(so.data(), h->d.slot_of, sizeof(int32_t) * h->g.n, cudaMemcpyDeviceToHost, h->stream));
+  const int64_t n = h->g.nphys;
+  std::vector<int32_t> so(n);
+  CK(cudaMemcpyAsync(so.data(), h->d.slot_of, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  for (int64_t i = 0; i < h->g.n; i++) so[i] = so[i] / h->g.cap;
+  for (int64_t i = 0; i < n; i++) so[i] = so[i] / h->g.cap;
   if (h->mem == KMC_MEM_DEVICE) {
-    CK(cudaMemcpy(leaf, so.data(), sizeof(int32_t) * h->g.n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(leaf, so.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
   } else {
-    memcpy(leaf, so.data(), sizeof(int32_t) * h->g.n);
+    memcpy(leaf, so.data(), sizeof(int32_t) * n);
   }
   return KMC_OK;
 }
@@ -889,7 +988,7 @@ int kmc_fmm_positions(kmc_handle h, double* positions) {
   int r = guard(h);
   if (r) return r;
   if (!positions) return fail(h, KMC_ERR_ARG, "positions is NULL");
-  CK(cudaMemcpyAsync(positions, h->d.pos, sizeof(double) * 3 * h->g.n, out_kind(h), h->stream));
+  CK(cudaMemcpyAsync(positions, h->d.pos, sizeof(double) * 3 * h->g.nphys, out_kind(h), h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return KMC_OK;
 }
