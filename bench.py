@@ -85,24 +85,40 @@ def step_bytes(E: int, L: int, N: int, p: int) -> int:
     return 6 * N * (8 + 4) + ML * W ** 3 * 16 + ML * P * 8
 
 
-def pair_count(E: int, L: int, sites: np.ndarray, nhop: int = 6) -> dict:
+def pair_count(E: int, L: int, sites: np.ndarray, nhop: int = 6, bc: str = "periodic") -> dict:
     """Evaluation sites and near-field pairs of one propose launch, counted
     from the configuration.  The potential is needed once per distinct site:
     every occupied site (old positions) and every empty site that some charge
     can hop to; per leaf, pairs = needed sites x charges in the 27
-    neighbouring leaves (the pair at distance 0 included in the count)."""
+    neighbouring leaves (the pair at distance 0 included in the count).
+    hops = the unmasked proposals (dU evaluations) of the caller's charges.
+    Free space: no wrapping, hops out of the box masked.  Dirichlet walls: the
+    kernel works on the mirrored cell (the charges and their mirrors); hops
+    through a wall are masked."""
     nL = 2 ** (L - 1)
     W = E // nL
+    phys = np.asarray(sites, dtype=np.int64)
+    if bc == "dirichlet":
+        x, y, z = phys % E, (phys // E) % E, phys // (E * E)
+        sites = np.concatenate([phys, x + E * (y + E * (E - 1 - z))])
     xyz = workloads.site_xyz(E, sites)
     occ = np.zeros(E ** 3, dtype=bool)
     occ[sites] = True
     needed = occ.copy()
     hops = 0
+    nph = len(phys)
     for (dx, dy, dz) in workloads.hop_vectors(nhop).tolist():
-        t = (xyz + np.array([dx, dy, dz])) % E
+        raw = xyz + np.array([dx, dy, dz])
+        t = raw % E
         ts = t[:, 0] + E * (t[:, 1] + E * t[:, 2])
         ok = ~occ[ts]
-        hops += int(ok.sum())
+        if bc == "free":
+            ok &= np.all((raw >= 0) & (raw < E), axis=1)
+        if bc == "dirichlet":
+            wall = (raw[:, 2] < 0) | (raw[:, 2] >= E // 2)
+            hops += int((ok[:nph] & ~wall[:nph]).sum())
+        else:
+            hops += int(ok.sum())
         needed[ts[ok]] = True
     ns = np.nonzero(needed)[0]
     nxyz = workloads.site_xyz(E, ns) // W
@@ -110,10 +126,17 @@ def pair_count(E: int, L: int, sites: np.ndarray, nhop: int = 6) -> dict:
     leafc = xyz // W
     cnt = np.bincount(leafc[:, 0] + nL * (leafc[:, 1] + nL * leafc[:, 2]), minlength=nL ** 3).reshape(nL, nL, nL)
     src = np.zeros_like(cnt)
-    for oz in (-1, 0, 1):
-        for oy in (-1, 0, 1):
-            for ox in (-1, 0, 1):
-                src += np.roll(cnt, shift=(oz, oy, ox), axis=(0, 1, 2))
+    if bc == "free":  # no neighbour leaves beyond the box
+        pad = np.pad(cnt, 1)
+        for oz in (0, 1, 2):
+            for oy in (0, 1, 2):
+                for ox in (0, 1, 2):
+                    src += pad[oz:oz + nL, oy:oy + nL, ox:ox + nL]
+    else:
+        for oz in (-1, 0, 1):
+            for oy in (-1, 0, 1):
+                for ox in (-1, 0, 1):
+                    src += np.roll(cnt, shift=(oz, oy, ox), axis=(0, 1, 2))
     pairs = int(np.sum(pts * src.reshape(-1)))
     return dict(points=int(pts.sum()), pairs=pairs, hops=hops, leaves=nL ** 3)
 
@@ -312,14 +335,17 @@ def run_gpu(args):
     # replicas: every rank runs an independent replica with its own seed
     if world > 1 and rank > 0:
         sites, q = workloads.uniform_lattice(E, w["N"], w["seed"] + 7919 * rank)
+    if args.bc == "dirichlet":  # the caller's charges below z = E/2; the library adds the mirrors
+        sites, q = workloads.lower_half_lattice(E, w["N"], w["seed"] + 7919 * rank)
     pos = workloads.site_positions(E, sites)
     stream = torch.cuda.current_stream(dev)
     t0 = time.perf_counter()
+    fz = 0.1 if args.bc == "dirichlet" else 0.0
     h = k.kmc_fmm_init(pos, q, float(E), L, p, precision="mixed", lattice_edge=E, kT=kT, stream=stream, device=dev,
-                       hops=nhop, bc=args.bc)
+                       hops=nhop, bc=args.bc, field_z=fz)
     torch.cuda.synchronize()
     init_s = time.perf_counter() - t0
-    work = pair_count(E, L, sites, nhop)
+    work = pair_count(E, L, sites, nhop, args.bc)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
     u = workloads.uniforms(args.warmup + args.steps + args.e2e_steps + 16, w["seed"])
 
@@ -391,7 +417,7 @@ def run_gpu(args):
         del h
         torch.cuda.synchronize()
         h64 = k.kmc_fmm_init(pos, q, float(E), L, p, precision="fp64", lattice_edge=E, kT=kT, stream=stream, hops=nhop,
-                             bc=args.bc,
+                             bc=args.bc, field_z=fz,
                              device=dev)
         k.kmc_run_profiled(h64, u[:1])
         ms64 = []
@@ -539,7 +565,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--bc", default="periodic", choices=["periodic", "free"],
+    ap.add_argument("--bc", default="periodic", choices=["periodic", "free", "dirichlet"],
                     help="boundary conditions of the lattice workloads (the configs are periodic)")
     ap.add_argument("--workload", default="large", choices=["small", "medium", "large", "blobs", "tile", "sec53", "batch"])
     ap.add_argument("--replicas", type=int, default=None)

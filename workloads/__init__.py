@@ -41,6 +41,14 @@ HOPS = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
         (1, 1, 1), (-1, 1, 1), (1, -1, 1), (-1, -1, 1), (1, 1, -1), (-1, 1, -1), (1, -1, -1), (-1, -1, -1)]
 
 
+def lower_half_lattice(E: int, N: int, seed: int):
+    """N distinct sites below the plane z = E/2 (grounded-wall systems: the library adds the
+    mirror images above it) and N/2 charges of each sign, seeded."""
+    rng = np.random.default_rng(seed)
+    sites = rng.choice((E ** 3) // 2, N, replace=False).astype(np.int64)  # z < E/2 <=> s < E^3/2
+    return sites, neutral_charges(rng, N)
+
+
 def hop_vectors(nhop: int = 6) -> np.ndarray:
     """The first nhop hop vectors (6: faces; 14: faces and body diagonals), int64 (nhop, 3)."""
     assert nhop in (6, 14)
