@@ -241,6 +241,32 @@ def kmc_fmm_propose(h: Handle, particle, target, mask=None):
     return out
 
 
+def flatten_proposals(P):
+    """The paper's proposal list (Sec. 4.2, "Proposing moves"): a sequence of tuples
+    (i, R_i), R_i an n_i x 3 array of new positions for charge i, flattened into the
+    (particle[m], target[m x 3]) form of kmc_fmm_propose, plus the split offsets."""
+    idx, tgt, counts = [], [], []
+    for i, R in P:
+        R = np.asarray(R, dtype=np.float64).reshape(-1, 3)
+        idx.append(np.full(R.shape[0], int(i), dtype=np.int32))
+        tgt.append(R)
+        counts.append(R.shape[0])
+    if not counts:
+        return np.zeros(0, np.int32), np.zeros((0, 3)), np.zeros(1, np.int64)
+    off = np.concatenate(([0], np.cumsum(counts))).astype(np.int64)
+    return np.concatenate(idx), np.ascontiguousarray(np.concatenate(tgt)), off
+
+
+def kmc_fmm_propose_tuples(h: Handle, P):
+    """dU for the paper's proposal list P = ((i1, R_i1), (i2, R_i2), ...): returns a tuple
+    (U_i1, U_i2, ...) of host arrays, U_i[k] the energy change of moving charge i to R_i[k]."""
+    particle, target, off = flatten_proposals(P)
+    dU = kmc_fmm_propose(h, particle, target)
+    if _is_torch(dU):
+        dU = dU.cpu().numpy()
+    return tuple(dU[off[k]:off[k + 1]] for k in range(len(off) - 1))
+
+
 def _given(h: Handle, x, shape, dtype):
     """A caller-provided output buffer (numpy array or torch tensor) in the
     handle's memory kind: checked for shape, dtype and contiguity."""

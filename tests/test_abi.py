@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -47,3 +48,16 @@ def test_null_handle_is_rejected():
     U = ctypes.c_double()
     assert lib.kmc_fmm_energy(None, ctypes.byref(U)) == k.KMC_ERR_ARG
     lib.kmc_fmm_destroy(None)
+
+
+def test_proposal_tuples_flatten_in_order():
+    """The tuple-list form of the proposals (Sec. 4.2) flattens charge by charge, targets in
+    their given order, with offsets that split the energy changes back per charge."""
+    import paper_1905_04065_gb300 as k
+    P = ((3, [[0.11, 0.13, 0.09], [0.90, 0.10, 0.08]]), (7, [[0.45, 0.28, 0.89]]), (3, np.zeros((0, 3))))
+    part, tgt, off = k.flatten_proposals(P)
+    assert part.dtype == np.int32 and part.tolist() == [3, 3, 7]
+    assert tgt.shape == (3, 3) and tgt[1].tolist() == [0.90, 0.10, 0.08] and tgt[2].tolist() == [0.45, 0.28, 0.89]
+    assert off.tolist() == [0, 2, 3, 3]
+    part, tgt, off = k.flatten_proposals(())
+    assert part.shape == (0,) and tgt.shape == (0, 3) and off.tolist() == [0]

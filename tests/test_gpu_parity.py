@@ -175,6 +175,39 @@ def test_general_propose_matches_oracle(small):
     assert err < 1e-4, err
 
 
+def test_proposal_tuples_match_oracle(small):
+    """The paper's proposal list ((i, R_i), ...) with 1-4 targets per charge (Sec. 4.2): one
+    array of energy changes per tuple, each entry against the oracle."""
+    k = _k()
+    w, sites, q, st = small
+    E = w["E"]
+    h = _init(E, sites, q, w["L"], 12)
+    rng = np.random.default_rng(17)
+    occ = set(sites.tolist())
+    P, ref_parts, ref_sites = [], [], []
+    for i in rng.choice(len(q), size=60, replace=False):
+        ts = set()
+        for _ in range(int(rng.integers(1, 5))):
+            d = rng.integers(-2, 3, size=3)
+            t = (workloads.site_xyz(E, [sites[i]])[0] + d) % E
+            s = int(t[0] + E * (t[1] + E * t[2]))
+            if d.any() and s not in occ:
+                ts.add(s)
+        ts = sorted(ts)
+        if not ts:
+            continue
+        P.append((int(i), workloads.site_positions(E, ts)))
+        ref_parts += [int(i)] * len(ts)
+        ref_sites += ts
+    U = k.kmc_fmm_propose_tuples(h, P)
+    assert isinstance(U, tuple) and len(U) == len(P)
+    assert [len(u) for u in U] == [len(R) for _, R in P]
+    ref = st.delta_u_list(ref_parts, ref_sites)
+    got = np.concatenate(U)
+    err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    assert err < 1e-4, err
+
+
 def test_singular_general_proposal_rejected(small):
     k = _k()
     w, sites, q, st = small
