@@ -623,7 +623,10 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
 
   // (2) hop targets inside this leaf: the leaf's own hops and the hops that
   // enter it from the neighbours of its entry list
-#pragma unroll
+  // not unrolled: with the 14-hop set (27 entries, seven per warp) unrolled
+  // copies of this loop and of the write-out's made the launch twice as slow
+  // (larger code, more register spills)
+#pragma unroll 1
   for (int i = 0; i < (ne + 3) / 4; i++) {
     const int e = warp + 4 * i;
     if (e >= ne) break;
@@ -837,7 +840,7 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
   }
   __syncthreads();
   // (5) write-out: old-position potentials and unmasked hop potentials
-#pragma unroll
+#pragma unroll 1
   for (int i = 0; i < (ne + 3) / 4; i++) {
     const int e = warp + 4 * i;
     if (e >= ne) break;
