@@ -114,12 +114,19 @@ typedef struct kmc_opts {
   int hops;           /* kmc_hops: lattice hop set (nh = 6 or 14 hops per charge) */
   int bc;             /* kmc_bc: boundary conditions */
   double field_z;     /* applied electric field along z with Dirichlet walls (energy -q field_z z) */
+  int near_cache;     /* lattice mode: 1 = keep the near-field sum (the direct part of phi, Sec. 3,
+                         Eq. (proposed_energy_sr): charges in the 27 leaves around the site's leaf) of
+                         every site in device memory, 8 bytes per site, filled at init and recompute
+                         and updated by every accepted move for the sites whose neighbourhood holds
+                         the old or the new position; proposals then read it instead of summing the
+                         pairs.  The values agree with the per-step sum to rounding (fixed point,
+                         2^-k with 2^k |sum| < 2^62).  0 = sum every step (default). */
 } kmc_opts;
 
 typedef struct kmc_fmm* kmc_handle;
 
 /* Fill opts with defaults: FP64, off-lattice, h = 1, kT = 1, NULL stream, host memory, device 0,
- * tensor-core M2L, 6 hops, periodic, no applied field. */
+ * tensor-core M2L, 6 hops, periodic, no applied field, near field summed every step. */
 void kmc_opts_default(kmc_opts* opts);
 
 /*

@@ -70,6 +70,7 @@ class kmc_opts(ctypes.Structure):
         ("hops", ctypes.c_int),
         ("bc", ctypes.c_int),
         ("field_z", ctypes.c_double),
+        ("near_cache", ctypes.c_int),
     ]
 
 
@@ -180,12 +181,14 @@ def _out(h: Handle, shape, dtype):
 def kmc_fmm_init(positions, charges, box: float, levels: int, order: int, precision: str = "fp64",
                  lattice_edge: int = 0, lattice_h: float = 1.0, kT: float = 1.0, stream=None, device: int = 0,
                  leaf_capacity: int = 0, m2l: str = "tensor", hops: int = 6, bc: str = "periodic",
-                 field_z: float = 0.0) -> Handle:
+                 field_z: float = 0.0, near_cache: bool = False) -> Handle:
     """Create a handle and run the one-off full FMM.  precision: 'fp64' or 'mixed';
     m2l: 'tensor' (bf16 tensor cores with exact slicing) or 'fp64' (FP64 CUDA cores);
     hops: the lattice hop set, 6 (faces) or 14 (faces and body diagonals);
     bc: 'periodic' (neutral systems), 'free' (free space) or 'dirichlet' (grounded walls at z = 0 and
-    z = box/2, lattice mode, every charge below box/2, applied field field_z along z)."""
+    z = box/2, lattice mode, every charge below box/2, applied field field_z along z);
+    near_cache: lattice mode, keep every site's near-field sum on the device and update it per
+    accepted move instead of summing the pairs every step."""
     lib = load_library()
     opts = kmc_opts()
     lib.kmc_opts_default(ctypes.byref(opts))
@@ -199,6 +202,7 @@ def kmc_fmm_init(positions, charges, box: float, levels: int, order: int, precis
     opts.hops = {6: KMC_HOPS_6, 14: KMC_HOPS_14}[int(hops)]
     opts.bc = {"periodic": KMC_BC_PERIODIC, "free": KMC_BC_FREE, "dirichlet": KMC_BC_DIRICHLET_Z}[bc]
     opts.field_z = float(field_z)
+    opts.near_cache = 1 if near_cache else 0
     dev = _is_torch(positions) and positions.is_cuda
     opts.mem = KMC_MEM_DEVICE if dev else KMC_MEM_HOST
     if stream is not None:

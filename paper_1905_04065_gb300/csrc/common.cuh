@@ -93,6 +93,8 @@ struct Geo {
   int dirichlet;          // 1: grounded walls at z = 0 and z = a/2 by mirror charges (lattice mode)
   int64_t nphys;          // charges below the mirror plane (the caller's); their mirrors follow
   double field_z;         // applied field along z (Dirichlet walls)
+  int near_cache;         // 1: near-field sums of every site kept in d.nearfx (lattice mode)
+  int near_ks;            // their fixed-point exponent: value = nearfx * 2^-near_ks
 };
 
 // cell coordinate of x on a level with n cells per side, floor(x n / a)
@@ -139,6 +141,8 @@ struct Dev {
   double* dirB;       // [nhop E/2]  C(hx h, hy h, (2z + hz + 1 - E) h): after hop k, to the old mirror
   float* dirA32;
   float* dirB32;
+  long long* nearfx;  // [ML * cap] near-field sum at every site of every leaf (local site index
+                      // x + W (y + W z)), fixed point; FP32 form in lattice units, FP64 physical
   double* dip;        // [3] dipole moment M
   float* fdip;        // [3] (4 pi / 3V) M in FP32 for the mixed rate assembly
   double* U;          // [1] total energy
@@ -218,6 +222,7 @@ size_t fmm_m2l_scratch_bytes(const Geo& g);
 void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s);
 void fmm_dirichlet_tables(const Geo& g, const Dev& d, cudaStream_t s);
 void kmc_mirror_move(const Geo& g, const Dev& d, cudaStream_t s);
+void kmc_near_fill(const Geo& g, const Dev& d, int prec, cudaStream_t s);
 void kmc_dirichlet_energy(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_lattice_sums(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_far_field(const Geo& g, const Dev& d, cudaStream_t s);

@@ -490,7 +490,11 @@ __device__ __forceinline__ void fixed_add(long long* a, double v) {
 // coordinates come from the slot positions (coalesced), user indices only
 // where an output is written.  Potentials are written in precision T (FP32
 // arrays in the mixed form, FP64 arrays in the FP64 form).
-template <typename T, int NH>
+// mode: PROP_SUM (the pair sums of this step), PROP_FILL (pair sums at every
+// site of the leaf into the near-field cache d.nearfx; no hops, no L2P, no
+// outputs) or PROP_CACHED (the near-field sums read from the cache, no pairs).
+enum { PROP_SUM = 0, PROP_FILL = 1, PROP_CACHED = 2 };
+template <typename T, int NH, int mode>
 __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g, const Dev d, int chunk) {
   typedef typename cplx<T>::type C;
   typedef typename vec4<T>::type V4;
@@ -583,7 +587,7 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
       misc[1] = 0;
     }
     __syncwarp();
-    if (F32) {  // first pass: one bulk copy per leaf (one lane each), overlapped with phases 1-3
+    if (F32 && mode != PROP_CACHED) {  // first pass: one bulk copy per leaf (one lane each), overlapped with phases 1-3
       const int q1 = pq[1];
       if (lane == 0) mbar_expect_tx(bar, (uint32_t)(nb_off[q1] * 80));
       __syncwarp();
@@ -627,7 +631,7 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
   // copies of this loop and of the write-out's made the launch twice as slow
   // (larger code, more register spills)
 #pragma unroll 1
-  for (int i = 0; i < (ne + 3) / 4; i++) {
+  for (int i = 0; i < (mode == PROP_FILL ? 0 : (ne + 3) / 4); i++) {
     const int e = warp + 4 * i;
     if (e >= ne) break;
     const int li = c_ent_leaf[hs][e];
@@ -662,6 +666,8 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
       }
     }
   }
+  if (mode == PROP_FILL)  // every site of the leaf
+    for (int c = tid; c < nbw; c += blockDim.x) need[c] = 32 * c + 32 <= W3 ? 0xffffffffu : (1u << (W3 - 32 * c)) - 1u;
   __syncthreads();
   // (3) compact the needed sites (ascending local index); word offsets by a
   // warp scan
@@ -714,7 +720,8 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
     const int sv = sites[b];
     acc[(sv & 15) + W * (((sv >> 4) & 15) + W * (sv >> 8))] = 0;
   }
-  const int npass = nsites ? misc[0] : 1;  // no sites: only the prefetch to drain
+  // no sites: only the prefetch to drain; cached sums: no pairs (and no prefetch)
+  const int npass = mode == PROP_CACHED ? 0 : (nsites ? misc[0] : 1);
   int ks;
   {
     const double bound = g.qmax * (double)max(nb_off[27] * (F32 ? 4 : 1), 1) * (F32 ? 1.0 : (double)ih);
@@ -808,6 +815,18 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
       }
     }
   }
+  if (mode == PROP_FILL) {  // the sums at every site into the cache, rescaled to 2^-near_ks
+    __syncthreads();
+    const int sh = g.near_ks - ks;
+    long long* dst = d.nearfx + leaf * (int64_t)g.cap;
+    for (int b = tid; b < nsites; b += blockDim.x) {
+      const int sv = sites[b];
+      const int l = (sv & 15) + W * (((sv >> 4) & 15) + W * (sv >> 8));
+      const long long a = (long long)acc[l];
+      dst[l] = sh >= 0 ? a * (1LL << sh) : (a + (1LL << (-sh - 1))) >> -sh;
+    }
+    return;
+  }
   // the write-out's inputs (first 32 charges of this warp's first two
   // entries) are loaded now, so that their latency passes during the L2P
   V4 wv[2];
@@ -829,11 +848,13 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
   {
     const T hw = (T)(0.5 * W);
     const T back = (T)ldexp(1.0, -ks) * (F32 ? ih : (T)1);
+    const T cback = (T)ldexp(1.0, -g.near_ks) * (F32 ? ih : (T)1);
+    const long long* cache = mode == PROP_CACHED ? d.nearfx + leaf * (int64_t)g.cap : nullptr;
     for (int b = tid; b < nsites; b += blockDim.x) {
       const int sv = sites[b];
       const int ix = sv & 15, iy = (sv >> 4) & 15, iz = sv >> 8;
       const int l = ix + W * (iy + W * iz);
-      const T near = (T)acc[l] * back;
+      const T near = cache ? (T)cache[l] * cback : (T)acc[l] * back;
       phis[l] = near + l2p_point<T, C>(Lc, g.p, (small_to<T>(ix) + (T)0.5 - hw) * h,
                                         (small_to<T>(iy) + (T)0.5 - hw) * h, (small_to<T>(iz) + (T)0.5 - hw) * h);
     }
@@ -890,31 +911,56 @@ static int propose_chunk(const Geo& g) {
 
 static void kmc_preload();
 
+template <int MODE>
+static void prepare_m(const Geo& g, int prec, size_t sm) {
+  if (g.nhop == KMC_MAXHOP) {
+    if (prec == 0) raise_dynamic_smem((const void*)k_propose_lattice<double, KMC_MAXHOP, MODE>, sm);
+    else raise_dynamic_smem((const void*)k_propose_lattice<float, KMC_MAXHOP, MODE>, sm);
+  } else {
+    if (prec == 0) raise_dynamic_smem((const void*)k_propose_lattice<double, KMC_NHOP, MODE>, sm);
+    else raise_dynamic_smem((const void*)k_propose_lattice<float, KMC_NHOP, MODE>, sm);
+  }
+}
+
 void kmc_prepare(const Geo& g, int prec) {
   kmc_preload();
   if (g.E <= 0) return;
   const int chunk = propose_chunk(g);
   const size_t sm = propose_smem(g, prec, chunk);
-  if (g.nhop == KMC_MAXHOP) {
-    if (prec == 0) raise_dynamic_smem((const void*)k_propose_lattice<double, KMC_MAXHOP>, sm);
-    else raise_dynamic_smem((const void*)k_propose_lattice<float, KMC_MAXHOP>, sm);
-  } else {
-    if (prec == 0) raise_dynamic_smem((const void*)k_propose_lattice<double, KMC_NHOP>, sm);
-    else raise_dynamic_smem((const void*)k_propose_lattice<float, KMC_NHOP>, sm);
+  prepare_m<PROP_SUM>(g, prec, sm);
+  if (g.near_cache) {
+    prepare_m<PROP_FILL>(g, prec, sm);
+    prepare_m<PROP_CACHED>(g, prec, sm);
   }
 }
 
-void kmc_propose_lattice(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
+template <int MODE>
+static void propose_launch_m(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
   const int chunk = propose_chunk(g);
   const size_t sm = propose_smem(g, prec, chunk);
   const unsigned nb = (unsigned)g.ML;
   if (g.nhop == KMC_MAXHOP) {
-    if (prec == 0) k_propose_lattice<double, KMC_MAXHOP><<<nb, PROP_THREADS, sm, s>>>(g, d, chunk);
-    else k_propose_lattice<float, KMC_MAXHOP><<<nb, PROP_THREADS, sm, s>>>(g, d, chunk);
+    if (prec == 0) k_propose_lattice<double, KMC_MAXHOP, MODE><<<nb, PROP_THREADS, sm, s>>>(g, d, chunk);
+    else k_propose_lattice<float, KMC_MAXHOP, MODE><<<nb, PROP_THREADS, sm, s>>>(g, d, chunk);
   } else {
-    if (prec == 0) k_propose_lattice<double, KMC_NHOP><<<nb, PROP_THREADS, sm, s>>>(g, d, chunk);
-    else k_propose_lattice<float, KMC_NHOP><<<nb, PROP_THREADS, sm, s>>>(g, d, chunk);
+    if (prec == 0) k_propose_lattice<double, KMC_NHOP, MODE><<<nb, PROP_THREADS, sm, s>>>(g, d, chunk);
+    else k_propose_lattice<float, KMC_NHOP, MODE><<<nb, PROP_THREADS, sm, s>>>(g, d, chunk);
   }
+}
+
+static void propose_launch(const Geo& g, const Dev& d, int prec, int mode, cudaStream_t s) {
+  if (mode == PROP_CACHED) propose_launch_m<PROP_CACHED>(g, d, prec, s);
+  else if (mode == PROP_FILL) propose_launch_m<PROP_FILL>(g, d, prec, s);
+  else propose_launch_m<PROP_SUM>(g, d, prec, s);
+}
+
+void kmc_propose_lattice(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
+  propose_launch(g, d, prec, g.near_cache ? PROP_CACHED : PROP_SUM, s);
+}
+
+// near-field cache: the pair sums at every site of every leaf
+void kmc_near_fill(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
+  if (g.near_cache) propose_launch(g, d, prec, PROP_FILL, s);
 }
 
 // ------------------------------------------------------------------ dU, rates, block sums
@@ -1718,6 +1764,43 @@ __global__ void __launch_bounds__(ACC_THREADS) k_acc_fused(const Geo g, const De
   if (threadIdx.x == 0) acc_move_role(g, d, mv);
 }
 
+// Near-field cache update for an accepted move of charge q from site r to site
+// r'.  Block (side, o): the leaf T = S - o around the source leaf S of r (side
+// 0, -q) or r' (side 1, +q); in T's frame the source sits at its position in
+// S plus o W sites, as in T's propose CTA, so every site t of T gets
+// +-q / |t - r_T| (lattice units in the FP32 form, physical in FP64), except
+// the pair at distance 0.  Free space: leaves beyond the box do not exist.
+__global__ void __launch_bounds__(128) k_near_update(const Geo g, const Dev d) {
+  const MoveRec mv = *d.move;
+  if (!mv.valid || mv.site_old < 0 || mv.site_new < 0) return;
+  const int side = blockIdx.x / 27, o = blockIdx.x % 27;
+  const int site = side ? mv.site_new : mv.site_old;
+  const int E = g.E, W = g.W, nL = g.nL;
+  const int sx = site % E, sy = (site / E) % E, sz = site / (E * E);
+  const int Sx = sx / W, Sy = sy / W, Sz = sz / W;
+  const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+  int Tx = Sx - ox, Ty = Sy - oy, Tz = Sz - oz;
+  if (g.bc) {
+    if (Tx < 0 || Tx >= nL || Ty < 0 || Ty >= nL || Tz < 0 || Tz >= nL) return;
+  } else {
+    Tx = (Tx + nL) % nL;
+    Ty = (Ty + nL) % nL;
+    Tz = (Tz + nL) % nL;
+  }
+  const double rx = (double)(sx - Sx * W + ox * W), ry = (double)(sy - Sy * W + oy * W),
+               rz = (double)(sz - Sz * W + oz * W);
+  const double f = (side ? mv.q : -mv.q) * ldexp(1.0, g.near_ks) * (g.prec == 1 ? 1.0 : 1.0 / g.h);
+  long long* dst = d.nearfx + ((int64_t)Tx + (int64_t)nL * (Ty + (int64_t)nL * Tz)) * g.cap;
+  const int W3 = W * W * W;
+  for (int l = threadIdx.x; l < W3; l += blockDim.x) {
+    const int x = l % W, y = (l / W) % W, z = l / (W * W);
+    const double dx = x - rx, dy = y - ry, dz = z - rz;
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 == 0.0) continue;
+    atomicAdd((unsigned long long*)(dst + l), (unsigned long long)__double2ll_rn(f / sqrt(r2)));
+  }
+}
+
 void kmc_accept_apply(const Geo& g, const Dev& d, cudaStream_t s) {
   AccPlan ap;
   ap.nmp = (g.L * g.P + ACC_THREADS - 1) / ACC_THREADS;
@@ -1728,6 +1811,7 @@ void kmc_accept_apply(const Geo& g, const Dev& d, cudaStream_t s) {
   ap.nfine = g.L >= 4 ? (ap.fine_per_level * (g.L - 3) + ACC_THREADS - 1) / ACC_THREADS : 0;
   k_acc_fused<<<ap.nmp + ap.nfar + ap.ncoarse + ap.nfine + 1, ACC_THREADS, 0, s>>>(g, d, d.acc_scratch, ap);
   k_acc_coarse_reduce<<<KMC_COARSE_CELLS, 32 * ACR_WARPS, sizeof(double2) * ACR_WARPS * g.P, s>>>(g, d, d.acc_scratch);
+  if (g.near_cache) k_near_update<<<2 * 27, 128, 0, s>>>(g, d);
 }
 
 // ------------------------------------------------------------------ general points
@@ -1964,10 +2048,15 @@ void kmc_stage_general(const Geo& g, const Dev& d, int64_t m, const int32_t* par
 // launch inside a stream capture would invalidate the capture
 static void kmc_preload() {
   cudaFuncAttributes fa;
-  cudaFuncGetAttributes(&fa, k_propose_lattice<float, KMC_NHOP>);
-  cudaFuncGetAttributes(&fa, k_propose_lattice<double, KMC_NHOP>);
-  cudaFuncGetAttributes(&fa, k_propose_lattice<float, KMC_MAXHOP>);
-  cudaFuncGetAttributes(&fa, k_propose_lattice<double, KMC_MAXHOP>);
+  cudaFuncGetAttributes(&fa, k_propose_lattice<float, KMC_NHOP, PROP_SUM>);
+  cudaFuncGetAttributes(&fa, k_propose_lattice<double, KMC_NHOP, PROP_SUM>);
+  cudaFuncGetAttributes(&fa, k_propose_lattice<float, KMC_MAXHOP, PROP_SUM>);
+  cudaFuncGetAttributes(&fa, k_propose_lattice<double, KMC_MAXHOP, PROP_SUM>);
+  cudaFuncGetAttributes(&fa, k_propose_lattice<float, KMC_NHOP, PROP_CACHED>);
+  cudaFuncGetAttributes(&fa, k_propose_lattice<double, KMC_NHOP, PROP_CACHED>);
+  cudaFuncGetAttributes(&fa, k_propose_lattice<float, KMC_MAXHOP, PROP_CACHED>);
+  cudaFuncGetAttributes(&fa, k_propose_lattice<double, KMC_MAXHOP, PROP_CACHED>);
+  cudaFuncGetAttributes(&fa, k_near_update);
   cudaFuncGetAttributes(&fa, k_finalize<true, KMC_NHOP>);
   cudaFuncGetAttributes(&fa, k_finalize<false, KMC_NHOP>);
   cudaFuncGetAttributes(&fa, k_finalize<true, KMC_MAXHOP>);

@@ -144,6 +144,7 @@ static int full_fmm(kmc_fmm* h) {
   fmm_far_field(g, d, s);
   fmm_shadow_all(g, d, s);
   fmm_self_and_dipole(g, d, s);
+  if (g.near_cache) kmc_near_fill(g, d, h->prec, s);  // near-field sums of every site, afresh
   CKLAUNCH();
   h->peff_valid = false;
   h->rates_valid = false;
@@ -217,6 +218,7 @@ void kmc_opts_default(kmc_opts* o) {
   o->hops = KMC_HOPS_6;
   o->bc = KMC_BC_PERIODIC;
   o->field_z = 0.0;
+  o->near_cache = 0;
 }
 
 const char* kmc_last_error(kmc_handle h) { return h ? h->msg : g_static_msg; }
@@ -295,6 +297,8 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   if (o.bc != KMC_BC_PERIODIC && o.bc != KMC_BC_FREE && o.bc != KMC_BC_DIRICHLET_Z)
     return fail(h, KMC_ERR_ARG, "unknown boundary conditions");
   if (!isfinite(o.field_z)) return fail(h, KMC_ERR_ARG, "field_z must be finite");
+  if (o.near_cache != 0 && o.near_cache != 1) return fail(h, KMC_ERR_ARG, "near_cache must be 0 or 1");
+  if (o.near_cache && o.lattice_edge <= 0) return fail(h, KMC_ERR_ARG, "near_cache needs lattice mode");
   // input arrays: read in the caller's memory kind, except with Dirichlet walls,
   // where the library appends the mirrors on the host first
   bool dev_in = h->mem == KMC_MEM_DEVICE;
@@ -353,6 +357,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
     if ((int64_t)E * E * E > 0x7fffffffLL) return fail(h, KMC_ERR_ARG, "lattice too large");
     if (n > (int64_t)E * E * E) return fail(h, KMC_ERR_ARG, "more charges than sites");
     g.cap = g.W * g.W * g.W;
+    g.near_cache = o.near_cache;
   } else {
     g.E = 0;
     g.h = 1.0;
@@ -375,6 +380,13 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
     g.qmax = fmax(g.qmax, fabs(qh[i]));
   }
   if (!g.bc && fabs(qs) > 1e-12 * qa) return fail(h, KMC_ERR_NOT_NEUTRAL, "sum of charges %.3e is not zero", qs);
+  if (g.near_cache) {
+    // fixed-point exponent of the cached near-field sums: 2^k bound < 2^61, bound = max|q| x
+    // (27 leaves x cap charges) at the smallest separation, one site (FP32 form: lattice
+    // units; FP64 form: physical units)
+    const double bound = fmax(g.qmax, 1e-300) * 27.0 * g.cap * (h->prec == 1 ? 1.0 : 1.0 / g.h);
+    g.near_ks = 61 - (ilogb(bound) + 1);
+  }
   // off-lattice capacity from the initial occupancy
   std::vector<double> ph;
   if (g.E == 0) {
@@ -415,6 +427,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   ALLOC(d.spos64, sizeof(double4_32a) * nslot);
   ALLOC(d.spos32, sizeof(float4) * nslot);
   if (g.E > 0) ALLOC(d.sgrp, sizeof(float) * 20 * (size_t)g.ML * (size_t)sgrp_groups(g.cap));
+  if (g.near_cache) ALLOC(d.nearfx, sizeof(long long) * (size_t)g.ML * (size_t)g.cap);
   ALLOC(d.Mt, sizeof(double2) * g.ncell_total * g.P);
   ALLOC(d.Psi, sizeof(double2) * g.ncell_total * g.P);
   ALLOC(d.Peff, (h->prec == 0 ? sizeof(double2) : sizeof(float2)) * g.ncell_total * g.P);
