@@ -494,8 +494,12 @@ __device__ __forceinline__ void fixed_add(long long* a, double v) {
 // site of the leaf into the near-field cache d.nearfx; no hops, no L2P, no
 // outputs) or PROP_CACHED (the near-field sums read from the cache, no pairs).
 enum { PROP_SUM = 0, PROP_FILL = 1, PROP_CACHED = 2 };
+// The cached form holds no source chunk in shared memory and runs twelve CTAs
+// per SM (more resident leaves hide its load and barrier latency; sixteen
+// spilled too much of the L2P).
 template <typename T, int NH, int mode>
-__global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g, const Dev d, int chunk) {
+__global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
+    k_propose_lattice(const Geo g, const Dev d, int chunk) {
   typedef typename cplx<T>::type C;
   typedef typename vec4<T>::type V4;
   constexpr bool F32 = sizeof(T) == 4;
@@ -572,7 +576,7 @@ __global__ void __launch_bounds__(PROP_THREADS, 9) k_propose_lattice(const Geo g
       // neighbourhood is dense); one leaf always fits (pass_cap >= capacity)
       int np = 0;
       pq[0] = 0;
-      if (total > pass_cap) {
+      if (mode != PROP_CACHED && total > pass_cap) {
         int start = 0;
         for (int q = 0; q < 27; q++) {
           const int uq = F32 ? (nb_cnt[q] + 3) >> 2 : nb_cnt[q];
@@ -930,13 +934,13 @@ void kmc_prepare(const Geo& g, int prec) {
   prepare_m<PROP_SUM>(g, prec, sm);
   if (g.near_cache) {
     prepare_m<PROP_FILL>(g, prec, sm);
-    prepare_m<PROP_CACHED>(g, prec, sm);
+    prepare_m<PROP_CACHED>(g, prec, propose_smem(g, prec, 0));
   }
 }
 
 template <int MODE>
 static void propose_launch_m(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
-  const int chunk = propose_chunk(g);
+  const int chunk = MODE == PROP_CACHED ? 0 : propose_chunk(g);  // cached sums: no source staging
   const size_t sm = propose_smem(g, prec, chunk);
   const unsigned nb = (unsigned)g.ML;
   if (g.nhop == KMC_MAXHOP) {
