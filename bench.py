@@ -141,6 +141,14 @@ def pair_count(E: int, L: int, sites: np.ndarray, nhop: int = 6, bc: str = "peri
     return dict(points=int(pts.sum()), pairs=pairs, hops=hops, leaves=nL ** 3)
 
 
+# DRAM bytes (read + write) of one summing propose launch per leaf, from the ncu capture of the
+# 128^3 tile case (4096 leaves of 8^3 sites, 32 charges each, 6 hops, mixed precision:
+# profiles/propose_tile_full.md, 9.10 MB read, 512 B written).  Valid for workloads with the same
+# leaf shape (tile, large); scaled by the number of leaves.
+PROPOSE_DRAM_BYTES_PER_LEAF = (9.095936e6 + 512) / 4096
+TRAFFIC_WORKLOADS = ("tile", "large")
+
+
 def l2p_flops(p: int) -> int:
     """FP32 operations of one L2P (recurrence 6 + accumulate 2 per (n, m), m >= 0)."""
     return 8 * (p + 1) * (p + 2) // 2
@@ -482,7 +490,12 @@ def run_gpu(args):
     roof = {"bound": "alu", "kernel": "k_propose_lattice<float>",
             "achieved": achieved / 1e9, "peak": mufu_peak / 1e9, "unit": "G pair-interactions/s (MUFU rsqrt)",
             "work": "pairs = distinct evaluation sites x charges in the 27 neighbouring leaves",
-            "frac": achieved / mufu_peak, "traffic": None,
+            "frac": achieved / mufu_peak,
+            "traffic": (PROPOSE_DRAM_BYTES_PER_LEAF * work["leaves"]
+                        if args.workload in TRAFFIC_WORKLOADS and args.bc == "periodic" else None),
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the 128^3 tile case "
+                               "(same leaf shape), scaled by leaves" if args.workload in TRAFFIC_WORKLOADS
+                               and args.bc == "periodic" else None),
             "peak_source": f"16 MUFU/clk/SM x {nsm} SMs x {sm_max:.0f} MHz ({src} max clock)",
             "pairs_per_launch": pairs, "points_per_launch": work["points"],
             "fp32_ops_per_launch": fp32_ops, "t_min_ms": 1e3 * max(t_mufu, t_fma), "t_meas_ms": prop_ms,
