@@ -70,8 +70,11 @@ def aggregate(units: float, ms: float, device=None):
 
 # per KMC step: downward root + (L - 1) levels, propose, finalize, select,
 # record, move-from-event and two accept kernels
-def launches_per_step(L: int) -> int:
-    return L + 7
+def launches_per_step(L: int, bc: str = "periodic") -> int:
+    """Kernels of one device-driven step: the downward pass (root and levels 2..L: L launches),
+    propose, rates, select, move record, event decode, the fused accept and its coarse reduction;
+    grounded walls add the mirror move and its accept (3)."""
+    return L + 7 + (3 if bc == "dirichlet" else 0)
 
 
 # --------------------------------------------------------------- algorithmic work
@@ -168,10 +171,18 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.device), "-lms", "200"],
+                                          "-i", str(self.device), "-lms", "50"],
                                          stdout=open(path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # the sampler takes a moment to start: wait (at most 3 s) for its first line, so that the
+        # samples that follow fall inside the timed region
+        t0 = time.time()
+        while time.time() - t0 < 3.0 and self.proc.poll() is None:
+            if os.path.getsize(path) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -521,7 +532,7 @@ def run_gpu(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": launches_per_step(L) * args.steps,
+        "gpu_launches": launches_per_step(L, args.bc) * args.steps,
         "paper_context": PAPER_SEC53 if args.workload == "sec53" else None,
         "clocks": clocks,
     }
@@ -602,7 +613,7 @@ def run_batch(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--bc", default="periodic", choices=["periodic", "free", "dirichlet"],
