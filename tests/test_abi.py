@@ -61,3 +61,18 @@ def test_proposal_tuples_flatten_in_order():
     assert off.tolist() == [0, 2, 3, 3]
     part, tgt, off = k.flatten_proposals(())
     assert part.shape == (0,) and tgt.shape == (0, 3) and off.tolist() == [0]
+
+
+def test_options_struct_layout_matches_the_header():
+    """kmc_opts_default fills exactly the binding's kmc_opts: the bytes after it stay untouched
+    (a C struct larger than the binding's would overwrite them), and every field, the last one
+    included, gets its documented default."""
+    import paper_1905_04065_gb300 as k
+    lib = k.load_library()
+    n = ctypes.sizeof(k.kmc_opts)
+    buf = (ctypes.c_ubyte * (n + 64))(*([0xAB] * (n + 64)))
+    lib.kmc_opts_default(ctypes.cast(buf, ctypes.c_void_p))
+    assert bytes(buf[n:]) == b"\xab" * 64
+    opts = k.kmc_opts.from_buffer_copy(bytes(buf[:n]))
+    assert opts.kT == 1.0 and opts.lattice_edge == 0 and opts.hops == k.KMC_HOPS_6
+    assert opts.bc == k.KMC_BC_PERIODIC and opts.field_z == 0.0 and opts.near_cache == 0
