@@ -32,6 +32,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -373,8 +374,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     # timed region
     clk = Clocks(dev)
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    clk.start(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv"))
+    os.makedirs(args.clocks_dir, exist_ok=True)
+    clk.start(os.path.join(args.clocks_dir, f"clocks_rank{rank}.csv"))
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -580,8 +581,8 @@ def run_batch(args):
     # the replicas' working set (rates, expansions, charges) exceeds the 129 MB
     # L2, so the K timed steps run as one call: the graph is replayed K times
     clk = Clocks(dev)
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    clk.start(os.path.join(ROOT, "gpurun_out", f"clocks_batch_rank{rank}.csv"))
+    os.makedirs(args.clocks_dir, exist_ok=True)
+    clk.start(os.path.join(args.clocks_dir, f"clocks_batch_rank{rank}.csv"))
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     k.kmc_batch_run(bat, u[args.warmup: args.warmup + args.steps])
@@ -623,6 +624,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--clocks-dir", default=tempfile.gettempdir(),
+                    help="directory for the nvidia-smi clock samples of the timed region")
     ap.add_argument("--near-cache-steps", type=int, default=20,
                     help="steps of the near-field cache form reported beside the headline (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
