@@ -588,7 +588,10 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
       }
       pq[++np] = 27;
       misc[0] = np;
-      misc[1] = 0;
+      {  // fixed-point exponent of the near-field sums: 2^ks * bound < 2^(bits - 2)
+        const double bound = g.qmax * (double)max(nb_off[27] * (F32 ? 4 : 1), 1) * (F32 ? 1.0 : (double)ih);
+        misc[1] = (F32 ? 30 : 62) - (ilogb(bound) + 1);
+      }
     }
     __syncwarp();
     if (F32 && mode != PROP_CACHED) {  // first pass: one bulk copy per leaf (one lane each), overlapped with phases 1-3
@@ -726,11 +729,7 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
   }
   // no sites: only the prefetch to drain; cached sums: no pairs (and no prefetch)
   const int npass = mode == PROP_CACHED ? 0 : (nsites ? misc[0] : 1);
-  int ks;
-  {
-    const double bound = g.qmax * (double)max(nb_off[27] * (F32 ? 4 : 1), 1) * (F32 ? 1.0 : (double)ih);
-    ks = (F32 ? 30 : 62) - (ilogb(bound) + 1);
-  }
+  const int ks = misc[1];
   const T scale = (T)ldexp(1.0, ks);
   for (int pass = 0; pass < npass; pass++) {
     const int q0 = pq[pass], q1 = pq[pass + 1];
@@ -757,28 +756,31 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
         __syncthreads();
         return;
       }
-      // the copied groups into this leaf's corner frame (own leaf: already)
-      for (int q = max(q0, 1) + warp; q < q1; q += nwarp) {
+      // the copied groups into this leaf's corner frame (own leaf: already):
+      // every thread takes groups of the pass, finding a group's leaf q (the
+      // largest with nb_off[q] <= group) by a binary search over nb_off
+      for (int gg = nb_off[max(q0, 1)] + tid; gg < nb_off[q1]; gg += blockDim.x) {
+        int q = 0;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1)
+          if (q + st <= 27 && nb_off[q + st] <= gg) q += st;
         const int qq = q <= 13 ? q - 1 : q;
         const float ox = i2f((qq % 3 - 1) * W), oy = i2f(((qq / 3) % 3 - 1) * W);
         const float oz = i2f((qq / 9 - 1) * W);
-        float4* G = (float4*)src + 5 * (nb_off[q] - nb_off[q0]);
-        const int ng = (nb_cnt[q] + 3) >> 2;
-        for (int gi = lane; gi < ng; gi += 32) {
+        float4* G = (float4*)src + 5 * (gg - nb_off[q0]);
 #pragma unroll
-          for (int pr = 0; pr < 2; pr++) {
-            float4 A = G[5 * gi + 2 * pr], B = G[5 * gi + 2 * pr + 1];
-            A.x += ox;
-            A.y += ox;
-            A.z += oy;
-            A.w += oy;
-            B.x += oz;
-            B.y += oz;
-            B.z = A.x * A.x + A.z * A.z + B.x * B.x;
-            B.w = A.y * A.y + A.w * A.w + B.y * B.y;
-            G[5 * gi + 2 * pr] = A;
-            G[5 * gi + 2 * pr + 1] = B;
-          }
+        for (int pr = 0; pr < 2; pr++) {
+          float4 A = G[2 * pr], B = G[2 * pr + 1];
+          A.x += ox;
+          A.y += ox;
+          A.z += oy;
+          A.w += oy;
+          B.x += oz;
+          B.y += oz;
+          B.z = A.x * A.x + A.z * A.z + B.x * B.x;
+          B.w = A.y * A.y + A.w * A.w + B.y * B.y;
+          G[2 * pr] = A;
+          G[2 * pr + 1] = B;
         }
       }
     } else {
