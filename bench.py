@@ -147,9 +147,9 @@ def pair_count(E: int, L: int, sites: np.ndarray, nhop: int = 6, bc: str = "peri
 
 # DRAM bytes (read + write) of one summing propose launch per leaf, from the ncu capture of the
 # 128^3 tile case (4096 leaves of 8^3 sites, 32 charges each, 6 hops, mixed precision:
-# profiles/propose_tile_full.md, 9.10 MB read, 512 B written).  Valid for workloads with the same
+# profiles/propose_tile_full.md, 9.10 MB read, 256 B written).  Valid for workloads with the same
 # leaf shape (tile, large); scaled by the number of leaves.
-PROPOSE_DRAM_BYTES_PER_LEAF = (9.095936e6 + 512) / 4096
+PROPOSE_DRAM_BYTES_PER_LEAF = (9.097216e6 + 256) / 4096
 TRAFFIC_WORKLOADS = ("tile", "large")
 
 
