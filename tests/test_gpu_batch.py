@@ -54,3 +54,30 @@ def test_batch_rejects_off_lattice_member():
     h = k.kmc_fmm_init(pos, q, 8.0, 3, 6)
     with pytest.raises(k.KmcError):
         k.kmc_batch_create([h])
+
+
+def test_batch_with_near_cache_members():
+    """Replicas with the near-field cache (every other one) in the same graph as replicas that sum
+    the pairs: the same events, times and positions as each handle run alone with its own setting
+    (the cache's per-move update is part of every replica's captured step)."""
+    import paper_1905_04065_gb300 as k
+    reps = _replicas()
+    steps = 23
+    rng = np.random.default_rng(78)
+    u = 1.0 - rng.random((steps, len(reps), 2))
+
+    def make():
+        return [k.kmc_fmm_init(workloads.site_positions(E, s), q, float(E), L, 8, precision="mixed",
+                               lattice_edge=E, kT=0.1, near_cache=(r % 2 == 0))
+                for r, (E, N, L, s, q) in enumerate(reps)]
+
+    hs = make()
+    b = k.kmc_batch_create(hs)
+    ev_b, dt_b = k.kmc_batch_run(b, u)
+    pos_b = [k.kmc_fmm_positions(h) for h in hs]
+    del b
+    for r, h in enumerate(make()):
+        ev, dt = k.kmc_run(h, u[:, r, :])
+        assert np.array_equal(ev, ev_b[:, r]), r
+        np.testing.assert_allclose(dt, dt_b[:, r], rtol=1e-12)
+        assert np.array_equal(k.kmc_fmm_positions(h), pos_b[r])
