@@ -427,8 +427,11 @@ def run_gpu(args):
     e2e_ms = e2e_tot / es
     n = len(q)
     e2e = {"value": e2e_units / (e2e_tot * 1e-3), "unit": UNIT,
-           "h2d_bytes_per_step": 16 + 24 + 8,
-           "d2h_bytes_per_step": nhop * n * (1 + 8) + 8 + 8 + 8 + 24 + 8,
+           # host -> device: kmc_step's two uniforms, the accepted event; device -> host: mask and dU
+           # of every hop, the error flags (16 B) after the proposal and after the accept, kmc_step's
+           # event and (dt, Q), the accepted event's mask byte and FP32 dU
+           "h2d_bytes_per_step": 16 + 8,
+           "d2h_bytes_per_step": nhop * n * (1 + 8) + 16 + 8 + 16 + 1 + 4 + 16,
            "path": "kmc_fmm_propose_lattice (mask+dU into pinned host buffers) + kmc_step + kmc_fmm_accept_event"}
 
     # FP64 form (context)

@@ -716,7 +716,10 @@ int kmc_fmm_accept_event(kmc_handle h, int64_t event, double* dU_accepted) {
   const Geo& g = h->g;
   if (g.E <= 0) return fail(h, KMC_ERR_STATE, "kmc_fmm_accept_event needs lattice mode");
   if (event < 0 || event >= (int64_t)g.nhop * g.nphys) return fail(h, KMC_ERR_ARG, "event index out of range");
-  if (g.dirichlet) {  // the charge and its mirror move together: the device accept path, twice
+  // the device accept path: the move record built from the event on the device (with grounded
+  // walls, twice: the charge and its mirror); without walls it needs the current proposal's
+  // rates, else the general path below validates and applies the move
+  if (g.dirichlet || h->rates_valid) {
     cudaStream_t s = h->stream;
     if (!h->rates_valid) {
       r = refresh_peff(h);
@@ -727,23 +730,23 @@ int kmc_fmm_accept_event(kmc_handle h, int64_t event, double* dU_accepted) {
       h->rates_valid = true;
     }
     uint8_t mk = 0;
-    CK(cudaMemcpyAsync(&mk, h->d.mask + event, 1, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (!mk) return fail(h, KMC_ERR_ARG, "event %lld is masked (occupied target or a wall)", (long long)event);
+    float f = 0.f;
     double du = 0.0;
-    if (h->prec == 1) {
-      float f = 0.f;
-      CK(cudaMemcpyAsync(&f, h->d.dU32 + event, sizeof(f), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      du = f;
-    } else {
-      CK(cudaMemcpyAsync(&du, h->d.dU + event, sizeof(du), cudaMemcpyDeviceToHost, s));
-    }
+    CK(cudaMemcpyAsync(&mk, h->d.mask + event, 1, cudaMemcpyDeviceToHost, s));
+    if (h->prec == 1) CK(cudaMemcpyAsync(&f, h->d.dU32 + event, sizeof(f), cudaMemcpyDeviceToHost, s));
+    else CK(cudaMemcpyAsync(&du, h->d.dU + event, sizeof(du), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!mk)
+      return fail(h, KMC_ERR_ARG, "event %lld is masked (occupied target%s)", (long long)event,
+                  g.dirichlet ? " or a wall" : "");
+    if (h->prec == 1) du = f;
     CK(cudaMemcpyAsync(h->d.event, &event, sizeof(event), cudaMemcpyHostToDevice, s));
     kmc_accept_from_event(g, h->d, s);
     kmc_accept_apply(g, h->d, s);
-    kmc_mirror_move(g, h->d, s);
-    kmc_accept_apply(g, h->d, s);
+    if (g.dirichlet) {
+      kmc_mirror_move(g, h->d, s);
+      kmc_accept_apply(g, h->d, s);
+    }
     CKLAUNCH();
     CK(cudaStreamSynchronize(s));
     h->peff_valid = false;
