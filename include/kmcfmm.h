@@ -181,7 +181,15 @@ int kmc_fmm_propose_lattice(kmc_handle h, uint8_t* mask, double* dU);
  */
 int kmc_fmm_accept(kmc_handle h, int32_t particle, const double target[3], double* dU_accepted);
 
-/* Lattice mode: accept event j = nh i + k (hop k of particle i). */
+/*
+ * Lattice mode: accept event j = nh i + k (hop k of particle i), with the
+ * updates of kmc_fmm_accept.  When the rates of the last kmc_fmm_propose_lattice
+ * are still current (no accept since), the move is built on the device from the
+ * event and dU_accepted receives that proposal's dU (FP32 in the mixed form);
+ * otherwise the move goes through kmc_fmm_accept and dU is recomputed.  With
+ * Dirichlet walls the charge's mirror moves with it.  Errors: KMC_ERR_ARG (index
+ * out of range, a masked event: occupied target or, with walls, a wall).
+ */
 int kmc_fmm_accept_event(kmc_handle h, int64_t event, double* dU_accepted);
 
 /*
