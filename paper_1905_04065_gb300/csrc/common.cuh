@@ -25,6 +25,7 @@
 #define KMC_MAXL 10   // maximum number of levels
 #define KMC_MAXP 20   // maximum expansion degree
 #define KMC_NHOP 6    // lattice hop directions of the nearest-neighbour set (+x,-x,+y,-y,+z,-z)
+#define KMC_ISQ_N (3 * 23 * 23 + 1)  // squared lattice distances within 27 leaves of <= 12 sites
 #define KMC_MAXHOP 14 // with the 8 body diagonals (the hop set of the paper's Sec. 5.3 benchmark)
 
 // component a (0 = x, 1 = y, 2 = z) of lattice hop k: k < 6 the faces
@@ -142,7 +143,8 @@ struct Dev {
   float* dirA32;
   float* dirB32;
   long long* nearfx;  // [ML * cap] near-field sum at every site of every leaf (local site index
-                      // x + W (y + W z)), fixed point; FP32 form in lattice units, FP64 physical
+                      // x + W (y + W z)), fixed point, lattice units
+  double* isq;        // [KMC_ISQ_N] 1/sqrt(n), n the squared lattice distance (entry 0 = 0)
   double* dip;        // [3] dipole moment M
   float* fdip;        // [3] (4 pi / 3V) M in FP32 for the mixed rate assembly
   double* U;          // [1] total energy

@@ -230,29 +230,46 @@ template <> struct NearField<float> {
   }
 };
 
+// FP64 form.  On the lattice every squared distance is an exact integer n in
+// lattice units (|d| < 2W per axis, so n <= 3 (2W - 1)^2 < 2^24), so 1/|d|
+// comes from a table of correctly rounded 1/sqrt(n) (entry 0 = 0: the pair at
+// distance 0 adds nothing), indexed by the FP32-exact n; the only FP64
+// operation per pair is the accumulation q / |d|.  Staged source: (x, y, z,
+// |s|^2) in lattice units in the target leaf's frame (FP32, exact integers),
+// then the FP64 charge.
 template <> struct NearField<double> {
+  struct Src {
+    float4 p;
+    double q, pad;
+  };
   double a0, a1;
   __device__ __forceinline__ void reset() { a0 = a1 = 0.0; }
-  static __host__ __device__ __forceinline__ size_t bytes(int chunk) { return (size_t)chunk * 32; }
-  static __device__ __forceinline__ void stage(unsigned char* sm, int e, double4_32a v) { ((double4_32a*)sm)[e] = v; }
-  static __device__ __forceinline__ void pad(unsigned char*, int) {}
-  // sources [j0, j1); those below nguard are the targets' own leaf (skip the
-  // pair at distance 0)
-  __device__ __forceinline__ void run2(const unsigned char* sm, int j0, int j1, int nguard, bool two, double x0,
-                                       double y0, double z0, double x1, double y1, double z1) {
-    const double4_32a* src = (const double4_32a*)sm;
+  static __host__ __device__ __forceinline__ size_t bytes(int chunk) { return (size_t)chunk * sizeof(Src); }
+  static __device__ __forceinline__ void stage(unsigned char* sm, int e, int x, int y, int z, double q) {
+    Src v;
+    v.p = make_float4((float)x, (float)y, (float)z, (float)(x * x + y * y + z * z));
+    v.q = q;
+    v.pad = 0.0;
+    ((Src*)sm)[e] = v;
+  }
+  // sources [j0, j1) against the leaf-local targets t0 and t1 (t1 only when
+  // two is set; warp-uniform)
+  __device__ __forceinline__ void run2(const unsigned char* sm, const double* isq, int j0, int j1, bool two, int tx0,
+                                       int ty0, int tz0, int tx1, int ty1, int tz1) {
+    const Src* src = (const Src*)sm;
+    const float ax0 = (float)(-2 * tx0), ay0 = (float)(-2 * ty0), az0 = (float)(-2 * tz0);
+    const float ax1 = (float)(-2 * tx1), ay1 = (float)(-2 * ty1), az1 = (float)(-2 * tz1);
+    const float w0 = (float)(tx0 * tx0 + ty0 * ty0 + tz0 * tz0), w1 = (float)(tx1 * tx1 + ty1 * ty1 + tz1 * tz1);
     double s0 = a0, s1 = a1;
     for (int j = j0; j < j1; j++) {
-      const double4_32a v = src[j];
-      double dx = v.x - x0, dy = v.y - y0, dz = v.z - z0;
-      double r2 = dx * dx + dy * dy + dz * dz;
-      s0 += (j >= nguard || r2 > 0.0) ? v.w * rsqrt(r2) : 0.0;
+      const float4 v = src[j].p;
+      const double q = src[j].q;
+      // n = |s|^2 + |t|^2 - 2 s.t, exact; n + 2^23 holds n in its low mantissa bits
+      const float n0 = fmaf(ax0, v.x, fmaf(ay0, v.y, fmaf(az0, v.z, v.w + w0)));
+      s0 = fma(q, isq[__float_as_int(n0 + 8388608.f) - 0x4B000000], s0);
       if (two) {
-        dx = v.x - x1;
-        dy = v.y - y1;
-        dz = v.z - z1;
-        r2 = dx * dx + dy * dy + dz * dz;
-        s1 += (j >= nguard || r2 > 0.0) ? v.w * rsqrt(r2) : 0.0;
+        const float n1 = fmaf(ax1, v.x, fmaf(ay1, v.y, fmaf(az1, v.z, v.w + w1)));
+        s1 = fma(q, isq[__float_as_int(n1 + 8388608.f) - 0x4B000000], s1);
       }
     }
     a0 = s0;
@@ -459,15 +476,6 @@ int kmc_wait_probe(double limit_seconds, cudaStream_t s) {
   return e == cudaSuccess ? host : -1;
 }
 
-// FP64 form: one staged source in physical coordinates; (shx, shy, shz) is the
-// periodic image shift in sites
-__device__ __forceinline__ void stage_source(unsigned char* src, int e, double4_32a v, int shx, int shy, int shz,
-                                             double h) {
-  v.x += (double)shx * h;
-  v.y += (double)shy * h;
-  v.z += (double)shz * h;
-  NearField<double>::stage(src, e, v);
-}
 
 // partial near-field sum (already scaled) into a fixed-point accumulator in
 // shared memory, rounded to nearest
@@ -521,6 +529,9 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
   uint32_t* need = bits + nbw;                      // [nbw] sites where a potential is needed
   int* woff = (int*)(need + nbw);                   // [nbw + 1] prefix of needed sites per word
   uint16_t* sites = (uint16_t*)(woff + nbw + 1);    // [W3] needed local sites (x | y << 4 | z << 8), compacted
+  // FP64 form: 1/sqrt(n) for the squared lattice distances n <= 3 (2W - 1)^2, 8-byte aligned
+  double* isq = (double*)(((uintptr_t)(sites + ((W3 + 1) & ~1)) + 7) & ~(uintptr_t)7);
+  const int nisq = 3 * (2 * W - 1) * (2 * W - 1) + 1;
   T* out_old = (T*)(F32 ? (void*)d.phi_old32 : (void*)d.phi_old);
   T* out_new = (T*)(F32 ? (void*)d.phi_new32 : (void*)d.phi_new);
 
@@ -538,6 +549,8 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
 
   const C* Pe = (const C*)d.Peff + (g.cell_off[g.L] + leaf) * g.P;
   for (int c = tid; c < g.P; c += blockDim.x) Lc[c] = Pe[c];
+  if (!F32 && mode != PROP_CACHED)
+    for (int c = tid; c < nisq; c += blockDim.x) isq[c] = d.isq[c];
   for (int c = tid; c < nbw; c += blockDim.x) {
     bits[c] = 0u;
     need[c] = 0u;
@@ -589,7 +602,7 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
       pq[++np] = 27;
       misc[0] = np;
       {  // fixed-point exponent of the near-field sums: 2^ks * bound < 2^(bits - 2)
-        const double bound = g.qmax * (double)max(nb_off[27] * (F32 ? 4 : 1), 1) * (F32 ? 1.0 : (double)ih);
+        const double bound = g.qmax * (double)max(nb_off[27] * (F32 ? 4 : 1), 1);  // lattice units
         misc[1] = (F32 ? 30 : 62) - (ilogb(bound) + 1);
       }
     }
@@ -789,8 +802,11 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
         const int ux = lx + qq % 3 - 1, uy = ly + (qq / 3) % 3 - 1, uz = lz + qq / 9 - 1;
         const int shx = ux - wrap1(ux, nL), shy = uy - wrap1(uy, nL), shz = uz - wrap1(uz, nL);
         const int e0 = nb_off[q] - nb_off[q0];
-        for (int j = lane; j < nb_cnt[q]; j += 32)
-          stage_source(src, e0 + j, spos[nb_base[q] + j], shx * W, shy * W, shz * W, (double)h);
+        for (int j = lane; j < nb_cnt[q]; j += 32) {  // lattice coordinates in this leaf's frame
+          const V4 v = spos[nb_base[q] + j];
+          NearField<T>::stage(src, e0 + j, lattice_coord(v.x, ih) - gx0 + shx * W,
+                              lattice_coord(v.y, ih) - gy0 + shy * W, lattice_coord(v.z, ih) - gz0 + shz * W, v.w);
+        }
       }
     }
     __syncthreads();
@@ -812,9 +828,7 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
           nf.run_span((const float4*)src, u0, u1, nown, two, i2f(ix0), i2f(iy0), i2f(iz0), i2f(ix1), i2f(iy1),
                       i2f(iz1));
         } else {
-          nf.run2(src, u0, u1, nown, two, ((T)(gx0 + ix0) + (T)0.5) * h, ((T)(gy0 + iy0) + (T)0.5) * h,
-                  ((T)(gz0 + iz0) + (T)0.5) * h, ((T)(gx0 + ix1) + (T)0.5) * h, ((T)(gy0 + iy1) + (T)0.5) * h,
-                  ((T)(gz0 + iz1) + (T)0.5) * h);
+          nf.run2(src, isq, u0, u1, two, ix0, iy0, iz0, ix1, iy1, iz1);
         }
         if (b0 < nsites) fixed_add(&acc[l0], nf.sum(0) * scale);
         if (two && b1 < nsites) fixed_add(&acc[l1], nf.sum(1) * scale);
@@ -853,8 +867,8 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
   // the L2P of the leaf's local expansion
   {
     const T hw = (T)(0.5 * W);
-    const T back = (T)ldexp(1.0, -ks) * (F32 ? ih : (T)1);
-    const T cback = (T)ldexp(1.0, -g.near_ks) * (F32 ? ih : (T)1);
+    const T back = (T)ldexp(1.0, -ks) * ih;  // lattice units to physical
+    const T cback = (T)ldexp(1.0, -g.near_ks) * ih;
     const long long* cache = mode == PROP_CACHED ? d.nearfx + leaf * (int64_t)g.cap : nullptr;
     for (int b = tid; b < nsites; b += blockDim.x) {
       const int sv = sites[b];
@@ -902,8 +916,9 @@ static size_t propose_smem(const Geo& g, int prec, int chunk) {
   const int W3 = g.W * g.W * g.W;
   const int nbw = (W3 + 31) / 32;
   const size_t srcb = prec == 0 ? NearField<double>::bytes(chunk) : NearField<float>::bytes(chunk);
+  const size_t isqb = prec == 0 ? 8 + 8 * (size_t)(3 * (2 * g.W - 1) * (2 * g.W - 1) + 1) : 0;
   return srcb + 2 * ts * (size_t)g.P + 27 * 8 + 8 + (28 + 27 + 27 + 28 + 4) * 4 + ts * (size_t)W3 +
-         4 * (size_t)(3 * nbw + 1) + 2 * (size_t)((W3 + 1) & ~1);
+         4 * (size_t)(3 * nbw + 1) + 2 * (size_t)((W3 + 1) & ~1) + isqb;
 }
 
 // sources are streamed in chunks of at least 960 (every neighbour leaf's
@@ -1774,7 +1789,7 @@ __global__ void __launch_bounds__(ACC_THREADS) k_acc_fused(const Geo g, const De
 // r'.  Block (side, o): the leaf T = S - o around the source leaf S of r (side
 // 0, -q) or r' (side 1, +q); in T's frame the source sits at its position in
 // S plus o W sites, as in T's propose CTA, so every site t of T gets
-// +-q / |t - r_T| (lattice units in the FP32 form, physical in FP64), except
+// +-q / |t - r_T| (lattice units), except
 // the pair at distance 0.  Free space: leaves beyond the box do not exist.
 __global__ void __launch_bounds__(128) k_near_update(const Geo g, const Dev d) {
   const MoveRec mv = *d.move;
@@ -1795,7 +1810,7 @@ __global__ void __launch_bounds__(128) k_near_update(const Geo g, const Dev d) {
   }
   const double rx = (double)(sx - Sx * W + ox * W), ry = (double)(sy - Sy * W + oy * W),
                rz = (double)(sz - Sz * W + oz * W);
-  const double f = (side ? mv.q : -mv.q) * ldexp(1.0, g.near_ks) * (g.prec == 1 ? 1.0 : 1.0 / g.h);
+  const double f = (side ? mv.q : -mv.q) * ldexp(1.0, g.near_ks);  // lattice units
   long long* dst = d.nearfx + ((int64_t)Tx + (int64_t)nL * (Ty + (int64_t)nL * Tz)) * g.cap;
   const int W3 = W * W * W;
   for (int l = threadIdx.x; l < W3; l += blockDim.x) {

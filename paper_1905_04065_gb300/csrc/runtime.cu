@@ -382,9 +382,8 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   if (!g.bc && fabs(qs) > 1e-12 * qa) return fail(h, KMC_ERR_NOT_NEUTRAL, "sum of charges %.3e is not zero", qs);
   if (g.near_cache) {
     // fixed-point exponent of the cached near-field sums: 2^k bound < 2^61, bound = max|q| x
-    // (27 leaves x cap charges) at the smallest separation, one site (FP32 form: lattice
-    // units; FP64 form: physical units)
-    const double bound = fmax(g.qmax, 1e-300) * 27.0 * g.cap * (h->prec == 1 ? 1.0 : 1.0 / g.h);
+    // (27 leaves x cap charges) at the smallest separation, one site (lattice units)
+    const double bound = fmax(g.qmax, 1e-300) * 27.0 * g.cap;
     g.near_ks = 61 - (ilogb(bound) + 1);
   }
   // off-lattice capacity from the initial occupancy
@@ -426,7 +425,10 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   ALLOC(d.uid, sizeof(int32_t) * nslot);
   ALLOC(d.spos64, sizeof(double4_32a) * nslot);
   ALLOC(d.spos32, sizeof(float4) * nslot);
-  if (g.E > 0) ALLOC(d.sgrp, sizeof(float) * 20 * (size_t)g.ML * (size_t)sgrp_groups(g.cap));
+  if (g.E > 0) {
+    ALLOC(d.sgrp, sizeof(float) * 20 * (size_t)g.ML * (size_t)sgrp_groups(g.cap));
+    ALLOC(d.isq, sizeof(double) * KMC_ISQ_N);
+  }
   if (g.near_cache) ALLOC(d.nearfx, sizeof(long long) * (size_t)g.ML * (size_t)g.cap);
   ALLOC(d.Mt, sizeof(double2) * g.ncell_total * g.P);
   ALLOC(d.Psi, sizeof(double2) * g.ncell_total * g.P);
@@ -478,6 +480,11 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   }
   cudaStream_t s = h->stream;
   CK(cudaMemsetAsync(d.err, 0, sizeof(int) * 4, s));
+  if (g.E > 0) {  // correctly rounded 1/sqrt(n) of the squared lattice distances (FP64 near field)
+    std::vector<double> isq(KMC_ISQ_N, 0.0);
+    for (int k = 1; k < KMC_ISQ_N; k++) isq[k] = 1.0 / sqrt((double)k);
+    CK(cudaMemcpy(d.isq, isq.data(), sizeof(double) * KMC_ISQ_N, cudaMemcpyHostToDevice));
+  }
   CK(cudaMemsetAsync(d.uid, 0xff, sizeof(int32_t) * nslot, s));
   CK(cudaMemsetAsync(d.mask, 0, (size_t)g.nhop * n, s));
   CK(cudaMemsetAsync(d.Psi, 0, sizeof(double2) * g.ncell_total * g.P, s));
