@@ -151,7 +151,8 @@ __device__ __forceinline__ T l2p_eval(const C* L, int p, T x, T y, T z) {
 // frame) so that one packed FP32x2 instruction (FADD2 / FFMA2) serves two pair
 // interactions; 1/r from the MUFU rsqrt.approx (relative error < 2^-22),
 // scaled by 1/h once per target.  Each thread evaluates two targets against
-// every source it loads.  FP64: physical coordinates, one source per iteration.
+// every source it loads.  FP64: integer lattice coordinates too, 1/r from a
+// table of 1/sqrt(n) (below), one source per iteration.
 __device__ __forceinline__ float rsqrt_mufu(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -863,7 +864,7 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
     }
   }
   __syncthreads();
-  // near field back to floating point (FP32: lattice units, times 1/h), plus
+  // near field back to floating point (lattice units, times 1/h), plus
   // the L2P of the leaf's local expansion
   {
     const T hw = (T)(0.5 * W);
