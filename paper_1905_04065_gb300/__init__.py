@@ -224,7 +224,41 @@ def kmc_fmm_init(positions, charges, box: float, levels: int, order: int, precis
         lib.kmc_fmm_destroy(ptr)
         h.ptr = None
         raise KmcError(code, text)
+    # what a checkpoint needs to rebuild the system (positions come from the handle)
+    h.init_args = dict(charges=np.array(charges.detach().cpu().numpy() if _is_torch(charges) else charges,
+                                        dtype=np.float64),
+                       box=float(box), levels=int(levels), order=int(order), precision=precision,
+                       lattice_edge=int(lattice_edge), lattice_h=float(lattice_h), kT=float(kT),
+                       leaf_capacity=int(leaf_capacity), m2l=m2l, hops=int(hops), bc=bc, field_z=float(field_z),
+                       near_cache=bool(near_cache))
     return h
+
+
+# ------------------------------------------------------------------ checkpoint / resume
+def kmc_checkpoint(h: Handle, path: str, step: int = 0, **extra) -> None:
+    """Save the state of a KMC system to an .npz file: the charges' current positions (user
+    order), their charges, the arguments the handle was created with, the caller's step counter
+    (e.g. the index into its uniform stream) and any extra arrays or numbers."""
+    args = dict(h.init_args)
+    q = args.pop("charges")
+    pos = kmc_fmm_positions(h)
+    if _is_torch(pos):
+        pos = pos.cpu().numpy()
+    np.savez(path, positions=pos, charges=q, step=np.int64(step),
+             init_args=np.array(repr(args)), **{f"extra_{k}": np.asarray(v) for k, v in extra.items()})
+
+
+def kmc_resume(path: str, stream=None, device: int = 0):
+    """Rebuild a system from a checkpoint: a new handle (host-memory arguments) initialised from
+    the saved positions, the full FMM recomputed as at init.  The expansions then differ from the
+    incrementally updated ones of the saved run by the truncation error only (as after
+    kmc_fmm_recompute).  Returns (handle, step, extra)."""
+    import ast
+    z = np.load(path, allow_pickle=False)
+    args = ast.literal_eval(str(z["init_args"]))
+    h = kmc_fmm_init(z["positions"], z["charges"], stream=stream, device=device, **args)
+    extra = {k[len("extra_"):]: z[k] for k in z.files if k.startswith("extra_")}
+    return h, int(z["step"]), extra
 
 
 def kmc_fmm_energy(h: Handle) -> float:

@@ -16,8 +16,29 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/kmcfmm.h"
 #include "common.cuh"
+
+// NVTX range of one C-ABI call (domain "kmcfmm"), visible in Nsight Systems and
+// usable as an ncu --nvtx filter; without an attached tool the calls do nothing
+static nvtxDomainHandle_t trace_domain() {
+  static nvtxDomainHandle_t d = nvtxDomainCreateA("kmcfmm");
+  return d;
+}
+struct TraceRange {
+  explicit TraceRange(const char* name) {
+    nvtxEventAttributes_t a = {};
+    a.version = NVTX_VERSION;
+    a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+    a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+    a.message.ascii = name;
+    nvtxDomainRangePushEx(trace_domain(), &a);
+  }
+  ~TraceRange() { nvtxDomainRangePop(trace_domain()); }
+};
+#define KMC_TRACE(name) TraceRange trace_range_(name)
 
 struct kmc_fmm {
   Geo g;
@@ -262,6 +283,7 @@ static int init_impl(kmc_fmm* h, int64_t n, const double* positions, const doubl
 
 int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const double* charges, double box, int levels,
                  int order, const kmc_opts* opts) {
+  KMC_TRACE("kmc_fmm_init");
   if (!out) return KMC_ERR_ARG;
   *out = nullptr;
   kmc_opts o;
@@ -538,6 +560,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
 }
 
 int kmc_fmm_energy(kmc_handle h, double* U) {
+  KMC_TRACE("kmc_fmm_energy");
   int r = guard(h);
   if (r) return r;
   if (!U) return fail(h, KMC_ERR_ARG, "U is NULL");
@@ -547,6 +570,7 @@ int kmc_fmm_energy(kmc_handle h, double* U) {
 }
 
 int kmc_fmm_propose_lattice(kmc_handle h, uint8_t* mask, double* dU) {
+  KMC_TRACE("kmc_fmm_propose_lattice");
   int r = guard(h);
   if (r) return r;
   if (h->g.E <= 0) return fail(h, KMC_ERR_STATE, "kmc_fmm_propose_lattice needs lattice mode");
@@ -628,6 +652,7 @@ static int general_du(kmc_fmm* h, int64_t m) {
 
 int kmc_fmm_propose(kmc_handle h, int64_t m, const int32_t* particle, const double* target, const uint8_t* mask,
                     double* dU) {
+  KMC_TRACE("kmc_fmm_propose");
   int r = guard(h);
   if (r) return r;
   if (h->g.dirichlet)
@@ -703,6 +728,7 @@ static int accept_general(kmc_fmm* h, int32_t particle, const double* tgt_host, 
 }
 
 int kmc_fmm_accept(kmc_handle h, int32_t particle, const double target[3], double* dU_accepted) {
+  KMC_TRACE("kmc_fmm_accept");
   int r = guard(h);
   if (r) return r;
   if (h->g.dirichlet)
@@ -718,6 +744,7 @@ int kmc_fmm_accept(kmc_handle h, int32_t particle, const double target[3], doubl
 }
 
 int kmc_fmm_accept_event(kmc_handle h, int64_t event, double* dU_accepted) {
+  KMC_TRACE("kmc_fmm_accept_event");
   int r = guard(h);
   if (r) return r;
   const Geo& g = h->g;
@@ -771,6 +798,7 @@ int kmc_fmm_accept_event(kmc_handle h, int64_t event, double* dU_accepted) {
 }
 
 int kmc_step(kmc_handle h, const double* rates, double zeta, double xi, int64_t* event, double* dt, double* Q) {
+  KMC_TRACE("kmc_step");
   int r = guard(h);
   if (r) return r;
   if (!(zeta > 0.0 && zeta <= 1.0 && xi > 0.0 && xi <= 1.0))
@@ -821,6 +849,7 @@ static void enqueue_step(kmc_fmm* h) {
 #define KMC_GRAPH_STEPS 8
 
 int kmc_run(kmc_handle h, int steps, const double* uniforms, int64_t* events, double* dts) {
+  KMC_TRACE("kmc_run");
   int r = guard(h);
   if (r) return r;
   if (h->g.E <= 0) return fail(h, KMC_ERR_STATE, "kmc_run needs lattice mode");
@@ -880,6 +909,7 @@ int kmc_run(kmc_handle h, int steps, const double* uniforms, int64_t* events, do
 
 int kmc_run_profiled(kmc_handle h, int steps, const double* uniforms, int64_t* events, double* dts,
                      double* phase_ms) {
+  KMC_TRACE("kmc_run_profiled");
   int r = guard(h);
   if (r) return r;
   if (h->g.E <= 0) return fail(h, KMC_ERR_STATE, "kmc_run_profiled needs lattice mode");
@@ -945,6 +975,7 @@ int kmc_run_profiled(kmc_handle h, int steps, const double* uniforms, int64_t* e
 }
 
 int kmc_fmm_recompute(kmc_handle h, double* drift) {
+  KMC_TRACE("kmc_fmm_recompute");
   int r = guard(h);
   if (r) return r;
   const Geo& g = h->g;
@@ -1043,6 +1074,7 @@ static int bfail(kmc_batch* b, int code, const char* fmt, ...) {
 }
 
 int kmc_batch_create(kmc_batch_handle* out, int count, const kmc_handle* handles) {
+  KMC_TRACE("kmc_batch_create");
   if (!out) return KMC_ERR_ARG;
   *out = nullptr;
   if (count < 1 || !handles) return KMC_ERR_ARG;
@@ -1100,6 +1132,7 @@ void kmc_batch_destroy(kmc_batch_handle b) {
 }
 
 int kmc_batch_run(kmc_batch_handle b, int steps, const double* uniforms, int64_t* events, double* dts) {
+  KMC_TRACE("kmc_batch_run");
   if (!b) return KMC_ERR_ARG;
   const int R = (int)b->h.size();
   if (steps < 0 || !uniforms) return bfail(b, KMC_ERR_ARG, "steps >= 0 and uniforms are required");

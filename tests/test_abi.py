@@ -76,3 +76,31 @@ def test_options_struct_layout_matches_the_header():
     opts = k.kmc_opts.from_buffer_copy(bytes(buf[:n]))
     assert opts.kT == 1.0 and opts.lattice_edge == 0 and opts.hops == k.KMC_HOPS_6
     assert opts.bc == k.KMC_BC_PERIODIC and opts.field_z == 0.0 and opts.near_cache == 0
+
+
+def test_checkpoint_round_trip_host_logic(tmp_path, monkeypatch):
+    """kmc_checkpoint stores positions, charges, the creation arguments and the step counter;
+    kmc_resume re-creates the handle from exactly those (the device calls are faked here)."""
+    import paper_1905_04065_gb300 as k
+
+    class Fake:
+        n = 3
+        init_args = dict(charges=np.array([1.0, -1.0, 0.0]), box=4.0, levels=3, order=8, precision="mixed",
+                         lattice_edge=4, lattice_h=1.0, kT=0.1, leaf_capacity=0, m2l="tensor", hops=14,
+                         bc="free", field_z=0.0, near_cache=True)
+    pos = np.array([[0.5, 0.5, 0.5], [1.5, 0.5, 0.5], [2.5, 3.5, 1.5]])
+    monkeypatch.setattr(k, "kmc_fmm_positions", lambda h: pos)
+    seen = {}
+
+    def fake_init(positions, charges, **kw):
+        seen.update(positions=np.array(positions), charges=np.array(charges), **kw)
+        return "handle"
+    monkeypatch.setattr(k, "kmc_fmm_init", fake_init)
+    path = str(tmp_path / "state.npz")
+    k.kmc_checkpoint(Fake(), path, step=123, seed=np.array([7, 8]))
+    h, step, extra = k.kmc_resume(path)
+    assert h == "handle" and step == 123 and extra["seed"].tolist() == [7, 8]
+    assert np.array_equal(seen["positions"], pos) and seen["charges"].tolist() == [1.0, -1.0, 0.0]
+    for key, v in Fake.init_args.items():
+        if key != "charges":
+            assert seen[key] == v, key

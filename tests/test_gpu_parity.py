@@ -489,3 +489,32 @@ def test_bounded_device_wait_gives_up_and_context_survives(small):
     dU_o, mask_o = st.propose()
     assert np.array_equal(mask, mask_o)
     assert _rel_err(dU, dU_o, mask_o) < TOL[8]
+
+
+@pytest.mark.parametrize("near_cache", [False, True])
+def test_checkpoint_resume_continues_the_trajectory(small, tmp_path, near_cache):
+    """40 device-driven steps in one go against 20 steps, a checkpoint, a new handle from it and
+    the next 20 uniforms: the same events and positions (the resumed far field differs from the
+    incrementally updated one by truncation only, far below the gaps the uniforms fall into),
+    energies within 1e-5."""
+    k = _k()
+    w, sites, q, _ = small
+    E, kT = w["E"], w["kT"]
+    u = workloads.uniforms(40, w["seed"] + 40)
+
+    def make():
+        return k.kmc_fmm_init(workloads.site_positions(E, sites), q, float(E), w["L"], 12, precision="fp64",
+                              lattice_edge=E, kT=kT, near_cache=near_cache)
+    h1 = make()
+    ev_all, _ = k.kmc_run(h1, u)
+    h2 = make()
+    ev_a, _ = k.kmc_run(h2, u[:20])
+    path = str(tmp_path / "ckpt.npz")
+    k.kmc_checkpoint(h2, path, step=20)
+    del h2
+    h3, step, _ = k.kmc_resume(path)
+    assert step == 20
+    ev_b, _ = k.kmc_run(h3, u[step:])
+    assert np.array_equal(np.concatenate([ev_a, ev_b]), ev_all)
+    assert np.array_equal(k.kmc_fmm_positions(h3), k.kmc_fmm_positions(h1))
+    assert abs(k.kmc_fmm_energy(h3) - k.kmc_fmm_energy(h1)) < 1e-5 * abs(k.kmc_fmm_energy(h1))
