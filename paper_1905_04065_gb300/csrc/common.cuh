@@ -183,6 +183,21 @@ struct Dev {
 #define KMC_DERR_BADPOS 4
 #define KMC_DERR_BADSITE 8
 #define KMC_DERR_TIMEOUT 16
+#define KMC_DERR_BOUNDS 32  // checked builds: an index failed its bounds check
+
+// Bounds checks compiled into checked builds (-DKMC_CHECKS; compute-sanitizer is
+// not available): KMC_IN(cond, err) is true in normal builds; in checked builds
+// it sets KMC_DERR_BOUNDS in *err when cond fails, and the guarded access is
+// skipped.  Usage: if (KMC_IN(i < n, d.err)) a[i] = v;
+#ifdef KMC_CHECKS
+__device__ __forceinline__ bool kmc_in(bool ok, int* err) {
+  if (!ok) atomicOr(err, KMC_DERR_BOUNDS);
+  return ok;
+}
+#define KMC_IN(cond, err) kmc_in((cond), (err))
+#else
+#define KMC_IN(cond, err) true
+#endif
 
 // Lattice mode keeps, beside the slot arrays, the charges of every leaf in
 // the layout the near-field kernel consumes: groups of four slots, 80 bytes

@@ -256,7 +256,7 @@ template <> struct NearField<double> {
   // sources [j0, j1) against the leaf-local targets t0 and t1 (t1 only when
   // two is set; warp-uniform)
   __device__ __forceinline__ void run2(const unsigned char* sm, const double* isq, int j0, int j1, bool two, int tx0,
-                                       int ty0, int tz0, int tx1, int ty1, int tz1) {
+                                       int ty0, int tz0, int tx1, int ty1, int tz1, int nisq, int* err) {
     const Src* src = (const Src*)sm;
     const float ax0 = (float)(-2 * tx0), ay0 = (float)(-2 * ty0), az0 = (float)(-2 * tz0);
     const float ax1 = (float)(-2 * tx1), ay1 = (float)(-2 * ty1), az1 = (float)(-2 * tz1);
@@ -267,10 +267,12 @@ template <> struct NearField<double> {
       const double q = src[j].q;
       // n = |s|^2 + |t|^2 - 2 s.t, exact; n + 2^23 holds n in its low mantissa bits
       const float n0 = fmaf(ax0, v.x, fmaf(ay0, v.y, fmaf(az0, v.z, v.w + w0)));
-      s0 = fma(q, isq[__float_as_int(n0 + 8388608.f) - 0x4B000000], s0);
+      const int k0 = __float_as_int(n0 + 8388608.f) - 0x4B000000;
+      if (KMC_IN(k0 >= 0 && k0 < nisq, err)) s0 = fma(q, isq[k0], s0);
       if (two) {
         const float n1 = fmaf(ax1, v.x, fmaf(ay1, v.y, fmaf(az1, v.z, v.w + w1)));
-        s1 = fma(q, isq[__float_as_int(n1 + 8388608.f) - 0x4B000000], s1);
+        const int k1 = __float_as_int(n1 + 8388608.f) - 0x4B000000;
+        if (KMC_IN(k1 >= 0 && k1 < nisq, err)) s1 = fma(q, isq[k1], s1);
       }
     }
     a0 = s0;
@@ -641,8 +643,10 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
     for (int j = lane; j < cnt_own; j += 32) {
       const V4 v = j < 32 ? pv[0] : spos[base_own + j];
       const int ls = (lattice_coord(v.x, ih) - gx0) + W * (lattice_coord(v.y, ih) - gy0 + W * (lattice_coord(v.z, ih) - gz0));
-      atomicOr(&bits[ls >> 5], 1u << (ls & 31));
-      atomicOr(&need[ls >> 5], 1u << (ls & 31));
+      if (KMC_IN(ls >= 0 && ls < W3, d.err)) {
+        atomicOr(&bits[ls >> 5], 1u << (ls & 31));
+        atomicOr(&need[ls >> 5], 1u << (ls & 31));
+      }
     }
   __syncthreads();
 
@@ -668,8 +672,10 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
         if (g.bc && (rx < 0 || rx >= E || ry < 0 || ry >= E || rz < 0 || rz >= E)) {
           if (e == 0) {  // free space: a hop out of the box is not a move
             const int32_t u = d.uid[mb + j];
-            d.mask[(int64_t)nhop * u + k] = 0;
-            out_new[(int64_t)nhop * u + k] = qnan<T>();
+            if (KMC_IN(u >= 0 && u < g.n, d.err)) {
+              d.mask[(int64_t)nhop * u + k] = 0;
+              out_new[(int64_t)nhop * u + k] = qnan<T>();
+            }
           }
           continue;
         }
@@ -677,10 +683,13 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
         int ux = tx - gx0, uy = ty - gy0, uz = tz - gz0;
         if (ux < 0 || ux >= W || uy < 0 || uy >= W || uz < 0 || uz >= W) continue;  // another leaf's CTA
         int lt = ux + W * (uy + W * uz);
+        if (!KMC_IN(lt >= 0 && lt < W3, d.err)) continue;
         if (bits[lt >> 5] & (1u << (lt & 31))) {
           const int32_t u = d.uid[mb + j];
-          d.mask[(int64_t)nhop * u + k] = 0;
-          out_new[(int64_t)nhop * u + k] = qnan<T>();
+          if (KMC_IN(u >= 0 && u < g.n, d.err)) {
+            d.mask[(int64_t)nhop * u + k] = 0;
+            out_new[(int64_t)nhop * u + k] = qnan<T>();
+          }
         } else {
           atomicOr(&need[lt >> 5], 1u << (lt & 31));
         }
@@ -718,7 +727,8 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
       // l = x + W (y + W z) by reciprocal multiplication: floor(l rW / 2^16)
       // = floor(l / W) for l < 2^16 / W (W <= 12, l < 1728)
       const int q1 = (l * rW) >> 16, z = (q1 * rW) >> 16;
-      sites[o++] = (uint16_t)((l - q1 * W) | ((q1 - z * W) << 4) | (z << 8));
+      if (KMC_IN(o < W3, d.err)) sites[o] = (uint16_t)((l - q1 * W) | ((q1 - z * W) << 4) | (z << 8));
+      o++;
       m &= m - 1;
     }
   }
@@ -744,6 +754,8 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
   // no sites: only the prefetch to drain; cached sums: no pairs (and no prefetch)
   const int npass = mode == PROP_CACHED ? 0 : (nsites ? misc[0] : 1);
   const int ks = misc[1];
+  for (int pass = 0; pass < npass; pass++)
+    (void)KMC_IN(nb_off[pq[pass + 1]] - nb_off[pq[pass]] <= (F32 ? chunk / 4 + 1 : chunk), d.err);
   const T scale = (T)ldexp(1.0, ks);
   for (int pass = 0; pass < npass; pass++) {
     const int q0 = pq[pass], q1 = pq[pass + 1];
@@ -829,10 +841,10 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
           nf.run_span((const float4*)src, u0, u1, nown, two, i2f(ix0), i2f(iy0), i2f(iz0), i2f(ix1), i2f(iy1),
                       i2f(iz1));
         } else {
-          nf.run2(src, isq, u0, u1, two, ix0, iy0, iz0, ix1, iy1, iz1);
+          nf.run2(src, isq, u0, u1, two, ix0, iy0, iz0, ix1, iy1, iz1, nisq, d.err);
         }
-        if (b0 < nsites) fixed_add(&acc[l0], nf.sum(0) * scale);
-        if (two && b1 < nsites) fixed_add(&acc[l1], nf.sum(1) * scale);
+        if (b0 < nsites && KMC_IN(l0 >= 0 && l0 < W3, d.err)) fixed_add(&acc[l0], nf.sum(0) * scale);
+        if (two && b1 < nsites && KMC_IN(l1 >= 0 && l1 < W3, d.err)) fixed_add(&acc[l1], nf.sum(1) * scale);
       }
     }
   }
@@ -843,6 +855,7 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
     for (int b = tid; b < nsites; b += blockDim.x) {
       const int sv = sites[b];
       const int l = (sv & 15) + W * (((sv >> 4) & 15) + W * (sv >> 8));
+      if (!KMC_IN(l >= 0 && l < W3 && W3 <= g.cap, d.err)) continue;
       const long long a = (long long)acc[l];
       dst[l] = sh >= 0 ? a * (1LL << sh) : (a + (1LL << (-sh - 1))) >> -sh;
     }
@@ -875,6 +888,7 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
       const int sv = sites[b];
       const int ix = sv & 15, iy = (sv >> 4) & 15, iz = sv >> 8;
       const int l = ix + W * (iy + W * iz);
+      if (!KMC_IN(l >= 0 && l < W3, d.err)) continue;
       const T near = cache ? (T)cache[l] * cback : (T)acc[l] * back;
       phis[l] = near + l2p_point<T, C>(Lc, g.p, (small_to<T>(ix) + (T)0.5 - hw) * h,
                                         (small_to<T>(iy) + (T)0.5 - hw) * h, (small_to<T>(iz) + (T)0.5 - hw) * h);
@@ -895,7 +909,11 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
       const int32_t u = pre ? (i == 0 ? wu[0] : wu[1]) : d.uid[mb + j];
       const V4 v = pre ? (i == 0 ? wv[0] : wv[1]) : spos[mb + j];
       const int gx = lattice_coord(v.x, ih), gy = lattice_coord(v.y, ih), gz = lattice_coord(v.z, ih);
-      if (e == 0) out_old[u] = phis[(gx - gx0) + W * ((gy - gy0) + W * (gz - gz0))];
+      if (!KMC_IN(u >= 0 && u < g.n, d.err)) continue;
+      if (e == 0) {
+        const int lo = (gx - gx0) + W * ((gy - gy0) + W * (gz - gz0));
+        if (KMC_IN(lo >= 0 && lo < W3, d.err)) out_old[u] = phis[lo];
+      }
       for (uint32_t hb = hm; hb; hb &= hb - 1) {
         const int k = __ffs(hb) - 1;
         const int rx = gx + hop_c(k, 0), ry = gy + hop_c(k, 1), rz = gz + hop_c(k, 2);
@@ -1308,7 +1326,7 @@ __global__ void k_move_from_event(const Geo g, const Dev d) {
   MoveRec mv;
   int64_t j = *d.event;
   mv.valid = 0;
-  if (j >= 0) {
+  if (j >= 0 && KMC_IN(j < (int64_t)g.nhop * g.n, d.err)) {
     int64_t i = j / g.nhop;
     int k = (int)(j - (int64_t)g.nhop * i);
     int E = g.E;
@@ -1694,6 +1712,7 @@ __device__ __forceinline__ void acc_fine_role(const Geo& g, const Dev& d, const 
 // move the charge between leaf slots; dipole, energy and bookkeeping
 __device__ __forceinline__ void acc_move_role(const Geo& g, const Dev& d, const MoveRec& mv) {
   int32_t i = mv.i;
+  if (!KMC_IN(i >= 0 && i < g.n, d.err)) return;
   int32_t so = d.slot_of[i];
   int64_t lo = so / g.cap;
   int ln = 0;
@@ -1701,6 +1720,7 @@ __device__ __forceinline__ void acc_move_role(const Geo& g, const Dev& d, const 
     int cx = cell_at(mv.rn[0], g.nL, g.inv_a), cy = cell_at(mv.rn[1], g.nL, g.inv_a), cz = cell_at(mv.rn[2], g.nL, g.inv_a);
     ln = cx + g.nL * (cy + g.nL * cz);
   }
+  if (!KMC_IN(so >= 0 && lo < g.ML && so - lo * g.cap < d.cnt[lo] && ln >= 0 && ln < g.ML, d.err)) return;
   // remove: move the leaf's last entry into the hole
   int64_t last = lo * g.cap + d.cnt[lo] - 1;
   if (last != so) {
@@ -1798,6 +1818,7 @@ __global__ void __launch_bounds__(128) k_near_update(const Geo g, const Dev d) {
   const int side = blockIdx.x / 27, o = blockIdx.x % 27;
   const int site = side ? mv.site_new : mv.site_old;
   const int E = g.E, W = g.W, nL = g.nL;
+  if (!KMC_IN(site < E * E * E && W * W * W <= g.cap, d.err)) return;
   const int sx = site % E, sy = (site / E) % E, sz = site / (E * E);
   const int Sx = sx / W, Sy = sy / W, Sz = sz / W;
   const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;

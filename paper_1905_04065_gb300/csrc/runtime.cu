@@ -137,6 +137,7 @@ static int check_flags(kmc_fmm* h, const char* where) {
   if (e[0] & KMC_DERR_SINGULAR)
     return fail(h, KMC_ERR_ARG, "%s: a target coincides with a charge (singular move)", where);
   if (e[0] & KMC_DERR_TIMEOUT) return fail(h, KMC_ERR_TIMEOUT, "%s: a device-side wait exceeded its limit", where);
+  if (e[0] & KMC_DERR_BOUNDS) return fail(h, KMC_ERR_STATE, "%s: an index failed its bounds check (checked build)", where);
   return fail(h, KMC_ERR_STATE, "%s: device error flags 0x%x", where, e[0]);
 }
 
