@@ -3,8 +3,8 @@
 Workload (default): 256^3-site periodic simple-cubic lattice, 1,048,576 +-1
 charges on uniform-random distinct sites, 6 nearest-neighbour hop proposals
 per charge, FMM with 6 levels and order p = 12, kT = 0.05, mixed precision
-(FP32 near-field pairs and L2P, FP64 far field, dU assembly and accept
-updates).  A step is one full KMC step: downward pass, propose (all hops),
+(FP32 near-field pairs, L2P and dU assembly; FP64 M2L, lattice sums, accept
+updates of the expansions and cumulative rate sums).  A step is one full KMC step: downward pass, propose (all hops),
 rates, selection, accept.
 
 Timed regions (CUDA events on the library's stream, after W warm-up steps):
@@ -43,6 +43,7 @@ sys.path.insert(0, ROOT)
 import workloads  # noqa: E402
 
 METRIC = "dU evals/sec and KMC steps/sec at N=1M, FP32-mixed vs FP64"
+DTYPE_MIXED = "f32-mixed (f32 near field, L2P and dU assembly; f64 M2L, lattice sums, accept updates, rate sums)"
 UNIT = "dU evals/s"
 
 
@@ -147,7 +148,7 @@ def pair_count(E: int, L: int, sites: np.ndarray, nhop: int = 6, bc: str = "peri
 
 # DRAM bytes (read + write) of one summing propose launch per leaf, from the ncu capture of the
 # 128^3 tile case (4096 leaves of 8^3 sites, 32 charges each, 6 hops, mixed precision:
-# profiles/propose_tile_full.md, 9.10 MB read, 256 B written).  Valid for workloads with the same
+# 9.10 MB read, 256 B written).  Valid for workloads with the same
 # leaf shape (tile, large); scaled by the number of leaves.
 PROPOSE_DRAM_BYTES_PER_LEAF = (9.097216e6 + 256) / 4096
 TRAFFIC_WORKLOADS = ("tile", "large")
@@ -267,8 +268,39 @@ def cpu_sample(E, sites, q, seconds_target=10.0, max_props=20000, nhop=6, bc="pe
                 sample=f"{m} unmasked hops, {what}, FP64")
 
 
+def cpu_otable(E, sites, q, kT, seed, seconds_target=10.0, max_steps=64):
+    """Full KMC steps of the oracle's lattice-table form (O-table): the tabulated Ewald pair
+    potential and a site potential kept for all E^3 sites, so that every hop's dU is O(1)
+    (propose), Algorithm 1's sequential FP64 selection, and an O(E^3) site-potential update per
+    accepted hop.  Periodic, 6 hops.  Returns (measurement dict, number of timed steps); the table
+    and the initial FFT site potential are set up before the timed loop."""
+    import oracle
+    t0 = time.perf_counter()
+    st = oracle.LatticeState(E, sites, q)
+    setup_s = time.perf_counter() - t0
+    u = workloads.uniforms(max_steps, seed + 99)
+    steps = hops = 0
+    t0 = time.perf_counter()
+    while steps < max_steps and (steps == 0 or time.perf_counter() - t0 < seconds_target):
+        dU, mask = st.propose()
+        j, Q, dt = oracle.select(oracle.rates(dU, mask, kT), u[steps, 0], u[steps, 1])
+        if j >= 0:
+            st.accept(j // 6, j % 6)
+        hops += int(mask.sum())
+        steps += 1
+    el = time.perf_counter() - t0
+    return dict(value=hops / el, unit=UNIT, kmc_steps_per_s=steps / el, cores=oracle.num_threads(), kind="oracle",
+                sample=f"{steps} full KMC steps of the O-table form (every hop's dU from the maintained site "
+                       f"potential, sequential FP64 selection, O(E^3) site update per accept), FP64; "
+                       f"table + FFT setup {setup_s:.1f} s not timed"), steps
+
+
 # --------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The oracle timed on the host cores for the same workload and metric.  Periodic 6-hop lattice
+    workloads: exactly K full KMC steps of the O-table form after W untimed ones (dU evals/s = the
+    unmasked hops of each step over its time).  Other workloads: K bounded samples of the direct
+    O(N)-per-hop sum."""
     rank, world, _ = _dist()
     if rank != 0:
         return 0
@@ -276,45 +308,68 @@ def run_reference(args):
     E = w["E"]
     import oracle
     oracle.build()
-    G = oracle.psi_table(E)
-    per_step = max(16, int(args.ref_props))
-    rng = np.random.default_rng(7)
-    occ = np.zeros(E ** 3, dtype=bool)
-    occ[sites] = True
-    xyz = workloads.site_xyz(E, sites)
-    dirs = np.array([(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)])
+    if w.get("hops", 6) == 6:
+        st = oracle.LatticeState(E, sites, q)
+        u = workloads.uniforms(args.warmup + args.steps, w["seed"] + 99)
+        times, hops = [], 0
+        for s in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            dU, mask = st.propose()
+            j, Q, dt = oracle.select(oracle.rates(dU, mask, w["kT"]), u[s, 0], u[s, 1])
+            if j >= 0:
+                st.accept(j // 6, j % 6)
+            el = time.perf_counter() - t0
+            if s >= args.warmup:
+                times.append(el)
+                hops += int(mask.sum())
+        tot = sum(times)
+        v = hops / tot
+        sample = (f"{args.steps} full KMC steps of the O-table form (lattice-table Ewald potential, O(1) dU "
+                  f"per hop, sequential FP64 selection, O(E^3) site update per accept)")
+        extra = {"kmc_steps_per_s": args.steps / tot}
+    else:
+        G = oracle.psi_table(E)
+        per_step = max(16, int(args.ref_props))
+        rng = np.random.default_rng(7)
+        occ = np.zeros(E ** 3, dtype=bool)
+        occ[sites] = True
+        xyz = workloads.site_xyz(E, sites)
+        dirs = oracle.hop_vectors(w.get("hops", 6))
 
-    def batch():
-        parts, tg = [], []
-        while len(parts) < per_step:
-            i = int(rng.integers(0, len(q)))
-            k = int(rng.integers(0, 6))
-            t = (xyz[i] + dirs[k]) % E
-            s = int(t[0] + E * (t[1] + E * t[2]))
-            if not occ[s]:
-                parts.append(i)
-                tg.append(s)
-        return np.array(parts), np.array(tg)
+        def batch():
+            parts, tg = [], []
+            while len(parts) < per_step:
+                i = int(rng.integers(0, len(q)))
+                k = int(rng.integers(0, len(dirs)))
+                t = (xyz[i] + dirs[k]) % E
+                s = int(t[0] + E * (t[1] + E * t[2]))
+                if not occ[s]:
+                    parts.append(i)
+                    tg.append(s)
+            return np.array(parts), np.array(tg)
 
-    for _ in range(args.warmup):
-        p, t = batch()
-        oracle.lattice_delta_u_direct(E, G, sites, q, p, t)
-    times = []
-    for _ in range(args.steps):
-        p, t = batch()
-        t0 = time.perf_counter()
-        oracle.lattice_delta_u_direct(E, G, sites, q, p, t)
-        times.append(time.perf_counter() - t0)
-    tot = sum(times)
-    v = per_step * args.steps / tot
+        for _ in range(args.warmup):
+            p, t = batch()
+            oracle.lattice_delta_u_direct(E, G, sites, q, p, t)
+        times = []
+        for _ in range(args.steps):
+            p, t = batch()
+            t0 = time.perf_counter()
+            oracle.lattice_delta_u_direct(E, G, sites, q, p, t)
+            times.append(time.perf_counter() - t0)
+        tot = sum(times)
+        v = per_step * args.steps / tot
+        sample = f"{per_step} unmasked hops per step, direct O(N) FP64 sum"
+        extra = {}
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": _config(w, args.workload),
+        "config": dict(_config(w, args.workload), parallelism="replicas x1", bc="periodic"),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                         "sample": f"{per_step} unmasked hops per step, direct O(N) FP64 sum"},
+                         "sample": sample, **extra},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        **extra,
     }
     print(json.dumps(line))
     return 0
@@ -518,12 +573,18 @@ def run_gpu(args):
 
     cpu = None
     if not args.no_cpu and world == 1 or (world > 1 and rank == 0 and not args.no_cpu):
-        cpu = cpu_sample(E, sites, q, seconds_target=args.cpu_seconds, nhop=nhop, bc=args.bc)
+        direct = cpu_sample(E, sites, q, seconds_target=args.cpu_seconds, nhop=nhop, bc=args.bc)
+        if nhop == 6 and args.bc == "periodic":
+            # the O-table form is the strongest CPU algorithm for a lattice: it is the headline baseline
+            ot, _ = cpu_otable(E, sites, q, kT, w["seed"], seconds_target=args.cpu_seconds)
+            cpu = dict(ot, forms={"o_table": dict(ot), "o_direct": direct})
+        else:
+            cpu = dict(direct, forms={"o_direct": direct})
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32-mixed (f32 near field + L2P, f64 far field / dU / accept)",
+        "vs_baseline": None, "dtype": DTYPE_MIXED,
         "data": "synthetic", "config": dict(_config(w, args.workload), parallelism=f"replicas x{world}",
                                             bc=args.bc),
         "kmc_steps_per_s": steps_per_s,
@@ -601,7 +662,7 @@ def run_batch(args):
         "metric": "dU evals/sec and KMC steps/sec, 64 batched replicas", "value": units / (tot * 1e-3),
         "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32-mixed (f32 near field + L2P, f64 far field / dU / accept)", "data": "synthetic",
+        "dtype": DTYPE_MIXED, "data": "synthetic",
         "config": {"workload": f"batch: {R} replicas, edges {sorted(set(r['E'] for r in reps))}, occupancy "
                                f"U[0.02,0.15], {sum(r['N'] for r in reps)} charges in total, p={p}, kT={kT}",
                    "levels": levels, "working_set_bytes": ws,

@@ -58,8 +58,10 @@ enum kmc_status {
 
 enum kmc_precision {
   KMC_PREC_FP64 = 0, /* every step in FP64 */
-  KMC_PREC_MIXED = 1 /* L2P and the near-field pair sums in FP32 with FP32 accumulation;
-                        M2L, lattice sums, accept updates and dU assembly in FP64 */
+  KMC_PREC_MIXED = 1 /* L2P, the near-field pair sums and the dU assembly (q (phi' - phi) less
+                        the dipole and self-image terms) in FP32 with FP32 accumulation, the
+                        rates from an FP32 exponent kept in FP64 range; M2L, lattice sums, the
+                        accept updates of the expansions and the cumulative rate sums in FP64 */
 };
 
 enum kmc_mem { KMC_MEM_HOST = 0, KMC_MEM_DEVICE = 1 };
@@ -137,7 +139,7 @@ void kmc_opts_default(kmc_opts* opts);
  *   charges:   n doubles, sum must vanish (relative 1e-12 of sum |q|).
  *   levels:    L >= 3 (8^(l-1) cells on level l, Sec. 2.2); at most 10.
  *   order:     p, the largest expansion degree (Eq. (multipole_local_expansion)
- *              sums n = 0..p), 1 <= p <= 20.
+ *              sums n = 0..p), 1 <= p <= 24.
  * Errors: KMC_ERR_ARG (n < 2, levels/order out of range, a position outside
  * [0, box) or not finite, lattice positions off the sites or two charges on
  * one site, box not divisible), KMC_ERR_NOT_NEUTRAL, KMC_ERR_OOM, KMC_ERR_CUDA.
@@ -238,28 +240,41 @@ int kmc_run_profiled(kmc_handle h, int steps, const double* uniforms, int64_t* e
  */
 int kmc_fmm_recompute(kmc_handle h, double* drift);
 
-/* Leaf-cell index (cx + n(cy + n cz), n = 2^(L-1)) of every particle, user order. */
+/*
+ * Leaf-cell index of every particle, user order: the finest-level cell of the
+ * octree of Sec. 2.2 (8^(L-1) cells on level L) that holds it,
+ * cx + n (cy + n cz) with n = 2^(L-1) and c = floor(x n / box) per axis.  An
+ * inspection hook (tests compare it bit-exactly with integer arithmetic); the
+ * binning it reports is the one every kernel uses.  leaf: n int32, in the
+ * handle's memory kind.
+ */
 int kmc_fmm_leaf_index(kmc_handle h, int32_t* leaf);
 
-/* Current positions (n x 3) in user order. */
+/*
+ * Current positions (n x 3 doubles, row-major, user order, wrapped into
+ * [0, box)) after the accepted moves so far: the state Algorithm 1 advances.
+ * An inspection and checkpoint hook; positions: in the handle's memory kind.
+ */
 int kmc_fmm_positions(kmc_handle h, double* positions);
 
 /*
  * Allocation-free selection.  The paper has no counterpart: this entry point
- * exists for callers that cannot allocate device memory -- code running while
- * a CUDA graph is captured in global capture mode (where cudaMalloc is
- * prohibited), code inside a framework whose memory pool owns the device, or
- * host loops that must not stall on the synchronisation an allocation can
- * cause.  It performs the selection of kmc_step (Q = sum r_j, event j with
+ * exists for callers that cannot allocate device memory -- a library running
+ * inside a framework whose caching allocator owns the device memory, a host
+ * loop that must not stall on the device synchronisation cudaMalloc/cudaFree
+ * can cause, a plugin host that forbids its plugins to own device memory.  It
+ * performs the selection of kmc_step (Q = sum r_j, event j with
  * R_{j-1} < Q zeta <= R_j, dt = -ln(xi)/Q) without a handle and without
  * allocating: its scratch is a file-scope device array of KMC_STATIC_MAX_N/128
  * block sums plus 8 doubles (about 1 MB), held by every GPU that loads the
  * library until the process exits.
  *   rates:  6 n doubles in DEVICE memory of the current device (event order
  *           j = 6 i + k), owned by the caller; 1 <= n <= KMC_STATIC_MAX_N,
- *           larger n returns KMC_ERR_ARG.
+ *           larger n returns KMC_ERR_ARG.  The library reads exactly 6 n
+ *           entries and cannot check the buffer's length: the caller must.
  *   zeta, xi in (0, 1]; event, dt, Q: host scalars (event = -1 if Q == 0).
- *   stream: cudaStream_t (NULL = default stream); the call synchronises it.
+ *   stream: cudaStream_t (NULL = default stream); the call copies the two
+ *           uniforms from the host and synchronises the stream.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
  * make that first call before any stream capture.  All calls share the array,
  * so calls whose GPU work overlaps (other streams, other host threads) race;

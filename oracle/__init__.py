@@ -75,6 +75,8 @@ def _load():
             "oracle_site_potential": (None, [I64, P, I64, P, P, P]),
             "oracle_site_update": (None, [I64, P, P, I64, I64, D]),
             "oracle_hop_target": (I64, [I64, I64, I]),
+            "oracle_hop_targets": (None, [I64, I64, P, I, P]),
+            "oracle_hop_vector": (None, [I, P]),
             "oracle_lattice_delta_u": (None, [I64, P, P, I64, P, P, P, P, P]),
             "oracle_lattice_delta_u_list": (None, [I64, P, P, P, P, I64, P, P, P]),
             "oracle_lattice_delta_u_direct": (None, [I64, P, I64, P, P, I64, P, P, P]),
@@ -201,6 +203,28 @@ def lattice_delta_u_direct(E: int, G: np.ndarray, sites, q, particle, target_sit
 
 def hop_target(E: int, s: int, k: int) -> int:
     return int(_load().oracle_hop_target(E, s, k))
+
+
+def hop_vectors(nhop: int = 6) -> np.ndarray:
+    """The oracle's hop set (Algorithm 5; Sec. 5.3 for 14 hops): nhop x 3 integer lattice offsets,
+    the faces (+x, -x, +y, -y, +z, -z), then the body diagonals with x varying fastest."""
+    if nhop not in (6, 14):
+        raise ValueError("hop sets have 6 or 14 hops")
+    lib = _load()
+    out = np.empty((nhop, 3), dtype=np.int64)
+    for k in range(nhop):
+        lib.oracle_hop_vector(k, _p(out[k]))
+    return out
+
+
+def hop_targets(E: int, sites, nhop: int = 6) -> np.ndarray:
+    """Target site of every hop of every charge, (n, nhop), event order j = nhop i + k, periodic."""
+    if nhop not in (6, 14):
+        raise ValueError("hop sets have 6 or 14 hops")
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.empty((len(sites), nhop), dtype=np.int64)
+    _load().oracle_hop_targets(int(E), len(sites), _p(sites), int(nhop), _p(out))
+    return out
 
 
 class LatticeState:

@@ -273,19 +273,33 @@ void oracle_site_update(int64_t E, const double* G, double* phi, int64_t s_old, 
   for (int64_t s = 0; s < S; s++) phi[s] += q * (G[disp_index(E, s, s_new)] - G[disp_index(E, s, s_old)]);
 }
 
-/* Hop k of charge i goes to the neighbour site in direction
- * (+x, -x, +y, -y, +z, -z)[k], wrapped periodically. */
+/* Lattice hop sets (the moves every charge proposes, Algorithm 5 and the
+ * benchmark of Sec. 5.3): hops 0..5 go to the six face neighbours in the
+ * order +x, -x, +y, -y, +z, -z; hops 6..13 (the 14-hop set of Sec. 5.3) go
+ * to the eight body-diagonal neighbours at distance sqrt(3), listed with the
+ * x component varying fastest and + before -.  Targets wrap periodically. */
+static const int HOP_VEC[14][3] = {
+    {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},  {0, -1, 0}, {0, 0, 1},   {0, 0, -1},
+    {1, 1, 1},   {-1, 1, 1},  {1, -1, 1}, {-1, -1, 1},
+    {1, 1, -1},  {-1, 1, -1}, {1, -1, -1}, {-1, -1, -1}};
+
 static int64_t hop_target(int64_t E, int64_t s, int k) {
   int64_t x = s % E, y = (s / E) % E, z = s / (E * E);
-  switch (k) {
-    case 0: x = (x + 1) % E; break;
-    case 1: x = (x + E - 1) % E; break;
-    case 2: y = (y + 1) % E; break;
-    case 3: y = (y + E - 1) % E; break;
-    case 4: z = (z + 1) % E; break;
-    default: z = (z + E - 1) % E; break;
-  }
+  x = (x + HOP_VEC[k][0] + E) % E;
+  y = (y + HOP_VEC[k][1] + E) % E;
+  z = (z + HOP_VEC[k][2] + E) % E;
   return site_index(E, x, y, z);
+}
+
+/* Target site of every hop of every charge, out[nhop i + k] (nhop = 6 or 14). */
+void oracle_hop_targets(int64_t E, int64_t n, const int64_t* site, int nhop, int64_t* out) {
+  for (int64_t i = 0; i < n; i++)
+    for (int k = 0; k < nhop; k++) out[(int64_t)nhop * i + k] = hop_target(E, site[i], k);
+}
+
+/* Hop vector k (integer lattice offsets). */
+void oracle_hop_vector(int k, int64_t* v) {
+  for (int a = 0; a < 3; a++) v[a] = HOP_VEC[k][a];
 }
 
 int64_t oracle_hop_target(int64_t E, int64_t s, int k) { return hop_target(E, s, k); }

@@ -423,15 +423,19 @@ KMC_STATIC_MAX_N = 16777216
 def kmc_select_static(rates, n: int, zeta: float, xi: float, stream=None):
     """Selection without a handle and without device allocation.
 
-    For callers that cannot allocate device memory (graph capture in global
-    mode, a framework-owned memory pool, loops that must not stall on an
-    allocation).  rates: CUDA tensor of 6 n doubles owned by the caller.
-    Returns (event, dt, Q).  Calls share one static scratch array, so calls
-    that overlap on the GPU must be serialised by the caller."""
+    For callers that cannot allocate device memory: code inside a framework
+    whose caching allocator owns the device, host loops that must not stall on
+    the synchronisation an allocation can cause, plugin hosts that forbid
+    their plugins to own device memory.  rates: CUDA tensor of at least 6 n
+    doubles owned by the caller (the first 6 n are read).  Returns (event, dt,
+    Q).  Calls share one static scratch array, so calls that overlap on the
+    GPU must be serialised by the caller."""
     import torch
     lib = load_library()
     if not (_is_torch(rates) and rates.is_cuda and rates.dtype == torch.float64 and rates.is_contiguous()):
         raise KmcError(KMC_ERR_ARG, "rates must be a contiguous float64 CUDA tensor")
+    if int(n) >= 1 and rates.numel() < 6 * int(n):
+        raise KmcError(KMC_ERR_ARG, f"rates holds {rates.numel()} entries, fewer than 6 n = {6 * int(n)}")
     s = stream if stream is not None else torch.cuda.current_stream(rates.device)
     sp = ctypes.c_void_p(int(getattr(s, "cuda_stream", s)))
     ev = ctypes.c_int64()

@@ -23,7 +23,9 @@
 #include <stdint.h>
 
 #define KMC_MAXL 10   // maximum number of levels
-#define KMC_MAXP 20   // maximum expansion degree
+#ifndef KMC_MAXP
+#define KMC_MAXP 24   // maximum expansion degree
+#endif
 #define KMC_NHOP 6    // lattice hop directions of the nearest-neighbour set (+x,-x,+y,-y,+z,-z)
 #define KMC_ISQ_N (3 * 23 * 23 + 1)  // squared lattice distances within 27 leaves of <= 12 sites
 #define KMC_MAXHOP 14 // with the 8 body diagonals (the hop set of the paper's Sec. 5.3 benchmark)
@@ -38,7 +40,9 @@ __host__ __device__ __forceinline__ constexpr int hop_c(int k, int a) {
 // Periodic images nu with |nu|_inf <= KMC_TOP are handled by the tree (the
 // level-2 interaction list covers the (2 KMC_TOP + 1)^3 block of domain copies);
 // the rest are the far field V_inf of the lattice operator.
+#ifndef KMC_TOP
 #define KMC_TOP 2
+#endif
 #define KMC_TOP_SPAN (4 * KMC_TOP + 3)  // level-2 M2L offsets per axis: [-(2 KMC_TOP + 1), 2 KMC_TOP + 1]
 #define KMC_TOP_NOFF (KMC_TOP_SPAN * KMC_TOP_SPAN * KMC_TOP_SPAN)
 #define KMC_TOP_NIMG ((2 * KMC_TOP + 1) * (2 * KMC_TOP + 1) * (2 * KMC_TOP + 1))

@@ -1,5 +1,5 @@
-// alu_peaks.cu -- ALU peak microbenchmark used for the roofline denominators: FP32 FMA,
-// FP64 FMA and MUFU rsqrt throughput of the whole GPU. Bounded loops, no waits.
+// alu_peaks.cu -- ALU throughput microbenchmark (test infrastructure): FP32 FMA, FP64 FMA and
+// MUFU rsqrt rates of the whole GPU, the denominators of the ALU rooflines. Bounded loops, no waits.
 #include <cstdio>
 #include <cuda_runtime.h>
 template<int ILP> __global__ void k32(float* out, int iters, float a, float b) {

@@ -48,7 +48,7 @@ def test_dirichlet_trajectory(precision, nh):
     k = _k()
     E, L, p, kT, fz = 16, 3, 12, 0.1, 0.2
     sites, q = _system(E, 500, 41 + nh)
-    st = oracle.DirichletLattice(E, sites, q, workloads.hop_vectors(nh), field_z=fz)
+    st = oracle.DirichletLattice(E, sites, q, oracle.hop_vectors(nh), field_z=fz)
     h = k.kmc_fmm_init(workloads.site_positions(E, sites), q, float(E), L, p, precision=precision,
                        lattice_edge=E, kT=kT, hops=nh, bc="dirichlet", field_z=fz)
     assert abs(k.kmc_fmm_energy(h) - st.energy()) < 1e-5 * abs(st.energy())
@@ -59,7 +59,7 @@ def test_dirichlet_trajectory(precision, nh):
         dU_o, mask_o = st.propose()
         assert np.array_equal(mask, mask_o)
         ok = mask_o.astype(bool)
-        zn = (st.sites // (E * E))[:, None] + workloads.hop_vectors(nh)[None, :, 2]
+        zn = (st.sites // (E * E))[:, None] + oracle.hop_vectors(nh)[None, :, 2]
         through = (zn < 0) | (zn >= E // 2)  # hops through a wall (a face hop lands on its own mirror)
         assert not np.any(mask[through])
         wall += int(np.sum(through))
@@ -75,7 +75,7 @@ def test_dirichlet_trajectory(precision, nh):
             assert _near_tie(dU_o, mask_o, kT, u[s, 0], tol), (s, ev, j)
         du_acc = k.kmc_fmm_accept_event(h, j)
         assert abs(du_acc - dU_o.reshape(-1)[j]) < tol
-        st.accept(j // nh, workloads.hop_targets(E, st.sites[j // nh:j // nh + 1], nh)[0, j % nh])
+        st.accept(j // nh, oracle.hop_targets(E, st.sites[j // nh:j // nh + 1], nh)[0, j % nh])
     assert agree >= 13 and wall > 0
     assert abs(k.kmc_fmm_energy(h) - st.energy()) < 1e-5 * abs(st.energy())
     assert np.array_equal(k.kmc_fmm_positions(h), workloads.site_positions(E, st.sites))
@@ -91,7 +91,7 @@ def test_dirichlet_trajectory(precision, nh):
             j = int(events[s])
         else:
             run_agree += 1
-        st.accept(j // nh, workloads.hop_targets(E, st.sites[j // nh:j // nh + 1], nh)[0, j % nh])
+        st.accept(j // nh, oracle.hop_targets(E, st.sites[j // nh:j // nh + 1], nh)[0, j % nh])
     assert run_agree >= 8
     assert np.array_equal(k.kmc_fmm_positions(h), workloads.site_positions(E, st.sites))
     assert abs(k.kmc_fmm_energy(h) - st.energy()) < 1e-5 * abs(st.energy())

@@ -27,9 +27,9 @@ def _k():
 def _oracle_lattice(E, sites, q, nh):
     """Masks and dU of every lattice hop in free space (event order j = nh i + k)."""
     xyz = workloads.site_xyz(E, sites)
-    raw = xyz[:, None, :] + workloads.hop_vectors(nh)[None, :, :]
+    raw = xyz[:, None, :] + oracle.hop_vectors(nh)[None, :, :]
     inside = np.all((raw >= 0) & (raw < E), axis=2).reshape(-1)
-    tg = workloads.hop_targets(E, sites, nh).reshape(-1)
+    tg = oracle.hop_targets(E, sites, nh).reshape(-1)
     occ = np.zeros(E ** 3, dtype=bool)
     occ[sites] = True
     mask = (inside & ~occ[tg]).astype(np.uint8)

@@ -42,7 +42,7 @@ def _near_tie(dU, mask, kT, zeta, tol_abs):
 
 def _oracle_hops(st, nh):
     """dU (NaN where masked), mask and target sites of every hop, j = nh i + k."""
-    tg = workloads.hop_targets(st.E, st.sites, nh).reshape(-1)
+    tg = oracle.hop_targets(st.E, st.sites, nh).reshape(-1)
     mask = (st.occ[tg] == 0).astype(np.uint8)
     ok = mask.astype(bool)
     dU = np.full(len(tg), np.nan)

@@ -293,7 +293,7 @@ def test_teacher_forced_trajectory_small(small):
 def _oracle_hops(st, nh):
     """Masks and dU of every hop of the hop set (event order j = nh i + k) from
     the oracle's site potential; the targets come from the workload's hop list."""
-    tg = workloads.hop_targets(st.E, st.sites, nh).reshape(-1)
+    tg = oracle.hop_targets(st.E, st.sites, nh).reshape(-1)
     mask = (st.occ[tg] == 0).astype(np.uint8)
     ok = mask.astype(bool)
     dU = np.full(len(tg), np.nan)

@@ -2,20 +2,23 @@
 lattice workloads, in the configuration the benchmark times.
 
 medium (64^3 sites, 32768 charges, L=4, p=12): every dU of every step of a
-teacher-forced trajectory (the oracle's event is accepted on both sides), with
-a full recompute every 100 steps to measure the accept-update drift.
+1000-step teacher-forced trajectory (the oracle's event is accepted on both
+sides), with a full recompute every 100 steps to measure the accept-update
+drift, in the FP64 and the mixed form.
 
 large (256^3 sites, 1,048,576 charges, L=6, p=12, mixed precision -- the
 benchmark's launch configuration): every dU and mask of one propose against
 the oracle's lattice table, plus a sample of the oracle's own O(N) direct sum.
 
-Tolerances follow the truncation error at p = 12, stated against max |dU|:
-the bulk of the distribution is tight (99th percentile below 1e-5, mean ~1e-6;
-Sec. 5.1 Tab. 2 reports a mean relative error of ~9e-5 at p = 12 in its own
-metric), while the largest errors, ~1.5e-4, belong to charges that sit on a
-corner shared by the cells of every level, where the truncation errors of all
-levels' M2L translations reach their maximum together.  Masks and selected
-events are compared exactly (events except near ties)."""
+Tolerances at p = 12 are the measured truncation error, stated against
+max |dU| (the targets 1e-6 FP64 / 1e-4 mixed are asserted at the orders that
+meet them in test_gpu_contract.py).  The bulk of the distribution is tight
+(99th percentile below 1e-5, mean ~5e-7); the largest errors belong to hops
+across the boundary of a level-2 or level-3 cell, where the truncation errors
+of those levels' M2L translations between distance-two cells do not cancel
+between the old and the new site: 8e-5 on the medium workload (so the mixed
+form meets its 1e-4 target there), 1.55e-4 on the large one.  Masks and
+selected events are compared exactly (events except near ties)."""
 import numpy as np
 import pytest
 
@@ -24,7 +27,8 @@ import workloads
 
 pytestmark = pytest.mark.gpu
 
-TOL12 = 2.5e-4    # max over all hops, p = 12
+TOL12 = 2.5e-4    # max over all hops, p = 12, large workload (measured 1.55e-4)
+TOL12_MEDIUM = 1e-4  # max over all hops, p = 12, medium workload (measured 8.3e-5 over 1000 steps)
 TOL12_P99 = 1e-5  # 99th percentile, p = 12
 
 
@@ -46,7 +50,7 @@ def test_medium_teacher_forced_with_recompute(precision):
     k = _k()
     w, sites, q = workloads.workload("medium")
     E, L, p, kT = w["E"], w["L"], w["p"], w["kT"]
-    steps = 300 if precision == "fp64" else 1000
+    steps = 1000
     st = oracle.LatticeState(E, sites, q)
     h = k.kmc_fmm_init(workloads.site_positions(E, sites), q, float(E), L, p, precision=precision,
                        lattice_edge=E, kT=kT)
@@ -60,12 +64,12 @@ def test_medium_teacher_forced_with_recompute(precision):
         e = np.abs(dU - dU_o)[mask_o.astype(bool)] / scale
         err = e.max()
         worst = max(worst, err)
-        assert err < TOL12, (s, err)
+        assert err < TOL12_MEDIUM, (s, err)
         assert np.quantile(e, 0.99) < TOL12_P99, s
         ev, dt, Q = k.kmc_step(h, None, u[s, 0], u[s, 1])
         j, Q_o, dt_o = oracle.select(oracle.rates(dU_o, mask_o, kT), u[s, 0], u[s, 1])
         if ev != j:
-            assert _near_tie(dU_o, mask_o, kT, u[s, 0], TOL12 * scale), (s, ev, j)
+            assert _near_tie(dU_o, mask_o, kT, u[s, 0], TOL12_MEDIUM * scale), (s, ev, j)
             ties += 1
         k.kmc_fmm_accept_event(h, j)
         st.accept(j // 6, j % 6)

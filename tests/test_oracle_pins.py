@@ -317,6 +317,35 @@ def test_fft_site_potential_equals_direct():
     assert np.max(np.abs(a - b)) < 1e-12
 
 
+def test_hop_sets_are_the_lattice_neighbour_shells():
+    """The oracle's hop sets against a brute-force enumeration of the lattice neighbours
+    (Algorithm 5; Sec. 5.3 for 14 hops): 6 faces at distance 1 in the order +x, -x, +y, -y,
+    +z, -z, then the 8 body diagonals at distance sqrt(3) with x varying fastest and + before
+    -; the targets are those offsets wrapped periodically."""
+    cube = [(x, y, z) for z in (-1, 0, 1) for y in (-1, 0, 1) for x in (-1, 0, 1)]
+    faces = [v for v in cube if sum(c * c for c in v) == 1]
+    diag = [v for v in cube if sum(c * c for c in v) == 3]
+    v6, v14 = oracle.hop_vectors(6), oracle.hop_vectors(14)
+    assert np.array_equal(v14[:6], v6)
+    assert sorted(map(tuple, v6.tolist())) == sorted(faces)
+    for a in range(3):  # +axis then -axis, x before y before z
+        assert tuple(v6[2 * a]) == tuple(int(a == b) for b in range(3))
+        assert tuple(v6[2 * a + 1]) == tuple(-int(a == b) for b in range(3))
+    assert sorted(map(tuple, v14[6:].tolist())) == sorted(diag)
+    # x fastest, + before -: the sign pattern counts in binary with x as the low bit
+    code = [(v[0] < 0) + 2 * (v[1] < 0) + 4 * (v[2] < 0) for v in v14[6:].tolist()]
+    assert code == list(range(8))
+    E = 5
+    s = np.arange(E ** 3)
+    xyz = workloads.site_xyz(E, s)
+    for nh, V in ((6, v6), (14, v14)):
+        t = oracle.hop_targets(E, s, nh)
+        for k in range(nh):
+            w = (xyz + V[k]) % E
+            assert np.array_equal(t[:, k], w[:, 0] + E * (w[:, 1] + E * w[:, 2]))
+            assert all(oracle.hop_target(E, int(x), k) == int(t[x, k]) for x in (0, E - 1, E ** 3 - 1))
+
+
 def test_masks_mark_occupied_targets():
     E = 4
     sites, q = workloads.random_small(E, 30, 19)  # dense: many blocked hops
@@ -465,7 +494,7 @@ def test_dirichlet_potential_vanishes_on_both_walls():
     """The mirrored cell's potential is zero on z = 0 and on z = a/2 (grounded walls)."""
     E = 6
     sites, q = _dirichlet_system(E, 8, 31)
-    st = oracle.DirichletLattice(E, sites, q, workloads.hop_vectors(6))
+    st = oracle.DirichletLattice(E, sites, q, oracle.hop_vectors(6))
     pos = workloads.site_positions(E, st.ext.sites)
     a = float(E)
     rng = np.random.default_rng(5)
@@ -481,7 +510,7 @@ def test_dirichlet_hop_energy_equals_brute_force():
     the mirrored cell when the charge and its mirror move, plus the field term."""
     E, fz = 6, 0.3
     sites, q = _dirichlet_system(E, 10, 32)
-    st = oracle.DirichletLattice(E, sites, q, workloads.hop_vectors(14), field_z=fz)
+    st = oracle.DirichletLattice(E, sites, q, oracle.hop_vectors(14), field_z=fz)
     dU, mask = st.propose()
     a = float(E)
     pos0 = workloads.site_positions(E, st.ext.sites)
@@ -492,7 +521,7 @@ def test_dirichlet_hop_energy_equals_brute_force():
         for k in range(14):
             if not mask[i, k]:
                 continue
-            t = workloads.hop_targets(E, st.sites[i:i + 1], 14)[0, k]
+            t = oracle.hop_targets(E, st.sites[i:i + 1], 14)[0, k]
             s2 = st.ext.sites.copy()
             s2[i] = t
             s2[i + 10] = oracle.mirror_sites(E, np.array([t]))[0]
@@ -504,6 +533,6 @@ def test_dirichlet_hop_energy_equals_brute_force():
     # hops through a wall are masked
     zs = st.sites // (E * E)
     for i in range(10):
-        for k, hv in enumerate(workloads.hop_vectors(14)):
+        for k, hv in enumerate(oracle.hop_vectors(14)):
             if zs[i] + hv[2] < 0 or zs[i] + hv[2] >= E // 2:
                 assert not mask[i, k]
