@@ -159,6 +159,75 @@ def l2p_flops(p: int) -> int:
     return 8 * (p + 1) * (p + 2) // 2
 
 
+def l2l_cmacs(p: int) -> int:
+    """Complex multiply-adds of one L2L translation (parent to child, degree p, outputs 0 <= m <= n):
+    out(k, l) = sum_{n >= k} sum_m L(n, m) R(n - k, m - l) over the m the child table holds."""
+    tot = 0
+    for k in range(p + 1):
+        for lo in range(k + 1):
+            for n in range(k, p + 1):
+                j = n - k
+                tot += min(lo + j, n) - max(lo - j, -n) + 1
+    return tot
+
+
+def phase_rooflines(work: dict, phases: dict, E: int, L: int, N: int, p: int, nhop: int, peaks: dict,
+                    nsm: int, mixed: bool = True) -> dict:
+    """Roofline of every per-step phase (ms per step from the library's events), from the
+    algorithmic work of the phase: the operations or bytes the method needs, not what the
+    kernels issue.  Peaks: HBM from MEASURED_PEAKS.json; FP32 and FP64 FMA from unit counts
+    (128 and 2 FMA per clock per SM) at the maximum SM clock."""
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    hbm = float(peaks["hbm_gbs"]) * 1e9
+    fp32 = 2 * 128 * nsm * sm_max
+    fp64 = 2 * 2 * nsm * sm_max
+    P = (p + 1) * (p + 2) // 2
+    cells = sum(8 ** (l - 1) for l in range(2, L + 1))
+    parents = sum(8 ** (l - 2) for l in range(2, L + 1))
+    ts = 4 if mixed else 8  # bytes of a real coefficient in the downward pass's precision
+    out = {}
+    # downward: L2L of every cell of levels 2..L from its parent plus its own list expansion
+    fl = 8 * l2l_cmacs(p) * cells
+    by = cells * P * 2 * ts * 2 + parents * P * 2 * ts  # own + write, parent once
+    t = phases["downward"] * 1e-3
+    out["downward"] = {"kernels": "k_downward_root, k_downward_cell (levels < 512 parents), k_downward_par",
+                       "bound": "alu", "unit": "TFLOP/s", "achieved": fl / t / 1e12,
+                       "peak": (fp32 if mixed else fp64) / 1e12, "frac": fl / t / (fp32 if mixed else fp64),
+                       "work": f"{fl:.3e} {'FP32' if mixed else 'FP64'} flops ({l2l_cmacs(p)} complex MACs per cell, "
+                               f"{cells} cells); {by / 1e6:.1f} MB",
+                       "hbm_frac": by / t / hbm,
+                       "note": "L levels launched in sequence; the per-parent kernel reads its operands from "
+                               "shared memory (the binding unit), the coarse levels are latency-bound"}
+    # rates: per charge q, site, phi_old, nhop (phi_new, mask) read; nhop (dU, rate) written
+    b_rates = N * (4 + 4 + ts + nhop * (ts + 1) + nhop * (ts + 8))
+    t = phases["rates"] * 1e-3
+    out["rates"] = {"kernels": "k_finalize", "bound": "hbm", "unit": "GB/s", "achieved": b_rates / t / 1e9,
+                    "peak": hbm / 1e9, "frac": b_rates / t / hbm,
+                    "work": f"{b_rates / 1e6:.1f} MB ({b_rates / N:.0f} B per charge)"}
+    # select: the block sums and one block's rates
+    nb = (N + 127) // 128
+    b_sel = nb * 8 + 128 * nhop * 8
+    t = phases["select"] * 1e-3
+    out["select"] = {"kernels": "k_select, k_record", "bound": "latency", "unit": "GB/s",
+                     "achieved": b_sel / t / 1e9, "peak": hbm / 1e9, "frac": b_sel / t / hbm,
+                     "work": f"{b_sel / 1e3:.0f} kB: {nb} block sums and one block of rates",
+                     "note": "one CTA walks the cumulative sums: a chain of dependent reductions"}
+    # accept: FP64 P2L of the move (two positions) into every cell whose interaction list holds an
+    # image of them -- levels 2 (all images of the 5^3 block), 3 (27 images), >= 4 (<= 432
+    # candidate cells) -- the multipole changes of all levels, H += R dK, and the slot move
+    nl = 2 * (8 * 250 + 64 * 54) + 2 * 189 * max(L - 3, 0)  # P2L evaluations (upper estimate)
+    fl_acc = nl * P * 8 * 2 + L * P * 8 * 2 + P * P * 8
+    b_acc = (8 + 64 + 432 * max(L - 3, 0)) * P * (16 * 2 + 8)
+    t = phases["accept"] * 1e-3
+    out["accept"] = {"kernels": "k_move_from_event, k_acc_fused, k_acc_coarse_reduce", "bound": "latency",
+                     "unit": "TFLOP/s", "achieved": fl_acc / t / 1e12, "peak": fp64 / 1e12, "frac": fl_acc / t / fp64,
+                     "work": f"{fl_acc / 1e6:.1f} M FP64 flops (P2L of both positions into the cells whose lists "
+                             f"hold them), {b_acc / 1e6:.1f} MB",
+                     "hbm_frac": b_acc / t / hbm,
+                     "note": "three dependent launches of small grids; no unit is saturated"}
+    return out
+
+
 # --------------------------------------------------------------- clocks
 class Clocks:
     def __init__(self, device: int):
@@ -571,6 +640,16 @@ def run_gpu(args):
             "fp32_ops_per_launch": fp32_ops, "t_min_ms": 1e3 * max(t_mufu, t_fma), "t_meas_ms": prop_ms,
             "frac_of_alu_bound": 1e3 * max(t_mufu, t_fma) / prop_ms}
 
+    rooflines = phase_rooflines(work, {nm: phases[i] / args.steps for i, nm in enumerate(k.PHASES)}, E, L, len(q),
+                                p, nhop, peaks, nsm, mixed=True)
+    rooflines["propose"] = {kk: roof[kk] for kk in ("kernel", "bound", "achieved", "peak", "unit", "frac")}
+    if fp64 is not None:
+        # FP64 form: one FP64 FMA per pair (the lattice-table near field), at 2 FMA/clk/SM
+        fp64_peak = 2 * 2 * nsm * sm_max * 1e6
+        a64 = 2 * work["pairs"] / (fp64["propose_ms"] * 1e-3)
+        rooflines["propose_fp64_form"] = {"kernel": "k_propose_lattice<double>", "bound": "alu", "unit": "TFLOP/s",
+                                          "achieved": a64 / 1e12, "peak": fp64_peak / 1e12, "frac": a64 / fp64_peak,
+                                          "work": "one FP64 FMA (2 flops) per pair"}
     cpu = None
     if not args.no_cpu and world == 1 or (world > 1 and rank == 0 and not args.no_cpu):
         direct = cpu_sample(E, sites, q, seconds_target=args.cpu_seconds, nhop=nhop, bc=args.bc)
@@ -595,6 +674,7 @@ def run_gpu(args):
         "fp64_form": fp64,
         "near_cache_form": ncache,
         "roofline": roof,
+        "rooflines": rooflines,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches_per_step(L, args.bc) * args.steps,
@@ -609,8 +689,11 @@ def run_gpu(args):
 
 def run_batch(args):
     """Batched replicas: independent lattice systems of uneven sizes (edges from
-    {32, 48, 64, 96, 128}, occupancy U[0.02, 0.15]) advanced together, one KMC
-    step of every replica per graph replay; L per replica from the autotuner."""
+    {32, 48, 64, 96, 128}, occupancy U[0.02, 0.15]) advanced together by the
+    batched kernels (every launch covers all replicas); L per replica and the
+    batch's P2P tile from the autotuner.  The value is device-timed (CUDA events
+    around the K graph-replayed steps); e2e is the host wall clock of the same
+    call (uniform staging and event read-back included)."""
     import torch
     import paper_1905_04065_gb300 as k
     from paper_1905_04065_gb300 import autotune
@@ -625,51 +708,81 @@ def run_batch(args):
     reps = workloads.batch_replicas(nrep, first=rank * nrep)  # each rank its own replicas
     p, kT = B["p"], B["kT"]
     t0 = time.perf_counter()
-    handles, hops, levels = [], 0, []
+    levels, hops = [], 0
     for r in reps:
         pos = workloads.site_positions(r["E"], r["sites"])
         L = autotune.tune_levels(r["E"], pos, r["q"], p, "mixed", kT) if not args.no_tune else \
             autotune.valid_levels(r["E"])[0]
         levels.append(L)
-        handles.append(k.kmc_fmm_init(pos, r["q"], float(r["E"]), L, p, precision="mixed", lattice_edge=r["E"],
-                                      kT=kT, device=dev))
         hops += pair_count(r["E"], L, r["sites"])["hops"]
+
+    def make(precision):
+        return [k.kmc_fmm_init(workloads.site_positions(r["E"], r["sites"]), r["q"], float(r["E"]), L, p,
+                               precision=precision, lattice_edge=r["E"], kT=kT, device=dev)
+                for r, L in zip(reps, levels)]
+    handles = make("mixed")
     torch.cuda.synchronize()
     ws = sum(step_bytes(r["E"], L, r["N"], p) for r, L in zip(reps, levels))
     setup_s = time.perf_counter() - t0
     bat = k.kmc_batch_create(handles)
     R = len(handles)
+    tune = autotune.tune_batch_chunk(bat) if not args.no_tune else (k.kmc_batch_info(bat)["chunk"], {})
+    info = k.kmc_batch_info(bat)
     rng = np.random.default_rng(B["seed"] + 17)
     u = 1.0 - rng.random((args.warmup + args.steps, R, 2))
     k.kmc_batch_run(bat, u[: args.warmup])
     # the replicas' working set (rates, expansions, charges) exceeds the 129 MB
-    # L2, so the K timed steps run as one call: the graph is replayed K times
+    # L2, so the K timed steps run as one call: the graph is replayed K / 8 times
     clk = Clocks(dev)
     os.makedirs(args.clocks_dir, exist_ok=True)
     clk.start(os.path.join(args.clocks_dir, f"clocks_batch_rank{rank}.csv"))
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    k.kmc_batch_run(bat, u[args.warmup: args.warmup + args.steps])
-    torch.cuda.synchronize()
-    ms = [1e3 * (time.perf_counter() - t1) / args.steps] * args.steps
+    _, _, dev_ms = k.kmc_batch_run(bat, u[args.warmup: args.warmup + args.steps], timed=True)
+    wall_ms = 1e3 * (time.perf_counter() - t1)
     clocks = clk.stop()
-    units, tot = aggregate(hops * args.steps, sum(ms), device=f"cuda:{dev}")
+    units, tot = aggregate(hops * args.steps, dev_ms, device=f"cuda:{dev}")
+    e2e_units, e2e_tot = aggregate(hops * args.steps, wall_ms, device=f"cuda:{dev}")
+    del bat
+    # FP64 form of the same batch (context: the mixed form's speed-up)
+    fp64 = None
+    if args.fp64_steps > 0:
+        del handles
+        torch.cuda.synchronize()
+        h64 = make("fp64")
+        b64 = k.kmc_batch_create(h64)
+        u64 = 1.0 - rng.random((1 + args.fp64_steps, R, 2))
+        k.kmc_batch_run(b64, u64[:1])
+        _, _, ms64 = k.kmc_batch_run(b64, u64[1:], timed=True)
+        fp64 = {"dU_evals_per_s": hops * args.fp64_steps / (ms64 * 1e-3), "ms_per_step": ms64 / args.fp64_steps,
+                "steps": args.fp64_steps}
+        del b64, h64
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank != 0:
         return 0
+    value = units / (tot * 1e-3)
     line = {
-        "metric": "dU evals/sec and KMC steps/sec, 64 batched replicas", "value": units / (tot * 1e-3),
+        "metric": "dU evals/sec and KMC steps/sec, 64 batched replicas", "value": value,
         "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPE_MIXED, "data": "synthetic",
         "config": {"workload": f"batch: {R} replicas, edges {sorted(set(r['E'] for r in reps))}, occupancy "
                                f"U[0.02,0.15], {sum(r['N'] for r in reps)} charges in total, p={p}, kT={kT}",
-                   "levels": levels, "working_set_bytes": ws,
-                   "timing": "host wall clock around one kmc_batch_run of K steps (uniform staging and event "
-                             "read-back included); working set larger than L2, no flush"},
-        "replica_steps_per_s": world * R * args.steps / (tot * 1e-3), "setup_s": setup_s, "clocks": clocks,
-        "gpu_launches": launches_per_step(max(levels)) * R * args.steps,
+                   "levels": levels, "working_set_bytes": ws, "p2p_chunk": info["chunk"],
+                   "chunk_ms_per_step": {str(c): t for c, t in tune[1].items()},
+                   "timing": "CUDA events on the batch's stream around the K graph-replayed steps; working set "
+                             "larger than L2, no flush"},
+        "kmc_steps_per_s": world * args.steps / (tot * 1e-3),
+        "replica_steps_per_s": world * R * args.steps / (tot * 1e-3), "setup_s": setup_s,
+        "fp64_form": fp64,
+        "mixed_over_fp64": (value / fp64["dU_evals_per_s"]) if fp64 else None,
+        "e2e": {"value": e2e_units / (e2e_tot * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": 16 * R, "d2h_bytes_per_step": 16 * R,
+                "path": "kmc_batch_run from host uniforms to host events and time increments"},
+        "clocks": clocks,
+        "gpu_launches": info["launches_per_step"] * args.steps,
+        "batched_kernels": info["fused"],
     }
     print(json.dumps(line))
     return 0

@@ -288,16 +288,41 @@ int kmc_select_static(const double* rates, int64_t n, double zeta, double xi, in
 /*
  * Replica batches (many independent systems advanced together, the ensemble
  * parallelism of Sec. 5.4 on one GPU).  A batch holds `count` lattice-mode
- * handles on one device (not owned; they must outlive the batch) and replays
- * one KMC step of every member from a single CUDA graph whose branches are
- * the members' steps.
+ * handles on one device (not owned; they must outlive the batch).
+ *   When the members share precision, hop set and near-field mode and have no
+ *   Dirichlet walls, every launch of a batch step covers all members: the
+ *   downward pass (one launch per level), the propose over the flattened list
+ *   of all members' leaves, the rates over all members' charges, one
+ *   selection CTA per member (the per-member segment of the cumulative rate
+ *   sums), the members' move records and the accept updates -- L_max + 6
+ *   launches per step whatever the number of members (one more per extra
+ *   leaf-capacity class of the propose, one more with the near-field cache),
+ *   replayed from a CUDA graph.  Members may differ in size, levels and order.
+ *   Otherwise each member's own step is a parallel branch of one graph.
  *   kmc_batch_run: uniforms (HOST) steps x count x 2 values (zeta, xi) laid
  *   out [step][member][2]; events (int64) and dts (HOST, steps x count,
  *   [step][member], may be NULL).  Same results as kmc_run on each member.
+ *   kmc_batch_run_timed: the same, and device_ms (host) receives the device
+ *   time of the steps (CUDA events on the batch's stream around the step
+ *   launches; staging of the uniforms and reading of the events excluded).
+ *   kmc_batch_set_chunk: near-field sources staged in shared memory per pass
+ *   of the batched propose (the P2P tile): 0 = each member the smallest that
+ *   fits its leaves, members of equal capacity sharing one propose launch
+ *   (the default); else one capacity for all members (even, at least every
+ *   member's leaf capacity).  KMC_ERR_STATE for a batch of members' own
+ *   kernels.  Errors of every call: KMC_ERR_ARG, KMC_ERR_CUDA,
+ *   KMC_ERR_OOM, or a member's error (see kmc_batch_last_error).
+ *   kmc_batch_info: fused (1 = batched kernels), the largest pass capacity in
+ *   use, and the kernel launches of one batch step (host ints, each may be
+ *   NULL).
  */
 typedef struct kmc_batch* kmc_batch_handle;
 int kmc_batch_create(kmc_batch_handle* b, int count, const kmc_handle* handles);
 int kmc_batch_run(kmc_batch_handle b, int steps, const double* uniforms, int64_t* events, double* dts);
+int kmc_batch_run_timed(kmc_batch_handle b, int steps, const double* uniforms, int64_t* events, double* dts,
+                        double* device_ms);
+int kmc_batch_set_chunk(kmc_batch_handle b, int chunk);
+int kmc_batch_info(kmc_batch_handle b, int* fused, int* chunk, int* launches_per_step);
 const char* kmc_batch_last_error(kmc_batch_handle b);
 void kmc_batch_destroy(kmc_batch_handle b);
 

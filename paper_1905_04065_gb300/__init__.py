@@ -46,7 +46,8 @@ EXPORTS = [
     "kmc_fmm_accept", "kmc_fmm_accept_event", "kmc_step", "kmc_run", "kmc_run_profiled", "kmc_fmm_recompute",
     "kmc_fmm_leaf_index", "kmc_fmm_positions", "kmc_last_error", "kmc_fmm_destroy", "kmc_select_static",
     "kmc_check_bounded_wait",
-    "kmc_batch_create", "kmc_batch_run", "kmc_batch_last_error", "kmc_batch_destroy",
+    "kmc_batch_create", "kmc_batch_run", "kmc_batch_run_timed", "kmc_batch_set_chunk", "kmc_batch_info",
+    "kmc_batch_last_error", "kmc_batch_destroy",
 ]
 
 
@@ -106,6 +107,9 @@ def load_library(path: str | None = None):
             "kmc_check_bounded_wait": (I, [I, D]),
             "kmc_batch_create": (I, [P, I, P]),
             "kmc_batch_run": (I, [P, I, P, P, P]),
+            "kmc_batch_run_timed": (I, [P, I, P, P, P, P]),
+            "kmc_batch_set_chunk": (I, [P, I]),
+            "kmc_batch_info": (I, [P, P, P, P]),
             "kmc_batch_last_error": (ctypes.c_char_p, [P]),
             "kmc_batch_destroy": (None, [P]),
         }
@@ -476,20 +480,39 @@ def kmc_batch_create(handles) -> Batch:
     return b
 
 
-def kmc_batch_run(b: Batch, uniforms):
-    """uniforms: [steps, members, 2]; returns (events, dts), each [steps, members]."""
+def _batch_check(b: Batch, code: int):
+    if code != KMC_OK:
+        msg = load_library().kmc_batch_last_error(b.ptr)
+        raise KmcError(code, msg.decode() if msg else "")
+
+
+def kmc_batch_run(b: Batch, uniforms, timed: bool = False):
+    """uniforms: [steps, members, 2]; returns (events, dts), each [steps, members]; with
+    timed=True also the device time of the steps in ms."""
     lib = load_library()
     u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64))
     steps, R = int(u.shape[0]), len(b.handles)
-    assert u.shape == (steps, R, 2)
+    if u.shape != (steps, R, 2):
+        raise ValueError(f"uniforms must have shape (steps, {R}, 2)")
     ev = np.empty((steps, R), dtype=np.int64)
     dt = np.empty((steps, R), dtype=np.float64)
-    code = lib.kmc_batch_run(b.ptr, steps, u.ctypes.data_as(ctypes.c_void_p), ev.ctypes.data_as(ctypes.c_void_p),
-                             dt.ctypes.data_as(ctypes.c_void_p))
-    if code != KMC_OK:
-        msg = lib.kmc_batch_last_error(b.ptr)
-        raise KmcError(code, msg.decode() if msg else "")
-    return ev, dt
+    ms = ctypes.c_double()
+    _batch_check(b, lib.kmc_batch_run_timed(b.ptr, steps, u.ctypes.data_as(ctypes.c_void_p),
+                                            ev.ctypes.data_as(ctypes.c_void_p), dt.ctypes.data_as(ctypes.c_void_p),
+                                            ctypes.byref(ms)))
+    return (ev, dt, ms.value) if timed else (ev, dt)
+
+
+def kmc_batch_set_chunk(b: Batch, chunk: int) -> None:
+    """P2P tile of the batched propose: near-field sources staged per pass (0 = smallest that fits)."""
+    _batch_check(b, load_library().kmc_batch_set_chunk(b.ptr, int(chunk)))
+
+
+def kmc_batch_info(b: Batch) -> dict:
+    """{'fused': batched kernels?, 'chunk': P2P pass capacity, 'launches_per_step': kernels per step}."""
+    f, c, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _batch_check(b, load_library().kmc_batch_info(b.ptr, ctypes.byref(f), ctypes.byref(c), ctypes.byref(n)))
+    return {"fused": bool(f.value), "chunk": c.value, "launches_per_step": n.value}
 
 
 def kmc_batch_last_error(b: Batch) -> str:

@@ -1,11 +1,17 @@
-"""Leaf-level autotuner for lattice systems.
+"""Autotuner for lattice systems and replica batches.
 
-The number of FMM levels L sets the leaf width W = E / 2^(L-1) and so the
-balance between the near-field pair sums (∝ charges per leaf) and the
+Leaf tile: the number of FMM levels L sets the leaf width W = E / 2^(L-1) and
+so the balance between the near-field pair sums (∝ charges per leaf) and the
 expansion work (∝ leaves).  For a lattice system the tuner times a few device
 steps for every valid L and keeps the fastest, caching the choice per GPU,
 lattice edge, occupancy bucket, order and precision in a JSON file beside
 this module.
+
+P2P tile of a batch: the batched propose stages the charges of a leaf's 27
+neighbour leaves in shared memory in passes of `chunk` sources; a larger pass
+needs fewer passes in dense neighbourhoods but more shared memory per CTA
+(fewer resident CTAs).  tune_batch_chunk times the batch's step for a few
+pass capacities and keeps the fastest.
 
 Valid L: at least 4 leaves per side (L >= 3) and 2 <= W <= 12 sites per leaf
 side (the propose kernel keeps a leaf's sites in shared memory).
@@ -88,3 +94,30 @@ def tune_levels(E: int, positions, charges, p: int, precision: str = "mixed", kT
             table[key] = {"L": best, "ms_per_step": {str(L): t for L, t in times.items()}}
             _store(table)
     return best
+
+
+def tune_batch_chunk(b, steps: int = 8, factors=(1.0, 1.5, 2.0), seed: int = 5):
+    """Pick the batched propose's pass capacity (the P2P tile) by device-timing `steps` batch
+    steps per candidate: 0 (each member its smallest capacity, members grouped by capacity into
+    one propose launch per group) and multiples of the largest member's smallest capacity (one
+    launch for all).  The timed steps are real KMC steps of the batch (its members advance).
+    Returns (chosen request, {request: ms per step})."""
+    import paper_1905_04065_gb300 as k
+
+    info = k.kmc_batch_info(b)
+    if not info["fused"]:
+        return 0, {}
+    k.kmc_batch_set_chunk(b, 0)
+    base = k.kmc_batch_info(b)["chunk"]
+    cands = [0] + sorted({int(2 * round(base * f / 2)) for f in factors})
+    rng = np.random.default_rng(seed)
+    R = len(b.handles)
+    times = {}
+    for c in cands:
+        k.kmc_batch_set_chunk(b, c)
+        k.kmc_batch_run(b, 1.0 - rng.random((2, R, 2)))  # graph capture, warm-up
+        _, _, ms = k.kmc_batch_run(b, 1.0 - rng.random((steps, R, 2)), timed=True)
+        times[c] = ms / steps
+    best = min(times, key=times.get)
+    k.kmc_batch_set_chunk(b, best)
+    return best, times

@@ -181,6 +181,27 @@ struct Dev {
   double* dt_hist;    // [steps] time increments
 };
 
+// One member of a batch of independent systems advanced by the same kernels:
+// its geometry and its device buffers.  A batched launch covers the blocks of
+// every member; blocks [off[r], off[r + 1]) belong to member r.
+struct BatchRep {
+  Geo g;
+  Dev d;
+};
+
+// member r of block b: the largest r with off[r] <= b (members without
+// blocks in this launch have off[r] == off[r + 1] and are skipped); off[R] is
+// the launch's block count
+__device__ __forceinline__ int batch_find(const int* off, int R, int b) {
+  int lo = 0, hi = R;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // device error codes (bit flags in err[0])
 #define KMC_DERR_CAPACITY 1
 #define KMC_DERR_SINGULAR 2
@@ -277,4 +298,41 @@ void fmm_shadow_all(const Geo& g, const Dev& d, cudaStream_t s);
 int kmc_coarse_slots();
 void raise_dynamic_smem(const void* fn, size_t bytes);
 void kmc_energy_reduce(const Geo& g, const Dev& d, cudaStream_t s);
+
+// Launch plan of one batched KMC step: every launch covers all members of a
+// batch (BatchRep), member r owning blocks [off[r], off[r + 1]) of it.  Host
+// struct; the arrays it points to live on the device.
+struct BatchPlan {
+  int R;                      // members
+  int prec, nhop, near_cache; // shared by all members
+  int Lmax;                   // deepest tree among the members
+  int chunk;                  // requested pass capacity (0: each member's smallest)
+  const BatchRep* reps;       // [R]
+  const int* off_down[KMC_MAXL + 1];  // level l >= 2: the parent cells of level l - 1 of members with L >= l
+  int nblk_down[KMC_MAXL + 1];
+  size_t smem_down;
+  // propose: one launch per class of members with the same pass capacity (their leaves)
+  int nprop;
+  int chunk_c[KMC_MAXL];
+  const int* off_prop[KMC_MAXL];
+  int nblk_prop[KMC_MAXL];
+  size_t smem_prop[KMC_MAXL];
+  const int* off_fin;         // rate blocks of KMC_FIN_PARTICLES charges
+  int nblk_fin;
+  const int* off_acc;         // fused accept blocks
+  int nblk_acc;
+  const int* off_acr;         // coarse-cell reduction blocks (72 per member)
+  int nblk_acr;
+  size_t smem_acr;
+  const int* off_nu;          // near-field cache update blocks (54 per member with the cache)
+  int nblk_nu;
+};
+void fmm_downward_batch(const BatchPlan& bp, cudaStream_t s);
+void kmc_step_batch(const BatchPlan& bp, cudaStream_t s);  // propose, rates, select, record, accept
+void kmc_batch_prepare(const BatchPlan& bp);                // load the kernels, raise their smem limits
+int kmc_propose_chunk_min(const Geo& g);                    // smallest pass capacity for g's leaves
+size_t kmc_propose_smem_for(const Geo& g, int prec, int chunk, int cached);
+int kmc_acc_blocks_for(const Geo& g);
+int kmc_acr_blocks();
+size_t kmc_acr_smem_for(const Geo& g);
 void kmc_validate(const Geo& g, const Dev& d, cudaStream_t s);

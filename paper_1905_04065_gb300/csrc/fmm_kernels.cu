@@ -1233,14 +1233,14 @@ __global__ void __launch_bounds__(128) k_downward_cell(const Geo g, const Dev d,
 // parent coefficient read is shared by 8 lanes.  Tasks go to warps in snake
 // order (their cost falls with the degree).
 template <typename T>
-__global__ void __launch_bounds__(256) k_downward_par(const Geo g, const Dev d, int l) {
+__device__ __forceinline__ void downward_par_blk(const Geo& g, const Dev& d, const int l, const int blk0) {
   typedef typename cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char shraw[];
   const int F = (g.p + 1) * (g.p + 1);
   C* Lf = (C*)shraw;  // [F] parent expansion, entry n^2 + n + m
   C* Rf = Lf + F;     // [8][F] child-offset tables, same order
   const int nl = 1 << (l - 1), np = nl >> 1, sh = l - 2;  // np = 2^(l-2)
-  const int64_t par = blockIdx.x;
+  const int64_t par = (int64_t)blockIdx.x - blk0;
   const int px = (int)(par & (np - 1)), py = (int)((par >> sh) & (np - 1)), pz = (int)(par >> (2 * sh));
   const C* Pp = (const C*)d.Peff + (g.cell_off[l - 1] + par) * g.P;
   const C* Rt = child_table<T>(d) + (int64_t)l * 8 * g.P;
@@ -1284,6 +1284,28 @@ __global__ void __launch_bounds__(256) k_downward_par(const Geo g, const Dev d, 
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_downward_par(const Geo g, const Dev d, int l) {
+  downward_par_blk<T>(g, d, l, 0);
+}
+
+// level l of every member of a batch that has it (blocks of member r: its parent cells)
+template <typename T>
+__global__ void __launch_bounds__(256) k_downward_par_batch(const BatchRep* reps, const int* off, int R, int l) {
+  const int r = batch_find(off, R, blockIdx.x);
+  downward_par_blk<T>(reps[r].g, reps[r].d, l, off[r]);
+}
+
+// level 1 of every member: the leaf-independent part H
+template <typename T>
+__global__ void k_downward_root_batch(const BatchRep* reps) {
+  typedef typename cplx<T>::type C;
+  const Geo& g = reps[blockIdx.x].g;
+  const Dev& d = reps[blockIdx.x].d;
+  C* Pe = (C*)d.Peff;
+  for (int c = threadIdx.x; c < g.P; c += blockDim.x) Pe[g.cell_off[1] * g.P + c] = own_coef<T>(d, g.cell_off[1] * g.P + c);
+}
+
 void fmm_prepare(const Geo& g, int prec) {
   // load every per-step kernel now: with lazy module loading a first launch
   // inside a stream capture would invalidate the capture
@@ -1297,6 +1319,10 @@ void fmm_prepare(const Geo& g, int prec) {
   const int smax = 9 * (KMC_MAXP + 1) * (KMC_MAXP + 1) * (int)sizeof(double2);
   cudaFuncSetAttribute(k_downward_par<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
   cudaFuncSetAttribute(k_downward_par<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax / 2);
+  cudaFuncGetAttributes(&fa, k_downward_root_batch<double>);
+  cudaFuncGetAttributes(&fa, k_downward_root_batch<float>);
+  cudaFuncSetAttribute(k_downward_par_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  cudaFuncSetAttribute(k_downward_par_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax / 2);
   (void)g;
   (void)prec;
 }
@@ -1315,6 +1341,20 @@ void fmm_downward(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
       if (prec == 0) k_downward_par<double><<<parents, 256, smp, s>>>(g, d, l);
       else k_downward_par<float><<<parents, 256, smp, s>>>(g, d, l);
     }
+  }
+}
+
+// downward pass of every member of a batch: H into level 1, then one launch
+// per level (members with fewer levels take no blocks of the deeper launches)
+void fmm_downward_batch(const BatchPlan& bp, cudaStream_t s) {
+  if (bp.prec == 0) k_downward_root_batch<double><<<bp.R, 128, 0, s>>>(bp.reps);
+  else k_downward_root_batch<float><<<bp.R, 128, 0, s>>>(bp.reps);
+  for (int l = 2; l <= bp.Lmax; l++) {
+    if (bp.nblk_down[l] <= 0) continue;
+    if (bp.prec == 0)
+      k_downward_par_batch<double><<<bp.nblk_down[l], 256, bp.smem_down, s>>>(bp.reps, bp.off_down[l], bp.R, l);
+    else
+      k_downward_par_batch<float><<<bp.nblk_down[l], 256, bp.smem_down, s>>>(bp.reps, bp.off_down[l], bp.R, l);
   }
 }
 

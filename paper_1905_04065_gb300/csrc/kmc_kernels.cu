@@ -509,8 +509,7 @@ enum { PROP_SUM = 0, PROP_FILL = 1, PROP_CACHED = 2 };
 // per SM (more resident leaves hide its load and barrier latency; sixteen
 // spilled too much of the L2P).
 template <typename T, int NH, int mode>
-__global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
-    k_propose_lattice(const Geo g, const Dev d, int chunk) {
+__device__ __forceinline__ void propose_leaf(const Geo g, const Dev d, const int chunk, const int blk0) {
   typedef typename cplx<T>::type C;
   typedef typename vec4<T>::type V4;
   constexpr bool F32 = sizeof(T) == 4;
@@ -540,7 +539,7 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   const int nL = g.nL, E = g.E;
-  const int64_t leaf = blockIdx.x;
+  const int64_t leaf = (int64_t)blockIdx.x - blk0;  // the member's leaf (blk0: its first block)
   const int lsh = g.L - 1;  // nL = 2^(L-1)
   const int lx = (int)(leaf & (nL - 1)), ly = (int)((leaf >> lsh) & (nL - 1)), lz = (int)(leaf >> (2 * lsh));
   const int gx0 = lx * W, gy0 = ly * W, gz0 = lz * W;
@@ -930,6 +929,21 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
   }
 }
 
+// one CTA per leaf of one system
+template <typename T, int NH, int mode>
+__global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
+    k_propose_lattice(const Geo g, const Dev d, int chunk) {
+  propose_leaf<T, NH, mode>(g, d, chunk, 0);
+}
+
+// one CTA per leaf of every replica of a batch (blocks [off[r], off[r + 1]) are replica r's leaves)
+template <typename T, int NH, int mode>
+__global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
+    k_propose_batch(const BatchRep* reps, const int* off, int R, int chunk) {
+  const int r = batch_find(off, R, blockIdx.x);
+  propose_leaf<T, NH, mode>(reps[r].g, reps[r].d, chunk, off[r]);
+}
+
 static size_t propose_smem(const Geo& g, int prec, int chunk) {
   const size_t ts = prec == 0 ? 8 : 4;
   const int W3 = g.W * g.W * g.W;
@@ -1055,9 +1069,10 @@ __device__ __forceinline__ double scale_pow2(float m, int e) {
 // FP64 range down to 2^-1021 (an FP64 exp below that).  FP64: every
 // operation in FP64.
 template <bool MIXED, int NH>
-__global__ void __launch_bounds__(FIN_THREADS) k_finalize(const Geo g, const Dev d) {
+__device__ __forceinline__ void finalize_blk(const Geo& g, const Dev& d, const int blk0) {
   __shared__ double ts[FIN_THREADS];
-  const int64_t i = blockIdx.x * (int64_t)FIN_THREADS + threadIdx.x;
+  const int64_t blk = (int64_t)blockIdx.x - blk0;
+  const int64_t i = blk * FIN_THREADS + threadIdx.x;
   double tsum = 0.0;
   if (i < g.n) {
     const int E = g.E;
@@ -1172,7 +1187,18 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize(const Geo g, const Dev
   ts[threadIdx.x] = tsum;
   __syncthreads();
   block_scan(ts, FIN_THREADS);
-  if (threadIdx.x == 0) d.bsum[blockIdx.x] = ts[FIN_THREADS - 1];
+  if (threadIdx.x == 0) d.bsum[blk] = ts[FIN_THREADS - 1];
+}
+
+template <bool MIXED, int NH>
+__global__ void __launch_bounds__(FIN_THREADS) k_finalize(const Geo g, const Dev d) {
+  finalize_blk<MIXED, NH>(g, d, 0);
+}
+
+template <bool MIXED, int NH>
+__global__ void __launch_bounds__(FIN_THREADS) k_finalize_batch(const BatchRep* reps, const int* off, int R) {
+  const int r = batch_find(off, R, blockIdx.x);
+  finalize_blk<MIXED, NH>(reps[r].g, reps[r].d, off[r]);
 }
 
 // block sums of caller-provided rates (same block structure as k_finalize)
@@ -1205,7 +1231,7 @@ void kmc_finalize_rates(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
 // finalize kernel, chunks of block sums per thread here); dt = -ln(xi)/Q.
 #define SEL_THREADS 1024
 
-__global__ void __launch_bounds__(SEL_THREADS) k_select(const Geo g, const Dev d, int use_counter) {
+__device__ __forceinline__ void select_one(const Geo& g, const Dev& d, const int use_counter) {
   __shared__ double cs[SEL_THREADS];
   __shared__ double ts[FIN_THREADS];
   __shared__ double sh_target, sh_prev;
@@ -1298,6 +1324,15 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(const Geo g, const Dev d
   }
 }
 
+__global__ void __launch_bounds__(SEL_THREADS) k_select(const Geo g, const Dev d, int use_counter) {
+  select_one(g, d, use_counter);
+}
+
+// one CTA per member of a batch (the device step counter of each member)
+__global__ void __launch_bounds__(SEL_THREADS) k_select_batch(const BatchRep* reps) {
+  select_one(reps[blockIdx.x].g, reps[blockIdx.x].d, 1);
+}
+
 void kmc_rate_bsum(const Geo& g, const Dev& d, cudaStream_t s) {
   unsigned nb = (unsigned)((g.n + FIN_THREADS - 1) / FIN_THREADS);
   k_rate_bsum<<<nb, FIN_THREADS, 0, s>>>(g, d);
@@ -1308,12 +1343,14 @@ void kmc_select(const Geo& g, const Dev& d, int use_counter, cudaStream_t s) {
 }
 
 // store the step's event and dt, advance the device step counter
-__global__ void k_record(const Dev d) {
+__device__ __forceinline__ void record_one(const Dev& d) {
   int st = *d.stepc;
   d.ev_hist[st] = *d.event;
   d.dt_hist[st] = d.dtq[0];
   *d.stepc = st + 1;
 }
+
+__global__ void k_record(const Dev d) { record_one(d); }
 
 void kmc_record(const Geo& g, const Dev& d, cudaStream_t s) {
   (void)g;
@@ -1322,7 +1359,7 @@ void kmc_record(const Geo& g, const Dev& d, cudaStream_t s) {
 
 // ------------------------------------------------------------------ accept
 // Move record from a lattice event index (device resident, no host sync).
-__global__ void k_move_from_event(const Geo g, const Dev d) {
+__device__ __forceinline__ void move_from_event_one(const Geo& g, const Dev& d) {
   MoveRec mv;
   int64_t j = *d.event;
   mv.valid = 0;
@@ -1347,6 +1384,16 @@ __global__ void k_move_from_event(const Geo g, const Dev d) {
     mv.dU = g.prec ? (double)d.dU32[j] : d.dU[j];
   }
   *d.move = mv;
+}
+
+__global__ void k_move_from_event(const Geo g, const Dev d) { move_from_event_one(g, d); }
+
+// thread per member of a batch: record the step's event, then its move record
+__global__ void k_record_move_batch(const BatchRep* reps, int R) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  record_one(reps[r].d);
+  move_from_event_one(reps[r].g, reps[r].d);
 }
 
 void kmc_accept_from_event(const Geo& g, const Dev& d, cudaStream_t s) { k_move_from_event<<<1, 1, 0, s>>>(g, d); }
@@ -1581,11 +1628,11 @@ __device__ __forceinline__ void acc_coarse_role(const Geo& g, const MoveRec& mv,
 // the cell (lanes over coefficients, coalesced rows), then the eight warp
 // partials are added in warp order
 #define ACR_WARPS 8
-__global__ void __launch_bounds__(32 * ACR_WARPS) k_acc_coarse_reduce(const Geo g, const Dev d, const double2* scratch) {
+__device__ __forceinline__ void acc_coarse_reduce_blk(const Geo& g, const Dev& d, const double2* scratch, const int blk0) {
   extern __shared__ double2 acr[];  // [ACR_WARPS][P]
   MoveRec mv = *d.move;
   if (!mv.valid) return;
-  const int cc = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cc = blockIdx.x - blk0, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int l, cell, first, nslot;
   if (cc < 8) { l = 2; cell = cc; first = cc * 2 * KMC_TOP_NIMG; nslot = 2 * KMC_TOP_NIMG; }
   else { l = 3; cell = cc - 8; first = KMC_L2_SLOTS + cell * 54; nslot = 54; }
@@ -1614,6 +1661,15 @@ __global__ void __launch_bounds__(32 * ACR_WARPS) k_acc_coarse_reduce(const Geo 
     d.Psi[at] = v;
     if (d.Psi32) d.Psi32[at] = make_float2((float)v.x, (float)v.y);
   }
+}
+
+__global__ void __launch_bounds__(32 * ACR_WARPS) k_acc_coarse_reduce(const Geo g, const Dev d, const double2* scratch) {
+  acc_coarse_reduce_blk(g, d, scratch, 0);
+}
+
+__global__ void __launch_bounds__(32 * ACR_WARPS) k_acc_coarse_reduce_batch(const BatchRep* reps, const int* off, int R) {
+  const int r = batch_find(off, R, blockIdx.x);
+  acc_coarse_reduce_blk(reps[r].g, reps[r].d, reps[r].d.acc_scratch, off[r]);
 }
 
 int kmc_coarse_slots() { return KMC_COARSE_SLOTS; }
@@ -1778,11 +1834,25 @@ struct AccPlan {
   int nmp, nfar, ncoarse, nfine, fine_per_level;
 };
 #define ACC_THREADS 128
-__global__ void __launch_bounds__(ACC_THREADS) k_acc_fused(const Geo g, const Dev d, double2* scratch, AccPlan ap) {
+// the block ranges of the roles for a system of L levels and order p
+__host__ __device__ __forceinline__ AccPlan acc_plan(const Geo& g) {
+  AccPlan ap;
+  ap.nmp = (g.L * g.P + ACC_THREADS - 1) / ACC_THREADS;
+  ap.nfar = (g.P + ACC_THREADS / 32 - 1) / (ACC_THREADS / 32);
+  // coarse levels 2 and 3 (8 + 64 cells, L >= 3 always): all cells x all images
+  ap.ncoarse = (KMC_COARSE_SLOTS * (g.p + 1) + ACC_THREADS - 1) / ACC_THREADS;
+  ap.fine_per_level = 432 * (g.p + 1);
+  ap.nfine = g.L >= 4 ? (ap.fine_per_level * (g.L - 3) + ACC_THREADS - 1) / ACC_THREADS : 0;
+  return ap;
+}
+__host__ __device__ __forceinline__ int acc_blocks(const AccPlan& ap) { return ap.nmp + ap.nfar + ap.ncoarse + ap.nfine + 1; }
+
+__device__ __forceinline__ void acc_fused_blk(const Geo& g, const Dev& d, double2* scratch, const AccPlan& ap,
+                                              const int blk0) {
   __shared__ double2 dks[ncoef(KMC_MAXP)];
   const MoveRec mv = *d.move;
   if (!mv.valid) return;
-  int b = blockIdx.x;
+  int b = blockIdx.x - blk0;
   if (b < ap.nmp) {
     acc_multipole_role(g, d, mv, b * ACC_THREADS + threadIdx.x);
     return;
@@ -1806,16 +1876,27 @@ __global__ void __launch_bounds__(ACC_THREADS) k_acc_fused(const Geo g, const De
   if (threadIdx.x == 0) acc_move_role(g, d, mv);
 }
 
+__global__ void __launch_bounds__(ACC_THREADS) k_acc_fused(const Geo g, const Dev d, double2* scratch, AccPlan ap) {
+  acc_fused_blk(g, d, scratch, ap, 0);
+}
+
+__global__ void __launch_bounds__(ACC_THREADS) k_acc_fused_batch(const BatchRep* reps, const int* off, int R) {
+  const int r = batch_find(off, R, blockIdx.x);
+  const AccPlan ap = acc_plan(reps[r].g);
+  acc_fused_blk(reps[r].g, reps[r].d, reps[r].d.acc_scratch, ap, off[r]);
+}
+
 // Near-field cache update for an accepted move of charge q from site r to site
 // r'.  Block (side, o): the leaf T = S - o around the source leaf S of r (side
 // 0, -q) or r' (side 1, +q); in T's frame the source sits at its position in
 // S plus o W sites, as in T's propose CTA, so every site t of T gets
 // +-q / |t - r_T| (lattice units), except
 // the pair at distance 0.  Free space: leaves beyond the box do not exist.
-__global__ void __launch_bounds__(128) k_near_update(const Geo g, const Dev d) {
+__device__ __forceinline__ void near_update_blk(const Geo& g, const Dev& d, const int blk0) {
   const MoveRec mv = *d.move;
   if (!mv.valid || mv.site_old < 0 || mv.site_new < 0) return;
-  const int side = blockIdx.x / 27, o = blockIdx.x % 27;
+  const int bb = blockIdx.x - blk0;
+  const int side = bb / 27, o = bb % 27;
   const int site = side ? mv.site_new : mv.site_old;
   const int E = g.E, W = g.W, nL = g.nL;
   if (!KMC_IN(site < E * E * E && W * W * W <= g.cap, d.err)) return;
@@ -1844,17 +1925,88 @@ __global__ void __launch_bounds__(128) k_near_update(const Geo g, const Dev d) {
   }
 }
 
+__global__ void __launch_bounds__(128) k_near_update(const Geo g, const Dev d) { near_update_blk(g, d, 0); }
+
+__global__ void __launch_bounds__(128) k_near_update_batch(const BatchRep* reps, const int* off, int R) {
+  const int r = batch_find(off, R, blockIdx.x);
+  near_update_blk(reps[r].g, reps[r].d, off[r]);
+}
+
 void kmc_accept_apply(const Geo& g, const Dev& d, cudaStream_t s) {
-  AccPlan ap;
-  ap.nmp = (g.L * g.P + ACC_THREADS - 1) / ACC_THREADS;
-  ap.nfar = (g.P + ACC_THREADS / 32 - 1) / (ACC_THREADS / 32);
-  // coarse levels 2 and 3 (8 + 64 cells, L >= 3 always): all cells x all images
-  ap.ncoarse = (KMC_COARSE_SLOTS * (g.p + 1) + ACC_THREADS - 1) / ACC_THREADS;
-  ap.fine_per_level = 432 * (g.p + 1);
-  ap.nfine = g.L >= 4 ? (ap.fine_per_level * (g.L - 3) + ACC_THREADS - 1) / ACC_THREADS : 0;
-  k_acc_fused<<<ap.nmp + ap.nfar + ap.ncoarse + ap.nfine + 1, ACC_THREADS, 0, s>>>(g, d, d.acc_scratch, ap);
+  const AccPlan ap = acc_plan(g);
+  k_acc_fused<<<acc_blocks(ap), ACC_THREADS, 0, s>>>(g, d, d.acc_scratch, ap);
   k_acc_coarse_reduce<<<KMC_COARSE_CELLS, 32 * ACR_WARPS, sizeof(double2) * ACR_WARPS * g.P, s>>>(g, d, d.acc_scratch);
   if (g.near_cache) k_near_update<<<2 * 27, 128, 0, s>>>(g, d);
+}
+
+// ------------------------------------------------------------------ batched step
+// One KMC step of every member of a batch, each launch covering all members
+// (propose over all members' leaves, rates over all members' charges, one
+// selection CTA per member, the members' move records, then the accept
+// updates of all members).  The members share precision, hop set and
+// near-field mode; their sizes, levels and orders may differ.
+int kmc_propose_chunk_min(const Geo& g) { return propose_chunk(g); }
+size_t kmc_propose_smem_for(const Geo& g, int prec, int chunk, int cached) {
+  return propose_smem(g, prec, cached ? 0 : chunk);
+}
+int kmc_acc_blocks_for(const Geo& g) { return acc_blocks(acc_plan(g)); }
+int kmc_acr_blocks() { return KMC_COARSE_CELLS; }
+size_t kmc_acr_smem_for(const Geo& g) { return sizeof(double2) * ACR_WARPS * g.P; }
+
+template <typename T, int NH>
+static void step_batch_t(const BatchPlan& bp, cudaStream_t s) {
+  constexpr bool MIXED = sizeof(T) == 4;
+  for (int c = 0; c < bp.nprop; c++) {
+    if (bp.nblk_prop[c] <= 0) continue;
+    if (bp.near_cache)
+      k_propose_batch<T, NH, PROP_CACHED><<<bp.nblk_prop[c], PROP_THREADS, bp.smem_prop[c], s>>>(bp.reps, bp.off_prop[c],
+                                                                                                 bp.R, 0);
+    else
+      k_propose_batch<T, NH, PROP_SUM><<<bp.nblk_prop[c], PROP_THREADS, bp.smem_prop[c], s>>>(bp.reps, bp.off_prop[c],
+                                                                                              bp.R, bp.chunk_c[c]);
+  }
+  k_finalize_batch<MIXED, NH><<<bp.nblk_fin, FIN_THREADS, 0, s>>>(bp.reps, bp.off_fin, bp.R);
+  k_select_batch<<<bp.R, SEL_THREADS, 0, s>>>(bp.reps);
+  k_record_move_batch<<<(bp.R + 127) / 128, 128, 0, s>>>(bp.reps, bp.R);
+  k_acc_fused_batch<<<bp.nblk_acc, ACC_THREADS, 0, s>>>(bp.reps, bp.off_acc, bp.R);
+  k_acc_coarse_reduce_batch<<<bp.nblk_acr, 32 * ACR_WARPS, bp.smem_acr, s>>>(bp.reps, bp.off_acr, bp.R);
+  if (bp.near_cache && bp.nblk_nu > 0) k_near_update_batch<<<bp.nblk_nu, 128, 0, s>>>(bp.reps, bp.off_nu, bp.R);
+}
+
+void kmc_step_batch(const BatchPlan& bp, cudaStream_t s) {
+  if (bp.nhop == KMC_MAXHOP) {
+    if (bp.prec == 0) step_batch_t<double, KMC_MAXHOP>(bp, s);
+    else step_batch_t<float, KMC_MAXHOP>(bp, s);
+  } else {
+    if (bp.prec == 0) step_batch_t<double, KMC_NHOP>(bp, s);
+    else step_batch_t<float, KMC_NHOP>(bp, s);
+  }
+}
+
+template <typename T, int NH>
+static void prepare_batch_t(const BatchPlan& bp) {
+  constexpr bool MIXED = sizeof(T) == 4;
+  cudaFuncAttributes fa;
+  for (int c = 0; c < bp.nprop; c++) {
+    if (bp.near_cache) raise_dynamic_smem((const void*)k_propose_batch<T, NH, PROP_CACHED>, bp.smem_prop[c]);
+    else raise_dynamic_smem((const void*)k_propose_batch<T, NH, PROP_SUM>, bp.smem_prop[c]);
+  }
+  cudaFuncGetAttributes(&fa, k_finalize_batch<MIXED, NH>);
+  cudaFuncGetAttributes(&fa, k_select_batch);
+  cudaFuncGetAttributes(&fa, k_record_move_batch);
+  cudaFuncGetAttributes(&fa, k_acc_fused_batch);
+  raise_dynamic_smem((const void*)k_acc_coarse_reduce_batch, bp.smem_acr);
+  cudaFuncGetAttributes(&fa, k_near_update_batch);
+}
+
+void kmc_batch_prepare(const BatchPlan& bp) {
+  if (bp.nhop == KMC_MAXHOP) {
+    if (bp.prec == 0) prepare_batch_t<double, KMC_MAXHOP>(bp);
+    else prepare_batch_t<float, KMC_MAXHOP>(bp);
+  } else {
+    if (bp.prec == 0) prepare_batch_t<double, KMC_NHOP>(bp);
+    else prepare_batch_t<float, KMC_NHOP>(bp);
+  }
 }
 
 // ------------------------------------------------------------------ general points

@@ -11,6 +11,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -1049,10 +1050,14 @@ int kmc_fmm_positions(kmc_handle h, double* positions) {
 }
 
 // ------------------------------------------------------------------ replica batches
-// A batch replays one KMC step of every member handle from a single CUDA
-// graph: the steps of different replicas are independent branches of the
-// graph (fork/join over one stream per replica), so small replicas overlap
-// on the GPU instead of waiting for each other's launches.
+// A batch advances many independent lattice systems together.  When the
+// members share precision, hop set and near-field mode (and have no Dirichlet
+// walls), a step of the whole batch is L_max + 6 launches, each covering every
+// member (BatchPlan: member r owns a block range of each launch), replayed
+// from a CUDA graph of KMC_GRAPH_STEPS steps; each member keeps its own
+// uniforms, step counter and event history in batch-owned arrays.  Otherwise
+// the members' own steps are the parallel branches of one graph (fork/join
+// over one stream per member).
 struct kmc_batch {
   std::vector<kmc_fmm*> h;
   std::vector<cudaStream_t> streams;
@@ -1063,6 +1068,20 @@ struct kmc_batch {
   int graph_cap;
   std::vector<int> gen;  // members' buffer generations the graph was captured with
   bool parallel;         // members captured as parallel branches
+  // batched kernels
+  bool fused;
+  BatchPlan bp;
+  BatchRep* reps;        // [R] device
+  int* offs;             // block offsets of every launch, device
+  double* uni;           // [R][cap][2] uniforms
+  int* stepc;            // [R] step counters
+  int64_t* ev;           // [R][cap] events
+  double* dt;            // [R][cap] time increments
+  int cap;
+  int chunk_req;         // requested near-field pass capacity (0: the smallest that fits)
+  cudaGraphExec_t fgraph;
+  std::vector<BatchRep> reps_host;
+  cudaEvent_t t0, t1;
   char msg[512];
 };
 
@@ -1074,6 +1093,134 @@ static int bfail(kmc_batch* b, int code, const char* fmt, ...) {
   return code;
 }
 
+// block offsets of one batched launch from per-member block counts
+static void push_offsets(std::vector<int>& all, const std::vector<int>& cnt, int* total) {
+  int acc = 0;
+  for (int c : cnt) {
+    all.push_back(acc);
+    acc += c;
+  }
+  all.push_back(acc);
+  *total = acc;
+}
+
+// the launch plan of the batched step (offsets uploaded to b->offs)
+static int batch_plan(kmc_batch* b) {
+  const int R = (int)b->h.size();
+  BatchPlan& bp = b->bp;
+  bp.R = R;
+  bp.prec = b->h[0]->prec;
+  bp.nhop = b->h[0]->g.nhop;
+  bp.near_cache = b->h[0]->g.near_cache;
+  bp.Lmax = 0;
+  int cmin = 2;
+  for (kmc_fmm* h : b->h) {
+    bp.Lmax = h->g.L > bp.Lmax ? h->g.L : bp.Lmax;
+    const int c = kmc_propose_chunk_min(h->g);
+    cmin = c > cmin ? c : cmin;
+  }
+  if (b->chunk_req > 0 && (b->chunk_req < cmin || (b->chunk_req & 1)))
+    return bfail(b, KMC_ERR_ARG, "near-field pass capacity %d below %d or odd", b->chunk_req, cmin);
+  bp.chunk = b->chunk_req;
+  // members' pass capacities: the smallest that fits their leaves, or the requested one; members
+  // of equal capacity share a propose launch (its shared memory fits the class, not the largest leaf)
+  std::vector<int> mch(R);
+  std::vector<int> classes;
+  for (int r = 0; r < R; r++) {
+    const int c = kmc_propose_chunk_min(b->h[r]->g);
+    mch[r] = b->chunk_req > c ? b->chunk_req : c;
+    bool seen = false;
+    for (int x : classes) seen |= x == mch[r];
+    if (!seen) classes.push_back(mch[r]);
+  }
+  std::sort(classes.begin(), classes.end());
+  if ((int)classes.size() > KMC_MAXL) return bfail(b, KMC_ERR_ARG, "too many leaf shapes in one batch");
+  bp.nprop = (int)classes.size();
+  std::vector<int> all, cnt(R);
+  std::vector<size_t> pos;  // index of each launch's offsets in all
+  size_t ts = bp.prec == 0 ? sizeof(double2) : sizeof(float2);
+  bp.smem_down = 0;
+  bp.smem_acr = 0;
+  for (int l = 2; l <= bp.Lmax; l++) {
+    for (int r = 0; r < R; r++) cnt[r] = b->h[r]->g.L >= l ? 1 << (3 * (l - 2)) : 0;
+    pos.push_back(all.size());
+    push_offsets(all, cnt, &bp.nblk_down[l]);
+  }
+  for (int r = 0; r < R; r++) {
+    const Geo& g = b->h[r]->g;
+    const size_t sd = 9 * (size_t)(g.p + 1) * (g.p + 1) * ts;
+    bp.smem_down = sd > bp.smem_down ? sd : bp.smem_down;
+    const size_t sa = kmc_acr_smem_for(g);
+    bp.smem_acr = sa > bp.smem_acr ? sa : bp.smem_acr;
+  }
+  size_t p_prop[KMC_MAXL];
+  for (int c = 0; c < bp.nprop; c++) {
+    bp.chunk_c[c] = classes[c];
+    bp.smem_prop[c] = 0;
+    for (int r = 0; r < R; r++) {
+      cnt[r] = mch[r] == classes[c] ? (int)b->h[r]->g.ML : 0;
+      if (cnt[r]) {
+        const size_t sp = kmc_propose_smem_for(b->h[r]->g, bp.prec, classes[c], bp.near_cache);
+        bp.smem_prop[c] = sp > bp.smem_prop[c] ? sp : bp.smem_prop[c];
+      }
+    }
+    p_prop[c] = all.size();
+    push_offsets(all, cnt, &bp.nblk_prop[c]);
+  }
+  for (int r = 0; r < R; r++) cnt[r] = (int)((b->h[r]->g.n + KMC_FIN_PARTICLES - 1) / KMC_FIN_PARTICLES);
+  const size_t p_fin = all.size();
+  push_offsets(all, cnt, &bp.nblk_fin);
+  for (int r = 0; r < R; r++) cnt[r] = kmc_acc_blocks_for(b->h[r]->g);
+  const size_t p_acc = all.size();
+  push_offsets(all, cnt, &bp.nblk_acc);
+  for (int r = 0; r < R; r++) cnt[r] = kmc_acr_blocks();
+  const size_t p_acr = all.size();
+  push_offsets(all, cnt, &bp.nblk_acr);
+  for (int r = 0; r < R; r++) cnt[r] = bp.near_cache ? 2 * 27 : 0;
+  const size_t p_nu = all.size();
+  push_offsets(all, cnt, &bp.nblk_nu);
+  if (b->offs) cudaFree(b->offs);
+  b->offs = nullptr;
+  if (cudaMalloc(&b->offs, sizeof(int) * all.size()) != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, KMC_ERR_OOM, "batch offsets: device allocation failed");
+  }
+  if (cudaMemcpy(b->offs, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bfail(b, KMC_ERR_CUDA, "batch offsets: copy failed");
+  for (int l = 2; l <= bp.Lmax; l++) bp.off_down[l] = b->offs + pos[l - 2];
+  for (int c = 0; c < bp.nprop; c++) bp.off_prop[c] = b->offs + p_prop[c];
+  bp.off_fin = b->offs + p_fin;
+  bp.off_acc = b->offs + p_acc;
+  bp.off_acr = b->offs + p_acr;
+  bp.off_nu = b->offs + p_nu;
+  bp.reps = b->reps;
+  kmc_batch_prepare(bp);
+  if (cudaGetLastError() != cudaSuccess) return bfail(b, KMC_ERR_CUDA, "batch kernels could not be prepared");
+  return KMC_OK;
+}
+
+// batch-owned run buffers for at least `need` steps per member
+static int batch_reserve(kmc_batch* b, int need) {
+  if (need <= b->cap) return KMC_OK;
+  const int R = (int)b->h.size();
+  const int cap = need < 1024 ? 1024 : need;
+  cudaFree(b->uni);
+  cudaFree(b->ev);
+  cudaFree(b->dt);
+  b->uni = nullptr;
+  b->ev = nullptr;
+  b->dt = nullptr;
+  b->cap = 0;
+  if (cudaMalloc(&b->uni, sizeof(double) * 2 * (size_t)cap * R) != cudaSuccess ||
+      cudaMalloc(&b->ev, sizeof(int64_t) * (size_t)cap * R) != cudaSuccess ||
+      cudaMalloc(&b->dt, sizeof(double) * (size_t)cap * R) != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, KMC_ERR_OOM, "batch run buffers: device allocation failed");
+  }
+  b->cap = cap;
+  return KMC_OK;
+}
+
 int kmc_batch_create(kmc_batch_handle* out, int count, const kmc_handle* handles) {
   KMC_TRACE("kmc_batch_create");
   if (!out) return KMC_ERR_ARG;
@@ -1083,6 +1230,17 @@ int kmc_batch_create(kmc_batch_handle* out, int count, const kmc_handle* handles
   b->graph = nullptr;
   b->graph_cap = 0;
   b->parallel = false;
+  b->fused = false;
+  b->reps = nullptr;
+  b->offs = nullptr;
+  b->uni = nullptr;
+  b->stepc = nullptr;
+  b->ev = nullptr;
+  b->dt = nullptr;
+  b->cap = 0;
+  b->chunk_req = 0;
+  b->fgraph = nullptr;
+  b->t0 = b->t1 = nullptr;
   b->msg[0] = 0;
   *out = b;
   int dev = -1;
@@ -1106,6 +1264,64 @@ int kmc_batch_create(kmc_batch_handle* out, int count, const kmc_handle* handles
     if (cudaStreamCreateWithFlags(&b->streams[r], cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->join[r], cudaEventDisableTiming) != cudaSuccess)
       return bfail(b, KMC_ERR_CUDA, "stream / event creation failed");
+  if (cudaEventCreate(&b->t0) != cudaSuccess || cudaEventCreate(&b->t1) != cudaSuccess)
+    return bfail(b, KMC_ERR_CUDA, "event creation failed");
+  // batched kernels when the members share the kernels' template choices
+  bool same = true;
+  for (int r = 1; r < count; r++) {
+    const kmc_fmm* a = b->h[0];
+    const kmc_fmm* h = b->h[r];
+    if (h->prec != a->prec || h->g.nhop != a->g.nhop || h->g.near_cache != a->g.near_cache) same = false;
+  }
+  for (int r = 0; r < count; r++)
+    if (b->h[r]->g.dirichlet) same = false;
+  if (same) {
+    if (cudaMalloc(&b->reps, sizeof(BatchRep) * count) != cudaSuccess ||
+        cudaMalloc(&b->stepc, sizeof(int) * count) != cudaSuccess) {
+      cudaGetLastError();
+      return bfail(b, KMC_ERR_OOM, "batch descriptors: device allocation failed");
+    }
+    int rc = batch_plan(b);
+    if (rc) return rc;
+    b->fused = true;
+  }
+  return KMC_OK;
+}
+
+int kmc_batch_set_chunk(kmc_batch_handle b, int chunk) {
+  KMC_TRACE("kmc_batch_set_chunk");
+  if (!b) return KMC_ERR_ARG;
+  if (!b->fused) return bfail(b, KMC_ERR_STATE, "the batch runs its members' own kernels (mixed modes)");
+  if (chunk < 0) return bfail(b, KMC_ERR_ARG, "negative pass capacity");
+  if (cudaSetDevice(b->h[0]->device) != cudaSuccess) return bfail(b, KMC_ERR_CUDA, "cudaSetDevice failed");
+  if (b->s0) cudaStreamSynchronize(b->s0);
+  const int old = b->chunk_req;
+  b->chunk_req = chunk;
+  int rc = batch_plan(b);
+  if (rc) {
+    b->chunk_req = old;
+    batch_plan(b);
+    return rc;
+  }
+  if (b->fgraph) cudaGraphExecDestroy(b->fgraph);
+  b->fgraph = nullptr;
+  return KMC_OK;
+}
+
+int kmc_batch_info(kmc_batch_handle b, int* fused, int* chunk, int* launches_per_step) {
+  if (!b) return KMC_ERR_ARG;
+  if (fused) *fused = b->fused ? 1 : 0;
+  if (chunk) *chunk = b->fused ? b->bp.chunk_c[b->bp.nprop - 1] : 0;
+  if (launches_per_step) {
+    int n = 0;
+    if (b->fused) {
+      n = 1 + 5 + b->bp.nprop + (b->bp.near_cache ? 1 : 0);
+      for (int l = 2; l <= b->bp.Lmax; l++) n += b->bp.nblk_down[l] > 0;
+    } else {
+      for (kmc_fmm* h : b->h) n += h->g.L + 7 + (h->g.near_cache ? 1 : 0) + (h->g.dirichlet ? 3 : 0);
+    }
+    *launches_per_step = n;
+  }
   return KMC_OK;
 }
 
@@ -1123,6 +1339,15 @@ void kmc_batch_destroy(kmc_batch_handle b) {
   if (!b->h.empty()) cudaSetDevice(b->h[0]->device);
   if (b->s0) cudaStreamSynchronize(b->s0);
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->fgraph) cudaGraphExecDestroy(b->fgraph);
+  cudaFree(b->reps);
+  cudaFree(b->offs);
+  cudaFree(b->uni);
+  cudaFree(b->stepc);
+  cudaFree(b->ev);
+  cudaFree(b->dt);
+  if (b->t0) cudaEventDestroy(b->t0);
+  if (b->t1) cudaEventDestroy(b->t1);
   for (size_t r = 0; r < b->streams.size(); r++) {
     if (b->streams[r]) cudaStreamDestroy(b->streams[r]);
     if (b->join[r]) cudaEventDestroy(b->join[r]);
@@ -1132,15 +1357,112 @@ void kmc_batch_destroy(kmc_batch_handle b) {
   delete b;
 }
 
-int kmc_batch_run(kmc_batch_handle b, int steps, const double* uniforms, int64_t* events, double* dts) {
-  KMC_TRACE("kmc_batch_run");
+#define BCK(call, what)                                                                              \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) return bfail(b, KMC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e_));   \
+  } while (0)
+
+// the batched-kernel path: K steps of every member, device time in *ms
+static int batch_run_fused(kmc_batch* b, int steps, const double* uniforms, int64_t* events, double* dts,
+                           double* ms) {
+  const int R = (int)b->h.size();
+  int rc = batch_reserve(b, steps);
+  if (rc) return rc;
+  const size_t cap = (size_t)b->cap;
+  b->reps_host.resize(R);
+  for (int r = 0; r < R; r++) {
+    kmc_fmm* h = b->h[r];
+    BatchRep& x = b->reps_host[r];
+    x.g = h->g;
+    x.d = h->d;
+    x.d.uni_run = b->uni + 2 * cap * r;
+    x.d.ev_hist = b->ev + cap * r;
+    x.d.dt_hist = b->dt + cap * r;
+    x.d.stepc = b->stepc + r;
+    if (h->stream) BCK(cudaStreamSynchronize(h->stream), "member stream synchronisation");
+  }
+  // uniforms [step][member][2] -> [member][step][2] with row pitch 2 cap
+  std::vector<double> col(2 * (size_t)steps * R);
+  for (int r = 0; r < R; r++)
+    for (int st = 0; st < steps; st++) {
+      col[((size_t)r * steps + st) * 2] = uniforms[((size_t)st * R + r) * 2];
+      col[((size_t)r * steps + st) * 2 + 1] = uniforms[((size_t)st * R + r) * 2 + 1];
+    }
+  cudaStream_t s = b->s0;
+  BCK(cudaMemcpy2DAsync(b->uni, sizeof(double) * 2 * cap, col.data(), sizeof(double) * 2 * steps,
+                        sizeof(double) * 2 * steps, R, cudaMemcpyHostToDevice, s), "staging uniforms");
+  BCK(cudaMemcpyAsync(b->reps, b->reps_host.data(), sizeof(BatchRep) * R, cudaMemcpyHostToDevice, s),
+      "staging member descriptors");
+  BCK(cudaMemsetAsync(b->stepc, 0, sizeof(int) * R, s), "clearing step counters");
+  if (!b->fgraph) {
+    cudaGraph_t gr = nullptr;
+    BCK(cudaStreamSynchronize(s), "stream synchronisation");
+    BCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture begin");
+    for (int k = 0; k < KMC_GRAPH_STEPS; k++) {
+      fmm_downward_batch(b->bp, s);
+      kmc_step_batch(b->bp, s);
+    }
+    cudaError_t le = cudaGetLastError();
+    cudaError_t ce = cudaStreamEndCapture(s, &gr);
+    if (le != cudaSuccess || ce != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      return bfail(b, KMC_ERR_CUDA, "batch graph capture failed: %s / %s", cudaGetErrorString(le),
+                   cudaGetErrorString(ce));
+    }
+    ce = cudaGraphInstantiate(&b->fgraph, gr, 0);
+    cudaGraphDestroy(gr);
+    if (ce != cudaSuccess) {
+      b->fgraph = nullptr;
+      return bfail(b, KMC_ERR_CUDA, "batch graph instantiate failed: %s", cudaGetErrorString(ce));
+    }
+  }
+  BCK(cudaEventRecord(b->t0, s), "event record");
+  const int full = steps / KMC_GRAPH_STEPS, rest = steps % KMC_GRAPH_STEPS;
+  for (int k = 0; k < full; k++) BCK(cudaGraphLaunch(b->fgraph, s), "graph launch");
+  for (int k = 0; k < rest; k++) {
+    fmm_downward_batch(b->bp, s);
+    kmc_step_batch(b->bp, s);
+  }
+  BCK(cudaGetLastError(), "batch kernel launch");
+  BCK(cudaEventRecord(b->t1, s), "event record");
+  BCK(cudaStreamSynchronize(s), "batch run");
+  if (ms) {
+    float f = 0.f;
+    BCK(cudaEventElapsedTime(&f, b->t0, b->t1), "event timing");
+    *ms = f;
+  }
+  std::vector<int64_t> ev((size_t)steps * R);
+  std::vector<double> dt((size_t)steps * R);
+  BCK(cudaMemcpy2D(ev.data(), sizeof(int64_t) * steps, b->ev, sizeof(int64_t) * cap, sizeof(int64_t) * steps, R,
+                   cudaMemcpyDeviceToHost), "reading events");
+  BCK(cudaMemcpy2D(dt.data(), sizeof(double) * steps, b->dt, sizeof(double) * cap, sizeof(double) * steps, R,
+                   cudaMemcpyDeviceToHost), "reading time increments");
+  for (int r = 0; r < R; r++) {
+    kmc_fmm* h = b->h[r];
+    h->peff_valid = false;
+    h->rates_valid = false;
+    int rc2 = check_flags(h, "batch run");
+    if (rc2) return bfail(b, rc2, "member %d: %s", r, h->msg);
+    for (int st = 0; st < steps; st++) {
+      if (events) events[(size_t)st * R + r] = ev[(size_t)r * steps + st];
+      if (dts) dts[(size_t)st * R + r] = dt[(size_t)r * steps + st];
+    }
+  }
+  return KMC_OK;
+}
+
+static int batch_run_impl(kmc_batch* b, int steps, const double* uniforms, int64_t* events, double* dts,
+                          double* ms) {
   if (!b) return KMC_ERR_ARG;
   const int R = (int)b->h.size();
   if (steps < 0 || !uniforms) return bfail(b, KMC_ERR_ARG, "steps >= 0 and uniforms are required");
+  if (ms) *ms = 0.0;
   if (steps == 0) return KMC_OK;
   if (cudaSetDevice(b->h[0]->device) != cudaSuccess) return bfail(b, KMC_ERR_CUDA, "cudaSetDevice failed");
   for (int r = 0; r < R; r++)
     if (b->h[r]->broken) return bfail(b, KMC_ERR_STATE, "member %d broken: %s", r, b->h[r]->msg);
+  if (b->fused) return batch_run_fused(b, steps, uniforms, events, dts, ms);
   // per-member buffers for the uniforms and the event history
   int need = steps;
   bool realloc = false;
@@ -1216,9 +1538,16 @@ int kmc_batch_run(kmc_batch_handle b, int steps, const double* uniforms, int64_t
     b->gen.resize(R);
     for (int r = 0; r < R; r++) b->gen[r] = b->h[r]->run_gen;
   }
+  if (cudaEventRecord(b->t0, b->s0) != cudaSuccess) return bfail(b, KMC_ERR_CUDA, "event record failed");
   for (int s = 0; s < steps; s++)
     if (cudaGraphLaunch(b->graph, b->s0) != cudaSuccess) return bfail(b, KMC_ERR_CUDA, "graph launch failed");
+  if (cudaEventRecord(b->t1, b->s0) != cudaSuccess) return bfail(b, KMC_ERR_CUDA, "event record failed");
   if (cudaStreamSynchronize(b->s0) != cudaSuccess) return bfail(b, KMC_ERR_CUDA, "batch run failed");
+  if (ms) {
+    float f = 0.f;
+    if (cudaEventElapsedTime(&f, b->t0, b->t1) != cudaSuccess) return bfail(b, KMC_ERR_CUDA, "event timing failed");
+    *ms = f;
+  }
   std::vector<int64_t> ev(steps);
   std::vector<double> dt(steps);
   for (int r = 0; r < R; r++) {
@@ -1236,6 +1565,17 @@ int kmc_batch_run(kmc_batch_handle b, int steps, const double* uniforms, int64_t
     }
   }
   return KMC_OK;
+}
+
+int kmc_batch_run(kmc_batch_handle b, int steps, const double* uniforms, int64_t* events, double* dts) {
+  KMC_TRACE("kmc_batch_run");
+  return batch_run_impl(b, steps, uniforms, events, dts, nullptr);
+}
+
+int kmc_batch_run_timed(kmc_batch_handle b, int steps, const double* uniforms, int64_t* events, double* dts,
+                        double* device_ms) {
+  KMC_TRACE("kmc_batch_run_timed");
+  return batch_run_impl(b, steps, uniforms, events, dts, device_ms);
 }
 
 }  // extern "C"
