@@ -70,13 +70,11 @@ def aggregate(units: float, ms: float, device=None):
     return float(u.item()), float(m.item())
 
 
-# per KMC step: downward root + (L - 1) levels, propose, finalize, select,
-# record, move-from-event and two accept kernels
 def launches_per_step(L: int, bc: str = "periodic") -> int:
-    """Kernels of one device-driven step: the downward pass (root and levels 2..L: L launches),
-    propose, rates, select, move record, event decode, the fused accept and its coarse reduction;
-    grounded walls add the mirror move and its accept (3)."""
-    return L + 7 + (3 if bc == "dirichlet" else 0)
+    """Kernels of one device-driven step: the downward pass (levels 2..4 in one launch, each deeper
+    level one), propose, rates, select, move record, event decode, the fused accept and its coarse
+    reduction; grounded walls add the mirror move and its accept (3)."""
+    return 1 + max(L - 4, 0) + 7 + (3 if bc == "dirichlet" else 0)
 
 
 # --------------------------------------------------------------- algorithmic work

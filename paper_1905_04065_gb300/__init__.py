@@ -530,3 +530,4 @@ def kmc_check_bounded_wait(device: int = 0, limit_seconds: float = 0.05) -> int:
     """Status of the bounded-wait diagnostic: KMC_ERR_TIMEOUT (6) when the
     device-side wait gave up and returned as designed."""
     return int(load_library().kmc_check_bounded_wait(int(device), float(limit_seconds)))
+

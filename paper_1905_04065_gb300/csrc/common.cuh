@@ -37,6 +37,15 @@ __host__ __device__ __forceinline__ constexpr int hop_c(int k, int a) {
   return k < 6 ? ((k >> 1) == a ? ((k & 1) ? -1 : 1) : 0) : ((((k - 6) >> a) & 1) ? -1 : 1);
 }
 #define KMC_FIN_PARTICLES 128  // particles per block sum of the rates
+#define KMC_DOWN_COARSE 4      // downward levels 2 .. 4 (fewer than 512 parents) share one launch
+// R(c_b - c_a) for a cell b of level l <= KMC_DOWN_COARSE and its ancestor a of level la < l, one
+// table per position of b inside a: 8^(l - la) tables for (l, la), in the order (2,1), (3,1),
+// (3,2), (4,1), (4,2), (4,3): 8 + 64 + 8 + 512 + 64 + 8
+#define KMC_COARSE_TABLES 664
+__host__ __device__ __forceinline__ int coarse_table_base(int l, int la) {
+  // first table of (l, la) in the order above
+  return l == 2 ? 0 : l == 3 ? (la == 1 ? 8 : 72) : (la == 1 ? 80 : la == 2 ? 592 : 656);
+}
 // Periodic images nu with |nu|_inf <= KMC_TOP are handled by the tree (the
 // level-2 interaction list covers the (2 KMC_TOP + 1)^3 block of domain copies);
 // the rest are the far field V_inf of the lattice operator.
@@ -139,6 +148,7 @@ struct Dev {
   double2* Itab;      // M2L irregular values [(L+1) * 343 * P2]
   double2* Itab2;     // level-2 M2L irregular values [KMC_TOP_NOFF * P2]
   double2* Rch;       // child-offset regular harmonics [(L+1) * 8 * P]
+  double2* Rcoarse;   // ancestor-offset regular harmonics of levels 2..KMC_DOWN_COARSE [KMC_COARSE_TABLES * P]
   double2* S;         // lattice sums over the far images [P2]
   double* selfc;      // [KMC_MAXHOP] self-pair correction C(d) per hop direction
   // Dirichlet walls: C(d) of the charge-mirror displacements, FP64 and FP32
@@ -157,6 +167,7 @@ struct Dev {
   float* selfc32;     // [KMC_MAXHOP]
   float2* Psi32;      // per-level locals, all levels
   float2* Rch32;      // child-offset regular harmonics
+  float2* Rcoarse32;  // ancestor-offset regular harmonics
   float* phi_old32;   // [n]
   float* phi_new32;   // [nhop n]
   float* dU32;        // [6n]
@@ -259,7 +270,7 @@ void fmm_bin(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_p2m(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_m2m(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_itab(const Geo& g, const Dev& d, cudaStream_t s);
-void fmm_child_tables(const Geo& g, const Dev& d, cudaStream_t s);
+void fmm_child_tables(const Geo& g, const Dev& d, cudaStream_t s);  // child and ancestor offset tables
 size_t fmm_m2l_scratch_bytes(const Geo& g);
 void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s);
 void fmm_dirichlet_tables(const Geo& g, const Dev& d, cudaStream_t s);
@@ -328,6 +339,7 @@ struct BatchPlan {
   int nblk_nu;
 };
 void fmm_downward_batch(const BatchPlan& bp, cudaStream_t s);
+size_t fmm_coarse_smem(int p, int prec);  // dynamic shared memory of the coarse-level downward kernel
 void kmc_step_batch(const BatchPlan& bp, cudaStream_t s);  // propose, rates, select, record, accept
 void kmc_batch_prepare(const BatchPlan& bp);                // load the kernels, raise their smem limits
 int kmc_propose_chunk_min(const Geo& g);                    // smallest pass capacity for g's leaves

@@ -59,6 +59,27 @@ __device__ void regular_table(double x, double y, double z, int p, double2* out)
   }
 }
 
+// Column m of the same table, out[tri(n, m)] for n = m .. p (the same
+// operations as regular_table, so the same values): p + 1 threads build a table.
+__device__ void regular_column(double x, double y, double z, int p, int m, double2* out) {
+  const double r2 = x * x + y * y + z * z;
+  double2 mm = make_double2(1.0, 0.0);
+  for (int j = 1; j <= m; j++) {
+    const double s = -0.5 / j;
+    mm = make_double2(s * (x * mm.x - y * mm.y), s * (x * mm.y + y * mm.x));
+  }
+  out[tri(m, m)] = mm;
+  double2 a2 = make_double2(0.0, 0.0), a1 = mm;
+  for (int n = m + 1; n <= p; n++) {
+    const double c = f_inv_nm[tri(n, m)];
+    const double zz = (2 * n - 1) * z;
+    const double2 v = make_double2((zz * a1.x - r2 * a2.x) * c, (zz * a1.y - r2 * a2.y) * c);
+    out[tri(n, m)] = v;
+    a2 = a1;
+    a1 = v;
+  }
+}
+
 // Full table of irregular harmonics I_n^m(x), 0 <= m <= n <= p (FP64).
 __device__ void irregular_table(double x, double y, double z, int p, double2* out, int64_t stride = 1) {
   double r2 = x * x + y * y + z * z;
@@ -207,7 +228,32 @@ __global__ void k_child_tables(const Geo g, const Dev d) {
     for (int c = 0; c < g.P; c++) d.Rch32[((int64_t)l * 8 + o) * g.P + c] = make_float2((float)out[c].x, (float)out[c].y);
 }
 
-void fmm_child_tables(const Geo& g, const Dev& d, cudaStream_t s) { k_child_tables<<<g.L - 1, 32, 0, s>>>(g, d); }
+// R(c_b - c_a) for every position of a cell b of level l (2 .. KMC_DOWN_COARSE) inside its
+// ancestor a of level la: block = table, thread = column m
+__global__ void k_coarse_tables(const Geo g, const Dev d) {
+  int t = blockIdx.x, l = 2, la = 1;
+  for (l = 2; l <= KMC_DOWN_COARSE; l++) {
+    for (la = 1; la < l; la++) {
+      const int nt = 1 << (3 * (l - la));
+      if (t < coarse_table_base(l, la) + nt) goto found;
+    }
+  }
+  return;
+found:
+  const int i = t - coarse_table_base(l, la), k = 1 << (l - la);  // position of b inside a, k per axis
+  const double wl = g.a / (1 << (l - 1)), half = 0.5 * k;
+  const double ox = ((i % k) + 0.5 - half) * wl, oy = (((i / k) % k) + 0.5 - half) * wl, oz = ((i / (k * k)) + 0.5 - half) * wl;
+  double2* out = d.Rcoarse + (int64_t)t * g.P;
+  if ((int)threadIdx.x <= g.p) regular_column(ox, oy, oz, g.p, threadIdx.x, out);
+  __syncthreads();
+  if (d.Rcoarse32)
+    for (int c = threadIdx.x; c < g.P; c += blockDim.x) d.Rcoarse32[(int64_t)t * g.P + c] = make_float2((float)out[c].x, (float)out[c].y);
+}
+
+void fmm_child_tables(const Geo& g, const Dev& d, cudaStream_t s) {
+  k_child_tables<<<g.L - 1, 32, 0, s>>>(g, d);
+  k_coarse_tables<<<KMC_COARSE_TABLES, 32, 0, s>>>(g, d);
+}
 
 // ------------------------------------------------------------------ M2M
 // level l (parents, n_l per side) from level l+1.  thread per (parent, coefficient)
@@ -1161,67 +1207,125 @@ template <typename T> __device__ __forceinline__ typename cplx<T>::type child_co
 template <> __device__ __forceinline__ float2 child_coef<float>(const Dev& d, int64_t idx) { return d.Rch32[idx]; }
 template <> __device__ __forceinline__ double2 child_coef<double>(const Dev& d, int64_t idx) { return d.Rch[idx]; }
 
-template <typename T>
-__global__ void k_downward_root(const Geo g, const Dev d) {
-  typedef typename cplx<T>::type C;
-  C* Pe = (C*)d.Peff;
-  for (int c = threadIdx.x; c < g.P; c += blockDim.x) Pe[g.cell_off[1] * g.P + c] = own_coef<T>(d, g.cell_off[1] * g.P + c);
-}
 
-// Downward pass for levels with few cells, one level per launch: CTA per
-// child cell, thread per output coefficient.  The parent's expansion and the child-offset table are first
-// expanded to every order -n..n (the conjugate symmetry applied once), so the
-// inner loop is branch-free: out(k, lo) = sum_{n >= k} sum_m L(n, m) R(n - k, m - lo).
 template <typename T> __device__ __forceinline__ const typename cplx<T>::type* child_table(const Dev& d);
 template <> __device__ __forceinline__ const float2* child_table<float>(const Dev& d) { return d.Rch32; }
 template <> __device__ __forceinline__ const double2* child_table<double>(const Dev& d) { return d.Rch; }
 
+
+// Downward pass of the levels with few cells, 2 .. lc, in one launch (CTA per
+// cell, thread per output coefficient).  The expansion of cell b on level l is
+// the sum over its ancestors a on levels 1 .. l - 1 (level 1: H) of the L2L of
+// their interaction-list expansions to its centre, plus its own:
+//   Peff_l[b] = Psi_l[b] + sum_{l' < l} L2L(Psi_l'[a_l'(b)] -> c_b).
+// The L2L of a degree-p local expansion is exact and L2L(a -> b) L2L(c -> a) =
+// L2L(c -> b), so this equals the level-by-level recursion up to rounding,
+// without one dependent launch per level.  The offset tables R(c_b - c_a) are
+// built at init (k_coarse_tables), one per position of b inside a.
+template <typename T> __device__ __forceinline__ const typename cplx<T>::type* own_ptr(const Dev& d);
+template <> __device__ __forceinline__ const float2* own_ptr<float>(const Dev& d) { return d.Psi32; }
+template <> __device__ __forceinline__ const double2* own_ptr<double>(const Dev& d) { return d.Psi; }
+
+#define DC_PER 3  // output coefficients per thread: 128 threads cover P <= 384
+template <typename T> __device__ __forceinline__ const typename cplx<T>::type* coarse_tab(const Dev& d);
+template <> __device__ __forceinline__ const float2* coarse_tab<float>(const Dev& d) { return d.Rcoarse32; }
+template <> __device__ __forceinline__ const double2* coarse_tab<double>(const Dev& d) { return d.Rcoarse; }
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_downward_cell(const Geo g, const Dev d, int l) {
+__device__ __forceinline__ void downward_coarse_blk(const Geo& g, const Dev& d, const int lc, const int blk0) {
   typedef typename cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char shraw[];
   const int F = (g.p + 1) * (g.p + 1);
-  C* Lf = (C*)shraw;  // [F] parent expansion, entry n^2 + n + m
-  C* Rf = Lf + F;     // [F] child-offset regular table, same order
-  const int nl = 1 << (l - 1), np = nl / 2;
-  const int64_t cell = blockIdx.x;
-  const int bx = (int)(cell % nl), by = (int)((cell / nl) % nl), bz = (int)(cell / ((int64_t)nl * nl));
-  const int64_t par = (bx >> 1) + (int64_t)np * ((by >> 1) + (int64_t)np * (bz >> 1));
-  const int o = (bx & 1) + 2 * (by & 1) + 4 * (bz & 1);
-  const C* Pp = (const C*)d.Peff + (g.cell_off[l - 1] + par) * g.P;
-  const C* Ro = child_table<T>(d) + ((int64_t)l * 8 + o) * g.P;
-  for (int t = threadIdx.x; t < F; t += blockDim.x) {
-    int n = (int)sqrtf((float)t);
-    while ((n + 1) * (n + 1) <= t) n++;
-    while (n * n > t) n--;
-    const int m = t - n * n - n;
-    Lf[t] = tab_get(Pp, n, m);
-    Rf[t] = tab_get(Ro, n, m);
+  C* Lf = (C*)shraw;  // [F] ancestor expansion, entry n^2 + n + m
+  C* Rf = Lf + F;     // [F] offset table, same order
+  int64_t b = (int64_t)blockIdx.x - blk0;
+  int l = 2;
+  while (l < lc && b >= ((int64_t)1 << (3 * (l - 1)))) {
+    b -= (int64_t)1 << (3 * (l - 1));
+    l++;
   }
-  __syncthreads();
-  C* Pe = (C*)d.Peff;
-  for (int ci = threadIdx.x; ci < g.P; ci += blockDim.x) {
-    const short2 km = f_nm[ci];
-    const int k = km.x, lo = km.y;
-    T ax = 0, ay = 0;
-    for (int n = k; n <= g.p; n++) {
-      const int j = n - k;
-      const int mlo = max(lo - j, -n), mhi = min(lo + j, n);
-      const C* a = Lf + n * n + n;
-      const C* b = Rf + j * j + j - lo;
-      for (int m = mlo; m <= mhi; m++) {
-        const C u = a[m], v = b[m];
-        ax += u.x * v.x - u.y * v.y;
-        ay += u.x * v.y + u.y * v.x;
-      }
+  const int nl = 1 << (l - 1);
+  const int bx = (int)(b % nl), by = (int)((b / nl) % nl), bz = (int)(b / ((int64_t)nl * nl));
+  T ax[DC_PER], ay[DC_PER];
+#pragma unroll
+  for (int j = 0; j < DC_PER; j++) ax[j] = ay[j] = (T)0;
+  const C* own = own_ptr<T>(d);
+  for (int la = 1; la < l; la++) {
+    const int na = 1 << (la - 1), sh = l - la;
+    const int Ax = bx >> sh, Ay = by >> sh, Az = bz >> sh;
+    const int64_t acell = Ax + (int64_t)na * (Ay + (int64_t)na * Az);
+    const int k = 1 << sh;  // b's position inside a, k per axis
+    const C* Ro = coarse_tab<T>(d) +
+                  (int64_t)(coarse_table_base(l, la) + (bx & (k - 1)) + k * ((by & (k - 1)) + k * (bz & (k - 1)))) * g.P;
+    __syncthreads();  // the previous ancestor's tables are consumed
+    const C* Pa = own + (g.cell_off[la] + acell) * g.P;
+    for (int t = threadIdx.x; t < F; t += blockDim.x) {
+      const int n = (int)sqrtf((float)t + 0.5f), m = t - n * n - n;  // exact: sqrt(n^2 - 1/2) < n <= sqrt(n^2 + 1/2)
+      Lf[t] = tab_get(Pa, n, m);
+      Rf[t] = tab_get(Ro, n, m);
     }
-    const int64_t at = (g.cell_off[l] + cell) * g.P + ci;
-    const C own = own_coef<T>(d, at);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < DC_PER; j++) {
+      const int ci = threadIdx.x + j * blockDim.x;
+      if (ci >= g.P) break;
+      const short2 km = f_nm[ci];
+      const int k = km.x, lo = km.y;
+      T sx = 0, sy = 0;
+      for (int n = k; n <= g.p; n++) {
+        const int jj = n - k;
+        const int mlo = max(lo - jj, -n), mhi = min(lo + jj, n);
+        const C* a = Lf + n * n + n;
+        const C* r = Rf + jj * jj + jj - lo;
+        for (int m = mlo; m <= mhi; m++) {
+          const C u = a[m], v = r[m];
+          sx += u.x * v.x - u.y * v.y;
+          sy += u.x * v.y + u.y * v.x;
+        }
+      }
+      ax[j] += sx;
+      ay[j] += sy;
+    }
+  }
+  C* Pe = (C*)d.Peff;
+#pragma unroll
+  for (int j = 0; j < DC_PER; j++) {
+    const int ci = threadIdx.x + j * blockDim.x;
+    if (ci >= g.P) break;
+    const int64_t at = (g.cell_off[l] + b) * g.P + ci;
+    const C o = own[at];
     C v;
-    v.x = ax + own.x;
-    v.y = ay + own.y;
+    v.x = ax[j] + o.x;
+    v.y = ay[j] + o.y;
     Pe[at] = v;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_downward_coarse(const Geo g, const Dev d, int lc) {
+  downward_coarse_blk<T>(g, d, lc, 0);
+}
+
+// level 1 of every member of a batch: H (the parent expansion of level 2)
+template <typename T>
+__global__ void k_downward_root_batch(const BatchRep* reps) {
+  typedef typename cplx<T>::type C;
+  const Geo& g = reps[blockIdx.x].g;
+  const Dev& d = reps[blockIdx.x].d;
+  C* Pe = (C*)d.Peff;
+  const C* own = own_ptr<T>(d);
+  for (int c = threadIdx.x; c < g.P; c += blockDim.x) Pe[g.cell_off[1] * g.P + c] = own[g.cell_off[1] * g.P + c];
+}
+
+// cells of levels 2 .. lc
+static __host__ __device__ __forceinline__ int64_t coarse_cells(int lc) {
+  int64_t n = 0;
+  for (int l = 2; l <= lc; l++) n += (int64_t)1 << (3 * (l - 1));
+  return n;
+}
+size_t fmm_coarse_smem(int p, int prec) {
+  const int F = (p + 1) * (p + 1);
+  return 2 * (size_t)F * (prec == 0 ? sizeof(double2) : sizeof(float2));
 }
 
 // Downward pass, one level per launch: CTA per parent cell of level l - 1,
@@ -1296,29 +1400,19 @@ __global__ void __launch_bounds__(256) k_downward_par_batch(const BatchRep* reps
   downward_par_blk<T>(reps[r].g, reps[r].d, l, off[r]);
 }
 
-// level 1 of every member: the leaf-independent part H
-template <typename T>
-__global__ void k_downward_root_batch(const BatchRep* reps) {
-  typedef typename cplx<T>::type C;
-  const Geo& g = reps[blockIdx.x].g;
-  const Dev& d = reps[blockIdx.x].d;
-  C* Pe = (C*)d.Peff;
-  for (int c = threadIdx.x; c < g.P; c += blockDim.x) Pe[g.cell_off[1] * g.P + c] = own_coef<T>(d, g.cell_off[1] * g.P + c);
-}
 
 void fmm_prepare(const Geo& g, int prec) {
   // load every per-step kernel now: with lazy module loading a first launch
   // inside a stream capture would invalidate the capture
   cudaFuncAttributes fa;
-  cudaFuncGetAttributes(&fa, k_downward_root<double>);
-  cudaFuncGetAttributes(&fa, k_downward_root<float>);
-  cudaFuncGetAttributes(&fa, k_downward_cell<double>);
-  cudaFuncGetAttributes(&fa, k_downward_cell<float>);
   cudaFuncGetAttributes(&fa, k_downward_par<double>);
   cudaFuncGetAttributes(&fa, k_downward_par<float>);
   const int smax = 9 * (KMC_MAXP + 1) * (KMC_MAXP + 1) * (int)sizeof(double2);
   cudaFuncSetAttribute(k_downward_par<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
   cudaFuncSetAttribute(k_downward_par<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax / 2);
+  const int csm = (int)fmm_coarse_smem(KMC_MAXP, 0);
+  cudaFuncSetAttribute(k_downward_coarse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, csm);
+  cudaFuncSetAttribute(k_downward_coarse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, csm);
   cudaFuncGetAttributes(&fa, k_downward_root_batch<double>);
   cudaFuncGetAttributes(&fa, k_downward_root_batch<float>);
   cudaFuncSetAttribute(k_downward_par_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
@@ -1327,20 +1421,19 @@ void fmm_prepare(const Geo& g, int prec) {
   (void)prec;
 }
 
+// the levels with fewer than 512 parents (2 .. 4) in one launch, the rest one launch per level
+static int coarse_top(int L) { return L < KMC_DOWN_COARSE ? L : KMC_DOWN_COARSE; }
+
 void fmm_downward(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
-  if (prec == 0) k_downward_root<double><<<1, 128, 0, s>>>(g, d);
-  else k_downward_root<float><<<1, 128, 0, s>>>(g, d);
-  const size_t smc = (size_t)2 * (g.p + 1) * (g.p + 1) * (prec == 0 ? sizeof(double2) : sizeof(float2));
+  const int lc = coarse_top(g.L);
+  const size_t smc = fmm_coarse_smem(g.p, prec);
   const size_t smp = (size_t)9 * (g.p + 1) * (g.p + 1) * (prec == 0 ? sizeof(double2) : sizeof(float2));
-  for (int l = 2; l <= g.L; l++) {
+  if (prec == 0) k_downward_coarse<double><<<(unsigned)coarse_cells(lc), 128, smc, s>>>(g, d, lc);
+  else k_downward_coarse<float><<<(unsigned)coarse_cells(lc), 128, smc, s>>>(g, d, lc);
+  for (int l = lc + 1; l <= g.L; l++) {
     const unsigned parents = 1u << (3 * (l - 2));
-    if (parents < 512) {  // few cells: one CTA per child keeps the latency of a level short
-      if (prec == 0) k_downward_cell<double><<<8 * parents, 128, smc, s>>>(g, d, l);
-      else k_downward_cell<float><<<8 * parents, 128, smc, s>>>(g, d, l);
-    } else {
-      if (prec == 0) k_downward_par<double><<<parents, 256, smp, s>>>(g, d, l);
-      else k_downward_par<float><<<parents, 256, smp, s>>>(g, d, l);
-    }
+    if (prec == 0) k_downward_par<double><<<parents, 256, smp, s>>>(g, d, l);
+    else k_downward_par<float><<<parents, 256, smp, s>>>(g, d, l);
   }
 }
 

@@ -943,7 +943,6 @@ __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
   const int r = batch_find(off, R, blockIdx.x);
   propose_leaf<T, NH, mode>(reps[r].g, reps[r].d, chunk, off[r]);
 }
-
 static size_t propose_smem(const Geo& g, int prec, int chunk) {
   const size_t ts = prec == 0 ? 8 : 4;
   const int W3 = g.W * g.W * g.W;
@@ -1557,6 +1556,51 @@ __device__ void p2l_column(double2* out, double q, double dx, double dy, double 
   }
 }
 
+// The same columns from a group of 16 lanes (p <= 15): lane m of the group
+// computes column m.  1/|d| and 1/|d|^2 are computed once (lane 0) and
+// broadcast, and the sectoral values I_m^m(d) = prod_{j <= m} f_j with f_0 =
+// 1/|d|, f_j = -(2j - 1) (dx + i dy) / |d|^2 come from an inclusive prefix
+// product over the lanes (four shuffle steps), instead of every thread
+// recomputing the square root, the division and its O(m) chain.  gmask: the
+// group's 16 lanes; every lane of the group calls this (lanes m > p only take
+// part in the shuffles).
+#define P2L_GROUP 16
+__device__ __forceinline__ void p2l_group_column(double q, double dx, double dy, double dz, int p, int m,
+                                                 unsigned gmask, double2* acc_out, bool accumulate) {
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  double inv = 0.0, rinv = 0.0;
+  if (m == 0) {
+    inv = 1.0 / r2;
+    rinv = 1.0 / sqrt(r2);
+  }
+  inv = __shfl_sync(gmask, inv, 0, P2L_GROUP);
+  rinv = __shfl_sync(gmask, rinv, 0, P2L_GROUP);
+  double2 f = m == 0 ? make_double2(rinv, 0.0)
+                     : make_double2(-(2.0 * m - 1.0) * inv * dx, -(2.0 * m - 1.0) * inv * dy);
+#pragma unroll
+  for (int o = 1; o < P2L_GROUP; o <<= 1) {
+    const double tx = __shfl_up_sync(gmask, f.x, o, P2L_GROUP), ty = __shfl_up_sync(gmask, f.y, o, P2L_GROUP);
+    if (m >= o) f = make_double2(tx * f.x - ty * f.y, tx * f.y + ty * f.x);
+  }
+  if (m > p) return;
+  double2 a1 = f, a2 = make_double2(0.0, 0.0), v = f;
+  for (int n = m; n <= p; n++) {
+    if (n > m) {
+      const double zz = (2 * n - 1) * dz;
+      const double c2 = (double)((n - 1) * (n - 1) - m * m);
+      v = make_double2((zz * a1.x - c2 * a2.x) * inv, (zz * a1.y - c2 * a2.y) * inv);
+      a2 = a1;
+      a1 = v;
+    }
+    if (accumulate) {
+      acc_out[n].x += q * v.x;
+      acc_out[n].y -= q * v.y;
+    } else {
+      acc_out[tri(n, m)] = make_double2(q * v.x, -q * v.y);
+    }
+  }
+}
+
 // the image nu (0..26) of position x, seen from cell b on level l: true when
 // its cell u = cell(x) + n_l nu lies in the interaction list of b, i.e.
 // |floor(u/2) - floor(b/2)|_inf <= 1 and |u - b|_inf >= 2.
@@ -1583,9 +1627,13 @@ __device__ __forceinline__ bool image_in_il(const int u0[3], int nl, int nu, con
 #define KMC_COARSE_SLOTS (KMC_L2_SLOTS + 64 * 54)
 #define KMC_COARSE_CELLS 72
 
+// lanes per P2L column set: a 16-lane group (p <= 15) or p + 1 threads (p > 15)
+__host__ __device__ __forceinline__ int p2l_lanes(int p) { return p < P2L_GROUP ? P2L_GROUP : p + 1; }
+
 __device__ __forceinline__ void acc_coarse_role(const Geo& g, const MoveRec& mv, double2* scratch, int t) {
-  // t = (slot, m)
-  const int slot = t / (g.p + 1), m = t - slot * (g.p + 1);
+  // t = (slot, m); with p <= 15 the 16 lanes of a slot form a shuffle group (slot uniform in it)
+  const int lanes = p2l_lanes(g.p);
+  const int slot = t / lanes, m = t - slot * lanes;
   if (slot >= KMC_COARSE_SLOTS) return;
   int l, cell, im, nimg1, span;
   if (slot < KMC_L2_SLOTS) {
@@ -1621,7 +1669,8 @@ __device__ __forceinline__ void acc_coarse_role(const Geo& g, const MoveRec& mv,
   }
   double dx = x[0] + g.a * nv[0] - (b[0] + 0.5) * wl, dy = x[1] + g.a * nv[1] - (b[1] + 0.5) * wl,
          dz = x[2] + g.a * nv[2] - (b[2] + 0.5) * wl;
-  p2l_column(out, q, dx, dy, dz, g.p, m);
+  if (g.p < P2L_GROUP) p2l_group_column(q, dx, dy, dz, g.p, m, 0xffffu << (threadIdx.x & 16), out, false);
+  else p2l_column(out, q, dx, dy, dz, g.p, m);
 }
 
 // one CTA (8 warps) per coarse cell: warp w sums the slots w, w + 8, ... of
@@ -1636,16 +1685,37 @@ __device__ __forceinline__ void acc_coarse_reduce_blk(const Geo& g, const Dev& d
   int l, cell, first, nslot;
   if (cc < 8) { l = 2; cell = cc; first = cc * 2 * KMC_TOP_NIMG; nslot = 2 * KMC_TOP_NIMG; }
   else { l = 3; cell = cc - 8; first = KMC_L2_SLOTS + cell * 54; nslot = 54; }
+  // eight slots in flight per lane (independent partial sums, combined in a fixed order)
+  constexpr int ILP = 8;
   for (int c0 = 0; c0 < g.P; c0 += 32) {
     const int c = c0 + lane;
-    double ax = 0.0, ay = 0.0;
-    if (c < g.P)
-      for (int s2 = warp; s2 < nslot; s2 += ACR_WARPS) {
-        const double2 v = scratch[((int64_t)first + s2) * g.P + c];
-        ax += v.x;
-        ay += v.y;
+    if (c >= g.P) continue;
+    double2 ps[ILP];
+#pragma unroll
+    for (int k = 0; k < ILP; k++) ps[k] = make_double2(0.0, 0.0);
+    int s2 = warp;
+    for (; s2 + (ILP - 1) * ACR_WARPS < nslot; s2 += ILP * ACR_WARPS) {
+      double2 v[ILP];
+#pragma unroll
+      for (int k = 0; k < ILP; k++) v[k] = scratch[((int64_t)first + s2 + k * ACR_WARPS) * g.P + c];
+#pragma unroll
+      for (int k = 0; k < ILP; k++) {
+        ps[k].x += v[k].x;
+        ps[k].y += v[k].y;
       }
-    if (c < g.P) acr[warp * g.P + c] = make_double2(ax, ay);
+    }
+    for (; s2 < nslot; s2 += ACR_WARPS) {
+      const double2 v = scratch[((int64_t)first + s2) * g.P + c];
+      ps[0].x += v.x;
+      ps[0].y += v.y;
+    }
+    double ax = 0.0, ay = 0.0;
+#pragma unroll
+    for (int k = 0; k < ILP; k++) {
+      ax += ps[k].x;
+      ay += ps[k].y;
+    }
+    acr[warp * g.P + c] = make_double2(ax, ay);
   }
   __syncthreads();
   for (int c = threadIdx.x; c < g.P; c += blockDim.x) {
@@ -1684,7 +1754,9 @@ __device__ __forceinline__ int wdist(int a, int b, int n) {
 }
 
 __device__ __forceinline__ void acc_fine_role(const Geo& g, const Dev& d, const MoveRec& mv, int l, int t) {
-  int cand = t / (g.p + 1), m = t % (g.p + 1);
+  // t = (candidate, m); with p <= 15 the 16 lanes of a candidate form a shuffle group
+  const int lanes = p2l_lanes(g.p);
+  int cand = t / lanes, m = t % lanes;
   if (cand >= 432) return;
   const int nl = 1 << (l - 1), np = nl >> 1;
   const double wl = g.a / nl;
@@ -1732,6 +1804,10 @@ __device__ __forceinline__ void acc_fine_role(const Geo& g, const Dev& d, const 
     any = true;
     const double dx = x[0] + g.a * nv[0] - (b[0] + 0.5) * wl, dy = x[1] + g.a * nv[1] - (b[1] + 0.5) * wl,
                  dz = x[2] + g.a * nv[2] - (b[2] + 0.5) * wl;
+    if (g.p < P2L_GROUP) {
+      p2l_group_column(q, dx, dy, dz, g.p, m, 0xffffu << (threadIdx.x & 16), acc, true);
+      continue;
+    }
     const double r2 = dx * dx + dy * dy + dz * dz, inv = 1.0 / r2;
     double2 mm = make_double2(1.0 / sqrt(r2), 0.0);
     for (int j = 1; j <= m; j++) {
@@ -1840,8 +1916,8 @@ __host__ __device__ __forceinline__ AccPlan acc_plan(const Geo& g) {
   ap.nmp = (g.L * g.P + ACC_THREADS - 1) / ACC_THREADS;
   ap.nfar = (g.P + ACC_THREADS / 32 - 1) / (ACC_THREADS / 32);
   // coarse levels 2 and 3 (8 + 64 cells, L >= 3 always): all cells x all images
-  ap.ncoarse = (KMC_COARSE_SLOTS * (g.p + 1) + ACC_THREADS - 1) / ACC_THREADS;
-  ap.fine_per_level = 432 * (g.p + 1);
+  ap.ncoarse = (KMC_COARSE_SLOTS * p2l_lanes(g.p) + ACC_THREADS - 1) / ACC_THREADS;
+  ap.fine_per_level = 432 * p2l_lanes(g.p);
   ap.nfine = g.L >= 4 ? (ap.fine_per_level * (g.L - 3) + ACC_THREADS - 1) / ACC_THREADS : 0;
   return ap;
 }

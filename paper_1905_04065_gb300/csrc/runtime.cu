@@ -461,6 +461,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   ALLOC(d.Itab2, sizeof(double2) * (size_t)KMC_TOP_NOFF * g.P2);
   ALLOC(d.S, sizeof(double2) * g.P2);
   ALLOC(d.Rch, sizeof(double2) * (size_t)(g.L + 1) * 8 * g.P);
+  ALLOC(d.Rcoarse, sizeof(double2) * (size_t)KMC_COARSE_TABLES * g.P);
   ALLOC(d.selfc, sizeof(double) * KMC_MAXHOP);
   if (g.dirichlet) {
     ALLOC(d.dirA, sizeof(double) * (g.E / 2));
@@ -474,6 +475,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
     ALLOC(d.selfc32, sizeof(float) * KMC_MAXHOP);
     ALLOC(d.Psi32, sizeof(float2) * g.ncell_total * g.P);
     ALLOC(d.Rch32, sizeof(float2) * (size_t)(g.L + 1) * 8 * g.P);
+    ALLOC(d.Rcoarse32, sizeof(float2) * (size_t)KMC_COARSE_TABLES * g.P);
     if (g.dirichlet) {
       ALLOC(d.dirA32, sizeof(float) * (g.E / 2));
       ALLOC(d.dirB32, sizeof(float) * (g.E / 2) * g.nhop);
@@ -1141,6 +1143,8 @@ static int batch_plan(kmc_batch* b) {
   size_t ts = bp.prec == 0 ? sizeof(double2) : sizeof(float2);
   bp.smem_down = 0;
   bp.smem_acr = 0;
+  // downward: one launch per level, the parent cells of the members that have the level (with many
+  // members a level's launch is wide enough; the single-system path fuses the coarse levels instead)
   for (int l = 2; l <= bp.Lmax; l++) {
     for (int r = 0; r < R; r++) cnt[r] = b->h[r]->g.L >= l ? 1 << (3 * (l - 2)) : 0;
     pos.push_back(all.size());
@@ -1315,7 +1319,7 @@ int kmc_batch_info(kmc_batch_handle b, int* fused, int* chunk, int* launches_per
   if (launches_per_step) {
     int n = 0;
     if (b->fused) {
-      n = 1 + 5 + b->bp.nprop + (b->bp.near_cache ? 1 : 0);
+      n = 1 + 5 + b->bp.nprop + (b->bp.near_cache ? 1 : 0);  // level 1, rates .. accept, propose(s)
       for (int l = 2; l <= b->bp.Lmax; l++) n += b->bp.nblk_down[l] > 0;
     } else {
       for (kmc_fmm* h : b->h) n += h->g.L + 7 + (h->g.near_cache ? 1 : 0) + (h->g.dirichlet ? 3 : 0);

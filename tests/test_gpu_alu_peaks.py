@@ -38,6 +38,8 @@ def test_alu_peaks_bound_the_derived_roofline(tmp_path):
     assert m["mufu_rsqrt_tops"] <= 1.02 * mufu_peak
     assert m["fp32_fma_tflops"] <= 1.02 * fp32_peak
     assert m["fp64_fma_tflops"] <= 1.02 * fp64_peak
+    # packed FP32x2 FMA: at most two lanes' FMAs per FP32 lane and clock
+    assert m["fp32x2_fma_tflops"] <= 1.02 * 2 * fp32_peak
     # and the units do run at their nominal widths (a clock of at least 1.5 GHz under this load)
     assert m["mufu_rsqrt_tops"] >= 16 * sms * 1.5e9 / 1e12
     assert m["fp32_fma_tflops"] >= 2 * 128 * sms * 1.5e9 / 1e12

@@ -1,9 +1,12 @@
 """Replica batches (the ensemble parallelism of Sec. 5.4, on one GPU).
 
 * The batched kernels (every launch covering all members) give the same
-  events, times and positions as running each member alone, in both
-  precisions and with the near-field cache; members of mixed modes fall back
-  to their own kernels as parallel graph branches, with the same results.
+  events and positions as running each member alone, in both precisions and
+  with the near-field cache, and the same time increments up to rounding (the
+  single-system downward pass sums the coarse levels' translations in one
+  launch, the batch level by level: the same expansions in another order);
+  members of mixed modes fall back to their own kernels as parallel graph
+  branches, with identical results.
 * Config-4 replicas (64 systems, edges 32..128, occupancy U[0.02, 0.15],
   p = 10, mixed form) through the batched path against the oracle: every
   event equals the oracle's selection from the exact dU with the same
@@ -28,7 +31,7 @@ def _replicas():
     return out
 
 
-def _same_as_single_runs(make, steps, seed, twice=False):
+def _same_as_single_runs(make, steps, seed, twice=False, rtol=1e-6):
     import paper_1905_04065_gb300 as k
     reps = _replicas()
     rng = np.random.default_rng(seed)
@@ -44,7 +47,7 @@ def _same_as_single_runs(make, steps, seed, twice=False):
     for r, h in enumerate(make()):
         ev, dt = k.kmc_run(h, u[:, r, :])
         assert np.array_equal(ev, ev_b[:, r]), r
-        np.testing.assert_allclose(dt, dt_b[:, r], rtol=1e-12)
+        np.testing.assert_allclose(dt, dt_b[:, r], rtol=rtol)
         if twice:
             ev2, dt2 = k.kmc_run(h, u[:, r, :])
             assert np.array_equal(ev2, ev_b2[:, r]), r
@@ -61,7 +64,8 @@ def test_batch_equals_single_runs(precision):
                                lattice_edge=E, kT=0.1) for (E, N, L, s, q) in _replicas()]
     info = _same_as_single_runs(make, 17, 77, twice=True)
     assert info["fused"]  # one set of launches for all members
-    assert info["launches_per_step"] == 4 + 6  # levels 1..4, propose, rates, select, record, 2 accept
+    # level-1 copy, downward levels 2..4, propose, rates, select, record and move, fused accept, reduction
+    assert info["launches_per_step"] == 4 + 6
 
 
 def test_batch_14_hops_with_near_cache_equals_single_runs():
@@ -116,7 +120,7 @@ def test_batch_with_mixed_modes_uses_member_kernels():
         return [k.kmc_fmm_init(workloads.site_positions(E, s), q, float(E), L, 8, precision="mixed",
                                lattice_edge=E, kT=0.1, near_cache=(r % 2 == 0))
                 for r, (E, N, L, s, q) in enumerate(_replicas())]
-    info = _same_as_single_runs(make, 23, 78)
+    info = _same_as_single_runs(make, 23, 78, rtol=1e-12)  # the members' own kernels: bit-identical
     assert not info["fused"]
 
 

@@ -72,3 +72,4 @@ def test_checked_build_runs_every_mode_clean():
         assert a[:4] == b[:4] and a[6] == b[6], (a[:4], a[6], b[6])  # same case, same events
         for x, y in ((a[4], b[4]), (a[5], b[5])):
             assert abs(x - y) <= 1e-9 * max(abs(y), 1.0), (a[:4], x, y)
+

@@ -518,3 +518,4 @@ def test_checkpoint_resume_continues_the_trajectory(small, tmp_path, near_cache)
     assert np.array_equal(np.concatenate([ev_a, ev_b]), ev_all)
     assert np.array_equal(k.kmc_fmm_positions(h3), k.kmc_fmm_positions(h1))
     assert abs(k.kmc_fmm_energy(h3) - k.kmc_fmm_energy(h1)) < 1e-5 * abs(k.kmc_fmm_energy(h1))
+
