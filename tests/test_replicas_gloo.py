@@ -54,5 +54,6 @@ def test_single_process_aggregation_is_identity():
     import bench
 
     assert bench.aggregate(5.0, 2.0) == (5.0, 2.0)
-    assert bench.launches_per_step(6) == 13  # 6 downward, propose, finalize, select, record, move, 2 accept
+    # downward levels 2-4 in one launch plus levels 5 and 6, propose, finalize, select, record, move, 2 accept
+    assert bench.launches_per_step(6) == 10
     assert np.isclose(bench.step_bytes(256, 6, 1 << 20, 12), 6 * (1 << 20) * 12 + 32768 * 512 * 16 + 32768 * 91 * 8)
