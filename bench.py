@@ -293,6 +293,11 @@ def cpu_sample(E, sites, q, seconds_target=10.0, max_props=20000, nhop=6, bc="pe
     tabulated Ewald pair potential; free space: the direct Coulomb sum) on a
     seeded sample of unmasked hops."""
     import oracle
+    if bc == "dirichlet":  # the oracle's grounded walls: the periodic mirrored cell (charges and mirrors)
+        ext = np.concatenate([sites, oracle.mirror_sites(E, np.asarray(sites, dtype=np.int64))])
+        r = cpu_sample(E, ext, np.concatenate([q, -np.asarray(q)]), seconds_target, max_props, nhop, "periodic")
+        r["sample"] += " of the mirrored cell (the charges and their mirrors)"
+        return r
     G = oracle.psi_table(E) if bc == "periodic" else None
     pos = workloads.site_positions(E, sites)
 
@@ -759,6 +764,26 @@ def run_batch(args):
         torch.distributed.destroy_process_group()
     if rank != 0:
         return 0
+    cpu = None
+    if not args.no_cpu:
+        # the oracle's O-table form: one full KMC step of every replica (one batch step), host cores
+        import oracle
+        ch, ct, ns = 0, 0.0, 0
+        for r in reps:
+            st = oracle.LatticeState(r["E"], r["sites"], r["q"])
+            t0 = time.perf_counter()
+            dU, mask = st.propose()
+            j, Q, dt = oracle.select(oracle.rates(dU, mask, kT), 0.5, 0.5)
+            if j >= 0:
+                st.accept(j // 6, j % 6)
+            ct += time.perf_counter() - t0
+            ch += int(mask.sum())
+            ns += 1
+        cpu = {"value": ch / ct, "unit": UNIT, "kmc_steps_per_s": 1.0 / ct, "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": f"one full KMC step of each of the {ns} replicas (one batch step) in the "
+                                           "O-table form (lattice-table Ewald potential, O(1) dU per hop, sequential "
+                                           "FP64 selection, O(E^3) site update per accept); kmc_steps_per_s = batch "
+                                           "steps per second"}
     value = units / (tot * 1e-3)
     line = {
         "metric": "dU evals/sec and KMC steps/sec, 64 batched replicas", "value": value,
@@ -779,6 +804,7 @@ def run_batch(args):
                 "h2d_bytes_per_step": 16 * R, "d2h_bytes_per_step": 16 * R,
                 "path": "kmc_batch_run from host uniforms to host events and time increments"},
         "clocks": clocks,
+        "cpu_baseline": cpu,
         "gpu_launches": info["launches_per_step"] * args.steps,
         "batched_kernels": info["fused"],
     }

@@ -301,7 +301,12 @@ int kmc_select_static(const double* rates, int64_t n, double zeta, double xi, in
  *   Otherwise each member's own step is a parallel branch of one graph.
  *   kmc_batch_run: uniforms (HOST) steps x count x 2 values (zeta, xi) laid
  *   out [step][member][2]; events (int64) and dts (HOST, steps x count,
- *   [step][member], may be NULL).  Same results as kmc_run on each member.
+ *   [step][member], may be NULL).  The same events as kmc_run on each
+ *   member (unless a uniform falls within rounding of a cumulative-rate
+ *   boundary); with batched kernels the time increments agree to rounding
+ *   (the batch translates the downward pass level by level, a single system
+ *   sums the coarse levels' translations in one launch: the same expansions
+ *   in another order).
  *   kmc_batch_run_timed: the same, and device_ms (host) receives the device
  *   time of the steps (CUDA events on the batch's stream around the step
  *   launches; staging of the uniforms and reading of the events excluded).

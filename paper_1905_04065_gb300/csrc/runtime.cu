@@ -1301,14 +1301,18 @@ int kmc_batch_set_chunk(kmc_batch_handle b, int chunk) {
   if (b->s0) cudaStreamSynchronize(b->s0);
   const int old = b->chunk_req;
   b->chunk_req = chunk;
+  // the plan's offsets are reallocated: a captured graph refers to the old ones
+  if (b->fgraph) cudaGraphExecDestroy(b->fgraph);
+  b->fgraph = nullptr;
   int rc = batch_plan(b);
   if (rc) {
     b->chunk_req = old;
-    batch_plan(b);
+    char keep[sizeof(b->msg)];
+    memcpy(keep, b->msg, sizeof(keep));
+    if (batch_plan(b)) b->fused = false;  // cannot restore the plan: fall back to the members' own kernels
+    memcpy(b->msg, keep, sizeof(keep));
     return rc;
   }
-  if (b->fgraph) cudaGraphExecDestroy(b->fgraph);
-  b->fgraph = nullptr;
   return KMC_OK;
 }
 
