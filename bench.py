@@ -146,9 +146,9 @@ def pair_count(E: int, L: int, sites: np.ndarray, nhop: int = 6, bc: str = "peri
 
 # DRAM bytes (read + write) of one summing propose launch per leaf, from the ncu capture of the
 # 128^3 tile case (4096 leaves of 8^3 sites, 32 charges each, 6 hops, mixed precision:
-# 9.10 MB read, 256 B written).  Valid for workloads with the same
+# 10.10 MB read, 32 kB written).  Valid for workloads with the same
 # leaf shape (tile, large); scaled by the number of leaves.
-PROPOSE_DRAM_BYTES_PER_LEAF = (9.097216e6 + 256) / 4096
+PROPOSE_DRAM_BYTES_PER_LEAF = (10.0992e6 + 32e3) / 4096
 TRAFFIC_WORKLOADS = ("tile", "large")
 
 
@@ -188,7 +188,7 @@ def phase_rooflines(work: dict, phases: dict, E: int, L: int, N: int, p: int, nh
     fl = 8 * l2l_cmacs(p) * cells
     by = cells * P * 2 * ts * 2 + parents * P * 2 * ts  # own + write, parent once
     t = phases["downward"] * 1e-3
-    out["downward"] = {"kernels": "k_downward_root, k_downward_cell (levels < 512 parents), k_downward_par",
+    out["downward"] = {"kernels": "k_downward_coarse (levels 2-4 in one launch), k_downward_par (deeper levels)",
                        "bound": "alu", "unit": "TFLOP/s", "achieved": fl / t / 1e12,
                        "peak": (fp32 if mixed else fp64) / 1e12, "frac": fl / t / (fp32 if mixed else fp64),
                        "work": f"{fl:.3e} {'FP32' if mixed else 'FP64'} flops ({l2l_cmacs(p)} complex MACs per cell, "
