@@ -140,7 +140,6 @@ struct Dev {
   int32_t* uid;       // [ML*cap]
   double4_32a* spos64;    // [ML*cap] (x,y,z,q)
   float4* spos32;     // [ML*cap]
-  float* sgrp;        // lattice mode: per leaf, groups of four slots (see sgrp_put); nullptr off-lattice
   // expansions (all levels, cell-major, ncoef(p) per cell)
   double2* Mt;        // multipoles
   double2* Psi;       // per-level interaction-list local expansions; level 1 holds H
@@ -235,30 +234,6 @@ __device__ __forceinline__ bool kmc_in(bool ok, int* err) {
 #define KMC_IN(cond, err) true
 #endif
 
-// Lattice mode keeps, beside the slot arrays, the charges of every leaf in
-// the layout the near-field kernel consumes: groups of four slots, 80 bytes
-// each, {x0 x1 y0 y1} {z0 z1 w0 w1} {x2 x3 y2 y3} {z2 z3 w2 w3} {q0 q1 q2 q3},
-// with (x, y, z) the site coordinates relative to the leaf corner (integers in
-// [0, W)), w = x^2 + y^2 + z^2 and q the charge.  Leaf c owns groups
-// [c * sgrp_groups(cap), ...); a slot without a charge holds a chargeless
-// entry far outside the leaf, so a leaf's first ceil(cnt / 4) groups can be
-// copied as one block.
-__host__ __device__ __forceinline__ int64_t sgrp_groups(int cap) { return (cap + 3) / 4; }
-__device__ __forceinline__ void sgrp_put(float* sg, int cap, int64_t slot, float x, float y, float z, float q) {
-  const int64_t leaf = slot / cap;
-  const int j = (int)(slot - leaf * cap);
-  float* G = sg + 20 * (leaf * sgrp_groups(cap) + (j >> 2));
-  const int r = j & 3, o = r & 1;
-  float* A = G + 8 * (r >> 1);
-  A[o] = x;
-  A[2 + o] = y;
-  A[4 + o] = z;
-  A[6 + o] = x * x + y * y + z * z;
-  G[16 + r] = q;
-}
-__device__ __forceinline__ void sgrp_pad(float* sg, int cap, int64_t slot) {
-  sgrp_put(sg, cap, slot, 1024.f, 1024.f, 1024.f, 0.f);
-}
 
 // 1/((n-m)(n+m)) for n > m, table built on the host into constant memory by each TU
 #define KMC_NTRI (((2 * KMC_MAXP + 1) * (2 * KMC_MAXP + 2)) / 2)

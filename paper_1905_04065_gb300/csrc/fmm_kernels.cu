@@ -148,21 +148,12 @@ __global__ void k_bin_fill(const Geo g, const Dev d) {
   if (s >= g.ML * g.cap) return;
   int64_t leaf = s / g.cap;
   int j = (int)(s - leaf * g.cap);
-  if (j >= d.cnt[leaf]) {
-    if (d.sgrp) sgrp_pad(d.sgrp, g.cap, s);
-    return;
-  }
+  if (j >= d.cnt[leaf]) return;
   int32_t i = d.uid[s];
   d.slot_of[i] = (int32_t)s;
   double x = d.pos[3 * i], y = d.pos[3 * i + 1], z = d.pos[3 * i + 2], q = d.q[i];
   d.spos64[s] = make_double4_32a(x, y, z, q);
   d.spos32[s] = make_float4((float)x, (float)y, (float)z, (float)q);
-  if (d.sgrp) {
-    const int st = d.site[i], E = g.E, W = g.W;
-    const int lx = (int)(leaf % g.nL), ly = (int)((leaf / g.nL) % g.nL), lz = (int)(leaf / ((int64_t)g.nL * g.nL));
-    sgrp_put(d.sgrp, g.cap, s, (float)(st % E - lx * W), (float)((st / E) % E - ly * W), (float)(st / (E * E) - lz * W),
-             (float)q);
-  }
 }
 
 void fmm_bin(const Geo& g, const Dev& d, cudaStream_t s) {

@@ -20,6 +20,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include <cuda_fp16.h>
 
 __constant__ float c_inv_f[KMC_NTRI];
 __constant__ double c_inv_d[KMC_NTRI];
@@ -141,18 +142,13 @@ __device__ __forceinline__ T l2p_eval(const C* L, int p, T x, T y, T z) {
 
 
 // ------------------------------------------------------------------ near-field helpers
-// FP32 (lattice proposals): coordinates in lattice units relative to the
-// target leaf's corner, so that for source s and target t every term of
-// |s - t|^2 = w_s + w_t - 2 s.t (w = |.|^2) is an integer far below 2^24 and
-// the squared distance is exact; that form takes four FP32 operations per pair
-// instead of six.  Sources come in groups of four ({x0 x1 y0 y1} {z0 z1 w0 w1}
-// {x2 x3 y2 y3} {z2 z3 w2 w3} {q0 q1 q2 q3}: the per-leaf layout kept in
-// device memory, copied as blocks and shifted once into the target leaf's
-// frame) so that one packed FP32x2 instruction (FADD2 / FFMA2) serves two pair
-// interactions; 1/r from the MUFU rsqrt.approx (relative error < 2^-22),
-// scaled by 1/h once per target.  Each thread evaluates two targets against
-// every source it loads.  FP64: integer lattice coordinates too, 1/r from a
-// table of 1/sqrt(n) (below), one source per iteration.
+// Lattice proposals take coordinates in lattice units relative to the target
+// leaf's corner, so that for source s and target t every term of
+// |s - t|^2 = |s|^2 + |t|^2 - 2 s.t is a small integer and the squared
+// distance is exact.  FP32: the squared distances from f16 tensor-core
+// products (nfmma below), 1/r from the MUFU rsqrt.approx (relative error
+// < 2^-22), scaled by 1/h once per target.  FP64: 1/r from a table of
+// 1/sqrt(n) (below), one source per iteration.
 __device__ __forceinline__ float rsqrt_mufu(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -161,75 +157,131 @@ __device__ __forceinline__ float rsqrt_mufu(float x) {
 
 template <typename T> struct NearField;
 
-template <> struct NearField<float> {
-  float2 c0, e0, c1, e1;  // target 0 and target 1, two accumulation chains each
-  __device__ __forceinline__ void reset() { c0 = e0 = c1 = e1 = make_float2(0.f, 0.f); }
-  // shared-memory bytes for `chunk` sources in groups of four (80 bytes each)
-  static __host__ __device__ __forceinline__ size_t bytes(int chunk) { return (size_t)((chunk + 3) / 4 + 1) * 80; }
-  struct Tgt {
-    float2 tx2, ty2, tz2, wt;  // -2 t and |t|^2, duplicated for the packed lanes
-  };
-  static __device__ __forceinline__ Tgt target(float tx, float ty, float tz) {
-    Tgt t;
-    t.tx2 = make_float2(-2.f * tx, -2.f * tx);
-    t.ty2 = make_float2(-2.f * ty, -2.f * ty);
-    t.tz2 = make_float2(-2.f * tz, -2.f * tz);
-    const float w = tx * tx + ty * ty + tz * tz;
-    t.wt = make_float2(w, w);
-    return t;
-  }
-  template <bool GUARD>
-  static __device__ __forceinline__ void pair2(const float4& A, const float4& B, float2 q, const Tgt& t, float2& acc) {
-    float2 r2 = __fadd2_rn(make_float2(B.z, B.w), t.wt);
-    r2 = __ffma2_rn(make_float2(A.x, A.y), t.tx2, r2);
-    r2 = __ffma2_rn(make_float2(A.z, A.w), t.ty2, r2);
-    r2 = __ffma2_rn(make_float2(B.x, B.y), t.tz2, r2);
-    float2 iv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-    if (GUARD) {
-      iv.x = r2.x > 0.f ? iv.x : 0.f;
-      iv.y = r2.y > 0.f ? iv.y : 0.f;
+// small integer (|i| < 2^22) to float on the FMA pipe: the float with bits
+// 0x4B400000 + i is 1.5 2^23 + i
+__device__ __forceinline__ float i2f(int i) { return __int_as_float(0x4B400000 + i) - 12582912.f; }
+
+// FP32 form: the pair sums on the tensor cores and the MUFU.  On the lattice
+// the squared distance between a site t and a source s (lattice units, the
+// target leaf's frame) is the integer n = t.t + s.s - 2 t.s, and for leaf
+// edges W <= 12 every coordinate and every term of that sum is an integer
+// of at most 11 bits (|s| < 2W per axis, n <= 3 (2W - 1)^2 < 2^11), exact in
+// f16.  One m16n8k8 f16 MMA with FP32 accumulation therefore gives n exactly
+// for 16 sites x 8 sources, from site features (tx, ty, tz, 1, t.t, 0, 0, 0)
+// and source features (-2sx, -2sy, -2sz, s.s, 1, 0, 0, 0): the distance
+// arithmetic leaves the FP32 pipes, which carry only the accumulation
+// q / sqrt(n); 1 / sqrt(n) comes from the MUFU.
+// Fragments (PTX m16n8k8, lane = 4 g + c): A rows g and g + 8, columns 2c and
+// 2c + 1; B column (source) g, rows 2c and 2c + 1; D rows g and g + 8, columns
+// 2c and 2c + 1.  Staged source (16 bytes, written over the copied slot
+// position): word 0 = f16x2 (-2sx, -2sy), word 1 = f16x2 (-2sz, s.s), word 2 =
+// q (FP32), word 3 unused; feature rows 4..7 (1, 0, 0, 0) are constants of the
+// lanes with c = 2, 3.
+namespace nfmma {
+constexpr int TMAX = 2;  // site tiles of 16 per round (32 sites; four tiles measured 3% slower)
+// shared-memory bytes of a pass of `chunk` sources, padded to a whole tile of eight
+__host__ __device__ __forceinline__ size_t bytes(int chunk) { return 16 * ((size_t)chunk + 8); }
+__device__ __forceinline__ uint32_t h2bits(float lo, float hi) {
+  const __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+// the staged record of a source at (sx, sy, sz) (frame lattice units) with charge q
+__device__ __forceinline__ float4 record(int sx, int sy, int sz, float q) {
+  const float x = i2f(sx), y = i2f(sy), z = i2f(sz);
+  return make_float4(__uint_as_float(h2bits(-2.f * x, -2.f * y)),
+                     __uint_as_float(h2bits(-2.f * z, fmaf(x, x, fmaf(y, y, z * z)))), q, 0.f);
+}
+// padding record: no charge, n = t.t + 1024 > 0
+__device__ __forceinline__ float4 pad_record() {
+  return make_float4(0.f, __uint_as_float(h2bits(0.f, 1024.f)), 0.f, 0.f);
+}
+// A fragment word of a site (x, y, z) for this lane's columns 2c, 2c + 1
+__device__ __forceinline__ uint32_t site_word(int c, int x, int y, int z) {
+  const float fx = i2f(x), fy = i2f(y), fz = i2f(z);
+  const float tt = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+  const float lo = c == 0 ? fx : (c == 1 ? fz : (c == 2 ? tt : 0.f));
+  const float hi = c == 0 ? fy : (c == 1 ? 1.f : 0.f);
+  return h2bits(lo, hi);
+}
+__device__ __forceinline__ void mma(uint32_t a0, uint32_t a1, uint32_t b, float& d0, float& d1, float& d2,
+                                    float& d3) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5}, {%6}, {%7, %7, %7, %7};"
+      : "=f"(d0), "=f"(d1), "=f"(d2), "=f"(d3)
+      : "r"(a0), "r"(a1), "r"(b), "f"(0.f));
+}
+// source tiles [j0, j1) (8 staged records each, R = first record) against
+// the NT site tiles of a[]; GUARD: the tiles hold the sites' own charges
+// (the pair at n = 0 adds nothing)
+template <int NT, bool GUARD>
+__device__ __forceinline__ void run(const uint32_t* R, int j0, int j1, const uint32_t (&a)[TMAX][2],
+                                    float2 (&acc)[TMAX][2], int g, int c, uint32_t bc) {
+#pragma unroll 1
+  for (int j = j0; j < j1; j++) {
+    const uint32_t* T = R + 32 * j;
+    const uint32_t bw = T[4 * g + c];
+    const uint32_t b = c < 2 ? bw : bc;
+    const float2 qv = make_float2(__uint_as_float(T[8 * c + 2]), __uint_as_float(T[8 * c + 6]));
+    // all products, then all rsqrts, then the accumulation: no rsqrt waits
+    // behind an accumulation that waits for an earlier rsqrt
+    float dd[TMAX][4];
+#pragma unroll
+    for (int s = 0; s < NT; s++) mma(a[s][0], a[s][1], b, dd[s][0], dd[s][1], dd[s][2], dd[s][3]);
+    float2 uu[TMAX][2];
+#pragma unroll
+    for (int s = 0; s < NT; s++) {
+      uu[s][0] = make_float2(rsqrt_mufu(dd[s][0]), rsqrt_mufu(dd[s][1]));
+      uu[s][1] = make_float2(rsqrt_mufu(dd[s][2]), rsqrt_mufu(dd[s][3]));
     }
-    acc = __ffma2_rn(q, iv, acc);
-  }
-  template <bool GUARD, bool TWO>
-  __device__ __forceinline__ void run_range(const float4* G, int ng, const Tgt& t0, const Tgt& t1) {
-    float2 a = c0, b = e0, c = c1, d = e1;
-#pragma unroll 2
-    for (int g = 0; g < ng; g++, G += 5) {
-      const float4 A0 = G[0], B0 = G[1], A1 = G[2], B1 = G[3], Q = G[4];
-      const float2 q01 = make_float2(Q.x, Q.y), q23 = make_float2(Q.z, Q.w);
-      pair2<GUARD>(A0, B0, q01, t0, a);
-      pair2<GUARD>(A1, B1, q23, t0, b);
-      if (TWO) {
-        pair2<GUARD>(A0, B0, q01, t1, c);
-        pair2<GUARD>(A1, B1, q23, t1, d);
+#pragma unroll
+    for (int s = 0; s < NT; s++) {
+      if (GUARD) {
+        uu[s][0].x = dd[s][0] > 0.f ? uu[s][0].x : 0.f;
+        uu[s][0].y = dd[s][1] > 0.f ? uu[s][0].y : 0.f;
+        uu[s][1].x = dd[s][2] > 0.f ? uu[s][1].x : 0.f;
+        uu[s][1].y = dd[s][3] > 0.f ? uu[s][1].y : 0.f;
       }
-    }
-    c0 = a;
-    e0 = b;
-    c1 = c;
-    e1 = d;
-  }
-  // groups [g0, g1) in the targets' frame; groups below ngg are the targets'
-  // own leaf (skip the pair at distance 0).  Target 1 is evaluated only when
-  // two is set (warp-uniform).
-  __device__ __forceinline__ void run_span(const float4* G, int g0, int g1, int ngg, bool two, float tx0, float ty0,
-                                           float tz0, float tx1, float ty1, float tz1) {
-    const Tgt t0 = target(tx0, ty0, tz0), t1 = target(tx1, ty1, tz1);
-    const int gm = min(max(ngg, g0), g1);
-    if (two) {
-      if (gm > g0) run_range<true, true>(G + 5 * g0, gm - g0, t0, t1);
-      if (g1 > gm) run_range<false, true>(G + 5 * gm, g1 - gm, t0, t1);
-    } else {
-      if (gm > g0) run_range<true, false>(G + 5 * g0, gm - g0, t0, t1);
-      if (g1 > gm) run_range<false, false>(G + 5 * gm, g1 - gm, t0, t1);
+      acc[s][0] = __ffma2_rn(uu[s][0], qv, acc[s][0]);
+      acc[s][1] = __ffma2_rn(uu[s][1], qv, acc[s][1]);
     }
   }
-  __device__ __forceinline__ float sum(int side) const {
-    const float2 s = side ? __fadd2_rn(c1, e1) : __fadd2_rn(c0, e0);
-    return s.x + s.y;
+}
+// one round: site tiles [t0, t0 + NT) of the compacted site list against this
+// warp's source tiles [j0, j1) (the first jg of them guarded); the row sums
+// go to the fixed-point accumulators accs (scaled by `scale`)
+template <int NT>
+__device__ __forceinline__ void round(const uint32_t* R, const uint16_t* sites, int nsites, int W, int t0, int j0,
+                                      int jg, int j1, int* accs, float scale, int lane, int* err) {
+  const int g = lane >> 2, c = lane & 3;
+  uint32_t a[TMAX][2];
+  float2 acc[TMAX][2];
+#pragma unroll
+  for (int s = 0; s < NT; s++)
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int i = 16 * (t0 + s) + g + 8 * h;
+      const int sv = i < nsites ? sites[i] : 0;
+      a[s][h] = site_word(c, sv & 15, (sv >> 4) & 15, sv >> 8);
+      acc[s][h] = make_float2(0.f, 0.f);
+    }
+  const uint32_t bc = c == 2 ? 0x3C00u : 0u;  // f16x2 (1, 0) for rows 4, 5; 0 for rows 6, 7
+  if (jg > j0) run<NT, true>(R, j0, jg, a, acc, g, c, bc);
+  if (j1 > jg) run<NT, false>(R, jg, j1, a, acc, g, c, bc);
+#pragma unroll
+  for (int s = 0; s < NT; s++) {
+    float v0 = acc[s][0].x + acc[s][0].y, v1 = acc[s][1].x + acc[s][1].y;
+    v0 += __shfl_xor_sync(0xffffffffu, v0, 1);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
+    v0 += __shfl_xor_sync(0xffffffffu, v0, 2);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, 2);
+    const int i = 16 * (t0 + s) + g + 8 * c;  // lane c = 0: row g, c = 1: row g + 8
+    if (c < 2 && i < nsites) {
+      const int sv = sites[i];
+      const int l = (sv & 15) + W * (((sv >> 4) & 15) + W * (sv >> 8));
+      if (KMC_IN(l >= 0 && l < W * W * W, err)) atomicAdd(&accs[l], __float2int_rn((c ? v1 : v0) * scale));
+    }
   }
-};
+}
+}  // namespace nfmma
 
 // FP64 form.  On the lattice every squared distance is an exact integer n in
 // lattice units (|d| < 2W per axis, so n <= 3 (2W - 1)^2 < 2^24), so 1/|d|
@@ -396,9 +448,6 @@ __device__ __forceinline__ int lattice_coord(float x, float ih) {
 }
 __device__ __forceinline__ int lattice_coord(double x, double ih) { return (int)floor(x * ih); }
 
-// small integer (|i| < 2^22) to float on the FMA pipe: the float with bits
-// 0x4B400000 + i is 1.5 2^23 + i
-__device__ __forceinline__ float i2f(int i) { return __int_as_float(0x4B400000 + i) - 12582912.f; }
 template <typename T> __device__ __forceinline__ T small_to(int i);
 template <> __device__ __forceinline__ float small_to<float>(int i) { return i2f(i); }
 template <> __device__ __forceinline__ double small_to<double>(int i) { return (double)i; }
@@ -503,90 +552,121 @@ __device__ __forceinline__ void fixed_add(long long* a, double v) {
 // needed once even when several charges propose to hop there, and at an own
 // charge's site it is that charge's old-position potential (the pair at
 // distance 0 is skipped).  Phases: (0) the 27 neighbour leaves (slot base,
-// count) and the source passes; in the FP32 form the first pass's charge
-// groups are copied into shared memory by bulk asynchronous copies that run
-// while phases 1-3 proceed; (1) occupancy bits; (2) needed-site bits, masked
-// hops written; (3) compact site list; (4) near-field sums (sources split
-// between the warps, fixed-point reduction) + L2P; (5) write-out by
-// re-enumerating the same hops.  Site
-// coordinates come from the slot positions (coalesced), user indices only
-// where an output is written.  Potentials are written in precision T (FP32
-// arrays in the mixed form, FP64 arrays in the FP64 form).
+// count) and the source passes; in the FP32 form the first pass's slot
+// positions are copied into shared memory by bulk asynchronous copies that
+// run while phases 1-3 proceed; (1) occupancy bits; (2) needed-site bits,
+// masked hops written; (3) compact site list; (4) near-field sums (sources
+// split between the warps, fixed-point reduction) + L2P; (5) write-out by
+// re-enumerating the same hops.  Site coordinates come from the slot
+// positions (coalesced), user indices only where an output is written.
 // mode: PROP_SUM (the pair sums of this step), PROP_FILL (pair sums at every
 // site of the leaf into the near-field cache d.nearfx; no hops, no L2P, no
 // outputs) or PROP_CACHED (the near-field sums read from the cache, no pairs).
-enum { PROP_SUM = 0, PROP_FILL = 1, PROP_CACHED = 2 };
 // The cached form holds no source chunk in shared memory and runs twelve CTAs
 // per SM (more resident leaves hide its load and barrier latency; sixteen
 // spilled too much of the L2P).
-template <typename T, int NH, int mode>
-__device__ __forceinline__ void propose_leaf(const Geo g, const Dev d, const int chunk, const int blk0) {
+enum { PROP_SUM = 0, PROP_FILL = 1, PROP_CACHED = 2 };
+
+// shared-memory layout of one leaf (byte count: propose_smem)
+template <typename T> struct LeafSmem {
   typedef typename cplx<T>::type C;
-  typedef typename vec4<T>::type V4;
-  constexpr bool F32 = sizeof(T) == 4;
-  extern __shared__ __align__(128) unsigned char sm[];
-  const int W = g.W, W3 = W * W * W;
-  const int nbw = (W3 + 31) / 32;
-  const int rW = (65536 + W - 1) / W;
-  unsigned char* src = sm;
-  C* Lc = (C*)(sm + NearField<T>::bytes(chunk));  // 16-byte aligned
-  int64_t* nb_base = (int64_t*)(Lc + g.P);          // [27] slot base: own leaf, then the 26 others
-  uint64_t* bar = (uint64_t*)(nb_base + 27);        // [1] copy barrier (FP32 form)
-  int* nb_off = (int*)(bar + 1);                    // [28] first source of each leaf (FP64) / first group (FP32)
-  int* nb_cnt = nb_off + 28;                        // [27] charges per leaf
-  int* nb_leaf = nb_cnt + 27;                       // [27] leaf index
-  int* pq = nb_leaf + 27;                           // [28] first leaf of each source pass; pq[npass] = 27
-  int* misc = pq + 28;                              // [4] number of passes (padded to 8 bytes)
-  T* phis = (T*)(misc + 4);                         // [W3] potential per local site
-  uint32_t* bits = (uint32_t*)(phis + W3);          // [nbw] occupied sites
-  uint32_t* need = bits + nbw;                      // [nbw] sites where a potential is needed
-  int* woff = (int*)(need + nbw);                   // [nbw + 1] prefix of needed sites per word
-  uint16_t* sites = (uint16_t*)(woff + nbw + 1);    // [W3] needed local sites (x | y << 4 | z << 8), compacted
-  // FP64 form: 1/sqrt(n) for the squared lattice distances n <= 3 (2W - 1)^2, 8-byte aligned
-  double* isq = (double*)(((uintptr_t)(sites + ((W3 + 1) & ~1)) + 7) & ~(uintptr_t)7);
-  const int nisq = 3 * (2 * W - 1) * (2 * W - 1) + 1;
-  T* out_old = (T*)(F32 ? (void*)d.phi_old32 : (void*)d.phi_old);
-  T* out_new = (T*)(F32 ? (void*)d.phi_new32 : (void*)d.phi_new);
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  const int nL = g.nL, E = g.E;
-  const int64_t leaf = (int64_t)blockIdx.x - blk0;  // the member's leaf (blk0: its first block)
-  const int lsh = g.L - 1;  // nL = 2^(L-1)
-  const int lx = (int)(leaf & (nL - 1)), ly = (int)((leaf >> lsh) & (nL - 1)), lz = (int)(leaf >> (2 * lsh));
-  const int gx0 = lx * W, gy0 = ly * W, gz0 = lz * W;
-  const T h = (T)g.h, ih = (T)(1.0 / g.h);
-  const V4* spos = (const V4*)(F32 ? (const void*)d.spos32 : (const void*)d.spos64);
-  const int64_t gpl = sgrp_groups(g.cap);  // groups per leaf in the FP32 source layout
-  // capacity of one pass: sources (FP64) or groups of four (FP32)
-  const int pass_cap = F32 ? chunk / 4 : chunk;
-
-  const C* Pe = (const C*)d.Peff + (g.cell_off[g.L] + leaf) * g.P;
-  for (int c = tid; c < g.P; c += blockDim.x) Lc[c] = Pe[c];
-  if (!F32 && mode != PROP_CACHED)
-    for (int c = tid; c < nisq; c += blockDim.x) isq[c] = d.isq[c];
-  for (int c = tid; c < nbw; c += blockDim.x) {
-    bits[c] = 0u;
-    need[c] = 0u;
+  unsigned char* src;  // sources of the current pass (FP32: staged records; FP64: NearField<double>::Src)
+  C* Lc;               // [P] the leaf's local expansion, 16-byte aligned
+  int64_t* nb_base;    // [27] slot base: own leaf, then the 26 others
+  uint64_t* bar;       // [1] copy barrier (FP32 form)
+  int* nb_off;         // [28] first source of each leaf in the pass layout
+  int* nb_cnt;         // [27] charges per leaf
+  int* nb_leaf;        // [27] leaf index
+  int* pq;             // [28] first leaf of each source pass; pq[npass] = 27
+  int* misc;           // [4] number of passes, fixed-point exponent, number of sites (padded to 8 bytes)
+  T* phis;             // [W3] potential per local site (fixed-point near-field sums before the L2P)
+  uint32_t* bits;      // [nbw] occupied sites
+  uint32_t* need;      // [nbw] sites where a potential is needed
+  int* woff;           // [nbw + 1] prefix of needed sites per word
+  uint16_t* sites;     // [W3] needed local sites (x | y << 4 | z << 8), compacted
+  double* isq;         // FP64 form: 1/sqrt(n) for the squared lattice distances n <= 3 (2W - 1)^2
+  __device__ __forceinline__ LeafSmem(unsigned char* sm, const Geo& g, int chunk) {
+    constexpr bool F32 = sizeof(T) == 4;
+    const int W3 = g.W * g.W * g.W, nbw = (W3 + 31) / 32;
+    src = sm;
+    Lc = (C*)(sm + (F32 ? nfmma::bytes(chunk) : NearField<double>::bytes(chunk)));
+    nb_base = (int64_t*)(Lc + g.P);
+    bar = (uint64_t*)(nb_base + 27);
+    nb_off = (int*)(bar + 1);
+    nb_cnt = nb_off + 28;
+    nb_leaf = nb_cnt + 27;
+    pq = nb_leaf + 27;
+    misc = pq + 28;
+    phis = (T*)(misc + 4);
+    bits = (uint32_t*)(phis + W3);
+    need = bits + nbw;
+    woff = (int*)(need + nbw);
+    sites = (uint16_t*)(woff + nbw + 1);
+    isq = (double*)(((uintptr_t)(sites + ((W3 + 1) & ~1)) + 7) & ~(uintptr_t)7);
   }
-  // (0) list entry 0 is this leaf, entries 1..26 the other neighbours in
+};
+
+// the leaf of a CTA and the thread's indices
+struct LeafCtx {
+  int64_t leaf;
+  int lx, ly, lz, gx0, gy0, gz0;
+  int tid, lane, warp;  // thread (0..127), lane, warp (0..3)
+};
+__device__ __forceinline__ LeafCtx leaf_ctx(const Geo& g, int64_t leaf, int tid) {
+  LeafCtx x;
+  const int nL = g.nL, lsh = g.L - 1;  // nL = 2^(L-1)
+  x.leaf = leaf;
+  x.lx = (int)(leaf & (nL - 1));
+  x.ly = (int)((leaf >> lsh) & (nL - 1));
+  x.lz = (int)(leaf >> (2 * lsh));
+  x.gx0 = x.lx * g.W;
+  x.gy0 = x.ly * g.W;
+  x.gz0 = x.lz * g.W;
+  x.tid = tid;
+  x.lane = tid & 31;
+  x.warp = tid >> 5;
+  return x;
+}
+
+// Setup of a leaf: its local expansion, cleared site bitmaps and (warp 0) the
+// 27 neighbour leaves (slot base, count), the split of their sources into
+// passes of at most `chunk` (whole leaves), the fixed-point exponent and, in
+// the FP32 form, the bulk copies of the first pass's slot positions, which
+// land while the site phases run.
+template <typename T, int mode>
+__device__ __forceinline__ void leaf_setup(const Geo& g, const Dev& d, const LeafSmem<T>& S, const LeafCtx& x, int chunk) {
+  typedef typename cplx<T>::type C;
+  constexpr bool F32 = sizeof(T) == 4;
+  const int W3 = g.W * g.W * g.W, nbw = (W3 + 31) / 32, nL = g.nL;
+  const int nisq = 3 * (2 * g.W - 1) * (2 * g.W - 1) + 1;
+  const int tid = x.tid, lane = x.lane;
+  const C* Pe = (const C*)d.Peff + (g.cell_off[g.L] + x.leaf) * g.P;
+  for (int c = tid; c < g.P; c += 128) S.Lc[c] = Pe[c];
+  if (!F32 && mode != PROP_CACHED)
+    for (int c = tid; c < nisq; c += 128) S.isq[c] = d.isq[c];
+  for (int c = tid; c < nbw; c += 128) {
+    S.bits[c] = 0u;
+    S.need[c] = 0u;
+  }
+  // list entry 0 is this leaf, entries 1..26 the other neighbours in
   // 27-neighbourhood order (x fastest), centre skipped
-  if (F32 && tid == 0) mbar_init(bar, 1);
-  if (warp == 0) {
+  if (F32 && tid == 0) mbar_init(S.bar, 1);
+  if (x.warp == 0) {
     int u = 0;
     if (lane < 27) {
       const int qq = lane == 0 ? 13 : (lane <= 13 ? lane - 1 : lane);
-      const int ux = lx + qq % 3 - 1, uy = ly + (qq / 3) % 3 - 1, uz = lz + qq / 9 - 1;
+      const int ux = x.lx + qq % 3 - 1, uy = x.ly + (qq / 3) % 3 - 1, uz = x.lz + qq / 9 - 1;
       const int sx = wrap1(ux, nL), sy = wrap1(uy, nL), sz = wrap1(uz, nL);
       const int nleaf = sx + nL * (sy + nL * sz);
-      nb_leaf[lane] = nleaf;
-      nb_base[lane] = (int64_t)nleaf * g.cap;
+      S.nb_leaf[lane] = nleaf;
+      S.nb_base[lane] = (int64_t)nleaf * g.cap;
       // free space: a neighbour beyond the box does not exist (no images)
       const bool exists = !g.bc || (ux >= 0 && ux < nL && uy >= 0 && uy < nL && uz >= 0 && uz < nL);
       const int c = exists ? d.cnt[nleaf] : 0;
-      nb_cnt[lane] = c;
-      u = F32 ? (c + 3) >> 2 : c;
+      S.nb_cnt[lane] = c;
+      u = c;
     }
-    // offsets of the leaves (sources or groups): warp scan
+    // offsets of the leaves' sources: warp scan
     int incl = u;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -594,72 +674,82 @@ __device__ __forceinline__ void propose_leaf(const Geo g, const Dev d, const int
       if (lane >= o) incl += t2;
     }
     const int total = __shfl_sync(0xffffffffu, incl, 26);
-    if (lane < 27) nb_off[lane] = incl - u;
-    if (lane == 0) nb_off[27] = total;
+    if (lane < 27) S.nb_off[lane] = incl - u;
+    if (lane == 0) S.nb_off[27] = total;
     __syncwarp();
     if (lane == 0) {
       // the split into passes at leaf boundaries (one pass unless the
-      // neighbourhood is dense); one leaf always fits (pass_cap >= capacity)
+      // neighbourhood is dense); one leaf always fits (chunk >= capacity)
       int np = 0;
-      pq[0] = 0;
-      if (mode != PROP_CACHED && total > pass_cap) {
+      S.pq[0] = 0;
+      if (mode != PROP_CACHED && total > chunk) {
         int start = 0;
         for (int q = 0; q < 27; q++) {
-          const int uq = F32 ? (nb_cnt[q] + 3) >> 2 : nb_cnt[q];
-          if (nb_off[q] + uq - start > pass_cap) {
-            pq[++np] = q;
-            start = nb_off[q];
+          if (S.nb_off[q] + S.nb_cnt[q] - start > chunk) {
+            S.pq[++np] = q;
+            start = S.nb_off[q];
           }
         }
       }
-      pq[++np] = 27;
-      misc[0] = np;
+      S.pq[++np] = 27;
+      S.misc[0] = np;
       {  // fixed-point exponent of the near-field sums: 2^ks * bound < 2^(bits - 2)
-        const double bound = g.qmax * (double)max(nb_off[27] * (F32 ? 4 : 1), 1);  // lattice units
-        misc[1] = (F32 ? 30 : 62) - (ilogb(bound) + 1);
+        const double bound = g.qmax * (double)max(total, 1);  // lattice units
+        S.misc[1] = (F32 ? 30 : 62) - (ilogb(bound) + 1);
       }
     }
     __syncwarp();
-    if (F32 && mode != PROP_CACHED) {  // first pass: one bulk copy per leaf (one lane each), overlapped with phases 1-3
-      const int q1 = pq[1];
-      if (lane == 0) mbar_expect_tx(bar, (uint32_t)(nb_off[q1] * 80));
+    if (F32 && mode != PROP_CACHED) {  // first pass: one bulk copy per leaf (one lane each)
+      const int q1 = S.pq[1];
+      if (lane == 0) mbar_expect_tx(S.bar, (uint32_t)(S.nb_off[q1] * 16));
       __syncwarp();
-      if (lane < q1) {
-        const int ng = (nb_cnt[lane] + 3) >> 2;
-        if (ng) bulk_copy_g2s(src + 80 * nb_off[lane], d.sgrp + 20 * (int64_t)nb_leaf[lane] * gpl, (uint32_t)(80 * ng), bar);
-      }
+      if (lane < q1 && S.nb_cnt[lane])
+        bulk_copy_g2s(S.src + 16 * S.nb_off[lane], d.spos32 + S.nb_base[lane], (uint32_t)(16 * S.nb_cnt[lane]), S.bar);
     }
   }
   __syncthreads();
+}
 
-  // (1) + (2): warp w handles the leaves f = w and w + 4 of {own leaf (f = 0),
-  // the neighbour across face f - 1 (f = 1..6)}; the first 32 charges of
-  // each are loaded at once, before the occupancy barrier
-  static_assert(PROP_THREADS == 128, "four warps: entries warp, warp + 4, ...");
+// The sites of a leaf: (1) occupancy bits; (2) needed-site bits, masked hops
+// written; (3) the compacted list of needed sites; their fixed-point sums
+// cleared.  Returns the number of sites (also in S.misc[2]).
+template <typename T, int NH, int mode>
+__device__ __forceinline__ int leaf_sites(const Geo& g, const Dev& d, const LeafSmem<T>& S, const LeafCtx& x) {
+  typedef typename vec4<T>::type V4;
+  constexpr bool F32 = sizeof(T) == 4;
+  const int W = g.W, W3 = W * W * W, nbw = (W3 + 31) / 32, E = g.E;
+  const int rW = (65536 + W - 1) / W;
+  const int tid = x.tid, lane = x.lane, warp = x.warp;
+  const T ih = (T)(1.0 / g.h);
+  const V4* spos = (const V4*)(F32 ? (const void*)d.spos32 : (const void*)d.spos64);
+  T* out_new = (T*)(F32 ? (void*)d.phi_new32 : (void*)d.phi_new);
+  // warp w handles the leaves f = w and w + 4 of {own leaf (f = 0), the
+  // neighbour across face f - 1 (f = 1..6)}; the first 32 charges of each
+  // are loaded at once, before the occupancy barrier
   constexpr int hs = NH == KMC_NHOP ? 0 : 1, ne = hs ? 27 : 1 + KMC_NHOP, nhop = NH;
-  const int cnt_own = nb_cnt[0];
-  const int64_t base_own = nb_base[0];
+  const int cnt_own = S.nb_cnt[0];
+  const int64_t base_own = S.nb_base[0];
   V4 pv[2];
 #pragma unroll
   for (int i = 0; i < 2; i++) {
     const int e = warp + 4 * i;
     if (e < ne) {
       const int li = c_ent_leaf[hs][e];
-      if (lane < nb_cnt[li]) pv[i] = spos[nb_base[li] + lane];
+      if (lane < S.nb_cnt[li]) pv[i] = spos[S.nb_base[li] + lane];
     }
   }
   // (1) occupancy bitmap of this leaf's sites (warp 0)
   if (warp == 0)
     for (int j = lane; j < cnt_own; j += 32) {
       const V4 v = j < 32 ? pv[0] : spos[base_own + j];
-      const int ls = (lattice_coord(v.x, ih) - gx0) + W * (lattice_coord(v.y, ih) - gy0 + W * (lattice_coord(v.z, ih) - gz0));
+      const int ls = (lattice_coord(v.x, ih) - x.gx0) +
+                     W * (lattice_coord(v.y, ih) - x.gy0 + W * (lattice_coord(v.z, ih) - x.gz0));
       if (KMC_IN(ls >= 0 && ls < W3, d.err)) {
-        atomicOr(&bits[ls >> 5], 1u << (ls & 31));
-        atomicOr(&need[ls >> 5], 1u << (ls & 31));
+        atomicOr(&S.bits[ls >> 5], 1u << (ls & 31));
+        atomicOr(&S.need[ls >> 5], 1u << (ls & 31));
       }
     }
   __syncthreads();
-
   // (2) hop targets inside this leaf: the leaf's own hops and the hops that
   // enter it from the neighbours of its entry list
   // not unrolled: with the 14-hop set (27 entries, seven per warp) unrolled
@@ -671,8 +761,8 @@ __device__ __forceinline__ void propose_leaf(const Geo g, const Dev d, const int
     if (e >= ne) break;
     const int li = c_ent_leaf[hs][e];
     const uint32_t hm = c_ent_hops[hs][e];
-    const int64_t mb = nb_base[li];
-    const int cm = nb_cnt[li];
+    const int64_t mb = S.nb_base[li];
+    const int cm = S.nb_cnt[li];
     for (int j = lane; j < cm; j += 32) {
       const V4 v = (j < 32 && i < 2) ? (i == 0 ? pv[0] : pv[1]) : spos[mb + j];
       const int gx = lattice_coord(v.x, ih), gy = lattice_coord(v.y, ih), gz = lattice_coord(v.z, ih);
@@ -690,24 +780,24 @@ __device__ __forceinline__ void propose_leaf(const Geo g, const Dev d, const int
           continue;
         }
         const int tx = wrap1(rx, E), ty = wrap1(ry, E), tz = wrap1(rz, E);
-        int ux = tx - gx0, uy = ty - gy0, uz = tz - gz0;
+        const int ux = tx - x.gx0, uy = ty - x.gy0, uz = tz - x.gz0;
         if (ux < 0 || ux >= W || uy < 0 || uy >= W || uz < 0 || uz >= W) continue;  // another leaf's CTA
-        int lt = ux + W * (uy + W * uz);
+        const int lt = ux + W * (uy + W * uz);
         if (!KMC_IN(lt >= 0 && lt < W3, d.err)) continue;
-        if (bits[lt >> 5] & (1u << (lt & 31))) {
+        if (S.bits[lt >> 5] & (1u << (lt & 31))) {
           const int32_t u = d.uid[mb + j];
           if (KMC_IN(u >= 0 && u < g.n, d.err)) {
             d.mask[(int64_t)nhop * u + k] = 0;
             out_new[(int64_t)nhop * u + k] = qnan<T>();
           }
         } else {
-          atomicOr(&need[lt >> 5], 1u << (lt & 31));
+          atomicOr(&S.need[lt >> 5], 1u << (lt & 31));
         }
       }
     }
   }
   if (mode == PROP_FILL)  // every site of the leaf
-    for (int c = tid; c < nbw; c += blockDim.x) need[c] = 32 * c + 32 <= W3 ? 0xffffffffu : (1u << (W3 - 32 * c)) - 1u;
+    for (int c = tid; c < nbw; c += 128) S.need[c] = 32 * c + 32 <= W3 ? 0xffffffffu : (1u << (W3 - 32 * c)) - 1u;
   __syncthreads();
   // (3) compact the needed sites (ascending local index); word offsets by a
   // warp scan
@@ -715,155 +805,175 @@ __device__ __forceinline__ void propose_leaf(const Geo g, const Dev d, const int
     int base = 0;
     for (int w0 = 0; w0 < nbw; w0 += 32) {
       const int w2 = w0 + lane;
-      const int c = w2 < nbw ? __popc(need[w2]) : 0;
+      const int c = w2 < nbw ? __popc(S.need[w2]) : 0;
       int incl = c;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int t2 = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += t2;
       }
-      if (w2 < nbw) woff[w2] = base + incl - c;
+      if (w2 < nbw) S.woff[w2] = base + incl - c;
       base += __shfl_sync(0xffffffffu, incl, 31);
     }
-    if (lane == 0) woff[nbw] = base;
+    if (lane == 0) {
+      S.woff[nbw] = base;
+      S.misc[2] = base;
+    }
   }
   __syncthreads();
-  for (int w2 = tid; w2 < nbw; w2 += blockDim.x) {
-    uint32_t m = need[w2];
-    int o = woff[w2];
+  for (int w2 = tid; w2 < nbw; w2 += 128) {
+    uint32_t m = S.need[w2];
+    int o = S.woff[w2];
     while (m) {
-      int b = __ffs(m) - 1;
+      const int b = __ffs(m) - 1;
       const int l = 32 * w2 + b;
       // l = x + W (y + W z) by reciprocal multiplication: floor(l rW / 2^16)
       // = floor(l / W) for l < 2^16 / W (W <= 12, l < 1728)
       const int q1 = (l * rW) >> 16, z = (q1 * rW) >> 16;
-      if (KMC_IN(o < W3, d.err)) sites[o] = (uint16_t)((l - q1 * W) | ((q1 - z * W) << 4) | (z << 8));
+      if (KMC_IN(o < W3, d.err)) S.sites[o] = (uint16_t)((l - q1 * W) | ((q1 - z * W) << 4) | (z << 8));
       o++;
       m &= m - 1;
     }
   }
   __syncthreads();
-  const int nsites = woff[nbw];
-
-  // (4) near-field pair sums.  Sources: own leaf first (pairs at distance 0
-  // skipped), then the 26 other leaves, in passes of whole leaves.  The
-  // sources of a pass are split evenly between the four warps, and every warp
-  // evaluates all needed sites against its share, two sites per lane per
-  // round, so that the four warps (one per SM sub-partition) carry the same
-  // number of rsqrt lanes whatever the number of sites.  The per-warp partial
-  // sums meet in fixed point: integer adds are associative, so the potentials
-  // do not depend on the order in which the warps arrive.  Scale 2^ks with
-  // 2^ks * bound < 2^(bits - 2), where bound >= |any partial or total| is
-  // max|q| times the number of sources over the smallest separation (1 site).
+  const int nsites = S.woff[nbw];
+  // fixed-point sums of the needed sites cleared (integer view of phis)
   typedef typename std::conditional<F32, int, long long>::type Acc;
-  Acc* acc = (Acc*)phis;
-  for (int b = tid; b < nsites; b += blockDim.x) {
-    const int sv = sites[b];
+  Acc* acc = (Acc*)S.phis;
+  for (int b = tid; b < nsites; b += 128) {
+    const int sv = S.sites[b];
     acc[(sv & 15) + W * (((sv >> 4) & 15) + W * (sv >> 8))] = 0;
   }
-  // no sites: only the prefetch to drain; cached sums: no pairs (and no prefetch)
-  const int npass = mode == PROP_CACHED ? 0 : (nsites ? misc[0] : 1);
-  const int ks = misc[1];
-  for (int pass = 0; pass < npass; pass++)
-    (void)KMC_IN(nb_off[pq[pass + 1]] - nb_off[pq[pass]] <= (F32 ? chunk / 4 + 1 : chunk), d.err);
-  const T scale = (T)ldexp(1.0, ks);
-  for (int pass = 0; pass < npass; pass++) {
-    const int q0 = pq[pass], q1 = pq[pass + 1];
-    if (pass > 0) {
-      __syncthreads();  // everyone is done with the previous pass's sources
-      if (F32 && tid == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(bar, (uint32_t)(80 * (nb_off[q1] - nb_off[q0])));
-        for (int q = q0; q < q1; q++) {
-          const int ng = (nb_cnt[q] + 3) >> 2;
-          if (ng)
-            bulk_copy_g2s(src + 80 * (nb_off[q] - nb_off[q0]), d.sgrp + 20 * (int64_t)nb_leaf[q] * gpl,
-                          (uint32_t)(80 * ng), bar);
-        }
+  return nsites;
+}
+
+// Staging of source pass [q0, q1) into S.src.  FP32: waits (bounded) for the
+// pass's bulk copies (barrier phase `parity`), then turns the copied slot
+// positions into staged records in this leaf's frame (a warp per leaf, a lane
+// per source) and pads the last tile of eight.  FP64: loads the pass from the
+// slot arrays.  Returns false for the whole CTA when the copies did not
+// arrive (flagged; the copies drained); the caller then leaves the leaf.
+template <typename T>
+__device__ __forceinline__ bool leaf_stage(const Geo& g, const Dev& d, const LeafSmem<T>& S, const LeafCtx& x, int q0,
+                                           int q1, uint32_t parity) {
+  typedef typename vec4<T>::type V4;
+  constexpr bool F32 = sizeof(T) == 4;
+  const int W = g.W, nL = g.nL;
+  const T ih = (T)(1.0 / g.h);
+  if constexpr (F32) {
+    const bool ok = mbar_wait_bounded(S.bar, parity, KMC_WAIT_NS);
+    if (__syncthreads_or(!ok)) {
+      if (x.tid == 0) {
+        atomicOr(&d.err[0], KMC_DERR_TIMEOUT);
+        mbar_wait_bounded(S.bar, parity, KMC_WAIT_NS);
+      }
+      __syncthreads();
+      return false;
+    }
+    for (int q = q0 + x.warp; q < q1; q += 4) {
+      const int qq = q == 0 ? 13 : (q <= 13 ? q - 1 : q);
+      const int ux = x.lx + qq % 3 - 1, uy = x.ly + (qq / 3) % 3 - 1, uz = x.lz + qq / 9 - 1;
+      const int ox = (ux - wrap1(ux, nL)) * W - x.gx0, oy = (uy - wrap1(uy, nL)) * W - x.gy0;
+      const int oz = (uz - wrap1(uz, nL)) * W - x.gz0;
+      float4* Sr = (float4*)S.src + (S.nb_off[q] - S.nb_off[q0]);
+      for (int j = x.lane; j < S.nb_cnt[q]; j += 32) {
+        const float4 v = Sr[j];
+        Sr[j] = nfmma::record(lattice_coord(v.x, ih) + ox, lattice_coord(v.y, ih) + oy, lattice_coord(v.z, ih) + oz, v.w);
       }
     }
-    if constexpr (F32) {
-      const bool ok = mbar_wait_bounded(bar, pass & 1, KMC_WAIT_NS);
-      if (__syncthreads_or(!ok)) {  // copies did not arrive: flag, drain, leave
-        if (tid == 0) {
-          atomicOr(&d.err[0], KMC_DERR_TIMEOUT);
-          mbar_wait_bounded(bar, pass & 1, KMC_WAIT_NS);
-        }
-        __syncthreads();
-        return;
-      }
-      // the copied groups into this leaf's corner frame (own leaf: already):
-      // every thread takes groups of the pass, finding a group's leaf q (the
-      // largest with nb_off[q] <= group) by a binary search over nb_off
-      for (int gg = nb_off[max(q0, 1)] + tid; gg < nb_off[q1]; gg += blockDim.x) {
-        int q = 0;
-#pragma unroll
-        for (int st = 16; st > 0; st >>= 1)
-          if (q + st <= 27 && nb_off[q + st] <= gg) q += st;
-        const int qq = q <= 13 ? q - 1 : q;
-        const float ox = i2f((qq % 3 - 1) * W), oy = i2f(((qq / 3) % 3 - 1) * W);
-        const float oz = i2f((qq / 9 - 1) * W);
-        float4* G = (float4*)src + 5 * (gg - nb_off[q0]);
-#pragma unroll
-        for (int pr = 0; pr < 2; pr++) {
-          float4 A = G[2 * pr], B = G[2 * pr + 1];
-          A.x += ox;
-          A.y += ox;
-          A.z += oy;
-          A.w += oy;
-          B.x += oz;
-          B.y += oz;
-          B.z = A.x * A.x + A.z * A.z + B.x * B.x;
-          B.w = A.y * A.y + A.w * A.w + B.y * B.y;
-          G[2 * pr] = A;
-          G[2 * pr + 1] = B;
-        }
-      }
-    } else {
-      for (int q = q0 + warp; q < q1; q += nwarp) {
-        const int qq = q == 0 ? 13 : (q <= 13 ? q - 1 : q);
-        const int ux = lx + qq % 3 - 1, uy = ly + (qq / 3) % 3 - 1, uz = lz + qq / 9 - 1;
-        const int shx = ux - wrap1(ux, nL), shy = uy - wrap1(uy, nL), shz = uz - wrap1(uz, nL);
-        const int e0 = nb_off[q] - nb_off[q0];
-        for (int j = lane; j < nb_cnt[q]; j += 32) {  // lattice coordinates in this leaf's frame
-          const V4 v = spos[nb_base[q] + j];
-          NearField<T>::stage(src, e0 + j, lattice_coord(v.x, ih) - gx0 + shx * W,
-                              lattice_coord(v.y, ih) - gy0 + shy * W, lattice_coord(v.z, ih) - gz0 + shz * W, v.w);
-        }
-      }
-    }
-    __syncthreads();
-    // this warp's share of the pass's groups (FP32) or sources (FP64)
-    const int nu = nb_off[q1] - nb_off[q0];
-    const int u0 = (nu * warp) / nwarp, u1 = (nu * (warp + 1)) / nwarp;
-    const int nown = q0 == 0 ? (F32 ? (cnt_own + 3) >> 2 : cnt_own) : 0;  // own-leaf units lead pass 0
-    if (u1 > u0) {
-      for (int rb = 0; rb < nsites; rb += 64) {
-        const int b0 = rb + lane, b1 = b0 + 32;
-        const bool two = rb + 32 < nsites;  // warp-uniform
-        const int sv0 = b0 < nsites ? sites[b0] : 0, sv1 = b1 < nsites ? sites[b1] : 0;
-        const int ix0 = sv0 & 15, iy0 = (sv0 >> 4) & 15, iz0 = sv0 >> 8;
-        const int ix1 = sv1 & 15, iy1 = (sv1 >> 4) & 15, iz1 = sv1 >> 8;
-        const int l0 = ix0 + W * (iy0 + W * iz0), l1 = ix1 + W * (iy1 + W * iz1);
-        NearField<T> nf;
-        nf.reset();
-        if constexpr (F32) {
-          nf.run_span((const float4*)src, u0, u1, nown, two, i2f(ix0), i2f(iy0), i2f(iz0), i2f(ix1), i2f(iy1),
-                      i2f(iz1));
-        } else {
-          nf.run2(src, isq, u0, u1, two, ix0, iy0, iz0, ix1, iy1, iz1, nisq, d.err);
-        }
-        if (b0 < nsites && KMC_IN(l0 >= 0 && l0 < W3, d.err)) fixed_add(&acc[l0], nf.sum(0) * scale);
-        if (two && b1 < nsites && KMC_IN(l1 >= 0 && l1 < W3, d.err)) fixed_add(&acc[l1], nf.sum(1) * scale);
+    const int ns = S.nb_off[q1] - S.nb_off[q0];
+    if (x.tid < ((8 - (ns & 7)) & 7)) ((float4*)S.src)[ns + x.tid] = nfmma::pad_record();
+  } else {
+    const V4* spos = (const V4*)d.spos64;
+    for (int q = q0 + x.warp; q < q1; q += 4) {
+      const int qq = q == 0 ? 13 : (q <= 13 ? q - 1 : q);
+      const int ux = x.lx + qq % 3 - 1, uy = x.ly + (qq / 3) % 3 - 1, uz = x.lz + qq / 9 - 1;
+      const int shx = ux - wrap1(ux, nL), shy = uy - wrap1(uy, nL), shz = uz - wrap1(uz, nL);
+      const int e0 = S.nb_off[q] - S.nb_off[q0];
+      for (int j = x.lane; j < S.nb_cnt[q]; j += 32) {  // lattice coordinates in this leaf's frame
+        const V4 v = spos[S.nb_base[q] + j];
+        NearField<T>::stage(S.src, e0 + j, lattice_coord(v.x, ih) - x.gx0 + shx * W,
+                            lattice_coord(v.y, ih) - x.gy0 + shy * W, lattice_coord(v.z, ih) - x.gz0 + shz * W, v.w);
       }
     }
   }
+  return true;
+}
+
+// Pair sums of the staged pass [q0, q1) for warp `warp` of the four that share
+// it: the pass's sources (FP32: tiles of eight) are split evenly between the
+// warps, and every warp evaluates all needed sites against its share; the
+// partial sums meet in fixed point (integer adds are associative, so the
+// potentials do not depend on the order in which the warps arrive).  Scale
+// 2^ks with 2^ks * bound < 2^(bits - 2), bound = max|q| times the number of
+// sources over the smallest separation (1 site).
+template <typename T>
+__device__ __forceinline__ void leaf_pairs(const Geo& g, const Dev& d, const LeafSmem<T>& S, int nsites, int q0, int q1,
+                                           T scale, int warp, int lane) {
+  constexpr bool F32 = sizeof(T) == 4;
+  const int W = g.W, W3 = W * W * W;
+  const int ns = S.nb_off[q1] - S.nb_off[q0];
+  const int nu = F32 ? (ns + 7) >> 3 : ns;
+  const int u0 = (nu * warp) >> 2, u1 = (nu * (warp + 1)) >> 2;
+  if (u1 <= u0) return;
+  if constexpr (F32) {
+    const int jg = min(max(q0 == 0 ? (S.nb_cnt[0] + 7) >> 3 : 0, u0), u1);  // own-leaf tiles lead pass 0
+    const int nts = (nsites + 15) >> 4;
+    const uint32_t* R = (const uint32_t*)S.src;
+    int* acc = (int*)S.phis;
+    for (int t0 = 0; t0 < nts; t0 += nfmma::TMAX) {
+      const int nt = min(nfmma::TMAX, nts - t0);
+      if (nt == 2) nfmma::round<2>(R, S.sites, nsites, W, t0, u0, jg, u1, acc, scale, lane, d.err);
+      else nfmma::round<1>(R, S.sites, nsites, W, t0, u0, jg, u1, acc, scale, lane, d.err);
+    }
+  } else {
+    const int nisq = 3 * (2 * W - 1) * (2 * W - 1) + 1;
+    long long* acc = (long long*)S.phis;
+    for (int rb = 0; rb < nsites; rb += 64) {
+      const int b0 = rb + lane, b1 = b0 + 32;
+      const bool two = rb + 32 < nsites;  // warp-uniform
+      const int sv0 = b0 < nsites ? S.sites[b0] : 0, sv1 = b1 < nsites ? S.sites[b1] : 0;
+      const int ix0 = sv0 & 15, iy0 = (sv0 >> 4) & 15, iz0 = sv0 >> 8;
+      const int ix1 = sv1 & 15, iy1 = (sv1 >> 4) & 15, iz1 = sv1 >> 8;
+      const int l0 = ix0 + W * (iy0 + W * iz0), l1 = ix1 + W * (iy1 + W * iz1);
+      NearField<T> nf;
+      nf.reset();
+      nf.run2(S.src, S.isq, u0, u1, two, ix0, iy0, iz0, ix1, iy1, iz1, nisq, d.err);
+      if (b0 < nsites && KMC_IN(l0 >= 0 && l0 < W3, d.err)) fixed_add(&acc[l0], nf.sum(0) * scale);
+      if (two && b1 < nsites && KMC_IN(l1 >= 0 && l1 < W3, d.err)) fixed_add(&acc[l1], nf.sum(1) * scale);
+    }
+  }
+}
+
+// Finish of a leaf whose fixed-point near-field sums are complete: PROP_FILL
+// writes them to the near-field cache; otherwise (4) near field back to
+// floating point plus the L2P of the leaf's local expansion at every needed
+// site, then (5) the write-out of old-position potentials and unmasked hop
+// potentials by re-enumerating the hops of phase 2.  Potentials are written
+// in precision T (FP32 arrays in the mixed form, FP64 arrays in the FP64 form).
+template <typename T, int NH, int mode>
+__device__ __forceinline__ void leaf_finish(const Geo& g, const Dev& d, const LeafSmem<T>& S, const LeafCtx& x,
+                                            int nsites) {
+  typedef typename cplx<T>::type C;
+  typedef typename vec4<T>::type V4;
+  constexpr bool F32 = sizeof(T) == 4;
+  typedef typename std::conditional<F32, int, long long>::type Acc;
+  const int W = g.W, W3 = W * W * W, nbw = (W3 + 31) / 32, E = g.E;
+  const int tid = x.tid, lane = x.lane, warp = x.warp;
+  const T h = (T)g.h, ih = (T)(1.0 / g.h);
+  const V4* spos = (const V4*)(F32 ? (const void*)d.spos32 : (const void*)d.spos64);
+  T* out_old = (T*)(F32 ? (void*)d.phi_old32 : (void*)d.phi_old);
+  T* out_new = (T*)(F32 ? (void*)d.phi_new32 : (void*)d.phi_new);
+  const Acc* acc = (const Acc*)S.phis;
+  const int ks = S.misc[1];
+  constexpr int hs = NH == KMC_NHOP ? 0 : 1, ne = hs ? 27 : 1 + KMC_NHOP, nhop = NH;
+  (void)nbw;
   if (mode == PROP_FILL) {  // the sums at every site into the cache, rescaled to 2^-near_ks
     __syncthreads();
     const int sh = g.near_ks - ks;
-    long long* dst = d.nearfx + leaf * (int64_t)g.cap;
-    for (int b = tid; b < nsites; b += blockDim.x) {
-      const int sv = sites[b];
+    long long* dst = d.nearfx + x.leaf * (int64_t)g.cap;
+    for (int b = tid; b < nsites; b += 128) {
+      const int sv = S.sites[b];
       const int l = (sv & 15) + W * (((sv >> 4) & 15) + W * (sv >> 8));
       if (!KMC_IN(l >= 0 && l < W3 && W3 <= g.cap, d.err)) continue;
       const long long a = (long long)acc[l];
@@ -880,40 +990,37 @@ __device__ __forceinline__ void propose_leaf(const Geo g, const Dev d, const int
     const int e = warp + 4 * i;
     if (e < ne) {
       const int li = c_ent_leaf[hs][e];
-      if (lane < nb_cnt[li]) {
-        wu[i] = d.uid[nb_base[li] + lane];
-        wv[i] = spos[nb_base[li] + lane];
+      if (lane < S.nb_cnt[li]) {
+        wu[i] = d.uid[S.nb_base[li] + lane];
+        wv[i] = spos[S.nb_base[li] + lane];
       }
     }
   }
   __syncthreads();
-  // near field back to floating point (lattice units, times 1/h), plus
-  // the L2P of the leaf's local expansion
   {
     const T hw = (T)(0.5 * W);
     const T back = (T)ldexp(1.0, -ks) * ih;  // lattice units to physical
     const T cback = (T)ldexp(1.0, -g.near_ks) * ih;
-    const long long* cache = mode == PROP_CACHED ? d.nearfx + leaf * (int64_t)g.cap : nullptr;
-    for (int b = tid; b < nsites; b += blockDim.x) {
-      const int sv = sites[b];
+    const long long* cache = mode == PROP_CACHED ? d.nearfx + x.leaf * (int64_t)g.cap : nullptr;
+    for (int b = tid; b < nsites; b += 128) {
+      const int sv = S.sites[b];
       const int ix = sv & 15, iy = (sv >> 4) & 15, iz = sv >> 8;
       const int l = ix + W * (iy + W * iz);
       if (!KMC_IN(l >= 0 && l < W3, d.err)) continue;
       const T near = cache ? (T)cache[l] * cback : (T)acc[l] * back;
-      phis[l] = near + l2p_point<T, C>(Lc, g.p, (small_to<T>(ix) + (T)0.5 - hw) * h,
-                                        (small_to<T>(iy) + (T)0.5 - hw) * h, (small_to<T>(iz) + (T)0.5 - hw) * h);
+      S.phis[l] = near + l2p_point<T, C>(S.Lc, g.p, (small_to<T>(ix) + (T)0.5 - hw) * h,
+                                         (small_to<T>(iy) + (T)0.5 - hw) * h, (small_to<T>(iz) + (T)0.5 - hw) * h);
     }
   }
   __syncthreads();
-  // (5) write-out: old-position potentials and unmasked hop potentials
 #pragma unroll 1
   for (int i = 0; i < (ne + 3) / 4; i++) {
     const int e = warp + 4 * i;
     if (e >= ne) break;
     const int li = c_ent_leaf[hs][e];
     const uint32_t hm = c_ent_hops[hs][e];
-    const int64_t mb = nb_base[li];
-    const int cm = nb_cnt[li];
+    const int64_t mb = S.nb_base[li];
+    const int cm = S.nb_cnt[li];
     for (int j = lane; j < cm; j += 32) {
       const bool pre = j < 32 && i < 2;
       const int32_t u = pre ? (i == 0 ? wu[0] : wu[1]) : d.uid[mb + j];
@@ -921,30 +1028,69 @@ __device__ __forceinline__ void propose_leaf(const Geo g, const Dev d, const int
       const int gx = lattice_coord(v.x, ih), gy = lattice_coord(v.y, ih), gz = lattice_coord(v.z, ih);
       if (!KMC_IN(u >= 0 && u < g.n, d.err)) continue;
       if (e == 0) {
-        const int lo = (gx - gx0) + W * ((gy - gy0) + W * (gz - gz0));
-        if (KMC_IN(lo >= 0 && lo < W3, d.err)) out_old[u] = phis[lo];
+        const int lo = (gx - x.gx0) + W * ((gy - x.gy0) + W * (gz - x.gz0));
+        if (KMC_IN(lo >= 0 && lo < W3, d.err)) out_old[u] = S.phis[lo];
       }
       for (uint32_t hb = hm; hb; hb &= hb - 1) {
         const int k = __ffs(hb) - 1;
         const int rx = gx + hop_c(k, 0), ry = gy + hop_c(k, 1), rz = gz + hop_c(k, 2);
         if (g.bc && (rx < 0 || rx >= E || ry < 0 || ry >= E || rz < 0 || rz >= E)) continue;  // phase 2
         const int tx = wrap1(rx, E), ty = wrap1(ry, E), tz = wrap1(rz, E);
-        int ux = tx - gx0, uy = ty - gy0, uz = tz - gz0;
+        const int ux = tx - x.gx0, uy = ty - x.gy0, uz = tz - x.gz0;
         if (ux < 0 || ux >= W || uy < 0 || uy >= W || uz < 0 || uz >= W) continue;
-        int lt = ux + W * (uy + W * uz);
-        if (bits[lt >> 5] & (1u << (lt & 31))) continue;  // masked: written in phase 2
-        out_new[(int64_t)nhop * u + k] = phis[lt];
+        const int lt = ux + W * (uy + W * uz);
+        if (S.bits[lt >> 5] & (1u << (lt & 31))) continue;  // masked: written in phase 2
+        out_new[(int64_t)nhop * u + k] = S.phis[lt];
         d.mask[(int64_t)nhop * u + k] = 1;
       }
     }
   }
 }
 
+// One leaf by one CTA of four warps (the per-leaf kernels: FP64 form, the
+// near-field cache modes, replica batches): setup, sites, then the source
+// passes (staged, summed) and the finish.
+// mode: PROP_SUM (the pair sums of this step), PROP_FILL (pair sums at every
+// site of the leaf into the near-field cache d.nearfx; no hops, no L2P, no
+// outputs) or PROP_CACHED (the near-field sums read from the cache, no pairs).
+template <typename T, int NH, int mode>
+__device__ __forceinline__ void propose_leaf(const Geo& g, const Dev& d, const int chunk, const int64_t leaf) {
+  constexpr bool F32 = sizeof(T) == 4;
+  extern __shared__ __align__(128) unsigned char sm[];
+  const LeafSmem<T> S(sm, g, chunk);
+  const LeafCtx x = leaf_ctx(g, leaf, threadIdx.x);
+  leaf_setup<T, mode>(g, d, S, x, chunk);
+  const int nsites = leaf_sites<T, NH, mode>(g, d, S, x);
+  // no sites: only the first pass's copies to drain; cached sums: no pairs (and no copies)
+  const int npass = mode == PROP_CACHED ? 0 : (nsites ? S.misc[0] : 1);
+  for (int pass = 0; pass < npass; pass++)
+    (void)KMC_IN(S.nb_off[S.pq[pass + 1]] - S.nb_off[S.pq[pass]] <= chunk, d.err);
+  const T scale = (T)ldexp(1.0, S.misc[1]);
+  for (int pass = 0; pass < npass; pass++) {
+    const int q0 = S.pq[pass], q1 = S.pq[pass + 1];
+    if (pass > 0) {
+      __syncthreads();  // everyone is done with the previous pass's sources
+      if (F32 && x.tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(S.bar, (uint32_t)(16 * (S.nb_off[q1] - S.nb_off[q0])));
+        for (int q = q0; q < q1; q++)
+          if (S.nb_cnt[q])
+            bulk_copy_g2s(S.src + 16 * (S.nb_off[q] - S.nb_off[q0]), d.spos32 + S.nb_base[q],
+                          (uint32_t)(16 * S.nb_cnt[q]), S.bar);
+      }
+    }
+    if (!leaf_stage<T>(g, d, S, x, q0, q1, pass & 1)) return;
+    __syncthreads();
+    leaf_pairs<T>(g, d, S, nsites, q0, q1, scale, x.warp, x.lane);
+  }
+  leaf_finish<T, NH, mode>(g, d, S, x, nsites);
+}
+
 // one CTA per leaf of one system
 template <typename T, int NH, int mode>
 __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
     k_propose_lattice(const Geo g, const Dev d, int chunk) {
-  propose_leaf<T, NH, mode>(g, d, chunk, 0);
+  propose_leaf<T, NH, mode>(g, d, chunk, (int64_t)blockIdx.x);
 }
 
 // one CTA per leaf of every replica of a batch (blocks [off[r], off[r + 1]) are replica r's leaves)
@@ -952,13 +1098,14 @@ template <typename T, int NH, int mode>
 __global__ void __launch_bounds__(PROP_THREADS, mode == PROP_CACHED ? 12 : 9)
     k_propose_batch(const BatchRep* reps, const int* off, int R, int chunk) {
   const int r = batch_find(off, R, blockIdx.x);
-  propose_leaf<T, NH, mode>(reps[r].g, reps[r].d, chunk, off[r]);
+  propose_leaf<T, NH, mode>(reps[r].g, reps[r].d, chunk, (int64_t)blockIdx.x - off[r]);
 }
+
 static size_t propose_smem(const Geo& g, int prec, int chunk) {
   const size_t ts = prec == 0 ? 8 : 4;
   const int W3 = g.W * g.W * g.W;
   const int nbw = (W3 + 31) / 32;
-  const size_t srcb = prec == 0 ? NearField<double>::bytes(chunk) : NearField<float>::bytes(chunk);
+  const size_t srcb = prec == 0 ? NearField<double>::bytes(chunk) : nfmma::bytes(chunk);
   const size_t isqb = prec == 0 ? 8 + 8 * (size_t)(3 * (2 * g.W - 1) * (2 * g.W - 1) + 1) : 0;
   return srcb + 2 * ts * (size_t)g.P + 27 * 8 + 8 + (28 + 27 + 27 + 28 + 4) * 4 + ts * (size_t)W3 +
          4 * (size_t)(3 * nbw + 1) + 2 * (size_t)((W3 + 1) & ~1) + isqb;
@@ -1872,14 +2019,7 @@ __device__ __forceinline__ void acc_move_role(const Geo& g, const Dev& d, const 
     d.spos64[so] = d.spos64[last];
     d.spos32[so] = d.spos32[last];
     d.slot_of[ul] = so;
-    if (d.sgrp) {
-      const int sl = d.site[ul], E = g.E, W = g.W;
-      const int lx = (int)(lo % g.nL), ly = (int)((lo / g.nL) % g.nL), lz = (int)(lo / ((int64_t)g.nL * g.nL));
-      sgrp_put(d.sgrp, g.cap, so, (float)(sl % E - lx * W), (float)((sl / E) % E - ly * W),
-               (float)(sl / (E * E) - lz * W), d.spos32[last].w);
-    }
   }
-  if (d.sgrp) sgrp_pad(d.sgrp, g.cap, last);
   d.cnt[lo] -= 1;
   int c = d.cnt[ln];
   if (c >= g.cap) {  // cannot place: undo the removal accounting and flag
@@ -1892,12 +2032,6 @@ __device__ __forceinline__ void acc_move_role(const Geo& g, const Dev& d, const 
   d.uid[sn] = i;
   d.spos64[sn] = make_double4_32a(mv.rn[0], mv.rn[1], mv.rn[2], mv.q);
   d.spos32[sn] = make_float4((float)mv.rn[0], (float)mv.rn[1], (float)mv.rn[2], (float)mv.q);
-  if (d.sgrp) {
-    const int sn2 = mv.site_new, E = g.E, W = g.W;
-    const int lx = ln % g.nL, ly = (ln / g.nL) % g.nL, lz = ln / (g.nL * g.nL);
-    sgrp_put(d.sgrp, g.cap, sn, (float)(sn2 % E - lx * W), (float)((sn2 / E) % E - ly * W),
-             (float)(sn2 / (E * E) - lz * W), (float)mv.q);
-  }
   d.slot_of[i] = (int32_t)sn;
   d.pos[3 * i] = mv.rn[0];
   d.pos[3 * i + 1] = mv.rn[1];

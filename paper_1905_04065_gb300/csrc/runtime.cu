@@ -450,7 +450,6 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   ALLOC(d.spos64, sizeof(double4_32a) * nslot);
   ALLOC(d.spos32, sizeof(float4) * nslot);
   if (g.E > 0) {
-    ALLOC(d.sgrp, sizeof(float) * 20 * (size_t)g.ML * (size_t)sgrp_groups(g.cap));
     ALLOC(d.isq, sizeof(double) * KMC_ISQ_N);
   }
   if (g.near_cache) ALLOC(d.nearfx, sizeof(long long) * (size_t)g.ML * (size_t)g.cap);
