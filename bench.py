@@ -625,7 +625,8 @@ def run_gpu(args):
     mufu_peak = 16 * nsm * sm_max * 1e6  # rsqrt/s
     pairs = work["pairs"]
     achieved = pairs / (prop_ms * 1e-3)
-    fp32_ops = 8 * pairs + l2p_flops(p) * work["points"]
+    # FP32 pipes: one FMA per pair (the squared distances come from the tensor cores) and the L2P
+    fp32_ops = 2 * pairs + l2p_flops(p) * work["points"]
     fma_peak = 128 * nsm * sm_max * 1e6
     t_mufu = pairs / mufu_peak
     t_fma = fp32_ops / fma_peak
@@ -640,7 +641,8 @@ def run_gpu(args):
                                and args.bc == "periodic" else None),
             "peak_source": f"16 MUFU/clk/SM x {nsm} SMs x {sm_max:.0f} MHz ({src} max clock)",
             "pairs_per_launch": pairs, "points_per_launch": work["points"],
-            "fp32_ops_per_launch": fp32_ops, "t_min_ms": 1e3 * max(t_mufu, t_fma), "t_meas_ms": prop_ms,
+            "fp32_ops_per_launch": fp32_ops, "tensor_f16_flops_per_launch": 16 * pairs,
+            "t_min_ms": 1e3 * max(t_mufu, t_fma), "t_meas_ms": prop_ms,
             "frac_of_alu_bound": 1e3 * max(t_mufu, t_fma) / prop_ms}
 
     rooflines = phase_rooflines(work, {nm: phases[i] / args.steps for i, nm in enumerate(k.PHASES)}, E, L, len(q),
@@ -711,13 +713,15 @@ def run_batch(args):
     reps = workloads.batch_replicas(nrep, first=rank * nrep)  # each rank its own replicas
     p, kT = B["p"], B["kT"]
     t0 = time.perf_counter()
-    levels, hops = [], 0
+    levels, hops, pairs = [], 0, 0
     for r in reps:
         pos = workloads.site_positions(r["E"], r["sites"])
         L = autotune.tune_levels(r["E"], pos, r["q"], p, "mixed", kT) if not args.no_tune else \
             autotune.valid_levels(r["E"])[0]
         levels.append(L)
-        hops += pair_count(r["E"], L, r["sites"])["hops"]
+        pc = pair_count(r["E"], L, r["sites"])
+        hops += pc["hops"]
+        pairs += pc["pairs"]
 
     def make(precision):
         return [k.kmc_fmm_init(workloads.site_positions(r["E"], r["sites"]), r["q"], float(r["E"]), L, p,
@@ -744,6 +748,7 @@ def run_batch(args):
     _, _, dev_ms = k.kmc_batch_run(bat, u[args.warmup: args.warmup + args.steps], timed=True)
     wall_ms = 1e3 * (time.perf_counter() - t1)
     clocks = clk.stop()
+    prop_ms = k.kmc_batch_propose_timed(bat, 10) if info["fused"] else None
     units, tot = aggregate(hops * args.steps, dev_ms, device=f"cuda:{dev}")
     e2e_units, e2e_tot = aggregate(hops * args.steps, wall_ms, device=f"cuda:{dev}")
     del bat
@@ -785,6 +790,21 @@ def run_batch(args):
                                            "FP64 selection, O(E^3) site update per accept); kmc_steps_per_s = batch "
                                            "steps per second"}
     value = units / (tot * 1e-3)
+    roof = None
+    if prop_ms:
+        peaks, src = measured_peaks()
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        mufu_peak = 16 * nsm * sm_max * 1e6
+        roof = {"bound": "alu", "kernel": "k_propose_batch<float> (every member's leaves, one launch per pass "
+                                          "capacity class)",
+                "achieved": pairs / (prop_ms * 1e-3) / 1e9, "peak": mufu_peak / 1e9,
+                "unit": "G pair-interactions/s (MUFU rsqrt)", "frac": pairs / (prop_ms * 1e-3) / mufu_peak,
+                "traffic": None, "pairs_per_launch": pairs, "t_meas_ms": prop_ms,
+                "work": "pairs = distinct evaluation sites x charges in the 27 neighbouring leaves, summed over "
+                        "the replicas (initial configuration)",
+                "timing": "the batch step's propose launches alone, 10 times, CUDA events on the batch stream",
+                "peak_source": f"16 MUFU/clk/SM x {nsm} SMs x {sm_max:.0f} MHz ({src} max clock)"}
     line = {
         "metric": "dU evals/sec and KMC steps/sec, 64 batched replicas", "value": value,
         "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps,
@@ -807,6 +827,7 @@ def run_batch(args):
         "cpu_baseline": cpu,
         "gpu_launches": info["launches_per_step"] * args.steps,
         "batched_kernels": info["fused"],
+        "roofline": roof,
     }
     print(json.dumps(line))
     return 0

@@ -320,6 +320,13 @@ int kmc_select_static(const double* rates, int64_t n, double zeta, double xi, in
  *   kmc_batch_info: fused (1 = batched kernels), the largest pass capacity in
  *   use, and the kernel launches of one batch step (host ints, each may be
  *   NULL).
+ *   kmc_batch_propose_timed: a measurement hook with no counterpart in the
+ *   paper: runs only the batch step's propose launches (Sec. 3, Eq.
+ *   (proposed_energy_sr) for every member) `reps` times on the batch's stream and stores in
+ *   device_ms (host) the mean device time of one set (CUDA events).  The
+ *   members' state is not changed (the next run recomputes every potential
+ *   it uses).  KMC_ERR_ARG if the batch is not on the batched kernels or has
+ *   not run yet.
  */
 typedef struct kmc_batch* kmc_batch_handle;
 int kmc_batch_create(kmc_batch_handle* b, int count, const kmc_handle* handles);
@@ -328,6 +335,7 @@ int kmc_batch_run_timed(kmc_batch_handle b, int steps, const double* uniforms, i
                         double* device_ms);
 int kmc_batch_set_chunk(kmc_batch_handle b, int chunk);
 int kmc_batch_info(kmc_batch_handle b, int* fused, int* chunk, int* launches_per_step);
+int kmc_batch_propose_timed(kmc_batch_handle b, int reps, double* device_ms);
 const char* kmc_batch_last_error(kmc_batch_handle b);
 void kmc_batch_destroy(kmc_batch_handle b);
 

@@ -47,7 +47,7 @@ EXPORTS = [
     "kmc_fmm_leaf_index", "kmc_fmm_positions", "kmc_last_error", "kmc_fmm_destroy", "kmc_select_static",
     "kmc_check_bounded_wait",
     "kmc_batch_create", "kmc_batch_run", "kmc_batch_run_timed", "kmc_batch_set_chunk", "kmc_batch_info",
-    "kmc_batch_last_error", "kmc_batch_destroy",
+    "kmc_batch_propose_timed", "kmc_batch_last_error", "kmc_batch_destroy",
 ]
 
 
@@ -110,6 +110,7 @@ def load_library(path: str | None = None):
             "kmc_batch_run_timed": (I, [P, I, P, P, P, P]),
             "kmc_batch_set_chunk": (I, [P, I]),
             "kmc_batch_info": (I, [P, P, P, P]),
+            "kmc_batch_propose_timed": (I, [P, I, P]),
             "kmc_batch_last_error": (ctypes.c_char_p, [P]),
             "kmc_batch_destroy": (None, [P]),
         }
@@ -513,6 +514,13 @@ def kmc_batch_info(b: Batch) -> dict:
     f, c, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _batch_check(b, load_library().kmc_batch_info(b.ptr, ctypes.byref(f), ctypes.byref(c), ctypes.byref(n)))
     return {"fused": bool(f.value), "chunk": c.value, "launches_per_step": n.value}
+
+
+def kmc_batch_propose_timed(b: Batch, reps: int = 10) -> float:
+    """Mean device ms of one set of the batch step's propose launches (measurement hook)."""
+    ms = ctypes.c_double()
+    _batch_check(b, load_library().kmc_batch_propose_timed(b.ptr, int(reps), ctypes.byref(ms)))
+    return ms.value
 
 
 def kmc_batch_last_error(b: Batch) -> str:

@@ -315,6 +315,7 @@ struct BatchPlan {
 };
 void fmm_downward_batch(const BatchPlan& bp, cudaStream_t s);
 size_t fmm_coarse_smem(int p, int prec);  // dynamic shared memory of the coarse-level downward kernel
+void kmc_propose_batch(const BatchPlan& bp, cudaStream_t s);
 void kmc_step_batch(const BatchPlan& bp, cudaStream_t s);  // propose, rates, select, record, accept
 void kmc_batch_prepare(const BatchPlan& bp);                // load the kernels, raise their smem limits
 int kmc_propose_chunk_min(const Geo& g);                    // smallest pass capacity for g's leaves

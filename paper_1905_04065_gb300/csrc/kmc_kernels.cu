@@ -2174,9 +2174,9 @@ int kmc_acc_blocks_for(const Geo& g) { return acc_blocks(acc_plan(g)); }
 int kmc_acr_blocks() { return KMC_COARSE_CELLS; }
 size_t kmc_acr_smem_for(const Geo& g) { return sizeof(double2) * ACR_WARPS * g.P; }
 
+// the propose launches of a batch step (one per class of pass capacity)
 template <typename T, int NH>
-static void step_batch_t(const BatchPlan& bp, cudaStream_t s) {
-  constexpr bool MIXED = sizeof(T) == 4;
+static void propose_batch_t(const BatchPlan& bp, cudaStream_t s) {
   for (int c = 0; c < bp.nprop; c++) {
     if (bp.nblk_prop[c] <= 0) continue;
     if (bp.near_cache)
@@ -2186,6 +2186,22 @@ static void step_batch_t(const BatchPlan& bp, cudaStream_t s) {
       k_propose_batch<T, NH, PROP_SUM><<<bp.nblk_prop[c], PROP_THREADS, bp.smem_prop[c], s>>>(bp.reps, bp.off_prop[c],
                                                                                               bp.R, bp.chunk_c[c]);
   }
+}
+
+void kmc_propose_batch(const BatchPlan& bp, cudaStream_t s) {
+  if (bp.nhop == KMC_MAXHOP) {
+    if (bp.prec == 0) propose_batch_t<double, KMC_MAXHOP>(bp, s);
+    else propose_batch_t<float, KMC_MAXHOP>(bp, s);
+  } else {
+    if (bp.prec == 0) propose_batch_t<double, KMC_NHOP>(bp, s);
+    else propose_batch_t<float, KMC_NHOP>(bp, s);
+  }
+}
+
+template <typename T, int NH>
+static void step_batch_t(const BatchPlan& bp, cudaStream_t s) {
+  constexpr bool MIXED = sizeof(T) == 4;
+  propose_batch_t<T, NH>(bp, s);
   k_finalize_batch<MIXED, NH><<<bp.nblk_fin, FIN_THREADS, 0, s>>>(bp.reps, bp.off_fin, bp.R);
   k_select_batch<<<bp.R, SEL_THREADS, 0, s>>>(bp.reps);
   k_record_move_batch<<<(bp.R + 127) / 128, 128, 0, s>>>(bp.reps, bp.R);

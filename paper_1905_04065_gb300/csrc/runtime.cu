@@ -1585,4 +1585,29 @@ int kmc_batch_run_timed(kmc_batch_handle b, int steps, const double* uniforms, i
   return batch_run_impl(b, steps, uniforms, events, dts, device_ms);
 }
 
+
+int kmc_batch_propose_timed(kmc_batch_handle b, int reps, double* device_ms) {
+  KMC_TRACE("kmc_batch_propose_timed");
+  if (!b || reps <= 0 || !device_ms) return KMC_ERR_ARG;
+  *device_ms = 0.0;
+  if (!b->fused) return bfail(b, KMC_ERR_ARG, "propose timing needs a batch on the batched kernels");
+  if (!b->fgraph) return bfail(b, KMC_ERR_ARG, "run the batch once before timing its propose launches");
+  if (cudaSetDevice(b->h[0]->device) != cudaSuccess) return bfail(b, KMC_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = b->s0;
+  BCK(cudaEventRecord(b->t0, s), "event record");
+  for (int k = 0; k < reps; k++) kmc_propose_batch(b->bp, s);
+  BCK(cudaGetLastError(), "batch propose launch");
+  BCK(cudaEventRecord(b->t1, s), "event record");
+  BCK(cudaStreamSynchronize(s), "batch propose");
+  float f = 0.f;
+  BCK(cudaEventElapsedTime(&f, b->t0, b->t1), "event timing");
+  *device_ms = f / reps;
+  for (kmc_fmm* h : b->h) {
+    h->rates_valid = false;
+    const int rc = check_flags(h, "batch propose");
+    if (rc) return bfail(b, rc, "%s", h->msg);
+  }
+  return KMC_OK;
+}
+
 }  // extern "C"

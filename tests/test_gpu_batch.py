@@ -180,3 +180,28 @@ def test_config4_replicas_through_the_batch_against_the_oracle():
         err = np.max(np.abs(dU[ok] - dU_o[ok])) / np.max(np.abs(dU_o[ok]))
         print(f"replica E={pick[r]['E']} N={pick[r]['N']}: max dU error {err:.2e} of max|dU|")
         assert err < TOL10
+
+
+def test_batch_propose_timing_leaves_the_state():
+    """The propose-only timing hook: a positive device time, refused before the first run, and the
+    run after it gives the same events as the same batch that was not timed."""
+    import paper_1905_04065_gb300 as k
+    reps = _replicas()
+    rng = np.random.default_rng(81)
+    u = 1.0 - rng.random((12, len(reps), 2))
+
+    def make():
+        return [k.kmc_fmm_init(workloads.site_positions(E, s), q, float(E), L, 8, precision="mixed",
+                               lattice_edge=E, kT=0.1) for (E, N, L, s, q) in reps]
+    evs = []
+    for timed in (False, True):
+        b = k.kmc_batch_create(make())
+        if timed:
+            with pytest.raises(k.KmcError):
+                k.kmc_batch_propose_timed(b, 2)
+        e1, _ = k.kmc_batch_run(b, u[:6])
+        if timed:
+            assert k.kmc_batch_propose_timed(b, 3) > 0.0
+        e2, _ = k.kmc_batch_run(b, u[6:])
+        evs.append(np.concatenate([e1, e2]))
+    assert np.array_equal(evs[0], evs[1])
