@@ -540,7 +540,8 @@ def run_gpu(args):
     e1 = torch.cuda.Event(enable_timing=True)
     # pinned host buffers, allocated once: the caller owns the outputs
     mask_h = torch.empty((len(q), nhop), dtype=torch.uint8, pin_memory=True)
-    dU_h = torch.empty((len(q), nhop), dtype=torch.float64, pin_memory=True)
+    # the mixed form's own FP32 dU (4 bytes per hop)
+    dU_h = torch.empty((len(q), nhop), dtype=torch.float32, pin_memory=True)
     torch.cuda.synchronize()
     e0.record(stream)
     for s in range(es):
@@ -558,8 +559,9 @@ def run_gpu(args):
            # of every hop, the error flags (16 B) after the proposal and after the accept, kmc_step's
            # event and (dt, Q), the accepted event's mask byte and FP32 dU
            "h2d_bytes_per_step": 16 + 8,
-           "d2h_bytes_per_step": nhop * n * (1 + 8) + 16 + 8 + 16 + 1 + 4 + 16,
-           "path": "kmc_fmm_propose_lattice (mask+dU into pinned host buffers) + kmc_step + kmc_fmm_accept_event"}
+           "d2h_bytes_per_step": nhop * n * (1 + 4) + 16 + 8 + 16 + 1 + 4 + 16,
+           "path": "kmc_fmm_propose_lattice_f32 (mask and FP32 dU into pinned host buffers) + kmc_step + "
+                   "kmc_fmm_accept_event"}
 
     # FP64 form (context)
     fp64 = None

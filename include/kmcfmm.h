@@ -172,6 +172,12 @@ int kmc_fmm_propose(kmc_handle h, int64_t m, const int32_t* particle, const doub
  * kept on the device.
  */
 int kmc_fmm_propose_lattice(kmc_handle h, uint8_t* mask, double* dU);
+/*
+ * The same for the mixed-precision form, with dU in FP32: the form's own
+ * result (its dU assembly is FP32), copied without widening, 4 bytes per hop
+ * instead of 8.  KMC_ERR_STATE for an FP64-form handle.
+ */
+int kmc_fmm_propose_lattice_f32(kmc_handle h, uint8_t* mask, float* dU);
 
 /*
  * Accept the move of particle to target (wrapped), whether proposed or not:

@@ -43,6 +43,7 @@ KMC_BC_DIRICHLET_Z = 2
 
 EXPORTS = [
     "kmc_opts_default", "kmc_fmm_init", "kmc_fmm_energy", "kmc_fmm_propose", "kmc_fmm_propose_lattice",
+    "kmc_fmm_propose_lattice_f32",
     "kmc_fmm_accept", "kmc_fmm_accept_event", "kmc_step", "kmc_run", "kmc_run_profiled", "kmc_fmm_recompute",
     "kmc_fmm_leaf_index", "kmc_fmm_positions", "kmc_last_error", "kmc_fmm_destroy", "kmc_select_static",
     "kmc_check_bounded_wait",
@@ -93,6 +94,7 @@ def load_library(path: str | None = None):
             "kmc_fmm_energy": (I, [P, P]),
             "kmc_fmm_propose": (I, [P, I64, P, P, P, P]),
             "kmc_fmm_propose_lattice": (I, [P, P, P]),
+            "kmc_fmm_propose_lattice_f32": (I, [P, P, P]),
             "kmc_fmm_accept": (I, [P, ctypes.c_int32, P, P]),
             "kmc_fmm_accept_event": (I, [P, I64, P]),
             "kmc_step": (I, [P, P, D, D, P, P, P]),
@@ -174,7 +176,7 @@ def _arg(h: Handle, x, dtype, torch_dtype=None):
 def _out(h: Handle, shape, dtype):
     if h.mem == KMC_MEM_DEVICE:
         import torch
-        tdt = {np.float64: torch.float64, np.uint8: torch.uint8, np.int64: torch.int64,
+        tdt = {np.float64: torch.float64, np.float32: torch.float32, np.uint8: torch.uint8, np.int64: torch.int64,
                np.int32: torch.int32}[np.dtype(dtype).type]
         t = torch.empty(shape, dtype=tdt, device=f"cuda:{h.device}")
         return t, ctypes.c_void_p(t.data_ptr())
@@ -315,7 +317,7 @@ def _given(h: Handle, x, shape, dtype):
     handle's memory kind: checked for shape, dtype and contiguity."""
     if _is_torch(x):
         import torch
-        tdt = {np.float64: torch.float64, np.uint8: torch.uint8}[np.dtype(dtype).type]
+        tdt = {np.float64: torch.float64, np.float32: torch.float32, np.uint8: torch.uint8}[np.dtype(dtype).type]
         if tuple(x.shape) != shape or x.dtype != tdt or not x.is_contiguous() or \
                 (x.device.type == "cuda") != (h.mem == KMC_MEM_DEVICE):
             raise ValueError(f"output buffer must be a contiguous {shape} {tdt} tensor in the handle's memory")
@@ -327,14 +329,21 @@ def _given(h: Handle, x, shape, dtype):
     return x, x.ctypes.data_as(ctypes.c_void_p)
 
 
-def kmc_fmm_propose_lattice(h: Handle, mask=None, dU=None):
+def kmc_fmm_propose_lattice(h: Handle, mask=None, dU=None, dtype=np.float64):
     """(mask[n,nh], dU[n,nh]) for all hops of the handle's hop set.  mask and dU may be
-    caller-owned buffers (e.g. pinned host memory) that are filled in place."""
+    caller-owned buffers (e.g. pinned host memory) that are filled in place.  dtype (or the
+    given dU buffer's dtype) float32: the mixed form's FP32 dU, copied without widening."""
     lib = load_library()
     nh = h.nhop
+    if dU is not None:
+        dtype = np.float32 if str(dU.dtype).endswith("float32") else np.float64
+    dtype = np.dtype(dtype).type
     mask, mp = _out(h, (h.n, nh), np.uint8) if mask is None else _given(h, mask, (h.n, nh), np.uint8)
-    dU, dp = _out(h, (h.n, nh), np.float64) if dU is None else _given(h, dU, (h.n, nh), np.float64)
-    _check(h, lib.kmc_fmm_propose_lattice(h.ptr, mp, dp))
+    dU, dp = _out(h, (h.n, nh), dtype) if dU is None else _given(h, dU, (h.n, nh), dtype)
+    if dtype is np.float32:
+        _check(h, lib.kmc_fmm_propose_lattice_f32(h.ptr, mp, dp))
+    else:
+        _check(h, lib.kmc_fmm_propose_lattice(h.ptr, mp, dp))
     return mask, dU
 
 

@@ -572,11 +572,11 @@ int kmc_fmm_energy(kmc_handle h, double* U) {
   return KMC_OK;
 }
 
-int kmc_fmm_propose_lattice(kmc_handle h, uint8_t* mask, double* dU) {
-  KMC_TRACE("kmc_fmm_propose_lattice");
+static int propose_lattice_impl(kmc_fmm* h, uint8_t* mask, double* dU, float* dU32) {
   int r = guard(h);
   if (r) return r;
   if (h->g.E <= 0) return fail(h, KMC_ERR_STATE, "kmc_fmm_propose_lattice needs lattice mode");
+  if (dU32 && h->prec != 1) return fail(h, KMC_ERR_STATE, "FP32 dU needs the mixed-precision form");
   r = refresh_peff(h);
   if (r) return r;
   kmc_propose_lattice(h->g, h->d, h->prec, h->stream);
@@ -589,7 +589,18 @@ int kmc_fmm_propose_lattice(kmc_handle h, uint8_t* mask, double* dU) {
     if (h->prec == 1) kmc_widen(h->d.dU32, h->d.dU, m, h->stream);
     CK(cudaMemcpyAsync(dU, h->d.dU, sizeof(double) * m, out_kind(h), h->stream));
   }
+  if (dU32) CK(cudaMemcpyAsync(dU32, h->d.dU32, sizeof(float) * m, out_kind(h), h->stream));
   return check_flags(h, "propose_lattice");
+}
+
+int kmc_fmm_propose_lattice(kmc_handle h, uint8_t* mask, double* dU) {
+  KMC_TRACE("kmc_fmm_propose_lattice");
+  return propose_lattice_impl(h, mask, dU, nullptr);
+}
+
+int kmc_fmm_propose_lattice_f32(kmc_handle h, uint8_t* mask, float* dU) {
+  KMC_TRACE("kmc_fmm_propose_lattice_f32");
+  return propose_lattice_impl(h, mask, nullptr, dU);
 }
 
 static int ensure_gen(kmc_fmm* h, int64_t m) {

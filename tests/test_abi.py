@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "kmcfmm.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"\b(kmc_[a-z_]+)\s*\(", src)
+    names = re.findall(r"\b(kmc_[a-z0-9_]+)\s*\(", src)
     return sorted(set(names))
 
 

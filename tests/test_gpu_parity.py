@@ -432,6 +432,26 @@ def test_device_memory_interface(small):
     np.testing.assert_array_equal(dU.cpu().numpy(), dU2)
 
 
+def test_mixed_form_fp32_output(small):
+    """The mixed form's FP32 dU: the same values as its widened FP64 output (NaN where masked), the
+    same mask, into a caller-owned pinned float32 buffer too; refused for an FP64-form handle."""
+    import torch
+    k = _k()
+    w, sites, q, st = small
+    h = _init(w["E"], sites, q, w["L"], 12, precision="mixed")
+    m64, d64 = k.kmc_fmm_propose_lattice(h)
+    m32, d32 = k.kmc_fmm_propose_lattice(h, dtype=np.float32)
+    assert d32.dtype == np.float32 and np.array_equal(m32, m64)
+    np.testing.assert_array_equal(d32.astype(np.float64), d64)
+    buf = torch.empty((len(q), 6), dtype=torch.float32, pin_memory=True)
+    _, d32b = k.kmc_fmm_propose_lattice(h, None, buf)
+    assert d32b is buf
+    np.testing.assert_array_equal(buf.numpy(), d32)
+    h64 = _init(w["E"], sites, q, w["L"], 8)
+    with pytest.raises(k.KmcError):
+        k.kmc_fmm_propose_lattice(h64, dtype=np.float32)
+
+
 def test_caller_owned_pinned_outputs(small):
     """Outputs written in place into caller-owned pinned host buffers equal the
     library-allocated ones; mismatched buffers are refused."""
