@@ -539,16 +539,19 @@ def run_gpu(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     # pinned host buffers, allocated once: the caller owns the outputs
-    mask_h = torch.empty((len(q), nhop), dtype=torch.uint8, pin_memory=True)
-    # the mixed form's own FP32 dU (4 bytes per hop)
-    dU_h = torch.empty((len(q), nhop), dtype=torch.float32, pin_memory=True)
+    # the mixed form's own FP32 dU (4 bytes per hop); two buffer pairs: the copies of step s run
+    # beside its selection and accept, and a pair is reused once the next proposal has returned
+    bufs = [(torch.empty((len(q), nhop), dtype=torch.uint8, pin_memory=True),
+             torch.empty((len(q), nhop), dtype=torch.float32, pin_memory=True)) for _ in range(2)]
     torch.cuda.synchronize()
     e0.record(stream)
     for s in range(es):
-        mask, dU = k.kmc_fmm_propose_lattice(h, mask_h, dU_h)
+        mask_h, dU_h = bufs[s & 1]
+        k.kmc_fmm_propose_lattice(h, mask_h, dU_h, wait=False)
         ev, dt, Q = k.kmc_step(h, None, u[base + s, 0], u[base + s, 1])
         if ev >= 0:
             k.kmc_fmm_accept_event(h, ev)
+    k.kmc_fmm_outputs_wait(h)  # the last step's outputs are on the host
     e1.record(stream)
     e1.synchronize()
     e2e_units, e2e_tot = aggregate(hops * es, e0.elapsed_time(e1), device=f"cuda:{dev}")
@@ -560,8 +563,9 @@ def run_gpu(args):
            # event and (dt, Q), the accepted event's mask byte and FP32 dU
            "h2d_bytes_per_step": 16 + 8,
            "d2h_bytes_per_step": nhop * n * (1 + 4) + 16 + 8 + 16 + 1 + 4 + 16,
-           "path": "kmc_fmm_propose_lattice_f32 (mask and FP32 dU into pinned host buffers) + kmc_step + "
-                   "kmc_fmm_accept_event"}
+           "path": "kmc_fmm_propose_lattice_async (mask and FP32 dU into pinned host buffers, the copies "
+                   "beside kmc_step and kmc_fmm_accept_event) + kmc_step + kmc_fmm_accept_event, "
+                   "kmc_fmm_outputs_wait after the last step"}
 
     # FP64 form (context)
     fp64 = None

@@ -178,6 +178,22 @@ int kmc_fmm_propose_lattice(kmc_handle h, uint8_t* mask, double* dU);
  * instead of 8.  KMC_ERR_STATE for an FP64-form handle.
  */
 int kmc_fmm_propose_lattice_f32(kmc_handle h, uint8_t* mask, float* dU);
+/*
+ * The mixed-form FP32 call without waiting: the proposal, the rates and the
+ * copies of mask and dU are enqueued and the call returns (kmc_step may follow
+ * at once: it runs after the proposal); the copies into mask and dU (pinned
+ * host or device memory, owned by the caller) run on a stream of their own,
+ * overlapping the calls that follow.  Errors of the proposal's kernels are
+ * reported by the next call that synchronises (kmc_step, kmc_fmm_outputs_wait).
+ * kmc_step and kmc_fmm_accept_event run beside the copies; every other call
+ * on the handle is ordered after them.  The outputs may be read, and their
+ * memory reused or freed, after kmc_fmm_outputs_wait (which blocks until the
+ * pending copies are done; KMC_OK when none is pending) or after the next
+ * proposal call on the handle has returned (it is ordered after them and
+ * waits for its own kernels).  KMC_ERR_STATE for an FP64-form handle.
+ */
+int kmc_fmm_propose_lattice_async(kmc_handle h, uint8_t* mask, float* dU);
+int kmc_fmm_outputs_wait(kmc_handle h);
 
 /*
  * Accept the move of particle to target (wrapped), whether proposed or not:

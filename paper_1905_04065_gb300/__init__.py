@@ -43,7 +43,7 @@ KMC_BC_DIRICHLET_Z = 2
 
 EXPORTS = [
     "kmc_opts_default", "kmc_fmm_init", "kmc_fmm_energy", "kmc_fmm_propose", "kmc_fmm_propose_lattice",
-    "kmc_fmm_propose_lattice_f32",
+    "kmc_fmm_propose_lattice_f32", "kmc_fmm_propose_lattice_async", "kmc_fmm_outputs_wait",
     "kmc_fmm_accept", "kmc_fmm_accept_event", "kmc_step", "kmc_run", "kmc_run_profiled", "kmc_fmm_recompute",
     "kmc_fmm_leaf_index", "kmc_fmm_positions", "kmc_last_error", "kmc_fmm_destroy", "kmc_select_static",
     "kmc_check_bounded_wait",
@@ -95,6 +95,8 @@ def load_library(path: str | None = None):
             "kmc_fmm_propose": (I, [P, I64, P, P, P, P]),
             "kmc_fmm_propose_lattice": (I, [P, P, P]),
             "kmc_fmm_propose_lattice_f32": (I, [P, P, P]),
+            "kmc_fmm_propose_lattice_async": (I, [P, P, P]),
+            "kmc_fmm_outputs_wait": (I, [P]),
             "kmc_fmm_accept": (I, [P, ctypes.c_int32, P, P]),
             "kmc_fmm_accept_event": (I, [P, I64, P]),
             "kmc_step": (I, [P, P, D, D, P, P, P]),
@@ -138,6 +140,7 @@ class Handle:
         self.lattice = lattice
         self.device = device
         self.nhop = nhop  # lattice hops per charge (events j = nhop * i + k)
+        self._pending = None  # output buffers of an asynchronous proposal still being copied
 
     def __del__(self):
         try:
@@ -329,10 +332,13 @@ def _given(h: Handle, x, shape, dtype):
     return x, x.ctypes.data_as(ctypes.c_void_p)
 
 
-def kmc_fmm_propose_lattice(h: Handle, mask=None, dU=None, dtype=np.float64):
+def kmc_fmm_propose_lattice(h: Handle, mask=None, dU=None, dtype=np.float64, wait: bool = True):
     """(mask[n,nh], dU[n,nh]) for all hops of the handle's hop set.  mask and dU may be
     caller-owned buffers (e.g. pinned host memory) that are filled in place.  dtype (or the
-    given dU buffer's dtype) float32: the mixed form's FP32 dU, copied without widening."""
+    given dU buffer's dtype) float32: the mixed form's FP32 dU, copied without widening.
+    wait=False (FP32 only): the copies keep running after the call (kmc_step and
+    kmc_fmm_accept_event may run beside them); the buffers hold the outputs after
+    kmc_fmm_outputs_wait(h)."""
     lib = load_library()
     nh = h.nhop
     if dU is not None:
@@ -340,11 +346,22 @@ def kmc_fmm_propose_lattice(h: Handle, mask=None, dU=None, dtype=np.float64):
     dtype = np.dtype(dtype).type
     mask, mp = _out(h, (h.n, nh), np.uint8) if mask is None else _given(h, mask, (h.n, nh), np.uint8)
     dU, dp = _out(h, (h.n, nh), dtype) if dU is None else _given(h, dU, (h.n, nh), dtype)
-    if dtype is np.float32:
+    if not wait:
+        if dtype is not np.float32:
+            raise ValueError("wait=False needs the FP32 output (dtype float32)")
+        _check(h, lib.kmc_fmm_propose_lattice_async(h.ptr, mp, dp))
+        h._pending = (mask, dU)  # the buffers stay alive while their copies run
+    elif dtype is np.float32:
         _check(h, lib.kmc_fmm_propose_lattice_f32(h.ptr, mp, dp))
     else:
         _check(h, lib.kmc_fmm_propose_lattice(h.ptr, mp, dp))
     return mask, dU
+
+
+def kmc_fmm_outputs_wait(h: Handle) -> None:
+    """Block until the copies of the last kmc_fmm_propose_lattice(..., wait=False) are done."""
+    _check(h, load_library().kmc_fmm_outputs_wait(h.ptr))
+    h._pending = None
 
 
 def kmc_fmm_accept(h: Handle, particle: int, target) -> float:

@@ -52,6 +52,11 @@ struct kmc_fmm {
   bool broken;
   bool peff_valid;    // leaf expansions reflect the current expansions
   bool rates_valid;   // device rates belong to the current configuration
+  // asynchronous output copies (kmc_fmm_propose_lattice_async): a copy stream,
+  // the events that order it after the proposal and the next writers after it
+  cudaStream_t cstream;
+  cudaEvent_t ev_ready, ev_copied;
+  bool copy_pending;
   std::vector<void*> allocs;
   // general-propose scratch
   size_t gen_cap;
@@ -142,11 +147,18 @@ static int check_flags(kmc_fmm* h, const char* where) {
   return fail(h, KMC_ERR_STATE, "%s: device error flags 0x%x", where, e[0]);
 }
 
-static int guard(kmc_fmm* h) {
+// after_copies: order the call's work after a pending asynchronous output copy
+// (every call but kmc_step and kmc_fmm_accept_event, which write neither the
+// masks nor the dU the copy reads)
+static int guard(kmc_fmm* h, bool after_copies = true) {
   if (!h) return KMC_ERR_ARG;
   if (h->broken) return fail(h, KMC_ERR_STATE, "handle unusable after an earlier error: %s", h->msg);
   cudaError_t e = cudaSetDevice(h->device);
   if (e != cudaSuccess) return fail(h, KMC_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  if (after_copies && h->copy_pending) {
+    e = cudaStreamWaitEvent(h->stream, h->ev_copied, 0);
+    if (e != cudaSuccess) return fail(h, KMC_ERR_CUDA, "cudaStreamWaitEvent: %s", cudaGetErrorString(e));
+  }
   return KMC_OK;
 }
 
@@ -250,6 +262,12 @@ void kmc_fmm_destroy(kmc_handle h) {
   if (!h) return;
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->cstream) {
+    cudaStreamSynchronize(h->cstream);
+    cudaStreamDestroy(h->cstream);
+    cudaEventDestroy(h->ev_ready);
+    cudaEventDestroy(h->ev_copied);
+  }
   if (h->graph) cudaGraphExecDestroy(h->graph);
   for (void* p : h->allocs) cudaFree(p);
   delete h;
@@ -603,6 +621,45 @@ int kmc_fmm_propose_lattice_f32(kmc_handle h, uint8_t* mask, float* dU) {
   return propose_lattice_impl(h, mask, nullptr, dU);
 }
 
+int kmc_fmm_propose_lattice_async(kmc_handle h, uint8_t* mask, float* dU) {
+  KMC_TRACE("kmc_fmm_propose_lattice_async");
+  int r = guard(h, false);  // the downward pass runs beside the previous call's copies
+  if (r) return r;
+  if (h->g.E <= 0) return fail(h, KMC_ERR_STATE, "kmc_fmm_propose_lattice_async needs lattice mode");
+  if (h->prec != 1) return fail(h, KMC_ERR_STATE, "FP32 dU needs the mixed-precision form");
+  if (!h->cstream) {
+    CK(cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_ready, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_copied, cudaEventDisableTiming));
+  }
+  r = refresh_peff(h);
+  if (r) return r;
+  if (h->copy_pending) CK(cudaStreamWaitEvent(h->stream, h->ev_copied, 0));  // before masks and dU are rewritten
+  kmc_propose_lattice(h->g, h->d, h->prec, h->stream);
+  kmc_finalize_rates(h->g, h->d, h->prec, h->stream);
+  CKLAUNCH();
+  h->rates_valid = true;
+  const int64_t m = (int64_t)h->g.nhop * h->g.nphys;
+  CK(cudaEventRecord(h->ev_ready, h->stream));
+  CK(cudaStreamWaitEvent(h->cstream, h->ev_ready, 0));
+  if (mask) CK(cudaMemcpyAsync(mask, h->d.mask, m, out_kind(h), h->cstream));
+  if (dU) CK(cudaMemcpyAsync(dU, h->d.dU32, sizeof(float) * m, out_kind(h), h->cstream));
+  CK(cudaEventRecord(h->ev_copied, h->cstream));
+  h->copy_pending = true;
+  return KMC_OK;  // the kernels' error flags are read by the next call that synchronises
+}
+
+int kmc_fmm_outputs_wait(kmc_handle h) {
+  KMC_TRACE("kmc_fmm_outputs_wait");
+  int r = guard(h, false);
+  if (r) return r;
+  if (h->copy_pending) {
+    CK(cudaEventSynchronize(h->ev_copied));
+    h->copy_pending = false;
+  }
+  return check_flags(h, "outputs_wait");
+}
+
 static int ensure_gen(kmc_fmm* h, int64_t m) {
   if ((size_t)m <= h->gen_cap) return KMC_OK;
   size_t c = (size_t)m < 1024 ? 1024 : (size_t)m;
@@ -759,7 +816,7 @@ int kmc_fmm_accept(kmc_handle h, int32_t particle, const double target[3], doubl
 
 int kmc_fmm_accept_event(kmc_handle h, int64_t event, double* dU_accepted) {
   KMC_TRACE("kmc_fmm_accept_event");
-  int r = guard(h);
+  int r = guard(h, false);
   if (r) return r;
   const Geo& g = h->g;
   if (g.E <= 0) return fail(h, KMC_ERR_STATE, "kmc_fmm_accept_event needs lattice mode");
@@ -770,6 +827,7 @@ int kmc_fmm_accept_event(kmc_handle h, int64_t event, double* dU_accepted) {
   if (g.dirichlet || h->rates_valid) {
     cudaStream_t s = h->stream;
     if (!h->rates_valid) {
+      if (h->copy_pending) CK(cudaStreamWaitEvent(s, h->ev_copied, 0));  // a proposal rewrites masks and dU
       r = refresh_peff(h);
       if (r) return r;
       kmc_propose_lattice(g, h->d, h->prec, s);
@@ -813,7 +871,7 @@ int kmc_fmm_accept_event(kmc_handle h, int64_t event, double* dU_accepted) {
 
 int kmc_step(kmc_handle h, const double* rates, double zeta, double xi, int64_t* event, double* dt, double* Q) {
   KMC_TRACE("kmc_step");
-  int r = guard(h);
+  int r = guard(h, false);
   if (r) return r;
   if (!(zeta > 0.0 && zeta <= 1.0 && xi > 0.0 && xi <= 1.0))
     return fail(h, KMC_ERR_ARG, "zeta and xi must lie in (0, 1]");

@@ -452,6 +452,39 @@ def test_mixed_form_fp32_output(small):
         k.kmc_fmm_propose_lattice(h64, dtype=np.float32)
 
 
+def test_asynchronous_outputs_follow_the_synchronous_path(small):
+    """kmc_fmm_propose_lattice(..., wait=False): the copies overlap kmc_step and the accept; after
+    kmc_fmm_outputs_wait (or the next proposal) the buffers hold what the synchronous FP32 call gives
+    on a second handle driven by the same uniforms, step by step; FP64 output refused."""
+    import torch
+    k = _k()
+    w, sites, q, st = small
+    ha = _init(w["E"], sites, q, w["L"], 12, precision="mixed", kT=w["kT"])
+    hs = _init(w["E"], sites, q, w["L"], 12, precision="mixed", kT=w["kT"])
+    u = workloads.uniforms(6, 17)
+    bufs = [(torch.empty((len(q), 6), dtype=torch.uint8, pin_memory=True),
+             torch.empty((len(q), 6), dtype=torch.float32, pin_memory=True)) for _ in range(2)]
+    ref = []
+    for s in range(6):
+        k.kmc_fmm_propose_lattice(ha, *bufs[s & 1], wait=False)
+        ev_a, dt_a, _ = k.kmc_step(ha, None, u[s, 0], u[s, 1])
+        k.kmc_fmm_accept_event(ha, ev_a)
+        m_s, d_s = k.kmc_fmm_propose_lattice(hs, dtype=np.float32)
+        ev_s, dt_s, _ = k.kmc_step(hs, None, u[s, 0], u[s, 1])
+        k.kmc_fmm_accept_event(hs, ev_s)
+        assert ev_a == ev_s and dt_a == dt_s
+        ref.append((m_s, d_s))
+        if s >= 1:  # the previous step's buffers are complete once this step's proposal returned
+            mp, dp = bufs[(s - 1) & 1]
+            assert np.array_equal(mp.numpy(), ref[s - 1][0])
+            np.testing.assert_array_equal(dp.numpy(), ref[s - 1][1])
+    k.kmc_fmm_outputs_wait(ha)
+    assert np.array_equal(bufs[1][0].numpy(), ref[5][0])
+    np.testing.assert_array_equal(bufs[1][1].numpy(), ref[5][1])
+    with pytest.raises(ValueError):
+        k.kmc_fmm_propose_lattice(ha, wait=False)
+
+
 def test_caller_owned_pinned_outputs(small):
     """Outputs written in place into caller-owned pinned host buffers equal the
     library-allocated ones; mismatched buffers are refused."""
