@@ -567,6 +567,12 @@ __device__ __forceinline__ void fixed_add(long long* a, double v) {
 // spilled too much of the L2P).
 enum { PROP_SUM = 0, PROP_FILL = 1, PROP_CACHED = 2 };
 
+// Outputs of a leaf recorded by the site phases for the write-out: (output
+// index, local site) pairs, nhop u + k for hop k of charge u (unmasked, target
+// in this leaf) and -1 - u for the old position of an own charge u.  A leaf with
+// more entries (a dense leaf) re-enumerates its hops instead.
+template <int NH> __host__ __device__ constexpr int wlist_cap() { return NH == KMC_NHOP ? 384 : 768; }
+
 // shared-memory layout of one leaf (byte count: propose_smem)
 template <typename T> struct LeafSmem {
   typedef typename cplx<T>::type C;
@@ -578,13 +584,14 @@ template <typename T> struct LeafSmem {
   int* nb_cnt;         // [27] charges per leaf
   int* nb_leaf;        // [27] leaf index
   int* pq;             // [28] first leaf of each source pass; pq[npass] = 27
-  int* misc;           // [4] number of passes, fixed-point exponent, number of sites (padded to 8 bytes)
+  int* misc;           // [4] number of passes, fixed-point exponent, number of sites, write-list entries
   T* phis;             // [W3] potential per local site (fixed-point near-field sums before the L2P)
   uint32_t* bits;      // [nbw] occupied sites
   uint32_t* need;      // [nbw] sites where a potential is needed
   int* woff;           // [nbw + 1] prefix of needed sites per word
   uint16_t* sites;     // [W3] needed local sites (x | y << 4 | z << 8), compacted
   double* isq;         // FP64 form: 1/sqrt(n) for the squared lattice distances n <= 3 (2W - 1)^2
+  int2* wl;            // [wlist_cap] recorded outputs (output index, local site)
   __device__ __forceinline__ LeafSmem(unsigned char* sm, const Geo& g, int chunk) {
     constexpr bool F32 = sizeof(T) == 4;
     const int W3 = g.W * g.W * g.W, nbw = (W3 + 31) / 32;
@@ -603,6 +610,7 @@ template <typename T> struct LeafSmem {
     woff = (int*)(need + nbw);
     sites = (uint16_t*)(woff + nbw + 1);
     isq = (double*)(((uintptr_t)(sites + ((W3 + 1) & ~1)) + 7) & ~(uintptr_t)7);
+    wl = (int2*)(isq + (F32 ? 0 : 3 * (2 * g.W - 1) * (2 * g.W - 1) + 1));
   }
 };
 
@@ -693,6 +701,7 @@ __device__ __forceinline__ void leaf_setup(const Geo& g, const Dev& d, const Lea
       }
       S.pq[++np] = 27;
       S.misc[0] = np;
+      S.misc[3] = 0;  // write-list entries
       {  // fixed-point exponent of the near-field sums: 2^ks * bound < 2^(bits - 2)
         const double bound = g.qmax * (double)max(total, 1);  // lattice units
         S.misc[1] = (F32 ? 30 : 62) - (ilogb(bound) + 1);
@@ -730,15 +739,20 @@ __device__ __forceinline__ int leaf_sites(const Geo& g, const Dev& d, const Leaf
   const int cnt_own = S.nb_cnt[0];
   const int64_t base_own = S.nb_base[0];
   V4 pv[2];
+  int32_t pu[2];
 #pragma unroll
   for (int i = 0; i < 2; i++) {
     const int e = warp + 4 * i;
     if (e < ne) {
       const int li = c_ent_leaf[hs][e];
-      if (lane < S.nb_cnt[li]) pv[i] = spos[S.nb_base[li] + lane];
+      if (lane < S.nb_cnt[li]) {
+        pv[i] = spos[S.nb_base[li] + lane];
+        pu[i] = d.uid[S.nb_base[li] + lane];
+      }
     }
   }
   // (1) occupancy bitmap of this leaf's sites (warp 0)
+  constexpr int wcap = wlist_cap<NH>();
   if (warp == 0)
     for (int j = lane; j < cnt_own; j += 32) {
       const V4 v = j < 32 ? pv[0] : spos[base_own + j];
@@ -747,6 +761,11 @@ __device__ __forceinline__ int leaf_sites(const Geo& g, const Dev& d, const Leaf
       if (KMC_IN(ls >= 0 && ls < W3, d.err)) {
         atomicOr(&S.bits[ls >> 5], 1u << (ls & 31));
         atomicOr(&S.need[ls >> 5], 1u << (ls & 31));
+        if (mode != PROP_FILL) {  // the old-position potential of this charge
+          const int32_t u = j < 32 ? pu[0] : d.uid[base_own + j];
+          const int w = atomicAdd(&S.misc[3], 1);
+          if (w < wcap) S.wl[w] = make_int2(-1 - u, ls);
+        }
       }
     }
   __syncthreads();
@@ -764,18 +783,18 @@ __device__ __forceinline__ int leaf_sites(const Geo& g, const Dev& d, const Leaf
     const int64_t mb = S.nb_base[li];
     const int cm = S.nb_cnt[li];
     for (int j = lane; j < cm; j += 32) {
-      const V4 v = (j < 32 && i < 2) ? (i == 0 ? pv[0] : pv[1]) : spos[mb + j];
+      const bool pre = j < 32 && i < 2;
+      const V4 v = pre ? (i == 0 ? pv[0] : pv[1]) : spos[mb + j];
+      const int32_t u = pre ? (i == 0 ? pu[0] : pu[1]) : d.uid[mb + j];
+      const bool uok = KMC_IN(u >= 0 && u < g.n, d.err);
       const int gx = lattice_coord(v.x, ih), gy = lattice_coord(v.y, ih), gz = lattice_coord(v.z, ih);
       for (uint32_t hb = hm; hb; hb &= hb - 1) {
         const int k = __ffs(hb) - 1;
         const int rx = gx + hop_c(k, 0), ry = gy + hop_c(k, 1), rz = gz + hop_c(k, 2);
         if (g.bc && (rx < 0 || rx >= E || ry < 0 || ry >= E || rz < 0 || rz >= E)) {
-          if (e == 0) {  // free space: a hop out of the box is not a move
-            const int32_t u = d.uid[mb + j];
-            if (KMC_IN(u >= 0 && u < g.n, d.err)) {
-              d.mask[(int64_t)nhop * u + k] = 0;
-              out_new[(int64_t)nhop * u + k] = qnan<T>();
-            }
+          if (e == 0 && uok) {  // free space: a hop out of the box is not a move
+            d.mask[(int64_t)nhop * u + k] = 0;
+            out_new[(int64_t)nhop * u + k] = qnan<T>();
           }
           continue;
         }
@@ -785,13 +804,16 @@ __device__ __forceinline__ int leaf_sites(const Geo& g, const Dev& d, const Leaf
         const int lt = ux + W * (uy + W * uz);
         if (!KMC_IN(lt >= 0 && lt < W3, d.err)) continue;
         if (S.bits[lt >> 5] & (1u << (lt & 31))) {
-          const int32_t u = d.uid[mb + j];
-          if (KMC_IN(u >= 0 && u < g.n, d.err)) {
+          if (uok) {
             d.mask[(int64_t)nhop * u + k] = 0;
             out_new[(int64_t)nhop * u + k] = qnan<T>();
           }
         } else {
           atomicOr(&S.need[lt >> 5], 1u << (lt & 31));
+          if (uok) {  // the write-out's entry for this hop
+            const int w = atomicAdd(&S.misc[3], 1);
+            if (w < wcap) S.wl[w] = make_int2(nhop * u + k, lt);
+          }
         }
       }
     }
@@ -981,14 +1003,18 @@ __device__ __forceinline__ void leaf_finish(const Geo& g, const Dev& d, const Le
     }
     return;
   }
-  // the write-out's inputs (first 32 charges of this warp's first two
-  // entries) are loaded now, so that their latency passes during the L2P
+  // the outputs were recorded by the site phases unless the leaf had more than
+  // wlist_cap of them; then its hops are enumerated again, and the inputs of
+  // that (first 32 charges of this warp's first two entries) are loaded now,
+  // so that their latency passes during the L2P
+  const int nw = S.misc[3];
+  const bool listed = nw <= wlist_cap<NH>();
   V4 wv[2];
   int32_t wu[2];
 #pragma unroll
   for (int i = 0; i < 2; i++) {
     const int e = warp + 4 * i;
-    if (e < ne) {
+    if (!listed && e < ne) {
       const int li = c_ent_leaf[hs][e];
       if (lane < S.nb_cnt[li]) {
         wu[i] = d.uid[S.nb_base[li] + lane];
@@ -1013,6 +1039,20 @@ __device__ __forceinline__ void leaf_finish(const Geo& g, const Dev& d, const Le
     }
   }
   __syncthreads();
+  if (listed) {  // (5) write-out from the recorded list
+    for (int i = tid; i < nw; i += 128) {
+      const int2 w = S.wl[i];
+      if (!KMC_IN(w.y >= 0 && w.y < W3, d.err)) continue;
+      const T v = S.phis[w.y];
+      if (w.x < 0) {
+        out_old[-1 - w.x] = v;
+      } else {
+        out_new[w.x] = v;
+        d.mask[w.x] = 1;
+      }
+    }
+    return;
+  }
 #pragma unroll 1
   for (int i = 0; i < (ne + 3) / 4; i++) {
     const int e = warp + 4 * i;
@@ -1107,8 +1147,9 @@ static size_t propose_smem(const Geo& g, int prec, int chunk) {
   const int nbw = (W3 + 31) / 32;
   const size_t srcb = prec == 0 ? NearField<double>::bytes(chunk) : nfmma::bytes(chunk);
   const size_t isqb = prec == 0 ? 8 + 8 * (size_t)(3 * (2 * g.W - 1) * (2 * g.W - 1) + 1) : 0;
+  const size_t wlb = 8 + 8 * (size_t)(g.nhop == KMC_MAXHOP ? wlist_cap<KMC_MAXHOP>() : wlist_cap<KMC_NHOP>());
   return srcb + 2 * ts * (size_t)g.P + 27 * 8 + 8 + (28 + 27 + 27 + 28 + 4) * 4 + ts * (size_t)W3 +
-         4 * (size_t)(3 * nbw + 1) + 2 * (size_t)((W3 + 1) & ~1) + isqb;
+         4 * (size_t)(3 * nbw + 1) + 2 * (size_t)((W3 + 1) & ~1) + isqb + wlb;
 }
 
 // sources are streamed in chunks of at least 960 (every neighbour leaf's
