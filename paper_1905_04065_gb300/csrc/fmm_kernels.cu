@@ -536,8 +536,14 @@ __global__ void k_m2l_top(const Geo g, const Dev d, const double2* Iagg) {
 //    (at most 2*128*64 + (S-2)*64*64 per term), so it is exact; it is then
 //    added into an int32 per diagonal (189 translations below 2^31 for
 //    p <= 16), and the diagonals are combined in FP64 with their weight
-//    2^(er(i) - 7 D).  S = 6: 43 significant bits per operand.
+//    2^(er(i) - 7 D).  S = 6: 43 significant bits per operand (FP64 form).
+//  * The mixed form keeps the first four slices (diagonals D <= 5, 10 of the
+//    21 slice products): 29 significant bits, an entry error of about K 2^-28
+//    of its row and column scales, below the FP32 arithmetic of that form's
+//    near field, L2P and dU.
 #define OZ_S 6
+#define OZ_S_MIXED 4
+static __host__ __device__ __forceinline__ int oz_slices(const Geo& g) { return g.prec == 1 ? OZ_S_MIXED : OZ_S; }
 #define OZ_MT 64
 #define OZ_NT 64
 #define OZ_KC 32
@@ -651,8 +657,9 @@ __global__ void __launch_bounds__(128) k_m2l_oz(const Geo g, const Dev d, int l,
                                                 const unsigned short* Bs, const unsigned long long* rowmax,
                                                 int ntile, long long* acc64) {
   extern __shared__ __align__(128) unsigned short oz_sm[];
-  unsigned short* sA = oz_sm;                      // [OZ_S][OZ_MT][OZ_LD]
-  unsigned short* sB = sA + OZ_S * OZ_MT * OZ_LD;  // [OZ_S][OZ_NT][OZ_LD]
+  const int S = oz_slices(g);                   // slices in use
+  unsigned short* sA = oz_sm;                   // [S][OZ_MT][OZ_LD]
+  unsigned short* sB = sA + S * OZ_MT * OZ_LD;  // [S][OZ_NT][OZ_LD]
   __shared__ int bcell[OZ_NT], scell[OZ_NT];
   const int nl = 1 << (l - 1), h2 = nl >> 1;
   const int o = blockIdx.y, ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
@@ -684,7 +691,7 @@ __global__ void __launch_bounds__(128) k_m2l_oz(const Geo g, const Dev d, int l,
   const unsigned short* Bl = Bs;
   double* Ps = (double*)(d.Psi + g.cell_off[l] * g.P);
 
-  for (int D = 2; D <= OZ_S + 1; D++) {
+  for (int D = 2; D <= S + 1; D++) {
     const int ns = D - 1;  // slices 0 .. ns - 1 of both operands meet on this diagonal
     int iacc[2][4][4];
 #pragma unroll
@@ -798,12 +805,12 @@ __global__ void k_oz_finish(const Geo g, const Dev d, int l, const long long* ac
     const int i = (int)(e % n2);
     const int er = oz_exp(rowmax[i]);
     double v = 0.0;
-    for (int D = 2; D <= OZ_S + 1; D++) v += ldexp((double)acc64[(int64_t)(D - 2) * ncell * n2 + e], er - 7 * D);
+    for (int D = 2; D <= oz_slices(g) + 1; D++) v += ldexp((double)acc64[(int64_t)(D - 2) * ncell * n2 + e], er - 7 * D);
     Ps[e] = v;
   }
 }
 
-static size_t oz_dyn_smem() { return (size_t)2 * OZ_S * OZ_MT * OZ_LD * sizeof(unsigned short); }
+static size_t oz_dyn_smem(int S) { return (size_t)2 * S * OZ_MT * OZ_LD * sizeof(unsigned short); }
 
 // interaction-list splits of level l: enough CTAs for three per SM (152 SMs)
 static int oz_splits(const Geo& g, int l) {
@@ -856,7 +863,7 @@ void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s) {
     As = (unsigned short*)(rowmax + nr);
     Bs = As + 343 * OZ_S * nr * nc;
     acc64 = (long long*)(Bs + (size_t)OZ_S * (size_t)g.ML * nc);
-    cudaFuncSetAttribute(k_m2l_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_dyn_smem());
+    cudaFuncSetAttribute(k_m2l_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_dyn_smem(OZ_S));
   }
   for (int l = 3; l <= g.L; l++) {
     k_m2l_rmat<<<343, 128, 0, s>>>(g, d, l, R);
@@ -873,7 +880,7 @@ void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s) {
       const int64_t ncell = (int64_t)1 << (3 * (l - 1));
       if (nsplit > 1) cudaMemsetAsync(acc64, 0, (size_t)OZ_S * ncell * n2 * sizeof(long long), s);
       dim3 grid((unsigned)(ntile * nsplit), 8, (unsigned)(nr / OZ_MT));
-      k_m2l_oz<<<grid, 128, oz_dyn_smem(), s>>>(g, d, l, As, Bs, rowmax, ntile, nsplit > 1 ? acc64 : nullptr);
+      k_m2l_oz<<<grid, 128, oz_dyn_smem(oz_slices(g)), s>>>(g, d, l, As, Bs, rowmax, ntile, nsplit > 1 ? acc64 : nullptr);
       if (nsplit > 1) k_oz_finish<<<(unsigned)((ncell * n2 + 255) / 256 < 4096 ? (ncell * n2 + 255) / 256 : 4096), 256, 0, s>>>(g, d, l, acc64, rowmax);
     } else {
       dim3 grid((unsigned)((h2 * h2 * h2 + G_NT - 1) / G_NT), 8, (unsigned)((n2 + G_MT - 1) / G_MT));

@@ -64,3 +64,25 @@ def test_small_tensor_m2l_matches_fp64_m2l(p):
     w, sites, q = workloads.workload("small")
     err = _check(_pair(w["E"], sites, q, w["L"], p), 1e-11, 1e-9)
     print(f"small p={p}: max |dU_tensor - dU_fp64| / max|dU| = {err:.2e}")
+
+
+def test_mixed_form_four_slice_m2l_matches_fp64_m2l():
+    """The mixed form keeps four slices (29 bits): an M2L entry error of about K 2^-28 ~ 7e-7 of its
+    row and column scales, ten times that in a dU relative to max|dU|, beside the form's own FP32
+    rounding of the near field, L2P and dU (~1e-6): 2e-5 with a margin of two."""
+    k = _k()
+    w, sites, q = workloads.workload("medium")
+    pos = workloads.site_positions(w["E"], sites)
+    out = {}
+    for m2l in ("tensor", "fp64"):
+        h = k.kmc_fmm_init(pos, q, float(w["E"]), w["L"], w["p"], precision="mixed", lattice_edge=w["E"],
+                           kT=0.1, m2l=m2l)
+        mask, dU = k.kmc_fmm_propose_lattice(h)
+        out[m2l] = (np.asarray(mask), np.asarray(dU))
+        k.kmc_fmm_destroy(h)
+    (mt, dt), (mf, df) = out["tensor"], out["fp64"]
+    assert np.array_equal(mt, mf)
+    ok = mf.astype(bool)
+    err = float(np.max(np.abs(dt[ok] - df[ok])) / np.max(np.abs(df[ok])))
+    print(f"medium, mixed form: max |dU_tensor - dU_fp64| / max|dU| = {err:.2e}")
+    assert err <= 2e-5, err
