@@ -60,8 +60,9 @@ enum kmc_precision {
   KMC_PREC_FP64 = 0, /* every step in FP64 */
   KMC_PREC_MIXED = 1 /* L2P, the near-field pair sums and the dU assembly (q (phi' - phi) less
                         the dipole and self-image terms) in FP32 with FP32 accumulation, the
-                        rates from an FP32 exponent kept in FP64 range; M2L, lattice sums, the
-                        accept updates of the expansions and the cumulative rate sums in FP64 */
+                        rates from an FP32 exponent kept in FP64 range; lattice sums, the
+                        accept updates of the expansions and the cumulative rate sums in FP64;
+                        the tensor-core M2L on four slices (29-bit operands, see kmc_m2l) */
 };
 
 enum kmc_mem { KMC_MEM_HOST = 0, KMC_MEM_DEVICE = 1 };
@@ -93,10 +94,12 @@ enum kmc_hops {
 };
 
 /* Arithmetic of the one-off M2L (Algorithm 2, translations grouped by vector
- * as dense real matrix products).  Both give FP64-accurate results. */
+ * as dense real matrix products).  Both give FP64-accurate results in the FP64
+ * form. */
 enum kmc_m2l {
   KMC_M2L_TENSOR = 0, /* bf16 tensor cores with exact integer slicing of the FP64 operands
-                         (six 7-bit slices, 21 slice products, exact per-diagonal sums);
+                         (six 7-bit slices, 21 slice products, exact per-diagonal sums; the
+                         mixed form four slices, 10 products, 29 significant bits);
                          FP64 CUDA cores when p > 16 */
   KMC_M2L_FP64 = 1    /* FP64 CUDA cores */
 };
