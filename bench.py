@@ -567,6 +567,13 @@ def run_gpu(args):
                    "beside kmc_step and kmc_fmm_accept_event) + kmc_step + kmc_fmm_accept_event, "
                    "kmc_fmm_outputs_wait after the last step"}
 
+    # one recompute (full FMM from the current charges, the drift control of kmc_fmm_recompute)
+    torch.cuda.synchronize()
+    t_r = time.perf_counter()
+    k.kmc_fmm_recompute(h)
+    torch.cuda.synchronize()
+    recompute_s = time.perf_counter() - t_r
+
     # FP64 form (context)
     fp64 = None
     if args.fp64_steps > 0:
@@ -681,7 +688,7 @@ def run_gpu(args):
         "propose_only_dU_evals_per_s": hops / (prop_ms * 1e-3),
         "phase_ms_per_step": {nm: phases[i] / args.steps for i, nm in enumerate(k.PHASES)},
         "ms_per_step_incl_call_overhead": float(np.mean(outer_ms)),
-        "init_s": init_s,
+        "init_s": init_s, "recompute_s": recompute_s,
         "fp64_form": fp64,
         "near_cache_form": ncache,
         "roofline": roof,

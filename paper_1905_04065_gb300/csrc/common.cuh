@@ -129,6 +129,7 @@ struct MoveRec {
 };
 
 // All device buffers owned by a handle (plain pointers, passed by value).
+#define KMC_DIP_BLOCKS 304  // blocks of the dipole reduction (two per SM)
 struct Dev {
   // particles, user order
   double* q;          // [n]
@@ -159,6 +160,7 @@ struct Dev {
                       // x + W (y + W z)), fixed point, lattice units
   double* isq;        // [KMC_ISQ_N] 1/sqrt(n), n the squared lattice distance (entry 0 = 0)
   double* dip;        // [3] dipole moment M
+  double* dip_part;   // [3 * KMC_DIP_BLOCKS] per-block partial sums of M
   float* fdip;        // [3] (4 pi / 3V) M in FP32 for the mixed rate assembly
   double* U;          // [1] total energy
   // FP32 copies used by the mixed form (NULL in the FP64 form)

@@ -198,8 +198,87 @@ __global__ void k_p2m(const Geo g, const Dev d) {
   for (int n = m; n <= g.p; n++) out[tri(n, m)] = acc[n];
 }
 
+// The same P2M with the degree P known at compile time: one warp per leaf, lane
+// m (m <= P) the column m.  The leaf's charges are loaded 32 at a time and
+// broadcast by shuffles; per charge the lane forms the sectoral value
+// R_m^m = prod_{j <= m} -(x + i y) / (2j) and the column's recurrence up to
+// degree P (steps below m or beyond P predicated off), all P + 1 accumulators
+// in registers.  T: the arithmetic of the recurrence and the sums (FP64; FP32
+// in the mixed form, whose M2L keeps 29 bits); the expansion is stored in FP64.
+template <int P, typename T>
+__global__ void __launch_bounds__(128) k_p2m_w(const Geo g, const Dev d) {
+  const int lane = threadIdx.x & 31, m = lane;
+  const int64_t leaf = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (leaf >= g.ML) return;  // whole warps
+  const int cx = (int)(leaf % g.nL), cy = (int)((leaf / g.nL) % g.nL), cz = (int)(leaf / ((int64_t)g.nL * g.nL));
+  const double c0 = (cx + 0.5) * g.w, c1 = (cy + 0.5) * g.w, c2 = (cz + 0.5) * g.w;
+  T ax[P + 1], ay[P + 1], ci[P + 1];
+#pragma unroll
+  for (int n = 0; n <= P; n++) {
+    ax[n] = ay[n] = (T)0;
+    ci[n] = n > m ? (T)(1.0 / ((double)(n - m) * (double)(n + m))) : (T)0;
+  }
+  const int c = d.cnt[leaf];
+  const double4_32a* sp = d.spos64 + leaf * g.cap;
+  for (int j0 = 0; j0 < c; j0 += 32) {
+    double4_32a v = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    if (j0 + lane < c) v = sp[j0 + lane];
+    const int nj = min(32, c - j0);
+    for (int jj = 0; jj < nj; jj++) {
+      const T x = (T)(__shfl_sync(0xffffffffu, v.x, jj) - c0), y = (T)(__shfl_sync(0xffffffffu, v.y, jj) - c1);
+      const T z = (T)(__shfl_sync(0xffffffffu, v.z, jj) - c2), q = (T)__shfl_sync(0xffffffffu, v.w, jj);
+      T mx = (T)1, my = (T)0;
+#pragma unroll
+      for (int j = 1; j <= P; j++)
+        if (j <= m) {
+          const T sc = (T)(-0.5 / j);
+          const T tx = sc * (x * mx - y * my), ty = sc * (x * my + y * mx);
+          mx = tx;
+          my = ty;
+        }
+      const T r2 = x * x + y * y + z * z;
+      T a1x = mx, a1y = my, a2x = (T)0, a2y = (T)0;
+#pragma unroll
+      for (int n = 0; n <= P; n++) {
+        if (n == m) {
+          ax[n] += q * a1x;
+          ay[n] += q * a1y;
+        } else if (n > m) {
+          const T zz = (T)(2 * n - 1) * z;
+          const T vx = (zz * a1x - r2 * a2x) * ci[n], vy = (zz * a1y - r2 * a2y) * ci[n];
+          ax[n] += q * vx;
+          ay[n] += q * vy;
+          a2x = a1x;
+          a2y = a1y;
+          a1x = vx;
+          a1y = vy;
+        }
+      }
+    }
+  }
+  if (m > P) return;
+  double2* out = d.Mt + (g.cell_off[g.L] + leaf) * g.P;
+#pragma unroll
+  for (int n = 0; n <= P; n++)
+    if (n >= m) out[tri(n, m)] = make_double2((double)ax[n], (double)ay[n]);
+}
+
+template <typename T>
+static bool p2m_fixed(const Geo& g, const Dev& d, cudaStream_t s) {
+  const unsigned nb = (unsigned)((g.ML * 32 + 127) / 128);
+  switch (g.p) {
+#define KMC_P2M_CASE(P) \
+  case P: k_p2m_w<P, T><<<nb, 128, 0, s>>>(g, d); return true;
+    KMC_P2M_CASE(4) KMC_P2M_CASE(6) KMC_P2M_CASE(8) KMC_P2M_CASE(10) KMC_P2M_CASE(12) KMC_P2M_CASE(14)
+    KMC_P2M_CASE(16) KMC_P2M_CASE(18) KMC_P2M_CASE(20) KMC_P2M_CASE(22) KMC_P2M_CASE(24)
+#undef KMC_P2M_CASE
+    default: return false;
+  }
+}
+
 void fmm_p2m(const Geo& g, const Dev& d, cudaStream_t s) {
-  int64_t nt = g.ML * (g.p + 1);
+  if (g.prec == 1 ? p2m_fixed<float>(g, d, s) : p2m_fixed<double>(g, d, s)) return;
+  int64_t nt = g.ML * (g.p + 1);  // other degrees: one thread per (leaf, column)
   k_p2m<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(g, d);
 }
 
@@ -280,11 +359,83 @@ __global__ void k_m2m(const Geo g, const Dev d, int l) {
   d.Mt[(g.cell_off[l] + cell) * g.P + ci] = acc;
 }
 
+// The same M2M with the eight children's expansions and the child-offset
+// tables staged in shared memory in full (n, m) order (entry n^2 + n + m, m < 0
+// by conjugate symmetry): one CTA per parent cell, one output coefficient per
+// thread, no global loads in the sums.  T: the arithmetic (FP64; FP32 in the
+// mixed form, whose M2L keeps 29 bits); the expansion is stored in FP64.
+template <typename T>
+__global__ void __launch_bounds__(128) k_m2m_blk(const Geo g, const Dev d, int l) {
+  typedef typename cplx<T>::type C;
+  extern __shared__ __align__(16) unsigned char m2m_sm[];
+  const int F = (g.p + 1) * (g.p + 1);
+  C* Ms = (C*)m2m_sm;  // [8][F] children
+  C* Rs = Ms + 8 * F;  // [8][F] child-offset tables
+  const int nl = 1 << (l - 1), nc = 2 * nl;
+  const int64_t cell = blockIdx.x;
+  const int px = (int)(cell % nl), py = (int)((cell / nl) % nl), pz = (int)(cell / ((int64_t)nl * nl));
+  for (int t = threadIdx.x; t < 16 * F; t += blockDim.x) {
+    const int tb = t / F, u = t - tb * F;
+    const int n = (int)sqrtf((float)u + 0.5f), m = u - n * n - n;  // exact: sqrt(n^2 - 1/2) < n <= sqrt(n^2 + 1/2)
+    const int o = tb & 7;
+    double2 v;
+    if (tb < 8) {
+      const int cx = 2 * px + (o & 1), cy = 2 * py + ((o >> 1) & 1), cz = 2 * pz + ((o >> 2) & 1);
+      const int64_t child = cx + (int64_t)nc * (cy + (int64_t)nc * cz);
+      v = tab_get(d.Mt + (g.cell_off[l + 1] + child) * g.P, n, m);
+    } else {
+      v = tab_get(d.Rch + ((int64_t)(l + 1) * 8 + o) * g.P, n, m);
+    }
+    C w;
+    w.x = (T)v.x;
+    w.y = (T)v.y;
+    (tb < 8 ? Ms : Rs)[o * F + u] = w;
+  }
+  __syncthreads();
+  for (int ci = threadIdx.x; ci < g.P; ci += blockDim.x) {
+    int n = 0;
+    while (tri(n + 1, 0) <= ci) n++;
+    const int m = ci - tri(n, 0);
+    T ax = 0, ay = 0;
+    for (int o = 0; o < 8; o++) {
+      const C* Mo = Ms + o * F;
+      const C* Ro = Rs + o * F;
+      for (int k = 0; k <= n; k++) {
+        const int j = n - k;
+        const int lo = max(-k, m - j), hi = min(k, m + j);
+        const C* a = Mo + k * k + k;
+        const C* b = Ro + j * j + j + m;
+        for (int ll = lo; ll <= hi; ll++) {
+          const C u = a[ll], v = b[-ll];
+          ax += u.x * v.x - u.y * v.y;
+          ay += u.x * v.y + u.y * v.x;
+        }
+      }
+    }
+    d.Mt[(g.cell_off[l] + cell) * g.P + ci] = make_double2((double)ax, (double)ay);
+  }
+}
+
+static size_t fmm_m2m_smem(int p, int prec) {
+  return (size_t)16 * (p + 1) * (p + 1) * (prec == 1 ? sizeof(float2) : sizeof(double2));
+}
+
 void fmm_m2m(const Geo& g, const Dev& d, cudaStream_t s) {
+  const size_t sm = fmm_m2m_smem(g.p, g.prec);
+  const bool staged = sm <= 200 * 1024;
+  if (staged) {
+    if (g.prec == 1) cudaFuncSetAttribute(k_m2m_blk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    else cudaFuncSetAttribute(k_m2m_blk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  }
   for (int l = g.L - 1; l >= 1; l--) {
     int64_t ncl = (int64_t)1 << (3 * (l - 1));
-    int64_t nt = ncl * g.P;
-    k_m2m<<<(unsigned)((nt + 127) / 128), 128, 8 * g.P * sizeof(double2), s>>>(g, d, l);
+    if (staged) {
+      if (g.prec == 1) k_m2m_blk<float><<<(unsigned)ncl, 128, sm, s>>>(g, d, l);
+      else k_m2m_blk<double><<<(unsigned)ncl, 128, sm, s>>>(g, d, l);
+    } else {
+      int64_t nt = ncl * g.P;
+      k_m2m<<<(unsigned)((nt + 127) / 128), 128, 8 * g.P * sizeof(double2), s>>>(g, d, l);
+    }
   }
 }
 
@@ -1046,12 +1197,14 @@ void fmm_far_field(const Geo& g, const Dev& d, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ dipole, self term
-// M = sum q r over user-order positions (fixed-order block reduction)
-__global__ void k_dipole(const Geo g, const Dev d) {
-  __shared__ double sh[3][512];
+// M = sum q r over user-order positions: KMC_DIP_BLOCKS blocks each sum a
+// fixed strided subset (tree within the block), then one block adds the
+// partial sums in block order -- a fixed order, so M is deterministic
+__global__ void __launch_bounds__(256) k_dipole_part(const Geo g, const Dev d) {
+  __shared__ double sh[3][256];
   double a0 = 0, a1 = 0, a2 = 0;
-  for (int64_t i = threadIdx.x; i < g.n; i += blockDim.x) {
-    double q = d.q[i];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double q = d.q[i];
     a0 += q * d.pos[3 * i];
     a1 += q * d.pos[3 * i + 1];
     a2 += q * d.pos[3 * i + 2];
@@ -1065,10 +1218,15 @@ __global__ void k_dipole(const Geo g, const Dev d) {
       for (int c = 0; c < 3; c++) sh[c][threadIdx.x] += sh[c][threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x < 3) {
-    d.dip[threadIdx.x] = sh[threadIdx.x][0];
-    d.fdip[threadIdx.x] = (float)(g.dipc * sh[threadIdx.x][0]);
-  }
+  if (threadIdx.x < 3) d.dip_part[3 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_dipole(const Geo g, const Dev d) {
+  if (threadIdx.x >= 3) return;
+  double a = 0.0;
+  for (int b = 0; b < KMC_DIP_BLOCKS; b++) a += d.dip_part[3 * b + threadIdx.x];
+  d.dip[threadIdx.x] = a;
+  d.fdip[threadIdx.x] = (float)(g.dipc * a);
 }
 
 // C(d) = sum_{nu in V} 1/|d - a nu| - sum_{nu in V, nu != 0} 1/|a nu| + g(d) - g(0) + 2 pi |d|^2 / (3V)
@@ -1158,7 +1316,8 @@ void fmm_dirichlet_tables(const Geo& g, const Dev& d, cudaStream_t s) {
 }
 
 void fmm_self_and_dipole(const Geo& g, const Dev& d, cudaStream_t s) {
-  k_dipole<<<1, 512, 0, s>>>(g, d);
+  k_dipole_part<<<KMC_DIP_BLOCKS, 256, 0, s>>>(g, d);
+  k_dipole<<<1, 32, 0, s>>>(g, d);
   k_selfcorr<<<1, 32, 0, s>>>(g, d);
 }
 

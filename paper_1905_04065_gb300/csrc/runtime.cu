@@ -485,6 +485,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
     ALLOC(d.dirB, sizeof(double) * (g.E / 2) * g.nhop);
   }
   ALLOC(d.dip, sizeof(double) * 3);
+  ALLOC(d.dip_part, sizeof(double) * 3 * KMC_DIP_BLOCKS);
   ALLOC(d.fdip, sizeof(float) * 4);
   ALLOC(d.U, sizeof(double));
   if (h->prec == 1) {
