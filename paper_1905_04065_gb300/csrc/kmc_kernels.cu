@@ -1236,17 +1236,48 @@ __device__ __forceinline__ double widen_nonneg(float v) {
   return __longlong_as_double((long long)bits);
 }
 
-// inclusive prefix sum over a shared array of n <= blockDim values
-// (Hillis-Steele, fixed order); every thread of the block must call it
-__device__ __forceinline__ void block_scan(double* v, int n) {
+// Inclusive scan of one value per thread over the first n threads of the block
+// (n a power of two, 32..1024; every thread of the block calls it, the others'
+// results are meaningless): Kogge-Stone by shuffles within each warp, then over
+// the warp totals; the last lane of warp w takes the warp-total scan's own
+// entry.  The total (element n - 1) is then the sum over aligned blocks level
+// by level -- the same additions, bit for bit, as block_total and as the last
+// element of a Hillis-Steele scan -- with two barriers in all.
+// wt: 32 doubles of shared memory.
+__device__ __forceinline__ double block_scan_shfl(double x, int n, double* wt) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = n >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31 && w < nw) wt[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    double t = lane < nw ? wt[lane] : 0.0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o && o < nw) t += y;
+    }
+    if (lane < nw) wt[lane] = t;
+  }
+  __syncthreads();
+  if (w >= nw) return 0.0;
+  if (lane == 31) return wt[w];
+  return w > 0 ? x + wt[w - 1] : x;
+}
+
+// the block total of one value per thread (blockDim.x == n, a power of two) as
+// adjacent aligned blocks added level by level (v: n doubles of shared memory)
+__device__ __forceinline__ double block_total(double* v, int n) {
   for (int off = 1; off < n; off <<= 1) {
-    double x = 0.0;
-    if (threadIdx.x < n) x = v[threadIdx.x] + (threadIdx.x >= off ? v[threadIdx.x - off] : 0.0);
-    __syncthreads();
-    if (threadIdx.x < n) v[threadIdx.x] = x;
+    if ((threadIdx.x & (2 * off - 1)) == 0) v[threadIdx.x] += v[threadIdx.x + off];
     __syncthreads();
   }
+  return v[0];
 }
+
 
 // rate = m 2^-e for m in (0.5, 1] and 0 <= e <= 1021, formed by moving the
 // IEEE-754 fields (exact; no FP64 arithmetic)
@@ -1258,9 +1289,9 @@ __device__ __forceinline__ double scale_pow2(float m, int e) {
 
 // One thread per particle i and its 6 events j = 6 i + k: phi_new and mask
 // read and dU and rate written as 8- and 16-byte vectors.  The per-particle
-// sum of the 6 rates is sequential in k and the block sum is the last element
-// of the same fixed-order scan the selection walk takes, so both see the same
-// cumulative sums.
+// sum of the 6 rates is sequential in k and the block sum equals the last
+// element of the same fixed-order scan the selection walk takes, so both see
+// the same cumulative sums.
 // MIXED: the assembly in FP32 (the dU tolerance of the mixed form is far
 // above FP32 rounding); rate = exp(-x) = 2^-y, y = x log2(e) = n + f, with
 // 2^-f from the MUFU ex2 and 2^-n put into the FP64 exponent, so rates keep
@@ -1384,8 +1415,11 @@ __device__ __forceinline__ void finalize_blk(const Geo& g, const Dev& d, const i
   }
   ts[threadIdx.x] = tsum;
   __syncthreads();
-  block_scan(ts, FIN_THREADS);
-  if (threadIdx.x == 0) d.bsum[blk] = ts[FIN_THREADS - 1];
+  // the block sum as the selection's scan forms its last element (the same additions, bit for
+  // bit), with a seventh of a scan's FP64 adds
+  static_assert((FIN_THREADS & (FIN_THREADS - 1)) == 0, "aligned pairs need a power of two");
+  const double tot = block_total(ts, FIN_THREADS);
+  if (threadIdx.x == 0) d.bsum[blk] = tot;
 }
 
 template <bool MIXED, int NH>
@@ -1408,8 +1442,8 @@ __global__ void __launch_bounds__(FIN_THREADS) k_rate_bsum(const Geo g, const De
     for (int k = 0; k < g.nhop; k++) tsum += d.rate[(int64_t)g.nhop * i + k];
   ts[threadIdx.x] = tsum;
   __syncthreads();
-  block_scan(ts, FIN_THREADS);
-  if (threadIdx.x == 0) d.bsum[blockIdx.x] = ts[FIN_THREADS - 1];
+  const double tot = block_total(ts, FIN_THREADS);
+  if (threadIdx.x == 0) d.bsum[blockIdx.x] = tot;
 }
 
 void kmc_finalize_rates(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
@@ -1432,6 +1466,7 @@ void kmc_finalize_rates(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
 __device__ __forceinline__ void select_one(const Geo& g, const Dev& d, const int use_counter) {
   __shared__ double cs[SEL_THREADS];
   __shared__ double ts[FIN_THREADS];
+  __shared__ double wt[32];
   __shared__ double sh_target, sh_prev;
   __shared__ int sh_t;
   __shared__ int64_t sh_blk;
@@ -1442,10 +1477,9 @@ __device__ __forceinline__ void select_one(const Geo& g, const Dev& d, const int
   const double zeta = uni[0], xi = uni[1];
   double c = 0.0;
   for (int64_t b = tid * per; b < min(nb, (tid + 1) * per); b++) c += d.bsum[b];
-  cs[tid] = c;
   if (tid == 0) { sh_t = -1; sh_blk = -1; }
+  cs[tid] = block_scan_shfl(c, SEL_THREADS, wt);
   __syncthreads();
-  block_scan(cs, SEL_THREADS);
   const double Q = cs[SEL_THREADS - 1];
   const double target = Q * zeta;
   if (Q > 0.0) {
@@ -1483,16 +1517,16 @@ __device__ __forceinline__ void select_one(const Geo& g, const Dev& d, const int
     if (tid == 0) *d.event = -1;
     return;
   }
+  double t = 0.0;
   if (tid < FIN_THREADS) {
     int64_t i = blk * FIN_THREADS + tid;
-    double t = 0.0;
     if (i < g.n)
       for (int k = 0; k < g.nhop; k++) t += d.rate[(int64_t)g.nhop * i + k];
-    ts[tid] = t;
   }
   if (tid == 0) sh_t = -1;
+  t = block_scan_shfl(t, FIN_THREADS, wt);
+  if (tid < FIN_THREADS) ts[tid] = t;
   __syncthreads();
-  block_scan(ts, FIN_THREADS);
   const double res = sh_target;
   if (tid < FIN_THREADS) {
     double prev = tid ? ts[tid - 1] : 0.0;
