@@ -215,7 +215,7 @@ __device__ __forceinline__ void mma(uint32_t a0, uint32_t a1, uint32_t b, float&
 template <int NT, bool GUARD>
 __device__ __forceinline__ void run(const uint32_t* R, int j0, int j1, const uint32_t (&a)[TMAX][2],
                                     float2 (&acc)[TMAX][2], int g, int c, uint32_t bc) {
-#pragma unroll 1
+#pragma unroll 2  // 1: 1.6% slower on the 1M-charge workload, 4: 2.4% slower
   for (int j = j0; j < j1; j++) {
     const uint32_t* T = R + 32 * j;
     const uint32_t bw = T[4 * g + c];
