@@ -146,9 +146,9 @@ def pair_count(E: int, L: int, sites: np.ndarray, nhop: int = 6, bc: str = "peri
 
 # DRAM bytes (read + write) of one summing propose launch per leaf, from the ncu capture of the
 # 128^3 tile case (4096 leaves of 8^3 sites, 32 charges each, 6 hops, mixed precision:
-# 7.16 MB read, 63 kB written).  Valid for workloads with the same
+# 6.16 MB read, 1 kB written).  Valid for workloads with the same
 # leaf shape (tile, large); scaled by the number of leaves.
-PROPOSE_DRAM_BYTES_PER_LEAF = (7.158016e6 + 62.72e3) / 4096
+PROPOSE_DRAM_BYTES_PER_LEAF = (6.16448e6 + 1.024e3) / 4096
 TRAFFIC_WORKLOADS = ("tile", "large")
 
 
