@@ -843,18 +843,16 @@ __device__ __forceinline__ int leaf_sites(const Geo& g, const Dev& d, const Leaf
     }
   }
   __syncthreads();
-  for (int w2 = tid; w2 < nbw; w2 += 128) {
-    uint32_t m = S.need[w2];
-    int o = S.woff[w2];
-    while (m) {
-      const int b = __ffs(m) - 1;
-      const int l = 32 * w2 + b;
+  // one thread per local site: a needed site's place is its word's offset plus
+  // the needed sites below it in the word
+  for (int l = tid; l < W3; l += 128) {
+    const uint32_t m = S.need[l >> 5], bit = 1u << (l & 31);
+    if (m & bit) {
+      const int o = S.woff[l >> 5] + __popc(m & (bit - 1u));
       // l = x + W (y + W z) by reciprocal multiplication: floor(l rW / 2^16)
       // = floor(l / W) for l < 2^16 / W (W <= 12, l < 1728)
       const int q1 = (l * rW) >> 16, z = (q1 * rW) >> 16;
       if (KMC_IN(o < W3, d.err)) S.sites[o] = (uint16_t)((l - q1 * W) | ((q1 - z * W) << 4) | (z << 8));
-      o++;
-      m &= m - 1;
     }
   }
   __syncthreads();
