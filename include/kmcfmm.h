@@ -97,11 +97,14 @@ enum kmc_hops {
  * as dense real matrix products).  Both give FP64-accurate results in the FP64
  * form. */
 enum kmc_m2l {
-  KMC_M2L_TENSOR = 0, /* bf16 tensor cores with exact integer slicing of the FP64 operands
-                         (six 7-bit slices, 21 slice products, exact per-diagonal sums; the
-                         mixed form four slices, 10 products, 29 significant bits);
-                         FP64 CUDA cores when p > 16 */
-  KMC_M2L_FP64 = 1    /* FP64 CUDA cores */
+  KMC_M2L_TENSOR = 0,      /* bf16 tensor cores with exact integer slicing of the FP64 operands
+                              (six 7-bit slices, 21 slice products, exact per-diagonal sums; the
+                              mixed form four slices, 10 products, 29 significant bits), on the
+                              fifth-generation MMA (tcgen05, TMEM accumulators, TMA staging) for
+                              p <= 14, the mma.sync form for p = 15, 16; FP64 CUDA cores when p > 16 */
+  KMC_M2L_FP64 = 1,        /* FP64 CUDA cores */
+  KMC_M2L_TENSOR_SYNC = 2  /* the same slicing on the warp-level mma.sync form (p <= 16, else FP64):
+                              bit for bit the result of KMC_M2L_TENSOR, kept as its cross-check */
 };
 
 typedef struct kmc_opts {
@@ -374,6 +377,23 @@ void kmc_batch_destroy(kmc_batch_handle b);
  * Allocates a 4-byte flag for the duration of the call; no handle needed.
  */
 int kmc_check_bounded_wait(int device, double limit_seconds);
+
+/*
+ * Diagnostic with no counterpart in the paper: four fifth-generation
+ * tensor-core MMAs (tcgen05.mma kind::f16, M = 128, N = 192, K = 4 x 16, bf16 x
+ * bf16 -> FP32 in tensor memory) of small integer operands, staged in shared
+ * memory exactly as the tensor-core M2L stages its operands (cp.async pieces
+ * for A, one 2D TMA box of a contiguous block for B, 128-byte-swizzled K-major
+ * tiles, the K step advanced inside the swizzle atom), read back with tcgen05.ld
+ * and compared on the host with the exact integer product.  Returns 0 when
+ * every entry agrees, 1 on a mismatch, -KMC_ERR_TIMEOUT when a bounded wait
+ * gave up, -KMC_ERR_CUDA / -KMC_ERR_OOM when the device, the driver's
+ * tensor-map encoder or an allocation is unavailable.  out: NULL, or a host
+ * array of 128 * 192 floats that receives the product as read from tensor
+ * memory (row-major, row = M index).  Allocates and frees about 100 kB of
+ * device memory; no handle needed.
+ */
+int kmc_check_tensor_mma(int device, float* out);
 
 /* Message of the last error on this handle (static string if h is NULL). */
 const char* kmc_last_error(kmc_handle h);

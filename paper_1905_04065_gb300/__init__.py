@@ -35,6 +35,7 @@ KMC_MEM_HOST = 0
 KMC_MEM_DEVICE = 1
 KMC_M2L_TENSOR = 0
 KMC_M2L_FP64 = 1
+KMC_M2L_TENSOR_SYNC = 2
 KMC_HOPS_6 = 0
 KMC_HOPS_14 = 1
 KMC_BC_PERIODIC = 0
@@ -47,6 +48,7 @@ EXPORTS = [
     "kmc_fmm_accept", "kmc_fmm_accept_event", "kmc_step", "kmc_run", "kmc_run_profiled", "kmc_fmm_recompute",
     "kmc_fmm_leaf_index", "kmc_fmm_positions", "kmc_last_error", "kmc_fmm_destroy", "kmc_select_static",
     "kmc_check_bounded_wait",
+    "kmc_check_tensor_mma",
     "kmc_batch_create", "kmc_batch_run", "kmc_batch_run_timed", "kmc_batch_set_chunk", "kmc_batch_info",
     "kmc_batch_propose_timed", "kmc_batch_last_error", "kmc_batch_destroy",
 ]
@@ -109,6 +111,7 @@ def load_library(path: str | None = None):
             "kmc_fmm_destroy": (None, [P]),
             "kmc_select_static": (I, [P, I64, D, D, P, P, P, P]),
             "kmc_check_bounded_wait": (I, [I, D]),
+            "kmc_check_tensor_mma": (I, [I, ctypes.c_void_p]),
             "kmc_batch_create": (I, [P, I, P]),
             "kmc_batch_run": (I, [P, I, P, P, P]),
             "kmc_batch_run_timed": (I, [P, I, P, P, P, P]),
@@ -193,7 +196,8 @@ def kmc_fmm_init(positions, charges, box: float, levels: int, order: int, precis
                  leaf_capacity: int = 0, m2l: str = "tensor", hops: int = 6, bc: str = "periodic",
                  field_z: float = 0.0, near_cache: bool = False) -> Handle:
     """Create a handle and run the one-off full FMM.  precision: 'fp64' or 'mixed';
-    m2l: 'tensor' (bf16 tensor cores with exact slicing) or 'fp64' (FP64 CUDA cores);
+    m2l: 'tensor' (bf16 tensor cores with exact slicing, tcgen05 MMA), 'tensor_sync' (the same slicing on
+    the mma.sync form, bit for bit the same result) or 'fp64' (FP64 CUDA cores);
     hops: the lattice hop set, 6 (faces) or 14 (faces and body diagonals);
     bc: 'periodic' (neutral systems), 'free' (free space) or 'dirichlet' (grounded walls at z = 0 and
     z = box/2, lattice mode, every charge below box/2, applied field field_z along z);
@@ -208,7 +212,7 @@ def kmc_fmm_init(positions, charges, box: float, levels: int, order: int, precis
     opts.kT = float(kT)
     opts.device = int(device)
     opts.leaf_capacity = int(leaf_capacity)
-    opts.m2l = {"tensor": KMC_M2L_TENSOR, "fp64": KMC_M2L_FP64}[m2l]
+    opts.m2l = {"tensor": KMC_M2L_TENSOR, "fp64": KMC_M2L_FP64, "tensor_sync": KMC_M2L_TENSOR_SYNC}[m2l]
     opts.hops = {6: KMC_HOPS_6, 14: KMC_HOPS_14}[int(hops)]
     opts.bc = {"periodic": KMC_BC_PERIODIC, "free": KMC_BC_FREE, "dirichlet": KMC_BC_DIRICHLET_Z}[bc]
     opts.field_z = float(field_z)
@@ -564,4 +568,15 @@ def kmc_check_bounded_wait(device: int = 0, limit_seconds: float = 0.05) -> int:
     """Status of the bounded-wait diagnostic: KMC_ERR_TIMEOUT (6) when the
     device-side wait gave up and returned as designed."""
     return int(load_library().kmc_check_bounded_wait(int(device), float(limit_seconds)))
+
+
+def kmc_check_tensor_mma(device: int = 0, out=None) -> int:
+    """One tcgen05 MMA of small integer operands, staged as the tensor-core M2L stages them, against
+    the exact product: 0 agreement, 1 mismatch, negative: unavailable or timed out.  out: None or a
+    float32 array of 128 x 192 that receives the product read back from tensor memory."""
+    ptr = None
+    if out is not None:
+        assert out.dtype == np.float32 and out.size == 128 * 192 and out.flags["C_CONTIGUOUS"]
+        ptr = out.ctypes.data
+    return int(load_library().kmc_check_tensor_mma(int(device), ptr))
 

@@ -100,7 +100,8 @@ struct Geo {
   double inv_a;           // 1 / a
   int prec;               // 0 = FP64 form, 1 = mixed form
   double qmax;            // largest |charge|
-  int m2l;                // M2L arithmetic: 0 = bf16 tensor-core slicing (p <= 16, else FP64), 1 = FP64
+  int m2l;                // M2L arithmetic (kmc_m2l): 0 tensor cores (tcgen05, p <= 14; mma.sync to p = 16; else FP64),
+                          // 1 FP64, 2 the mma.sync tensor-core form
   int nhop;               // lattice hops per charge: 6 (faces) or 14 (faces and body diagonals)
   int bc;                 // boundary conditions: 0 periodic (tinfoil), 1 free space
   double dipc;            // 4 pi / (3 V): the dipole (surface) term's factor; 0 in free space
@@ -240,6 +241,82 @@ __device__ __forceinline__ bool kmc_in(bool ok, int* err) {
 // 1/((n-m)(n+m)) for n > m, table built on the host into constant memory by each TU
 #define KMC_NTRI (((2 * KMC_MAXP + 1) * (2 * KMC_MAXP + 2)) / 2)
 
+// ---- bulk asynchronous copies (global -> shared) completed on an mbarrier
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// bytes: a multiple of 16; both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  uint64_t gsrc;
+  asm("cvta.to.global.u64 %0, %1;" : "=l"(gsrc) : "l"(src));
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// potentially blocking test: the thread is suspended until the phase completes
+// or a time limit of the hardware runs out, so a waiting warp issues few
+// instructions
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// wait for phase `parity` of the barrier, at most ~limit_ns; false on timeout
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_test(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try(bar, parity)) {
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+#define KMC_WAIT_NS 1000000000ull  // one second
+
+// ---------------------------------------------------------------- M2L slicing (Algorithm 2 on the tensor cores)
+// slice counts, tile paddings and the scaling exponent shared by the slicing
+// kernels and both tensor-core M2L kernels
+#define OZ_S 6
+#define OZ_S_MIXED 4
+static __host__ __device__ __forceinline__ int oz_slices(const Geo& g) { return g.prec == 1 ? OZ_S_MIXED : OZ_S; }
+#define OZ_MT 64
+#define OZ_NT 64
+#define OZ_KC 32
+#define OZ_LD (OZ_KC + 8)  // shared row stride (bf16): 80 B rows, conflict-free ldmatrix
+#define OZ_MAXP 16
+
+static __host__ __device__ __forceinline__ int oz_rows(int n2) { return (n2 + OZ_MT - 1) / OZ_MT * OZ_MT; }
+static __host__ __device__ __forceinline__ int oz_cols(int n2) { return (n2 + OZ_KC - 1) / OZ_KC * OZ_KC; }
+
+// 2^e with e the smallest integer such that |x| < 2^e for every |x| <= m (0 if m = 0)
+__device__ __forceinline__ int oz_exp(unsigned long long mbits) {
+  const double m = __longlong_as_double((long long)mbits);
+  return m > 0.0 ? ilogb(m) + 1 : 0;
+}
+
 // ---------------------------------------------------------------- launch wrappers
 // (defined in the .cu files, called by the host runtime)
 void fmm_upload_constants(int p);
@@ -250,6 +327,13 @@ void fmm_itab(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_child_tables(const Geo& g, const Dev& d, cudaStream_t s);  // child and ancestor offset tables
 size_t fmm_m2l_scratch_bytes(const Geo& g);
 void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s);
+bool fmm_m2l_tc_ok(const Geo& g);           // the tcgen05 M2L applies (KMC_M2L_TENSOR, p <= 14)
+int fmm_m2l_tc_rows(const Geo& g);           // its MMA N (rows of its A-slice layout), 0 if p > 14
+int fmm_m2l_tc_kchunks(const Geo& g);        // its K chunks of 64 values
+// level l's M2L from the slices in the tcgen05 layouts (As: k_oz_aslice_tc, Bp:
+// k_oz_bslice_tc) into acc64 (zeroed; k_oz_finish converts); false: not launched
+bool fmm_m2l_tc(const Geo& g, const Dev& d, int l, const unsigned short* As, const unsigned short* Bp,
+                long long* acc64, cudaStream_t s);
 void fmm_dirichlet_tables(const Geo& g, const Dev& d, cudaStream_t s);
 void kmc_mirror_move(const Geo& g, const Dev& d, cudaStream_t s);
 void kmc_near_fill(const Geo& g, const Dev& d, int prec, cudaStream_t s);

@@ -692,23 +692,6 @@ __global__ void k_m2l_top(const Geo g, const Dev d, const double2* Iagg) {
 //    21 slice products): 29 significant bits, an entry error of about K 2^-28
 //    of its row and column scales, below the FP32 arithmetic of that form's
 //    near field, L2P and dU.
-#define OZ_S 6
-#define OZ_S_MIXED 4
-static __host__ __device__ __forceinline__ int oz_slices(const Geo& g) { return g.prec == 1 ? OZ_S_MIXED : OZ_S; }
-#define OZ_MT 64
-#define OZ_NT 64
-#define OZ_KC 32
-#define OZ_LD (OZ_KC + 8)  // shared row stride (bf16): 80 B rows, conflict-free ldmatrix
-#define OZ_MAXP 16
-
-static __host__ __device__ __forceinline__ int oz_rows(int n2) { return (n2 + OZ_MT - 1) / OZ_MT * OZ_MT; }
-static __host__ __device__ __forceinline__ int oz_cols(int n2) { return (n2 + OZ_KC - 1) / OZ_KC * OZ_KC; }
-
-// 2^e with e the smallest integer such that |x| < 2^e for every |x| <= m (0 if m = 0)
-__device__ __forceinline__ int oz_exp(unsigned long long mbits) {
-  const double m = __longlong_as_double((long long)mbits);
-  return m > 0.0 ? ilogb(m) + 1 : 0;
-}
 
 __device__ __forceinline__ void oz_split(double x, unsigned short* out, size_t stride) {
   double r = x;
@@ -765,6 +748,30 @@ __global__ void k_oz_aslice(const Geo g, const double* R, const unsigned long lo
     double x = 0.0;
     if (i < n2 && kk < n2) x = ldexp(Rv[(int64_t)kk * n2 + i], oz_exp(colmax[kk]) - oz_exp(rowmax[i]));
     oz_split(x, As + (size_t)v * OZ_S * stride + e, stride);
+  }
+}
+
+// A slices in the layout of the tcgen05 M2L: per translation v, slice s and K
+// chunk c of 64 one contiguous block of NN rows x 64 values in the order of
+// the MMA's 128-byte-swizzled K-major shared-memory operand (row i at
+// (i / 8) 512 + (i mod 8) 64 values, its eight pieces of 8 values permuted
+// by i mod 8); rows i >= 2P and values kk >= 2P are zero.
+__global__ void k_oz_aslice_tc(const Geo g, const double* R, const unsigned long long* colmax,
+                               const unsigned long long* rowmax, unsigned short* As, int NN, int nkc) {
+  const int v = blockIdx.x;
+  const int tx = v % 7 - 3, ty = (v / 7) % 7 - 3, tz = v / 49 - 3;
+  if (abs(tx) <= 1 && abs(ty) <= 1 && abs(tz) <= 1) return;
+  const int n2 = 2 * g.P, K = 64 * nkc;
+  const double* Rv = R + (int64_t)v * n2 * n2;
+  const size_t stride = (size_t)NN * K;
+  for (int e = threadIdx.x + blockIdx.y * blockDim.x; e < NN * K; e += blockDim.x * gridDim.y) {
+    const int i = e / K, kk = e % K;
+    double x = 0.0;
+    if (i < n2 && kk < n2) x = ldexp(Rv[(int64_t)kk * n2 + i], oz_exp(colmax[kk]) - oz_exp(rowmax[i]));
+    const int k = kk & 63;
+    const size_t off = (size_t)(kk >> 6) * NN * 64 + (size_t)(i >> 3) * 512 + (i & 7) * 64 +
+                       ((((k >> 3) ^ i) & 7) << 3) + (k & 7);
+    oz_split(x, As + (size_t)v * OZ_S * stride + off, stride);
   }
 }
 
@@ -948,6 +955,37 @@ __global__ void __launch_bounds__(128) k_m2l_oz(const Geo g, const Dev d, int l,
 }
 
 // Psi from the split CTAs' per-diagonal integer sums
+// B slices in the layout of the tcgen05 M2L: per slice and parity class
+// (cls = (x & 1) + 2 (y & 1) + 4 (z & 1)) the class's cells on a grid of
+// (h2 + 4)^3 positions, two ghost layers on each side (their periodic images,
+// zero in free space), so that the source cells of a box of target cells
+// under one translation form one box of this array:
+// Bp[(((s 8 + cls) Xp + z') Xp + y') Xp + x'][kk], cell x = 2 (x' - 2) + (cls & 1).
+__global__ void k_oz_bslice_tc(const Geo g, const Dev d, int l, const unsigned long long* colmax, unsigned short* Bp) {
+  const int n2 = 2 * g.P, nc = oz_cols(n2);
+  const int nl = 1 << (l - 1), Xp = (nl >> 1) + 4;
+  const int64_t npos = (int64_t)8 * Xp * Xp * Xp;
+  const double* Mt = (const double*)(d.Mt + g.cell_off[l] * g.P);
+  const size_t stride = (size_t)npos * nc;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < npos * nc; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pi = e / nc;
+    const int kk = (int)(e % nc);
+    const int xp = (int)(pi % Xp), yp = (int)((pi / Xp) % Xp), zp = (int)((pi / Xp / Xp) % Xp), cls = (int)(pi / Xp / Xp / Xp);
+    int x = 2 * (xp - 2) + (cls & 1), y = 2 * (yp - 2) + ((cls >> 1) & 1), z = 2 * (zp - 2) + (cls >> 2);
+    bool in = true;
+    if (g.bc) {
+      in = x >= 0 && x < nl && y >= 0 && y < nl && z >= 0 && z < nl;
+    } else {
+      x = (x + 2 * nl) % nl;
+      y = (y + 2 * nl) % nl;
+      z = (z + 2 * nl) % nl;
+    }
+    double v = 0.0;
+    if (in && kk < n2) v = ldexp(Mt[((int64_t)x + nl * ((int64_t)y + nl * z)) * n2 + kk], -oz_exp(colmax[kk]));
+    oz_split(v, Bp + e, stride);
+  }
+}
+
 __global__ void k_oz_finish(const Geo g, const Dev d, int l, const long long* acc64, const unsigned long long* rowmax) {
   const int n2 = 2 * g.P;
   const int64_t ncell = (int64_t)1 << (3 * (l - 1));
@@ -973,17 +1011,31 @@ static int oz_splits(const Geo& g, int l) {
 
 // scratch: R tables of one level (343 (2P)^2 doubles), 64 aggregated I
 // tables and, for the tensor-core form, the scaling maxima and the slices
+// elements of the B-slice scratch: the mma.sync layout, or the ghost-padded
+// class layout of the tcgen05 form at the leaf level
+static size_t oz_bs_elems(const Geo& g) {
+  const size_t nc = oz_cols(2 * g.P);
+  size_t e = (size_t)OZ_S * (size_t)g.ML * nc;
+  if (fmm_m2l_tc_rows(g) > 0) {
+    const size_t xp = (size_t)g.nL / 2 + 4, t = (size_t)OZ_S * 8 * xp * xp * xp * nc;
+    e = t > e ? t : e;
+  }
+  return e;
+}
+
 size_t fmm_m2l_scratch_bytes(const Geo& g) {
   const size_t n2 = 2 * (size_t)g.P;
   size_t b = 343 * n2 * n2 * sizeof(double) + 64 * (size_t)g.P2 * sizeof(double2);
-  if (g.m2l == 0 && g.p <= OZ_MAXP) {
+  if ((g.m2l == 0 || g.m2l == 2) && g.p <= OZ_MAXP) {
     const size_t nr = oz_rows((int)n2), nc = oz_cols((int)n2);
     b += 2 * nr * sizeof(unsigned long long);                      // colmax, rowmax
-    b += 343 * OZ_S * nr * nc * sizeof(unsigned short);             // A slices
-    b += (size_t)OZ_S * (size_t)g.ML * nc * sizeof(unsigned short);  // B slices (leaf level is the largest)
-    size_t acc = 0;  // per-diagonal integer sums of the split levels
+    const size_t tce = (size_t)fmm_m2l_tc_rows(g) * 64 * fmm_m2l_tc_kchunks(g);  // tcgen05 layout
+    const size_t ase = nr * nc > tce ? nr * nc : tce;
+    b += 343 * OZ_S * ase * sizeof(unsigned short);                 // A slices (either layout)
+    b += oz_bs_elems(g) * sizeof(unsigned short);  // B slices (leaf level is the largest)
+    size_t acc = 0;  // per-diagonal integer sums (split levels; every level of the tcgen05 form)
     for (int l = 3; l <= g.L; l++)
-      if (oz_splits(g, l) > 1) {
+      if (oz_splits(g, l) > 1 || fmm_m2l_tc_rows(g) > 0) {
         const size_t a = (size_t)(OZ_S) * ((size_t)1 << (3 * (l - 1))) * n2 * sizeof(long long);
         acc = a > acc ? a : acc;
       }
@@ -1003,7 +1055,8 @@ void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s) {
     k_m2l_top_agg<<<64, 128, 0, s>>>(g, d, Iagg);
     k_m2l_top<<<8, bs, g.P * sizeof(double2), s>>>(g, d, Iagg);
   }
-  const bool tensor = g.m2l == 0 && g.p <= OZ_MAXP;
+  const bool tensor = (g.m2l == 0 || g.m2l == 2) && g.p <= OZ_MAXP;
+  const bool tc = tensor && fmm_m2l_tc_ok(g);  // the tcgen05 form
   unsigned long long *colmax = nullptr, *rowmax = nullptr;
   unsigned short *As = nullptr, *Bs = nullptr;
   long long* acc64 = nullptr;
@@ -1012,8 +1065,9 @@ void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s) {
     colmax = (unsigned long long*)(Iagg + 64 * (size_t)g.P2);
     rowmax = colmax + nr;
     As = (unsigned short*)(rowmax + nr);
-    Bs = As + 343 * OZ_S * nr * nc;
-    acc64 = (long long*)(Bs + (size_t)OZ_S * (size_t)g.ML * nc);
+    const size_t tce = (size_t)fmm_m2l_tc_rows(g) * 64 * fmm_m2l_tc_kchunks(g);
+    Bs = As + 343 * OZ_S * (nr * nc > tce ? nr * nc : tce);
+    acc64 = (long long*)(Bs + oz_bs_elems(g));
     cudaFuncSetAttribute(k_m2l_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_dyn_smem(OZ_S));
   }
   for (int l = 3; l <= g.L; l++) {
@@ -1024,15 +1078,29 @@ void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s) {
       cudaMemsetAsync(colmax, 0, 2 * nr * sizeof(unsigned long long), s);
       k_oz_colmax<<<256, 256, 0, s>>>(g, d, l, colmax);
       k_oz_rowmax<<<343, 256, 0, s>>>(g, R, colmax, rowmax);
-      k_oz_aslice<<<dim3(343, 8), 256, 0, s>>>(g, R, colmax, rowmax, As);
-      const int64_t nb = ((((int64_t)1 << (3 * (l - 1))) * oz_cols((int)n2)) + 255) / 256;
-      k_oz_bslice<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, s>>>(g, d, l, colmax, Bs);
-      const int ntile = (int)((h2 * h2 * h2 + OZ_NT - 1) / OZ_NT), nsplit = oz_splits(g, l);
       const int64_t ncell = (int64_t)1 << (3 * (l - 1));
-      if (nsplit > 1) cudaMemsetAsync(acc64, 0, (size_t)OZ_S * ncell * n2 * sizeof(long long), s);
-      dim3 grid((unsigned)(ntile * nsplit), 8, (unsigned)(nr / OZ_MT));
-      k_m2l_oz<<<grid, 128, oz_dyn_smem(oz_slices(g)), s>>>(g, d, l, As, Bs, rowmax, ntile, nsplit > 1 ? acc64 : nullptr);
-      if (nsplit > 1) k_oz_finish<<<(unsigned)((ncell * n2 + 255) / 256 < 4096 ? (ncell * n2 + 255) / 256 : 4096), 256, 0, s>>>(g, d, l, acc64, rowmax);
+      const unsigned nfin = (unsigned)((ncell * n2 + 255) / 256 < 4096 ? (ncell * n2 + 255) / 256 : 4096);
+      bool done = false;
+      if (tc) {  // tcgen05: slices in its layouts, every level's diagonals through acc64
+        k_oz_aslice_tc<<<dim3(343, 8), 256, 0, s>>>(g, R, colmax, rowmax, As, fmm_m2l_tc_rows(g),
+                                                     fmm_m2l_tc_kchunks(g));
+        const int xp = (int)(h2 / 2) + 4;
+        const int64_t nbp = ((int64_t)8 * xp * xp * xp * oz_cols((int)n2) + 255) / 256;
+        k_oz_bslice_tc<<<(unsigned)(nbp < 4096 ? nbp : 4096), 256, 0, s>>>(g, d, l, colmax, Bs);
+        cudaMemsetAsync(acc64, 0, (size_t)OZ_S * ncell * n2 * sizeof(long long), s);
+        done = fmm_m2l_tc(g, d, l, As, Bs, acc64, s);
+        if (done) k_oz_finish<<<nfin, 256, 0, s>>>(g, d, l, acc64, rowmax);
+      }
+      if (!done) {  // the mma.sync form (also when the tcgen05 launch was not possible)
+        k_oz_aslice<<<dim3(343, 8), 256, 0, s>>>(g, R, colmax, rowmax, As);
+        const int64_t nb = ((ncell * oz_cols((int)n2)) + 255) / 256;
+        k_oz_bslice<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, s>>>(g, d, l, colmax, Bs);
+        const int ntile = (int)((h2 * h2 * h2 + OZ_NT - 1) / OZ_NT), nsplit = oz_splits(g, l);
+        if (nsplit > 1) cudaMemsetAsync(acc64, 0, (size_t)OZ_S * ncell * n2 * sizeof(long long), s);
+        dim3 grid((unsigned)(ntile * nsplit), 8, (unsigned)(nr / OZ_MT));
+        k_m2l_oz<<<grid, 128, oz_dyn_smem(oz_slices(g)), s>>>(g, d, l, As, Bs, rowmax, ntile, nsplit > 1 ? acc64 : nullptr);
+        if (nsplit > 1) k_oz_finish<<<nfin, 256, 0, s>>>(g, d, l, acc64, rowmax);
+      }
     } else {
       dim3 grid((unsigned)((h2 * h2 * h2 + G_NT - 1) / G_NT), 8, (unsigned)((n2 + G_MT - 1) / G_MT));
       k_m2l_gemm<<<grid, 256, 0, s>>>(g, d, l, R);

@@ -455,60 +455,6 @@ template <> __device__ __forceinline__ double small_to<double>(int i) { return (
 // coordinate c + dc (|dc| <= 1) wrapped into [0, E)
 __device__ __forceinline__ int wrap1(int c, int E) { return c < 0 ? c + E : (c >= E ? c - E : c); }
 
-// ---- bulk asynchronous copies (global -> shared) completed on an mbarrier
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-// bytes: a multiple of 16; both addresses 16-byte aligned
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  uint64_t gsrc;
-  asm("cvta.to.global.u64 %0, %1;" : "=l"(gsrc) : "l"(src));
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_addr(dst)),
-               "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// potentially blocking test: the thread is suspended until the phase completes
-// or a time limit of the hardware runs out, so a waiting warp issues few
-// instructions
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// wait for phase `parity` of the barrier, at most ~limit_ns; false on timeout
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
-  if (mbar_test(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try(bar, parity)) {
-    if (global_ns() - t0 > limit_ns) return false;
-  }
-  return true;
-}
-#define KMC_WAIT_NS 1000000000ull  // one second
 
 // diagnostic: the bounded wait against a phase that never completes (16
 // bytes expected on the barrier, nothing copied)

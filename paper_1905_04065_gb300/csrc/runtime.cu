@@ -334,7 +334,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   if (o.precision != KMC_PREC_FP64 && o.precision != KMC_PREC_MIXED) return fail(h, KMC_ERR_ARG, "unknown precision");
   if (o.mem != KMC_MEM_HOST && o.mem != KMC_MEM_DEVICE) return fail(h, KMC_ERR_ARG, "unknown memory kind");
   if (!(o.kT > 0.0)) return fail(h, KMC_ERR_ARG, "kT must be positive");
-  if (o.m2l != KMC_M2L_TENSOR && o.m2l != KMC_M2L_FP64) return fail(h, KMC_ERR_ARG, "unknown M2L arithmetic");
+  if (o.m2l != KMC_M2L_TENSOR && o.m2l != KMC_M2L_FP64 && o.m2l != KMC_M2L_TENSOR_SYNC) return fail(h, KMC_ERR_ARG, "unknown M2L arithmetic");
   if (o.hops != KMC_HOPS_6 && o.hops != KMC_HOPS_14) return fail(h, KMC_ERR_ARG, "unknown hop set");
   if (o.bc != KMC_BC_PERIODIC && o.bc != KMC_BC_FREE && o.bc != KMC_BC_DIRICHLET_Z)
     return fail(h, KMC_ERR_ARG, "unknown boundary conditions");

@@ -86,3 +86,60 @@ def test_mixed_form_four_slice_m2l_matches_fp64_m2l():
     err = float(np.max(np.abs(dt[ok] - df[ok])) / np.max(np.abs(df[ok])))
     print(f"medium, mixed form: max |dU_tensor - dU_fp64| / max|dU| = {err:.2e}")
     assert err <= 2e-5, err
+
+
+def test_tensor_mma_self_check():
+    """Four tcgen05 MMAs (M = 128, N = 192, K = 4 x 16) of small integers, staged as the M2L stages
+    its operands (cp.async pieces and one 2D TMA box, 128-byte-swizzled K-major tiles, the K step
+    advanced inside the swizzle atom), equal the exact product."""
+    out = np.zeros((128, 192), np.float32)
+    rc = _k().kmc_check_tensor_mma(0, out)
+    r, n, kk = np.arange(128)[:, None, None], np.arange(192)[None, :, None], np.arange(64)[None, None, :]
+    want = (((r * 7 + kk * 3) % 17 - 8) * ((n * 5 + kk * 11) % 13 - 6)).sum(axis=2).astype(np.float32)
+    bad = np.argwhere(out != want)
+    detail = [(int(i), int(j), float(out[i, j]), float(want[i, j])) for i, j in bad[:12]]
+    assert rc == 0 and bad.size == 0, (rc, len(bad), detail, out[:2, :12].tolist(), out[8:10, :12].tolist())
+
+
+def _tc_pair(E, sites, q, L, p, precision, bc="periodic"):
+    k = _k()
+    pos = workloads.site_positions(E, sites)
+    out = {}
+    for m2l in ("tensor", "tensor_sync"):
+        h = k.kmc_fmm_init(pos, q, float(E), L, p, precision=precision, lattice_edge=E, kT=0.1, m2l=m2l, bc=bc)
+        U = k.kmc_fmm_energy(h)
+        mask, dU = k.kmc_fmm_propose_lattice(h)
+        out[m2l] = (U, np.asarray(mask).copy(), np.asarray(dU).copy())
+        k.kmc_fmm_destroy(h)
+    return out
+
+
+def _identical(out):
+    (Ut, mt, dt), (Us, ms, ds) = out["tensor"], out["tensor_sync"]
+    assert Ut == Us, (Ut, Us)
+    assert np.array_equal(mt, ms)
+    ok = mt.astype(bool)  # masked hops carry no dU (NaN in both)
+    assert np.array_equal(dt[ok], ds[ok]), float(np.max(np.abs(dt[ok] - ds[ok])))
+
+
+@pytest.mark.parametrize("p", [8, 10, 12, 14])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tcgen05_m2l_bit_identical_to_mma_sync_medium(p, precision):
+    """Both tensor-core forms sum the same exact integer slice products, so the expansions, the
+    energy and every dU agree bit for bit (levels 3 and 4 of the medium system: split levels)."""
+    w, sites, q = workloads.workload("medium")
+    _identical(_tc_pair(w["E"], sites, q, w["L"], p, precision))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tcgen05_m2l_bit_identical_free_space(precision):
+    w, sites, q = workloads.workload("medium")
+    _identical(_tc_pair(w["E"], sites, q, w["L"], 10, precision, bc="free"))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tcgen05_m2l_bit_identical_six_levels(precision):
+    """Six levels: the leaf level (32^3 cells, 256 CTAs of 128 target cells) runs without
+    interaction-list splits, the coarser levels with them."""
+    sites, q = workloads.uniform_lattice(128, 16384, 2024)
+    _identical(_tc_pair(128, sites, q, 6, 12, precision))
