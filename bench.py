@@ -279,6 +279,25 @@ class Clocks:
                 "samples": len(mhz)}
 
 
+def m2l_roofline(levels: dict, total_ms: float, L: int, p: int, peaks: dict, precision: str) -> dict:
+    """The leaf level's M2L product kernel against the dense bf16 tensor peak: algorithmic bf16 flops
+    = 2 (2P)^2 per slice product, translation and cell (189 far translations per cell of the
+    periodic box, 10 slice products with four slices, 21 with six), over its CUDA-event time."""
+    P = (p + 1) * (p + 2) // 2
+    nslp = 10 if precision == "mixed" else 21
+    ncell = 8 ** (L - 1)
+    flops = 2.0 * (2 * P) ** 2 * 189 * ncell * nslp
+    ms = levels.get(L)
+    out = {"kernel": "k_m2l_tc (leaf level)", "bound": "tensor", "unit": "TFLOP/s", "peak": peaks["bf16_tflops"],
+           "peak_source": "bf16_tflops of MEASURED_PEAKS.json (cuBLAS bf16 burst)",
+           "work": f"{flops:.3e} bf16 flops: {nslp} slice products x 189 translations x {ncell} cells x 2 (2P)^2",
+           "level_ms": {str(k): v for k, v in sorted(levels.items())}, "m2l_total_ms": total_ms}
+    if ms:
+        out["achieved"] = flops / (ms * 1e-3) / 1e12
+        out["frac"] = out["achieved"] / peaks["bf16_tflops"]
+    return out
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -574,6 +593,9 @@ def run_gpu(args):
     torch.cuda.synchronize()
     recompute_s = time.perf_counter() - t_r
 
+    # the one-off M2L's product kernels, timed by the library's events (into scratch: state unchanged)
+    m2l_levels, m2l_total_ms = k.kmc_fmm_m2l_timed(h, 3)
+
     # FP64 form (context)
     fp64 = None
     if args.fp64_steps > 0:
@@ -661,6 +683,7 @@ def run_gpu(args):
     rooflines = phase_rooflines(work, {nm: phases[i] / args.steps for i, nm in enumerate(k.PHASES)}, E, L, len(q),
                                 p, nhop, peaks, nsm, mixed=True)
     rooflines["propose"] = {kk: roof[kk] for kk in ("kernel", "bound", "achieved", "peak", "unit", "frac")}
+    rooflines["m2l"] = m2l_roofline(m2l_levels, m2l_total_ms, L, p, peaks, precision="mixed")
     if fp64 is not None:
         # FP64 form: one FP64 FMA per pair (the lattice-table near field), at 2 FMA/clk/SM
         fp64_peak = 2 * 2 * nsm * sm_max * 1e6

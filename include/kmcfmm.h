@@ -368,6 +368,19 @@ const char* kmc_batch_last_error(kmc_batch_handle b);
 void kmc_batch_destroy(kmc_batch_handle b);
 
 /*
+ * Timing hook with no counterpart in the paper: runs the one-off M2L of the
+ * handle's current multipole expansions (Algorithm 2, every level, in the
+ * handle's M2L arithmetic, kmc_m2l) reps times into a scratch copy of the
+ * local expansions, so the handle's state is unchanged, and reports the mean
+ * device time per run of each level's product kernel (level_ms[l], l = 3 ..
+ * levels; an array of 11 doubles, other entries 0) and of the whole M2L with
+ * its operand slicing (total_ms), from CUDA events on the handle's stream.
+ * Allocates the M2L scratch (as init does) for the duration of the call.
+ * Errors: KMC_ERR_ARG (reps <= 0, null outputs), KMC_ERR_OOM, KMC_ERR_CUDA.
+ */
+int kmc_fmm_m2l_timed(kmc_handle h, int reps, double* level_ms, double* total_ms);
+
+/*
  * Diagnostic with no counterpart in the paper: runs, on `device`, the bounded
  * device-side wait that the FP32 lattice propose uses for its bulk copies,
  * against a barrier phase that can never complete (bytes expected, nothing

@@ -49,6 +49,7 @@ EXPORTS = [
     "kmc_fmm_leaf_index", "kmc_fmm_positions", "kmc_last_error", "kmc_fmm_destroy", "kmc_select_static",
     "kmc_check_bounded_wait",
     "kmc_check_tensor_mma",
+    "kmc_fmm_m2l_timed",
     "kmc_batch_create", "kmc_batch_run", "kmc_batch_run_timed", "kmc_batch_set_chunk", "kmc_batch_info",
     "kmc_batch_propose_timed", "kmc_batch_last_error", "kmc_batch_destroy",
 ]
@@ -112,6 +113,7 @@ def load_library(path: str | None = None):
             "kmc_select_static": (I, [P, I64, D, D, P, P, P, P]),
             "kmc_check_bounded_wait": (I, [I, D]),
             "kmc_check_tensor_mma": (I, [I, ctypes.c_void_p]),
+            "kmc_fmm_m2l_timed": (I, [P, I, P, P]),
             "kmc_batch_create": (I, [P, I, P]),
             "kmc_batch_run": (I, [P, I, P, P, P]),
             "kmc_batch_run_timed": (I, [P, I, P, P, P, P]),
@@ -568,6 +570,15 @@ def kmc_check_bounded_wait(device: int = 0, limit_seconds: float = 0.05) -> int:
     """Status of the bounded-wait diagnostic: KMC_ERR_TIMEOUT (6) when the
     device-side wait gave up and returned as designed."""
     return int(load_library().kmc_check_bounded_wait(int(device), float(limit_seconds)))
+
+
+def kmc_fmm_m2l_timed(h: Handle, reps: int = 3):
+    """(per-level ms of the M2L product kernel {level: ms}, ms of the whole M2L) over reps runs into
+    scratch; the handle's state is unchanged."""
+    lv = np.zeros(11, np.float64)
+    tot = ctypes.c_double(0.0)
+    _check(h, load_library().kmc_fmm_m2l_timed(h.ptr, int(reps), lv.ctypes.data, ctypes.byref(tot)))
+    return {l: float(lv[l]) for l in range(3, 11) if lv[l] > 0.0}, float(tot.value)
 
 
 def kmc_check_tensor_mma(device: int = 0, out=None) -> int:

@@ -307,6 +307,7 @@ static __host__ __device__ __forceinline__ int oz_slices(const Geo& g) { return 
 #define OZ_KC 32
 #define OZ_LD (OZ_KC + 8)  // shared row stride (bf16): 80 B rows, conflict-free ldmatrix
 #define OZ_MAXP 16
+#define OZ_MAXP_P 153  // ncoef(OZ_MAXP)
 
 static __host__ __device__ __forceinline__ int oz_rows(int n2) { return (n2 + OZ_MT - 1) / OZ_MT * OZ_MT; }
 static __host__ __device__ __forceinline__ int oz_cols(int n2) { return (n2 + OZ_KC - 1) / OZ_KC * OZ_KC; }
@@ -326,7 +327,8 @@ void fmm_m2m(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_itab(const Geo& g, const Dev& d, cudaStream_t s);
 void fmm_child_tables(const Geo& g, const Dev& d, cudaStream_t s);  // child and ancestor offset tables
 size_t fmm_m2l_scratch_bytes(const Geo& g);
-void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s);
+// ev: null, or 2 (KMC_MAXL + 1) events recorded around level l's M2L product kernel (2 l, 2 l + 1)
+void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s, cudaEvent_t* ev = nullptr);
 bool fmm_m2l_tc_ok(const Geo& g);           // the tcgen05 M2L applies (KMC_M2L_TENSOR, p <= 14)
 int fmm_m2l_tc_rows(const Geo& g);           // its MMA N (rows of its A-slice layout), 0 if p > 14
 int fmm_m2l_tc_kchunks(const Geo& g);        // its K chunks of 64 values

@@ -679,8 +679,10 @@ __global__ void k_m2l_top(const Geo g, const Dev d, const double2* Iagg) {
 //    |Mt[., kk]|), the translation entries R_t[i][kk] are multiplied by it, and
 //    row i of all R_t is divided by 2^er(i) (er from the row's largest entry),
 //    so that every scaled value lies in (-1, 1).
-//  * Slicing: x = sum_{s=1..S} x_s 2^(-7 s) + O(2^(-7S - 1)) with integer
-//    slices, |x_1| <= 128 and |x_s| <= 64 (s > 1), held exactly in bf16.
+//  * Slicing: x = sum_{s=1..S} x_s 2^(-7 s) + r, |r| <= 2^(-7S - 1), with
+//    integer slices, |x_1| <= 128 and -64 <= x_s <= 63 (s > 1), held exactly
+//    in bf16: the balanced base-128 digits of N = rint(x 2^(7S)) (|N| <= 2^42,
+//    exact in int64), cut with integer arithmetic.
 //  * The product keeps the slice pairs with a + b = D <= S + 1 and sums each
 //    diagonal D separately: per translation (K = 2P padded, at most 352
 //    terms) the FP32 tensor-core accumulation of integers stays below 2^24
@@ -693,16 +695,22 @@ __global__ void k_m2l_top(const Geo g, const Dev d, const double2* Iagg) {
 //    of its row and column scales, below the FP32 arithmetic of that form's
 //    near field, L2P and dU.
 
+// bf16 bits of a small integer (|v| <= 256: exact in bf16)
+__device__ __forceinline__ unsigned short oz_bf16_int(long long v) {
+  const __nv_bfloat16 b = __float2bfloat16_rn((float)v);
+  return *(const unsigned short*)&b;
+}
 __device__ __forceinline__ void oz_split(double x, unsigned short* out, size_t stride) {
-  double r = x;
+  // x 2^(7S) is exact (a power-of-two scaling of |x| < 1); its nearest integer has at most 42 bits
+  long long n = __double2ll_rn(x * 4398046511104.0);  // 2^42 = 2^(7 OZ_S)
+  static_assert(OZ_S == 6, "2^(7 OZ_S)");
 #pragma unroll
-  for (int sl = 0; sl < OZ_S; sl++) {
-    r *= 128.0;
-    const double q = rint(r);
-    const __nv_bfloat16 b = __float2bfloat16_rn((float)q);  // |q| <= 128, an integer: exact
-    out[sl * stride] = *(const unsigned short*)&b;
-    r -= q;
+  for (int sl = OZ_S - 1; sl > 0; sl--) {
+    const long long dg = ((n + 64) & 127) - 64;  // balanced digit in [-64, 63]
+    out[sl * stride] = oz_bf16_int(dg);
+    n = (n - dg) >> 7;  // exact: n - dg is a multiple of 128
   }
+  out[0] = oz_bf16_int(n);  // |n| <= 128
 }
 
 // largest |Mt[cell][kk]| over the cells of level l, per real coefficient kk
@@ -726,11 +734,24 @@ __global__ void k_oz_rowmax(const Geo g, const double* R, const unsigned long lo
   const int tx = v % 7 - 3, ty = (v / 7) % 7 - 3, tz = v / 49 - 3;
   if (abs(tx) <= 1 && abs(ty) <= 1 && abs(tz) <= 1) return;
   const int n2 = 2 * g.P;
+  __shared__ int ec[2 * OZ_MAXP_P];
+  for (int k = threadIdx.x; k < n2; k += blockDim.x) ec[k] = oz_exp(colmax[k]);
+  __syncthreads();
   const double* Rv = R + (int64_t)v * n2 * n2;
   for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-    double m = 0.0;
-    for (int kk = 0; kk < n2; kk++) m = fmax(m, ldexp(fabs(Rv[(int64_t)kk * n2 + i]), oz_exp(colmax[kk])));
-    atomicMax(&rowmax[i], (unsigned long long)__double_as_longlong(m));
+    // max of |R| 2^ec over kk, compared as the bit patterns of non-negative doubles; the
+    // power-of-two scaling by an exponent add where the result stays normal, else by ldexp
+    long long m = 0;
+    for (int kk = 0; kk < n2; kk++) {
+      long long b = __double_as_longlong(Rv[(int64_t)kk * n2 + i]) & 0x7FFFFFFFFFFFFFFFll;
+      const int ex = (int)(b >> 52) + ec[kk];
+      if ((b >> 52) != 0 && ex > 0 && ex < 2047)
+        b += (long long)ec[kk] << 52;
+      else if (b != 0)
+        b = __double_as_longlong(ldexp(__longlong_as_double(b), ec[kk]));
+      m = b > m ? b : m;
+    }
+    atomicMax(&rowmax[i], (unsigned long long)m);
   }
 }
 
@@ -741,12 +762,18 @@ __global__ void k_oz_aslice(const Geo g, const double* R, const unsigned long lo
   const int tx = v % 7 - 3, ty = (v / 7) % 7 - 3, tz = v / 49 - 3;
   if (abs(tx) <= 1 && abs(ty) <= 1 && abs(tz) <= 1) return;
   const int n2 = 2 * g.P, nr = oz_rows(n2), nc = oz_cols(n2);
+  __shared__ int ec[2 * OZ_MAXP_P], er[2 * OZ_MAXP_P];  // the scaling exponents
+  for (int k = threadIdx.x; k < n2; k += blockDim.x) {
+    ec[k] = oz_exp(colmax[k]);
+    er[k] = oz_exp(rowmax[k]);
+  }
+  __syncthreads();
   const double* Rv = R + (int64_t)v * n2 * n2;
   const size_t stride = (size_t)nr * nc;
   for (int e = threadIdx.x + blockIdx.y * blockDim.x; e < nr * nc; e += blockDim.x * gridDim.y) {
     const int i = e / nc, kk = e % nc;
     double x = 0.0;
-    if (i < n2 && kk < n2) x = ldexp(Rv[(int64_t)kk * n2 + i], oz_exp(colmax[kk]) - oz_exp(rowmax[i]));
+    if (i < n2 && kk < n2) x = ldexp(Rv[(int64_t)kk * n2 + i], ec[kk] - er[i]);
     oz_split(x, As + (size_t)v * OZ_S * stride + e, stride);
   }
 }
@@ -762,12 +789,18 @@ __global__ void k_oz_aslice_tc(const Geo g, const double* R, const unsigned long
   const int tx = v % 7 - 3, ty = (v / 7) % 7 - 3, tz = v / 49 - 3;
   if (abs(tx) <= 1 && abs(ty) <= 1 && abs(tz) <= 1) return;
   const int n2 = 2 * g.P, K = 64 * nkc;
+  __shared__ int ec[2 * OZ_MAXP_P], er[2 * OZ_MAXP_P];  // the scaling exponents
+  for (int k = threadIdx.x; k < n2; k += blockDim.x) {
+    ec[k] = oz_exp(colmax[k]);
+    er[k] = oz_exp(rowmax[k]);
+  }
+  __syncthreads();
   const double* Rv = R + (int64_t)v * n2 * n2;
   const size_t stride = (size_t)NN * K;
   for (int e = threadIdx.x + blockIdx.y * blockDim.x; e < NN * K; e += blockDim.x * gridDim.y) {
     const int i = e / K, kk = e % K;
     double x = 0.0;
-    if (i < n2 && kk < n2) x = ldexp(Rv[(int64_t)kk * n2 + i], oz_exp(colmax[kk]) - oz_exp(rowmax[i]));
+    if (i < n2 && kk < n2) x = ldexp(Rv[(int64_t)kk * n2 + i], ec[kk] - er[i]);
     const int k = kk & 63;
     const size_t off = (size_t)(kk >> 6) * NN * 64 + (size_t)(i >> 3) * 512 + (i & 7) * 64 +
                        ((((k >> 3) ^ i) & 7) << 3) + (k & 7);
@@ -781,10 +814,13 @@ __global__ void k_oz_bslice(const Geo g, const Dev d, int l, const unsigned long
   const int64_t ncell = (int64_t)1 << (3 * (l - 1));
   const double* Mt = (const double*)(d.Mt + g.cell_off[l] * g.P);
   const size_t stride = (size_t)ncell * nc;
+  __shared__ int ec[2 * OZ_MAXP_P];
+  for (int k = threadIdx.x; k < n2; k += blockDim.x) ec[k] = oz_exp(colmax[k]);
+  __syncthreads();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ncell * nc; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = e / nc;
     const int kk = (int)(e % nc);
-    const double x = kk < n2 ? ldexp(Mt[c * n2 + kk], -oz_exp(colmax[kk])) : 0.0;
+    const double x = kk < n2 ? ldexp(Mt[c * n2 + kk], -ec[kk]) : 0.0;
     oz_split(x, Bs + e, stride);
   }
 }
@@ -967,6 +1003,9 @@ __global__ void k_oz_bslice_tc(const Geo g, const Dev d, int l, const unsigned l
   const int64_t npos = (int64_t)8 * Xp * Xp * Xp;
   const double* Mt = (const double*)(d.Mt + g.cell_off[l] * g.P);
   const size_t stride = (size_t)npos * nc;
+  __shared__ int ec[2 * OZ_MAXP_P];
+  for (int k = threadIdx.x; k < n2; k += blockDim.x) ec[k] = oz_exp(colmax[k]);
+  __syncthreads();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < npos * nc; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t pi = e / nc;
     const int kk = (int)(e % nc);
@@ -981,7 +1020,7 @@ __global__ void k_oz_bslice_tc(const Geo g, const Dev d, int l, const unsigned l
       z = (z + 2 * nl) % nl;
     }
     double v = 0.0;
-    if (in && kk < n2) v = ldexp(Mt[((int64_t)x + nl * ((int64_t)y + nl * z)) * n2 + kk], -oz_exp(colmax[kk]));
+    if (in && kk < n2) v = ldexp(Mt[((int64_t)x + nl * ((int64_t)y + nl * z)) * n2 + kk], -ec[kk]);
     oz_split(v, Bp + e, stride);
   }
 }
@@ -1044,7 +1083,7 @@ size_t fmm_m2l_scratch_bytes(const Geo& g) {
   return b;
 }
 
-void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s) {
+void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s, cudaEvent_t* ev) {
   const size_t n2 = 2 * (size_t)g.P;
   double* R = (double*)scratch;
   double2* Iagg = (double2*)(R + 343 * n2 * n2);
@@ -1088,7 +1127,9 @@ void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s) {
         const int64_t nbp = ((int64_t)8 * xp * xp * xp * oz_cols((int)n2) + 255) / 256;
         k_oz_bslice_tc<<<(unsigned)(nbp < 4096 ? nbp : 4096), 256, 0, s>>>(g, d, l, colmax, Bs);
         cudaMemsetAsync(acc64, 0, (size_t)OZ_S * ncell * n2 * sizeof(long long), s);
+        if (ev) cudaEventRecord(ev[2 * l], s);
         done = fmm_m2l_tc(g, d, l, As, Bs, acc64, s);
+        if (ev) cudaEventRecord(ev[2 * l + 1], s);
         if (done) k_oz_finish<<<nfin, 256, 0, s>>>(g, d, l, acc64, rowmax);
       }
       if (!done) {  // the mma.sync form (also when the tcgen05 launch was not possible)
@@ -1098,12 +1139,16 @@ void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s) {
         const int ntile = (int)((h2 * h2 * h2 + OZ_NT - 1) / OZ_NT), nsplit = oz_splits(g, l);
         if (nsplit > 1) cudaMemsetAsync(acc64, 0, (size_t)OZ_S * ncell * n2 * sizeof(long long), s);
         dim3 grid((unsigned)(ntile * nsplit), 8, (unsigned)(nr / OZ_MT));
+        if (ev) cudaEventRecord(ev[2 * l], s);
         k_m2l_oz<<<grid, 128, oz_dyn_smem(oz_slices(g)), s>>>(g, d, l, As, Bs, rowmax, ntile, nsplit > 1 ? acc64 : nullptr);
+        if (ev) cudaEventRecord(ev[2 * l + 1], s);
         if (nsplit > 1) k_oz_finish<<<nfin, 256, 0, s>>>(g, d, l, acc64, rowmax);
       }
     } else {
       dim3 grid((unsigned)((h2 * h2 * h2 + G_NT - 1) / G_NT), 8, (unsigned)((n2 + G_MT - 1) / G_MT));
+      if (ev) cudaEventRecord(ev[2 * l], s);
       k_m2l_gemm<<<grid, 256, 0, s>>>(g, d, l, R);
+      if (ev) cudaEventRecord(ev[2 * l + 1], s);
     }
   }
 }

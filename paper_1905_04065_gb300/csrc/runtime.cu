@@ -1656,6 +1656,56 @@ int kmc_batch_run_timed(kmc_batch_handle b, int steps, const double* uniforms, i
 }
 
 
+int kmc_fmm_m2l_timed(kmc_handle h, int reps, double* level_ms, double* total_ms) {
+  KMC_TRACE("kmc_fmm_m2l_timed");
+  if (!h || reps <= 0 || !level_ms || !total_ms) return KMC_ERR_ARG;
+  int rc = guard(h);
+  if (rc) return rc;
+  const Geo& g = h->g;
+  cudaStream_t s = h->stream;
+  for (int l = 0; l <= KMC_MAXL; l++) level_ms[l] = 0.0;
+  *total_ms = 0.0;
+  Dev d2 = h->d;  // the products go to a scratch copy of the local expansions
+  void* scratch = nullptr;
+  double2* psi = nullptr;
+  cudaEvent_t ev[2 * (KMC_MAXL + 1)], t0 = nullptr, t1 = nullptr;
+  int made = 0;
+  rc = KMC_OK;
+  for (; made < 2 * (KMC_MAXL + 1); made++)
+    if (cudaEventCreate(&ev[made]) != cudaSuccess) break;
+  if (made < 2 * (KMC_MAXL + 1) || cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess ||
+      cudaMallocAsync(&scratch, fmm_m2l_scratch_bytes(g), s) != cudaSuccess ||
+      cudaMallocAsync((void**)&psi, sizeof(double2) * g.ncell_total * g.P, s) != cudaSuccess) {
+    rc = fail(h, KMC_ERR_OOM, "M2L timing: events or scratch unavailable");
+  } else {
+    d2.Psi = psi;
+    for (int r = 0; r < reps && rc == KMC_OK; r++) {
+      cudaEventRecord(t0, s);
+      fmm_m2l(g, d2, scratch, s, ev);
+      cudaEventRecord(t1, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess) {
+        rc = fail(h, KMC_ERR_CUDA, "M2L timing: %s", cudaGetErrorString(cudaGetLastError()));
+        break;
+      }
+      float f = 0.f;
+      cudaEventElapsedTime(&f, t0, t1);
+      *total_ms += f / reps;
+      for (int l = 3; l <= g.L; l++) {
+        cudaEventElapsedTime(&f, ev[2 * l], ev[2 * l + 1]);
+        level_ms[l] += f / reps;
+      }
+    }
+  }
+  if (scratch) cudaFreeAsync(scratch, s);
+  if (psi) cudaFreeAsync(psi, s);
+  cudaStreamSynchronize(s);
+  for (int k = 0; k < made; k++) cudaEventDestroy(ev[k]);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (rc) return rc;
+  return check_flags(h, "M2L timing");
+}
+
 int kmc_batch_propose_timed(kmc_batch_handle b, int reps, double* device_ms) {
   KMC_TRACE("kmc_batch_propose_timed");
   if (!b || reps <= 0 || !device_ms) return KMC_ERR_ARG;

@@ -143,3 +143,20 @@ def test_tcgen05_m2l_bit_identical_six_levels(precision):
     interaction-list splits, the coarser levels with them."""
     sites, q = workloads.uniform_lattice(128, 16384, 2024)
     _identical(_tc_pair(128, sites, q, 6, 12, precision))
+
+
+def test_m2l_timing_hook_leaves_the_state():
+    """kmc_fmm_m2l_timed runs the M2L into scratch: per-level times for levels 3 .. L, and every dU
+    afterwards bit for bit as before."""
+    k = _k()
+    w, sites, q = workloads.workload("medium")
+    pos = workloads.site_positions(w["E"], sites)
+    h = k.kmc_fmm_init(pos, q, float(w["E"]), w["L"], w["p"], precision="mixed", lattice_edge=w["E"], kT=0.1)
+    m0, d0 = (np.asarray(a).copy() for a in k.kmc_fmm_propose_lattice(h))
+    levels, total = k.kmc_fmm_m2l_timed(h, 2)
+    m1, d1 = (np.asarray(a).copy() for a in k.kmc_fmm_propose_lattice(h))
+    k.kmc_fmm_destroy(h)
+    assert sorted(levels) == list(range(3, w["L"] + 1)) and all(v > 0 for v in levels.values())
+    assert total >= sum(levels.values())
+    ok = m0.astype(bool)
+    assert np.array_equal(m0, m1) and np.array_equal(d0[ok], d1[ok])
