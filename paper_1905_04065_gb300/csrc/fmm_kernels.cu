@@ -1029,11 +1029,17 @@ __global__ void k_oz_finish(const Geo g, const Dev d, int l, const long long* ac
   const int n2 = 2 * g.P;
   const int64_t ncell = (int64_t)1 << (3 * (l - 1));
   double* Ps = (double*)(d.Psi + g.cell_off[l] * g.P);
+  const int S = oz_slices(g);
+  __shared__ double pw[OZ_S][2 * OZ_MAXP_P];  // 2^(er(i) - 7 D): exact powers of two
+  for (int k = threadIdx.x; k < n2; k += blockDim.x) {
+    const int er = oz_exp(rowmax[k]);
+    for (int D = 2; D <= S + 1; D++) pw[D - 2][k] = ldexp(1.0, er - 7 * D);
+  }
+  __syncthreads();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ncell * n2; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % n2);
-    const int er = oz_exp(rowmax[i]);
-    double v = 0.0;
-    for (int D = 2; D <= oz_slices(g) + 1; D++) v += ldexp((double)acc64[(int64_t)(D - 2) * ncell * n2 + e], er - 7 * D);
+    double v = 0.0;  // the diagonals in order D = 2, 3, ...; each term exact (an integer times a power of two)
+    for (int D = 2; D <= S + 1; D++) v += (double)acc64[(int64_t)(D - 2) * ncell * n2 + e] * pw[D - 2][i];
     Ps[e] = v;
   }
 }
