@@ -107,6 +107,15 @@ enum kmc_m2l {
                               bit for bit the result of KMC_M2L_TENSOR, kept as its cross-check */
 };
 
+/* Arithmetic of the mixed form's per-step downward pass (the L2L translations
+ * of the accumulated local expansions, Algorithm 2's downward pass) on its two
+ * finest levels; the FP64 form and the coarser levels always use CUDA cores. */
+enum kmc_l2l {
+  KMC_L2L_TENSOR = 0, /* tcgen05 kind::tf32 MMAs, each FP32 operand split into two TF32 parts
+                         (hi hi + hi lo + lo hi, FP32 accumulation), p <= 14 */
+  KMC_L2L_CUDA = 1    /* FP32 CUDA cores */
+};
+
 typedef struct kmc_opts {
   int precision;      /* kmc_precision */
   int lattice_edge;   /* E > 0: lattice mode, sites at ((i+1/2)h, (j+1/2)h, (k+1/2)h),
@@ -129,6 +138,7 @@ typedef struct kmc_opts {
                          the old or the new position; proposals then read it instead of summing the
                          pairs.  The values agree with the per-step sum to rounding (fixed point,
                          2^-k with 2^k |sum| < 2^62).  0 = sum every step (default). */
+  int l2l;            /* kmc_l2l: arithmetic of the mixed form's per-step downward pass */
 } kmc_opts;
 
 typedef struct kmc_fmm* kmc_handle;
@@ -393,20 +403,23 @@ int kmc_check_bounded_wait(int device, double limit_seconds);
 
 /*
  * Diagnostic with no counterpart in the paper: four fifth-generation
- * tensor-core MMAs (tcgen05.mma kind::f16, M = 128, N = 192, K = 4 x 16, bf16 x
- * bf16 -> FP32 in tensor memory) of small integer operands, staged in shared
- * memory exactly as the tensor-core M2L stages its operands (cp.async pieces
+ * tensor-core MMAs of small integer operands, staged in shared memory exactly
+ * as the library's tensor-core kernels stage theirs, read back from tensor
+ * memory with tcgen05.ld and compared on the host with the exact integer
+ * product.  kind 0: tcgen05.mma kind::f16, M = 128, N = 192, K = 4 x 16,
+ * bf16 x bf16 -> FP32, staged as the M2L stages its operands (cp.async pieces
  * for A, one 2D TMA box of a contiguous block for B, 128-byte-swizzled K-major
- * tiles, the K step advanced inside the swizzle atom), read back with tcgen05.ld
- * and compared on the host with the exact integer product.  Returns 0 when
+ * tiles, the K step advanced inside the swizzle atom); kind 1: kind::tf32,
+ * M = 128, N = 192, K = 4 x 8, staged as the downward pass stages its operands
+ * (2D TMA boxes of 32 FP32 values per row, 128-byte swizzle).  Returns 0 when
  * every entry agrees, 1 on a mismatch, -KMC_ERR_TIMEOUT when a bounded wait
- * gave up, -KMC_ERR_CUDA / -KMC_ERR_OOM when the device, the driver's
- * tensor-map encoder or an allocation is unavailable.  out: NULL, or a host
- * array of 128 * 192 floats that receives the product as read from tensor
- * memory (row-major, row = M index).  Allocates and frees about 100 kB of
- * device memory; no handle needed.
+ * gave up, -KMC_ERR_ARG for an unknown kind, -KMC_ERR_CUDA / -KMC_ERR_OOM when
+ * the device, the driver's tensor-map encoder or an allocation is unavailable.
+ * out: NULL, or a host array of 128 * 192 floats that receives the product as
+ * read from tensor memory (row-major, row = M index).  Allocates and frees
+ * about 100 kB of device memory; no handle needed.
  */
-int kmc_check_tensor_mma(int device, float* out);
+int kmc_check_tensor_mma(int device, int kind, float* out);
 
 /* Message of the last error on this handle (static string if h is NULL). */
 const char* kmc_last_error(kmc_handle h);

@@ -36,6 +36,8 @@ KMC_MEM_DEVICE = 1
 KMC_M2L_TENSOR = 0
 KMC_M2L_FP64 = 1
 KMC_M2L_TENSOR_SYNC = 2
+KMC_L2L_TENSOR = 0
+KMC_L2L_CUDA = 1
 KMC_HOPS_6 = 0
 KMC_HOPS_14 = 1
 KMC_BC_PERIODIC = 0
@@ -76,6 +78,7 @@ class kmc_opts(ctypes.Structure):
         ("bc", ctypes.c_int),
         ("field_z", ctypes.c_double),
         ("near_cache", ctypes.c_int),
+        ("l2l", ctypes.c_int),
     ]
 
 
@@ -112,7 +115,7 @@ def load_library(path: str | None = None):
             "kmc_fmm_destroy": (None, [P]),
             "kmc_select_static": (I, [P, I64, D, D, P, P, P, P]),
             "kmc_check_bounded_wait": (I, [I, D]),
-            "kmc_check_tensor_mma": (I, [I, ctypes.c_void_p]),
+            "kmc_check_tensor_mma": (I, [I, I, ctypes.c_void_p]),
             "kmc_fmm_m2l_timed": (I, [P, I, P, P]),
             "kmc_batch_create": (I, [P, I, P]),
             "kmc_batch_run": (I, [P, I, P, P, P]),
@@ -196,7 +199,7 @@ def _out(h: Handle, shape, dtype):
 def kmc_fmm_init(positions, charges, box: float, levels: int, order: int, precision: str = "fp64",
                  lattice_edge: int = 0, lattice_h: float = 1.0, kT: float = 1.0, stream=None, device: int = 0,
                  leaf_capacity: int = 0, m2l: str = "tensor", hops: int = 6, bc: str = "periodic",
-                 field_z: float = 0.0, near_cache: bool = False) -> Handle:
+                 field_z: float = 0.0, near_cache: bool = False, l2l: str = "tensor") -> Handle:
     """Create a handle and run the one-off full FMM.  precision: 'fp64' or 'mixed';
     m2l: 'tensor' (bf16 tensor cores with exact slicing, tcgen05 MMA), 'tensor_sync' (the same slicing on
     the mma.sync form, bit for bit the same result) or 'fp64' (FP64 CUDA cores);
@@ -204,7 +207,9 @@ def kmc_fmm_init(positions, charges, box: float, levels: int, order: int, precis
     bc: 'periodic' (neutral systems), 'free' (free space) or 'dirichlet' (grounded walls at z = 0 and
     z = box/2, lattice mode, every charge below box/2, applied field field_z along z);
     near_cache: lattice mode, keep every site's near-field sum on the device and update it per
-    accepted move instead of summing the pairs every step."""
+    accepted move instead of summing the pairs every step;
+    l2l: the mixed form's per-step downward pass on its two finest levels, 'tensor' (tcgen05 tf32
+    MMAs, FP32 operands split in two, p <= 14) or 'cuda' (FP32 CUDA cores)."""
     lib = load_library()
     opts = kmc_opts()
     lib.kmc_opts_default(ctypes.byref(opts))
@@ -219,6 +224,7 @@ def kmc_fmm_init(positions, charges, box: float, levels: int, order: int, precis
     opts.bc = {"periodic": KMC_BC_PERIODIC, "free": KMC_BC_FREE, "dirichlet": KMC_BC_DIRICHLET_Z}[bc]
     opts.field_z = float(field_z)
     opts.near_cache = 1 if near_cache else 0
+    opts.l2l = {"tensor": KMC_L2L_TENSOR, "cuda": KMC_L2L_CUDA}[l2l]
     dev = _is_torch(positions) and positions.is_cuda
     opts.mem = KMC_MEM_DEVICE if dev else KMC_MEM_HOST
     if stream is not None:
@@ -246,7 +252,7 @@ def kmc_fmm_init(positions, charges, box: float, levels: int, order: int, precis
                        box=float(box), levels=int(levels), order=int(order), precision=precision,
                        lattice_edge=int(lattice_edge), lattice_h=float(lattice_h), kT=float(kT),
                        leaf_capacity=int(leaf_capacity), m2l=m2l, hops=int(hops), bc=bc, field_z=float(field_z),
-                       near_cache=bool(near_cache))
+                       near_cache=bool(near_cache), l2l=l2l)
     return h
 
 
@@ -581,7 +587,7 @@ def kmc_fmm_m2l_timed(h: Handle, reps: int = 3):
     return {l: float(lv[l]) for l in range(3, 11) if lv[l] > 0.0}, float(tot.value)
 
 
-def kmc_check_tensor_mma(device: int = 0, out=None) -> int:
+def kmc_check_tensor_mma(device: int = 0, out=None, kind: int = 0) -> int:
     """One tcgen05 MMA of small integer operands, staged as the tensor-core M2L stages them, against
     the exact product: 0 agreement, 1 mismatch, negative: unavailable or timed out.  out: None or a
     float32 array of 128 x 192 that receives the product read back from tensor memory."""
@@ -589,5 +595,5 @@ def kmc_check_tensor_mma(device: int = 0, out=None) -> int:
     if out is not None:
         assert out.dtype == np.float32 and out.size == 128 * 192 and out.flags["C_CONTIGUOUS"]
         ptr = out.ctypes.data
-    return int(load_library().kmc_check_tensor_mma(int(device), ptr))
+    return int(load_library().kmc_check_tensor_mma(int(device), int(kind), ptr))
 

@@ -18,8 +18,8 @@ LIB = os.path.join(BUILD, "libkmcfmm.so")
 # checked build: bounds checks compiled in (-DKMC_CHECKS), for tests only
 BUILD_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(BUILD_CHECKED, "libkmcfmm.so")
-SOURCES = ["runtime.cu", "fmm_kernels.cu", "kmc_kernels.cu", "static_select.cu", "m2l_tc.cu"]
-HEADERS = ["common.cuh"]
+SOURCES = ["runtime.cu", "fmm_kernels.cu", "kmc_kernels.cu", "static_select.cu", "m2l_tc.cu", "l2l_tc.cu"]
+HEADERS = ["common.cuh", "tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

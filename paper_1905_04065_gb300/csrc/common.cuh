@@ -110,6 +110,7 @@ struct Geo {
   double field_z;         // applied field along z (Dirichlet walls)
   int near_cache;         // 1: near-field sums of every site kept in d.nearfx (lattice mode)
   int near_ks;            // their fixed-point exponent: value = nearfx * 2^-near_ks
+  int l2l;                // kmc_l2l: arithmetic of the mixed form's per-step downward pass
 };
 
 // cell coordinate of x on a level with n cells per side, floor(x n / a)
@@ -173,6 +174,8 @@ struct Dev {
   float* phi_old32;   // [n]
   float* phi_new32;   // [nhop n]
   float* dU32;        // [6n]
+  float* l2lT;        // tensor-core downward pass: translation matrices (hi, lo planes), or NULL
+  float* l2lA;        // its split parents' expansions (hi, lo planes)
   // per step
   double* phi_old;    // [n]
   double* phi_new;    // [nhop n]
@@ -329,6 +332,13 @@ void fmm_child_tables(const Geo& g, const Dev& d, cudaStream_t s);  // child and
 size_t fmm_m2l_scratch_bytes(const Geo& g);
 // ev: null, or 2 (KMC_MAXL + 1) events recorded around level l's M2L product kernel (2 l, 2 l + 1)
 void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s, cudaEvent_t* ev = nullptr);
+// per-step downward pass of the mixed form's two finest levels on tcgen05 (tf32 x 3)
+int fmm_l2l_tc_first(const Geo& g);               // first level it covers, 0 if none
+size_t fmm_l2l_tc_table_floats(const Geo& g);     // l2lT size
+size_t fmm_l2l_tc_split_floats(const Geo& g);     // l2lA size
+void fmm_l2l_tc_tables(const Geo& g, const Dev& d, cudaStream_t s);  // at init, after the child tables
+bool fmm_l2l_tc(const Geo& g, const Dev& d, int l, cudaStream_t s);  // level l; false: not launched
+int tc_probe_tf32(float* out);                    // self-check of the tf32 MMA path
 bool fmm_m2l_tc_ok(const Geo& g);           // the tcgen05 M2L applies (KMC_M2L_TENSOR, p <= 14)
 int fmm_m2l_tc_rows(const Geo& g);           // its MMA N (rows of its A-slice layout), 0 if p > 14
 int fmm_m2l_tc_kchunks(const Geo& g);        // its K chunks of 64 values

@@ -1708,6 +1708,7 @@ void fmm_downward(const Geo& g, const Dev& d, int prec, cudaStream_t s) {
   else k_downward_coarse<float><<<(unsigned)coarse_cells(lc), 128, smc, s>>>(g, d, lc);
   for (int l = lc + 1; l <= g.L; l++) {
     const unsigned parents = 1u << (3 * (l - 2));
+    if (prec == 1 && fmm_l2l_tc(g, d, l, s)) continue;  // the finest levels on the tensor cores
     if (prec == 0) k_downward_par<double><<<parents, 256, smp, s>>>(g, d, l);
     else k_downward_par<float><<<parents, 256, smp, s>>>(g, d, l);
   }

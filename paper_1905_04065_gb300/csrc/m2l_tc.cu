@@ -51,9 +51,8 @@
 // TMEM and returns.
 #include "common.cuh"
 #include "kmcfmm.h"
+#include "tc.cuh"
 
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -67,64 +66,6 @@
 #define TC_MIN_SMEM (120 * 1024)  // one CTA per SM (its TMEM allocation is the whole SM's)
 #define TC_ATILE (TC_M * 128)     // A tile: 128 rows x 64 values
 
-namespace {
-
-// shared-memory matrix descriptor, K-major, 128-byte swizzle: atoms of 8 rows x
-// 128 bytes 1024 bytes apart (the stride field), the leading-byte field unused;
-// addr is the atom-aligned tile start plus 32 bytes per K step of 16
-__device__ __forceinline__ uint64_t tc_sdesc_sw128(uint32_t addr) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
-         (2ull << 61);
-}
-// byte offset of value k (0..63) of row r in a 128-byte-swizzled K-major tile
-__host__ __device__ __forceinline__ uint32_t tc_sw128(int r, int k) {
-  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 3) ^ r) & 7) << 4) + (k & 7) * 2);
-}
-// instruction descriptor of kind::f16: bf16 x bf16 -> f32, A and B K-major
-__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tc_mma(uint32_t dt, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-      "l"(a), "l"(b), "r"(id), "r"(acc)
-      : "memory");
-}
-// arrives once on the barrier when every tcgen05 operation this thread issued before has completed
-__device__ __forceinline__ void tc_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tc_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-}
-// the loaded registers pass through the wait, so no use is scheduled before it
-__device__ __forceinline__ void tc_wait_ld(uint32_t (&r)[8]) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;"
-               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
-               :
-               : "memory");
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-          "r"(dst),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_addr(bar))
-      : "memory");
-}
-__device__ __forceinline__ void cp_async16_tc(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-
-
-}  // namespace
 
 // Geometry of one level's launch: target tiles are boxes of bx x by x bz
 // cells of a parity class (at most 8 x 4 x 4 = 128, the MMA's M); the cells'
@@ -166,30 +107,6 @@ __device__ __forceinline__ int tc_nfar(const TcLevel& L, const TcItem& it) {
   int n = 0, tx, ty, tz;
   for (int q = tc_q0(L, it.split); q < tc_q0(L, it.split + 1); q++) n += tc_trans(it.cls, q, tx, ty, tz);
   return n;
-}
-// bounded wait that also gives up when another role of the CTA has given up
-__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t par, volatile int* abort_flag) {
-  if (mbar_test(bar, par)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try(bar, par)) {
-    if (*abort_flag) return false;
-    if (global_ns() - t0 > KMC_WAIT_NS) {
-      *abort_flag = 1;
-      return false;
-    }
-  }
-  return true;
-}
-__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                            int c4, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
-      "%6}], [%7];" ::"r"(dst),
-      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_addr(bar))
-      : "memory");
-}
-__device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 // Persistent CTAs (one per SM) over the level's work items, warp-specialised:
@@ -387,25 +304,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // ------------------------------------------------------------------ host side
-typedef CUresult (*TcEncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// the driver's tensor-map encoder, looked up once through the runtime (no link against libcuda)
-static TcEncodeTiled tc_encode() {
-  static TcEncodeTiled fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (TcEncodeTiled)p;
-  }
-  return fn;
-}
-
 // x8 column groups per thread half: NN = 16 * nc8 >= 2P (0: p too large for one MMA N)
 static int tc_nc8(const Geo& g) {
   const int c = (2 * g.P + 15) / 16;
@@ -575,8 +473,10 @@ static unsigned short tc_bf16_int(int v) {
 static int tc_probe_a(int r, int k) { return (r * 7 + k * 3) % 17 - 8; }
 static int tc_probe_b(int n, int k) { return (n * 5 + k * 11) % 13 - 6; }
 
-int kmc_check_tensor_mma(int device, float* out) {
+int kmc_check_tensor_mma(int device, int kind, float* out) {
   if (cudaSetDevice(device) != cudaSuccess) return -KMC_ERR_CUDA;
+  if (kind == 1) return tc_probe_tf32(out);
+  if (kind != 0) return -KMC_ERR_ARG;
   const TcEncodeTiled enc = tc_encode();
   if (!enc) return -KMC_ERR_CUDA;
   static unsigned short hA[TC_M * 64], hB[TC_PROBE_N * 64];

@@ -254,6 +254,7 @@ void kmc_opts_default(kmc_opts* o) {
   o->bc = KMC_BC_PERIODIC;
   o->field_z = 0.0;
   o->near_cache = 0;
+  o->l2l = KMC_L2L_TENSOR;
 }
 
 const char* kmc_last_error(kmc_handle h) { return h ? h->msg : g_static_msg; }
@@ -340,6 +341,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
     return fail(h, KMC_ERR_ARG, "unknown boundary conditions");
   if (!isfinite(o.field_z)) return fail(h, KMC_ERR_ARG, "field_z must be finite");
   if (o.near_cache != 0 && o.near_cache != 1) return fail(h, KMC_ERR_ARG, "near_cache must be 0 or 1");
+  if (o.l2l != KMC_L2L_TENSOR && o.l2l != KMC_L2L_CUDA) return fail(h, KMC_ERR_ARG, "unknown downward-pass arithmetic");
   if (o.near_cache && o.lattice_edge <= 0) return fail(h, KMC_ERR_ARG, "near_cache needs lattice mode");
   // input arrays: read in the caller's memory kind, except with Dirichlet walls,
   // where the library appends the mirrors on the host first
@@ -400,6 +402,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
     if (n > (int64_t)E * E * E) return fail(h, KMC_ERR_ARG, "more charges than sites");
     g.cap = g.W * g.W * g.W;
     g.near_cache = o.near_cache;
+    g.l2l = o.l2l;
   } else {
     g.E = 0;
     g.h = 1.0;
@@ -501,6 +504,10 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
     ALLOC(d.phi_old32, sizeof(float) * n);
     ALLOC(d.phi_new32, sizeof(float) * g.nhop * n);
     ALLOC(d.dU32, sizeof(float) * g.nhop * n);
+    if (fmm_l2l_tc_first(g)) {
+      ALLOC(d.l2lT, sizeof(float) * fmm_l2l_tc_table_floats(g));
+      ALLOC(d.l2lA, sizeof(float) * fmm_l2l_tc_split_floats(g));
+    }
   }
   ALLOC(d.phi_old, sizeof(double) * n);
   ALLOC(d.phi_new, sizeof(double) * g.nhop * n);
@@ -571,6 +578,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
   if (r) return r;
   fmm_itab(g, d, s);
   fmm_child_tables(g, d, s);
+  fmm_l2l_tc_tables(g, d, s);
   fmm_lattice_sums(g, d, s);
   if (g.dirichlet) fmm_dirichlet_tables(g, d, s);
   CKLAUNCH();

@@ -93,7 +93,7 @@ def test_tensor_mma_self_check():
     its operands (cp.async pieces and one 2D TMA box, 128-byte-swizzled K-major tiles, the K step
     advanced inside the swizzle atom), equal the exact product."""
     out = np.zeros((128, 192), np.float32)
-    rc = _k().kmc_check_tensor_mma(0, out)
+    rc = _k().kmc_check_tensor_mma(0, out, kind=0)
     r, n, kk = np.arange(128)[:, None, None], np.arange(192)[None, :, None], np.arange(64)[None, None, :]
     want = (((r * 7 + kk * 3) % 17 - 8) * ((n * 5 + kk * 11) % 13 - 6)).sum(axis=2).astype(np.float32)
     bad = np.argwhere(out != want)
@@ -160,3 +160,16 @@ def test_m2l_timing_hook_leaves_the_state():
     assert total >= sum(levels.values())
     ok = m0.astype(bool)
     assert np.array_equal(m0, m1) and np.array_equal(d0[ok], d1[ok])
+
+
+def test_tensor_mma_tf32_self_check():
+    """Four tcgen05 kind::tf32 MMAs (M = 128, N = 192, K = 4 x 8) of small integers, both operands
+    staged as the tensor-core downward pass stages them (2D TMA boxes, 128-byte swizzle), equal the
+    exact product."""
+    out = np.zeros((128, 192), np.float32)
+    rc = _k().kmc_check_tensor_mma(0, out, kind=1)
+    r, n, kk = np.arange(128)[:, None, None], np.arange(192)[None, :, None], np.arange(32)[None, None, :]
+    want = (((r * 5 + kk * 7) % 23 - 11) * ((n * 3 + kk * 13) % 19 - 9)).sum(axis=2).astype(np.float32)
+    bad = np.argwhere(out != want)
+    detail = [(int(i), int(j), float(out[i, j]), float(want[i, j])) for i, j in bad[:12]]
+    assert rc == 0 and bad.size == 0, (rc, len(bad), detail)
