@@ -332,7 +332,12 @@ void fmm_child_tables(const Geo& g, const Dev& d, cudaStream_t s);  // child and
 size_t fmm_m2l_scratch_bytes(const Geo& g);
 // ev: null, or 2 (KMC_MAXL + 1) events recorded around level l's M2L product kernel (2 l, 2 l + 1)
 void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s, cudaEvent_t* ev = nullptr);
-// per-step downward pass of the mixed form's two finest levels on tcgen05 (tf32 x 3)
+// per-step downward pass of the mixed form's finest level on tcgen05 (tf32 x 3)
+// its split parents' expansions: planes hi / lo of [l2l_npad(L)][l2l_K(P)] FP32 values
+__host__ __device__ __forceinline__ int l2l_K(int P) { return 32 * ((2 * P + 31) / 32); }
+__host__ __device__ __forceinline__ int64_t l2l_npad(int L) { return ((((int64_t)1 << (3 * (L - 2))) + 127) / 128) * 128; }
+// x rounded to the nearest TF32 value (10 explicit mantissa bits; ties away from zero)
+__device__ __forceinline__ float l2l_tf32(float x) { return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u); }
 int fmm_l2l_tc_first(const Geo& g);               // first level it covers, 0 if none
 size_t fmm_l2l_tc_table_floats(const Geo& g);     // l2lT size
 size_t fmm_l2l_tc_split_floats(const Geo& g);     // l2lA size

@@ -37,15 +37,12 @@
 #define LT_TMEM_COLS 256
 #define LT_ATILE (LT_M * 128)  // one plane of the parents' tile per chunk
 
-static int lt_K(const Geo& g) { return LT_KC * ((2 * g.P + LT_KC - 1) / LT_KC); }
+static int lt_K(const Geo& g) { return l2l_K(g.P); }
 static int lt_nc8(const Geo& g) {
   const int c = (2 * g.P + 15) / 16;
   return c <= 6 ? 6 : c <= 9 ? 9 : c <= 12 ? 12 : c <= 15 ? 15 : 0;
 }
-static int64_t lt_npad(const Geo& g, int l) {  // parents of level l, padded to whole tiles
-  const int64_t np = (int64_t)1 << (3 * (l - 2));
-  return (np + LT_M - 1) / LT_M * LT_M;
-}
+static int64_t lt_npad(const Geo& g, int l) { return (void)g, l2l_npad(l); }  // parents of level l, whole tiles
 // first level on the tensor cores, 0: none.  Only the finest level with at least 4096
 // parents (256 CTAs of 128 parents x 8 children, two per SM): a level with fewer parents
 // has too few CTAs to hide the per-CTA chain of K chunks, and runs faster on the CUDA cores.
@@ -57,9 +54,8 @@ int fmm_l2l_tc_first(const Geo& g) {
 size_t fmm_l2l_tc_table_floats(const Geo& g) { return (size_t)2 * 8 * 2 * (16 * lt_nc8(g)) * lt_K(g); }
 size_t fmm_l2l_tc_split_floats(const Geo& g) { return (size_t)2 * lt_npad(g, g.L) * lt_K(g); }
 
-// x rounded to the nearest TF32 value (10 explicit mantissa bits; ties away from zero):
 // x = tf32(x) + r with |r| <= 2^-11 |x|, r exact in FP32
-__device__ __forceinline__ float lt_tf32(float x) { return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u); }
+__device__ __forceinline__ float lt_tf32(float x) { return l2l_tf32(x); }
 
 // degree and order of the stored coefficient c (c = n (n + 1) / 2 + m, 0 <= m <= n)
 __device__ __forceinline__ void lt_nm(int c, int& n, int& m) {
@@ -283,8 +279,10 @@ bool fmm_l2l_tc(const Geo& g, const Dev& d, int l, cudaStream_t s) {
   const int64_t npad = lt_npad(g, l);
   CUtensorMap amap, bmap;
   if (!lt_map(&amap, d.l2lA, K, 2 * npad, LT_M) || !lt_map(&bmap, d.l2lT, K, (int64_t)2 * 8 * 2 * N, N)) return false;
-  const int64_t nb = (npad * K + 255) / 256;
-  k_l2l_split<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, s>>>(g, d, l, npad, K, d.l2lA);
+  if (l - 1 <= KMC_DOWN_COARSE) {  // the parents' level ran in the coarse launch: split them here
+    const int64_t nb = (npad * K + 255) / 256;
+    k_l2l_split<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, s>>>(g, d, l, npad, K, d.l2lA);
+  }  // else the per-parent kernel of level l - 1 wrote the split with its outputs
   const size_t dyn = 2 * (size_t)LT_ATILE + 2 * (size_t)N * 128 + 1024;
   const dim3 grid((unsigned)(npad / LT_M), 8);
   cudaError_t e;

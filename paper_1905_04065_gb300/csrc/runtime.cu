@@ -507,6 +507,7 @@ int kmc_fmm_init(kmc_handle* out, int64_t n, const double* positions, const doub
     if (fmm_l2l_tc_first(g)) {
       ALLOC(d.l2lT, sizeof(float) * fmm_l2l_tc_table_floats(g));
       ALLOC(d.l2lA, sizeof(float) * fmm_l2l_tc_split_floats(g));
+      CK(cudaMemset(d.l2lA, 0, sizeof(float) * fmm_l2l_tc_split_floats(g)));  // the padding stays zero
     }
   }
   ALLOC(d.phi_old, sizeof(double) * n);
