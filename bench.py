@@ -188,14 +188,17 @@ def phase_rooflines(work: dict, phases: dict, E: int, L: int, N: int, p: int, nh
     fl = 8 * l2l_cmacs(p) * cells
     by = cells * P * 2 * ts * 2 + parents * P * 2 * ts  # own + write, parent once
     t = phases["downward"] * 1e-3
-    out["downward"] = {"kernels": "k_downward_coarse (levels 2-4 in one launch), k_downward_par (deeper levels)",
+    out["downward"] = {"kernels": "k_downward_coarse (levels 2-4 in one launch), k_downward_par (deeper levels); "
+                                  "the mixed form's leaf level with >= 4096 parents on tcgen05 tf32 (k_l2l_tc)",
                        "bound": "alu", "unit": "TFLOP/s", "achieved": fl / t / 1e12,
                        "peak": (fp32 if mixed else fp64) / 1e12, "frac": fl / t / (fp32 if mixed else fp64),
                        "work": f"{fl:.3e} {'FP32' if mixed else 'FP64'} flops ({l2l_cmacs(p)} complex MACs per cell, "
                                f"{cells} cells); {by / 1e6:.1f} MB",
                        "hbm_frac": by / t / hbm,
-                       "note": "L levels launched in sequence; the per-parent kernel reads its operands from "
-                               "shared memory (the binding unit), the coarse levels are latency-bound"}
+                       "note": "L levels launched in sequence; the work counts the complex MACs of the L2L "
+                               "(the tensor-core leaf level does the dense 2P x 2P products, three tf32 products "
+                               "each); the per-parent kernel is bound by shared-memory loads, the coarse levels "
+                               "and the tensor-core leaf level by latency"}
     # rates: per charge q, site, phi_old, nhop (phi_new, mask) read; nhop (dU, rate) written
     b_rates = N * (4 + 4 + ts + nhop * (ts + 1) + nhop * (ts + 8))
     t = phases["rates"] * 1e-3
