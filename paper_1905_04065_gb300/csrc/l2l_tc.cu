@@ -181,50 +181,63 @@ __global__ void __launch_bounds__(LT_THREADS, 2)
     if (used == nkc) tc_commit(&accf);
     s_used = used;
   }
-  // ---- every warp: its 32 parents' rows of the accumulator, plus the children's own expansions
+  // ---- every warp: its 32 parents' rows of the accumulator, through shared memory (the stage is
+  // free once the last MMA has completed) so that the children's rows are read and written by
+  // whole warps, plus the children's own expansions
   bool ok = tc_wait(&accf, 0, abortv);
   ok = __all_sync(0xffffffffu, ok);
+  ok = __syncthreads_and(ok);
   if (ok) {
     tc_fence_after();
-    const int r = 32 * warp + lane;
-    const int64_t par = (int64_t)tile * LT_M + r, np = (int64_t)1 << (3 * (l - 2));
-    const int nl = 1 << (l - 1), sh = l - 2, npl = nl >> 1;
-    int64_t child = -1;
-    if (par < np) {
-      const int px = (int)(par & (npl - 1)), py = (int)((par >> sh) & (npl - 1)), pz = (int)(par >> (2 * sh));
-      child = (2 * px + (o & 1)) + (int64_t)nl * ((2 * py + ((o >> 1) & 1)) + (int64_t)nl * (2 * pz + (o >> 2)));
-    }
+    constexpr int NHALF = N / 2, LD = NHALF + 1;  // columns per pass; padded row stride (floats)
+    static_assert(NHALF % 8 == 0, "whole x8 groups per pass");
+    float* T = (float*)(lt_sm + (sm0 - smem_addr(lt_sm)));  // 128 x LD floats <= the stage
     const uint32_t ta = tbase + ((uint32_t)(32 * warp) << 16);
-    float2* Pe = (float2*)d.Peff + (g.cell_off[l] + (child >= 0 ? child : 0)) * g.P;
-    const float2* own = d.Psi32 + (g.cell_off[l] + (child >= 0 ? child : 0)) * g.P;
-    // 16 columns (8 complex coefficients) per round: two TMEM loads in flight, the child's own
-    // coefficients of the next round loaded during this one
-    float2 w[8], wn[8];
+    const int r = 32 * warp + lane;
+    const int64_t np = (int64_t)1 << (3 * (l - 2));
+    const int nl = 1 << (l - 1), sh = l - 2, npl = nl >> 1, n2 = 2 * g.P;
+    for (int hf = 0; hf < 2; hf++) {
 #pragma unroll
-    for (int q = 0; q < 8; q++) w[q] = (child >= 0 && q < g.P) ? own[q] : make_float2(0.f, 0.f);
+      for (int gq = 0; gq < NHALF / 8; gq++) {
+        uint32_t v[8];
+        tc_ld8(ta + hf * NHALF + 8 * gq, v);
+        tc_wait_ld(v);
 #pragma unroll
-    for (int gq = 0; gq < NC8; gq++) {
-      uint32_t v0[8], v1[8];
-      tc_ld8(ta + 16 * gq, v0);
-      tc_ld8(ta + 16 * gq + 8, v1);
-#pragma unroll
-      for (int q = 0; q < 8; q++) {
-        const int cn = 8 * (gq + 1) + q;
-        wn[q] = (child >= 0 && gq + 1 < NC8 && cn < g.P) ? own[cn] : make_float2(0.f, 0.f);
+        for (int q = 0; q < 8; q++) T[r * LD + 8 * gq + q] = __uint_as_float(v[q]);
       }
-      tc_wait_ld(v0);
-      tc_wait_ld(v1);
-      if (child >= 0) {
+      __syncthreads();
+      // a warp per row, four rows at a time: their own coefficients all in flight before the stores
+      constexpr int NCI = (NHALF + 31) / 32;
+      for (int r0 = 4 * warp; r0 < LT_M; r0 += 4 * (LT_THREADS / 32)) {
+        int64_t cb[4];
+        float w[4][NCI];
 #pragma unroll
-        for (int q = 0; q < 8; q++) {
-          const int ci = 8 * gq + q;
-          const uint32_t* v = q < 4 ? v0 : v1;
-          if (ci < g.P)
-            Pe[ci] = make_float2(__uint_as_float(v[2 * (q & 3)]) + w[q].x, __uint_as_float(v[2 * (q & 3) + 1]) + w[q].y);
+        for (int u = 0; u < 4; u++) {
+          const int64_t par = (int64_t)tile * LT_M + r0 + u;
+          cb[u] = -1;
+          if (par < np) {
+            const int px = (int)(par & (npl - 1)), py = (int)((par >> sh) & (npl - 1)), pz = (int)(par >> (2 * sh));
+            const int64_t child = (2 * px + (o & 1)) +
+                                  (int64_t)nl * ((2 * py + ((o >> 1) & 1)) + (int64_t)nl * (2 * pz + (o >> 2)));
+            cb[u] = (g.cell_off[l] + child) * n2;
+          }
+#pragma unroll
+          for (int j = 0; j < NCI; j++) {
+            const int col = hf * NHALF + lane + 32 * j;
+            w[u][j] = (cb[u] >= 0 && lane + 32 * j < NHALF && col < n2) ? __ldg((const float*)d.Psi32 + cb[u] + col) : 0.f;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          if (cb[u] < 0) continue;
+#pragma unroll
+          for (int j = 0; j < NCI; j++) {
+            const int c = lane + 32 * j, col = hf * NHALF + c;
+            if (c < NHALF && col < n2) ((float*)d.Peff)[cb[u] + col] = T[(r0 + u) * LD + c] + w[u][j];
+          }
         }
       }
-#pragma unroll
-      for (int q = 0; q < 8; q++) w[q] = wn[q];
+      __syncthreads();
     }
   } else if (lane == 0) {
     *abortv = 1;
