@@ -333,7 +333,16 @@ size_t fmm_m2l_scratch_bytes(const Geo& g);
 // ev: null, or 2 (KMC_MAXL + 1) events recorded around level l's M2L product kernel (2 l, 2 l + 1)
 void fmm_m2l(const Geo& g, const Dev& d, void* scratch, cudaStream_t s, cudaEvent_t* ev = nullptr);
 // per-step downward pass of the mixed form's finest level on tcgen05 (tf32 x 3)
-// its split parents' expansions: planes hi / lo of [l2l_npad(L)][l2l_K(P)] FP32 values
+// its operands (the split parents' expansions, planes hi / lo of l2l_npad(L) rows x l2l_K(P)
+// values, and the translation tables) sit in blocks of `rows` rows x 32 values (block
+// (r / rows) nkc + c / 32), each block in the order of the MMA's 128-byte-swizzled K-major
+// shared-memory operand, so that one block is one contiguous TMA copy: the offset (in values)
+// of row r, column c
+__host__ __device__ __forceinline__ int64_t l2l_sw_off(int64_t r, int c, int rows, int nkc) {
+  const int64_t blk = (r / rows) * nkc + (c >> 5);
+  const int rr = (int)(r % rows), k = c & 31;
+  return blk * rows * 32 + (((rr >> 3) * 1024 + (rr & 7) * 128 + ((((k >> 2) ^ rr) & 7) << 4)) >> 2) + (k & 3);
+}
 __host__ __device__ __forceinline__ int l2l_K(int P) { return 32 * ((2 * P + 31) / 32); }
 __host__ __device__ __forceinline__ int64_t l2l_npad(int L) { return ((((int64_t)1 << (3 * (L - 2))) + 127) / 128) * 128; }
 // x rounded to the nearest TF32 value (10 explicit mantissa bits; ties away from zero)

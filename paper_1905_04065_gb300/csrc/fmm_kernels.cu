@@ -1662,11 +1662,11 @@ __device__ __forceinline__ void downward_par_blk(const Geo& g, const Dev& d, con
     v.y = ay + own.y;
     Pe[at] = v;
     if (sizeof(T) == 4 && d.l2lA && l == g.L - 1) {  // the next level's tensor-core operand: hi / lo planes
-      const int64_t K = l2l_K(g.P), row = child * K + 2 * ci, plane = l2l_npad(g.L) * K;
+      const int K = l2l_K(g.P);
+      const int64_t at2 = l2l_sw_off(child, 2 * ci, 128, K / 32), plane = l2l_npad(g.L) * K;
       const float x = (float)v.x, y = (float)v.y, hx = l2l_tf32(x), hy = l2l_tf32(y);
-      float2* A = (float2*)(d.l2lA + row);
-      A[0] = make_float2(hx, hy);
-      A[plane / 2] = make_float2(l2l_tf32(x - hx), l2l_tf32(y - hy));
+      *(float2*)(d.l2lA + at2) = make_float2(hx, hy);  // columns 2 ci, 2 ci + 1: one 8-byte pair
+      *(float2*)(d.l2lA + plane + at2) = make_float2(l2l_tf32(x - hx), l2l_tf32(y - hy));
     }
   }
 }

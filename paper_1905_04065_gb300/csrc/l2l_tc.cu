@@ -19,7 +19,8 @@
 //
 // One CTA per (tile of 128 parents, child position): thread 0 issues the TMA
 // loads of one K chunk of 32 values (hi and lo of the parents' tile and of
-// T_o, 128-byte swizzle), thread 32 issues the twelve MMAs of the chunk, and
+// T_o, each one contiguous block already in the 128-byte swizzle: 512-byte
+// rows for the TMA), thread 32 issues the twelve MMAs of the chunk, and
 // all four warps read the accumulator out (tcgen05.ld), add the child's own
 // interaction-list expansion and write its accumulated expansion.  Every wait
 // is bounded (KMC_WAIT_NS); on a timeout the CTA flags KMC_DERR_TIMEOUT, drains
@@ -69,8 +70,8 @@ __device__ __forceinline__ void lt_nm(int c, int& n, int& m) {
 __global__ void k_l2l_tables(const Geo g, const Dev d, int l, int ts, int N, int K, float* T) {
   const int o = blockIdx.y, row = blockIdx.x;
   const int ci = row >> 1, oc = row & 1;
-  float* hi = T + ((size_t)(ts * 8 + o) * 2 + 0) * N * K + (size_t)row * K;
-  float* lo = T + ((size_t)(ts * 8 + o) * 2 + 1) * N * K + (size_t)row * K;
+  float* hi = T + ((size_t)(ts * 8 + o) * 2 + 0) * N * K;  // the table's blocks, one per K chunk
+  float* lo = T + ((size_t)(ts * 8 + o) * 2 + 1) * N * K;
   const double2* Rt = d.Rch + ((int64_t)l * 8 + o) * g.P;
   int kk = 0, lo_m = 0;
   if (ci < g.P) lt_nm(ci, kk, lo_m);
@@ -95,8 +96,9 @@ __global__ void k_l2l_tables(const Geo g, const Dev d, int l, int ts, int N, int
       }
     }
     const float f = (float)v, h = lt_tf32(f);
-    hi[col] = h;
-    lo[col] = lt_tf32(f - h);
+    const int64_t at = l2l_sw_off(row, col, N, K / LT_KC);
+    hi[at] = h;
+    lo[at] = lt_tf32(f - h);
   }
 }
 
@@ -110,8 +112,9 @@ __global__ void k_l2l_split(const Geo g, const Dev d, int l, int64_t npad, int K
     const int k = (int)(e % K);
     const float x = (par < np && k < n2) ? Pe[par * n2 + k] : 0.f;
     const float h = lt_tf32(x);
-    A[e] = h;
-    A[npad * K + e] = lt_tf32(x - h);
+    const int64_t at = l2l_sw_off(par, k, LT_M, K / LT_KC);
+    A[at] = h;
+    A[npad * K + at] = lt_tf32(x - h);
   }
 }
 
@@ -156,11 +159,13 @@ __global__ void __launch_bounds__(LT_THREADS, 2)
     for (int kc = 0; kc < nkc; kc++) {
       if (kc > 0 && !tc_wait(&empty, (uint32_t)((kc - 1) & 1), abortv)) break;
       mbar_expect_tx(&full, (uint32_t)(2 * LT_ATILE + 2 * BTILE));
-      const int x = kc * LT_KC, ya = tile * LT_M, yb = (ts * 8 + o) * 2 * N;
-      tma_load_2d(sAh, &amap, x, ya, &full);
-      tma_load_2d(sAl, &amap, x, npad + ya, &full);
-      tma_load_2d(sBh, &bmap, x, yb, &full);
-      tma_load_2d(sBl, &bmap, x, yb + N, &full);
+      // one contiguous pre-swizzled block per operand plane (rows of 128 values in the maps)
+      const int ya = (tile * nkc + kc) * (LT_M * LT_KC / 128), yl = npad * K / 128;
+      const int yb = ((ts * 8 + o) * 2 * N * K + kc * N * LT_KC) / 128, ybl = N * K / 128;
+      tma_load_2d(sAh, &amap, 0, ya, &full);
+      tma_load_2d(sAl, &amap, 0, yl + ya, &full);
+      tma_load_2d(sBh, &bmap, 0, yb, &full);
+      tma_load_2d(sBl, &bmap, 0, yb + ybl, &full);
       loaded = kc + 1;
     }
   } else if (tid == 32) {  // ---- MMAs: hi hi + hi lo + lo hi per chunk
@@ -268,14 +273,15 @@ static cudaError_t lt_launch(dim3 grid, size_t dyn, cudaStream_t s, const Geo& g
   return cudaGetLastError();
 }
 
-static bool lt_map(CUtensorMap* map, float* base, int K, int64_t rows, int box_rows) {
-  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)K * sizeof(float)};
-  const cuuint32_t box[2] = {LT_KC, (cuuint32_t)box_rows};
+// rows x cols FP32 values, boxes of box_rows x box_cols; swizzled: the TMA writes the 128-byte swizzle
+static bool lt_map(CUtensorMap* map, float* base, int cols, int64_t rows, int box_cols, int box_rows, bool swizzled) {
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return tc_encode()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, swizzled ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 void fmm_l2l_tc_tables(const Geo& g, const Dev& d, cudaStream_t s) {
@@ -291,7 +297,10 @@ bool fmm_l2l_tc(const Geo& g, const Dev& d, int l, cudaStream_t s) {
   const int nc8 = lt_nc8(g), N = 16 * nc8, K = lt_K(g), ts = l - first;
   const int64_t npad = lt_npad(g, l);
   CUtensorMap amap, bmap;
-  if (!lt_map(&amap, d.l2lA, K, 2 * npad, LT_M) || !lt_map(&bmap, d.l2lT, K, (int64_t)2 * 8 * 2 * N, N)) return false;
+  // the pre-swizzled blocks as rows of 128 values: a parents' block is 32 rows, a table block N / 4
+  if (!lt_map(&amap, d.l2lA, 128, 2 * npad * K / 128, 128, LT_M * LT_KC / 128, false) ||
+      !lt_map(&bmap, d.l2lT, 128, (int64_t)2 * 8 * 2 * N * K / 128, 128, N * LT_KC / 128, false))
+    return false;
   if (l - 1 <= KMC_DOWN_COARSE) {  // the parents' level ran in the coarse launch: split them here
     const int64_t nb = (npad * K + 255) / 256;
     k_l2l_split<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, s>>>(g, d, l, npad, K, d.l2lA);
@@ -398,7 +407,7 @@ int tc_probe_tf32(float* out) {
       cudaMemcpy(dB, hB, sizeof hB, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(dO, 0xff, nout * sizeof(float)) != cudaSuccess || cudaMemset(dF, 0, sizeof(int)) != cudaSuccess)
     goto done;
-  if (!lt_map(&am, dA, 32, LT_M, LT_M) || !lt_map(&bm, dB, 32, LT_PROBE_N, LT_PROBE_N)) goto done;
+  if (!lt_map(&am, dA, 32, LT_M, 32, LT_M, true) || !lt_map(&bm, dB, 32, LT_PROBE_N, 32, LT_PROBE_N, true)) goto done;
   if (cudaFuncSetAttribute(k_tc_probe_tf32, cudaFuncAttributeMaxDynamicSharedMemorySize, LT_PROBE_SMEM) != cudaSuccess)
     goto done;
   k_tc_probe_tf32<<<1, 128, LT_PROBE_SMEM>>>(dO, dF, am, bm);
