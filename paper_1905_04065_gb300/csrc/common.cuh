@@ -289,13 +289,19 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 // wait for phase `parity` of the barrier, at most ~limit_ns; false on timeout
+// (the clock is read on every 32nd retry only: a read of %globaltimer costs more than a retry,
+// and a thread that reads it right after the phase completes wakes late)
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_test(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try(bar, parity)) {
-    if (global_ns() - t0 > limit_ns) return false;
+  uint64_t t0 = 0;
+  for (uint32_t it = 1;; it++) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 31) == 0) {
+      const uint64_t t = global_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > limit_ns) return false;
+    }
   }
-  return true;
 }
 #define KMC_WAIT_NS 1000000000ull  // one second
 

@@ -84,15 +84,20 @@ __host__ __device__ __forceinline__ uint32_t tc_sw128_32(int r, int k) {
 // bounded wait that also gives up when another role of the CTA has given up
 __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t par, volatile int* abort_flag) {
   if (mbar_test(bar, par)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try(bar, par)) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 1;; it++) {
+    if (mbar_try(bar, par)) return true;
     if (*abort_flag) return false;
-    if (global_ns() - t0 > KMC_WAIT_NS) {
-      *abort_flag = 1;
-      return false;
+    if ((it & 31) == 0) {  // the clock on every 32nd retry only (as mbar_wait_bounded)
+      const uint64_t t = global_ns();
+      if (t0 == 0) {
+        t0 = t;
+      } else if (t - t0 > KMC_WAIT_NS) {
+        *abort_flag = 1;
+        return false;
+      }
     }
   }
-  return true;
 }
 __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             int c4, uint64_t* bar) {
