@@ -155,6 +155,8 @@ __global__ void __launch_bounds__(LT_THREADS, 2)
   const uint32_t sAh = sm0, sAl = sm0 + LT_ATILE, sBh = sm0 + 2 * LT_ATILE, sBl = sBh + BTILE;
   int loaded = 0, used = 0;
   (void)used;
+  // the loading and the issuing lane each run their loop while the rest of their warp waits at
+  // __syncwarp, not in an mbarrier wait beside them
   if (tid == 0) {  // ---- loads: one K chunk at a time into the single stage
     for (int kc = 0; kc < nkc; kc++) {
       if (kc > 0 && !tc_wait(&empty, (uint32_t)((kc - 1) & 1), abortv)) break;
@@ -186,6 +188,7 @@ __global__ void __launch_bounds__(LT_THREADS, 2)
     if (used == nkc) tc_commit(&accf);
     s_used = used;
   }
+  if (warp < 2) __syncwarp();
   // ---- every warp: its 32 parents' rows of the accumulator, through shared memory (the stage is
   // free once the last MMA has completed) so that the children's rows are read and written by
   // whole warps, plus the children's own expansions
