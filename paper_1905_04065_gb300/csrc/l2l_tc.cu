@@ -1,7 +1,8 @@
-// Per-step downward pass of the mixed form's finest levels on the
-// fifth-generation tensor cores: the L2L translation of every parent's
-// accumulated local expansion to its 8 children (the downward pass of
-// Algorithm 2, translation by the child-offset regular harmonics).
+// Per-step downward pass of the mixed form's finest level (when it has at
+// least 4096 parents) on the fifth-generation tensor cores: the L2L
+// translation of every parent's accumulated local expansion to its 8 children
+// (the downward pass of Algorithm 2, translation by the child-offset regular
+// harmonics).
 //
 // For one child position o the translation is a fixed real linear map of the
 // parent's stored coefficients (P complex values, m >= 0; the m < 0 terms
@@ -18,9 +19,10 @@
 // residuals r leave about 3 2^-22 relative error per product).
 //
 // One CTA per (tile of 128 parents, child position): thread 0 issues the TMA
-// loads of one K chunk of 32 values (hi and lo of the parents' tile and of
-// T_o, each one contiguous block already in the 128-byte swizzle: 512-byte
-// rows for the TMA), thread 32 issues the twelve MMAs of the chunk, and
+// loads of one K chunk of 32 values (hi and lo of the parents' tile, written
+// by the level above's per-parent kernel with its outputs, and of T_o, each
+// one contiguous block already in the 128-byte swizzle: 512-byte rows for the
+// TMA), thread 32 issues the twelve MMAs of the chunk, and
 // all four warps read the accumulator out (tcgen05.ld), add the child's own
 // interaction-list expansion and write its accumulated expansion.  Every wait
 // is bounded (KMC_WAIT_NS); on a timeout the CTA flags KMC_DERR_TIMEOUT, drains
